@@ -1,0 +1,191 @@
+/*
+ * mlsgd.h - C ABI of the GB300 multilevel entropic-risk gradient engine.
+ *
+ * The library evaluates the per-sample hot path of the multilevel stochastic
+ * gradient method of Baumgarten, Guth, Schneiderhan and Vanzan ("Multilevel
+ * Stochastic Gradient Descent for Risk-Averse PDE-Constrained
+ * Optimization"): the random coefficient, the state and adjoint solves, the
+ * entropic weights X = exp(theta Phi) B*q, Y = exp(theta Phi)
+ * (eq:definition_Xell_Yell), the level differences (eq:delta-notation), the
+ * per-level Chan statistics (Algorithm 1, PairwiseUpdate), the multilevel
+ * gradient (eq:gradient_estimator) and the projected step
+ * (eq:gradientdescentMLMC), on one GPU.
+ *
+ * Problem (Sec. 5): D = (0,1)^3, -div(a grad y) = z with y = 0 on the
+ * boundary, a = exp(log a), log a = sigma sum_k sqrt(lambda_k) xi_k phi_k
+ * with the K largest tensor-product KL modes of the exponential covariance
+ * exp(-|x - x'| / corr_len) per coordinate, xi_k ~ N(0,1); target
+ * g = sin(pi x) sin(pi y) sin(pi z); Phi = 1/2 ||y - g||^2_{L2} (eq:cost).
+ * Discretisation: Q1 hexahedra on level l with N_l = n0 * 2^l cells per side,
+ * coefficient constant per cell (value at the cell centre); the control z is
+ * constant per cell of the control grid (level ctrl_level).
+ *
+ * Conventions shared by every entry point
+ *   - Every *_dev pointer is DEVICE memory owned by the caller (for example a
+ *     torch tensor's data_ptr()).  The library never frees caller memory.  The
+ *     library owns its scratch (grown on demand, freed by mlsgd_destroy).
+ *   - Node vectors of a grid with N cells per side hold (N+1)^3 doubles per
+ *     sample, node (i,j,k) at flat index i + (N+1)*(j + (N+1)*k), boundary
+ *     nodes included (always 0).  Cell fields hold N^3 values per sample, cell
+ *     (i,j,k) at i + N*(j + N*k).  Batched arrays are sample-major.
+ *   - `stream` is a cudaStream_t (NULL = legacy default stream).  Calls are
+ *     asynchronous on that stream unless stated otherwise.
+ *   - Every call returns a status and never aborts; mlsgd_last_error() gives
+ *     a one-line description of the last failure on that context.
+ *   - Sample identity is (seed, iteration, level, sample index): a sample's
+ *     draw xi and every per-sample result are independent of how samples are
+ *     grouped into calls.
+ */
+#ifndef MLSGD_H
+#define MLSGD_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  MLSGD_OK = 0,
+  MLSGD_EINVAL = 1,      /* bad argument (sizes, levels, NULL pointers)          */
+  MLSGD_ENOMEM = 2,      /* device scratch could not be allocated                 */
+  MLSGD_ENOCONV = 3,     /* a solve hit max_iter; per-sample status flags say which */
+  MLSGD_ENONFINITE = 4,  /* NaN/Inf in an input or a reduced result               */
+  MLSGD_ECUDA = 5,       /* CUDA runtime error                                    */
+  MLSGD_ENOTIMPL = 6
+} mlsgd_status;
+
+typedef enum { MLSGD_FP64 = 0, MLSGD_MIXED = 1 } mlsgd_precision;
+
+/* Workload and solver configuration. */
+typedef struct {
+  int n_levels;     /* levels 0..n_levels-1                                          */
+  int n0;           /* cells per side on level 0 (8 in every preset)                 */
+  int ctrl_level;   /* level whose cells carry z; must be >= every level solved      */
+  int n_modes;      /* K, number of KL modes (even)                                  */
+  double corr_len;  /* correlation length of the 1D exponential covariance           */
+  double sigma;     /* standard-deviation factor of log a                           */
+  double theta;     /* risk aversion (eq:entropic-risk)                              */
+  double alpha;     /* control cost, the paper's lambda (eq:cost)                    */
+  double rtol;      /* stop when ||b - A y||_2 <= rtol ||b||_2 (true residual, FP64) */
+  int max_iter;     /* cap on PCG iterations (FP64) or refinement steps (MIXED)      */
+  int precision;    /* mlsgd_precision                                               */
+  int inner_iters;  /* MIXED only: FP32 PCG iterations per refinement step (0 = 6)   */
+  int max_batch;    /* samples per internal chunk of mlsgd_level_gradient (0 = 256)  */
+  uint64_t seed;
+} mlsgd_config;
+
+typedef struct mlsgd_ctx mlsgd_ctx;
+
+/* Per-level statistics of the level differences, in device memory, mergeable
+ * across calls (Algorithm 1, PairwiseUpdate; Sec. 4.2 b).
+ *   field_dev   [n_ctrl_cells] FP64: sample mean of dX~ = X~_l - X~_{l-1}
+ *   scalars_dev [MLSGD_NSCALARS] FP64, see the MLSGD_S_* indices.
+ * X~ and Y~ carry the factor exp(-theta * shift): X~ = exp(theta (Phi - shift)) B*q. */
+enum {
+  MLSGD_S_COUNT = 0,   /* number of samples merged                                     */
+  MLSGD_S_SHIFT = 1,   /* shift c of this level                                        */
+  MLSGD_S_MEAN_DY = 2, /* mean of dY~                                                  */
+  MLSGD_S_S2_DY = 3,   /* sum over samples of (dY~ - mean)^2                           */
+  MLSGD_S_S2_DX = 4,   /* sum over samples of ||dX~ - mean||_U^2                       */
+  MLSGD_S_PHI_MAX = 5, /* largest Phi seen on this level (either grid)                 */
+  MLSGD_S_ITERS = 6,   /* total solver iterations spent (state + adjoint, both grids) */
+  MLSGD_S_NOCONV = 7,  /* number of solves that hit max_iter                           */
+  MLSGD_NSCALARS = 8
+};
+typedef struct {
+  int level;
+  double* field_dev;
+  double* scalars_dev;
+} mlsgd_level_stats;
+
+/* Result of mlsgd_step (host memory). */
+typedef struct {
+  double grad_norm;   /* ||grad J^ML||_U                                               */
+  double risk;        /* multilevel estimate of R_theta(Phi) = shift + log(E^ML[Y~])/theta */
+  double ey;          /* E^ML[Y~] at the common shift                                  */
+  double shift;       /* common shift c* = max_l c_l                                   */
+  int truncated;      /* 1 if max{1, E^ML[Y]} took the value 1                         */
+  double err_sam;     /* eq:mse-estimate-mlmc sampling part                            */
+  double err_num;     /* eq:squared-bias-estimate-mlmc                                 */
+  double alpha_hat;   /* fitted weak rate                                              */
+  double eps2;        /* (eta ||grad||)^2                                              */
+  int next_levels;    /* L_{k+1} (eq:optimal-level)                                    */
+  int64_t next_counts[16]; /* M_{k+1,l} (eq:optimal-batch-size)                         */
+} mlsgd_step_report;
+
+/* Create a context on the current CUDA device.  Builds the KL mode table on
+ * the host and uploads the 1D mode tables.  Returns MLSGD_EINVAL for an
+ * inconsistent configuration (n_modes odd or < 2, ctrl_level outside
+ * [0, n_levels), n_levels > 16, non-positive corr_len / rtol). */
+mlsgd_status mlsgd_create(const mlsgd_config* cfg, mlsgd_ctx** out);
+void mlsgd_destroy(mlsgd_ctx* ctx);
+const char* mlsgd_last_error(const mlsgd_ctx* ctx);
+const char* mlsgd_status_string(mlsgd_status s);
+
+/* Number of control cells (n0 * 2^ctrl_level)^3 and of selected 1D KL modes. */
+int64_t mlsgd_n_ctrl_cells(const mlsgd_ctx* ctx);
+/* Bytes of library scratch one chunk of n_samples at `level` needs (both
+ * grids of the level difference); used for admission by HBM footprint. */
+size_t mlsgd_workspace_bytes(const mlsgd_ctx* ctx, int level, int n_samples);
+
+/* Copy the KL mode table to host arrays (each may be NULL):
+ * idx [3*n_modes] 1D mode indices (x, y, z) of each 3D mode, lam [n_modes]
+ * lambda_i lambda_j lambda_k.  Returns the number of 1D modes used. */
+int mlsgd_mode_table(const mlsgd_ctx* ctx, int* idx, double* lam);
+
+/* a1 + a2: draw xi^(m, level) for samples first_sample .. first_sample+n_samples-1
+ * of optimisation step `iter` and write log a at the cell centres of grid
+ * level `grid` (grid == level or level - 1: the same draw on both grids,
+ * eq:shorthand-notation).  xi_dev (optional, may be NULL) receives
+ * [n_samples][n_modes] normals; log_a_dev receives [n_samples][N_grid^3]. */
+mlsgd_status mlsgd_sample_field(mlsgd_ctx* ctx, int iter, int level, int grid, int64_t first_sample,
+                                int n_samples, double* xi_dev, double* log_a_dev, void* stream);
+
+/* a3..a6: for each sample s, with a = exp(log_a_dev[s]) on grid level `grid`:
+ * solve the state problem A y = B z (eq:sys), Phi = 1/2 (y - g_h)^T M (y - g_h)
+ * (eq:cost with the nodal interpolant g_h and the Q1 mass M), and the adjoint
+ * problem A q = M (y - g_h) (Sec. 2.2 adjoint equation; A is symmetric).
+ * Inputs: log_a_dev [n_samples][N^3], z_dev [n_ctrl_cells].
+ * Outputs: y_dev, q_dev [n_samples][(N+1)^3]; phi_dev [n_samples];
+ * iters_dev [n_samples] PCG iterations (FP64) or inner iterations (MIXED),
+ * state + adjoint; status_dev [n_samples] 0 = converged, 1 = hit max_iter.
+ * Returns MLSGD_ENOCONV (after writing every output) if any solve hit max_iter. */
+mlsgd_status mlsgd_solve_state_adjoint(mlsgd_ctx* ctx, int grid, int n_samples, const double* log_a_dev,
+                                       const double* z_dev, double* y_dev, double* q_dev, double* phi_dev,
+                                       int* iters_dev, int* status_dev, void* stream);
+
+/* a1..a9 for one level: samples first_sample .. first_sample+n_samples-1 of
+ * step `iter` on `level` (and level-1 on the same draw when level > 0):
+ * fields, state and adjoint solves, B*q at the control-cell centres, shifted
+ * weights, dX~ = X~_l - X~_{l-1}, dY~, and the Chan merge of this batch into
+ * *stats (which must have been reset with mlsgd_stats_reset or hold earlier
+ * batches of the same level).  The shift becomes max(old shift, max Phi of the
+ * batch) and older sums are rescaled to it. */
+mlsgd_status mlsgd_level_gradient(mlsgd_ctx* ctx, int iter, int level, int64_t first_sample, int n_samples,
+                                  const double* z_dev, mlsgd_level_stats* stats, void* stream);
+
+/* Zero a statistics record (count 0, shift -inf). */
+mlsgd_status mlsgd_stats_reset(mlsgd_ctx* ctx, mlsgd_level_stats* stats, void* stream);
+/* Merge src into dst (both of the same level): Chan update with rescaling
+ * to the larger shift.  dst and src may live on different contexts of the
+ * same workload. */
+mlsgd_status mlsgd_stats_merge(mlsgd_ctx* ctx, mlsgd_level_stats* dst, const mlsgd_level_stats* src,
+                               void* stream);
+
+/* a10 + a11: combine levels 0..n_levels-1 (stats[l] of level l) into
+ * E^ML[X~], E^ML[Y~] at the common shift (eq:ml_estimator_numerator/denominator),
+ * grad = E^ML[X~] / max{exp(-theta c*), E^ML[Y~]} + alpha z (eq:gradient_estimator
+ * with its truncation), z <- z - tau grad (eq:gradientdescentMLMC; U_ad = U, so
+ * the projection is the identity), and fill *rep including the adaptive plan
+ * for the next step (eq:sec-order-sum .. eq:mse-estimate-mlmc) with eta and
+ * the level cap `max_levels`.  grad_dev (optional) receives the gradient.
+ * SYNCHRONOUS: returns after the report has been read back. */
+mlsgd_status mlsgd_step(mlsgd_ctx* ctx, const mlsgd_level_stats* stats, int n_levels, double tau, double eta,
+                        int max_levels, double* z_dev, double* grad_dev, mlsgd_step_report* rep, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MLSGD_H */

@@ -1,0 +1,521 @@
+// api.cu - the C ABI of libmlsgd (declared in include/mlsgd.h).
+//
+// Orchestrates one level's batch of samples: draw xi (row a1), fields on the
+// level and its coarse partner (a2), B z (a3), state solve (a4), Phi and the
+// adjoint right-hand side (a5), adjoint solve (a6), B*q, weights, level
+// differences and the Chan merge (a7-a9); the multilevel combine, projected
+// step (a10) and the adaptive plan (a11, host).
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "kernels.h"
+#include "kl_table.h"
+#include "mlsgd.h"
+
+using namespace mlsgd;
+
+struct mlsgd_ctx {
+  mlsgd_config cfg;
+  std::string err;
+  KLTable kl;
+  int n1x = 0;
+  int* d_iy = nullptr;
+  int* d_iz = nullptr;
+  double* d_scale = nullptr;
+  int* d_order = nullptr;
+  int* d_offs = nullptr;
+  std::vector<double*> d_phi;  // per level: [n1d][N] at cell centres
+  char* ws = nullptr;
+  size_t ws_size = 0;
+  int* count_host = nullptr;
+  double* host_buf = nullptr;  // pinned, for small read-backs
+  ModeTable mt() const {
+    ModeTable m;
+    m.iy = d_iy; m.iz = d_iz; m.scale = d_scale; m.order = d_order; m.offs = d_offs;
+    m.n1x = n1x; m.n1d = kl.n1d;
+    return m;
+  }
+  int N(int l) const { return cfg.n0 << l; }
+  int Nc() const { return cfg.n0 << cfg.ctrl_level; }
+  bool mixed() const { return cfg.precision == MLSGD_MIXED; }
+};
+
+namespace {
+
+mlsgd_status fail(mlsgd_ctx* c, mlsgd_status s, const std::string& msg) {
+  if (c) c->err = msg;
+  return s;
+}
+
+#define CK(call)                                                                          \
+  do {                                                                                    \
+    cudaError_t e_ = (call);                                                              \
+    if (e_ != cudaSuccess)                                                                \
+      return fail(ctx, MLSGD_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+
+size_t al(size_t v) { return (v + 255) & ~(size_t)255; }
+
+struct Bump {
+  char* p;
+  template <typename T>
+  T* take(size_t n) { T* r = (T*)p; p += al(n * sizeof(T)); return r; }
+};
+
+// scratch of one grid solve (solver buffers, y, badj, b, r64)
+size_t solve_scratch_bytes(const mlsgd_ctx* ctx, int N, int S) {
+  const size_t nodes = (size_t)nodes_of(N);
+  size_t b = solver_bytes(N, S, ctx->mixed() ? 4 : 8);
+  b += 2 * al(S * nodes * 8) + al(nodes * 8);
+  if (ctx->mixed()) b += al(S * nodes * 8);
+  return b + 4096;
+}
+size_t field_bytes(const mlsgd_ctx* ctx, int N, int S) {
+  const size_t cells = (size_t)cells_of(N);
+  return ctx->mixed() ? al(S * cells * 4) + al(S * cells * 2) : al(S * cells * 8);
+}
+// persistent per-grid results kept until the statistics kernel
+size_t grid_keep_bytes(const mlsgd_ctx* ctx, int N, int S) {
+  return field_bytes(ctx, N, S) + al((size_t)S * nodes_of(N) * 8) + al(S * 8);
+}
+size_t level_bytes(const mlsgd_ctx* ctx, int level, int S) {
+  const int N = ctx->N(level);
+  size_t b = al((size_t)S * ctx->cfg.n_modes * 8);
+  b += grid_keep_bytes(ctx, N, S);
+  if (level > 0) b += grid_keep_bytes(ctx, N / 2, S);
+  b += 2 * al((size_t)2 * S * 4);
+  b += solve_scratch_bytes(ctx, N, S);
+  const long long ncell = cells_of(ctx->Nc());
+  b += al((4 + 2 * (size_t)S) * 8) + al(((ncell + 255) / 256) * 8 + 64 * 8);
+  return b;
+}
+
+mlsgd_status ensure_ws(mlsgd_ctx* ctx, size_t bytes, cudaStream_t st) {
+  if (bytes <= ctx->ws_size) return MLSGD_OK;
+  CK(cudaStreamSynchronize(st));
+  if (ctx->ws) CK(cudaFree(ctx->ws));
+  ctx->ws = nullptr;
+  ctx->ws_size = 0;
+  if (cudaMalloc(&ctx->ws, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    ctx->ws = nullptr;
+    return fail(ctx, MLSGD_ENOMEM, "cannot allocate " + std::to_string(bytes) + " bytes of scratch");
+  }
+  ctx->ws_size = bytes;
+  return MLSGD_OK;
+}
+
+struct GridFields {
+  double* a64 = nullptr;
+  float* a32 = nullptr;
+  __nv_bfloat16* abf = nullptr;
+};
+
+GridFields carve_fields(const mlsgd_ctx* ctx, int N, int S, Bump& bp) {
+  GridFields f;
+  const size_t cells = (size_t)cells_of(N);
+  if (ctx->mixed()) { f.a32 = bp.take<float>(S * cells); f.abf = bp.take<__nv_bfloat16>(S * cells); }
+  else f.a64 = bp.take<double>(S * cells);
+  return f;
+}
+
+__global__ void k_record(const SolveScalars* __restrict__ sc, int S, int mixed, int* __restrict__ iters,
+                         int* __restrict__ status, int accumulate) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= S) return;
+  const int it = mixed ? sc[s].pad : sc[s].iters;
+  const int stv = sc[s].status;
+  iters[s] = accumulate ? iters[s] + it : it;
+  status[s] = accumulate ? (status[s] | stv) : stv;
+}
+
+// state + Phi + adjoint for S samples on grid N; scratch carved from bp (not kept)
+mlsgd_status solve_grid(mlsgd_ctx* ctx, int N, int S, const GridFields& f, const double* z, double* y, double* q,
+                        double* phi, int* iters, int* status, char* scratch, cudaStream_t st) {
+  const size_t nodes = (size_t)nodes_of(N);
+  char* p = scratch;
+  SolverBufs B;
+  carve_solver(B, N, S, ctx->mixed() ? 4 : 8, p);
+  B.count_host = ctx->count_host;
+  Bump bp{p};
+  double* badj = bp.take<double>(S * nodes);
+  double* b = bp.take<double>(nodes);
+  double* r64 = ctx->mixed() ? bp.take<double>(S * nodes) : nullptr;
+  double* ytmp = y ? y : bp.take<double>(S * nodes);
+  PcgParams prm{ctx->cfg.rtol, ctx->cfg.max_iter, 0.6, 4};
+  const int inner = ctx->cfg.inner_iters > 0 ? ctx->cfg.inner_iters : 6;
+  if (ctx->mixed()) build_hierarchy_mixed(B, f.abf, st);
+  else build_hierarchy_fp64(B, f.a64, st);
+  launch_rhs_state(z, ctx->Nc(), N, b, st);
+  cudaError_t e = ctx->mixed() ? ir_mixed(B, f.a32, f.abf, b, 0, ytmp, r64, prm, inner, st)
+                               : pcg_fp64(B, f.a64, b, 0, ytmp, prm, st);
+  CK(e);
+  k_record<<<(S + 127) / 128, 128, 0, st>>>(B.sc, S, ctx->mixed(), iters, status, 0);
+  launch_phi_adjrhs(ytmp, N, S, badj, phi, B.partial, st);
+  e = ctx->mixed() ? ir_mixed(B, f.a32, f.abf, badj, (long long)nodes, q, r64, prm, inner, st)
+                   : pcg_fp64(B, f.a64, badj, (long long)nodes, q, prm, st);
+  CK(e);
+  k_record<<<(S + 127) / 128, 128, 0, st>>>(B.sc, S, ctx->mixed(), iters, status, 1);
+  CK(cudaGetLastError());
+  return MLSGD_OK;
+}
+
+mlsgd_status make_field(mlsgd_ctx* ctx, const double* xi, int grid, int S, const GridFields& f, double* log_a,
+                        cudaStream_t st) {
+  FieldOut o{log_a, f.a64, f.a32, f.abf};
+  CK(launch_field(xi, ctx->cfg.n_modes, ctx->mt(), ctx->d_phi[grid], ctx->N(grid), S, o, st));
+  return MLSGD_OK;
+}
+
+// ---------------------------------------------------------------- adaptive plan (host)
+// Sec. 4.1 with the readings stated in the header of mlsgd.h's mlsgd_step:
+// Giles-form batch sizes, Giles bias extrapolation, least-squares rates.
+double cost_model(int n0, int l) {
+  const double N = (double)(n0 << l);
+  return (N - 1) * (N - 1) * (N - 1) * (1.0 + (l >= 1 ? 0.125 : 0.0));
+}
+double ls_slope(const std::vector<double>& x, const std::vector<double>& y) {
+  double xm = 0, ym = 0;
+  for (size_t i = 0; i < x.size(); ++i) { xm += x[i]; ym += y[i]; }
+  xm /= x.size(); ym /= y.size();
+  double num = 0, den = 0;
+  for (size_t i = 0; i < x.size(); ++i) { num += (x[i] - xm) * (y[i] - ym); den += (x[i] - xm) * (x[i] - xm); }
+  return num / den;
+}
+
+}  // namespace
+
+// ====================================================================== C ABI
+extern "C" {
+
+const char* mlsgd_status_string(mlsgd_status s) {
+  switch (s) {
+    case MLSGD_OK: return "ok";
+    case MLSGD_EINVAL: return "invalid argument";
+    case MLSGD_ENOMEM: return "out of device memory";
+    case MLSGD_ENOCONV: return "solver did not converge within max_iter";
+    case MLSGD_ENONFINITE: return "non-finite value";
+    case MLSGD_ECUDA: return "CUDA error";
+    case MLSGD_ENOTIMPL: return "not implemented";
+  }
+  return "unknown status";
+}
+
+const char* mlsgd_last_error(const mlsgd_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+mlsgd_status mlsgd_create(const mlsgd_config* cfg, mlsgd_ctx** out) {
+  if (!cfg || !out) return MLSGD_EINVAL;
+  *out = nullptr;
+  const mlsgd_config& c = *cfg;
+  if (c.n_levels < 1 || c.n_levels > 16 || c.n0 < 2 || (c.n0 & (c.n0 - 1)) != 0 || c.ctrl_level < 0 ||
+      c.ctrl_level >= c.n_levels || c.n_modes < 2 || (c.n_modes % 2) != 0 || c.n_modes > 4096 ||
+      !(c.corr_len > 0) || !(c.rtol > 0) || c.max_iter < 1 || (c.precision != MLSGD_FP64 && c.precision != MLSGD_MIXED) ||
+      (c.n0 << (c.n_levels - 1)) > 1024)
+    return MLSGD_EINVAL;
+  mlsgd_ctx* ctx = new mlsgd_ctx();
+  ctx->cfg = c;
+  if (ctx->cfg.max_batch <= 0) ctx->cfg.max_batch = 256;
+  ctx->kl = build_kl_table(c.corr_len, c.n_modes);
+  const int K = c.n_modes;
+  std::vector<int> iy(K), iz(K), order(K);
+  std::vector<double> scale(K);
+  int n1x = 0;
+  for (int k = 0; k < K; ++k) {
+    iy[k] = ctx->kl.iy[k];
+    iz[k] = ctx->kl.iz[k];
+    scale[k] = c.sigma * std::sqrt(ctx->kl.lam3[k]);
+    n1x = std::max(n1x, ctx->kl.ix[k] + 1);
+  }
+  std::vector<int> offs(n1x + 1, 0);
+  for (int k = 0; k < K; ++k) offs[ctx->kl.ix[k] + 1]++;
+  for (int i = 0; i < n1x; ++i) offs[i + 1] += offs[i];
+  std::vector<int> fill(offs.begin(), offs.end() - 1);
+  for (int k = 0; k < K; ++k) order[fill[ctx->kl.ix[k]]++] = k;
+  ctx->n1x = n1x;
+  auto up = [&](void** d, const void* h, size_t n) -> bool {
+    return cudaMalloc(d, n) == cudaSuccess && cudaMemcpy(*d, h, n, cudaMemcpyHostToDevice) == cudaSuccess;
+  };
+  bool ok = up((void**)&ctx->d_iy, iy.data(), K * sizeof(int)) && up((void**)&ctx->d_iz, iz.data(), K * sizeof(int)) &&
+            up((void**)&ctx->d_scale, scale.data(), K * sizeof(double)) &&
+            up((void**)&ctx->d_order, order.data(), K * sizeof(int)) &&
+            up((void**)&ctx->d_offs, offs.data(), (n1x + 1) * sizeof(int));
+  for (int l = 0; ok && l < c.n_levels; ++l) {
+    std::vector<double> phi = kl_cell_table(ctx->kl, ctx->N(l));
+    double* d = nullptr;
+    ok = up((void**)&d, phi.data(), phi.size() * sizeof(double));
+    ctx->d_phi.push_back(d);
+  }
+  ok = ok && cudaHostAlloc((void**)&ctx->count_host, sizeof(int), cudaHostAllocDefault) == cudaSuccess;
+  ok = ok && cudaHostAlloc((void**)&ctx->host_buf, 4096 * sizeof(double), cudaHostAllocDefault) == cudaSuccess;
+  if (!ok) {
+    cudaGetLastError();
+    mlsgd_destroy(ctx);
+    return MLSGD_ECUDA;
+  }
+  *out = ctx;
+  return MLSGD_OK;
+}
+
+void mlsgd_destroy(mlsgd_ctx* ctx) {
+  if (!ctx) return;
+  cudaFree(ctx->d_iy); cudaFree(ctx->d_iz); cudaFree(ctx->d_scale); cudaFree(ctx->d_order); cudaFree(ctx->d_offs);
+  for (double* d : ctx->d_phi) cudaFree(d);
+  if (ctx->ws) cudaFree(ctx->ws);
+  if (ctx->count_host) cudaFreeHost(ctx->count_host);
+  if (ctx->host_buf) cudaFreeHost(ctx->host_buf);
+  delete ctx;
+}
+
+int64_t mlsgd_n_ctrl_cells(const mlsgd_ctx* ctx) { return ctx ? cells_of(ctx->Nc()) : 0; }
+
+size_t mlsgd_workspace_bytes(const mlsgd_ctx* ctx, int level, int n_samples) {
+  if (!ctx || level < 0 || level >= ctx->cfg.n_levels || n_samples < 0) return 0;
+  const int S = std::min(n_samples, ctx->cfg.max_batch);
+  return level_bytes(ctx, level, S);
+}
+
+int mlsgd_mode_table(const mlsgd_ctx* ctx, int* idx, double* lam) {
+  if (!ctx) return 0;
+  for (int k = 0; k < ctx->cfg.n_modes; ++k) {
+    if (idx) { idx[3 * k] = ctx->kl.ix[k]; idx[3 * k + 1] = ctx->kl.iy[k]; idx[3 * k + 2] = ctx->kl.iz[k]; }
+    if (lam) lam[k] = ctx->kl.lam3[k];
+  }
+  return ctx->kl.n1d;
+}
+
+mlsgd_status mlsgd_sample_field(mlsgd_ctx* ctx, int iter, int level, int grid, int64_t first_sample, int n_samples,
+                                double* xi_dev, double* log_a_dev, void* stream) {
+  if (!ctx) return MLSGD_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  if (level < 0 || level >= ctx->cfg.n_levels || (grid != level && grid != level - 1) || grid < 0 || n_samples < 0 ||
+      first_sample < 0 || iter < 0 || (!log_a_dev && !xi_dev) || (n_samples > 0 && !log_a_dev && !xi_dev))
+    return fail(ctx, MLSGD_EINVAL, "mlsgd_sample_field: bad level/grid/sizes");
+  if (n_samples == 0) return MLSGD_OK;
+  const int K = ctx->cfg.n_modes;
+  double* xi = xi_dev;
+  if (!xi) {
+    mlsgd_status s = ensure_ws(ctx, al((size_t)n_samples * K * 8), st);
+    if (s != MLSGD_OK) return s;
+    xi = (double*)ctx->ws;
+  }
+  launch_draw_xi(ctx->cfg.seed, iter, level, first_sample, n_samples, K, xi, st);
+  if (log_a_dev) {
+    GridFields none;
+    mlsgd_status s = make_field(ctx, xi, grid, n_samples, none, log_a_dev, st);
+    if (s != MLSGD_OK) return s;
+  }
+  CK(cudaGetLastError());
+  return MLSGD_OK;
+}
+
+mlsgd_status mlsgd_solve_state_adjoint(mlsgd_ctx* ctx, int grid, int n_samples, const double* log_a_dev,
+                                       const double* z_dev, double* y_dev, double* q_dev, double* phi_dev,
+                                       int* iters_dev, int* status_dev, void* stream) {
+  if (!ctx) return MLSGD_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  if (grid < 0 || grid >= ctx->cfg.n_levels || grid > ctx->cfg.ctrl_level || n_samples < 0)
+    return fail(ctx, MLSGD_EINVAL, "mlsgd_solve_state_adjoint: bad grid or sample count");
+  if (n_samples == 0) return MLSGD_OK;
+  if (!log_a_dev || !z_dev || !y_dev || !q_dev || !phi_dev || !iters_dev || !status_dev)
+    return fail(ctx, MLSGD_EINVAL, "mlsgd_solve_state_adjoint: null pointer");
+  const int N = ctx->N(grid);
+  const int S = n_samples;
+  const size_t need = field_bytes(ctx, N, S) + solve_scratch_bytes(ctx, N, S);
+  mlsgd_status s = ensure_ws(ctx, need, st);
+  if (s != MLSGD_OK) return s;
+  Bump bp{ctx->ws};
+  GridFields f = carve_fields(ctx, N, S, bp);
+  FieldOut o{nullptr, f.a64, f.a32, f.abf};
+  launch_exp_field(log_a_dev, o, (long long)S * cells_of(N), st);
+  s = solve_grid(ctx, N, S, f, z_dev, y_dev, q_dev, phi_dev, iters_dev, status_dev, bp.p, st);
+  if (s != MLSGD_OK) return s;
+  // report non-convergence (synchronous check of the status flags)
+  std::vector<int> h(S);
+  CK(cudaMemcpyAsync(h.data(), status_dev, S * sizeof(int), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  for (int v : h)
+    if (v) return fail(ctx, MLSGD_ENOCONV, "mlsgd_solve_state_adjoint: a solve hit max_iter or went non-finite");
+  return MLSGD_OK;
+}
+
+mlsgd_status mlsgd_stats_reset(mlsgd_ctx* ctx, mlsgd_level_stats* stats, void* stream) {
+  if (!ctx || !stats || !stats->field_dev || !stats->scalars_dev) return MLSGD_EINVAL;
+  launch_stats_reset(stats->field_dev, stats->scalars_dev, cells_of(ctx->Nc()), (cudaStream_t)stream);
+  CK(cudaGetLastError());
+  return MLSGD_OK;
+}
+
+mlsgd_status mlsgd_stats_merge(mlsgd_ctx* ctx, mlsgd_level_stats* dst, const mlsgd_level_stats* src, void* stream) {
+  if (!ctx || !dst || !src || dst->level != src->level) return MLSGD_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  const long long nc = cells_of(ctx->Nc());
+  mlsgd_status s = ensure_ws(ctx, al(((nc + 255) / 256 + 64) * 8), st);
+  if (s != MLSGD_OK) return s;
+  const double hc = 1.0 / ctx->Nc();
+  launch_stats_merge(dst->field_dev, dst->scalars_dev, src->field_dev, src->scalars_dev, nc, hc * hc * hc,
+                     ctx->cfg.theta, (double*)ctx->ws, st);
+  CK(cudaGetLastError());
+  return MLSGD_OK;
+}
+
+mlsgd_status mlsgd_level_gradient(mlsgd_ctx* ctx, int iter, int level, int64_t first_sample, int n_samples,
+                                  const double* z_dev, mlsgd_level_stats* stats, void* stream) {
+  if (!ctx) return MLSGD_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  if (level < 0 || level >= ctx->cfg.n_levels || level > ctx->cfg.ctrl_level || n_samples < 0 || first_sample < 0 ||
+      iter < 0 || !z_dev || !stats || !stats->field_dev || !stats->scalars_dev || stats->level != level)
+    return fail(ctx, MLSGD_EINVAL, "mlsgd_level_gradient: bad arguments");
+  if (n_samples == 0) return MLSGD_OK;
+  const int chunk = std::min(n_samples, ctx->cfg.max_batch);
+  mlsgd_status s = ensure_ws(ctx, level_bytes(ctx, level, chunk), st);
+  if (s != MLSGD_OK) return s;
+  const int N = ctx->N(level), K = ctx->cfg.n_modes;
+  for (int64_t done = 0; done < n_samples; done += chunk) {
+    const int S = (int)std::min<int64_t>(chunk, n_samples - done);
+    Bump bp{ctx->ws};
+    double* xi = bp.take<double>((size_t)S * K);
+    GridFields ff = carve_fields(ctx, N, S, bp);
+    double* qf = bp.take<double>((size_t)S * nodes_of(N));
+    double* phif = bp.take<double>(S);
+    GridFields fc;
+    double *qc = nullptr, *phic = nullptr;
+    if (level > 0) {
+      fc = carve_fields(ctx, N / 2, S, bp);
+      qc = bp.take<double>((size_t)S * nodes_of(N / 2));
+      phic = bp.take<double>(S);
+    }
+    int* iters = bp.take<int>(2 * (size_t)S);
+    int* status = bp.take<int>(2 * (size_t)S);
+    double* work = bp.take<double>(4 + 2 * (size_t)S);
+    const long long ncell = cells_of(ctx->Nc());
+    double* spartial = bp.take<double>((size_t)((ncell + 255) / 256) + 64);
+    char* scratch = bp.p;
+    launch_draw_xi(ctx->cfg.seed, iter, level, first_sample + done, S, K, xi, st);
+    s = make_field(ctx, xi, level, S, ff, nullptr, st);
+    if (s != MLSGD_OK) return s;
+    s = solve_grid(ctx, N, S, ff, z_dev, nullptr, qf, phif, iters, status, scratch, st);
+    if (s != MLSGD_OK) return s;
+    if (level > 0) {
+      s = make_field(ctx, xi, level - 1, S, fc, nullptr, st);
+      if (s != MLSGD_OK) return s;
+      s = solve_grid(ctx, N / 2, S, fc, z_dev, nullptr, qc, phic, iters + S, status + S, scratch, st);
+      if (s != MLSGD_OK) return s;
+    }
+    launch_level_stats(qf, phif, N, qc, phic, N / 2, S, ctx->Nc(), ctx->cfg.theta, stats->field_dev,
+                       stats->scalars_dev, work, spartial, iters, status, st);
+    CK(cudaGetLastError());
+  }
+  return MLSGD_OK;
+}
+
+mlsgd_status mlsgd_step(mlsgd_ctx* ctx, const mlsgd_level_stats* stats, int n_levels, double tau, double eta,
+                        int max_levels, double* z_dev, double* grad_dev, mlsgd_step_report* rep, void* stream) {
+  if (!ctx) return MLSGD_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  if (!stats || n_levels < 1 || n_levels > 16 || !z_dev || !rep || n_levels > ctx->cfg.n_levels)
+    return fail(ctx, MLSGD_EINVAL, "mlsgd_step: bad arguments");
+  for (int l = 0; l < n_levels; ++l)
+    if (stats[l].level != l || !stats[l].field_dev || !stats[l].scalars_dev)
+      return fail(ctx, MLSGD_EINVAL, "mlsgd_step: stats[l] must hold level l");
+  const double theta = ctx->cfg.theta;
+  double* hb = ctx->host_buf;
+  for (int l = 0; l < n_levels; ++l)
+    CK(cudaMemcpyAsync(hb + l * MLSGD_NSCALARS, stats[l].scalars_dev, MLSGD_NSCALARS * sizeof(double),
+                       cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  std::vector<double> sc(hb, hb + n_levels * MLSGD_NSCALARS);
+  double cstar = -INFINITY;
+  for (int l = 0; l < n_levels; ++l) {
+    if (!(sc[l * MLSGD_NSCALARS + MLSGD_S_COUNT] >= 2))
+      return fail(ctx, MLSGD_EINVAL, "mlsgd_step: every level needs at least 2 samples");
+    cstar = std::max(cstar, sc[l * MLSGD_NSCALARS + MLSGD_S_SHIFT]);
+  }
+  std::vector<double> fac(n_levels);
+  double ey = 0.0;
+  for (int l = 0; l < n_levels; ++l) {
+    fac[l] = std::exp(theta * (sc[l * MLSGD_NSCALARS + MLSGD_S_SHIFT] - cstar));
+    ey += fac[l] * sc[l * MLSGD_NSCALARS + MLSGD_S_MEAN_DY];
+  }
+  const double floor_y = std::exp(-theta * cstar);
+  const double denom = std::max(floor_y, ey);
+  if (!std::isfinite(denom) || !std::isfinite(cstar)) return fail(ctx, MLSGD_ENONFINITE, "mlsgd_step: non-finite shift");
+  const long long nc = cells_of(ctx->Nc());
+  const int nblk = (int)((nc + 255) / 256);
+  const int rows = n_levels + 2;
+  mlsgd_status s = ensure_ws(ctx, al((size_t)(rows + 1) * nblk * 8 + 64 * 8) + al(16 * 8), st);
+  if (s != MLSGD_OK) return s;
+  double* partial = (double*)ctx->ws;
+  double* dfac = (double*)(ctx->ws + al((size_t)(rows + 1) * nblk * 8 + 64 * 8));
+  CK(cudaMemcpyAsync(dfac, fac.data(), n_levels * sizeof(double), cudaMemcpyHostToDevice, st));
+  std::vector<const double*> fields(n_levels);
+  for (int l = 0; l < n_levels; ++l) fields[l] = stats[l].field_dev;
+  launch_combine_step(fields.data(), dfac, n_levels, nc, denom, ctx->cfg.alpha, tau, z_dev, grad_dev, partial, nblk,
+                      st);
+  CK(cudaGetLastError());
+  CK(cudaMemcpyAsync(hb, partial + (size_t)rows * nblk, rows * sizeof(double), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  const double hc = 1.0 / ctx->Nc(), hc3 = hc * hc * hc;
+  const double g2 = hb[0] * hc3, ex2 = hb[1] * hc3;
+  std::memset(rep, 0, sizeof(*rep));
+  rep->grad_norm = std::sqrt(g2);
+  rep->ey = ey;
+  rep->shift = cstar;
+  rep->truncated = ey < floor_y ? 1 : 0;
+  rep->risk = ey > 0 ? cstar + std::log(ey) / theta : NAN;
+  if (!std::isfinite(rep->grad_norm)) return fail(ctx, MLSGD_ENONFINITE, "mlsgd_step: non-finite gradient");
+  // ---- adaptive plan (eq:sec-order-sum .. eq:mse-estimate-mlmc; see the readings in the header)
+  const int L = n_levels;
+  const double C_hat = ex2 / (ey * ey);
+  const double eps2 = (eta * rep->grad_norm) * (eta * rep->grad_norm);
+  std::vector<double> v2(L), bias2(L), M(L), V, C;
+  for (int l = 0; l < L; ++l) {
+    const double* q = &sc[l * MLSGD_NSCALARS];
+    const double f = std::exp(2.0 * theta * q[MLSGD_S_SHIFT]);
+    v2[l] = f * (q[MLSGD_S_S2_DX] + C_hat * q[MLSGD_S_S2_DY]);
+    bias2[l] = f * (hb[2 + l] * hc3 + C_hat * q[MLSGD_S_MEAN_DY] * q[MLSGD_S_MEAN_DY]);
+    M[l] = q[MLSGD_S_COUNT];
+  }
+  double err_sam = 0.0;
+  for (int l = 0; l < L; ++l) err_sam += v2[l] / (M[l] * (M[l] - 1.0));
+  double alpha_hat = 2.0;
+  if (L - 1 >= 2) {
+    std::vector<double> x, y;
+    for (int l = 1; l < L; ++l) { x.push_back(l); y.push_back(std::log2(std::sqrt(bias2[l]))); }
+    alpha_hat = -ls_slope(x, y);
+  }
+  double err_num = 0.0;
+  for (int l = 1; l < L; ++l) {
+    const double f = (std::pow(2.0, alpha_hat) - 1.0) * std::pow(std::pow(2.0, (double)(L - 1 - l)), alpha_hat);
+    err_num = std::max(err_num, bias2[l] / (f * f));
+  }
+  for (int l = 0; l < L; ++l) { V.push_back(v2[l] / (M[l] - 1.0)); C.push_back(cost_model(ctx->cfg.n0, l)); }
+  const int cap = std::min(max_levels, ctx->cfg.n_levels);
+  const int Lnext = (err_num > eps2 / 2.0 && L < cap) ? L + 1 : L;
+  if (Lnext > L) {
+    double beta = 4.0;
+    if (L - 1 >= 2) {
+      std::vector<double> x, y;
+      for (int l = 1; l < L; ++l) { x.push_back(l); y.push_back(std::log2(V[l])); }
+      beta = -ls_slope(x, y);
+    }
+    V.push_back(V[L - 1] * std::pow(2.0, -beta));
+    C.push_back(cost_model(ctx->cfg.n0, L));
+  }
+  double total = 0.0;
+  for (int l = 0; l < Lnext; ++l) total += std::sqrt(V[l] * C[l]);
+  rep->err_sam = err_sam;
+  rep->err_num = err_num;
+  rep->alpha_hat = alpha_hat;
+  rep->eps2 = eps2;
+  rep->next_levels = Lnext;
+  for (int l = 0; l < Lnext && l < 16; ++l) {
+    const double m = std::ceil(2.0 / eps2 * std::sqrt(V[l] / C[l]) * total);
+    rep->next_counts[l] = (int64_t)std::max(2.0, std::min(m, 9.0e15));
+  }
+  return MLSGD_OK;
+}
+
+}  // extern "C"

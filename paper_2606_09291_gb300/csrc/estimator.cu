@@ -1,0 +1,376 @@
+// estimator.cu - right-hand sides, Phi, B*q, entropic weights, level
+// differences, Chan statistics and the multilevel step (rows a3, a5, a7-a10).
+#include <math.h>
+
+#include "internal.cuh"
+#include "kernels.h"
+
+namespace mlsgd {
+
+// (B z)_n = int z phi_n = h_c^3 sum_c z_c phi_n(x_c) over the control cells c in
+// the support of phi_n (<B u, v> = int u v, Sec. 5; the midpoint rule is exact
+// for the multilinear phi_n on a control cell).  Control grid Nc = N * r.
+__global__ void k_rhs_state(const double* __restrict__ z, int Nc, int N, double* __restrict__ b) {
+  const int n1 = N + 1;
+  const long long nodes = (long long)n1 * n1 * n1;
+  const long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= nodes) return;
+  int i, j, k;
+  node_ijk(n, n1, i, j, k);
+  double acc = 0.0;
+  if (interior(i, j, k, N)) {
+    const int r = Nc / N;
+    const double inv_r = 1.0 / r;
+    for (int cz = r * (k - 1); cz < r * (k + 1); ++cz) {
+      const double wz = 1.0 - fabs((cz + 0.5) * inv_r - k);
+      for (int cy = r * (j - 1); cy < r * (j + 1); ++cy) {
+        const double wy = 1.0 - fabs((cy + 0.5) * inv_r - j);
+        const double* zr = z + (long long)Nc * (cy + (long long)Nc * cz);
+        double row = 0.0;
+        for (int cx = r * (i - 1); cx < r * (i + 1); ++cx) row += zr[cx] * (1.0 - fabs((cx + 0.5) * inv_r - i));
+        acc += wz * wy * row;
+      }
+    }
+    const double hc = 1.0 / Nc;
+    acc *= hc * hc * hc;
+  }
+  b[n] = acc;
+}
+
+void launch_rhs_state(const double* z, int Nc, int N, double* b, cudaStream_t st) {
+  k_rhs_state<<<node_blocks(N), kBlock, 0, st>>>(z, Nc, N, b);
+}
+
+// e = y - g_h with g_h the nodal interpolant of sin(pi x) sin(pi y) sin(pi z);
+// (M e)_n with the consistent Q1 mass M = (h/6)^3 [1 4 1]^(x3); badj = M e on
+// interior rows (adjoint right-hand side <y - g, v>_H, Sec. 2.2) and
+// Phi = 1/2 e^T M e (eq:cost), reduced per sample in FP64.
+__global__ void k_phi_adjrhs(const double* __restrict__ y, int N, double* __restrict__ badj,
+                             double* __restrict__ partial) {
+  const int s = blockIdx.y;
+  const int n1 = N + 1;
+  const long long nodes = (long long)n1 * n1 * n1;
+  const long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const double* ys = y + s * nodes;
+  double contrib = 0.0;
+  if (n < nodes) {
+    int i, j, k;
+    node_ijk(n, n1, i, j, k);
+    double me = 0.0;
+    if (interior(i, j, k, N)) {
+      const double invN = 1.0 / N;
+      double gx[3], gy[3], gz[3];
+      for (int d = -1; d <= 1; ++d) {
+        gx[d + 1] = sinpi((i + d) * invN);
+        gy[d + 1] = sinpi((j + d) * invN);
+        gz[d + 1] = sinpi((k + d) * invN);
+      }
+      for (int w = -1; w <= 1; ++w) {
+        const int kk = k + w;
+        const double mz = (w == 0) ? 4.0 : 1.0;
+        const double gzv = (kk == 0 || kk == N) ? 0.0 : gz[w + 1];
+        for (int v = -1; v <= 1; ++v) {
+          const int jj = j + v;
+          const double my = (v == 0) ? 4.0 : 1.0;
+          const double gyv = (jj == 0 || jj == N) ? 0.0 : gy[v + 1];
+          for (int u = -1; u <= 1; ++u) {
+            const int ii = i + u;
+            const double mx = (u == 0) ? 4.0 : 1.0;
+            const double gxv = (ii == 0 || ii == N) ? 0.0 : gx[u + 1];
+            const double e = ys[ii + (long long)n1 * (jj + (long long)n1 * kk)] - gxv * gyv * gzv;
+            me += mx * my * mz * e;
+          }
+        }
+      }
+      const double h6 = 1.0 / (6.0 * N);
+      me *= h6 * h6 * h6;
+      contrib = (ys[n] - gx[1] * gy[1] * gz[1]) * me;
+    }
+    badj[s * nodes + n] = me;
+  }
+  const double bs = block_sum(contrib);
+  if (threadIdx.x == 0) partial[(long long)s * gridDim.x + blockIdx.x] = bs;
+}
+
+__global__ void k_phi_finish(const double* __restrict__ partial, int nblk, int S, double* __restrict__ phi) {
+  const int s = blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (s >= S) return;
+  double v = 0.0;
+  for (int t = lane; t < nblk; t += 32) v += partial[(long long)s * nblk + t];
+  v = warp_sum(v);
+  if (lane == 0) phi[s] = 0.5 * v;
+}
+
+void launch_phi_adjrhs(const double* y, int N, int S, double* badj, double* phi, double* partial, cudaStream_t st) {
+  if (S == 0) return;
+  const int nb = node_blocks(N);
+  k_phi_adjrhs<<<dim3(nb, S), kBlock, 0, st>>>(y, N, badj, partial);
+  k_phi_finish<<<(S + 7) / 8, 256, 0, st>>>(partial, nb, S, phi);
+}
+
+// ---------------------------------------------------------------- level statistics
+// work layout: [0] shift_new, [1] scale_old = exp(theta (shift_old - shift_new)),
+// [2] n_old, [3] n_batch, [4..4+S) w_fine, [4+S..4+2S) w_coarse.
+//
+// Single block: shift, per-sample weights Y~ = exp(theta (Phi - shift)), and
+// the scalar statistics of dY~ = Y~_l - Y~_{l-1} (Welford over the batch,
+// then the Chan merge with the rescaled old sums; Algorithm 1, PairwiseUpdate).
+__global__ void k_level_scalars(const double* __restrict__ phif, const double* __restrict__ phic, int S,
+                                double theta, double* __restrict__ sc, double* __restrict__ work,
+                                const int* __restrict__ iters, const int* __restrict__ status) {
+  __shared__ double smax[kBlock / 32];
+  double m = -INFINITY;
+  for (int s = threadIdx.x; s < S; s += blockDim.x) {
+    m = fmax(m, phif[s]);
+    if (phic) m = fmax(m, phic[s]);
+  }
+  for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) smax[threadIdx.x >> 5] = m;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double bm = smax[0];
+    for (int w = 1; w < kBlock / 32; ++w) bm = fmax(bm, smax[w]);
+    const double n_old = sc[MLSGD_S_COUNT];
+    const double shift_old = sc[MLSGD_S_SHIFT];
+    const double shift = (n_old > 0.0) ? fmax(shift_old, bm) : bm;
+    work[0] = shift;
+    work[1] = (n_old > 0.0) ? exp(theta * (shift_old - shift)) : 0.0;
+    work[2] = n_old;
+    work[3] = (double)S;
+  }
+  __syncthreads();
+  const double shift = work[0];
+  for (int s = threadIdx.x; s < S; s += blockDim.x) {
+    work[4 + s] = exp(theta * (phif[s] - shift));
+    work[4 + S + s] = phic ? exp(theta * (phic[s] - shift)) : 0.0;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    // Welford over the batch in sample order
+    double mean = 0.0, s2 = 0.0;
+    for (int s = 0; s < S; ++s) {
+      const double v = work[4 + s] - work[4 + S + s];
+      const double d = v - mean;
+      mean += d / (s + 1);
+      s2 += d * (v - mean);
+    }
+    const double n_old = work[2], scale = work[1];
+    const double n = n_old + S;
+    const double mo = sc[MLSGD_S_MEAN_DY] * scale;
+    const double so = sc[MLSGD_S_S2_DY] * scale * scale;
+    const double delta = mo - mean;
+    sc[MLSGD_S_MEAN_DY] = mean + (n_old / n) * delta;
+    sc[MLSGD_S_S2_DY] = so + s2 + delta * delta * n_old * S / n;
+    sc[MLSGD_S_COUNT] = n;
+    sc[MLSGD_S_SHIFT] = shift;
+    double pmax = sc[MLSGD_S_PHI_MAX];
+    double it = 0.0, nc = 0.0;
+    for (int s = 0; s < S; ++s) {
+      pmax = fmax(pmax, fmax(phif[s], phic ? phic[s] : -INFINITY));
+    }
+    if (iters) {
+      const int nsolve = phic ? 2 * S : S;
+      for (int t = 0; t < nsolve; ++t) { it += iters[t]; nc += (status[t] != 0) ? 1.0 : 0.0; }
+    }
+    sc[MLSGD_S_PHI_MAX] = pmax;
+    sc[MLSGD_S_ITERS] += it;
+    sc[MLSGD_S_NOCONV] += nc;
+  }
+}
+
+// value of the nodal function q (grid N) at the centre of control cell (cx, cy, cz)
+__device__ __forceinline__ double eval_at_ctrl(const double* __restrict__ q, int N, int r, int cx, int cy, int cz) {
+  const int n1 = N + 1;
+  const int ex = cx / r, ey = cy / r, ez = cz / r;
+  const double tx = ((cx % r) + 0.5) / r, ty = ((cy % r) + 0.5) / r, tz = ((cz % r) + 0.5) / r;
+  const double* b = q + ex + (long long)n1 * (ey + (long long)n1 * ez);
+  const long long sy = n1, sz = (long long)n1 * n1;
+  const double c00 = b[0] * (1 - tx) + b[1] * tx;
+  const double c10 = b[sy] * (1 - tx) + b[sy + 1] * tx;
+  const double c01 = b[sz] * (1 - tx) + b[sz + 1] * tx;
+  const double c11 = b[sy + sz] * (1 - tx) + b[sy + sz + 1] * tx;
+  return (c00 * (1 - ty) + c10 * ty) * (1 - tz) + (c01 * (1 - ty) + c11 * ty) * tz;
+}
+
+// One thread per control cell: B*q at the cell centre for both grids
+// ((B*q)_c = q(x_c)), dX~_s = w_f[s] B*q_f[s] - w_c[s] B*q_c[s], Welford over
+// the batch, Chan merge with the rescaled old mean; block partials of
+// h_c^3 (M2_batch + delta^2 n_old S / n).
+__global__ void k_level_field(const double* __restrict__ qf, int Nf, const double* __restrict__ qc, int Ncs, int S,
+                              int Nc, const double* __restrict__ work, double* __restrict__ field,
+                              double* __restrict__ partial) {
+  const long long ncell = (long long)Nc * Nc * Nc;
+  const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  double contrib = 0.0;
+  if (c < ncell) {
+    const int cx = (int)(c % Nc), cy = (int)((c / Nc) % Nc), cz = (int)(c / ((long long)Nc * Nc));
+    const long long nf = nodes_of(Nf), ncn = qc ? nodes_of(Ncs) : 0;
+    const int rf = Nc / Nf, rc = qc ? Nc / Ncs : 1;
+    const double* wf = work + 4;
+    const double* wc = work + 4 + S;
+    double mean = 0.0, m2 = 0.0;
+    for (int s = 0; s < S; ++s) {
+      double v = wf[s] * eval_at_ctrl(qf + s * nf, Nf, rf, cx, cy, cz);
+      if (qc) v -= wc[s] * eval_at_ctrl(qc + s * ncn, Ncs, rc, cx, cy, cz);
+      const double d = v - mean;
+      mean += d / (s + 1);
+      m2 += d * (v - mean);
+    }
+    const double n_old = work[2], scale = work[1];
+    const double n = n_old + S;
+    const double mo = (n_old > 0.0) ? field[c] * scale : 0.0;
+    const double delta = mo - mean;
+    field[c] = mean + (n_old / n) * delta;
+    const double hc = 1.0 / Nc;
+    contrib = hc * hc * hc * (m2 + delta * delta * n_old * S / n);
+  }
+  const double bs = block_sum(contrib);
+  if (threadIdx.x == 0) partial[blockIdx.x] = bs;
+}
+
+// s2_dx = old * scale^2 + sum of partials (fixed order, one warp)
+__global__ void k_level_finish(const double* __restrict__ partial, int nblk, const double* __restrict__ work,
+                               double* __restrict__ sc) {
+  const int lane = threadIdx.x;
+  double v = 0.0;
+  for (int t = lane; t < nblk; t += 32) v += partial[t];
+  v = warp_sum(v);
+  if (lane == 0) {
+    const double scale = work[1];
+    sc[MLSGD_S_S2_DX] = (work[2] > 0.0 ? sc[MLSGD_S_S2_DX] * scale * scale : 0.0) + v;
+  }
+}
+
+void launch_level_stats(const double* qf, const double* phif, int Nf, const double* qc, const double* phic,
+                        int Ncoarse, int S, int Nc, double theta, double* field, double* scalars, double* work,
+                        double* partial, const int* iters, const int* status, cudaStream_t st) {
+  if (S == 0) return;
+  k_level_scalars<<<1, kBlock, 0, st>>>(phif, phic, S, theta, scalars, work, iters, status);
+  const long long ncell = (long long)Nc * Nc * Nc;
+  const int nblk = (int)((ncell + kBlock - 1) / kBlock);
+  k_level_field<<<nblk, kBlock, 0, st>>>(qf, Nf, qc, Ncoarse, S, Nc, work, field, partial);
+  k_level_finish<<<1, 32, 0, st>>>(partial, nblk, work, scalars);
+}
+
+__global__ void k_stats_reset(double* __restrict__ field, double* __restrict__ sc, long long n) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) field[i] = 0.0;
+  if (i < MLSGD_NSCALARS) sc[i] = (i == MLSGD_S_SHIFT || i == MLSGD_S_PHI_MAX) ? -INFINITY : 0.0;
+}
+
+void launch_stats_reset(double* field, double* scalars, long long ncells, cudaStream_t st) {
+  const long long n = ncells > MLSGD_NSCALARS ? ncells : MLSGD_NSCALARS;
+  k_stats_reset<<<(unsigned)((n + kBlock - 1) / kBlock), kBlock, 0, st>>>(field, scalars, ncells);
+}
+
+// Chan merge of two statistics records: src into dst, both rescaled to the larger shift.
+__global__ void k_merge_field(double* __restrict__ df, const double* __restrict__ dsc, const double* __restrict__ sf,
+                              const double* __restrict__ ssc, long long n, double theta, double hc3,
+                              double* __restrict__ partial) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const double na = dsc[MLSGD_S_COUNT], nb = ssc[MLSGD_S_COUNT];
+  const double shift = fmax(dsc[MLSGD_S_SHIFT], ssc[MLSGD_S_SHIFT]);
+  const double fa = na > 0.0 ? exp(theta * (dsc[MLSGD_S_SHIFT] - shift)) : 0.0;
+  const double fb = nb > 0.0 ? exp(theta * (ssc[MLSGD_S_SHIFT] - shift)) : 0.0;
+  const double nt = na + nb;
+  double contrib = 0.0;
+  if (i < n && nt > 0.0) {
+    const double a = df[i] * fa, b = sf[i] * fb;
+    const double d = a - b;
+    df[i] = b + (na / nt) * d;
+    contrib = hc3 * d * d * na * nb / nt;
+  }
+  const double bs = block_sum(contrib);
+  if (threadIdx.x == 0) partial[blockIdx.x] = bs;
+}
+
+__global__ void k_merge_scalars(const double* __restrict__ partial, int nblk, double* __restrict__ dsc,
+                                const double* __restrict__ ssc, double theta) {
+  const int lane = threadIdx.x;
+  double v = 0.0;
+  for (int t = lane; t < nblk; t += 32) v += partial[t];
+  v = warp_sum(v);
+  if (lane != 0) return;
+  const double na = dsc[MLSGD_S_COUNT], nb = ssc[MLSGD_S_COUNT];
+  const double nt = na + nb;
+  if (nt <= 0.0) return;
+  const double shift = fmax(dsc[MLSGD_S_SHIFT], ssc[MLSGD_S_SHIFT]);
+  const double fa = na > 0.0 ? exp(theta * (dsc[MLSGD_S_SHIFT] - shift)) : 0.0;
+  const double fb = nb > 0.0 ? exp(theta * (ssc[MLSGD_S_SHIFT] - shift)) : 0.0;
+  const double ya = dsc[MLSGD_S_MEAN_DY] * fa, yb = ssc[MLSGD_S_MEAN_DY] * fb;
+  const double d = ya - yb;
+  dsc[MLSGD_S_MEAN_DY] = yb + (na / nt) * d;
+  dsc[MLSGD_S_S2_DY] = dsc[MLSGD_S_S2_DY] * fa * fa + ssc[MLSGD_S_S2_DY] * fb * fb + d * d * na * nb / nt;
+  dsc[MLSGD_S_S2_DX] = dsc[MLSGD_S_S2_DX] * fa * fa + ssc[MLSGD_S_S2_DX] * fb * fb + v;
+  dsc[MLSGD_S_COUNT] = nt;
+  dsc[MLSGD_S_SHIFT] = shift;
+  dsc[MLSGD_S_PHI_MAX] = fmax(dsc[MLSGD_S_PHI_MAX], ssc[MLSGD_S_PHI_MAX]);
+  dsc[MLSGD_S_ITERS] += ssc[MLSGD_S_ITERS];
+  dsc[MLSGD_S_NOCONV] += ssc[MLSGD_S_NOCONV];
+}
+
+void launch_stats_merge(double* dfield, double* dsc, const double* sfield, const double* ssc, long long ncells,
+                        double hc3, double theta, double* partial, cudaStream_t st) {
+  const int nblk = (int)((ncells + kBlock - 1) / kBlock);
+  k_merge_field<<<nblk, kBlock, 0, st>>>(dfield, dsc, sfield, ssc, ncells, theta, hc3, partial);
+  k_merge_scalars<<<1, 32, 0, st>>>(partial, nblk, dsc, ssc, theta);
+}
+
+// ---------------------------------------------------------------- combine and step
+// EX = sum_l f_l mean_l (f_l = exp(theta (c_l - c*))), grad = EX / denom + alpha z,
+// z <- z - tau grad.  partial rows: 0 = ||grad||^2, 1 = ||EX||^2, 2+l = ||mean_l||^2
+// (unscaled, counted without h_c^3).
+struct FieldList { const double* f[16]; };
+
+__global__ void k_combine_step(FieldList fl, const double* __restrict__ factors, int L, long long n, double denom,
+                               double alpha, double tau, double* __restrict__ z, double* __restrict__ grad,
+                               double* __restrict__ partial, int nblk) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  double ex = 0.0, g = 0.0;
+  double ml[16];
+  for (int l = 0; l < L; ++l) ml[l] = 0.0;
+  if (i < n) {
+    for (int l = 0; l < L; ++l) {
+      const double m = fl.f[l][i];
+      ml[l] = m * m;
+      ex += factors[l] * m;
+    }
+    const double zi = z[i];
+    g = ex / denom + alpha * zi;
+    if (grad) grad[i] = g;
+    z[i] = zi - tau * g;
+  }
+  double v = block_sum(g * g);
+  if (threadIdx.x == 0) partial[blockIdx.x] = v;
+  __syncthreads();
+  v = block_sum(ex * ex);
+  if (threadIdx.x == 0) partial[(long long)nblk + blockIdx.x] = v;
+  for (int l = 0; l < L; ++l) {
+    __syncthreads();
+    v = block_sum(ml[l]);
+    if (threadIdx.x == 0) partial[(long long)(2 + l) * nblk + blockIdx.x] = v;
+  }
+}
+
+__global__ void k_rows_finish(const double* __restrict__ partial, int nblk, int rows, double* __restrict__ out) {
+  const int r = blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (r >= rows) return;
+  double v = 0.0;
+  for (int t = lane; t < nblk; t += 32) v += partial[(long long)r * nblk + t];
+  v = warp_sum(v);
+  if (lane == 0) out[r] = v;
+}
+
+void launch_combine_step(const double* const* fields, const double* factors, int L, long long ncells, double denom,
+                         double alpha, double tau, double* z, double* grad, double* partial, int nblk,
+                         cudaStream_t st) {
+  FieldList fl;
+  for (int l = 0; l < L && l < 16; ++l) fl.f[l] = fields[l];
+  k_combine_step<<<nblk, kBlock, 0, st>>>(fl, factors, L, ncells, denom, alpha, tau, z, grad, partial, nblk);
+  const int rows = L + 2;
+  k_rows_finish<<<(rows + 7) / 8, 256, 0, st>>>(partial, nblk, rows, partial + (long long)rows * nblk);
+}
+
+}  // namespace mlsgd

@@ -1,0 +1,118 @@
+// field.cu - random input xi and the log-normal coefficient field (rows a1, a2).
+//
+// xi^(m,l) ~ N(0,1) iid over modes, samples and levels (Sec. 2.2, after
+// eq:delta-notation); the coefficient is exp of the truncated KL sum
+// log a(x) = sigma sum_k sqrt(lambda_k) xi_k phi_ix(x) phi_iy(y) phi_iz(z)
+// (Sec. 5 field model, with the exponential-covariance modes of this
+// workload) evaluated at the cell centres of the requested grid.
+#include "internal.cuh"
+#include "kernels.h"
+
+namespace mlsgd {
+
+// one thread per (sample, mode pair): counter = (pair, sample, level, iteration),
+// key = seed; Box-Muller on two 53-bit uniforms.
+__global__ void k_draw_xi(uint32_t key0, uint32_t key1, uint32_t iter, uint32_t level, long long first,
+                          int S, int K, double* __restrict__ xi) {
+  const int pairs = K / 2;
+  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (long long)S * pairs) return;
+  const int s = (int)(idx / pairs), p = (int)(idx % pairs);
+  const uint64_t sample = (uint64_t)(first + s);
+  const U4 w = philox4x32_10(U4{(uint32_t)p, (uint32_t)sample, level, iter}, key0, key1);
+  const double u1 = uniform53(w.x, w.y), u2 = uniform53(w.z, w.w);
+  const double r = sqrt(-2.0 * log(u1));
+  double sn, cs;
+  sincospi(2.0 * u2, &sn, &cs);
+  xi[(long long)s * K + 2 * p] = r * cs;
+  xi[(long long)s * K + 2 * p + 1] = r * sn;
+}
+
+void launch_draw_xi(uint64_t seed, int iter, int level, long long first, int S, int K, double* xi,
+                    cudaStream_t st) {
+  const long long n = (long long)S * (K / 2);
+  if (n == 0) return;
+  k_draw_xi<<<(unsigned)((n + kBlock - 1) / kBlock), kBlock, 0, st>>>(
+      (uint32_t)(seed & 0xffffffffu), (uint32_t)(seed >> 32), (uint32_t)iter, (uint32_t)level, first, S, K, xi);
+}
+
+// Sum-factorised synthesis.  One block per (z plane, sample):
+//   T2[i][y] = sum_{k : ix_k = i} c_k phi_{iy_k}(y) phi_{iz_k}(z),  c_k = scale_k xi_k
+//   log a(x, y, z) = sum_i T2[i][y] phi_i(x)
+// costs K N^2 + n1x N^3 FMA per sample instead of K N^3.
+// Dynamic shared memory: c[K], phi[n1d][N], T2[n1x][N] (doubles).
+__global__ void k_field(const double* __restrict__ xi, int K, const ModeTable mt, const double* __restrict__ phi,
+                        int N, FieldOut out) {
+  extern __shared__ double sm[];
+  double* c = sm;
+  double* ph = c + K;
+  double* T2 = ph + mt.n1d * N;
+  const int z = blockIdx.x, s = blockIdx.y;
+  for (int k = threadIdx.x; k < K; k += blockDim.x) c[k] = mt.scale[k] * xi[(long long)s * K + k];
+  for (int e = threadIdx.x; e < mt.n1d * N; e += blockDim.x) ph[e] = phi[e];
+  __syncthreads();
+  for (int e = threadIdx.x; e < mt.n1x * N; e += blockDim.x) {
+    const int i = e / N, y = e % N;
+    double acc = 0.0;
+    for (int t = mt.offs[i]; t < mt.offs[i + 1]; ++t) {
+      const int k = mt.order[t];
+      acc += c[k] * ph[mt.iy[k] * N + y] * ph[mt.iz[k] * N + z];
+    }
+    T2[e] = acc;
+  }
+  __syncthreads();
+  const long long cs = (long long)N * N * N;
+  const long long base = (long long)s * cs + (long long)z * N * N;
+  for (int e = threadIdx.x; e < N * N; e += blockDim.x) {
+    const int x = e % N, y = e / N;
+    double la = 0.0;
+    for (int i = 0; i < mt.n1x; ++i) la += T2[i * N + y] * ph[i * N + x];
+    const long long o = base + e;
+    if (out.log_a) out.log_a[o] = la;
+    if (out.a64 || out.a32 || out.abf) {
+      const double a = exp(la);
+      if (out.a64) out.a64[o] = a;
+      if (out.a32) out.a32[o] = (float)a;
+      if (out.abf) out.abf[o] = __float2bfloat16_rn((float)a);
+    }
+  }
+}
+
+size_t field_smem_bytes(const ModeTable& mt, int K, int N) {
+  return sizeof(double) * ((size_t)K + (size_t)mt.n1d * N + (size_t)mt.n1x * N);
+}
+
+cudaError_t launch_field(const double* xi, int K, const ModeTable& mt, const double* phi, int N, int S,
+                         const FieldOut& out, cudaStream_t st) {
+  if (S == 0) return cudaSuccess;
+  const size_t smem = field_smem_bytes(mt, K, N);
+  cudaError_t e = cudaFuncSetAttribute(k_field, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  k_field<<<dim3(N, S), kBlock, smem, st>>>(xi, K, mt, phi, N, out);
+  return cudaGetLastError();
+}
+
+// exp of a stored log field (used when the caller passes log a)
+template <typename TO>
+__global__ void k_exp_field(const double* __restrict__ la, TO* __restrict__ a, long long n) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) a[i] = (TO)exp(la[i]);
+}
+__global__ void k_exp_field_mixed(const double* __restrict__ la, float* __restrict__ a32,
+                                  __nv_bfloat16* __restrict__ abf, long long n) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) {
+    const double a = exp(la[i]);
+    a32[i] = (float)a;
+    abf[i] = __float2bfloat16_rn((float)a);
+  }
+}
+
+void launch_exp_field(const double* la, const FieldOut& out, long long n, cudaStream_t st) {
+  if (n == 0) return;
+  const unsigned g = (unsigned)((n + kBlock - 1) / kBlock);
+  if (out.a64) k_exp_field<double><<<g, kBlock, 0, st>>>(la, out.a64, n);
+  if (out.a32 && out.abf) k_exp_field_mixed<<<g, kBlock, 0, st>>>(la, out.a32, out.abf, n);
+}
+
+}  // namespace mlsgd

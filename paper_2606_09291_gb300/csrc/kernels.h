@@ -1,0 +1,110 @@
+// kernels.h - host-visible declarations of the kernel launchers of libmlsgd.
+#pragma once
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <stddef.h>
+#include <stdint.h>
+
+namespace mlsgd {
+
+// KL mode table on the device (built on the host by kl_table.cpp)
+struct ModeTable {
+  const int* iy;        // [K] y-index of each 3D mode
+  const int* iz;        // [K] z-index
+  const double* scale;  // [K] sigma * sqrt(lambda_k)
+  const int* order;     // [K] modes sorted by x-index
+  const int* offs;      // [n1x+1] start of each x-index group in `order`
+  int n1x;              // number of x-indices (max + 1)
+  int n1d;              // number of 1D modes in the phi tables
+};
+
+// outputs of the field kernel (any may be null)
+struct FieldOut {
+  double* log_a;
+  double* a64;
+  float* a32;
+  __nv_bfloat16* abf;
+};
+
+void launch_draw_xi(uint64_t seed, int iter, int level, long long first, int S, int K, double* xi, cudaStream_t st);
+cudaError_t launch_field(const double* xi, int K, const ModeTable& mt, const double* phi, int N, int S,
+                         const FieldOut& out, cudaStream_t st);
+size_t field_smem_bytes(const ModeTable& mt, int K, int N);
+void launch_exp_field(const double* la, const FieldOut& out, long long n, cudaStream_t st);
+
+// ---------------------------------------------------------------- solver
+// per-sample scalar state of a (P)CG iteration
+struct SolveScalars {
+  double bb;     // ||b||^2 of the system being solved
+  double rz;     // r . z
+  double alpha;
+  double beta;
+  double rr;     // ||r||^2
+  int active;    // 1 while iterating
+  int iters;
+  int status;    // 0 converged, 1 hit the iteration cap
+  int pad;
+};
+
+__host__ __device__ inline long long nodes_of(int N) { return (long long)(N + 1) * (N + 1) * (N + 1); }
+__host__ __device__ inline long long cells_of(int N) { return (long long)N * N * N; }
+inline int node_blocks(int N) { return (int)((nodes_of(N) + 255) / 256); }
+
+// Buffers of one batched solve on a grid with N cells per side.  Vectors are
+// [S][nodes] (stride nodes_of(N)), coefficients [S][cells].
+struct SolverBufs {
+  int N, S, J;               // MG levels j = 0..J, N_j = N >> j, N_J = 2
+  // MG hierarchy (j >= 1 coarse; j = 0 uses the caller's operator coefficient)
+  void* acoef[8];            // coefficient per MG level (j = 0: the V-cycle's own copy, may alias)
+  void* vx[8];               // V-cycle iterate per level
+  void* vt[8];               // V-cycle temporary / output per level
+  void* vr[8];               // restricted residual (j >= 1)
+  // Krylov vectors
+  void* x;                   // solution / correction
+  void* r;                   // residual
+  void* p;
+  void* q;                   // A p
+  double* partial;           // [S][blocks]
+  SolveScalars* sc;          // [S]
+  int* count;                // device counter of active samples
+  int* count_host;           // pinned host mirror
+};
+
+// FP64 batched PCG: solve A(a64) x = b for S samples (b may be shared: bstride 0)
+struct PcgParams {
+  double rtol;
+  int max_iter;
+  double omega;   // Jacobi damping of the smoother
+  int check_every;
+};
+cudaError_t pcg_fp64(SolverBufs& B, const double* a64, const double* b, long long bstride, double* x_out,
+                     const PcgParams& prm, cudaStream_t st);
+// mixed: FP64 refinement around FP32 PCG (operator a32, V-cycle on abf)
+cudaError_t ir_mixed(SolverBufs& B, const float* a32, const __nv_bfloat16* abf, const double* b,
+                     long long bstride, double* x_out, double* r64, const PcgParams& prm, int inner_iters,
+                     cudaStream_t st);
+// coefficient hierarchy for the V-cycle from the level-0 coefficient
+void build_hierarchy_fp64(SolverBufs& B, const double* a64, cudaStream_t st);
+void build_hierarchy_mixed(SolverBufs& B, const __nv_bfloat16* abf, cudaStream_t st);
+// bytes the buffers need (elem = 8 for FP64, 4 for FP32 Krylov vectors)
+size_t solver_bytes(int N, int S, int elem);
+void carve_solver(SolverBufs& B, int N, int S, int elem, char*& ptr);
+
+// ---------------------------------------------------------------- estimator
+void launch_rhs_state(const double* z, int Nc, int N, double* b, cudaStream_t st);
+// Phi = 1/2 e^T M e, badj = M e (interior rows), e = y - g_h
+void launch_phi_adjrhs(const double* y, int N, int S, double* badj, double* phi, double* partial,
+                       cudaStream_t st);
+// batch statistics of one level merged into stats (see mlsgd_level_stats)
+void launch_level_stats(const double* qf, const double* phif, int Nf, const double* qc, const double* phic,
+                        int Ncoarse, int S, int Nc, double theta, double* field, double* scalars,
+                        double* work, double* partial, const int* iters, const int* status, cudaStream_t st);
+void launch_stats_reset(double* field, double* scalars, long long ncells, cudaStream_t st);
+void launch_stats_merge(double* dfield, double* dsc, const double* sfield, const double* ssc, long long ncells,
+                        double hc3, double theta, double* partial, cudaStream_t st);
+// combine levels and step; partial gets [L + 2][blocks] sums
+void launch_combine_step(const double* const* fields, const double* factors, int L, long long ncells,
+                         double denom, double alpha, double tau, double* z, double* grad, double* partial,
+                         int nblk, cudaStream_t st);
+
+}  // namespace mlsgd

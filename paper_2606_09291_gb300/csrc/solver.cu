@@ -1,0 +1,534 @@
+// solver.cu - batched, matrix-free, geometric-multigrid-preconditioned CG for
+// the discrete state and adjoint problems (rows a4, a6).
+//
+// The paper solves its FE systems with a multigrid-preconditioned CG (Sec. 5);
+// this is a GPU design of that solver, not a port: S independent samples are
+// advanced in lock step, each with its own scalars and an `active` flag that
+// freezes it the iteration it converges, so a sample's iterates do not depend
+// on the batch it is in.  Preconditioner: one V(1,1)-cycle with damped Jacobi
+// on rediscretised Q1 operators (coarse coefficient = mean of the 8 child
+// cells), trilinear prolongation P and restriction P^T, down to 2^3 cells
+// (one unknown, solved exactly).  Stop rule: ||r||_2 <= rtol ||b||_2.
+//
+// Mixed precision: iterative refinement in FP64 (residual b - A x with x in
+// FP64 and the accurate FP32-stored coefficient) around a fixed number of FP32
+// PCG iterations whose V-cycle reads the BF16 coefficient.
+#include <algorithm>
+
+#include "internal.cuh"
+#include "kernels.h"
+
+namespace mlsgd {
+
+enum ScalarMode { SM_INIT = 0, SM_RZ0, SM_ALPHA, SM_CONV, SM_BETA, SM_OUTER_CONV, SM_INNER_BEGIN, SM_OUTER_STEP };
+
+// ---------------------------------------------------------------- vector kernels
+#define SAMPLE_GUARD(sc)                         \
+  const int s = blockIdx.y;                      \
+  if ((sc) != nullptr && !(sc)[s].active) return;
+
+template <typename T, typename TA>
+__global__ void k_apply_dot(const T* __restrict__ x, const TA* __restrict__ a, T* __restrict__ y,
+                            double* __restrict__ partial, const SolveScalars* __restrict__ sc, int N) {
+  SAMPLE_GUARD(sc);
+  const int n1 = N + 1;
+  const long long nodes = (long long)n1 * n1 * n1;
+  const long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const T* xs = x + s * nodes;
+  T contrib = T(0);
+  if (n < nodes) {
+    int i, j, k;
+    node_ijk(n, n1, i, j, k);
+    T v = T(0);
+    if (interior(i, j, k, N)) {
+      Cells8<T, TA> C;
+      C.load(a + s * (long long)N * N * N, i, j, k, N);
+      v = T(1.0 / (12.0 * N)) * q1_row(C, xs, i, j, k, n1);
+    }
+    y[s * nodes + n] = v;
+    contrib = xs[n] * v;
+  }
+  const T b = block_sum(contrib);
+  if (threadIdx.x == 0) partial[(long long)s * gridDim.x + blockIdx.x] = (double)b;
+}
+
+template <typename T>
+__global__ void k_dot(const T* __restrict__ u, const T* __restrict__ v, double* __restrict__ partial,
+                      const SolveScalars* __restrict__ sc, long long nodes) {
+  SAMPLE_GUARD(sc);
+  const long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  T contrib = T(0);
+  if (n < nodes) contrib = u[s * nodes + n] * v[s * nodes + n];
+  const T b = block_sum(contrib);
+  if (threadIdx.x == 0) partial[(long long)s * gridDim.x + blockIdx.x] = (double)b;
+}
+
+// x += alpha p; r -= alpha q; partial = r.r
+template <typename T>
+__global__ void k_update_xr(T* __restrict__ x, T* __restrict__ r, const T* __restrict__ p, const T* __restrict__ q,
+                            double* __restrict__ partial, const SolveScalars* __restrict__ sc, long long nodes) {
+  SAMPLE_GUARD(sc);
+  const long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const T al = (T)sc[s].alpha;
+  T contrib = T(0);
+  if (n < nodes) {
+    const long long o = s * nodes + n;
+    x[o] += al * p[o];
+    const T rn = r[o] - al * q[o];
+    r[o] = rn;
+    contrib = rn * rn;
+  }
+  const T b = block_sum(contrib);
+  if (threadIdx.x == 0) partial[(long long)s * gridDim.x + blockIdx.x] = (double)b;
+}
+
+template <typename T>
+__global__ void k_p_update(T* __restrict__ p, const T* __restrict__ z, const SolveScalars* __restrict__ sc,
+                           long long nodes, int first) {
+  SAMPLE_GUARD(sc);
+  const long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (n < nodes) {
+    const long long o = s * nodes + n;
+    p[o] = first ? z[o] : z[o] + (T)sc[s].beta * p[o];
+  }
+}
+
+// r = b (shared or per sample), x = 0, partial = b.b  (not masked)
+template <typename T>
+__global__ void k_init(const double* __restrict__ b, long long bstride, T* __restrict__ r, T* __restrict__ x,
+                       double* __restrict__ partial, long long nodes) {
+  const int s = blockIdx.y;
+  const long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  double contrib = 0.0;
+  if (n < nodes) {
+    const double bv = b[s * bstride + n];
+    r[s * nodes + n] = (T)bv;
+    x[s * nodes + n] = T(0);
+    contrib = bv * bv;
+  }
+  const double bs = block_sum(contrib);
+  if (threadIdx.x == 0) partial[(long long)s * gridDim.x + blockIdx.x] = bs;
+}
+
+// one warp per sample: sum the block partials in a fixed order, then the scalar update
+__global__ void k_scalar(const double* __restrict__ partial, int nblk, SolveScalars* __restrict__ sc, int S,
+                         int mode, double tol2, int max_iter, int inner_iters, const SolveScalars* __restrict__ outer) {
+  const int s = blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (s >= S) return;
+  SolveScalars& c = sc[s];
+  if (mode == SM_INNER_BEGIN) {
+    if (lane == 0) c.active = outer[s].active;
+    return;
+  }
+  if (mode == SM_OUTER_STEP) {
+    if (lane == 0 && c.active) { c.iters += 1; c.pad += inner_iters; }
+    return;
+  }
+  if (mode != SM_INIT && !c.active) return;
+  double v = 0.0;
+  for (int t = lane; t < nblk; t += 32) v += partial[(long long)s * nblk + t];
+  v = warp_sum(v);
+  if (lane != 0) return;
+  switch (mode) {
+    case SM_INIT:
+      c.bb = v; c.rr = v; c.active = (v > 0.0) ? 1 : 0; c.iters = 0; c.status = 0; c.pad = 0;
+      c.rz = 0.0; c.alpha = 0.0; c.beta = 0.0;
+      if (!(v < INFINITY)) { c.active = 0; c.status = 2; }
+      break;
+    case SM_RZ0: c.rz = v; break;
+    case SM_ALPHA: c.alpha = (v > 0.0 && c.rz != 0.0) ? c.rz / v : 0.0; break;
+    case SM_CONV:
+      c.rr = v; c.iters += 1;
+      if (v <= tol2 * c.bb) c.active = 0;
+      else if (!(v < INFINITY)) { c.active = 0; c.status = 2; }
+      else if (c.iters >= max_iter) { c.active = 0; c.status = 1; }
+      break;
+    case SM_BETA: c.beta = (c.rz != 0.0) ? v / c.rz : 0.0; c.rz = v; break;
+    case SM_OUTER_CONV:
+      c.rr = v;
+      if (v <= tol2 * c.bb) c.active = 0;
+      else if (!(v < INFINITY)) { c.active = 0; c.status = 2; }
+      else if (c.iters >= max_iter) { c.active = 0; c.status = 1; }
+      break;
+  }
+}
+
+__global__ void k_count_active(const SolveScalars* __restrict__ sc, int S, int* __restrict__ count) {
+  int v = 0;
+  for (int s = threadIdx.x; s < S; s += blockDim.x) v += sc[s].active;
+  v = block_sum(v);
+  if (threadIdx.x == 0) *count = v;
+}
+
+// ---------------------------------------------------------------- multigrid kernels
+// x = omega D^{-1} r  (pre-smoothing from a zero initial guess), D = (h/3) sum_8 a
+template <typename T, typename TA>
+__global__ void k_jacobi0(const T* __restrict__ r, const TA* __restrict__ a, T* __restrict__ x,
+                          const SolveScalars* __restrict__ sc, int N, T omega) {
+  SAMPLE_GUARD(sc);
+  const int n1 = N + 1;
+  const long long nodes = (long long)n1 * n1 * n1;
+  const long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= nodes) return;
+  int i, j, k;
+  node_ijk(n, n1, i, j, k);
+  T v = T(0);
+  if (interior(i, j, k, N)) {
+    Cells8<T, TA> C;
+    C.load(a + s * (long long)N * N * N, i, j, k, N);
+    v = omega * r[s * nodes + n] / (T(1.0 / (3.0 * N)) * C.sum);
+  }
+  x[s * nodes + n] = v;
+}
+
+// t = r - A x   (mode 0)   or   t = x + omega D^{-1} (r - A x)   (mode 1, smoothing)
+template <typename T, typename TA, int MODE>
+__global__ void k_resid_smooth(const T* __restrict__ r, const T* __restrict__ x, const TA* __restrict__ a,
+                               T* __restrict__ t, const SolveScalars* __restrict__ sc, int N, T omega) {
+  SAMPLE_GUARD(sc);
+  const int n1 = N + 1;
+  const long long nodes = (long long)n1 * n1 * n1;
+  const long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= nodes) return;
+  int i, j, k;
+  node_ijk(n, n1, i, j, k);
+  T v = T(0);
+  if (interior(i, j, k, N)) {
+    Cells8<T, TA> C;
+    C.load(a + s * (long long)N * N * N, i, j, k, N);
+    const T* xs = x + s * nodes;
+    const T res = r[s * nodes + n] - T(1.0 / (12.0 * N)) * q1_row(C, xs, i, j, k, n1);
+    v = (MODE == 0) ? res : xs[n] + omega * res / (T(1.0 / (3.0 * N)) * C.sum);
+  }
+  t[s * nodes + n] = v;
+}
+
+// coarse = P^T fine: weights 1, 1/2 per axis around (2I, 2J, 2K)
+template <typename T>
+__global__ void k_restrict(const T* __restrict__ tf, T* __restrict__ rc, const SolveScalars* __restrict__ sc,
+                           int Nc) {
+  SAMPLE_GUARD(sc);
+  const int n1c = Nc + 1, Nf = 2 * Nc, n1f = Nf + 1;
+  const long long nc = (long long)n1c * n1c * n1c, nf = (long long)n1f * n1f * n1f;
+  const long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= nc) return;
+  int I, J, K;
+  node_ijk(n, n1c, I, J, K);
+  T v = T(0);
+  if (interior(I, J, K, Nc)) {
+    const T* f = tf + s * nf + (2 * I) + (long long)n1f * (2 * J) + (long long)n1f * n1f * (2 * K);
+#pragma unroll
+    for (int w = -1; w <= 1; ++w)
+#pragma unroll
+      for (int u = -1; u <= 1; ++u)
+#pragma unroll
+        for (int q = -1; q <= 1; ++q) {
+          const T wt = T((q == 0 ? 1.0 : 0.5) * (u == 0 ? 1.0 : 0.5) * (w == 0 ? 1.0 : 0.5));
+          v += wt * f[q + (long long)n1f * u + (long long)n1f * n1f * w];
+        }
+  }
+  rc[s * nc + n] = v;
+}
+
+// fine += P coarse (trilinear)
+template <typename T>
+__global__ void k_prolong_add(T* __restrict__ xf, const T* __restrict__ ec, const SolveScalars* __restrict__ sc,
+                              int Nf) {
+  SAMPLE_GUARD(sc);
+  const int n1f = Nf + 1, Nc = Nf / 2, n1c = Nc + 1;
+  const long long nf = (long long)n1f * n1f * n1f, nc = (long long)n1c * n1c * n1c;
+  const long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= nf) return;
+  int i, j, k;
+  node_ijk(n, n1f, i, j, k);
+  if (!interior(i, j, k, Nf)) return;
+  const int i0 = i >> 1, j0 = j >> 1, k0 = k >> 1;
+  const int i1 = i0 + (i & 1), j1 = j0 + (j & 1), k1 = k0 + (k & 1);
+  const T wi = (i & 1) ? T(0.5) : T(1), wj = (j & 1) ? T(0.5) : T(1), wk = (k & 1) ? T(0.5) : T(1);
+  const T* e = ec + s * nc;
+  auto at = [&](int a, int b, int c) { return e[a + (long long)n1c * b + (long long)n1c * n1c * c]; };
+  T v;
+  if ((i & 1) == 0 && (j & 1) == 0 && (k & 1) == 0) {
+    v = at(i0, j0, k0);
+  } else {
+    v = wi * wj * wk *
+        (at(i0, j0, k0) + ((i & 1) ? at(i1, j0, k0) : T(0)) + ((j & 1) ? at(i0, j1, k0) : T(0)) +
+         ((k & 1) ? at(i0, j0, k1) : T(0)) + (((i & 1) && (j & 1)) ? at(i1, j1, k0) : T(0)) +
+         (((i & 1) && (k & 1)) ? at(i1, j0, k1) : T(0)) + (((j & 1) && (k & 1)) ? at(i0, j1, k1) : T(0)) +
+         (((i & 1) && (j & 1) && (k & 1)) ? at(i1, j1, k1) : T(0)));
+  }
+  xf[s * nf + n] += v;
+}
+
+// 2^3 cells: the single interior unknown, x = r / D; all other nodes 0
+template <typename T, typename TA>
+__global__ void k_coarsest(const T* __restrict__ r, const TA* __restrict__ a, T* __restrict__ x,
+                           const SolveScalars* __restrict__ sc, int S) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= S || (sc != nullptr && !sc[s].active)) return;
+  T* xs = x + (long long)s * 27;
+  for (int n = 0; n < 27; ++n) xs[n] = T(0);
+  Cells8<T, TA> C;
+  C.load(a + (long long)s * 8, 1, 1, 1, 2);
+  xs[13] = r[(long long)s * 27 + 13] / (T(1.0 / 6.0) * C.sum);
+}
+
+// coarse cell coefficient = mean of the 8 children
+template <typename TI, typename TO>
+__global__ void k_coarsen_coef(const TI* __restrict__ af, TO* __restrict__ ac, int Nc, int S) {
+  const long long cc = (long long)Nc * Nc * Nc;
+  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= cc * S) return;
+  const int s = (int)(idx / cc);
+  const long long c = idx % cc;
+  const int I = (int)(c % Nc), J = (int)((c / Nc) % Nc), K = (int)(c / ((long long)Nc * Nc));
+  const int Nf = 2 * Nc;
+  const TI* f = af + (long long)s * Nf * Nf * Nf;
+  double acc = 0.0;
+  for (int r = 0; r < 2; ++r)
+    for (int q = 0; q < 2; ++q)
+      for (int p = 0; p < 2; ++p)
+        acc += to_double(f[(2 * I + p) + (long long)Nf * ((2 * J + q) + (long long)Nf * (2 * K + r))]);
+  ac[idx] = (TO)(0.125 * acc);
+}
+
+// ---------------------------------------------------------------- mixed-precision kernels
+// r64 = b - A(a) x64 in FP64, partial = r.r
+template <typename TA>
+__global__ void k_residual64(const double* __restrict__ b, long long bstride, const double* __restrict__ x,
+                             const TA* __restrict__ a, double* __restrict__ r, double* __restrict__ partial,
+                             const SolveScalars* __restrict__ sc, int N) {
+  SAMPLE_GUARD(sc);
+  const int n1 = N + 1;
+  const long long nodes = (long long)n1 * n1 * n1;
+  const long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  double contrib = 0.0;
+  if (n < nodes) {
+    int i, j, k;
+    node_ijk(n, n1, i, j, k);
+    double v = 0.0;
+    if (interior(i, j, k, N)) {
+      Cells8<double, TA> C;
+      C.load(a + s * (long long)N * N * N, i, j, k, N);
+      v = b[s * bstride + n] - (1.0 / (12.0 * N)) * q1_row(C, x + s * nodes, i, j, k, n1);
+    }
+    r[s * nodes + n] = v;
+    contrib = v * v;
+  }
+  const double bs = block_sum(contrib);
+  if (threadIdx.x == 0) partial[(long long)s * gridDim.x + blockIdx.x] = bs;
+}
+
+// r32 = (float) r64, d = 0
+__global__ void k_demote(const double* __restrict__ r64, float* __restrict__ r32, float* __restrict__ d,
+                         const SolveScalars* __restrict__ sc, long long nodes) {
+  SAMPLE_GUARD(sc);
+  const long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (n < nodes) {
+    r32[s * nodes + n] = (float)r64[s * nodes + n];
+    d[s * nodes + n] = 0.0f;
+  }
+}
+
+// x64 += d
+__global__ void k_accumulate(double* __restrict__ x, const float* __restrict__ d, const SolveScalars* __restrict__ sc,
+                             long long nodes) {
+  SAMPLE_GUARD(sc);
+  const long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (n < nodes) x[s * nodes + n] += (double)d[s * nodes + n];
+}
+
+// ---------------------------------------------------------------- host side
+static inline dim3 grid_nodes(int N, int S) { return dim3((unsigned)node_blocks(N), (unsigned)S); }
+
+static size_t align_up(size_t v) { return (v + 255) & ~(size_t)255; }
+
+static int mg_levels(int N) {
+  int J = 0;
+  while ((N >> J) > 2) ++J;
+  return J;
+}
+
+size_t solver_bytes(int N, int S, int elem) {
+  size_t b = 0;
+  const int J = mg_levels(N);
+  b += 6 * align_up((size_t)S * nodes_of(N) * elem);
+  for (int j = 1; j <= J; ++j) {
+    const int Nj = N >> j;
+    b += 3 * align_up((size_t)S * nodes_of(Nj) * elem) + align_up((size_t)S * cells_of(Nj) * elem);
+  }
+  b += align_up((size_t)S * node_blocks(N) * sizeof(double));
+  b += 2 * align_up((size_t)S * sizeof(SolveScalars));
+  b += align_up(sizeof(int));
+  return b;
+}
+
+void carve_solver(SolverBufs& B, int N, int S, int elem, char*& ptr) {
+  auto take = [&](size_t n) { void* p = ptr; ptr += align_up(n); return p; };
+  B.N = N;
+  B.S = S;
+  B.J = mg_levels(N);
+  const size_t v0 = (size_t)S * nodes_of(N) * elem;
+  B.x = take(v0); B.r = take(v0); B.p = take(v0); B.q = take(v0);
+  B.vx[0] = take(v0); B.vt[0] = take(v0); B.vr[0] = nullptr; B.acoef[0] = nullptr;
+  for (int j = 1; j <= B.J; ++j) {
+    const int Nj = N >> j;
+    const size_t vj = (size_t)S * nodes_of(Nj) * elem;
+    B.vx[j] = take(vj); B.vt[j] = take(vj); B.vr[j] = take(vj);
+    B.acoef[j] = take((size_t)S * cells_of(Nj) * elem);
+  }
+  B.partial = (double*)take((size_t)S * node_blocks(N) * sizeof(double));
+  B.sc = (SolveScalars*)take((size_t)2 * S * sizeof(SolveScalars));
+  B.count = (int*)take(sizeof(int));
+}
+
+template <typename TI, typename TO>
+static void coarsen_all(SolverBufs& B, const TI* a0, cudaStream_t st) {
+  for (int j = 1; j <= B.J; ++j) {
+    const int Nc = B.N >> j;
+    const long long n = cells_of(Nc) * B.S;
+    if (j == 1)
+      k_coarsen_coef<TI, TO><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(a0, (TO*)B.acoef[1], Nc, B.S);
+    else
+      k_coarsen_coef<TO, TO><<<(unsigned)((n + 255) / 256), 256, 0, st>>>((const TO*)B.acoef[j - 1],
+                                                                          (TO*)B.acoef[j], Nc, B.S);
+  }
+}
+void build_hierarchy_fp64(SolverBufs& B, const double* a64, cudaStream_t st) { coarsen_all<double, double>(B, a64, st); }
+void build_hierarchy_mixed(SolverBufs& B, const __nv_bfloat16* abf, cudaStream_t st) {
+  coarsen_all<__nv_bfloat16, float>(B, abf, st);
+}
+
+// One V(1,1)-cycle on r0 (level-0 coefficient a0); the result is left in vt[0].
+template <typename T, typename TA0>
+static void vcycle(SolverBufs& B, const T* r0, const TA0* a0, const SolveScalars* sc, T omega, cudaStream_t st) {
+  const int S = B.S, J = B.J;
+  auto rin = [&](int j) { return j == 0 ? r0 : (const T*)B.vr[j]; };
+  for (int j = 0; j < J; ++j) {
+    const int Nj = B.N >> j;
+    if (j == 0) {
+      k_jacobi0<T, TA0><<<grid_nodes(Nj, S), kBlock, 0, st>>>(rin(0), a0, (T*)B.vx[0], sc, Nj, omega);
+      k_resid_smooth<T, TA0, 0><<<grid_nodes(Nj, S), kBlock, 0, st>>>(rin(0), (const T*)B.vx[0], a0, (T*)B.vt[0],
+                                                                      sc, Nj, omega);
+    } else {
+      const T* aj = (const T*)B.acoef[j];
+      k_jacobi0<T, T><<<grid_nodes(Nj, S), kBlock, 0, st>>>(rin(j), aj, (T*)B.vx[j], sc, Nj, omega);
+      k_resid_smooth<T, T, 0><<<grid_nodes(Nj, S), kBlock, 0, st>>>(rin(j), (const T*)B.vx[j], aj, (T*)B.vt[j], sc,
+                                                                    Nj, omega);
+    }
+    k_restrict<T><<<grid_nodes(Nj / 2, S), kBlock, 0, st>>>((const T*)B.vt[j], (T*)B.vr[j + 1], sc, Nj / 2);
+  }
+  if (J == 0)
+    k_coarsest<T, TA0><<<(S + 127) / 128, 128, 0, st>>>(rin(0), a0, (T*)B.vt[0], sc, S);
+  else
+    k_coarsest<T, T><<<(S + 127) / 128, 128, 0, st>>>(rin(J), (const T*)B.acoef[J], (T*)B.vt[J], sc, S);
+  for (int j = J - 1; j >= 0; --j) {
+    const int Nj = B.N >> j;
+    k_prolong_add<T><<<grid_nodes(Nj, S), kBlock, 0, st>>>((T*)B.vx[j], (const T*)B.vt[j + 1], sc, Nj);
+    if (j == 0)
+      k_resid_smooth<T, TA0, 1><<<grid_nodes(Nj, S), kBlock, 0, st>>>(rin(0), (const T*)B.vx[0], a0, (T*)B.vt[0],
+                                                                      sc, Nj, omega);
+    else
+      k_resid_smooth<T, T, 1><<<grid_nodes(Nj, S), kBlock, 0, st>>>(rin(j), (const T*)B.vx[j],
+                                                                    (const T*)B.acoef[j], (T*)B.vt[j], sc, Nj, omega);
+  }
+}
+
+static void scalar(SolverBufs& B, SolveScalars* sc, int mode, double tol2, int max_iter, cudaStream_t st,
+                   int inner_iters = 0, const SolveScalars* outer = nullptr) {
+  const int warps = 8;
+  k_scalar<<<(B.S + warps - 1) / warps, 32 * warps, 0, st>>>(B.partial, node_blocks(B.N), sc, B.S, mode, tol2,
+                                                              max_iter, inner_iters, outer);
+}
+
+static cudaError_t count_active(SolverBufs& B, const SolveScalars* sc, cudaStream_t st, int& n) {
+  k_count_active<<<1, kBlock, 0, st>>>(sc, B.S, B.count);
+  cudaError_t e = cudaMemcpyAsync(B.count_host, B.count, sizeof(int), cudaMemcpyDeviceToHost, st);
+  if (e != cudaSuccess) return e;
+  e = cudaStreamSynchronize(st);
+  n = *B.count_host;
+  return e;
+}
+
+// Krylov loop shared by the FP64 solve and the FP32 inner solve.
+// fixed_iters > 0: run exactly that many iterations without a stop test.
+template <typename T, typename TAop, typename TA0>
+static cudaError_t pcg_loop(SolverBufs& B, const TAop* aop, const TA0* a0, T* x, T* r, SolveScalars* sc,
+                            const PcgParams& prm, int fixed_iters, cudaStream_t st) {
+  const int S = B.S, N = B.N;
+  const long long nodes = nodes_of(N);
+  const dim3 g = grid_nodes(N, S);
+  const T omega = (T)prm.omega;
+  T* p = (T*)B.p;
+  T* q = (T*)B.q;
+  vcycle<T, TA0>(B, r, a0, sc, omega, st);
+  const T* z = (const T*)B.vt[0];
+  k_dot<T><<<g, kBlock, 0, st>>>(r, z, B.partial, sc, nodes);
+  scalar(B, sc, SM_RZ0, 0, 0, st);
+  k_p_update<T><<<g, kBlock, 0, st>>>(p, z, sc, nodes, 1);
+  const double tol2 = prm.rtol * prm.rtol;
+  const int nit = fixed_iters > 0 ? fixed_iters : prm.max_iter;
+  for (int it = 0; it < nit; ++it) {
+    k_apply_dot<T, TAop><<<g, kBlock, 0, st>>>(p, aop, q, B.partial, sc, N);
+    scalar(B, sc, SM_ALPHA, 0, 0, st);
+    k_update_xr<T><<<g, kBlock, 0, st>>>(x, r, p, q, B.partial, sc, nodes);
+    if (fixed_iters > 0) {
+      if (it == nit - 1) break;
+    } else {
+      scalar(B, sc, SM_CONV, tol2, prm.max_iter, st);
+      if ((it + 1) % prm.check_every == 0 || it + 1 == nit) {
+        int n = 0;
+        cudaError_t e = count_active(B, sc, st, n);
+        if (e != cudaSuccess) return e;
+        if (n == 0) break;
+      }
+    }
+    vcycle<T, TA0>(B, r, a0, sc, omega, st);
+    k_dot<T><<<g, kBlock, 0, st>>>(r, z, B.partial, sc, nodes);
+    scalar(B, sc, SM_BETA, 0, 0, st);
+    k_p_update<T><<<g, kBlock, 0, st>>>(p, z, sc, nodes, 0);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t pcg_fp64(SolverBufs& B, const double* a64, const double* b, long long bstride, double* x_out,
+                     const PcgParams& prm, cudaStream_t st) {
+  const dim3 g = grid_nodes(B.N, B.S);
+  double* r = (double*)B.r;
+  k_init<double><<<g, kBlock, 0, st>>>(b, bstride, r, x_out, B.partial, nodes_of(B.N));
+  scalar(B, B.sc, SM_INIT, 0, 0, st);
+  return pcg_loop<double, double, double>(B, a64, a64, x_out, r, B.sc, prm, 0, st);
+}
+
+cudaError_t ir_mixed(SolverBufs& B, const float* a32, const __nv_bfloat16* abf, const double* b, long long bstride,
+                     double* x_out, double* r64, const PcgParams& prm, int inner_iters, cudaStream_t st) {
+  const long long nodes = nodes_of(B.N);
+  const dim3 g = grid_nodes(B.N, B.S);
+  SolveScalars* sco = B.sc;
+  SolveScalars* sci = B.sc + B.S;
+  float* d = (float*)B.x;
+  float* r32 = (float*)B.r;
+  const double tol2 = prm.rtol * prm.rtol;
+  k_init<double><<<g, kBlock, 0, st>>>(b, bstride, r64, x_out, B.partial, nodes);
+  scalar(B, sco, SM_INIT, 0, 0, st);
+  for (int step = 0;; ++step) {
+    if (step > 0) {
+      k_residual64<float><<<g, kBlock, 0, st>>>(b, bstride, x_out, a32, r64, B.partial, sco, B.N);
+      scalar(B, sco, SM_OUTER_CONV, tol2, prm.max_iter, st);
+    }
+    int n = 0;
+    cudaError_t e = count_active(B, sco, st, n);
+    if (e != cudaSuccess) return e;
+    if (n == 0) break;
+    k_demote<<<g, kBlock, 0, st>>>(r64, r32, d, sco, nodes);
+    scalar(B, sci, SM_INNER_BEGIN, 0, 0, st, 0, sco);
+    e = pcg_loop<float, float, __nv_bfloat16>(B, a32, abf, d, r32, sci, prm, inner_iters, st);
+    if (e != cudaSuccess) return e;
+    k_accumulate<<<g, kBlock, 0, st>>>(x_out, d, sco, nodes);
+    scalar(B, sco, SM_OUTER_STEP, 0, 0, st, inner_iters);
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace mlsgd
