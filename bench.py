@@ -1,0 +1,340 @@
+#!/usr/bin/env python
+"""Benchmark of the multilevel entropic-risk gradient hot path on GB300.
+
+Default workload (c3): 4096 sample-gradients per step at level 3 (64^3 cells,
+250,047 interior dofs) with their level-2 partners on the same draws, 256 KL
+modes (corr length 0.2, sigma 1), theta = 10, mixed precision (BF16
+coefficient for the V-cycle, FP32 MG-PCG, FP64 iterative refinement to rtol
+1e-8).  One step = one call of mlsgd_level_gradient over the whole batch: xi,
+fields on both grids, state and adjoint solves on both grids, B*q, entropic
+weights, level differences and the Chan merge.
+
+Prints ONE JSON line (rank 0).  --impl reference times the CPU FP64 oracle
+on a bounded sample of the same workload instead.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "sample-gradients/s (state+adjoint) at rtol 1e-8 vs plain FP64; p99 latency"
+UNIT = "sample-gradients/s"
+
+
+def workload_cfg(args):
+    from paper_2606_09291_gb300 import inputs
+    p = dict(inputs.PRESETS["c3"])
+    return dict(n_levels=p["n_levels"], n0=p["n0"], n_modes=p["n_modes"], corr_len=p["corr_len"], sigma=p["sigma"],
+                theta=p["theta"], alpha=p["alpha"], seed=p["seed"], rtol=1e-8, max_iter=50,
+                precision=args.precision, max_batch=args.samples, ctrl_level=p["n_levels"] - 1)
+
+
+def workload_name(args):
+    return ("c3: %d samples/step at level 3 (64^3 cells) + level-2 partners, K=256 modes, corr 0.2, sigma 1, "
+            "theta 10, %s, rtol 1e-8" % (args.samples, "BF16 coef / FP32 MG-PCG / FP64 IR" if args.precision == "mixed"
+                                          else "plain FP64 MG-PCG"))
+
+
+# ---------------------------------------------------------------- clocks
+class ClockSampler:
+    def __init__(self, device_index):
+        self.f = tempfile.NamedTemporaryFile(mode="w+", suffix=".csv", delete=False)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "--query-gpu=" + q, "--format=csv,noheader,nounits", "-lms", "200",
+                                       "-i", str(device_index)], stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return None
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.p.kill()
+        self.f.flush()
+        rows = []
+        with open(self.f.name) as fh:
+            for line in fh:
+                parts = [t.strip() for t in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    rows.append(dict(sm=float(parts[1]), smax=float(parts[2]), hw=parts[5], hwt=parts[6], swt=parts[7],
+                                     pcap=parts[8]))
+                except ValueError:
+                    continue
+        os.unlink(self.f.name)
+        if not rows:
+            return None
+        reasons = set()
+        for r in rows:
+            if r["hw"].lower() == "active":
+                reasons.add("hw_slowdown")
+            if r["hwt"].lower() == "active":
+                reasons.add("hw_thermal_slowdown")
+            if r["swt"].lower() == "active":
+                reasons.add("sw_thermal_slowdown")
+            if r["pcap"].lower() == "active":
+                reasons.add("sw_power_cap")
+        return {"sm_mhz": statistics.median(r["sm"] for r in rows), "sm_max_mhz": max(r["smax"] for r in rows),
+                "reasons": sorted(reasons), "samples": len(rows)}
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except (OSError, ValueError):
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+# ---------------------------------------------------------------- CPU oracle legs
+def oracle_rate(n_samples, it0=0):
+    """Oracle sample-gradients/s on n_samples level-3 samples of the workload (rtol 1e-8)."""
+    from oracle import mlmc
+    from paper_2606_09291_gb300 import inputs
+    p = inputs.PRESETS["c3"]
+    W = mlmc.Workload(n0=p["n0"], n_levels=p["n_levels"], n_modes=p["n_modes"], corr_len=p["corr_len"],
+                      sigma=p["sigma"], theta=p["theta"], alpha=p["alpha"], seed=p["seed"], rtol=1e-8)
+    z = inputs.z_test(64)
+    W.level(3), W.level(2)  # operators' static parts, outside the timing
+    t = time.perf_counter()
+    mlmc.level_batch(W, it0, 3, range(n_samples), z)
+    dt = time.perf_counter() - t
+    return n_samples / dt, dt
+
+
+def cpu_threads():
+    try:
+        import numpy  # noqa: F401
+        from threadpoolctl import threadpool_info
+        return max([i.get("num_threads", 1) for i in threadpool_info()] + [1])
+    except Exception:
+        return 1
+
+
+def run_reference(args, rank):
+    if rank != 0:
+        return
+    rates, times = [], []
+    for _ in range(args.warmup):
+        oracle_rate(1)
+    for k in range(args.steps):
+        r, dt = oracle_rate(args.ref_samples, it0=k + 1)
+        rates.append(r)
+        times.append(dt)
+    value = args.ref_samples * args.steps / sum(times)
+    sample = "%d level-3 samples (+ level-2 partners) of the c3 workload per step, rtol 1e-8" % args.ref_samples
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": workload_name(args), "reference": "CPU FP64 oracle (numpy/scipy), bounded sample"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cpu_threads(), "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------- GPU arm
+def run_gpu(args, rank, world):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    import __graft_entry__
+    from paper_2606_09291_gb300 import inputs, mlsgd
+
+    __graft_entry__.build()
+    dev = int(os.environ.get("LOCAL_RANK", 0))
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.current_stream()
+    cfg = workload_cfg(args)
+    ctx = mlsgd.Context(**cfg)
+    Nc = 8 << 3
+    z_host = torch.tensor(inputs.z_test(Nc), dtype=torch.float64).pin_memory()
+    z = z_host.to("cuda")
+    S = args.samples
+    level = 3
+    stats = ctx.new_stats(level)
+    first = rank * S  # weak scaling: each rank owns its own sample range
+
+    def step(k):
+        ctx.mlsgd_stats_reset(stats)
+        ctx.mlsgd_level_gradient(k, level, first, S, z, stats)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    # warm-up; the last warm-up step profiles every kernel class to find the dominant one
+    for k in range(args.warmup):
+        if k == args.warmup - 1:
+            mlsgd.mlsgd_profile_start("*")
+        step(k)
+    torch.cuda.synchronize()
+    prof_all = mlsgd.mlsgd_profile_stop()
+    dominant = max(prof_all.items(), key=lambda kv: kv[1]["total_ms"])[0]
+    total_prof = sum(v["total_ms"] for v in prof_all.values())
+    h = stats.host()
+    if h["noconv"] > 0:
+        raise RuntimeError("warm-up: %d solves hit max_iter" % h["noconv"])
+
+    # timed region
+    sampler = ClockSampler(dev) if rank == 0 else None
+    launches0 = mlsgd.mlsgd_launch_count()
+    mlsgd.mlsgd_profile_start(dominant)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+    barrier()
+    ev[0].record(stream)
+    for k in range(args.steps):
+        step(args.warmup + k)
+        ev[k + 1].record(stream)
+    barrier()
+    step_ms = [ev[k].elapsed_time(ev[k + 1]) for k in range(args.steps)]
+    total_ms = ev[0].elapsed_time(ev[-1])
+    prof = mlsgd.mlsgd_profile_stop().get(dominant)
+    gpu_launches = mlsgd.mlsgd_launch_count() - launches0
+    clocks = sampler.stop() if sampler else None
+    if world > 1:
+        t = torch.tensor([total_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    value = S * world * args.steps / (total_ms / 1e3)
+    iters_per_sample = stats.host()["iters"] / S
+
+    # end to end through the public API with host buffers: z H2D, stats D2H each step
+    out_field = torch.empty(stats.field.numel(), dtype=torch.float64).pin_memory()
+    out_sc = torch.empty(mlsgd.NSCALARS, dtype=torch.float64).pin_memory()
+    e2e_steps = max(1, min(args.steps, 3))
+    barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for k in range(e2e_steps):
+        z.copy_(z_host, non_blocking=True)
+        step(100 + k)
+        out_field.copy_(stats.field, non_blocking=True)
+        out_sc.copy_(stats.scalars, non_blocking=True)
+    e1.record(stream)
+    barrier()
+    e2e_ms = e0.elapsed_time(e1)
+    if world > 1:
+        t = torch.tensor([e2e_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+    e2e_value = S * world * e2e_steps / (e2e_ms / 1e3)
+
+    # plain FP64 path on a subset of the same workload (the metric's comparison)
+    fp64 = None
+    if args.fp64_samples > 0 and args.precision == "mixed":
+        c64 = dict(cfg, precision="fp64", max_batch=args.fp64_samples, max_iter=200)
+        ctx64 = mlsgd.Context(**c64)
+        st64 = ctx64.new_stats(level)
+        ctx64.mlsgd_level_gradient(0, level, first, args.fp64_samples, z, st64)  # warm-up
+        torch.cuda.synchronize()
+        f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        f0.record(stream)
+        ctx64.mlsgd_stats_reset(st64)
+        ctx64.mlsgd_level_gradient(1, level, first, args.fp64_samples, z, st64)
+        f1.record(stream)
+        torch.cuda.synchronize()
+        ms64 = f0.elapsed_time(f1)
+        fp64 = {"value": args.fp64_samples / (ms64 / 1e3), "unit": UNIT, "samples": args.fp64_samples,
+                "ms": ms64, "iters_per_sample": st64.host()["iters"] / args.fp64_samples}
+        ctx64.close()
+
+    peaks, peak_kind = load_peaks()
+    roof = None
+    if prof and prof["launches"] > 0:
+        per_launch_ms = prof["total_ms"] / prof["launches"]
+        if dominant in ("resid64", "apply_f64", "smooth_f64", "resid_f64", "jacobi0_f64") and prof["flops"] > 0:
+            ach = prof["flops"] / (prof["total_ms"] / 1e3) / 1e12
+            roof = {"bound": "alu", "achieved": ach, "peak": 1.25, "unit": "TFLOP/s", "frac": ach / 1.25,
+                    "traffic": None, "kernel": dominant, "peak_kind": "nominal FP64 dense"}
+        else:
+            ach = prof["bytes"] / (prof["total_ms"] / 1e3) / 1e9
+            roof = {"bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                    "frac": ach / peaks["hbm_gbs"], "traffic": args.traffic_bytes,
+                    "kernel": dominant, "peak_kind": peak_kind, "launches": prof["launches"],
+                    "avg_launch_ms": per_launch_ms, "alg_bytes_per_launch": prof["bytes"] / prof["launches"],
+                    "share_of_step": prof_all[dominant]["total_ms"] / total_prof}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        r, dt = oracle_rate(args.cpu_samples)
+        cpu = {"value": r, "unit": UNIT, "cores": cpu_threads(), "kind": "oracle",
+               "sample": "%d level-3 samples (+ level-2 partners) of this workload, rtol 1e-8, %.1f s" % (
+                   args.cpu_samples, dt)}
+
+    if rank == 0:
+        sm = sorted(step_ms)
+        p99 = sm[min(len(sm) - 1, int(np.ceil(0.99 * len(sm))) - 1)]
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None,
+                "dtype": "f32+f64 (bf16 coefficient)" if args.precision == "mixed" else "f64", "data": "synthetic",
+                "config": {"workload": workload_name(args), "samples_per_step_per_gpu": S, "level": level,
+                           "partner_level": level - 1, "n_modes": 256, "l2": "inputs larger than L2 (batch working "
+                           "set %.0f GB)" % (ctx.mlsgd_workspace_bytes(level, S) / 1e9),
+                           "parallelism": "replicas" if world > 1 else "single GPU"},
+                "latency_ms": {"p50": statistics.median(step_ms), "p99": p99, "per": "step (one batch)"},
+                "solver_iters_per_sample": iters_per_sample,
+                "roofline": roof, "cpu_baseline": cpu,
+                "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": z.numel() * 8,
+                        "d2h_bytes_per_step": (stats.field.numel() + mlsgd.NSCALARS) * 8},
+                "gpu_launches": gpu_launches, "clocks": clocks, "fp64_path": fp64,
+                "mixed_over_fp64": (value / world / fp64["value"]) if fp64 else None,
+                "kernel_shares": {k: round(v["total_ms"] / total_prof, 4) for k, v in
+                                  sorted(prof_all.items(), key=lambda kv: -kv[1]["total_ms"])[:8]}}
+        print(json.dumps(line), flush=True)
+    ctx.close()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--samples", type=int, default=4096)
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--fp64-samples", type=int, default=256)
+    ap.add_argument("--cpu-samples", type=int, default=6)
+    ap.add_argument("--ref-samples", type=int, default=2)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--traffic-bytes", type=float, default=None,
+                    help="ncu dram read+write bytes per launch of the dominant kernel, if captured")
+    args = ap.parse_args()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        if args.impl == "reference":
+            if rank != 0:
+                return
+        else:
+            torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
+            dist.init_process_group("nccl")
+    if args.impl == "reference":
+        run_reference(args, rank)
+    else:
+        run_gpu(args, rank, world)
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

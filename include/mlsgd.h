@@ -185,6 +185,27 @@ mlsgd_status mlsgd_stats_merge(mlsgd_ctx* ctx, mlsgd_level_stats* dst, const mls
 mlsgd_status mlsgd_step(mlsgd_ctx* ctx, const mlsgd_level_stats* stats, int n_levels, double tau, double eta,
                         int max_levels, double* z_dev, double* grad_dev, mlsgd_step_report* rep, void* stream);
 
+/* ---------------------------------------------------------------- instrumentation
+ * Process-wide.  Every kernel launch of the library is counted; when profiling
+ * is on, launches of the named kernel class ("*" = all classes) are bracketed
+ * by CUDA events recorded on their own stream, and the class's algorithmic
+ * traffic (each input read once, each output written once) and flops are
+ * summed.  Class names are listed in the launch sites (for example
+ * "smooth_f32", "apply_f64", "resid64", "field", "level_field"). */
+typedef struct {
+  char cls[32];
+  int64_t launches;
+  double total_ms;
+  double bytes;
+  double flops;
+} mlsgd_profile_entry;
+int64_t mlsgd_launch_count(void);
+/* start a profile (resets earlier records); kernel_class NULL turns profiling off */
+int mlsgd_profile_start(const char* kernel_class);
+/* stop, wait for the events, fill up to max_entries per-class totals; returns the
+ * number of classes seen (may exceed max_entries) or -1 on a CUDA error */
+int mlsgd_profile_stop(mlsgd_profile_entry* out, int max_entries);
+
 #ifdef __cplusplus
 }
 #endif

@@ -12,6 +12,7 @@
 #include <vector>
 
 #include "kernels.h"
+#include "launch.h"
 #include "kl_table.h"
 #include "mlsgd.h"
 
@@ -153,12 +154,14 @@ mlsgd_status solve_grid(mlsgd_ctx* ctx, int N, int S, const GridFields& f, const
   cudaError_t e = ctx->mixed() ? ir_mixed(B, f.a32, f.abf, b, 0, ytmp, r64, prm, inner, st)
                                : pcg_fp64(B, f.a64, b, 0, ytmp, prm, st);
   CK(e);
-  k_record<<<(S + 127) / 128, 128, 0, st>>>(B.sc, S, ctx->mixed(), iters, status, 0);
+  launch("record", 0.0, k_record, dim3((S + 127) / 128), 128, 0, st, (const SolveScalars*)B.sc, S, (int)ctx->mixed(),
+         iters, status, 0);
   launch_phi_adjrhs(ytmp, N, S, badj, phi, B.partial, st);
   e = ctx->mixed() ? ir_mixed(B, f.a32, f.abf, badj, (long long)nodes, q, r64, prm, inner, st)
                    : pcg_fp64(B, f.a64, badj, (long long)nodes, q, prm, st);
   CK(e);
-  k_record<<<(S + 127) / 128, 128, 0, st>>>(B.sc, S, ctx->mixed(), iters, status, 1);
+  launch("record", 0.0, k_record, dim3((S + 127) / 128), 128, 0, st, (const SolveScalars*)B.sc, S, (int)ctx->mixed(),
+         iters, status, 1);
   CK(cudaGetLastError());
   return MLSGD_OK;
 }

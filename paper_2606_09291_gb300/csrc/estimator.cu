@@ -4,6 +4,7 @@
 
 #include "internal.cuh"
 #include "kernels.h"
+#include "launch.h"
 
 namespace mlsgd {
 
@@ -38,7 +39,8 @@ __global__ void k_rhs_state(const double* __restrict__ z, int Nc, int N, double*
 }
 
 void launch_rhs_state(const double* z, int Nc, int N, double* b, cudaStream_t st) {
-  k_rhs_state<<<node_blocks(N), kBlock, 0, st>>>(z, Nc, N, b);
+  launch("rhs", (double)cells_of(Nc) * 8 + (double)nodes_of(N) * 8, k_rhs_state, dim3(node_blocks(N)), kBlock, 0, st,
+         z, Nc, N, b);
 }
 
 // e = y - g_h with g_h the nodal interpolant of sin(pi x) sin(pi y) sin(pi z);
@@ -105,8 +107,8 @@ __global__ void k_phi_finish(const double* __restrict__ partial, int nblk, int S
 void launch_phi_adjrhs(const double* y, int N, int S, double* badj, double* phi, double* partial, cudaStream_t st) {
   if (S == 0) return;
   const int nb = node_blocks(N);
-  k_phi_adjrhs<<<dim3(nb, S), kBlock, 0, st>>>(y, N, badj, partial);
-  k_phi_finish<<<(S + 7) / 8, 256, 0, st>>>(partial, nb, S, phi);
+  launch("phi_adjrhs", (double)S * nodes_of(N) * 16, k_phi_adjrhs, dim3(nb, S), kBlock, 0, st, y, N, badj, partial);
+  launch("phi_finish", 0.0, k_phi_finish, dim3((S + 7) / 8), 256, 0, st, (const double*)partial, nb, S, phi);
 }
 
 // ---------------------------------------------------------------- level statistics
@@ -246,11 +248,15 @@ void launch_level_stats(const double* qf, const double* phif, int Nf, const doub
                         int Ncoarse, int S, int Nc, double theta, double* field, double* scalars, double* work,
                         double* partial, const int* iters, const int* status, cudaStream_t st) {
   if (S == 0) return;
-  k_level_scalars<<<1, kBlock, 0, st>>>(phif, phic, S, theta, scalars, work, iters, status);
+  launch("level_scalars", 0.0, k_level_scalars, dim3(1), kBlock, 0, st, phif, phic, S, theta, scalars, work, iters,
+         status);
   const long long ncell = (long long)Nc * Nc * Nc;
   const int nblk = (int)((ncell + kBlock - 1) / kBlock);
-  k_level_field<<<nblk, kBlock, 0, st>>>(qf, Nf, qc, Ncoarse, S, Nc, work, field, partial);
-  k_level_finish<<<1, 32, 0, st>>>(partial, nblk, work, scalars);
+  const double qbytes = (double)S * 8 * (nodes_of(Nf) + (qc ? nodes_of(Ncoarse) : 0));
+  launch("level_field", qbytes + (double)ncell * 16, k_level_field, dim3(nblk), kBlock, 0, st, qf, Nf, qc, Ncoarse, S,
+         Nc, (const double*)work, field, partial);
+  launch("level_finish", 0.0, k_level_finish, dim3(1), 32, 0, st, (const double*)partial, nblk, (const double*)work,
+         scalars);
 }
 
 __global__ void k_stats_reset(double* __restrict__ field, double* __restrict__ sc, long long n) {
@@ -261,7 +267,8 @@ __global__ void k_stats_reset(double* __restrict__ field, double* __restrict__ s
 
 void launch_stats_reset(double* field, double* scalars, long long ncells, cudaStream_t st) {
   const long long n = ncells > MLSGD_NSCALARS ? ncells : MLSGD_NSCALARS;
-  k_stats_reset<<<(unsigned)((n + kBlock - 1) / kBlock), kBlock, 0, st>>>(field, scalars, ncells);
+  launch("stats_reset", (double)ncells * 8, k_stats_reset, dim3((unsigned)((n + kBlock - 1) / kBlock)), kBlock, 0, st,
+         field, scalars, ncells);
 }
 
 // Chan merge of two statistics records: src into dst, both rescaled to the larger shift.
@@ -313,8 +320,9 @@ __global__ void k_merge_scalars(const double* __restrict__ partial, int nblk, do
 void launch_stats_merge(double* dfield, double* dsc, const double* sfield, const double* ssc, long long ncells,
                         double hc3, double theta, double* partial, cudaStream_t st) {
   const int nblk = (int)((ncells + kBlock - 1) / kBlock);
-  k_merge_field<<<nblk, kBlock, 0, st>>>(dfield, dsc, sfield, ssc, ncells, theta, hc3, partial);
-  k_merge_scalars<<<1, 32, 0, st>>>(partial, nblk, dsc, ssc, theta);
+  launch("merge", (double)ncells * 24, k_merge_field, dim3(nblk), kBlock, 0, st, dfield, (const double*)dsc, sfield,
+         ssc, ncells, theta, hc3, partial);
+  launch("merge_scalars", 0.0, k_merge_scalars, dim3(1), 32, 0, st, (const double*)partial, nblk, dsc, ssc, theta);
 }
 
 // ---------------------------------------------------------------- combine and step
@@ -368,9 +376,11 @@ void launch_combine_step(const double* const* fields, const double* factors, int
                          cudaStream_t st) {
   FieldList fl;
   for (int l = 0; l < L && l < 16; ++l) fl.f[l] = fields[l];
-  k_combine_step<<<nblk, kBlock, 0, st>>>(fl, factors, L, ncells, denom, alpha, tau, z, grad, partial, nblk);
+  launch("combine", (double)ncells * 8 * (L + 2 + (grad ? 1 : 0)), k_combine_step, dim3(nblk), kBlock, 0, st, fl,
+         factors, L, ncells, denom, alpha, tau, z, grad, partial, nblk);
   const int rows = L + 2;
-  k_rows_finish<<<(rows + 7) / 8, 256, 0, st>>>(partial, nblk, rows, partial + (long long)rows * nblk);
+  launch("combine_finish", 0.0, k_rows_finish, dim3((rows + 7) / 8), 256, 0, st, (const double*)partial, nblk, rows,
+         partial + (long long)rows * nblk);
 }
 
 }  // namespace mlsgd

@@ -7,6 +7,7 @@
 // workload) evaluated at the cell centres of the requested grid.
 #include "internal.cuh"
 #include "kernels.h"
+#include "launch.h"
 
 namespace mlsgd {
 
@@ -32,8 +33,8 @@ void launch_draw_xi(uint64_t seed, int iter, int level, long long first, int S, 
                     cudaStream_t st) {
   const long long n = (long long)S * (K / 2);
   if (n == 0) return;
-  k_draw_xi<<<(unsigned)((n + kBlock - 1) / kBlock), kBlock, 0, st>>>(
-      (uint32_t)(seed & 0xffffffffu), (uint32_t)(seed >> 32), (uint32_t)iter, (uint32_t)level, first, S, K, xi);
+  launch("xi", (double)S * K * 8, k_draw_xi, dim3((unsigned)((n + kBlock - 1) / kBlock)), kBlock, 0, st,
+         (uint32_t)(seed & 0xffffffffu), (uint32_t)(seed >> 32), (uint32_t)iter, (uint32_t)level, first, S, K, xi);
 }
 
 // Sum-factorised synthesis.  One block per (z plane, sample):
@@ -88,7 +89,10 @@ cudaError_t launch_field(const double* xi, int K, const ModeTable& mt, const dou
   const size_t smem = field_smem_bytes(mt, K, N);
   cudaError_t e = cudaFuncSetAttribute(k_field, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  k_field<<<dim3(N, S), kBlock, smem, st>>>(xi, K, mt, phi, N, out);
+  const double cells = (double)S * N * N * N;
+  const double outb = cells * ((out.log_a ? 8 : 0) + (out.a64 ? 8 : 0) + (out.a32 ? 4 : 0) + (out.abf ? 2 : 0));
+  launch_flops("field", (double)S * K * 8 + outb, 2.0 * cells * mt.n1x + 2.0 * (double)S * K * N * N, k_field,
+               dim3(N, S), kBlock, smem, st, xi, K, mt, phi, N, out);
   return cudaGetLastError();
 }
 
@@ -111,8 +115,9 @@ __global__ void k_exp_field_mixed(const double* __restrict__ la, float* __restri
 void launch_exp_field(const double* la, const FieldOut& out, long long n, cudaStream_t st) {
   if (n == 0) return;
   const unsigned g = (unsigned)((n + kBlock - 1) / kBlock);
-  if (out.a64) k_exp_field<double><<<g, kBlock, 0, st>>>(la, out.a64, n);
-  if (out.a32 && out.abf) k_exp_field_mixed<<<g, kBlock, 0, st>>>(la, out.a32, out.abf, n);
+  if (out.a64) launch("expfield", (double)n * 16, k_exp_field<double>, dim3(g), kBlock, 0, st, la, out.a64, n);
+  if (out.a32 && out.abf)
+    launch("expfield", (double)n * 14, k_exp_field_mixed, dim3(g), kBlock, 0, st, la, out.a32, out.abf, n);
 }
 
 }  // namespace mlsgd

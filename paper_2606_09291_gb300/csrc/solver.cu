@@ -14,9 +14,11 @@
 // FP64 and the accurate FP32-stored coefficient) around a fixed number of FP32
 // PCG iterations whose V-cycle reads the BF16 coefficient.
 #include <algorithm>
+#include <cstdio>
 
 #include "internal.cuh"
 #include "kernels.h"
+#include "launch.h"
 
 namespace mlsgd {
 
@@ -383,16 +385,34 @@ void carve_solver(SolverBufs& B, int N, int S, int elem, char*& ptr) {
   B.count = (int*)take(sizeof(int));
 }
 
+// algorithmic bytes of a node kernel: `vec` vectors of T over S samples of grid N
+// plus `coef` reads of the cell coefficient TA
+template <typename T, typename TA>
+static double nbytes(int N, int S, double vec, double coef) {
+  return (double)S * (vec * (double)nodes_of(N) * sizeof(T) + coef * (double)cells_of(N) * sizeof(TA));
+}
+template <typename T> struct Tag;
+template <> struct Tag<double> { static constexpr const char* s = "f64"; };
+template <> struct Tag<float> { static constexpr const char* s = "f32"; };
+template <typename T>
+static const char* cls(const char* base, bool fine) {
+  static thread_local char buf[64];
+  snprintf(buf, sizeof(buf), "%s_%s%s", base, Tag<T>::s, fine ? "" : "_coarse");
+  return buf;
+}
+
 template <typename TI, typename TO>
 static void coarsen_all(SolverBufs& B, const TI* a0, cudaStream_t st) {
   for (int j = 1; j <= B.J; ++j) {
     const int Nc = B.N >> j;
     const long long n = cells_of(Nc) * B.S;
+    const dim3 g((unsigned)((n + 255) / 256));
     if (j == 1)
-      k_coarsen_coef<TI, TO><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(a0, (TO*)B.acoef[1], Nc, B.S);
+      launch("coarsen", (double)n * (8 * sizeof(TI) + sizeof(TO)), k_coarsen_coef<TI, TO>, g, 256, 0, st, a0,
+             (TO*)B.acoef[1], Nc, B.S);
     else
-      k_coarsen_coef<TO, TO><<<(unsigned)((n + 255) / 256), 256, 0, st>>>((const TO*)B.acoef[j - 1],
-                                                                          (TO*)B.acoef[j], Nc, B.S);
+      launch("coarsen", (double)n * 9 * sizeof(TO), k_coarsen_coef<TO, TO>, g, 256, 0, st, (const TO*)B.acoef[j - 1],
+             (TO*)B.acoef[j], Nc, B.S);
   }
 }
 void build_hierarchy_fp64(SolverBufs& B, const double* a64, cudaStream_t st) { coarsen_all<double, double>(B, a64, st); }
@@ -407,43 +427,50 @@ static void vcycle(SolverBufs& B, const T* r0, const TA0* a0, const SolveScalars
   auto rin = [&](int j) { return j == 0 ? r0 : (const T*)B.vr[j]; };
   for (int j = 0; j < J; ++j) {
     const int Nj = B.N >> j;
-    if (j == 0) {
-      k_jacobi0<T, TA0><<<grid_nodes(Nj, S), kBlock, 0, st>>>(rin(0), a0, (T*)B.vx[0], sc, Nj, omega);
-      k_resid_smooth<T, TA0, 0><<<grid_nodes(Nj, S), kBlock, 0, st>>>(rin(0), (const T*)B.vx[0], a0, (T*)B.vt[0],
-                                                                      sc, Nj, omega);
+    const bool fine = j == 0;
+    if (fine) {
+      launch(cls<T>("jacobi0", true), nbytes<T, TA0>(Nj, S, 2, 1), k_jacobi0<T, TA0>, grid_nodes(Nj, S), kBlock, 0,
+             st, rin(0), a0, (T*)B.vx[0], sc, Nj, omega);
+      launch(cls<T>("resid", true), nbytes<T, TA0>(Nj, S, 3, 1), k_resid_smooth<T, TA0, 0>, grid_nodes(Nj, S), kBlock,
+             0, st, rin(0), (const T*)B.vx[0], a0, (T*)B.vt[0], sc, Nj, omega);
     } else {
       const T* aj = (const T*)B.acoef[j];
-      k_jacobi0<T, T><<<grid_nodes(Nj, S), kBlock, 0, st>>>(rin(j), aj, (T*)B.vx[j], sc, Nj, omega);
-      k_resid_smooth<T, T, 0><<<grid_nodes(Nj, S), kBlock, 0, st>>>(rin(j), (const T*)B.vx[j], aj, (T*)B.vt[j], sc,
-                                                                    Nj, omega);
+      launch(cls<T>("jacobi0", false), nbytes<T, T>(Nj, S, 2, 1), k_jacobi0<T, T>, grid_nodes(Nj, S), kBlock, 0, st,
+             rin(j), aj, (T*)B.vx[j], sc, Nj, omega);
+      launch(cls<T>("resid", false), nbytes<T, T>(Nj, S, 3, 1), k_resid_smooth<T, T, 0>, grid_nodes(Nj, S), kBlock, 0,
+             st, rin(j), (const T*)B.vx[j], aj, (T*)B.vt[j], sc, Nj, omega);
     }
-    k_restrict<T><<<grid_nodes(Nj / 2, S), kBlock, 0, st>>>((const T*)B.vt[j], (T*)B.vr[j + 1], sc, Nj / 2);
+    launch(cls<T>("restrict", fine), nbytes<T, T>(Nj, S, 1, 0) + nbytes<T, T>(Nj / 2, S, 1, 0), k_restrict<T>,
+           grid_nodes(Nj / 2, S), kBlock, 0, st, (const T*)B.vt[j], (T*)B.vr[j + 1], sc, Nj / 2);
   }
   if (J == 0)
-    k_coarsest<T, TA0><<<(S + 127) / 128, 128, 0, st>>>(rin(0), a0, (T*)B.vt[0], sc, S);
+    launch("coarsest", 0.0, k_coarsest<T, TA0>, dim3((S + 127) / 128), 128, 0, st, rin(0), a0, (T*)B.vt[0], sc, S);
   else
-    k_coarsest<T, T><<<(S + 127) / 128, 128, 0, st>>>(rin(J), (const T*)B.acoef[J], (T*)B.vt[J], sc, S);
+    launch("coarsest", 0.0, k_coarsest<T, T>, dim3((S + 127) / 128), 128, 0, st, rin(J), (const T*)B.acoef[J],
+           (T*)B.vt[J], sc, S);
   for (int j = J - 1; j >= 0; --j) {
     const int Nj = B.N >> j;
-    k_prolong_add<T><<<grid_nodes(Nj, S), kBlock, 0, st>>>((T*)B.vx[j], (const T*)B.vt[j + 1], sc, Nj);
-    if (j == 0)
-      k_resid_smooth<T, TA0, 1><<<grid_nodes(Nj, S), kBlock, 0, st>>>(rin(0), (const T*)B.vx[0], a0, (T*)B.vt[0],
-                                                                      sc, Nj, omega);
+    const bool fine = j == 0;
+    launch(cls<T>("prolong", fine), nbytes<T, T>(Nj, S, 2, 0) + nbytes<T, T>(Nj / 2, S, 1, 0), k_prolong_add<T>,
+           grid_nodes(Nj, S), kBlock, 0, st, (T*)B.vx[j], (const T*)B.vt[j + 1], sc, Nj);
+    if (fine)
+      launch(cls<T>("smooth", true), nbytes<T, TA0>(Nj, S, 3, 1), k_resid_smooth<T, TA0, 1>, grid_nodes(Nj, S), kBlock,
+             0, st, rin(0), (const T*)B.vx[0], a0, (T*)B.vt[0], sc, Nj, omega);
     else
-      k_resid_smooth<T, T, 1><<<grid_nodes(Nj, S), kBlock, 0, st>>>(rin(j), (const T*)B.vx[j],
-                                                                    (const T*)B.acoef[j], (T*)B.vt[j], sc, Nj, omega);
+      launch(cls<T>("smooth", false), nbytes<T, T>(Nj, S, 3, 1), k_resid_smooth<T, T, 1>, grid_nodes(Nj, S), kBlock, 0,
+             st, rin(j), (const T*)B.vx[j], (const T*)B.acoef[j], (T*)B.vt[j], sc, Nj, omega);
   }
 }
 
 static void scalar(SolverBufs& B, SolveScalars* sc, int mode, double tol2, int max_iter, cudaStream_t st,
                    int inner_iters = 0, const SolveScalars* outer = nullptr) {
   const int warps = 8;
-  k_scalar<<<(B.S + warps - 1) / warps, 32 * warps, 0, st>>>(B.partial, node_blocks(B.N), sc, B.S, mode, tol2,
-                                                              max_iter, inner_iters, outer);
+  launch("scalar", 0.0, k_scalar, dim3((B.S + warps - 1) / warps), 32 * warps, 0, st, (const double*)B.partial,
+         node_blocks(B.N), sc, B.S, mode, tol2, max_iter, inner_iters, outer);
 }
 
 static cudaError_t count_active(SolverBufs& B, const SolveScalars* sc, cudaStream_t st, int& n) {
-  k_count_active<<<1, kBlock, 0, st>>>(sc, B.S, B.count);
+  launch("count", 0.0, k_count_active, dim3(1), kBlock, 0, st, sc, B.S, B.count);
   cudaError_t e = cudaMemcpyAsync(B.count_host, B.count, sizeof(int), cudaMemcpyDeviceToHost, st);
   if (e != cudaSuccess) return e;
   e = cudaStreamSynchronize(st);
@@ -464,15 +491,19 @@ static cudaError_t pcg_loop(SolverBufs& B, const TAop* aop, const TA0* a0, T* x,
   T* q = (T*)B.q;
   vcycle<T, TA0>(B, r, a0, sc, omega, st);
   const T* z = (const T*)B.vt[0];
-  k_dot<T><<<g, kBlock, 0, st>>>(r, z, B.partial, sc, nodes);
+  launch(cls<T>("dot", true), nbytes<T, T>(N, S, 2, 0), k_dot<T>, g, kBlock, 0, st, (const T*)r, z, B.partial,
+         (const SolveScalars*)sc, nodes);
   scalar(B, sc, SM_RZ0, 0, 0, st);
-  k_p_update<T><<<g, kBlock, 0, st>>>(p, z, sc, nodes, 1);
+  launch(cls<T>("pupdate", true), nbytes<T, T>(N, S, 2, 0), k_p_update<T>, g, kBlock, 0, st, p, z,
+         (const SolveScalars*)sc, nodes, 1);
   const double tol2 = prm.rtol * prm.rtol;
   const int nit = fixed_iters > 0 ? fixed_iters : prm.max_iter;
   for (int it = 0; it < nit; ++it) {
-    k_apply_dot<T, TAop><<<g, kBlock, 0, st>>>(p, aop, q, B.partial, sc, N);
+    launch(cls<T>("apply", true), nbytes<T, TAop>(N, S, 2, 1), k_apply_dot<T, TAop>, g, kBlock, 0, st, (const T*)p,
+           aop, q, B.partial, (const SolveScalars*)sc, N);
     scalar(B, sc, SM_ALPHA, 0, 0, st);
-    k_update_xr<T><<<g, kBlock, 0, st>>>(x, r, p, q, B.partial, sc, nodes);
+    launch(cls<T>("update", true), nbytes<T, T>(N, S, 6, 0), k_update_xr<T>, g, kBlock, 0, st, x, r, (const T*)p,
+           (const T*)q, B.partial, (const SolveScalars*)sc, nodes);
     if (fixed_iters > 0) {
       if (it == nit - 1) break;
     } else {
@@ -485,9 +516,11 @@ static cudaError_t pcg_loop(SolverBufs& B, const TAop* aop, const TA0* a0, T* x,
       }
     }
     vcycle<T, TA0>(B, r, a0, sc, omega, st);
-    k_dot<T><<<g, kBlock, 0, st>>>(r, z, B.partial, sc, nodes);
+    launch(cls<T>("dot", true), nbytes<T, T>(N, S, 2, 0), k_dot<T>, g, kBlock, 0, st, (const T*)r, z, B.partial,
+           (const SolveScalars*)sc, nodes);
     scalar(B, sc, SM_BETA, 0, 0, st);
-    k_p_update<T><<<g, kBlock, 0, st>>>(p, z, sc, nodes, 0);
+    launch(cls<T>("pupdate", true), nbytes<T, T>(N, S, 3, 0), k_p_update<T>, g, kBlock, 0, st, p, z,
+           (const SolveScalars*)sc, nodes, 0);
   }
   return cudaGetLastError();
 }
@@ -496,36 +529,44 @@ cudaError_t pcg_fp64(SolverBufs& B, const double* a64, const double* b, long lon
                      const PcgParams& prm, cudaStream_t st) {
   const dim3 g = grid_nodes(B.N, B.S);
   double* r = (double*)B.r;
-  k_init<double><<<g, kBlock, 0, st>>>(b, bstride, r, x_out, B.partial, nodes_of(B.N));
+  const double bb = (double)(bstride ? B.S : 1) * nodes_of(B.N) * 8;
+  launch("init_f64", bb + nbytes<double, double>(B.N, B.S, 2, 0), k_init<double>, g, kBlock, 0, st, b, bstride, r,
+         x_out, B.partial, nodes_of(B.N));
   scalar(B, B.sc, SM_INIT, 0, 0, st);
   return pcg_loop<double, double, double>(B, a64, a64, x_out, r, B.sc, prm, 0, st);
 }
 
 cudaError_t ir_mixed(SolverBufs& B, const float* a32, const __nv_bfloat16* abf, const double* b, long long bstride,
                      double* x_out, double* r64, const PcgParams& prm, int inner_iters, cudaStream_t st) {
-  const long long nodes = nodes_of(B.N);
-  const dim3 g = grid_nodes(B.N, B.S);
+  const int N = B.N, S = B.S;
+  const long long nodes = nodes_of(N);
+  const dim3 g = grid_nodes(N, S);
   SolveScalars* sco = B.sc;
-  SolveScalars* sci = B.sc + B.S;
+  SolveScalars* sci = B.sc + S;
   float* d = (float*)B.x;
   float* r32 = (float*)B.r;
   const double tol2 = prm.rtol * prm.rtol;
-  k_init<double><<<g, kBlock, 0, st>>>(b, bstride, r64, x_out, B.partial, nodes);
+  const double bb = (double)(bstride ? S : 1) * nodes * 8;
+  launch("init_f64", bb + nbytes<double, double>(N, S, 2, 0), k_init<double>, g, kBlock, 0, st, b, bstride, r64,
+         x_out, B.partial, nodes);
   scalar(B, sco, SM_INIT, 0, 0, st);
   for (int step = 0;; ++step) {
     if (step > 0) {
-      k_residual64<float><<<g, kBlock, 0, st>>>(b, bstride, x_out, a32, r64, B.partial, sco, B.N);
+      launch("resid64", bb + nbytes<double, float>(N, S, 2, 1), k_residual64<float>, g, kBlock, 0, st, b, bstride,
+             (const double*)x_out, a32, r64, B.partial, (const SolveScalars*)sco, N);
       scalar(B, sco, SM_OUTER_CONV, tol2, prm.max_iter, st);
     }
     int n = 0;
     cudaError_t e = count_active(B, sco, st, n);
     if (e != cudaSuccess) return e;
     if (n == 0) break;
-    k_demote<<<g, kBlock, 0, st>>>(r64, r32, d, sco, nodes);
+    launch("demote", (double)S * nodes * 16, k_demote, g, kBlock, 0, st, (const double*)r64, r32, d,
+           (const SolveScalars*)sco, nodes);
     scalar(B, sci, SM_INNER_BEGIN, 0, 0, st, 0, sco);
     e = pcg_loop<float, float, __nv_bfloat16>(B, a32, abf, d, r32, sci, prm, inner_iters, st);
     if (e != cudaSuccess) return e;
-    k_accumulate<<<g, kBlock, 0, st>>>(x_out, d, sco, nodes);
+    launch("accum", (double)S * nodes * 20, k_accumulate, g, kBlock, 0, st, x_out, (const float*)d,
+           (const SolveScalars*)sco, nodes);
     scalar(B, sco, SM_OUTER_STEP, 0, 0, st, inner_iters);
   }
   return cudaGetLastError();

@@ -38,9 +38,15 @@ class StepReport(ctypes.Structure):
                 ("next_levels", ctypes.c_int), ("next_counts", ctypes.c_int64 * 16)]
 
 
+class ProfileEntry(ctypes.Structure):
+    _fields_ = [("cls", ctypes.c_char * 32), ("launches", ctypes.c_int64), ("total_ms", ctypes.c_double),
+                ("bytes", ctypes.c_double), ("flops", ctypes.c_double)]
+
+
 EXPORTS = ["mlsgd_create", "mlsgd_destroy", "mlsgd_last_error", "mlsgd_status_string", "mlsgd_n_ctrl_cells",
            "mlsgd_workspace_bytes", "mlsgd_mode_table", "mlsgd_sample_field", "mlsgd_solve_state_adjoint",
-           "mlsgd_level_gradient", "mlsgd_stats_reset", "mlsgd_stats_merge", "mlsgd_step"]
+           "mlsgd_level_gradient", "mlsgd_stats_reset", "mlsgd_stats_merge", "mlsgd_step",
+           "mlsgd_launch_count", "mlsgd_profile_start", "mlsgd_profile_stop"]
 
 _lib = None
 
@@ -72,13 +78,35 @@ def load(path=LIB_PATH):
     L.mlsgd_stats_reset.argtypes = [vp, ctypes.POINTER(LevelStats), vp]
     L.mlsgd_stats_merge.argtypes = [vp, ctypes.POINTER(LevelStats), ctypes.POINTER(LevelStats), vp]
     L.mlsgd_step.argtypes = [vp, ctypes.POINTER(LevelStats), i32, dbl, dbl, i32, vp, vp, ctypes.POINTER(StepReport), vp]
+    L.mlsgd_launch_count.argtypes = []
+    L.mlsgd_launch_count.restype = i64
+    L.mlsgd_profile_start.argtypes = [ctypes.c_char_p]
+    L.mlsgd_profile_stop.argtypes = [ctypes.POINTER(ProfileEntry), i32]
     for name in EXPORTS:
         if name not in ("mlsgd_destroy", "mlsgd_last_error", "mlsgd_status_string", "mlsgd_n_ctrl_cells",
-                        "mlsgd_workspace_bytes", "mlsgd_mode_table"):
+                        "mlsgd_workspace_bytes", "mlsgd_mode_table", "mlsgd_launch_count"):
             getattr(L, name).restype = i32
     L.mlsgd_mode_table.restype = i32
     _lib = L
     return L
+
+
+def mlsgd_launch_count():
+    return int(load().mlsgd_launch_count())
+
+
+def mlsgd_profile_start(kernel_class):
+    load().mlsgd_profile_start(None if kernel_class is None else kernel_class.encode())
+
+
+def mlsgd_profile_stop(max_entries=128):
+    """Returns {class: dict(launches, total_ms, bytes, flops)}."""
+    arr = (ProfileEntry * max_entries)()
+    n = load().mlsgd_profile_stop(arr, max_entries)
+    if n < 0:
+        raise RuntimeError("mlsgd_profile_stop: CUDA error")
+    return {arr[i].cls.decode(): dict(launches=arr[i].launches, total_ms=arr[i].total_ms, bytes=arr[i].bytes,
+                                      flops=arr[i].flops) for i in range(min(n, max_entries))}
 
 
 class MlsgdError(RuntimeError):
