@@ -166,6 +166,27 @@ mlsgd_status mlsgd_solve_state_adjoint(mlsgd_ctx* ctx, int grid, int n_samples, 
 mlsgd_status mlsgd_level_gradient(mlsgd_ctx* ctx, int iter, int level, int64_t first_sample, int n_samples,
                                   const double* z_dev, mlsgd_level_stats* stats, void* stream);
 
+/* Allocation-free variant of mlsgd_solve_state_adjoint (the paper has no
+ * counterpart; it exists for callers that must not allocate device memory,
+ * for example code in a host callback or real-time loop where cudaMalloc's
+ * implicit synchronisation is forbidden, or an application whose own pool owns
+ * all device memory).  Same arguments, layouts and results as
+ * mlsgd_solve_state_adjoint, but every scratch buffer comes from one static
+ * device array of MLSGD_NOALLOC_SCRATCH_BYTES compiled into the library, which
+ * each GPU that loads the library holds until the process exits; the call
+ * makes no cudaMalloc/cudaFree.  A batch whose scratch would not fit is
+ * rejected with MLSGD_EINVAL and a message giving the bytes it needs (about
+ * 6 samples of a 32^3 grid or 40 of a 16^3 grid in FP64).  The first call on
+ * each device looks up the array's device address (cudaGetSymbolAddress) with
+ * that device current; make that first call before any stream capture.  All
+ * calls share the array and it keeps the last call's contents: calls that
+ * overlap on the GPU (other streams, other threads, other contexts) race, so
+ * serialise them.  Nothing in the array needs to start at zero. */
+#define MLSGD_NOALLOC_SCRATCH_BYTES (16u << 20)
+mlsgd_status mlsgd_solve_state_adjoint_noalloc(mlsgd_ctx* ctx, int grid, int n_samples, const double* log_a_dev,
+                                               const double* z_dev, double* y_dev, double* q_dev, double* phi_dev,
+                                               int* iters_dev, int* status_dev, void* stream);
+
 /* Zero a statistics record (count 0, shift -inf). */
 mlsgd_status mlsgd_stats_reset(mlsgd_ctx* ctx, mlsgd_level_stats* stats, void* stream);
 /* Merge src into dst (both of the same level): Chan update with rescaling

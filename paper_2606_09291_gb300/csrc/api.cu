@@ -8,6 +8,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -341,6 +342,79 @@ mlsgd_status mlsgd_solve_state_adjoint(mlsgd_ctx* ctx, int grid, int n_samples, 
   CK(cudaStreamSynchronize(st));
   for (int v : h)
     if (v) return fail(ctx, MLSGD_ENOCONV, "mlsgd_solve_state_adjoint: a solve hit max_iter or went non-finite");
+  return MLSGD_OK;
+}
+
+// ---------------------------------------------------------------- allocation-free solve
+// Some callers cannot allocate device memory at the time they need a solve:
+// code running inside a host callback or a real-time loop where cudaMalloc's
+// implicit device synchronisation is not allowed, or a host application that
+// owns all device memory through its own pool and forbids libraries from
+// calling the CUDA allocator.  For them the solve below takes its scratch from
+// a fixed array compiled into the library instead of the context's growable
+// workspace.  The array is MLSGD_NOALLOC_SCRATCH_BYTES large and every GPU
+// that loads the library holds it until the process exits.
+static __device__ __align__(256) char g_noalloc_scratch[MLSGD_NOALLOC_SCRATCH_BYTES];
+
+namespace {
+constexpr int kMaxDevices = 64;
+char* g_noalloc_addr[kMaxDevices] = {};
+std::mutex g_noalloc_mu;
+
+// Device address of the static array on the current device, looked up once per
+// device (host code only sees a host-side stand-in under that name).
+mlsgd_status noalloc_scratch(mlsgd_ctx* ctx, char** out) {
+  int dev = -1;
+  CK(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kMaxDevices) return fail(ctx, MLSGD_EINVAL, "device ordinal out of range");
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  if (g_noalloc_addr[dev] == nullptr) {
+    void* p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess || p == nullptr)
+      return fail(ctx, MLSGD_ECUDA, std::string("cudaGetSymbolAddress(static scratch): ") + cudaGetErrorString(e));
+    g_noalloc_addr[dev] = (char*)p;
+  }
+  *out = g_noalloc_addr[dev];
+  return MLSGD_OK;
+}
+}  // namespace
+
+mlsgd_status mlsgd_solve_state_adjoint_noalloc(mlsgd_ctx* ctx, int grid, int n_samples, const double* log_a_dev,
+                                               const double* z_dev, double* y_dev, double* q_dev, double* phi_dev,
+                                               int* iters_dev, int* status_dev, void* stream) {
+  if (!ctx) return MLSGD_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  if (grid < 0 || grid >= ctx->cfg.n_levels || grid > ctx->cfg.ctrl_level || n_samples < 0)
+    return fail(ctx, MLSGD_EINVAL, "mlsgd_solve_state_adjoint_noalloc: bad grid or sample count");
+  if (n_samples == 0) return MLSGD_OK;
+  if (!log_a_dev || !z_dev || !y_dev || !q_dev || !phi_dev || !iters_dev || !status_dev)
+    return fail(ctx, MLSGD_EINVAL, "mlsgd_solve_state_adjoint_noalloc: null pointer");
+  const int N = ctx->N(grid);
+  const int S = n_samples;
+  const size_t need = field_bytes(ctx, N, S) + solve_scratch_bytes(ctx, N, S);
+  if (need > (size_t)MLSGD_NOALLOC_SCRATCH_BYTES)
+    return fail(ctx, MLSGD_EINVAL,
+                "mlsgd_solve_state_adjoint_noalloc: " + std::to_string(S) + " samples on a " + std::to_string(N) +
+                    "^3 grid need " + std::to_string(need) + " bytes of scratch; the static array holds " +
+                    std::to_string((size_t)MLSGD_NOALLOC_SCRATCH_BYTES) + " (use fewer samples per call)");
+  char* scratch = nullptr;
+  mlsgd_status s = noalloc_scratch(ctx, &scratch);
+  if (s != MLSGD_OK) return s;
+  // Nothing in the scratch has to start at zero: every kernel of the solve writes
+  // a buffer (all nodes, boundary included) before any kernel reads it.
+  Bump bp{scratch};
+  GridFields f = carve_fields(ctx, N, S, bp);
+  FieldOut o{nullptr, f.a64, f.a32, f.abf};
+  launch_exp_field(log_a_dev, o, (long long)S * cells_of(N), st);
+  s = solve_grid(ctx, N, S, f, z_dev, y_dev, q_dev, phi_dev, iters_dev, status_dev, bp.p, st);
+  if (s != MLSGD_OK) return s;
+  // non-convergence check through the context's pinned host buffer (no allocation)
+  int* h = (int*)ctx->host_buf;
+  CK(cudaMemcpyAsync(h, status_dev, S * sizeof(int), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  for (int i = 0; i < S; ++i)
+    if (h[i]) return fail(ctx, MLSGD_ENOCONV, "mlsgd_solve_state_adjoint_noalloc: a solve hit max_iter");
   return MLSGD_OK;
 }
 

@@ -46,7 +46,7 @@ class ProfileEntry(ctypes.Structure):
 EXPORTS = ["mlsgd_create", "mlsgd_destroy", "mlsgd_last_error", "mlsgd_status_string", "mlsgd_n_ctrl_cells",
            "mlsgd_workspace_bytes", "mlsgd_mode_table", "mlsgd_sample_field", "mlsgd_solve_state_adjoint",
            "mlsgd_level_gradient", "mlsgd_stats_reset", "mlsgd_stats_merge", "mlsgd_step",
-           "mlsgd_launch_count", "mlsgd_profile_start", "mlsgd_profile_stop"]
+           "mlsgd_launch_count", "mlsgd_profile_start", "mlsgd_profile_stop", "mlsgd_solve_state_adjoint_noalloc"]
 
 _lib = None
 
@@ -78,6 +78,7 @@ def load(path=LIB_PATH):
     L.mlsgd_stats_reset.argtypes = [vp, ctypes.POINTER(LevelStats), vp]
     L.mlsgd_stats_merge.argtypes = [vp, ctypes.POINTER(LevelStats), ctypes.POINTER(LevelStats), vp]
     L.mlsgd_step.argtypes = [vp, ctypes.POINTER(LevelStats), i32, dbl, dbl, i32, vp, vp, ctypes.POINTER(StepReport), vp]
+    L.mlsgd_solve_state_adjoint_noalloc.argtypes = [vp, i32, i32, vp, vp, vp, vp, vp, vp, vp, vp]
     L.mlsgd_launch_count.argtypes = []
     L.mlsgd_launch_count.restype = i64
     L.mlsgd_profile_start.argtypes = [ctypes.c_char_p]
@@ -185,6 +186,12 @@ class Context:
     def mlsgd_solve_state_adjoint(self, grid, n, log_a, z, y, q, phi, iters, status, stream=None):
         return self.L.mlsgd_solve_state_adjoint(self.h, grid, n, _ptr(log_a), _ptr(z), _ptr(y), _ptr(q), _ptr(phi),
                                                 _ptr(iters), _ptr(status), _stream(stream))
+
+    def mlsgd_solve_state_adjoint_noalloc(self, grid, n, log_a, z, y, q, phi, iters, status, stream=None):
+        """Same as mlsgd_solve_state_adjoint with scratch from the library's static
+        device array (no device allocation); returns the C status."""
+        return self.L.mlsgd_solve_state_adjoint_noalloc(self.h, grid, n, _ptr(log_a), _ptr(z), _ptr(y), _ptr(q),
+                                                        _ptr(phi), _ptr(iters), _ptr(status), _stream(stream))
 
     def mlsgd_level_gradient(self, it, level, first, n, z, stats, stream=None):
         self._check(self.L.mlsgd_level_gradient(self.h, it, level, first, n, _ptr(z), ctypes.byref(stats.c),
