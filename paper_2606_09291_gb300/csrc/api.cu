@@ -30,6 +30,8 @@ struct mlsgd_ctx {
   int* d_order = nullptr;
   int* d_offs = nullptr;
   std::vector<double*> d_phi;  // per level: [n1d][N] at cell centres
+  std::vector<double*> d_gtab;   // per level: [N+1] sin(pi i / N), 0 at i = 0, N (nodal interpolant of g)
+  std::vector<double*> d_mgtab;  // per level: [N+1] (h/6)(g[i-1] + 4 g[i] + g[i+1]) (1D mass times g)
   char* ws = nullptr;
   size_t ws_size = 0;
   int* count_host = nullptr;
@@ -157,7 +159,10 @@ mlsgd_status solve_grid(mlsgd_ctx* ctx, int N, int S, const GridFields& f, const
   CK(e);
   launch("record", 0.0, k_record, dim3((S + 127) / 128), 128, 0, st, (const SolveScalars*)B.sc, S, (int)ctx->mixed(),
          iters, status, 0);
-  launch_phi_adjrhs(ytmp, N, S, badj, phi, B.partial, st);
+  int lev = 0;
+  while ((ctx->cfg.n0 << lev) < N) ++lev;
+  CK(cudaMemsetAsync(badj, 0, S * nodes * sizeof(double), st));  // boundary rows stay 0
+  launch_phi_adjrhs(ytmp, N, S, badj, phi, B.partial, ctx->d_gtab[lev], ctx->d_mgtab[lev], st);
   e = ctx->mixed() ? ir_mixed(B, f.a32, f.abf, badj, (long long)nodes, q, r64, prm, inner, st)
                    : pcg_fp64(B, f.a64, badj, (long long)nodes, q, prm, st);
   CK(e);
@@ -251,6 +256,14 @@ mlsgd_status mlsgd_create(const mlsgd_config* cfg, mlsgd_ctx** out) {
     double* d = nullptr;
     ok = up((void**)&d, phi.data(), phi.size() * sizeof(double));
     ctx->d_phi.push_back(d);
+    const int N = ctx->N(l);
+    std::vector<double> g(N + 1, 0.0), mg(N + 1, 0.0);
+    for (int i = 1; i < N; ++i) g[i] = std::sin(M_PI * (double)i / N);
+    for (int i = 1; i < N; ++i) mg[i] = (g[i - 1] + 4.0 * g[i] + g[i + 1]) / (6.0 * N);
+    double *dg = nullptr, *dmg = nullptr;
+    ok = ok && up((void**)&dg, g.data(), g.size() * sizeof(double)) && up((void**)&dmg, mg.data(), mg.size() * sizeof(double));
+    ctx->d_gtab.push_back(dg);
+    ctx->d_mgtab.push_back(dmg);
   }
   ok = ok && cudaHostAlloc((void**)&ctx->count_host, sizeof(int), cudaHostAllocDefault) == cudaSuccess;
   ok = ok && cudaHostAlloc((void**)&ctx->host_buf, 4096 * sizeof(double), cudaHostAllocDefault) == cudaSuccess;
@@ -267,6 +280,8 @@ void mlsgd_destroy(mlsgd_ctx* ctx) {
   if (!ctx) return;
   cudaFree(ctx->d_iy); cudaFree(ctx->d_iz); cudaFree(ctx->d_scale); cudaFree(ctx->d_order); cudaFree(ctx->d_offs);
   for (double* d : ctx->d_phi) cudaFree(d);
+  for (double* d : ctx->d_gtab) cudaFree(d);
+  for (double* d : ctx->d_mgtab) cudaFree(d);
   if (ctx->ws) cudaFree(ctx->ws);
   if (ctx->count_host) cudaFreeHost(ctx->count_host);
   if (ctx->host_buf) cudaFreeHost(ctx->host_buf);

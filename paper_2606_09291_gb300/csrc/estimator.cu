@@ -14,7 +14,7 @@ namespace mlsgd {
 __global__ void k_rhs_state(const double* __restrict__ z, int Nc, int N, double* __restrict__ b) {
   const int n1 = N + 1;
   const long long nodes = (long long)n1 * n1 * n1;
-  const long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const int n = blockIdx.x * blockDim.x + threadIdx.x;
   if (n >= nodes) return;
   int i, j, k;
   node_ijk(n, n1, i, j, k);
@@ -52,7 +52,7 @@ __global__ void k_phi_adjrhs(const double* __restrict__ y, int N, double* __rest
   const int s = blockIdx.y;
   const int n1 = N + 1;
   const long long nodes = (long long)n1 * n1 * n1;
-  const long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const int n = blockIdx.x * blockDim.x + threadIdx.x;
   const double* ys = y + s * nodes;
   double contrib = 0.0;
   if (n < nodes) {
@@ -104,8 +104,14 @@ __global__ void k_phi_finish(const double* __restrict__ partial, int nblk, int S
   if (lane == 0) phi[s] = 0.5 * v;
 }
 
-void launch_phi_adjrhs(const double* y, int N, int S, double* badj, double* phi, double* partial, cudaStream_t st) {
+void launch_phi_adjrhs(const double* y, int N, int S, double* badj, double* phi, double* partial, const double* gtab,
+                       const double* mgtab, cudaStream_t st) {
   if (S == 0) return;
+  if (N >= kTiledMinN && gtab != nullptr) {
+    const int nb = tiled_phi(y, N, S, gtab, mgtab, badj, partial, st);
+    launch("phi_finish", 0.0, k_phi_finish, dim3((S + 7) / 8), 256, 0, st, (const double*)partial, nb, S, phi);
+    return;
+  }
   const int nb = node_blocks(N);
   launch("phi_adjrhs", (double)S * nodes_of(N) * 16, k_phi_adjrhs, dim3(nb, S), kBlock, 0, st, y, N, badj, partial);
   launch("phi_finish", 0.0, k_phi_finish, dim3((S + 7) / 8), 256, 0, st, (const double*)partial, nb, S, phi);

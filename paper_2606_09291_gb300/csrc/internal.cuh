@@ -26,6 +26,11 @@ template <typename T> __device__ __forceinline__ T load_coef(const __nv_bfloat16
   return (T)__bfloat162float(*p);
 }
 
+// value already in registers / shared memory, converted to the arithmetic type
+template <typename T> __device__ __forceinline__ T smem_coef(double v) { return (T)v; }
+template <typename T> __device__ __forceinline__ T smem_coef(float v) { return (T)v; }
+template <typename T> __device__ __forceinline__ T smem_coef(__nv_bfloat16 v) { return (T)__bfloat162float(v); }
+
 // ---------------------------------------------------------------- Philox4x32-10
 // Salmon, Moraes, Dror, Shaw, "Parallel random numbers: as easy as 1, 2, 3"
 // (SC'11): 10 rounds; a round multiplies counter words 0 and 2 by the two
@@ -108,11 +113,11 @@ __device__ __forceinline__ T q1_row(const Cells8<T, TA>& C, const T* __restrict_
   return acc;
 }
 
-__device__ __forceinline__ void node_ijk(long long n, int n1, int& i, int& j, int& k) {
-  i = (int)(n % n1);
-  const long long t = n / n1;
-  j = (int)(t % n1);
-  k = (int)(t / n1);
+__device__ __forceinline__ void node_ijk(int n, int n1, int& i, int& j, int& k) {
+  const unsigned t = (unsigned)n / (unsigned)n1;
+  i = n - (int)t * n1;
+  k = (int)(t / (unsigned)n1);
+  j = (int)t - k * n1;
 }
 __device__ __forceinline__ bool interior(int i, int j, int k, int N) {
   return i > 0 && j > 0 && k > 0 && i < N && j < N && k < N;
@@ -125,16 +130,17 @@ __device__ __forceinline__ T warp_sum(T v) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   return v;
 }
-// block of kBlock threads; returns the sum in thread 0
+// block of kBlock threads (1-, 2- or 3-D); returns the sum in linear thread 0
 template <typename T>
 __device__ __forceinline__ T block_sum(T v) {
   __shared__ T red[kBlock / 32];
+  const int tid = threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z);
   v = warp_sum(v);
-  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  const int w = tid >> 5, l = tid & 31;
   if (l == 0) red[w] = v;
   __syncthreads();
   T s = T(0);
-  if (threadIdx.x < 32) {
+  if (tid < 32) {
     s = (l < kBlock / 32) ? red[l] : T(0);
     s = warp_sum(s);
   }

@@ -90,11 +90,31 @@ void build_hierarchy_mixed(SolverBufs& B, const __nv_bfloat16* abf, cudaStream_t
 size_t solver_bytes(int N, int S, int elem);
 void carve_solver(SolverBufs& B, int N, int S, int elem, char*& ptr);
 
+// tiled fine-grid kernels (tiled.cu); partial sums land in [S][blocks_per_sample]
+struct TiledShape { int bx, by, nzc, zc, blocks_per_sample; };
+TiledShape tiled_shape(int N, int S, int rows_per_thread);
+// partial-sum blocks per sample of the solver passes for elements of `elem` bytes
+int tiled_blocks_per_sample(int N, int S, int elem);
+template <typename T, typename TA>
+void tiled_apply(const T* z, const T* pold, T* pnew, const TA* a, T* q, double* partial, const SolveScalars* sc, int N,
+                 int S, int first, cudaStream_t st);
+template <typename T, typename TA>
+void tiled_pre(const T* r, const TA* a, T* t, const SolveScalars* sc, int N, int S, double omega, cudaStream_t st);
+template <typename T, typename TA>
+void tiled_post(const T* r, const TA* a, const T* ec, T* z, double* partial, const SolveScalars* sc, int N, int S,
+                double omega, cudaStream_t st);
+void tiled_res64(const double* b, long long bstride, const double* x, const float* a, double* r, double* partial,
+                 const SolveScalars* sc, int N, int S, cudaStream_t st);
+// Phi and the adjoint right-hand side; returns the partial-sum blocks per sample
+int tiled_phi(const double* y, int N, int S, const double* gtab, const double* mgtab, double* badj, double* partial,
+              cudaStream_t st);
+constexpr int kTiledMinN = 16;  // grids with at least this many cells per side use the tiled kernels
+
 // ---------------------------------------------------------------- estimator
 void launch_rhs_state(const double* z, int Nc, int N, double* b, cudaStream_t st);
 // Phi = 1/2 e^T M e, badj = M e (interior rows), e = y - g_h
 void launch_phi_adjrhs(const double* y, int N, int S, double* badj, double* phi, double* partial,
-                       cudaStream_t st);
+                       const double* gtab, const double* mgtab, cudaStream_t st);
 // batch statistics of one level merged into stats (see mlsgd_level_stats)
 void launch_level_stats(const double* qf, const double* phif, int Nf, const double* qc, const double* phic,
                         int Ncoarse, int S, int Nc, double theta, double* field, double* scalars,

@@ -35,7 +35,7 @@ __global__ void k_apply_dot(const T* __restrict__ x, const TA* __restrict__ a, T
   SAMPLE_GUARD(sc);
   const int n1 = N + 1;
   const long long nodes = (long long)n1 * n1 * n1;
-  const long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const int n = blockIdx.x * blockDim.x + threadIdx.x;
   const T* xs = x + s * nodes;
   T contrib = T(0);
   if (n < nodes) {
@@ -58,7 +58,7 @@ template <typename T>
 __global__ void k_dot(const T* __restrict__ u, const T* __restrict__ v, double* __restrict__ partial,
                       const SolveScalars* __restrict__ sc, long long nodes) {
   SAMPLE_GUARD(sc);
-  const long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const int n = blockIdx.x * blockDim.x + threadIdx.x;
   T contrib = T(0);
   if (n < nodes) contrib = u[s * nodes + n] * v[s * nodes + n];
   const T b = block_sum(contrib);
@@ -66,11 +66,11 @@ __global__ void k_dot(const T* __restrict__ u, const T* __restrict__ v, double* 
 }
 
 // x += alpha p; r -= alpha q; partial = r.r
-template <typename T>
+template <typename T, bool REDUCE>
 __global__ void k_update_xr(T* __restrict__ x, T* __restrict__ r, const T* __restrict__ p, const T* __restrict__ q,
                             double* __restrict__ partial, const SolveScalars* __restrict__ sc, long long nodes) {
   SAMPLE_GUARD(sc);
-  const long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const int n = blockIdx.x * blockDim.x + threadIdx.x;
   const T al = (T)sc[s].alpha;
   T contrib = T(0);
   if (n < nodes) {
@@ -80,15 +80,17 @@ __global__ void k_update_xr(T* __restrict__ x, T* __restrict__ r, const T* __res
     r[o] = rn;
     contrib = rn * rn;
   }
-  const T b = block_sum(contrib);
-  if (threadIdx.x == 0) partial[(long long)s * gridDim.x + blockIdx.x] = (double)b;
+  if (REDUCE) {
+    const T b = block_sum(contrib);
+    if (threadIdx.x == 0) partial[(long long)s * gridDim.x + blockIdx.x] = (double)b;
+  }
 }
 
 template <typename T>
 __global__ void k_p_update(T* __restrict__ p, const T* __restrict__ z, const SolveScalars* __restrict__ sc,
                            long long nodes, int first) {
   SAMPLE_GUARD(sc);
-  const long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const int n = blockIdx.x * blockDim.x + threadIdx.x;
   if (n < nodes) {
     const long long o = s * nodes + n;
     p[o] = first ? z[o] : z[o] + (T)sc[s].beta * p[o];
@@ -100,7 +102,7 @@ template <typename T>
 __global__ void k_init(const double* __restrict__ b, long long bstride, T* __restrict__ r, T* __restrict__ x,
                        double* __restrict__ partial, long long nodes) {
   const int s = blockIdx.y;
-  const long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const int n = blockIdx.x * blockDim.x + threadIdx.x;
   double contrib = 0.0;
   if (n < nodes) {
     const double bv = b[s * bstride + n];
@@ -171,7 +173,7 @@ __global__ void k_jacobi0(const T* __restrict__ r, const TA* __restrict__ a, T* 
   SAMPLE_GUARD(sc);
   const int n1 = N + 1;
   const long long nodes = (long long)n1 * n1 * n1;
-  const long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const int n = blockIdx.x * blockDim.x + threadIdx.x;
   if (n >= nodes) return;
   int i, j, k;
   node_ijk(n, n1, i, j, k);
@@ -191,7 +193,7 @@ __global__ void k_resid_smooth(const T* __restrict__ r, const T* __restrict__ x,
   SAMPLE_GUARD(sc);
   const int n1 = N + 1;
   const long long nodes = (long long)n1 * n1 * n1;
-  const long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const int n = blockIdx.x * blockDim.x + threadIdx.x;
   if (n >= nodes) return;
   int i, j, k;
   node_ijk(n, n1, i, j, k);
@@ -213,7 +215,7 @@ __global__ void k_restrict(const T* __restrict__ tf, T* __restrict__ rc, const S
   SAMPLE_GUARD(sc);
   const int n1c = Nc + 1, Nf = 2 * Nc, n1f = Nf + 1;
   const long long nc = (long long)n1c * n1c * n1c, nf = (long long)n1f * n1f * n1f;
-  const long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const int n = blockIdx.x * blockDim.x + threadIdx.x;
   if (n >= nc) return;
   int I, J, K;
   node_ijk(n, n1c, I, J, K);
@@ -240,7 +242,7 @@ __global__ void k_prolong_add(T* __restrict__ xf, const T* __restrict__ ec, cons
   SAMPLE_GUARD(sc);
   const int n1f = Nf + 1, Nc = Nf / 2, n1c = Nc + 1;
   const long long nf = (long long)n1f * n1f * n1f, nc = (long long)n1c * n1c * n1c;
-  const long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const int n = blockIdx.x * blockDim.x + threadIdx.x;
   if (n >= nf) return;
   int i, j, k;
   node_ijk(n, n1f, i, j, k);
@@ -304,7 +306,7 @@ __global__ void k_residual64(const double* __restrict__ b, long long bstride, co
   SAMPLE_GUARD(sc);
   const int n1 = N + 1;
   const long long nodes = (long long)n1 * n1 * n1;
-  const long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const int n = blockIdx.x * blockDim.x + threadIdx.x;
   double contrib = 0.0;
   if (n < nodes) {
     int i, j, k;
@@ -326,7 +328,7 @@ __global__ void k_residual64(const double* __restrict__ b, long long bstride, co
 __global__ void k_demote(const double* __restrict__ r64, float* __restrict__ r32, float* __restrict__ d,
                          const SolveScalars* __restrict__ sc, long long nodes) {
   SAMPLE_GUARD(sc);
-  const long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const int n = blockIdx.x * blockDim.x + threadIdx.x;
   if (n < nodes) {
     r32[s * nodes + n] = (float)r64[s * nodes + n];
     d[s * nodes + n] = 0.0f;
@@ -337,7 +339,7 @@ __global__ void k_demote(const double* __restrict__ r64, float* __restrict__ r32
 __global__ void k_accumulate(double* __restrict__ x, const float* __restrict__ d, const SolveScalars* __restrict__ sc,
                              long long nodes) {
   SAMPLE_GUARD(sc);
-  const long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const int n = blockIdx.x * blockDim.x + threadIdx.x;
   if (n < nodes) x[s * nodes + n] += (double)d[s * nodes + n];
 }
 
@@ -421,14 +423,21 @@ void build_hierarchy_mixed(SolverBufs& B, const __nv_bfloat16* abf, cudaStream_t
 }
 
 // One V(1,1)-cycle on r0 (level-0 coefficient a0); the result is left in vt[0].
+// Grids with N >= kTiledMinN run the fine level with the tiled passes (PRE
+// fuses the pre-smoothing into the residual, POST fuses prolongation,
+// post-smoothing and the r.z partial sums, which land in B.partial);
+// returns the partial-sum blocks per sample of r.z, or 0 if not computed.
 template <typename T, typename TA0>
-static void vcycle(SolverBufs& B, const T* r0, const TA0* a0, const SolveScalars* sc, T omega, cudaStream_t st) {
+static int vcycle(SolverBufs& B, const T* r0, const TA0* a0, const SolveScalars* sc, T omega, cudaStream_t st) {
   const int S = B.S, J = B.J;
+  const bool tiled = B.N >= kTiledMinN && J >= 1;
   auto rin = [&](int j) { return j == 0 ? r0 : (const T*)B.vr[j]; };
   for (int j = 0; j < J; ++j) {
     const int Nj = B.N >> j;
     const bool fine = j == 0;
-    if (fine) {
+    if (fine && tiled) {
+      tiled_pre<T, TA0>(r0, a0, (T*)B.vt[0], sc, Nj, S, (double)omega, st);
+    } else if (fine) {
       launch(cls<T>("jacobi0", true), nbytes<T, TA0>(Nj, S, 2, 1), k_jacobi0<T, TA0>, grid_nodes(Nj, S), kBlock, 0,
              st, rin(0), a0, (T*)B.vx[0], sc, Nj, omega);
       launch(cls<T>("resid", true), nbytes<T, TA0>(Nj, S, 3, 1), k_resid_smooth<T, TA0, 0>, grid_nodes(Nj, S), kBlock,
@@ -451,6 +460,10 @@ static void vcycle(SolverBufs& B, const T* r0, const TA0* a0, const SolveScalars
   for (int j = J - 1; j >= 0; --j) {
     const int Nj = B.N >> j;
     const bool fine = j == 0;
+    if (fine && tiled) {
+      tiled_post<T, TA0>(r0, a0, (const T*)B.vt[1], (T*)B.vt[0], B.partial, sc, Nj, S, (double)omega, st);
+      return tiled_blocks_per_sample(Nj, S, (int)sizeof(T));
+    }
     launch(cls<T>("prolong", fine), nbytes<T, T>(Nj, S, 2, 0) + nbytes<T, T>(Nj / 2, S, 1, 0), k_prolong_add<T>,
            grid_nodes(Nj, S), kBlock, 0, st, (T*)B.vx[j], (const T*)B.vt[j + 1], sc, Nj);
     if (fine)
@@ -460,13 +473,14 @@ static void vcycle(SolverBufs& B, const T* r0, const TA0* a0, const SolveScalars
       launch(cls<T>("smooth", false), nbytes<T, T>(Nj, S, 3, 1), k_resid_smooth<T, T, 1>, grid_nodes(Nj, S), kBlock, 0,
              st, rin(j), (const T*)B.vx[j], (const T*)B.acoef[j], (T*)B.vt[j], sc, Nj, omega);
   }
+  return 0;
 }
 
-static void scalar(SolverBufs& B, SolveScalars* sc, int mode, double tol2, int max_iter, cudaStream_t st,
+static void scalar(SolverBufs& B, SolveScalars* sc, int mode, double tol2, int max_iter, cudaStream_t st, int nblk,
                    int inner_iters = 0, const SolveScalars* outer = nullptr) {
   const int warps = 8;
-  launch("scalar", 0.0, k_scalar, dim3((B.S + warps - 1) / warps), 32 * warps, 0, st, (const double*)B.partial,
-         node_blocks(B.N), sc, B.S, mode, tol2, max_iter, inner_iters, outer);
+  launch("scalar", 0.0, k_scalar, dim3((B.S + warps - 1) / warps), 32 * warps, 0, st, (const double*)B.partial, nblk,
+         sc, B.S, mode, tol2, max_iter, inner_iters, outer);
 }
 
 static cudaError_t count_active(SolverBufs& B, const SolveScalars* sc, cudaStream_t st, int& n) {
@@ -486,28 +500,50 @@ static cudaError_t pcg_loop(SolverBufs& B, const TAop* aop, const TA0* a0, T* x,
   const int S = B.S, N = B.N;
   const long long nodes = nodes_of(N);
   const dim3 g = grid_nodes(N, S);
+  const int nb = node_blocks(N);
   const T omega = (T)prm.omega;
-  T* p = (T*)B.p;
+  const bool tiled = N >= kTiledMinN && B.J >= 1;
+  T* pbuf[2] = {(T*)B.p, (T*)B.vx[0]};  // tiled: ping-pong p (vx[0] is unused there)
+  int cur = 0;
   T* q = (T*)B.q;
-  vcycle<T, TA0>(B, r, a0, sc, omega, st);
   const T* z = (const T*)B.vt[0];
-  launch(cls<T>("dot", true), nbytes<T, T>(N, S, 2, 0), k_dot<T>, g, kBlock, 0, st, (const T*)r, z, B.partial,
-         (const SolveScalars*)sc, nodes);
-  scalar(B, sc, SM_RZ0, 0, 0, st);
-  launch(cls<T>("pupdate", true), nbytes<T, T>(N, S, 2, 0), k_p_update<T>, g, kBlock, 0, st, p, z,
-         (const SolveScalars*)sc, nodes, 1);
+  auto precondition = [&](int mode) {
+    const int nrz = vcycle<T, TA0>(B, r, a0, sc, omega, st);
+    if (nrz == 0) {
+      launch(cls<T>("dot", true), nbytes<T, T>(N, S, 2, 0), k_dot<T>, g, kBlock, 0, st, (const T*)r, z, B.partial,
+             (const SolveScalars*)sc, nodes);
+      scalar(B, sc, mode, 0, 0, st, nb);
+    } else {
+      scalar(B, sc, mode, 0, 0, st, nrz);
+    }
+  };
+  precondition(SM_RZ0);
+  if (!tiled)
+    launch(cls<T>("pupdate", true), nbytes<T, T>(N, S, 2, 0), k_p_update<T>, g, kBlock, 0, st, pbuf[0], z,
+           (const SolveScalars*)sc, nodes, 1);
   const double tol2 = prm.rtol * prm.rtol;
   const int nit = fixed_iters > 0 ? fixed_iters : prm.max_iter;
+  const int napply = tiled ? tiled_blocks_per_sample(N, S, (int)sizeof(T)) : nb;
   for (int it = 0; it < nit; ++it) {
-    launch(cls<T>("apply", true), nbytes<T, TAop>(N, S, 2, 1), k_apply_dot<T, TAop>, g, kBlock, 0, st, (const T*)p,
-           aop, q, B.partial, (const SolveScalars*)sc, N);
-    scalar(B, sc, SM_ALPHA, 0, 0, st);
-    launch(cls<T>("update", true), nbytes<T, T>(N, S, 6, 0), k_update_xr<T>, g, kBlock, 0, st, x, r, (const T*)p,
-           (const T*)q, B.partial, (const SolveScalars*)sc, nodes);
+    T* p;
+    if (tiled) {
+      p = pbuf[cur ^ 1];
+      tiled_apply<T, TAop>(z, pbuf[cur], p, aop, q, B.partial, sc, N, S, it == 0, st);
+      cur ^= 1;
+    } else {
+      p = pbuf[0];
+      launch(cls<T>("apply", true), nbytes<T, TAop>(N, S, 2, 1), k_apply_dot<T, TAop>, g, kBlock, 0, st, (const T*)p,
+             aop, q, B.partial, (const SolveScalars*)sc, N);
+    }
+    scalar(B, sc, SM_ALPHA, 0, 0, st, napply);
     if (fixed_iters > 0) {
+      launch(cls<T>("update", true), nbytes<T, T>(N, S, 6, 0), k_update_xr<T, false>, g, kBlock, 0, st, x, r,
+             (const T*)p, (const T*)q, B.partial, (const SolveScalars*)sc, nodes);
       if (it == nit - 1) break;
     } else {
-      scalar(B, sc, SM_CONV, tol2, prm.max_iter, st);
+      launch(cls<T>("update", true), nbytes<T, T>(N, S, 6, 0), k_update_xr<T, true>, g, kBlock, 0, st, x, r,
+             (const T*)p, (const T*)q, B.partial, (const SolveScalars*)sc, nodes);
+      scalar(B, sc, SM_CONV, tol2, prm.max_iter, st, nb);
       if ((it + 1) % prm.check_every == 0 || it + 1 == nit) {
         int n = 0;
         cudaError_t e = count_active(B, sc, st, n);
@@ -515,24 +551,37 @@ static cudaError_t pcg_loop(SolverBufs& B, const TAop* aop, const TA0* a0, T* x,
         if (n == 0) break;
       }
     }
-    vcycle<T, TA0>(B, r, a0, sc, omega, st);
-    launch(cls<T>("dot", true), nbytes<T, T>(N, S, 2, 0), k_dot<T>, g, kBlock, 0, st, (const T*)r, z, B.partial,
-           (const SolveScalars*)sc, nodes);
-    scalar(B, sc, SM_BETA, 0, 0, st);
-    launch(cls<T>("pupdate", true), nbytes<T, T>(N, S, 3, 0), k_p_update<T>, g, kBlock, 0, st, p, z,
-           (const SolveScalars*)sc, nodes, 0);
+    precondition(SM_BETA);
+    if (!tiled)
+      launch(cls<T>("pupdate", true), nbytes<T, T>(N, S, 3, 0), k_p_update<T>, g, kBlock, 0, st, pbuf[0], z,
+             (const SolveScalars*)sc, nodes, 0);
   }
   return cudaGetLastError();
+}
+
+// Buffers the tiled passes write only on interior nodes must hold zero
+// boundary nodes: clear them once per solve.
+static cudaError_t clear_tiled(SolverBufs& B, int elem, cudaStream_t st) {
+  if (!(B.N >= kTiledMinN && B.J >= 1)) return cudaSuccess;
+  const size_t v = (size_t)B.S * nodes_of(B.N) * elem;
+  void* bufs[4] = {B.p, B.vx[0], B.q, B.vt[0]};
+  for (void* b : bufs) {
+    cudaError_t e = cudaMemsetAsync(b, 0, v, st);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
 }
 
 cudaError_t pcg_fp64(SolverBufs& B, const double* a64, const double* b, long long bstride, double* x_out,
                      const PcgParams& prm, cudaStream_t st) {
   const dim3 g = grid_nodes(B.N, B.S);
   double* r = (double*)B.r;
+  cudaError_t e = clear_tiled(B, 8, st);
+  if (e != cudaSuccess) return e;
   const double bb = (double)(bstride ? B.S : 1) * nodes_of(B.N) * 8;
   launch("init_f64", bb + nbytes<double, double>(B.N, B.S, 2, 0), k_init<double>, g, kBlock, 0, st, b, bstride, r,
          x_out, B.partial, nodes_of(B.N));
-  scalar(B, B.sc, SM_INIT, 0, 0, st);
+  scalar(B, B.sc, SM_INIT, 0, 0, st, node_blocks(B.N));
   return pcg_loop<double, double, double>(B, a64, a64, x_out, r, B.sc, prm, 0, st);
 }
 
@@ -541,33 +590,42 @@ cudaError_t ir_mixed(SolverBufs& B, const float* a32, const __nv_bfloat16* abf, 
   const int N = B.N, S = B.S;
   const long long nodes = nodes_of(N);
   const dim3 g = grid_nodes(N, S);
+  const int nb = node_blocks(N);
+  const bool tiled = N >= kTiledMinN && B.J >= 1;
   SolveScalars* sco = B.sc;
   SolveScalars* sci = B.sc + S;
   float* d = (float*)B.x;
   float* r32 = (float*)B.r;
   const double tol2 = prm.rtol * prm.rtol;
   const double bb = (double)(bstride ? S : 1) * nodes * 8;
+  cudaError_t e = clear_tiled(B, 4, st);
+  if (e != cudaSuccess) return e;
   launch("init_f64", bb + nbytes<double, double>(N, S, 2, 0), k_init<double>, g, kBlock, 0, st, b, bstride, r64,
          x_out, B.partial, nodes);
-  scalar(B, sco, SM_INIT, 0, 0, st);
+  scalar(B, sco, SM_INIT, 0, 0, st, nb);
   for (int step = 0;; ++step) {
     if (step > 0) {
-      launch("resid64", bb + nbytes<double, float>(N, S, 2, 1), k_residual64<float>, g, kBlock, 0, st, b, bstride,
-             (const double*)x_out, a32, r64, B.partial, (const SolveScalars*)sco, N);
-      scalar(B, sco, SM_OUTER_CONV, tol2, prm.max_iter, st);
+      if (tiled) {
+        tiled_res64(b, bstride, x_out, a32, r64, B.partial, sco, N, S, st);
+        scalar(B, sco, SM_OUTER_CONV, tol2, prm.max_iter, st, tiled_blocks_per_sample(N, S, 8));
+      } else {
+        launch("resid64", bb + nbytes<double, float>(N, S, 2, 1), k_residual64<float>, g, kBlock, 0, st, b, bstride,
+               (const double*)x_out, a32, r64, B.partial, (const SolveScalars*)sco, N);
+        scalar(B, sco, SM_OUTER_CONV, tol2, prm.max_iter, st, nb);
+      }
     }
     int n = 0;
-    cudaError_t e = count_active(B, sco, st, n);
+    e = count_active(B, sco, st, n);
     if (e != cudaSuccess) return e;
     if (n == 0) break;
     launch("demote", (double)S * nodes * 16, k_demote, g, kBlock, 0, st, (const double*)r64, r32, d,
            (const SolveScalars*)sco, nodes);
-    scalar(B, sci, SM_INNER_BEGIN, 0, 0, st, 0, sco);
+    scalar(B, sci, SM_INNER_BEGIN, 0, 0, st, nb, 0, sco);
     e = pcg_loop<float, float, __nv_bfloat16>(B, a32, abf, d, r32, sci, prm, inner_iters, st);
     if (e != cudaSuccess) return e;
     launch("accum", (double)S * nodes * 20, k_accumulate, g, kBlock, 0, st, x_out, (const float*)d,
            (const SolveScalars*)sco, nodes);
-    scalar(B, sco, SM_OUTER_STEP, 0, 0, st, inner_iters);
+    scalar(B, sco, SM_OUTER_STEP, 0, 0, st, nb, inner_iters);
   }
   return cudaGetLastError();
 }

@@ -1,0 +1,536 @@
+// tiled.cu - z-marching shared-memory kernels for the fine-grid passes of the
+// solver (rows a4, a6) and for Phi / the adjoint right-hand side (row a5).
+//
+// Layout: a block of 32 x 8 threads owns a 32 x 8 tile of interior nodes
+// (x0 = 1 + 32 bx, y0 = 1 + 8 by) and marches along z over a chunk of interior
+// planes.  Each node plane of an input vector is staged once into shared
+// memory with a one-node halo (34 x 10), each cell plane with a two-cell halo
+// (35 x 11); three planes of each are kept in a ring.  So every value is read
+// from HBM about once per pass (halos come from L2) and there is no integer
+// division in the index arithmetic.  Node (lx, ly) of the staged plane is the
+// global node (x0 - 1 + lx, y0 - 1 + ly); its eight surrounding cells are the
+// staged cells (lx + p, ly + q), p, q in {0, 1}, of two cell planes.
+//
+// Fused passes (FE operator A: see q1_row in internal.cuh; D = (h/3) sum_8 a):
+//   APPLY : pn = z + beta p (pn = z on the first iteration); q = A pn;
+//           writes p = pn, q; partial p.q
+//   PRE   : x1 = omega D^{-1} r computed on the fly; t = r - A x1
+//   POST  : x2 = omega D^{-1} r + P e_c on the fly;
+//           z = x2 + omega D^{-1} (r - A x2); partial r.z
+//   RES64 : r = b - A x in FP64 (x FP64, a FP32), partial r.r
+// Vectors keep zero boundary nodes; only interior nodes are written.
+#include <cstdio>
+
+#include "internal.cuh"
+#include "kernels.h"
+#include "launch.h"
+
+namespace mlsgd {
+
+constexpr int TX = 32, TY = 8;
+constexpr int NPX = TX + 2, NPY = TY + 2, NP = NPX * NPY;  // node plane 34 x 10
+constexpr int CPX = TX + 3, CPY = TY + 3, CP = CPX * CPY;  // cell plane 35 x 11
+constexpr int NT = TX * TY;
+
+enum TiledMode { TM_APPLY = 0, TM_PRE = 1, TM_POST = 2, TM_RES64 = 3 };
+
+struct TiledArgs {
+  const void* in0;   // APPLY: z   PRE/POST: r    RES64: x (FP64)
+  const void* in1;   // APPLY: p (old)                RES64: b (FP64)
+  const void* ec;    // POST: coarse correction (grid N/2)
+  const void* a;     // cell coefficient
+  void* out0;        // APPLY: q   PRE: t   POST: z   RES64: r
+  void* out1;        // APPLY: p (new)
+  double* partial;   // [S][blocks per sample]
+  const SolveScalars* sc;
+  long long bstride; // RES64: b stride per sample (0 = shared)
+  int N;
+  int nzc;           // z chunks per sample
+  int zc;            // planes per chunk
+  int first;         // APPLY: first iteration (pn = z)
+  double omega;
+};
+
+__device__ __forceinline__ int ring3(int m) { return (m + 3) % 3; }
+
+// ---------------------------------------------------------------- async staging
+// cp.async (4- or 8-byte, zero-filled when the source is outside the grid)
+template <int BYTES>
+__device__ __forceinline__ void cp_async(void* smem, const void* gmem, bool valid) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  const int src = valid ? BYTES : 0;
+  asm volatile("cp.async.ca.shared.global [%0], [%1], %2, %3;\n" ::"r"(sa), "l"(gmem), "n"(BYTES), "r"(src)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+
+constexpr int RING = 5;   // raw planes resident: k-1, k, k+1 + two in flight
+constexpr int ERING = 4;  // coarse planes
+constexpr int CW = TX + 4;  // staged cell row: 36 cells from x0 - 3 (even start)
+constexpr int EWX = TX / 2 + 2;
+
+// Tile geometry for RY nodes per thread in y (block 32 x 8 threads, tile 32 x 8*RY nodes).
+template <int RY>
+struct Geo {
+  static constexpr int TYT = TY * RY;
+  static constexpr int NPYT = TYT + 2, NPL = NPX * NPYT;  // staged node plane (34 x (TYT+2))
+  static constexpr int CPYT = TYT + 3, CPL = CW * CPYT;   // staged cell plane (36 x (TYT+3))
+  static constexpr int EWYT = TYT / 2 + 2, EPL = EWX * EWYT;  // staged coarse plane
+};
+
+template <typename T> struct RowsPerThread { static constexpr int value = 4; };
+template <> struct RowsPerThread<double> { static constexpr int value = 2; };
+
+template <typename T, typename TA, int MODE>
+struct TiledSmem {
+  static constexpr int RY = RowsPerThread<T>::value;
+  using G = Geo<RY>;
+  static constexpr bool kPre = (MODE == TM_PRE || MODE == TM_POST);
+  static constexpr size_t raw0 = 0;
+  static constexpr size_t raw1 = raw0 + sizeof(T) * RING * G::NPL;
+  static constexpr size_t xs = raw1 + (MODE == TM_APPLY ? sizeof(T) * RING * G::NPL : 0);
+  static constexpr size_t s4 = xs + sizeof(T) * 3 * G::NPL;
+  static constexpr size_t ec = s4 + (kPre ? sizeof(T) * 3 * G::NPL : 0);
+  static constexpr size_t cells = ec + (MODE == TM_POST ? sizeof(T) * ERING * G::EPL : 0);
+  static constexpr size_t total = cells + sizeof(TA) * RING * G::CPL;
+};
+
+template <typename T> __device__ __forceinline__ T fdiv(T a, T b) { return a / b; }
+template <> __device__ __forceinline__ float fdiv<float>(float a, float b) { return __fdividef(a, b); }
+
+template <typename T, typename TA, int MODE>
+__global__ void __launch_bounds__(NT) k_tiled(TiledArgs A) {
+  using L = TiledSmem<T, TA, MODE>;
+  constexpr int RY = L::RY;
+  using G = typename L::G;
+  constexpr int NPL = G::NPL, CPL = G::CPL, EPL = G::EPL;
+  constexpr bool kPre = L::kPre;
+  constexpr bool kPairs = sizeof(TA) == 2;                 // BF16 cells staged as 4-byte pairs
+  constexpr int NCE = kPairs ? CPL / 2 : CPL;              // cell staging entries per plane
+  constexpr int MN = (NPL + NT - 1) / NT, MC = (NCE + NT - 1) / NT, ME = (EPL + NT - 1) / NT;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  T* raw0 = (T*)(smraw + L::raw0);
+  T* raw1 = (T*)(smraw + L::raw1);
+  T* xs = (T*)(smraw + L::xs);
+  T* s4 = (T*)(smraw + L::s4);
+  T* ecs = (T*)(smraw + L::ec);
+  TA* cs = (TA*)(smraw + L::cells);
+  const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * TX + tx;
+  const int N = A.N, n1 = N + 1;
+  const int s = blockIdx.z / A.nzc, chunk = blockIdx.z % A.nzc;
+  if (A.sc != nullptr && !A.sc[s].active) return;
+  const int x0 = 1 + TX * blockIdx.x, y0 = 1 + G::TYT * blockIdx.y;
+  const long long nodes = (long long)n1 * n1 * n1, cells = (long long)N * N * N;
+  const int kbeg = 1 + chunk * A.zc;
+  const int kend = min(N - 1, kbeg + A.zc - 1);
+  const T scale = T(1.0 / (12.0 * N));
+  const T dscale = T(4) * scale;  // D = (h/3) sum_8 a = dscale * sum_8 a
+  const T omega = (T)A.omega;
+  const T* in0 = (const T*)A.in0 + s * nodes;
+  const T* in1 = (MODE == TM_APPLY) ? (const T*)A.in1 + s * nodes : in0;
+  const TA* a = (const TA*)A.a + s * cells;
+  const int nc1 = N / 2 + 1;
+  const T* e0 = (MODE == TM_POST) ? (const T*)A.ec + s * (long long)nc1 * nc1 * nc1 : in0;
+  const int ex0 = (x0 - 1) / 2, ey0 = (y0 - 1) / 2;  // coarse tile origin
+  const long long pn = (long long)n1 * n1, pc = (long long)N * N, pe = (long long)nc1 * nc1;
+  T beta = T(0);
+  if (MODE == TM_APPLY && !A.first) beta = (T)A.sc[s].beta;
+
+  // ---- per-thread staging entries, fixed for the whole march (only the plane offset moves)
+  int noff[MN], dcb[MN], deb[MN];
+  unsigned char nflag[MN];  // bit0: entry exists, bit1: inside grid, bit2: interior (x,y), bit3/4: gi/gj odd
+#pragma unroll
+  for (int j = 0; j < MN; ++j) {
+    const int e = tid + j * NT;
+    const int lx = e % NPX, ly = e / NPX;
+    const int gi = x0 - 1 + lx, gj = y0 - 1 + ly;
+    const bool has = e < NPL, in = has && gi <= N && gj <= N;
+    const bool inter = has && gi > 0 && gj > 0 && gi < N && gj < N;
+    nflag[j] = (has ? 1 : 0) | (in ? 2 : 0) | (inter ? 4 : 0) | ((gi & 1) ? 8 : 0) | ((gj & 1) ? 16 : 0);
+    noff[j] = in ? gi + n1 * gj : 0;
+    dcb[j] = lx + 1 + CW * ly;
+    deb[j] = ((gi >> 1) - ex0) + EWX * ((gj >> 1) - ey0);
+  }
+  int coff[MC], cdst[MC];
+  bool cok[MC], chas[MC];
+#pragma unroll
+  for (int j = 0; j < MC; ++j) {
+    const int e = tid + j * NT;
+    const int cx = kPairs ? 2 * (e % (CW / 2)) : e % CW;
+    const int cy = kPairs ? e / (CW / 2) : e / CW;
+    const int gi = x0 - 3 + cx, gj = y0 - 2 + cy;
+    chas[j] = e < NCE;
+    cok[j] = chas[j] && gi >= 0 && gj >= 0 && gi + (kPairs ? 1 : 0) < N && gj < N;
+    coff[j] = cok[j] ? gi + N * gj : 0;
+    cdst[j] = cx + CW * cy;
+  }
+  int eoff[ME];
+  bool eok[ME], ehas[ME];
+#pragma unroll
+  for (int j = 0; j < ME; ++j) {
+    const int e = tid + j * NT;
+    const int ci = ex0 + e % EWX, cj = ey0 + e / EWX;
+    ehas[j] = (MODE == TM_POST) && e < EPL;
+    eok[j] = ehas[j] && ci < nc1 && cj < nc1;
+    eoff[j] = eok[j] ? ci + nc1 * cj : 0;
+  }
+  int coarse_issued = -1000;
+
+  auto issue = [&](int m) {
+    const int slot = (m + 2 * RING) % RING;
+    const bool mok = m >= 0 && m <= N;
+    const long long mo = mok ? (long long)m * pn : 0;
+#pragma unroll
+    for (int j = 0; j < MN; ++j) {
+      if (!(nflag[j] & 1)) continue;
+      const int e = tid + j * NT;
+      const bool ok = mok && (nflag[j] & 2);
+      cp_async<sizeof(T)>(raw0 + slot * NPL + e, in0 + (ok ? mo + noff[j] : 0), ok);
+      if (MODE == TM_APPLY && !A.first) cp_async<sizeof(T)>(raw1 + slot * NPL + e, in1 + (ok ? mo + noff[j] : 0), ok);
+    }
+    const bool cmok = m >= 0 && m < N;
+    const long long cmo = cmok ? (long long)m * pc : 0;
+#pragma unroll
+    for (int j = 0; j < MC; ++j) {
+      if (!chas[j]) continue;
+      const bool ok = cmok && cok[j];
+      cp_async<kPairs ? 4 : sizeof(TA)>(cs + slot * CPL + cdst[j], a + (ok ? cmo + coff[j] : 0), ok);
+    }
+    if (MODE == TM_POST) {
+      for (int c = (m >= 0 ? m / 2 : -1); c <= (m + 1) / 2; ++c) {
+        if (c <= coarse_issued) continue;
+        coarse_issued = c;
+        const bool cok2 = c >= 0 && c < nc1;
+#pragma unroll
+        for (int j = 0; j < ME; ++j) {
+          if (!ehas[j]) continue;
+          const bool ok = cok2 && eok[j];
+          cp_async<sizeof(T)>(ecs + ((c + 4 * ERING) % ERING) * EPL + tid + j * NT, e0 + (ok ? c * pe + eoff[j] : 0),
+                              ok);
+        }
+      }
+    }
+    cp_async_commit();
+  };
+
+  // operand plane m from its staged raw plane (plus 4-cell sums for PRE/POST)
+  auto derive = [&](int m) {
+    const int slot = (m + 2 * RING) % RING;
+    T* xp = xs + ring3(m) * NPL;
+    const T* r0 = raw0 + slot * NPL;
+    if (MODE == TM_APPLY) {
+      const T* r1 = raw1 + slot * NPL;
+#pragma unroll
+      for (int j = 0; j < MN; ++j) {
+        if (!(nflag[j] & 1)) continue;
+        const int e = tid + j * NT;
+        xp[e] = A.first ? r0[e] : r0[e] + beta * r1[e];
+      }
+    } else if (MODE == TM_RES64) {
+#pragma unroll
+      for (int j = 0; j < MN; ++j)
+        if (nflag[j] & 1) xp[tid + j * NT] = r0[tid + j * NT];
+    } else {
+      const T* sprev = s4 + ring3(m - 1) * NPL;
+      T* scur = s4 + ring3(m) * NPL;
+      const TA* cpl = cs + slot * CPL;
+      const bool mint = m > 0 && m < N;
+      const int dk = m & 1;
+      const T* c0p = ecs + ((m >> 1) % ERING) * EPL;
+      const T* c1p = ecs + (((m >> 1) + dk) % ERING) * EPL;
+#pragma unroll
+      for (int j = 0; j < MN; ++j) {
+        if (!(nflag[j] & 1)) continue;
+        const int e = tid + j * NT;
+        const TA* cb = cpl + dcb[j];
+        const T sum = (smem_coef<T>(cb[0]) + smem_coef<T>(cb[1])) + (smem_coef<T>(cb[CW]) + smem_coef<T>(cb[CW + 1]));
+        scur[e] = sum;
+        T v = T(0);
+        if (mint && (nflag[j] & 4)) {
+          v = fdiv<T>(omega * r0[e], dscale * (sprev[e] + sum));
+          if (MODE == TM_POST) {
+            const int b = deb[j];
+            const bool di = nflag[j] & 8, dj = nflag[j] & 16;
+            T acc = c0p[b] + (di ? c0p[b + 1] : T(0)) + (dj ? c0p[b + EWX] : T(0)) + ((di && dj) ? c0p[b + EWX + 1] : T(0));
+            if (dk) acc += c1p[b] + (di ? c1p[b + 1] : T(0)) + (dj ? c1p[b + EWX] : T(0)) + ((di && dj) ? c1p[b + EWX + 1] : T(0));
+            const T w = (di ? T(0.5) : T(1)) * (dj ? T(0.5) : T(1)) * (dk ? T(0.5) : T(1));
+            v += w * acc;
+          }
+        }
+        xp[e] = v;
+      }
+    }
+  };
+
+  // prologue: derive the planes before kbeg, keep two planes in flight
+  const int first_plane = kPre ? kbeg - 2 : kbeg - 1;
+  for (int m = first_plane; m <= kbeg + 2; ++m) issue(m);
+  cp_async_wait<2>();
+  __syncthreads();
+  for (int m = first_plane; m <= kbeg; ++m) {
+    derive(m);
+    __syncthreads();
+  }
+
+  // this thread's column: gi, rows gj = y0 + RY*ty + t (t < RY); staged node rows RY*ty + 1 + t
+  T red = T(0);
+  const int gi = x0 + tx;
+  const int gj0 = y0 + RY * ty;
+  const bool colok = gi < N;
+  const int xb = tx + NPX * (RY * ty);        // staged node (tx, RY*ty): top-left of the 3 x (RY+2) window
+  const int cbn = (tx + 2) + CW * (RY * ty + 1);  // staged cell (gi-1, gj0-1)
+  T* out0 = (T*)A.out0 + s * nodes + gi + (long long)n1 * gj0;
+  T* out1 = (MODE == TM_APPLY) ? (T*)A.out1 + s * nodes + gi + (long long)n1 * gj0 : nullptr;
+  const T* bptr = (MODE == TM_RES64) ? (const T*)A.in1 + s * A.bstride + gi + (long long)n1 * gj0 : nullptr;
+  for (int k = kbeg; k <= kend; ++k) {
+    issue(k + 3);
+    cp_async_wait<2>();
+    __syncthreads();
+    derive(k + 1);
+    __syncthreads();
+    if (colok) {
+      // registers: operand window X[plane][col][row] (3 x 3 x (RY+2)), cells C[r][p][row] (2 x 2 x (RY+1))
+      T X[3][3][RY + 2];
+      T C[2][2][RY + 1];
+#pragma unroll
+      for (int pl = 0; pl < 3; ++pl) {
+        const T* xp = xs + ring3(k - 1 + pl) * NPL + xb;
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+#pragma unroll
+          for (int rr = 0; rr < RY + 2; ++rr) X[pl][c][rr] = xp[c + NPX * rr];
+      }
+#pragma unroll
+      for (int r = 0; r < 2; ++r) {
+        const TA* cp = cs + ((k - 1 + r + 2 * RING) % RING) * CPL + cbn;
+#pragma unroll
+        for (int p = 0; p < 2; ++p)
+#pragma unroll
+          for (int cr = 0; cr < RY + 1; ++cr) C[r][p][cr] = smem_coef<T>(cp[p + CW * cr]);
+      }
+      const T* rk = raw0 + ((k + 2 * RING) % RING) * NPL + xb + 1 + NPX;
+#pragma unroll
+      for (int t = 0; t < RY; ++t) {
+        if (gj0 + t >= N) break;
+        // cells of node t: c[r][q][p] = C[r][p][t + q]; neighbour (du, dv) in plane pl: X[pl][1 + du][t + 1 + dv]
+        T pxy[2][2], pxz[2][2], pyz[2][2];
+#pragma unroll
+        for (int u = 0; u < 2; ++u)
+#pragma unroll
+          for (int v = 0; v < 2; ++v) {
+            pxy[v][u] = C[0][u][t + v] + C[1][u][t + v];   // cells (u, v, 0), (u, v, 1)
+            pxz[v][u] = C[v][u][t] + C[v][u][t + 1];       // cells (u, 0, v), (u, 1, v)
+            pyz[v][u] = C[v][0][t + u] + C[v][1][t + u];   // cells (0, u, v), (1, u, v)
+          }
+        const T sum8 = (pxy[0][0] + pxy[0][1]) + (pxy[1][0] + pxy[1][1]);
+        T acc = T(4) * sum8 * X[1][1][t + 1];
+#pragma unroll
+        for (int v = 0; v < 2; ++v)
+#pragma unroll
+          for (int u = 0; u < 2; ++u) acc -= pxy[v][u] * X[1][2 * u][t + 2 * v];
+#pragma unroll
+        for (int r = 0; r < 2; ++r) {
+          const int pl = 2 * r;  // plane k-1 (r = 0) or k+1 (r = 1)
+#pragma unroll
+          for (int u = 0; u < 2; ++u) {
+            acc -= pxz[r][u] * X[pl][2 * u][t + 1];
+            acc -= pyz[r][u] * X[pl][1][t + 2 * u];
+          }
+#pragma unroll
+          for (int q = 0; q < 2; ++q)
+#pragma unroll
+            for (int p = 0; p < 2; ++p) acc -= C[r][p][t + q] * X[pl][2 * p][t + 2 * q];
+        }
+        const T ax = scale * acc;
+        const long long o = (long long)n1 * n1 * k + (long long)n1 * t;
+        if (MODE == TM_APPLY) {
+          const T pv = X[1][1][t + 1];
+          out0[o] = ax;
+          out1[o] = pv;
+          red += pv * ax;
+        } else if (MODE == TM_PRE) {
+          out0[o] = rk[NPX * t] - ax;
+        } else if (MODE == TM_POST) {
+          const T rv = rk[NPX * t];
+          const T zv = X[1][1][t + 1] + fdiv<T>(omega * (rv - ax), dscale * sum8);
+          out0[o] = zv;
+          red += rv * zv;
+        } else {  // RES64
+          const T rv = bptr[o] - ax;
+          out0[o] = rv;
+          red += rv * rv;
+        }
+      }
+    }
+    __syncthreads();
+  }
+  cp_async_wait<0>();
+  if (MODE != TM_PRE) {
+    const T b = block_sum(red);
+    if (tid == 0) {
+      const int per = gridDim.x * gridDim.y * A.nzc;
+      const int bid = (chunk * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
+      A.partial[(long long)s * per + bid] = (double)b;
+    }
+  }
+}
+
+// Phi = 1/2 e^T M e and badj = M e on interior rows, e = y - g_h (row a5).
+// The consistent Q1 mass is (h/6)^3 [1 4 1] x [1 4 1] x [1 4 1]: a staged plane of
+// y is summed along x, then y, into the tile; three such planes combine along z.
+// g_h = gx(i) gx(j) gx(k) and M g_h = mg(i) mg(j) mg(k) are separable, so they
+// come from the 1D tables gtab[i] = sin(pi i / N) (0 at i = 0, N) and
+// mgtab[i] = (h/6)(g[i-1] + 4 g[i] + g[i+1]).
+__global__ void __launch_bounds__(NT) k_phi_tiled(const double* __restrict__ y, int N, const double* __restrict__ gtab,
+                                                  const double* __restrict__ mgtab, double* __restrict__ badj,
+                                                  double* __restrict__ partial, int nzc, int zc) {
+  __shared__ double ys[NP];
+  __shared__ double xsum[NPY][TX];
+  __shared__ double mxy[3][NT];
+  const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * TX + tx;
+  const int n1 = N + 1;
+  const int s = blockIdx.z / nzc, chunk = blockIdx.z % nzc;
+  const int x0 = 1 + TX * blockIdx.x, y0 = 1 + TY * blockIdx.y;
+  const long long nodes = (long long)n1 * n1 * n1;
+  const double* yb = y + s * nodes;
+  const int kbeg = 1 + chunk * zc;
+  const int kend = min(N - 1, kbeg + zc - 1);
+  const int gi = x0 + tx, gj = y0 + ty;
+  const bool mine = gi < N && gj < N;
+  double ycen[3] = {0.0, 0.0, 0.0};
+  auto advance = [&](int m) {
+    for (int e = tid; e < NP; e += NT) {
+      const int lx = e % NPX, ly = e / NPX;
+      const int i = x0 - 1 + lx, j = y0 - 1 + ly;
+      ys[e] = (m >= 0 && m <= N && i <= N && j <= N) ? yb[i + (long long)n1 * (j + (long long)n1 * m)] : 0.0;
+    }
+    __syncthreads();
+    for (int e = tid; e < NPY * TX; e += NT) {
+      const int ly = e / TX, lx = e % TX;
+      const double* row = ys + NPX * ly + lx;
+      xsum[ly][lx] = row[0] + 4.0 * row[1] + row[2];
+    }
+    ycen[(m + 3) % 3] = ys[(tx + 1) + NPX * (ty + 1)];
+    __syncthreads();
+    mxy[(m + 3) % 3][tid] = xsum[ty][tx] + 4.0 * xsum[ty + 1][tx] + xsum[ty + 2][tx];
+    __syncthreads();
+  };
+  const double h6 = 1.0 / (6.0 * N), h63 = h6 * h6 * h6;
+  double red = 0.0;
+  advance(kbeg - 1);
+  advance(kbeg);
+  for (int k = kbeg; k <= kend; ++k) {
+    advance(k + 1);
+    if (mine) {
+      const double my = mxy[(k + 2) % 3][tid] + 4.0 * mxy[k % 3][tid] + mxy[(k + 1) % 3][tid];
+      const double me = h63 * my - mgtab[gi] * mgtab[gj] * mgtab[k];
+      const double e = ycen[k % 3] - gtab[gi] * gtab[gj] * gtab[k];
+      badj[s * nodes + gi + (long long)n1 * (gj + (long long)n1 * k)] = me;
+      red += e * me;
+    }
+  }
+  const double b = block_sum(red);
+  if (tid == 0) partial[(long long)s * (gridDim.x * gridDim.y * nzc) + (chunk * gridDim.y + blockIdx.y) * gridDim.x +
+                        blockIdx.x] = b;
+}
+
+// ---------------------------------------------------------------- host side
+
+TiledShape tiled_shape(int N, int S, int ry) {
+  TiledShape t;
+  t.bx = (N - 1 + TX - 1) / TX;
+  t.by = (N - 1 + TY * ry - 1) / (TY * ry);
+  // enough blocks to fill the GPU: split z when the batch is small
+  const long long base = (long long)t.bx * t.by * S;
+  int nzc = 1;
+  while (base * nzc < 4 * 152 * 4 && nzc * 8 < N - 1) nzc *= 2;
+  t.nzc = nzc;
+  t.zc = (N - 1 + nzc - 1) / nzc;
+  t.blocks_per_sample = t.bx * t.by * t.nzc;
+  return t;
+}
+
+template <typename T, typename TA, int MODE>
+static void run_tiled(const char* cls, double bytes, TiledArgs args, int S, cudaStream_t st) {
+  const TiledShape t = tiled_shape(args.N, S, RowsPerThread<T>::value);
+  args.nzc = t.nzc;
+  args.zc = t.zc;
+  const size_t smem = TiledSmem<T, TA, MODE>::total;  // up to ~91 KB (FP64): opt in above 48 KB
+  if (smem > 48 * 1024) cudaFuncSetAttribute(k_tiled<T, TA, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  launch(cls, bytes, k_tiled<T, TA, MODE>, dim3(t.bx, t.by, (unsigned)(S * t.nzc)), dim3(TX, TY), smem, st, args);
+}
+
+template <typename T, typename TA>
+static double vbytes(int N, int S, double vec, double coef) {
+  return (double)S * (vec * (double)nodes_of(N) * sizeof(T) + coef * (double)cells_of(N) * sizeof(TA));
+}
+
+template <typename T> const char* tag();
+template <> const char* tag<double>() { return "f64"; }
+template <> const char* tag<float>() { return "f32"; }
+static const char* name(const char* base, const char* t) {
+  static thread_local char buf[64];
+  snprintf(buf, sizeof(buf), "%s_%s", base, t);
+  return buf;
+}
+
+// p is double-buffered: neighbouring tiles read the old p in their halos while
+// this tile writes the new one.
+template <typename T, typename TA>
+void tiled_apply(const T* z, const T* pold, T* pnew, const TA* a, T* q, double* partial, const SolveScalars* sc, int N,
+                 int S, int first, cudaStream_t st) {
+  TiledArgs A{};
+  A.in0 = z; A.in1 = pold; A.a = a; A.out0 = q; A.out1 = pnew; A.partial = partial; A.sc = sc; A.N = N;
+  A.first = first;
+  run_tiled<T, TA, TM_APPLY>(name("apply", tag<T>()), vbytes<T, TA>(N, S, first ? 3 : 4, 1), A, S, st);
+}
+template <typename T, typename TA>
+void tiled_pre(const T* r, const TA* a, T* t, const SolveScalars* sc, int N, int S, double omega, cudaStream_t st) {
+  TiledArgs A{};
+  A.in0 = r; A.a = a; A.out0 = t; A.sc = sc; A.N = N; A.omega = omega;
+  run_tiled<T, TA, TM_PRE>(name("pre", tag<T>()), vbytes<T, TA>(N, S, 2, 1), A, S, st);
+}
+template <typename T, typename TA>
+void tiled_post(const T* r, const TA* a, const T* ec, T* z, double* partial, const SolveScalars* sc, int N, int S,
+                double omega, cudaStream_t st) {
+  TiledArgs A{};
+  A.in0 = r; A.a = a; A.ec = ec; A.out0 = z; A.partial = partial; A.sc = sc; A.N = N; A.omega = omega;
+  run_tiled<T, TA, TM_POST>(name("post", tag<T>()), vbytes<T, TA>(N, S, 2, 1) + vbytes<T, T>(N / 2, S, 1, 0), A, S,
+                            st);
+}
+void tiled_res64(const double* b, long long bstride, const double* x, const float* a, double* r, double* partial,
+                 const SolveScalars* sc, int N, int S, cudaStream_t st) {
+  TiledArgs A{};
+  A.in0 = x; A.in1 = b; A.bstride = bstride; A.a = a; A.out0 = r; A.partial = partial; A.sc = sc; A.N = N;
+  const double bb = (double)(bstride ? S : 1) * nodes_of(N) * 8;
+  run_tiled<double, float, TM_RES64>("resid64", bb + vbytes<double, float>(N, S, 2, 1), A, S, st);
+}
+
+int tiled_phi(const double* y, int N, int S, const double* gtab, const double* mgtab, double* badj, double* partial,
+              cudaStream_t st) {
+  const TiledShape t = tiled_shape(N, S, 1);
+  launch("phi_adjrhs", (double)S * nodes_of(N) * 16, k_phi_tiled, dim3(t.bx, t.by, (unsigned)(S * t.nzc)),
+         dim3(TX, TY), 0, st, y, N, gtab, mgtab, badj, partial, t.nzc, t.zc);
+  return t.blocks_per_sample;
+}
+
+template void tiled_apply<float, float>(const float*, const float*, float*, const float*, float*, double*,
+                                        const SolveScalars*, int, int, int, cudaStream_t);
+template void tiled_apply<double, double>(const double*, const double*, double*, const double*, double*, double*,
+                                          const SolveScalars*, int, int, int, cudaStream_t);
+template void tiled_pre<float, __nv_bfloat16>(const float*, const __nv_bfloat16*, float*, const SolveScalars*, int, int,
+                                              double, cudaStream_t);
+template void tiled_pre<double, double>(const double*, const double*, double*, const SolveScalars*, int, int, double,
+                                        cudaStream_t);
+template void tiled_post<float, __nv_bfloat16>(const float*, const __nv_bfloat16*, const float*, float*, double*,
+                                               const SolveScalars*, int, int, double, cudaStream_t);
+template void tiled_post<double, double>(const double*, const double*, const double*, double*, double*,
+                                         const SolveScalars*, int, int, double, cudaStream_t);
+
+}  // namespace mlsgd
+
+namespace mlsgd {
+int tiled_blocks_per_sample(int N, int S, int elem) { return tiled_shape(N, S, elem == 8 ? 2 : 4).blocks_per_sample; }
+}  // namespace mlsgd
