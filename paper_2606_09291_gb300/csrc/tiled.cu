@@ -100,6 +100,27 @@ struct TiledSmem {
 template <typename T> __device__ __forceinline__ T fdiv(T a, T b) { return a / b; }
 template <> __device__ __forceinline__ float fdiv<float>(float a, float b) { return __fdividef(a, b); }
 
+// ---- error-free FP32 arithmetic for the refinement residual (TM_RES64)
+// two_sum: s + e == a + b exactly (Knuth); products use the FMA to split
+// c * x into p + pe exactly.  A coefficient is an unevaluated pair (h, l).
+struct F2 { float h, l; };
+__device__ __forceinline__ F2 two_sum(float a, float b) {
+  const float s = a + b;
+  const float bb = s - a;
+  return F2{s, (a - (s - bb)) + (b - bb)};
+}
+// (S, comp) += sgn * (c.h + c.l) * (x.x + x.y), sgn = +1 or -1
+template <bool NEG>
+__device__ __forceinline__ void df_term(float& S, float& comp, F2 c, float2 x) {
+  const float p = c.h * x.x;
+  const float pe = __fmaf_rn(c.h, x.x, -p);
+  const float low = __fmaf_rn(c.h, x.y, __fmaf_rn(c.l, x.x, pe));
+  const float q = NEG ? -p : p;
+  const F2 t = two_sum(S, q);
+  S = t.h;
+  comp += t.l + (NEG ? -low : low);
+}
+
 template <typename T, typename TA, int MODE>
 __global__ void __launch_bounds__(NT) k_tiled(TiledArgs A) {
   using L = TiledSmem<T, TA, MODE>;
@@ -229,9 +250,15 @@ __global__ void __launch_bounds__(NT) k_tiled(TiledArgs A) {
         xp[e] = A.first ? r0[e] : r0[e] + beta * r1[e];
       }
     } else if (MODE == TM_RES64) {
+      // x = hi + lo with hi, lo FP32 (one FP64 subtraction per staged value)
+      float2* xp2 = reinterpret_cast<float2*>(xp);
 #pragma unroll
       for (int j = 0; j < MN; ++j)
-        if (nflag[j] & 1) xp[tid + j * NT] = r0[tid + j * NT];
+        if (nflag[j] & 1) {
+          const double xd = (double)r0[tid + j * NT];
+          const float hi = __double2float_rn(xd);
+          xp2[tid + j * NT] = make_float2(hi, __double2float_rn(xd - (double)hi));
+        }
     } else {
       const T* sprev = s4 + ring3(m - 1) * NPL;
       T* scur = s4 + ring3(m) * NPL;
@@ -290,7 +317,77 @@ __global__ void __launch_bounds__(NT) k_tiled(TiledArgs A) {
     __syncthreads();
     derive(k + 1);
     __syncthreads();
-    if (colok) {
+    if constexpr (MODE == TM_RES64) {
+      if (colok) {
+        // b - A x with x = hi + lo (FP32 pairs) and FP32 cells, error-free products and
+        // compensated sums: exact pair sums of cells, exact products, one rounding of the
+        // unevaluated sum (S, comp) per term; the result is assembled in FP64.
+        float2 X[3][3][RY + 2];
+        float C[2][2][RY + 1];
+#pragma unroll
+        for (int pl = 0; pl < 3; ++pl) {
+          const float2* xp = reinterpret_cast<const float2*>(xs + ring3(k - 1 + pl) * NPL) + xb;
+#pragma unroll
+          for (int c = 0; c < 3; ++c)
+#pragma unroll
+            for (int rr = 0; rr < RY + 2; ++rr) X[pl][c][rr] = xp[c + NPX * rr];
+        }
+#pragma unroll
+        for (int r = 0; r < 2; ++r) {
+          const TA* cp = cs + ((k - 1 + r + 2 * RING) % RING) * CPL + cbn;
+#pragma unroll
+          for (int p = 0; p < 2; ++p)
+#pragma unroll
+            for (int cr = 0; cr < RY + 1; ++cr) C[r][p][cr] = (float)cp[p + CW * cr];
+        }
+#pragma unroll
+        for (int t = 0; t < RY; ++t) {
+          if (gj0 + t >= N) break;
+          F2 pxy[2][2], pxz[2][2], pyz[2][2];
+#pragma unroll
+          for (int u = 0; u < 2; ++u)
+#pragma unroll
+            for (int v = 0; v < 2; ++v) {
+              pxy[v][u] = two_sum(C[0][u][t + v], C[1][u][t + v]);
+              pxz[v][u] = two_sum(C[v][u][t], C[v][u][t + 1]);
+              pyz[v][u] = two_sum(C[v][0][t + u], C[v][1][t + u]);
+            }
+          float S8 = 0.f, E8 = 0.f;
+#pragma unroll
+          for (int v = 0; v < 2; ++v)
+#pragma unroll
+            for (int u = 0; u < 2; ++u) {
+              const F2 q = two_sum(S8, pxy[v][u].h);
+              S8 = q.h;
+              E8 += q.l + pxy[v][u].l;
+            }
+          float S = 0.f, comp = 0.f;
+          df_term<false>(S, comp, F2{4.f * S8, 4.f * E8}, X[1][1][t + 1]);
+#pragma unroll
+          for (int v = 0; v < 2; ++v)
+#pragma unroll
+            for (int u = 0; u < 2; ++u) df_term<true>(S, comp, pxy[v][u], X[1][2 * u][t + 2 * v]);
+#pragma unroll
+          for (int r = 0; r < 2; ++r) {
+            const int pl = 2 * r;
+#pragma unroll
+            for (int u = 0; u < 2; ++u) {
+              df_term<true>(S, comp, pxz[r][u], X[pl][2 * u][t + 1]);
+              df_term<true>(S, comp, pyz[r][u], X[pl][1][t + 2 * u]);
+            }
+#pragma unroll
+            for (int q = 0; q < 2; ++q)
+#pragma unroll
+              for (int p = 0; p < 2; ++p) df_term<true>(S, comp, F2{C[r][p][t + q], 0.f}, X[pl][2 * p][t + 2 * q]);
+          }
+          const double ax = ((double)S + (double)comp) * (1.0 / (12.0 * N));
+          const long long o = (long long)n1 * n1 * k + (long long)n1 * t;
+          const double rv = (double)bptr[o] - ax;
+          out0[o] = (T)rv;
+          red += (T)(rv * rv);
+        }
+      }
+    } else if (colok) {
       // registers: operand window X[plane][col][row] (3 x 3 x (RY+2)), cells C[r][p][row] (2 x 2 x (RY+1))
       T X[3][3][RY + 2];
       T C[2][2][RY + 1];
@@ -357,10 +454,6 @@ __global__ void __launch_bounds__(NT) k_tiled(TiledArgs A) {
           const T zv = X[1][1][t + 1] + fdiv<T>(omega * (rv - ax), dscale * sum8);
           out0[o] = zv;
           red += rv * zv;
-        } else {  // RES64
-          const T rv = bptr[o] - ax;
-          out0[o] = rv;
-          red += rv * rv;
         }
       }
     }
