@@ -113,6 +113,11 @@ typedef struct {
   double eps2;        /* (eta ||grad||)^2                                              */
   int next_levels;    /* L_{k+1} (eq:optimal-level)                                    */
   int64_t next_counts[16]; /* M_{k+1,l} (eq:optimal-batch-size)                         */
+  /* inputs of the plan, for inspection */
+  double ex_norm2;         /* ||E^ML[X~]||_U^2 at the common shift                        */
+  double c_hat;            /* ||E^ML[X]||^2 / E^ML[Y]^2                                   */
+  double mean_dx_norm2[16];/* ||mean dX~_l||_U^2 (shift of level l)                       */
+  double v2[16];           /* v^2_l in unshifted units (eq:sec-order-sum)                 */
 } mlsgd_step_report;
 
 /* Create a context on the current CUDA device.  Builds the KL mode table on

@@ -598,6 +598,12 @@ mlsgd_status mlsgd_step(mlsgd_ctx* ctx, const mlsgd_level_stats* stats, int n_le
   }
   double total = 0.0;
   for (int l = 0; l < Lnext; ++l) total += std::sqrt(V[l] * C[l]);
+  rep->ex_norm2 = ex2;
+  rep->c_hat = C_hat;
+  for (int l = 0; l < L; ++l) {
+    rep->mean_dx_norm2[l] = hb[2 + l] * hc3;
+    rep->v2[l] = v2[l];
+  }
   rep->err_sam = err_sam;
   rep->err_num = err_num;
   rep->alpha_hat = alpha_hat;

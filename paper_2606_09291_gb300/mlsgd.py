@@ -35,7 +35,9 @@ class StepReport(ctypes.Structure):
     _fields_ = [("grad_norm", ctypes.c_double), ("risk", ctypes.c_double), ("ey", ctypes.c_double),
                 ("shift", ctypes.c_double), ("truncated", ctypes.c_int), ("err_sam", ctypes.c_double),
                 ("err_num", ctypes.c_double), ("alpha_hat", ctypes.c_double), ("eps2", ctypes.c_double),
-                ("next_levels", ctypes.c_int), ("next_counts", ctypes.c_int64 * 16)]
+                ("next_levels", ctypes.c_int), ("next_counts", ctypes.c_int64 * 16),
+                ("ex_norm2", ctypes.c_double), ("c_hat", ctypes.c_double),
+                ("mean_dx_norm2", ctypes.c_double * 16), ("v2", ctypes.c_double * 16)]
 
 
 class ProfileEntry(ctypes.Structure):
@@ -210,8 +212,11 @@ class Context:
         ml = self.cfg["n_levels"] if max_levels is None else max_levels
         self._check(self.L.mlsgd_step(self.h, arr, n, tau, eta, ml, _ptr(z), _ptr(grad), ctypes.byref(rep),
                                       _stream(stream)))
-        out = {k: getattr(rep, k) for k, _ in StepReport._fields_ if k != "next_counts"}
+        out = {k: getattr(rep, k) for k, _ in StepReport._fields_
+               if k not in ("next_counts", "mean_dx_norm2", "v2")}
         out["next_counts"] = [int(rep.next_counts[l]) for l in range(rep.next_levels)]
+        out["mean_dx_norm2"] = [rep.mean_dx_norm2[l] for l in range(n)]
+        out["v2"] = [rep.v2[l] for l in range(n)]
         return out
 
     # --- helpers (allocation only) --------------------------------------
