@@ -33,12 +33,14 @@ def workload_cfg(args):
     p = dict(inputs.PRESETS["c3"])
     return dict(n_levels=p["n_levels"], n0=p["n0"], n_modes=p["n_modes"], corr_len=p["corr_len"], sigma=p["sigma"],
                 theta=p["theta"], alpha=p["alpha"], seed=p["seed"], rtol=1e-8, max_iter=50,
-                precision=args.precision, max_batch=args.samples, ctrl_level=p["n_levels"] - 1)
+                precision=args.precision, max_batch=args.samples, ctrl_level=p["n_levels"] - 1,
+                field_tc=1 if args.precision == "mixed" else 0)
 
 
 def workload_name(args):
     return ("c3: %d samples/step at level 3 (64^3 cells) + level-2 partners, K=256 modes, corr 0.2, sigma 1, "
-            "theta 10, %s, rtol 1e-8" % (args.samples, "BF16 coef / FP32 MG-PCG / FP64 IR" if args.precision == "mixed"
+            "theta 10, %s, rtol 1e-8" % (args.samples, "tensor-core BF16 coef / FP32 MG-PCG / FP64 IR"
+                                          if args.precision == "mixed"
                                           else "plain FP64 MG-PCG"))
 
 
@@ -270,6 +272,15 @@ def run_gpu(args, rank, world):
                     "avg_launch_ms": per_launch_ms, "alg_bytes_per_launch": prof["bytes"] / prof["launches"],
                     "share_of_step": prof_all[dominant]["total_ms"] / total_prof}
 
+    gemm = prof_all.get("kl_gemm")
+    roof_gemm = None
+    if gemm and gemm["launches"] > 0:
+        tf = gemm["flops"] / (gemm["total_ms"] / 1e3) / 1e12
+        roof_gemm = {"bound": "tensor", "achieved": tf, "peak": peaks["bf16_tflops"], "unit": "TFLOP/s",
+                     "frac": tf / peaks["bf16_tflops"], "kernel": "kl_gemm (tcgen05, BF16 in / FP32 acc)",
+                     "launches": gemm["launches"], "avg_launch_ms": gemm["total_ms"] / gemm["launches"],
+                     "share_of_step": gemm["total_ms"] / total_prof, "peak_kind": peak_kind + " (burst)"}
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         r, dt = oracle_rate(args.cpu_samples)
@@ -290,7 +301,7 @@ def run_gpu(args, rank, world):
                            "parallelism": "replicas" if world > 1 else "single GPU"},
                 "latency_ms": {"p50": statistics.median(step_ms), "p99": p99, "per": "step (one batch)"},
                 "solver_iters_per_sample": iters_per_sample,
-                "roofline": roof, "cpu_baseline": cpu,
+                "roofline": roof, "roofline_kl_gemm": roof_gemm, "cpu_baseline": cpu,
                 "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": z.numel() * 8,
                         "d2h_bytes_per_step": (stats.field.numel() + mlsgd.NSCALARS) * 8},
                 "gpu_launches": gpu_launches, "clocks": clocks, "fp64_path": fp64,

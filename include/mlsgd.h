@@ -73,6 +73,9 @@ typedef struct {
   int precision;    /* mlsgd_precision                                               */
   int inner_iters;  /* MIXED only: FP32 PCG iterations per refinement step (0 = 6)   */
   int max_batch;    /* samples per internal chunk of mlsgd_level_gradient (0 = 256)  */
+  int field_tc;     /* MIXED only: 1 = BF16 preconditioner coefficient synthesised on the
+                       tensor cores (tcgen05 GEMM, BF16 in / FP32 accumulate); 0 = rounded
+                       from the FP64 synthesis                                        */
   uint64_t seed;
 } mlsgd_config;
 
@@ -147,6 +150,15 @@ int mlsgd_mode_table(const mlsgd_ctx* ctx, int* idx, double* lam);
  * [n_samples][n_modes] normals; log_a_dev receives [n_samples][N_grid^3]. */
 mlsgd_status mlsgd_sample_field(mlsgd_ctx* ctx, int iter, int level, int grid, int64_t first_sample,
                                 int n_samples, double* xi_dev, double* log_a_dev, void* stream);
+
+/* a2 on the tensor cores: log a[s, c] = sum_k (sigma sqrt(lambda_k) xi[s,k]) phi_k(x_c)
+ * as a BF16 x BF16 -> FP32 GEMM (samples x modes) by (modes x cells) on the same
+ * draws as mlsgd_sample_field.  log_a_f32_dev (optional) [n_samples][N^3] FP32;
+ * a_bf16_dev (optional) [n_samples][N^3] BF16 exp(log a).  Requires n_modes % 64 == 0
+ * and N^3 % 128 == 0; returns MLSGD_ENOTIMPL otherwise.  Synchronous (checks
+ * the kernel's error flag). */
+mlsgd_status mlsgd_sample_field_tc(mlsgd_ctx* ctx, int iter, int level, int grid, int64_t first_sample,
+                                   int n_samples, float* log_a_f32_dev, void* a_bf16_dev, void* stream);
 
 /* a3..a6: for each sample s, with a = exp(log_a_dev[s]) on grid level `grid`:
  * solve the state problem A y = B z (eq:sys), Phi = 1/2 (y - g_h)^T M (y - g_h)

@@ -24,6 +24,7 @@ struct mlsgd_ctx {
   std::string err;
   KLTable kl;
   int n1x = 0;
+  int* d_ix = nullptr;
   int* d_iy = nullptr;
   int* d_iz = nullptr;
   double* d_scale = nullptr;
@@ -34,6 +35,8 @@ struct mlsgd_ctx {
   std::vector<double*> d_mgtab;  // per level: [N+1] (h/6)(g[i-1] + 4 g[i] + g[i+1]) (1D mass times g)
   char* ws = nullptr;
   size_t ws_size = 0;
+  std::vector<__nv_bfloat16*> d_phiT;  // per level: tensor-core B operand [N^3][K] (built on first use)
+  int* d_err = nullptr;                // device error flag of the tensor-core kernel
   int* count_host = nullptr;
   double* host_buf = nullptr;  // pinned, for small read-backs
   ModeTable mt() const {
@@ -45,6 +48,11 @@ struct mlsgd_ctx {
   int N(int l) const { return cfg.n0 << l; }
   int Nc() const { return cfg.n0 << cfg.ctrl_level; }
   bool mixed() const { return cfg.precision == MLSGD_MIXED; }
+  bool tc_ok(int level) const {
+    const long long cells = cells_of(N(level));
+    return cfg.n_modes % 64 == 0 && cells % 128 == 0 && kl_gemm_b_bytes(N(level), cfg.n_modes) <= ((size_t)1 << 30);
+  }
+  bool use_tc(int level) const { return mixed() && cfg.field_tc && tc_ok(level); }
 };
 
 namespace {
@@ -91,6 +99,7 @@ size_t level_bytes(const mlsgd_ctx* ctx, int level, int S) {
   b += grid_keep_bytes(ctx, N, S);
   if (level > 0) b += grid_keep_bytes(ctx, N / 2, S);
   b += 2 * al((size_t)2 * S * 4);
+  b += al(kl_gemm_a_bytes(S, ctx->cfg.n_modes));
   b += solve_scratch_bytes(ctx, N, S);
   const long long ncell = cells_of(ctx->Nc());
   b += al((4 + 2 * (size_t)S) * 8) + al(((ncell + 255) / 256) * 8 + 64 * 8);
@@ -172,10 +181,30 @@ mlsgd_status solve_grid(mlsgd_ctx* ctx, int N, int S, const GridFields& f, const
   return MLSGD_OK;
 }
 
+mlsgd_status ensure_phiT(mlsgd_ctx* ctx, int grid, cudaStream_t st) {
+  if (ctx->d_phiT[grid]) return MLSGD_OK;
+  __nv_bfloat16* b = nullptr;
+  if (cudaMalloc(&b, kl_gemm_b_bytes(ctx->N(grid), ctx->cfg.n_modes)) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(ctx, MLSGD_ENOMEM, "cannot allocate the tensor-core mode table");
+  }
+  kl_gemm_build_b(ctx->d_phi[grid], ctx->d_ix, ctx->d_iy, ctx->d_iz, ctx->N(grid), ctx->cfg.n_modes, b, st);
+  ctx->d_phiT[grid] = b;
+  return MLSGD_OK;
+}
+
+// fields of one grid; with the tensor-core option the BF16 coefficient comes from the GEMM
 mlsgd_status make_field(mlsgd_ctx* ctx, const double* xi, int grid, int S, const GridFields& f, double* log_a,
-                        cudaStream_t st) {
-  FieldOut o{log_a, f.a64, f.a32, f.abf};
+                        cudaStream_t st, __nv_bfloat16* gemm_a = nullptr) {
+  const bool tc = gemm_a != nullptr && f.abf != nullptr && ctx->use_tc(grid);
+  FieldOut o{log_a, f.a64, f.a32, tc ? nullptr : f.abf};
   CK(launch_field(xi, ctx->cfg.n_modes, ctx->mt(), ctx->d_phi[grid], ctx->N(grid), S, o, st));
+  if (tc) {
+    mlsgd_status s = ensure_phiT(ctx, grid, st);
+    if (s != MLSGD_OK) return s;
+    CK(kl_gemm(xi, ctx->d_scale, S, ctx->cfg.n_modes, ctx->d_phiT[grid], ctx->N(grid), gemm_a, f.abf, nullptr,
+               ctx->d_err, st));
+  }
   return MLSGD_OK;
 }
 
@@ -247,10 +276,14 @@ mlsgd_status mlsgd_create(const mlsgd_config* cfg, mlsgd_ctx** out) {
   auto up = [&](void** d, const void* h, size_t n) -> bool {
     return cudaMalloc(d, n) == cudaSuccess && cudaMemcpy(*d, h, n, cudaMemcpyHostToDevice) == cudaSuccess;
   };
-  bool ok = up((void**)&ctx->d_iy, iy.data(), K * sizeof(int)) && up((void**)&ctx->d_iz, iz.data(), K * sizeof(int)) &&
+  std::vector<int> ixv(ctx->kl.ix.begin(), ctx->kl.ix.end());
+  const int zero = 0;
+  bool ok = up((void**)&ctx->d_ix, ixv.data(), K * sizeof(int)) && up((void**)&ctx->d_err, &zero, sizeof(int)) &&
+            up((void**)&ctx->d_iy, iy.data(), K * sizeof(int)) && up((void**)&ctx->d_iz, iz.data(), K * sizeof(int)) &&
             up((void**)&ctx->d_scale, scale.data(), K * sizeof(double)) &&
             up((void**)&ctx->d_order, order.data(), K * sizeof(int)) &&
             up((void**)&ctx->d_offs, offs.data(), (n1x + 1) * sizeof(int));
+  ctx->d_phiT.assign(c.n_levels, nullptr);
   for (int l = 0; ok && l < c.n_levels; ++l) {
     std::vector<double> phi = kl_cell_table(ctx->kl, ctx->N(l));
     double* d = nullptr;
@@ -278,6 +311,8 @@ mlsgd_status mlsgd_create(const mlsgd_config* cfg, mlsgd_ctx** out) {
 
 void mlsgd_destroy(mlsgd_ctx* ctx) {
   if (!ctx) return;
+  cudaFree(ctx->d_ix); cudaFree(ctx->d_err);
+  for (__nv_bfloat16* b : ctx->d_phiT) cudaFree(b);
   cudaFree(ctx->d_iy); cudaFree(ctx->d_iz); cudaFree(ctx->d_scale); cudaFree(ctx->d_order); cudaFree(ctx->d_offs);
   for (double* d : ctx->d_phi) cudaFree(d);
   for (double* d : ctx->d_gtab) cudaFree(d);
@@ -327,6 +362,32 @@ mlsgd_status mlsgd_sample_field(mlsgd_ctx* ctx, int iter, int level, int grid, i
     if (s != MLSGD_OK) return s;
   }
   CK(cudaGetLastError());
+  return MLSGD_OK;
+}
+
+mlsgd_status mlsgd_sample_field_tc(mlsgd_ctx* ctx, int iter, int level, int grid, int64_t first_sample,
+                                   int n_samples, float* log_a_f32_dev, void* a_bf16_dev, void* stream) {
+  if (!ctx) return MLSGD_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  if (level < 0 || level >= ctx->cfg.n_levels || (grid != level && grid != level - 1) || grid < 0 || n_samples < 0 ||
+      first_sample < 0 || iter < 0)
+    return fail(ctx, MLSGD_EINVAL, "mlsgd_sample_field_tc: bad level/grid/sizes");
+  if (!ctx->tc_ok(grid)) return fail(ctx, MLSGD_ENOTIMPL, "mlsgd_sample_field_tc: needs n_modes % 64 == 0 and N^3 % 128 == 0");
+  if (n_samples == 0) return MLSGD_OK;
+  const int K = ctx->cfg.n_modes, S = n_samples;
+  mlsgd_status s = ensure_ws(ctx, al((size_t)S * K * 8) + al(kl_gemm_a_bytes(S, K)), st);
+  if (s != MLSGD_OK) return s;
+  Bump bp{ctx->ws};
+  double* xi = bp.take<double>((size_t)S * K);
+  __nv_bfloat16* A = bp.take<__nv_bfloat16>((size_t)S * K);
+  launch_draw_xi(ctx->cfg.seed, iter, level, first_sample, S, K, xi, st);
+  s = ensure_phiT(ctx, grid, st);
+  if (s != MLSGD_OK) return s;
+  CK(kl_gemm(xi, ctx->d_scale, S, K, ctx->d_phiT[grid], ctx->N(grid), A, (__nv_bfloat16*)a_bf16_dev, log_a_f32_dev,
+             ctx->d_err, st));
+  CK(cudaMemcpyAsync(ctx->count_host, ctx->d_err, sizeof(int), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  if (*ctx->count_host != 0) return fail(ctx, MLSGD_ECUDA, "tensor-core KL synthesis timed out on a barrier");
   return MLSGD_OK;
 }
 
@@ -481,17 +542,18 @@ mlsgd_status mlsgd_level_gradient(mlsgd_ctx* ctx, int iter, int level, int64_t f
     }
     int* iters = bp.take<int>(2 * (size_t)S);
     int* status = bp.take<int>(2 * (size_t)S);
+    __nv_bfloat16* gemm_a = bp.take<__nv_bfloat16>((size_t)S * K);
     double* work = bp.take<double>(4 + 2 * (size_t)S);
     const long long ncell = cells_of(ctx->Nc());
     double* spartial = bp.take<double>((size_t)((ncell + 255) / 256) + 64);
     char* scratch = bp.p;
     launch_draw_xi(ctx->cfg.seed, iter, level, first_sample + done, S, K, xi, st);
-    s = make_field(ctx, xi, level, S, ff, nullptr, st);
+    s = make_field(ctx, xi, level, S, ff, nullptr, st, gemm_a);
     if (s != MLSGD_OK) return s;
     s = solve_grid(ctx, N, S, ff, z_dev, nullptr, qf, phif, iters, status, scratch, st);
     if (s != MLSGD_OK) return s;
     if (level > 0) {
-      s = make_field(ctx, xi, level - 1, S, fc, nullptr, st);
+      s = make_field(ctx, xi, level - 1, S, fc, nullptr, st, gemm_a);
       if (s != MLSGD_OK) return s;
       s = solve_grid(ctx, N / 2, S, fc, z_dev, nullptr, qc, phic, iters + S, status + S, scratch, st);
       if (s != MLSGD_OK) return s;
@@ -517,7 +579,9 @@ mlsgd_status mlsgd_step(mlsgd_ctx* ctx, const mlsgd_level_stats* stats, int n_le
   for (int l = 0; l < n_levels; ++l)
     CK(cudaMemcpyAsync(hb + l * MLSGD_NSCALARS, stats[l].scalars_dev, MLSGD_NSCALARS * sizeof(double),
                        cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(ctx->count_host, ctx->d_err, sizeof(int), cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
+  if (*ctx->count_host != 0) return fail(ctx, MLSGD_ECUDA, "tensor-core KL synthesis timed out on a barrier");
   std::vector<double> sc(hb, hb + n_levels * MLSGD_NSCALARS);
   double cstar = -INFINITY;
   for (int l = 0; l < n_levels; ++l) {

@@ -110,6 +110,14 @@ int tiled_phi(const double* y, int N, int S, const double* gtab, const double* m
               cudaStream_t st);
 constexpr int kTiledMinN = 16;  // grids with at least this many cells per side use the tiled kernels
 
+// tensor-core KL synthesis (kl_gemm.cu)
+size_t kl_gemm_b_bytes(int N, int K);
+size_t kl_gemm_a_bytes(int S, int K);
+void kl_gemm_build_b(const double* phi, const int* ix, const int* iy, const int* iz, int N, int K, __nv_bfloat16* B,
+                     cudaStream_t st);
+cudaError_t kl_gemm(const double* xi, const double* scale, int S, int K, const __nv_bfloat16* B, int N,
+                    __nv_bfloat16* A_scratch, __nv_bfloat16* abf, float* loga, int* err, cudaStream_t st);
+
 // ---------------------------------------------------------------- estimator
 void launch_rhs_state(const double* z, int Nc, int N, double* b, cudaStream_t st);
 // Phi = 1/2 e^T M e, badj = M e (interior rows), e = y - g_h

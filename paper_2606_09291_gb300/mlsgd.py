@@ -24,7 +24,7 @@ class Config(ctypes.Structure):
                 ("n_modes", ctypes.c_int), ("corr_len", ctypes.c_double), ("sigma", ctypes.c_double),
                 ("theta", ctypes.c_double), ("alpha", ctypes.c_double), ("rtol", ctypes.c_double),
                 ("max_iter", ctypes.c_int), ("precision", ctypes.c_int), ("inner_iters", ctypes.c_int),
-                ("max_batch", ctypes.c_int), ("seed", ctypes.c_uint64)]
+                ("max_batch", ctypes.c_int), ("field_tc", ctypes.c_int), ("seed", ctypes.c_uint64)]
 
 
 class LevelStats(ctypes.Structure):
@@ -48,7 +48,8 @@ class ProfileEntry(ctypes.Structure):
 EXPORTS = ["mlsgd_create", "mlsgd_destroy", "mlsgd_last_error", "mlsgd_status_string", "mlsgd_n_ctrl_cells",
            "mlsgd_workspace_bytes", "mlsgd_mode_table", "mlsgd_sample_field", "mlsgd_solve_state_adjoint",
            "mlsgd_level_gradient", "mlsgd_stats_reset", "mlsgd_stats_merge", "mlsgd_step",
-           "mlsgd_launch_count", "mlsgd_profile_start", "mlsgd_profile_stop", "mlsgd_solve_state_adjoint_noalloc"]
+           "mlsgd_launch_count", "mlsgd_profile_start", "mlsgd_profile_stop", "mlsgd_solve_state_adjoint_noalloc",
+           "mlsgd_sample_field_tc"]
 
 _lib = None
 
@@ -80,6 +81,7 @@ def load(path=LIB_PATH):
     L.mlsgd_stats_reset.argtypes = [vp, ctypes.POINTER(LevelStats), vp]
     L.mlsgd_stats_merge.argtypes = [vp, ctypes.POINTER(LevelStats), ctypes.POINTER(LevelStats), vp]
     L.mlsgd_step.argtypes = [vp, ctypes.POINTER(LevelStats), i32, dbl, dbl, i32, vp, vp, ctypes.POINTER(StepReport), vp]
+    L.mlsgd_sample_field_tc.argtypes = [vp, i32, i32, i32, i64, i32, vp, vp, vp]
     L.mlsgd_solve_state_adjoint_noalloc.argtypes = [vp, i32, i32, vp, vp, vp, vp, vp, vp, vp, vp]
     L.mlsgd_launch_count.argtypes = []
     L.mlsgd_launch_count.restype = i64
@@ -138,7 +140,7 @@ class Context:
         c = Config()
         defaults = dict(n_levels=3, n0=8, ctrl_level=None, n_modes=64, corr_len=0.3, sigma=1.0, theta=1.0,
                         alpha=1e-4, rtol=1e-8, max_iter=200, precision=MLSGD_FP64, inner_iters=0,
-                        max_batch=256, seed=0)
+                        max_batch=256, field_tc=0, seed=0)
         defaults.update(cfg)
         if defaults["ctrl_level"] is None:
             defaults["ctrl_level"] = defaults["n_levels"] - 1
@@ -184,6 +186,10 @@ class Context:
     def mlsgd_sample_field(self, it, level, grid, first, n, xi=None, log_a=None, stream=None):
         self._check(self.L.mlsgd_sample_field(self.h, it, level, grid, first, n, _ptr(xi), _ptr(log_a),
                                               _stream(stream)))
+
+    def mlsgd_sample_field_tc(self, it, level, grid, first, n, log_a_f32=None, a_bf16=None, stream=None):
+        self._check(self.L.mlsgd_sample_field_tc(self.h, it, level, grid, first, n, _ptr(log_a_f32), _ptr(a_bf16),
+                                                 _stream(stream)))
 
     def mlsgd_solve_state_adjoint(self, grid, n, log_a, z, y, q, phi, iters, status, stream=None):
         return self.L.mlsgd_solve_state_adjoint(self.h, grid, n, _ptr(log_a), _ptr(z), _ptr(y), _ptr(q), _ptr(phi),
