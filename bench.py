@@ -34,7 +34,7 @@ def workload_cfg(args):
     return dict(n_levels=p["n_levels"], n0=p["n0"], n_modes=p["n_modes"], corr_len=p["corr_len"], sigma=p["sigma"],
                 theta=p["theta"], alpha=p["alpha"], seed=p["seed"], rtol=1e-8, max_iter=50,
                 precision=args.precision, max_batch=args.samples, ctrl_level=p["n_levels"] - 1,
-                field_tc=1 if args.precision == "mixed" else 0)
+                field_tc=1 if args.precision == "mixed" else 0, ir_steps=args.ir_steps)
 
 
 def workload_name(args):
@@ -324,6 +324,8 @@ def main():
     ap.add_argument("--cpu-samples", type=int, default=6)
     ap.add_argument("--ref-samples", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--ir-steps", type=int, default=3,
+                    help="mixed path: fixed refinement steps per solve (masked, no host sync); 0 = adaptive")
     ap.add_argument("--traffic-bytes", type=float, default=None,
                     help="ncu dram read+write bytes per launch of the dominant kernel, if captured")
     args = ap.parse_args()

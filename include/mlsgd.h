@@ -76,6 +76,12 @@ typedef struct {
   int field_tc;     /* MIXED only: 1 = BF16 preconditioner coefficient synthesised on the
                        tensor cores (tcgen05 GEMM, BF16 in / FP32 accumulate); 0 = rounded
                        from the FP64 synthesis                                        */
+  int ir_steps;     /* MIXED only: 0 = refine until converged, checking on the host after
+                       each step; k > 0 = exactly k refinement steps per solve with no host
+                       synchronisation (per-sample masks; a sample still above rtol after k
+                       steps gets status 1).  With k > 0 and the scratch already sized (one
+                       earlier call of the same size), mlsgd_level_gradient enqueues only
+                       stream work and can be captured into a CUDA graph.             */
   uint64_t seed;
 } mlsgd_config;
 

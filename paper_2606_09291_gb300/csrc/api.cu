@@ -163,7 +163,8 @@ mlsgd_status solve_grid(mlsgd_ctx* ctx, int N, int S, const GridFields& f, const
   if (ctx->mixed()) build_hierarchy_mixed(B, f.abf, st);
   else build_hierarchy_fp64(B, f.a64, st);
   launch_rhs_state(z, ctx->Nc(), N, b, st);
-  cudaError_t e = ctx->mixed() ? ir_mixed(B, f.a32, f.abf, b, 0, ytmp, r64, prm, inner, st)
+  const int fixed = ctx->cfg.ir_steps > 0 ? ctx->cfg.ir_steps : 0;
+  cudaError_t e = ctx->mixed() ? ir_mixed(B, f.a32, f.abf, b, 0, ytmp, r64, prm, inner, st, fixed)
                                : pcg_fp64(B, f.a64, b, 0, ytmp, prm, st);
   CK(e);
   launch("record", 0.0, k_record, dim3((S + 127) / 128), 128, 0, st, (const SolveScalars*)B.sc, S, (int)ctx->mixed(),
@@ -172,7 +173,7 @@ mlsgd_status solve_grid(mlsgd_ctx* ctx, int N, int S, const GridFields& f, const
   while ((ctx->cfg.n0 << lev) < N) ++lev;
   CK(cudaMemsetAsync(badj, 0, S * nodes * sizeof(double), st));  // boundary rows stay 0
   launch_phi_adjrhs(ytmp, N, S, badj, phi, B.partial, ctx->d_gtab[lev], ctx->d_mgtab[lev], st);
-  e = ctx->mixed() ? ir_mixed(B, f.a32, f.abf, badj, (long long)nodes, q, r64, prm, inner, st)
+  e = ctx->mixed() ? ir_mixed(B, f.a32, f.abf, badj, (long long)nodes, q, r64, prm, inner, st, fixed)
                    : pcg_fp64(B, f.a64, badj, (long long)nodes, q, prm, st);
   CK(e);
   launch("record", 0.0, k_record, dim3((S + 127) / 128), 128, 0, st, (const SolveScalars*)B.sc, S, (int)ctx->mixed(),

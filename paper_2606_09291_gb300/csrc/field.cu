@@ -87,8 +87,12 @@ cudaError_t launch_field(const double* xi, int K, const ModeTable& mt, const dou
                          const FieldOut& out, cudaStream_t st) {
   if (S == 0) return cudaSuccess;
   const size_t smem = field_smem_bytes(mt, K, N);
-  cudaError_t e = cudaFuncSetAttribute(k_field, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
+  static size_t smem_set = 48 * 1024;  // raised once per size (not on every enqueue: capture-friendly)
+  if (smem > smem_set) {
+    cudaError_t e = cudaFuncSetAttribute(k_field, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    smem_set = smem;
+  }
   const double cells = (double)S * N * N * N;
   const double outb = cells * ((out.log_a ? 8 : 0) + (out.a64 ? 8 : 0) + (out.a32 ? 4 : 0) + (out.abf ? 2 : 0));
   launch_flops("field", (double)S * K * 8 + outb, 2.0 * cells * mt.n1x + 2.0 * (double)S * K * N * N, k_field,

@@ -80,9 +80,10 @@ struct PcgParams {
 cudaError_t pcg_fp64(SolverBufs& B, const double* a64, const double* b, long long bstride, double* x_out,
                      const PcgParams& prm, cudaStream_t st);
 // mixed: FP64 refinement around FP32 PCG (operator a32, V-cycle on abf)
+// fixed_steps > 0: exactly that many refinement steps, no host synchronisation
 cudaError_t ir_mixed(SolverBufs& B, const float* a32, const __nv_bfloat16* abf, const double* b,
                      long long bstride, double* x_out, double* r64, const PcgParams& prm, int inner_iters,
-                     cudaStream_t st);
+                     cudaStream_t st, int fixed_steps = 0);
 // coefficient hierarchy for the V-cycle from the level-0 coefficient
 void build_hierarchy_fp64(SolverBufs& B, const double* a64, cudaStream_t st);
 void build_hierarchy_mixed(SolverBufs& B, const __nv_bfloat16* abf, cudaStream_t st);

@@ -277,8 +277,12 @@ cudaError_t kl_gemm(const double* xi, const double* scale, int S, int K, const _
   if (!make_map(&ta, A_scratch, (uint64_t)S, (uint64_t)K, GBM) || !make_map(&tb, B, (uint64_t)cells, (uint64_t)K, GBN))
     return cudaErrorInvalidValue;
   const size_t smem = 1024 + GSTAGES * (GSTAGE_A + GSTAGE_B) + 8 * (2 * GSTAGES + 1) + 16;
-  cudaError_t e = cudaFuncSetAttribute(k_kl_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
+  static bool smem_set = false;  // once per process (capture-friendly)
+  if (!smem_set) {
+    cudaError_t e = cudaFuncSetAttribute(k_kl_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    smem_set = true;
+  }
   const long long mt = (S + GBM - 1) / GBM, nt = cells / GBN;
   const double out_bytes = (double)S * cells * ((abf ? 2 : 0) + (loga ? 4 : 0));
   launch_flops("kl_gemm", out_bytes + (double)S * K * 2 + (double)cells * K * 2, 2.0 * S * (double)cells * K,

@@ -586,7 +586,8 @@ cudaError_t pcg_fp64(SolverBufs& B, const double* a64, const double* b, long lon
 }
 
 cudaError_t ir_mixed(SolverBufs& B, const float* a32, const __nv_bfloat16* abf, const double* b, long long bstride,
-                     double* x_out, double* r64, const PcgParams& prm, int inner_iters, cudaStream_t st) {
+                     double* x_out, double* r64, const PcgParams& prm, int inner_iters, cudaStream_t st,
+                     int fixed_steps) {
   const int N = B.N, S = B.S;
   const long long nodes = nodes_of(N);
   const dim3 g = grid_nodes(N, S);
@@ -605,19 +606,24 @@ cudaError_t ir_mixed(SolverBufs& B, const float* a32, const __nv_bfloat16* abf, 
   scalar(B, sco, SM_INIT, 0, 0, st, nb);
   for (int step = 0;; ++step) {
     if (step > 0) {
+      const int cap = fixed_steps > 0 ? fixed_steps : prm.max_iter;
       if (tiled) {
         tiled_res64(b, bstride, x_out, a32, r64, B.partial, sco, N, S, st);
-        scalar(B, sco, SM_OUTER_CONV, tol2, prm.max_iter, st, tiled_blocks_per_sample(N, S, 8));
+        scalar(B, sco, SM_OUTER_CONV, tol2, cap, st, tiled_blocks_per_sample(N, S, 8));
       } else {
         launch("resid64", bb + nbytes<double, float>(N, S, 2, 1), k_residual64<float>, g, kBlock, 0, st, b, bstride,
                (const double*)x_out, a32, r64, B.partial, (const SolveScalars*)sco, N);
-        scalar(B, sco, SM_OUTER_CONV, tol2, prm.max_iter, st, nb);
+        scalar(B, sco, SM_OUTER_CONV, tol2, cap, st, nb);
       }
     }
-    int n = 0;
-    e = count_active(B, sco, st, n);
-    if (e != cudaSuccess) return e;
-    if (n == 0) break;
+    if (fixed_steps > 0) {
+      if (step == fixed_steps) break;  // masked steps: no host round trip
+    } else {
+      int n = 0;
+      e = count_active(B, sco, st, n);
+      if (e != cudaSuccess) return e;
+      if (n == 0) break;
+    }
     launch("demote", (double)S * nodes * 16, k_demote, g, kBlock, 0, st, (const double*)r64, r32, d,
            (const SolveScalars*)sco, nodes);
     scalar(B, sci, SM_INNER_BEGIN, 0, 0, st, nb, 0, sco);

@@ -551,7 +551,11 @@ static void run_tiled(const char* cls, double bytes, TiledArgs args, int S, cuda
   args.nzc = t.nzc;
   args.zc = t.zc;
   const size_t smem = TiledSmem<T, TA, MODE>::total;  // up to ~91 KB (FP64): opt in above 48 KB
-  if (smem > 48 * 1024) cudaFuncSetAttribute(k_tiled<T, TA, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  static bool smem_set = false;  // once per instantiation (capture-friendly)
+  if (smem > 48 * 1024 && !smem_set) {
+    cudaFuncSetAttribute(k_tiled<T, TA, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    smem_set = true;
+  }
   launch(cls, bytes, k_tiled<T, TA, MODE>, dim3(t.bx, t.by, (unsigned)(S * t.nzc)), dim3(TX, TY), smem, st, args);
 }
 
