@@ -37,6 +37,15 @@ void launch_draw_xi(uint64_t seed, int iter, int level, long long first, int S, 
          (uint32_t)(seed & 0xffffffffu), (uint32_t)(seed >> 32), (uint32_t)iter, (uint32_t)level, first, S, K, xi);
 }
 
+// exp(la) for an FP32 result: FP64 range reduction la = k ln2 + r, |r| <= ln2/2,
+// then the FP32 exponential of r scaled by 2^k (about 1.5 ulp of FP32; the FP64
+// exponential is reserved for the FP64 coefficient).
+__device__ __forceinline__ float exp_to_f32(double la) {
+  const double k = rint(la * 1.4426950408889634);
+  const double r = fma(-k, 0.6931471805599453, la);
+  return ldexpf(expf((float)r), (int)k);
+}
+
 // Sum-factorised synthesis.  One block per (z plane, sample):
 //   T2[i][y] = sum_{k : ix_k = i} c_k phi_{iy_k}(y) phi_{iz_k}(z),  c_k = scale_k xi_k
 //   log a(x, y, z) = sum_i T2[i][y] phi_i(x)
@@ -70,11 +79,11 @@ __global__ void k_field(const double* __restrict__ xi, int K, const ModeTable mt
     for (int i = 0; i < mt.n1x; ++i) la += T2[i * N + y] * ph[i * N + x];
     const long long o = base + e;
     if (out.log_a) out.log_a[o] = la;
-    if (out.a64 || out.a32 || out.abf) {
-      const double a = exp(la);
-      if (out.a64) out.a64[o] = a;
-      if (out.a32) out.a32[o] = (float)a;
-      if (out.abf) out.abf[o] = __float2bfloat16_rn((float)a);
+    if (out.a64) out.a64[o] = exp(la);
+    if (out.a32 || out.abf) {
+      const float a = exp_to_f32(la);
+      if (out.a32) out.a32[o] = a;
+      if (out.abf) out.abf[o] = __float2bfloat16_rn(a);
     }
   }
 }

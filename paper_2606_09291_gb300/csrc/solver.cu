@@ -437,6 +437,8 @@ static int vcycle(SolverBufs& B, const T* r0, const TA0* a0, const SolveScalars*
     const bool fine = j == 0;
     if (fine && tiled) {
       tiled_pre<T, TA0>(r0, a0, (T*)B.vt[0], sc, Nj, S, (double)omega, st);
+    } else if (!fine && tiled && Nj >= kTiledMinN) {
+      tiled_pre<T, T>(rin(j), (const T*)B.acoef[j], (T*)B.vt[j], sc, Nj, S, (double)omega, st);
     } else if (fine) {
       launch(cls<T>("jacobi0", true), nbytes<T, TA0>(Nj, S, 2, 1), k_jacobi0<T, TA0>, grid_nodes(Nj, S), kBlock, 0,
              st, rin(0), a0, (T*)B.vx[0], sc, Nj, omega);
@@ -463,6 +465,12 @@ static int vcycle(SolverBufs& B, const T* r0, const TA0* a0, const SolveScalars*
     if (fine && tiled) {
       tiled_post<T, TA0>(r0, a0, (const T*)B.vt[1], (T*)B.vt[0], B.partial, sc, Nj, S, (double)omega, st);
       return tiled_blocks_per_sample(Nj, S, (int)sizeof(T));
+    }
+    if (!fine && tiled && Nj >= kTiledMinN) {
+      // the r.z partial sums of a coarse level are overwritten by the fine level's POST
+      tiled_post<T, T>(rin(j), (const T*)B.acoef[j], (const T*)B.vt[j + 1], (T*)B.vt[j], B.partial, sc, Nj, S,
+                       (double)omega, st);
+      continue;
     }
     launch(cls<T>("prolong", fine), nbytes<T, T>(Nj, S, 2, 0) + nbytes<T, T>(Nj / 2, S, 1, 0), k_prolong_add<T>,
            grid_nodes(Nj, S), kBlock, 0, st, (T*)B.vx[j], (const T*)B.vt[j + 1], sc, Nj);
@@ -569,6 +577,11 @@ static cudaError_t clear_tiled(SolverBufs& B, int elem, cudaStream_t st) {
     cudaError_t e = cudaMemsetAsync(b, 0, v, st);
     if (e != cudaSuccess) return e;
   }
+  for (int j = 1; j < B.J; ++j)  // coarse levels run by the tiled passes write interior nodes only
+    if ((B.N >> j) >= kTiledMinN) {
+      cudaError_t e = cudaMemsetAsync(B.vt[j], 0, (size_t)B.S * nodes_of(B.N >> j) * elem, st);
+      if (e != cudaSuccess) return e;
+    }
   return cudaSuccess;
 }
 

@@ -619,6 +619,10 @@ template void tiled_apply<double, double>(const double*, const double*, double*,
                                           const SolveScalars*, int, int, int, cudaStream_t);
 template void tiled_pre<float, __nv_bfloat16>(const float*, const __nv_bfloat16*, float*, const SolveScalars*, int, int,
                                               double, cudaStream_t);
+template void tiled_pre<float, float>(const float*, const float*, float*, const SolveScalars*, int, int, double,
+                                      cudaStream_t);
+template void tiled_post<float, float>(const float*, const float*, const float*, float*, double*, const SolveScalars*,
+                                       int, int, double, cudaStream_t);
 template void tiled_pre<double, double>(const double*, const double*, double*, const SolveScalars*, int, int, double,
                                         cudaStream_t);
 template void tiled_post<float, __nv_bfloat16>(const float*, const __nv_bfloat16*, const float*, float*, double*,
