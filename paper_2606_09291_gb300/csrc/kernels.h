@@ -62,6 +62,7 @@ struct SolverBufs {
   // Krylov vectors
   void* x;                   // solution / correction
   void* r;                   // residual
+  void* r2;                  // second residual buffer (fused inner solve)
   void* p;
   void* q;                   // A p
   double* partial;           // [S][blocks]
@@ -104,6 +105,10 @@ void tiled_pre(const T* r, const TA* a, T* t, const SolveScalars* sc, int N, int
 template <typename T, typename TA>
 void tiled_post(const T* r, const TA* a, const T* ec, T* z, double* partial, const SolveScalars* sc, int N, int S,
                 double omega, cudaStream_t st);
+void tiled_apply_x(const float* z, const float* pold, float* pnew, const float* a, float* q, float* x, double* partial,
+                   const SolveScalars* sc, int N, int S, cudaStream_t st);
+void tiled_pre_update(const float* r, const float* q, const __nv_bfloat16* a, float* t, float* rnew,
+                      const SolveScalars* sc, int N, int S, double omega, cudaStream_t st);
 void tiled_res64(const double* b, long long bstride, const double* x, const float* a, double* r, double* partial,
                  const SolveScalars* sc, int N, int S, cudaStream_t st);
 // Phi and the adjoint right-hand side; returns the partial-sum blocks per sample

@@ -15,6 +15,7 @@
 // PCG iterations whose V-cycle reads the BF16 coefficient.
 #include <algorithm>
 #include <cstdio>
+#include <type_traits>
 
 #include "internal.cuh"
 #include "kernels.h"
@@ -95,6 +96,14 @@ __global__ void k_p_update(T* __restrict__ p, const T* __restrict__ z, const Sol
     const long long o = s * nodes + n;
     p[o] = first ? z[o] : z[o] + (T)sc[s].beta * p[o];
   }
+}
+
+// x += alpha p (the last update of a fused inner solve)
+template <typename T>
+__global__ void k_axpy(T* __restrict__ x, const T* __restrict__ p, const SolveScalars* __restrict__ sc, long long nodes) {
+  SAMPLE_GUARD(sc);
+  const int n = blockIdx.x * blockDim.x + threadIdx.x;
+  if (n < nodes) x[s * nodes + n] += (T)sc[s].alpha * p[s * nodes + n];
 }
 
 // r = b (shared or per sample), x = 0, partial = b.b  (not masked)
@@ -357,7 +366,7 @@ static int mg_levels(int N) {
 size_t solver_bytes(int N, int S, int elem) {
   size_t b = 0;
   const int J = mg_levels(N);
-  b += 6 * align_up((size_t)S * nodes_of(N) * elem);
+  b += 7 * align_up((size_t)S * nodes_of(N) * elem);
   for (int j = 1; j <= J; ++j) {
     const int Nj = N >> j;
     b += 3 * align_up((size_t)S * nodes_of(Nj) * elem) + align_up((size_t)S * cells_of(Nj) * elem);
@@ -374,7 +383,7 @@ void carve_solver(SolverBufs& B, int N, int S, int elem, char*& ptr) {
   B.S = S;
   B.J = mg_levels(N);
   const size_t v0 = (size_t)S * nodes_of(N) * elem;
-  B.x = take(v0); B.r = take(v0); B.p = take(v0); B.q = take(v0);
+  B.x = take(v0); B.r = take(v0); B.r2 = take(v0); B.p = take(v0); B.q = take(v0);
   B.vx[0] = take(v0); B.vt[0] = take(v0); B.vr[0] = nullptr; B.acoef[0] = nullptr;
   for (int j = 1; j <= B.J; ++j) {
     const int Nj = N >> j;
@@ -427,15 +436,22 @@ void build_hierarchy_mixed(SolverBufs& B, const __nv_bfloat16* abf, cudaStream_t
 // fuses the pre-smoothing into the residual, POST fuses prolongation,
 // post-smoothing and the r.z partial sums, which land in B.partial);
 // returns the partial-sum blocks per sample of r.z, or 0 if not computed.
+// With fuse_q the fine-level PRE first applies the CG residual update
+// r_new = r0 - alpha fuse_q (written to r_new) and the V-cycle runs on r_new.
 template <typename T, typename TA0>
-static int vcycle(SolverBufs& B, const T* r0, const TA0* a0, const SolveScalars* sc, T omega, cudaStream_t st) {
+static int vcycle(SolverBufs& B, const T* r0, const TA0* a0, const SolveScalars* sc, T omega, cudaStream_t st,
+                  const T* fuse_q = nullptr, T* r_new = nullptr) {
   const int S = B.S, J = B.J;
   const bool tiled = B.N >= kTiledMinN && J >= 1;
-  auto rin = [&](int j) { return j == 0 ? r0 : (const T*)B.vr[j]; };
+  const T* rfine = fuse_q ? r_new : r0;  // residual the V-cycle works on after the fused update
+  auto rin = [&](int j) { return j == 0 ? rfine : (const T*)B.vr[j]; };
   for (int j = 0; j < J; ++j) {
     const int Nj = B.N >> j;
     const bool fine = j == 0;
-    if (fine && tiled) {
+    if (fine && tiled && fuse_q) {
+      if constexpr (std::is_same<T, float>::value && std::is_same<TA0, __nv_bfloat16>::value)
+        tiled_pre_update(r0, fuse_q, a0, (T*)B.vt[0], r_new, sc, Nj, S, (double)omega, st);
+    } else if (fine && tiled) {
       tiled_pre<T, TA0>(r0, a0, (T*)B.vt[0], sc, Nj, S, (double)omega, st);
     } else if (!fine && tiled && Nj >= kTiledMinN) {
       tiled_pre<T, T>(rin(j), (const T*)B.acoef[j], (T*)B.vt[j], sc, Nj, S, (double)omega, st);
@@ -463,7 +479,7 @@ static int vcycle(SolverBufs& B, const T* r0, const TA0* a0, const SolveScalars*
     const int Nj = B.N >> j;
     const bool fine = j == 0;
     if (fine && tiled) {
-      tiled_post<T, TA0>(r0, a0, (const T*)B.vt[1], (T*)B.vt[0], B.partial, sc, Nj, S, (double)omega, st);
+      tiled_post<T, TA0>(rfine, a0, (const T*)B.vt[1], (T*)B.vt[0], B.partial, sc, Nj, S, (double)omega, st);
       return tiled_blocks_per_sample(Nj, S, (int)sizeof(T));
     }
     if (!fine && tiled && Nj >= kTiledMinN) {
@@ -567,12 +583,50 @@ static cudaError_t pcg_loop(SolverBufs& B, const TAop* aop, const TA0* a0, T* x,
   return cudaGetLastError();
 }
 
+// Mixed inner solve on a tiled grid, `iters` PCG iterations with the vector
+// updates fused into the stencil passes: x += alpha_prev p_old happens inside the
+// next A p pass, r -= alpha q inside the next fine pre-smoothing pass; r and p are
+// double-buffered (neighbouring tiles read the old values in their halos).
+static cudaError_t pcg_inner_fused(SolverBufs& B, const float* a32, const __nv_bfloat16* abf, float* x, float* r,
+                                   SolveScalars* sc, const PcgParams& prm, int iters, cudaStream_t st) {
+  const int S = B.S, N = B.N;
+  const long long nodes = nodes_of(N);
+  const float omega = (float)prm.omega;
+  float* rb[2] = {r, (float*)B.r2};
+  float* pb[2] = {(float*)B.p, (float*)B.vx[0]};
+  int rc = 0, pc = 0;
+  float* q = (float*)B.q;
+  const float* z = (const float*)B.vt[0];
+  const int napply = tiled_blocks_per_sample(N, S, 4);
+  int nrz = vcycle<float, __nv_bfloat16>(B, rb[rc], abf, sc, omega, st);
+  scalar(B, sc, SM_RZ0, 0, 0, st, nrz);
+  for (int it = 0; it < iters; ++it) {
+    float* pold = pb[pc];
+    float* pnew = pb[pc ^ 1];
+    if (it == 0)
+      tiled_apply<float, float>(z, pold, pnew, a32, q, B.partial, sc, N, S, 1, st);
+    else
+      tiled_apply_x(z, pold, pnew, a32, q, x, B.partial, sc, N, S, st);
+    pc ^= 1;
+    scalar(B, sc, SM_ALPHA, 0, 0, st, napply);
+    if (it == iters - 1) {
+      launch("axpy_f32", (double)S * nodes * 12, k_axpy<float>, grid_nodes(N, S), kBlock, 0, st, x, (const float*)pnew,
+             (const SolveScalars*)sc, nodes);
+      break;
+    }
+    nrz = vcycle<float, __nv_bfloat16>(B, rb[rc], abf, sc, omega, st, q, rb[rc ^ 1]);
+    rc ^= 1;
+    scalar(B, sc, SM_BETA, 0, 0, st, nrz);
+  }
+  return cudaGetLastError();
+}
+
 // Buffers the tiled passes write only on interior nodes must hold zero
 // boundary nodes: clear them once per solve.
 static cudaError_t clear_tiled(SolverBufs& B, int elem, cudaStream_t st) {
   if (!(B.N >= kTiledMinN && B.J >= 1)) return cudaSuccess;
   const size_t v = (size_t)B.S * nodes_of(B.N) * elem;
-  void* bufs[4] = {B.p, B.vx[0], B.q, B.vt[0]};
+  void* bufs[5] = {B.p, B.vx[0], B.q, B.vt[0], B.r2};
   for (void* b : bufs) {
     cudaError_t e = cudaMemsetAsync(b, 0, v, st);
     if (e != cudaSuccess) return e;
@@ -640,7 +694,8 @@ cudaError_t ir_mixed(SolverBufs& B, const float* a32, const __nv_bfloat16* abf, 
     launch("demote", (double)S * nodes * 16, k_demote, g, kBlock, 0, st, (const double*)r64, r32, d,
            (const SolveScalars*)sco, nodes);
     scalar(B, sci, SM_INNER_BEGIN, 0, 0, st, nb, 0, sco);
-    e = pcg_loop<float, float, __nv_bfloat16>(B, a32, abf, d, r32, sci, prm, inner_iters, st);
+    e = tiled ? pcg_inner_fused(B, a32, abf, d, r32, sci, prm, inner_iters, st)
+              : pcg_loop<float, float, __nv_bfloat16>(B, a32, abf, d, r32, sci, prm, inner_iters, st);
     if (e != cudaSuccess) return e;
     launch("accum", (double)S * nodes * 20, k_accumulate, g, kBlock, 0, st, x_out, (const float*)d,
            (const SolveScalars*)sco, nodes);

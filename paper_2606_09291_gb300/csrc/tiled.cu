@@ -32,7 +32,10 @@ constexpr int NPX = TX + 2, NPY = TY + 2, NP = NPX * NPY;  // node plane 34 x 10
 constexpr int CPX = TX + 3, CPY = TY + 3, CP = CPX * CPY;  // cell plane 35 x 11
 constexpr int NT = TX * TY;
 
-enum TiledMode { TM_APPLY = 0, TM_PRE = 1, TM_POST = 2, TM_RES64 = 3 };
+enum TiledMode { TM_APPLY = 0, TM_PRE = 1, TM_POST = 2, TM_RES64 = 3, TM_PREU = 4, TM_APPLYX = 5 };
+// TM_PREU  : PRE with the CG residual update fused in: r_new = r - alpha q (staged from
+//            both), t = r_new - A x1, x1 = omega D^{-1} r_new; writes t and r_new
+// TM_APPLYX: APPLY with the previous iteration's x += alpha_prev p_old fused in
 
 struct TiledArgs {
   const void* in0;   // APPLY: z   PRE/POST: r    RES64: x (FP64)
@@ -40,7 +43,9 @@ struct TiledArgs {
   const void* ec;    // POST: coarse correction (grid N/2)
   const void* a;     // cell coefficient
   void* out0;        // APPLY: q   PRE: t   POST: z   RES64: r
-  void* out1;        // APPLY: p (new)
+  void* out1;        // APPLY: p (new)   PREU: r (new)
+  const void* q;     // PREU: A p of the current iteration
+  void* x;           // APPLYX: solution updated in place with alpha_prev * p_old
   double* partial;   // [S][blocks per sample]
   const SolveScalars* sc;
   long long bstride; // RES64: b stride per sample (0 = shared)
@@ -87,10 +92,12 @@ template <typename T, typename TA, int MODE>
 struct TiledSmem {
   static constexpr int RY = RowsPerThread<T>::value;
   using G = Geo<RY>;
-  static constexpr bool kPre = (MODE == TM_PRE || MODE == TM_POST);
+  static constexpr bool kPre = (MODE == TM_PRE || MODE == TM_POST || MODE == TM_PREU);
+  static constexpr bool kApply = (MODE == TM_APPLY || MODE == TM_APPLYX);
+  static constexpr bool kRaw1 = kApply || MODE == TM_PREU;
   static constexpr size_t raw0 = 0;
   static constexpr size_t raw1 = raw0 + sizeof(T) * RING * G::NPL;
-  static constexpr size_t xs = raw1 + (MODE == TM_APPLY ? sizeof(T) * RING * G::NPL : 0);
+  static constexpr size_t xs = raw1 + (kRaw1 ? sizeof(T) * RING * G::NPL : 0);
   static constexpr size_t s4 = xs + sizeof(T) * 3 * G::NPL;
   static constexpr size_t ec = s4 + (kPre ? sizeof(T) * 3 * G::NPL : 0);
   static constexpr size_t cells = ec + (MODE == TM_POST ? sizeof(T) * ERING * G::EPL : 0);
@@ -150,14 +157,17 @@ __global__ void __launch_bounds__(NT) k_tiled(TiledArgs A) {
   const T dscale = T(4) * scale;  // D = (h/3) sum_8 a = dscale * sum_8 a
   const T omega = (T)A.omega;
   const T* in0 = (const T*)A.in0 + s * nodes;
-  const T* in1 = (MODE == TM_APPLY) ? (const T*)A.in1 + s * nodes : in0;
+  constexpr bool kApply = L::kApply;
+  const T* in1 = kApply ? (const T*)A.in1 + s * nodes : (MODE == TM_PREU ? (const T*)A.q + s * nodes : in0);
+  const bool stage1 = (kApply && !A.first) || MODE == TM_PREU;  // raw1 holds p_old or q
   const TA* a = (const TA*)A.a + s * cells;
   const int nc1 = N / 2 + 1;
   const T* e0 = (MODE == TM_POST) ? (const T*)A.ec + s * (long long)nc1 * nc1 * nc1 : in0;
   const int ex0 = (x0 - 1) / 2, ey0 = (y0 - 1) / 2;  // coarse tile origin
   const long long pn = (long long)n1 * n1, pc = (long long)N * N, pe = (long long)nc1 * nc1;
-  T beta = T(0);
-  if (MODE == TM_APPLY && !A.first) beta = (T)A.sc[s].beta;
+  T beta = T(0), alpha = T(0);
+  if (kApply && !A.first) beta = (T)A.sc[s].beta;
+  if (MODE == TM_APPLYX || MODE == TM_PREU) alpha = (T)A.sc[s].alpha;  // APPLYX: previous iteration's
 
   // ---- per-thread staging entries, fixed for the whole march (only the plane offset moves)
   int noff[MN], dcb[MN], deb[MN];
@@ -209,7 +219,7 @@ __global__ void __launch_bounds__(NT) k_tiled(TiledArgs A) {
       const int e = tid + j * NT;
       const bool ok = mok && (nflag[j] & 2);
       cp_async<sizeof(T)>(raw0 + slot * NPL + e, in0 + (ok ? mo + noff[j] : 0), ok);
-      if (MODE == TM_APPLY && !A.first) cp_async<sizeof(T)>(raw1 + slot * NPL + e, in1 + (ok ? mo + noff[j] : 0), ok);
+      if (stage1) cp_async<sizeof(T)>(raw1 + slot * NPL + e, in1 + (ok ? mo + noff[j] : 0), ok);
     }
     const bool cmok = m >= 0 && m < N;
     const long long cmo = cmok ? (long long)m * pc : 0;
@@ -241,7 +251,7 @@ __global__ void __launch_bounds__(NT) k_tiled(TiledArgs A) {
     const int slot = (m + 2 * RING) % RING;
     T* xp = xs + ring3(m) * NPL;
     const T* r0 = raw0 + slot * NPL;
-    if (MODE == TM_APPLY) {
+    if (kApply) {
       const T* r1 = raw1 + slot * NPL;
 #pragma unroll
       for (int j = 0; j < MN; ++j) {
@@ -276,7 +286,8 @@ __global__ void __launch_bounds__(NT) k_tiled(TiledArgs A) {
         scur[e] = sum;
         T v = T(0);
         if (mint && (nflag[j] & 4)) {
-          v = fdiv<T>(omega * r0[e], dscale * (sprev[e] + sum));
+          const T rn = (MODE == TM_PREU) ? r0[e] - alpha * raw1[slot * NPL + e] : r0[e];
+          v = fdiv<T>(omega * rn, dscale * (sprev[e] + sum));
           if (MODE == TM_POST) {
             const int b = deb[j];
             const bool di = nflag[j] & 8, dj = nflag[j] & 16;
@@ -309,9 +320,17 @@ __global__ void __launch_bounds__(NT) k_tiled(TiledArgs A) {
   const int xb = tx + NPX * (RY * ty);        // staged node (tx, RY*ty): top-left of the 3 x (RY+2) window
   const int cbn = (tx + 2) + CW * (RY * ty + 1);  // staged cell (gi-1, gj0-1)
   T* out0 = (T*)A.out0 + s * nodes + gi + (long long)n1 * gj0;
-  T* out1 = (MODE == TM_APPLY) ? (T*)A.out1 + s * nodes + gi + (long long)n1 * gj0 : nullptr;
+  T* out1 = (kApply || MODE == TM_PREU) ? (T*)A.out1 + s * nodes + gi + (long long)n1 * gj0 : nullptr;
+  T* xio = (MODE == TM_APPLYX) ? (T*)A.x + s * nodes + gi + (long long)n1 * gj0 : nullptr;
   const T* bptr = (MODE == TM_RES64) ? (const T*)A.in1 + s * A.bstride + gi + (long long)n1 * gj0 : nullptr;
   for (int k = kbeg; k <= kend; ++k) {
+    // APPLYX: fetch this plane's x early so the load overlaps the staging below
+    T xv[RY];
+    if (MODE == TM_APPLYX) {
+#pragma unroll
+      for (int t = 0; t < RY; ++t)
+        xv[t] = (colok && gj0 + t < N) ? xio[(long long)n1 * n1 * k + (long long)n1 * t] : T(0);
+    }
     issue(k + 3);
     cp_async_wait<2>();
     __syncthreads();
@@ -442,13 +461,18 @@ __global__ void __launch_bounds__(NT) k_tiled(TiledArgs A) {
         }
         const T ax = scale * acc;
         const long long o = (long long)n1 * n1 * k + (long long)n1 * t;
-        if (MODE == TM_APPLY) {
+        if (kApply) {
           const T pv = X[1][1][t + 1];
           out0[o] = ax;
           out1[o] = pv;
           red += pv * ax;
+          if (MODE == TM_APPLYX) xio[o] = xv[t] + alpha * raw1[((k + 2 * RING) % RING) * NPL + xb + 1 + NPX * (t + 1)];
         } else if (MODE == TM_PRE) {
           out0[o] = rk[NPX * t] - ax;
+        } else if (MODE == TM_PREU) {
+          const T rn = rk[NPX * t] - alpha * raw1[((k + 2 * RING) % RING) * NPL + xb + 1 + NPX * (t + 1)];
+          out0[o] = rn - ax;
+          out1[o] = rn;
         } else if (MODE == TM_POST) {
           const T rv = rk[NPX * t];
           const T zv = X[1][1][t + 1] + fdiv<T>(omega * (rv - ax), dscale * sum8);
@@ -460,7 +484,7 @@ __global__ void __launch_bounds__(NT) k_tiled(TiledArgs A) {
     __syncthreads();
   }
   cp_async_wait<0>();
-  if (MODE != TM_PRE) {
+  if (MODE != TM_PRE && MODE != TM_PREU) {
     const T b = block_sum(red);
     if (tid == 0) {
       const int per = gridDim.x * gridDim.y * A.nzc;
@@ -583,6 +607,20 @@ void tiled_apply(const T* z, const T* pold, T* pnew, const TA* a, T* q, double* 
   A.first = first;
   run_tiled<T, TA, TM_APPLY>(name("apply", tag<T>()), vbytes<T, TA>(N, S, first ? 3 : 4, 1), A, S, st);
 }
+// fused variants of the mixed inner solve (see TM_PREU / TM_APPLYX)
+void tiled_apply_x(const float* z, const float* pold, float* pnew, const float* a, float* q, float* x, double* partial,
+                   const SolveScalars* sc, int N, int S, cudaStream_t st) {
+  TiledArgs A{};
+  A.in0 = z; A.in1 = pold; A.a = a; A.out0 = q; A.out1 = pnew; A.x = x; A.partial = partial; A.sc = sc; A.N = N;
+  run_tiled<float, float, TM_APPLYX>("apply_f32", vbytes<float, float>(N, S, 6, 1), A, S, st);
+}
+void tiled_pre_update(const float* r, const float* q, const __nv_bfloat16* a, float* t, float* rnew,
+                      const SolveScalars* sc, int N, int S, double omega, cudaStream_t st) {
+  TiledArgs A{};
+  A.in0 = r; A.q = q; A.a = a; A.out0 = t; A.out1 = rnew; A.sc = sc; A.N = N; A.omega = omega;
+  run_tiled<float, __nv_bfloat16, TM_PREU>("pre_f32", vbytes<float, __nv_bfloat16>(N, S, 4, 1), A, S, st);
+}
+
 template <typename T, typename TA>
 void tiled_pre(const T* r, const TA* a, T* t, const SolveScalars* sc, int N, int S, double omega, cudaStream_t st) {
   TiledArgs A{};
