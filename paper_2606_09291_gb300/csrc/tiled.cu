@@ -441,25 +441,30 @@ __global__ void __launch_bounds__(NT) k_tiled(TiledArgs A) {
             pyz[v][u] = C[v][0][t + u] + C[v][1][t + u];   // cells (0, u, v), (1, u, v)
           }
         const T sum8 = (pxy[0][0] + pxy[0][1]) + (pxy[1][0] + pxy[1][1]);
-        T acc = T(4) * sum8 * X[1][1][t + 1];
+        // three independent partial sums (centre plane, plane k-1, plane k+1): shorter
+        // dependency chains than one running accumulator
+        T accp[3];
+        accp[1] = T(4) * sum8 * X[1][1][t + 1];
 #pragma unroll
         for (int v = 0; v < 2; ++v)
 #pragma unroll
-          for (int u = 0; u < 2; ++u) acc -= pxy[v][u] * X[1][2 * u][t + 2 * v];
+          for (int u = 0; u < 2; ++u) accp[1] -= pxy[v][u] * X[1][2 * u][t + 2 * v];
 #pragma unroll
         for (int r = 0; r < 2; ++r) {
           const int pl = 2 * r;  // plane k-1 (r = 0) or k+1 (r = 1)
+          T a2 = T(0);
 #pragma unroll
           for (int u = 0; u < 2; ++u) {
-            acc -= pxz[r][u] * X[pl][2 * u][t + 1];
-            acc -= pyz[r][u] * X[pl][1][t + 2 * u];
+            a2 -= pxz[r][u] * X[pl][2 * u][t + 1];
+            a2 -= pyz[r][u] * X[pl][1][t + 2 * u];
           }
 #pragma unroll
           for (int q = 0; q < 2; ++q)
 #pragma unroll
-            for (int p = 0; p < 2; ++p) acc -= C[r][p][t + q] * X[pl][2 * p][t + 2 * q];
+            for (int p = 0; p < 2; ++p) a2 -= C[r][p][t + q] * X[pl][2 * p][t + 2 * q];
+          accp[pl] = a2;
         }
-        const T ax = scale * acc;
+        const T ax = scale * (accp[1] + (accp[0] + accp[2]));
         const long long o = (long long)n1 * n1 * k + (long long)n1 * t;
         if (kApply) {
           const T pv = X[1][1][t + 1];
