@@ -82,6 +82,11 @@ typedef struct {
                        steps gets status 1).  With k > 0 and the scratch already sized (one
                        earlier call of the same size), mlsgd_level_gradient enqueues only
                        stream work and can be captured into a CUDA graph.             */
+  int field_model;  /* 0 = tensorised KL of exp(-|x-x'|/corr_len), xi ~ N(0,1);
+                       1 = the paper's Sec. 5 field: modes cos(j pi x2) cos(k pi x3) cos(l pi x1),
+                       j,k,l = 1..m, m^3 = n_modes (ordered j, k, l with l fastest),
+                       lambda = exp(-pi (j+k+l) corr_len), xi ~ U(-4, 4), not normalised */
+  int target_freq;  /* g = prod_i sin(f pi x_i): 1 for the workload, 2 for the paper (0 = 1) */
   uint64_t seed;
 } mlsgd_config;
 
@@ -131,8 +136,9 @@ typedef struct {
 
 /* Create a context on the current CUDA device.  Builds the KL mode table on
  * the host and uploads the 1D mode tables.  Returns MLSGD_EINVAL for an
- * inconsistent configuration (n_modes odd or < 2, ctrl_level outside
- * [0, n_levels), n_levels > 16, non-positive corr_len / rtol). */
+ * inconsistent configuration (n_modes < 2, odd n_modes with field_model 0,
+ * n_modes not a cube with field_model 1, ctrl_level outside [0, n_levels),
+ * n_levels > 16, non-positive corr_len / rtol). */
 mlsgd_status mlsgd_create(const mlsgd_config* cfg, mlsgd_ctx** out);
 void mlsgd_destroy(mlsgd_ctx* ctx);
 const char* mlsgd_last_error(const mlsgd_ctx* ctx);

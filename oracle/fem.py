@@ -115,10 +115,12 @@ class Level:
         i, j, k = idx % n1, (idx // n1) % n1, idx // (n1 * n1)
         return i * self.h, j * self.h, k * self.h
 
-    def nodal_target(self):
-        """Nodal interpolant of g = sin(pi x) sin(pi y) sin(pi z); exactly 0 on the boundary."""
+    def nodal_target(self, freq=1):
+        """Nodal interpolant of g = sin(f pi x) sin(f pi y) sin(f pi z) (f = 1 for the workload,
+        f = 2 for the paper's Sec. 5 target); exactly 0 on the boundary."""
         x, y, z = self.node_coords()
-        g = np.sin(np.pi * x) * np.sin(np.pi * y) * np.sin(np.pi * z)
+        w = freq * np.pi
+        g = np.sin(w * x) * np.sin(w * y) * np.sin(w * z)
         g[~np.isin(np.arange(self.nn), self.interior)] = 0.0
         return g
 

@@ -93,6 +93,32 @@ def select_3d(lam1, K):
     return idx, lam3
 
 
+class PaperKLTable:
+    """The random field of the paper's numerical experiments (Sec. 5):
+    a~(x) = sum_{j,k,l=1}^{m} sqrt(lambda_jkl) phi_jkl(x) xi_jkl with
+    phi_jkl(x) = cos(j pi x2) cos(k pi x3) cos(l pi x1) (not normalised),
+    lambda_jkl = exp(-pi (j + k + l) rho), mean 0; xi ~ U(-4, 4) is drawn elsewhere.
+    Modes are ordered (j, k, l) with l fastest; idx holds the 1D indices along
+    (x, y, z) = (l - 1, j - 1, k - 1)."""
+
+    def __init__(self, rho, m):
+        self.rho, self.m, self.n_modes = rho, m, m ** 3
+        jkl = np.array([(j, k, l) for j in range(1, m + 1) for k in range(1, m + 1) for l in range(1, m + 1)])
+        self.jkl = jkl
+        self.idx = np.stack([jkl[:, 2] - 1, jkl[:, 0] - 1, jkl[:, 1] - 1], axis=1)
+        self.lam3 = np.exp(-np.pi * jkl.sum(axis=1) * rho)
+        self.sqrt_lam3 = np.sqrt(self.lam3)
+
+    def cell_modes(self, N):
+        """Phi[mode, cell] at the N^3 cell centres, cell index ix + N (iy + N iz)."""
+        xc = (np.arange(N) + 0.5) / N
+        cz, cy, cx = np.meshgrid(xc, xc, xc, indexing="ij")
+        j, k, l = self.jkl[:, 0], self.jkl[:, 1], self.jkl[:, 2]
+        phi = (np.cos(j[:, None, None, None] * np.pi * cy[None]) * np.cos(k[:, None, None, None] * np.pi * cz[None]) *
+               np.cos(l[:, None, None, None] * np.pi * cx[None]))
+        return phi.reshape(self.n_modes, N ** 3)
+
+
 class KLTable:
     """Mode table for a workload: 1D eigenpairs plus the K selected 3D modes."""
 

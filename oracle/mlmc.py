@@ -34,14 +34,20 @@ class Workload:
     """Fixed data of one workload: levels, KL table, control grid."""
 
     def __init__(self, n0, n_levels, n_modes, corr_len, sigma, theta, alpha, seed,
-                 ctrl_level=None, rtol=1e-13, method="auto"):
+                 ctrl_level=None, rtol=1e-13, method="auto", field_model=0, target_freq=1):
         self.n0, self.n_levels = n0, n_levels
         self.ctrl_level = n_levels - 1 if ctrl_level is None else ctrl_level
         self.Nc = n0 * 2 ** self.ctrl_level
         self.hc3 = (1.0 / self.Nc) ** 3
         self.sigma, self.theta, self.alpha, self.seed = sigma, theta, alpha, seed
         self.n_modes = n_modes
-        self.kl = kl.KLTable(corr_len, n_modes)
+        self.field_model, self.target_freq = field_model, target_freq
+        if field_model == 1:  # the paper's Sec. 5 field with n_modes = m^3
+            m = round(n_modes ** (1.0 / 3.0))
+            assert m ** 3 == n_modes
+            self.kl = kl.PaperKLTable(corr_len, m)
+        else:
+            self.kl = kl.KLTable(corr_len, n_modes)
         self.rtol, self.method = rtol, method
         self._levels = {}
 
@@ -49,13 +55,15 @@ class Workload:
         if l not in self._levels:
             lev = fem.Level(self.n0 * 2 ** l)
             lev.M_full = lev.mass()
-            lev.g = lev.nodal_target()
+            lev.g = lev.nodal_target(self.target_freq)
             lev.I = lev.interpolation(self.Nc)
             lev.phi = self.kl.cell_modes(lev.N)
             self._levels[l] = lev
         return self._levels[l]
 
     def xi(self, iteration, level, samples):
+        if self.field_model == 1:  # xi ~ U(-4, 4) (Sec. 5)
+            return philox.uniforms(self.seed, iteration, level, samples, self.n_modes, 4.0)
         return philox.normals(self.seed, iteration, level, samples, self.n_modes)
 
     def log_a(self, xi, grid_level):

@@ -62,6 +62,31 @@ def uniform53(w_hi, w_lo):
     return (m.astype(np.float64) + 1.0) * 2.0 ** -53
 
 
+def _pair_uniforms(seed, iteration, level, samples, n_pairs):
+    samples = np.asarray(samples, dtype=np.uint64)
+    S = samples.shape[0]
+    ctr = np.zeros((S, n_pairs, 4), dtype=np.uint64)
+    ctr[..., 0] = np.arange(n_pairs, dtype=np.uint64)[None, :]
+    ctr[..., 1] = (samples & MASK32)[:, None]
+    ctr[..., 2] = np.uint64(level)
+    ctr[..., 3] = np.uint64(iteration)
+    seed = int(seed)
+    key = np.array([seed & 0xFFFFFFFF, (seed >> 32) & 0xFFFFFFFF], dtype=np.uint64)
+    w = philox4x32_10(ctr, key)
+    return uniform53(w[..., 0], w[..., 1]), uniform53(w[..., 2], w[..., 3])
+
+
+def uniforms(seed, iteration, level, samples, n_modes, half_width):
+    """xi[s, k] ~ U(-half_width, half_width] from the same counters as `normals`:
+    mode 2p from the first uniform of pair p, mode 2p+1 from the second."""
+    npairs = (n_modes + 1) // 2
+    u1, u2 = _pair_uniforms(seed, iteration, level, samples, npairs)
+    xi = np.empty((u1.shape[0], 2 * npairs))
+    xi[:, 0::2] = -half_width + 2.0 * half_width * u1
+    xi[:, 1::2] = -half_width + 2.0 * half_width * u2
+    return xi[:, :n_modes]
+
+
 def normals(seed, iteration, level, samples, n_modes):
     """xi[s, k] ~ N(0, 1) for the given sample indices (array of int).
 

@@ -46,6 +46,8 @@ struct mlsgd_ctx {
     return m;
   }
   int N(int l) const { return cfg.n0 << l; }
+  int freq() const { return cfg.target_freq > 0 ? cfg.target_freq : 1; }
+  double xi_half_width() const { return cfg.field_model == 1 ? 4.0 : 0.0; }
   int Nc() const { return cfg.n0 << cfg.ctrl_level; }
   bool mixed() const { return cfg.precision == MLSGD_MIXED; }
   bool tc_ok(int level) const {
@@ -172,7 +174,7 @@ mlsgd_status solve_grid(mlsgd_ctx* ctx, int N, int S, const GridFields& f, const
   int lev = 0;
   while ((ctx->cfg.n0 << lev) < N) ++lev;
   CK(cudaMemsetAsync(badj, 0, S * nodes * sizeof(double), st));  // boundary rows stay 0
-  launch_phi_adjrhs(ytmp, N, S, badj, phi, B.partial, ctx->d_gtab[lev], ctx->d_mgtab[lev], st);
+  launch_phi_adjrhs(ytmp, N, S, badj, phi, B.partial, ctx->d_gtab[lev], ctx->d_mgtab[lev], st, ctx->freq());
   e = ctx->mixed() ? ir_mixed(B, f.a32, f.abf, badj, (long long)nodes, q, r64, prm, inner, st, fixed)
                    : pcg_fp64(B, f.a64, badj, (long long)nodes, q, prm, st);
   CK(e);
@@ -250,14 +252,19 @@ mlsgd_status mlsgd_create(const mlsgd_config* cfg, mlsgd_ctx** out) {
   *out = nullptr;
   const mlsgd_config& c = *cfg;
   if (c.n_levels < 1 || c.n_levels > 16 || c.n0 < 2 || (c.n0 & (c.n0 - 1)) != 0 || c.ctrl_level < 0 ||
-      c.ctrl_level >= c.n_levels || c.n_modes < 2 || (c.n_modes % 2) != 0 || c.n_modes > 4096 ||
+      c.ctrl_level >= c.n_levels || c.n_modes < 2 || (c.field_model == 0 && (c.n_modes % 2) != 0) || c.n_modes > 4096 ||
       !(c.corr_len > 0) || !(c.rtol > 0) || c.max_iter < 1 || (c.precision != MLSGD_FP64 && c.precision != MLSGD_MIXED) ||
-      (c.n0 << (c.n_levels - 1)) > 1024)
+      (c.n0 << (c.n_levels - 1)) > 1024 || c.field_model < 0 || c.field_model > 1 || c.target_freq < 0)
     return MLSGD_EINVAL;
+  int mcube = 0;
+  if (c.field_model == 1) {
+    while ((mcube + 1) * (mcube + 1) * (mcube + 1) <= c.n_modes) ++mcube;
+    if (mcube * mcube * mcube != c.n_modes) return MLSGD_EINVAL;
+  }
   mlsgd_ctx* ctx = new mlsgd_ctx();
   ctx->cfg = c;
   if (ctx->cfg.max_batch <= 0) ctx->cfg.max_batch = 256;
-  ctx->kl = build_kl_table(c.corr_len, c.n_modes);
+  ctx->kl = c.field_model == 1 ? build_paper_table(c.corr_len, mcube) : build_kl_table(c.corr_len, c.n_modes);
   const int K = c.n_modes;
   std::vector<int> iy(K), iz(K), order(K);
   std::vector<double> scale(K);
@@ -292,7 +299,7 @@ mlsgd_status mlsgd_create(const mlsgd_config* cfg, mlsgd_ctx** out) {
     ctx->d_phi.push_back(d);
     const int N = ctx->N(l);
     std::vector<double> g(N + 1, 0.0), mg(N + 1, 0.0);
-    for (int i = 1; i < N; ++i) g[i] = std::sin(M_PI * (double)i / N);
+    for (int i = 1; i < N; ++i) g[i] = std::sin(M_PI * (double)(ctx->freq() * i) / N);
     for (int i = 1; i < N; ++i) mg[i] = (g[i - 1] + 4.0 * g[i] + g[i + 1]) / (6.0 * N);
     double *dg = nullptr, *dmg = nullptr;
     ok = ok && up((void**)&dg, g.data(), g.size() * sizeof(double)) && up((void**)&dmg, mg.data(), mg.size() * sizeof(double));
@@ -356,7 +363,7 @@ mlsgd_status mlsgd_sample_field(mlsgd_ctx* ctx, int iter, int level, int grid, i
     if (s != MLSGD_OK) return s;
     xi = (double*)ctx->ws;
   }
-  launch_draw_xi(ctx->cfg.seed, iter, level, first_sample, n_samples, K, xi, st);
+  launch_draw_xi(ctx->cfg.seed, iter, level, first_sample, n_samples, K, xi, st, ctx->xi_half_width());
   if (log_a_dev) {
     GridFields none;
     mlsgd_status s = make_field(ctx, xi, grid, n_samples, none, log_a_dev, st);
@@ -381,7 +388,7 @@ mlsgd_status mlsgd_sample_field_tc(mlsgd_ctx* ctx, int iter, int level, int grid
   Bump bp{ctx->ws};
   double* xi = bp.take<double>((size_t)S * K);
   __nv_bfloat16* A = bp.take<__nv_bfloat16>((size_t)S * K);
-  launch_draw_xi(ctx->cfg.seed, iter, level, first_sample, S, K, xi, st);
+  launch_draw_xi(ctx->cfg.seed, iter, level, first_sample, S, K, xi, st, ctx->xi_half_width());
   s = ensure_phiT(ctx, grid, st);
   if (s != MLSGD_OK) return s;
   CK(kl_gemm(xi, ctx->d_scale, S, K, ctx->d_phiT[grid], ctx->N(grid), A, (__nv_bfloat16*)a_bf16_dev, log_a_f32_dev,
@@ -548,7 +555,7 @@ mlsgd_status mlsgd_level_gradient(mlsgd_ctx* ctx, int iter, int level, int64_t f
     const long long ncell = cells_of(ctx->Nc());
     double* spartial = bp.take<double>((size_t)((ncell + 255) / 256) + 64);
     char* scratch = bp.p;
-    launch_draw_xi(ctx->cfg.seed, iter, level, first_sample + done, S, K, xi, st);
+    launch_draw_xi(ctx->cfg.seed, iter, level, first_sample + done, S, K, xi, st, ctx->xi_half_width());
     s = make_field(ctx, xi, level, S, ff, nullptr, st, gemm_a);
     if (s != MLSGD_OK) return s;
     s = solve_grid(ctx, N, S, ff, z_dev, nullptr, qf, phif, iters, status, scratch, st);

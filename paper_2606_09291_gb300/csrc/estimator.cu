@@ -48,7 +48,7 @@ void launch_rhs_state(const double* z, int Nc, int N, double* b, cudaStream_t st
 // interior rows (adjoint right-hand side <y - g, v>_H, Sec. 2.2) and
 // Phi = 1/2 e^T M e (eq:cost), reduced per sample in FP64.
 __global__ void k_phi_adjrhs(const double* __restrict__ y, int N, double* __restrict__ badj,
-                             double* __restrict__ partial) {
+                             double* __restrict__ partial, int freq) {
   const int s = blockIdx.y;
   const int n1 = N + 1;
   const long long nodes = (long long)n1 * n1 * n1;
@@ -60,7 +60,7 @@ __global__ void k_phi_adjrhs(const double* __restrict__ y, int N, double* __rest
     node_ijk(n, n1, i, j, k);
     double me = 0.0;
     if (interior(i, j, k, N)) {
-      const double invN = 1.0 / N;
+      const double invN = (double)freq / N;  // g = prod sin(freq pi x)
       double gx[3], gy[3], gz[3];
       for (int d = -1; d <= 1; ++d) {
         gx[d + 1] = sinpi((i + d) * invN);
@@ -105,7 +105,7 @@ __global__ void k_phi_finish(const double* __restrict__ partial, int nblk, int S
 }
 
 void launch_phi_adjrhs(const double* y, int N, int S, double* badj, double* phi, double* partial, const double* gtab,
-                       const double* mgtab, cudaStream_t st) {
+                       const double* mgtab, cudaStream_t st, int freq) {
   if (S == 0) return;
   if (N >= kTiledMinN && gtab != nullptr) {
     const int nb = tiled_phi(y, N, S, gtab, mgtab, badj, partial, st);
@@ -113,7 +113,8 @@ void launch_phi_adjrhs(const double* y, int N, int S, double* badj, double* phi,
     return;
   }
   const int nb = node_blocks(N);
-  launch("phi_adjrhs", (double)S * nodes_of(N) * 16, k_phi_adjrhs, dim3(nb, S), kBlock, 0, st, y, N, badj, partial);
+  launch("phi_adjrhs", (double)S * nodes_of(N) * 16, k_phi_adjrhs, dim3(nb, S), kBlock, 0, st, y, N, badj, partial,
+         freq);
   launch("phi_finish", 0.0, k_phi_finish, dim3((S + 7) / 8), 256, 0, st, (const double*)partial, nb, S, phi);
 }
 

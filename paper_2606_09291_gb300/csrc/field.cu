@@ -13,28 +13,38 @@ namespace mlsgd {
 
 // one thread per (sample, mode pair): counter = (pair, sample, level, iteration),
 // key = seed; Box-Muller on two 53-bit uniforms.
+// half_width > 0: xi uniform on (-half_width, half_width] from the same uniforms
 __global__ void k_draw_xi(uint32_t key0, uint32_t key1, uint32_t iter, uint32_t level, long long first,
-                          int S, int K, double* __restrict__ xi) {
-  const int pairs = K / 2;
+                          int S, int K, double half_width, double* __restrict__ xi) {
+  const int pairs = (K + 1) / 2;
   const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= (long long)S * pairs) return;
   const int s = (int)(idx / pairs), p = (int)(idx % pairs);
   const uint64_t sample = (uint64_t)(first + s);
   const U4 w = philox4x32_10(U4{(uint32_t)p, (uint32_t)sample, level, iter}, key0, key1);
   const double u1 = uniform53(w.x, w.y), u2 = uniform53(w.z, w.w);
-  const double r = sqrt(-2.0 * log(u1));
-  double sn, cs;
-  sincospi(2.0 * u2, &sn, &cs);
-  xi[(long long)s * K + 2 * p] = r * cs;
-  xi[(long long)s * K + 2 * p + 1] = r * sn;
+  double v0, v1;
+  if (half_width > 0.0) {
+    v0 = -half_width + 2.0 * half_width * u1;
+    v1 = -half_width + 2.0 * half_width * u2;
+  } else {
+    const double r = sqrt(-2.0 * log(u1));
+    double sn, cs;
+    sincospi(2.0 * u2, &sn, &cs);
+    v0 = r * cs;
+    v1 = r * sn;
+  }
+  xi[(long long)s * K + 2 * p] = v0;
+  if (2 * p + 1 < K) xi[(long long)s * K + 2 * p + 1] = v1;
 }
 
-void launch_draw_xi(uint64_t seed, int iter, int level, long long first, int S, int K, double* xi,
-                    cudaStream_t st) {
-  const long long n = (long long)S * (K / 2);
+void launch_draw_xi(uint64_t seed, int iter, int level, long long first, int S, int K, double* xi, cudaStream_t st,
+                    double half_width) {
+  const long long n = (long long)S * ((K + 1) / 2);
   if (n == 0) return;
   launch("xi", (double)S * K * 8, k_draw_xi, dim3((unsigned)((n + kBlock - 1) / kBlock)), kBlock, 0, st,
-         (uint32_t)(seed & 0xffffffffu), (uint32_t)(seed >> 32), (uint32_t)iter, (uint32_t)level, first, S, K, xi);
+         (uint32_t)(seed & 0xffffffffu), (uint32_t)(seed >> 32), (uint32_t)iter, (uint32_t)level, first, S, K,
+         half_width, xi);
 }
 
 // exp(la) for an FP32 result: FP64 range reduction la = k ln2 + r, |r| <= ln2/2,

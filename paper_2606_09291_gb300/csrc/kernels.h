@@ -26,7 +26,9 @@ struct FieldOut {
   __nv_bfloat16* abf;
 };
 
-void launch_draw_xi(uint64_t seed, int iter, int level, long long first, int S, int K, double* xi, cudaStream_t st);
+// half_width > 0: uniform xi on (-half_width, half_width] (the paper's field), else N(0, 1)
+void launch_draw_xi(uint64_t seed, int iter, int level, long long first, int S, int K, double* xi, cudaStream_t st,
+                    double half_width = 0.0);
 cudaError_t launch_field(const double* xi, int K, const ModeTable& mt, const double* phi, int N, int S,
                          const FieldOut& out, cudaStream_t st);
 size_t field_smem_bytes(const ModeTable& mt, int K, int N);
@@ -128,7 +130,7 @@ cudaError_t kl_gemm(const double* xi, const double* scale, int S, int K, const _
 void launch_rhs_state(const double* z, int Nc, int N, double* b, cudaStream_t st);
 // Phi = 1/2 e^T M e, badj = M e (interior rows), e = y - g_h
 void launch_phi_adjrhs(const double* y, int N, int S, double* badj, double* phi, double* partial,
-                       const double* gtab, const double* mgtab, cudaStream_t st);
+                       const double* gtab, const double* mgtab, cudaStream_t st, int freq = 1);
 // batch statistics of one level merged into stats (see mlsgd_level_stats)
 void launch_level_stats(const double* qf, const double* phif, int Nf, const double* qc, const double* phic,
                         int Ncoarse, int S, int Nc, double theta, double* field, double* scalars,

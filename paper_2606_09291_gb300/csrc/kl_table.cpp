@@ -87,10 +87,29 @@ KLTable build_kl_table(double corr_len, int K) {
   }
 }
 
+KLTable build_paper_table(double rho, int m) {
+  KLTable T;
+  T.model = 1;
+  T.n1d = m;
+  for (int j = 1; j <= m; ++j)
+    for (int k = 1; k <= m; ++k)
+      for (int l = 1; l <= m; ++l) {
+        // phi_jkl(x) = cos(j pi x2) cos(k pi x3) cos(l pi x1): x-index l, y-index j, z-index k
+        T.ix.push_back(l - 1);
+        T.iy.push_back(j - 1);
+        T.iz.push_back(k - 1);
+        T.lam3.push_back(std::exp(-M_PI * (double)(j + k + l) * rho));
+      }
+  return T;
+}
+
 std::vector<double> kl_cell_table(const KLTable& T, int N) {
   std::vector<double> phi((size_t)T.n1d * N);
   for (int m = 0; m < T.n1d; ++m)
-    for (int x = 0; x < N; ++x) phi[(size_t)m * N + x] = kl_eval_1d(m, T.omega[m], T.norm[m], (x + 0.5) / N);
+    for (int x = 0; x < N; ++x) {
+      const double xc = (x + 0.5) / N;
+      phi[(size_t)m * N + x] = T.model == 1 ? std::cos((m + 1) * M_PI * xc) : kl_eval_1d(m, T.omega[m], T.norm[m], xc);
+    }
   return phi;
 }
 

@@ -20,6 +20,10 @@ PRESETS = {
     # serving mix over levels 0..5, N_l proportional to 2^(-2l)
     "c4": dict(n_levels=6, n0=8, n_modes=128, corr_len=0.2, sigma=1.0, theta=10.0, alpha=1e-4, seed=0,
                mix=(1024, 256, 64, 16, 4, 1), precision="mixed"),
+    # the paper's Sec. 5 setting: cos-product KL, 125 modes, rho = 0.15, xi ~ U(-4, 4),
+    # target prod sin(2 pi x_i); theta swept over {1, 8, 16, ..., 72}
+    "paper": dict(n_levels=4, n0=8, n_modes=125, corr_len=0.15, sigma=1.0, theta=8.0, alpha=1e-4, seed=0,
+                  field_model=1, target_freq=2, counts=(128, 16, 2), thetas=(1, 8, 16, 24, 32, 40, 48, 56, 64, 72)),
     # large risk aversion, levels 0..5, 512 modes
     "c5": dict(n_levels=6, n0=8, n_modes=512, corr_len=0.1, sigma=1.5, theta=100.0, alpha=1e-4, seed=0,
                precision="mixed"),
@@ -31,10 +35,11 @@ def ctrl_centres(Nc):
     return (c % Nc + 0.5) / Nc, ((c // Nc) % Nc + 0.5) / Nc, (c // (Nc * Nc) + 0.5) / Nc
 
 
-def z_test(Nc):
-    """z = 3 pi^2 sin(pi x) sin(pi y) sin(pi z) at the control-cell centres (so y ~ u_d for a ~ 1)."""
+def z_test(Nc, freq=1):
+    """z = 3 (f pi)^2 prod sin(f pi x_i) at the control-cell centres (so y ~ g for a ~ 1)."""
     x, y, z = ctrl_centres(Nc)
-    return 3.0 * np.pi ** 2 * np.sin(np.pi * x) * np.sin(np.pi * y) * np.sin(np.pi * z)
+    w = freq * np.pi
+    return 3.0 * w ** 2 * np.sin(w * x) * np.sin(w * y) * np.sin(w * z)
 
 
 def z_random(Nc, seed=0, scale=1.0):

@@ -25,7 +25,7 @@ class Config(ctypes.Structure):
                 ("theta", ctypes.c_double), ("alpha", ctypes.c_double), ("rtol", ctypes.c_double),
                 ("max_iter", ctypes.c_int), ("precision", ctypes.c_int), ("inner_iters", ctypes.c_int),
                 ("max_batch", ctypes.c_int), ("field_tc", ctypes.c_int), ("ir_steps", ctypes.c_int),
-                ("seed", ctypes.c_uint64)]
+                ("field_model", ctypes.c_int), ("target_freq", ctypes.c_int), ("seed", ctypes.c_uint64)]
 
 
 class LevelStats(ctypes.Structure):
@@ -141,7 +141,8 @@ class Context:
         c = Config()
         defaults = dict(n_levels=3, n0=8, ctrl_level=None, n_modes=64, corr_len=0.3, sigma=1.0, theta=1.0,
                         alpha=1e-4, rtol=1e-8, max_iter=200, precision=MLSGD_FP64, inner_iters=0,
-                        max_batch=256, field_tc=0, ir_steps=0, seed=0)
+                        max_batch=256, field_tc=0, ir_steps=0, field_model=0,
+                        target_freq=1, seed=0)
         defaults.update(cfg)
         if defaults["ctrl_level"] is None:
             defaults["ctrl_level"] = defaults["n_levels"] - 1
