@@ -132,6 +132,20 @@ typedef struct {
   double c_hat;            /* ||E^ML[X]||^2 / E^ML[Y]^2                                   */
   double mean_dx_norm2[16];/* ||mean dX~_l||_U^2 (shift of level l)                       */
   double v2[16];           /* v^2_l in unshifted units (eq:sec-order-sum)                 */
+  /* step size */
+  double tau;              /* the step taken                                              */
+  double l_hat;            /* L^ of eq:adaptive-step-size (NaN for a fixed or first step)  */
+  int tau_fallback;        /* 1: the adaptive rule gave a non-positive or non-finite step
+                              and tau_prev was taken instead                              */
+  /* rate diagnostics of this batch, unshifted, per level l (the difference samples) */
+  double m2_dx[16];        /* (1/M_l) sum_m ||dX_l^(m)||_U^2, left side of eq:decayNum     */
+  double m2_dy[16];        /* (1/M_l) sum_m |dY_l^(m)|^2, left side of eq:decayDenom       */
+  double mean_dx_norm[16]; /* ||mean dX_l||_U (eq:weakerror2 through the level difference) */
+  double mean_dy_abs[16];  /* |mean dY_l| (eq:weakerror)                                    */
+  /* exponents from least-squares fits of log2 of the above against l over l >= 1:
+     m2 ~ h_l^beta, means ~ h_l^alpha with h_l = h_0 2^-l (NaN with fewer than two
+     difference levels) */
+  double beta_x, beta_y, alpha_x, alpha_y;
 } mlsgd_step_report;
 
 /* Create a context on the current CUDA device.  Builds the KL mode table on
@@ -234,6 +248,24 @@ mlsgd_status mlsgd_stats_merge(mlsgd_ctx* ctx, mlsgd_level_stats* dst, const mls
  * SYNCHRONOUS: returns after the report has been read back. */
 mlsgd_status mlsgd_step(mlsgd_ctx* ctx, const mlsgd_level_stats* stats, int n_levels, double tau, double eta,
                         int max_levels, double* z_dev, double* grad_dev, mlsgd_step_report* rep, void* stream);
+
+/* mlsgd_step with the adaptive step size of Sec. 5 (eq:adaptive-step-size):
+ *   tau_k = (||g_k||^2 - err_sam_k) / (L^ ||g_k||^2),
+ *   L^    = ||g_k - g_{k-1}||_U / ||tau_{k-1} g_{k-1}||_U,
+ * g_k = grad J^ML(u_k) and err_sam_k as in *rep (the printed "t_{k-1}" is read as
+ * tau_{k-1}).  Reading where the rule gives no positive finite step (sampling
+ * error above ||g_k||^2, or g_k = g_{k-1}): keep tau_{k-1} and set
+ * rep->tau_fallback.
+ *   tau0           step of the first iteration (> 0), used when tau_prev <= 0
+ *   tau_prev       tau_{k-1} (<= 0 on the first iteration: grad_prev_dev is not read)
+ *   grad_prev_dev  [n_ctrl_cells] FP64 device, IN g_{k-1}, OUT g_k (caller-owned,
+ *                  kept between calls)
+ * The step taken is rep->tau; z_dev <- z_dev - rep->tau g_k.  Same plan, report
+ * and errors as mlsgd_step, plus MLSGD_EINVAL for a null grad_prev_dev, tau0 <= 0
+ * or a non-finite tau_prev.  SYNCHRONOUS. */
+mlsgd_status mlsgd_step_adaptive(mlsgd_ctx* ctx, const mlsgd_level_stats* stats, int n_levels, double tau0,
+                                 double tau_prev, double eta, int max_levels, double* z_dev, double* grad_prev_dev,
+                                 mlsgd_step_report* rep, void* stream);
 
 /* ---------------------------------------------------------------- instrumentation
  * Process-wide.  Every kernel launch of the library is counted; when profiling

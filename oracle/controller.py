@@ -86,3 +86,44 @@ def plan(level_info, EX_norm2, EY, grad_norm, eta, n0, L_max):
               for l in range(L_next)]
     return dict(L=L_next, M=M_next, err_sam=err_sam, err_num=err_num, alpha_hat=alpha,
                 eps2=eps2, C_hat=C_hat, v2=v2)
+
+
+def adaptive_tau(grad, grad_prev, tau_prev, err_sam, hc3, tau0):
+    """Adaptive step size of Sec. 5 (eq:adaptive-step-size).
+
+    tau_k = (||g_k||^2 - err_sam_k) / (L_hat ||g_k||^2) with
+    L_hat = ||g_k - g_{k-1}||_U / ||tau_{k-1} g_{k-1}||_U; the printed t_{k-1} is
+    read as tau_{k-1}.  First iteration (grad_prev None): tau0.  Reading where
+    the rule gives no positive finite step: keep tau_{k-1}.
+    Returns (tau, L_hat, fell_back)."""
+    if grad_prev is None:
+        return tau0, float("nan"), False
+    norm = lambda v: math.sqrt(hc3 * float(v @ v))
+    g2 = hc3 * float(grad @ grad)
+    l_hat = norm(grad - grad_prev) / (tau_prev * norm(grad_prev)) if norm(grad_prev) > 0 else float("inf")
+    with np.errstate(all="ignore"):
+        tau = (g2 - err_sam) / (l_hat * g2) if l_hat > 0 and g2 > 0 else float("nan")
+    if not (math.isfinite(tau) and tau > 0):
+        return tau_prev, l_hat, True
+    return tau, l_hat, False
+
+
+def rates(level_stats, level_shifts, theta, hc3):
+    """Rate diagnostics of one batch (unshifted): per level the second moments
+    (1/M) sum ||dX_l||_U^2 and (1/M) sum |dY_l|^2 (the left sides of eq:decayNum and
+    eq:decayDenom), ||mean dX_l||_U and |mean dY_l| (eq:weakerror2, eq:weakerror),
+    and the exponents beta_x, beta_y, alpha_x, alpha_y fitted over l >= 1 with
+    h_l = h_0 2^-l (NaN with fewer than two difference levels)."""
+    out = dict(m2_dx=[], m2_dy=[], mean_dx_norm=[], mean_dy_abs=[])
+    for S, c in zip(level_stats, level_shifts):
+        f = math.exp(theta * c)
+        mx2 = hc3 * float(S.mean_x @ S.mean_x)
+        out["m2_dx"].append(f * f * (S.s2_x / S.n + mx2))
+        out["m2_dy"].append(f * f * (S.s2_y / S.n + S.mean_y ** 2))
+        out["mean_dx_norm"].append(f * math.sqrt(mx2))
+        out["mean_dy_abs"].append(f * abs(S.mean_y))
+    L = len(level_stats)
+    for key, name in (("m2_dx", "beta_x"), ("m2_dy", "beta_y"), ("mean_dx_norm", "alpha_x"),
+                      ("mean_dy_abs", "alpha_y")):
+        out[name] = -_fit_slope(range(1, L), out[key][1:]) if L >= 3 else float("nan")
+    return out

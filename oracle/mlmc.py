@@ -190,3 +190,37 @@ def combine(W, level_stats, level_shifts, z, tau, project=None):
     risk = cstar + np.log(EY) / th if EY > 0 else float("nan")
     return dict(grad=grad, z_new=z_new, grad_norm=gnorm, EX=EX, EY=EY, shift=cstar,
                 risk=risk, truncated=EY < np.exp(-th * cstar))
+
+
+def mlsgd(W, z, counts, iterations, tau0, adaptive=False, eta=0.9, L_max=None, adapt_counts=False):
+    """MLSGD outer loop (Algorithm 1, function MLSGD): per iteration k, fresh draws
+    on every level with the current batch sizes, the multilevel gradient, the step
+    (fixed tau0, or eq:adaptive-step-size with tau_0 = tau0), and optionally the
+    next level count and batch sizes from the controller.
+    Returns (z, history) with one dict per iteration (tau, L_hat, grad_norm, risk,
+    err_sam, counts, rates)."""
+    from . import controller
+    L_max = W.n_levels if L_max is None else L_max
+    counts = list(counts)
+    z = np.array(z, dtype=np.float64)
+    g_prev, tau_prev, hist = None, 0.0, []
+    for k in range(iterations):
+        recs = [level_batch(W, k, l, range(m), z) for l, m in enumerate(counts)]
+        stats, shifts = [r["stats"] for r in recs], [r["shift"] for r in recs]
+        res = combine(W, stats, shifts, z, 0.0)
+        info = [dict(n=s.n, shift=c, theta=W.theta, s2_x=s.s2_x, s2_y=s.s2_y,
+                     mean_x_norm2=W.hc3 * float(s.mean_x @ s.mean_x), mean_y=s.mean_y)
+                for s, c in zip(stats, shifts)]
+        p = controller.plan(info, W.hc3 * float(res["EX"] @ res["EX"]), res["EY"], res["grad_norm"], eta, W.n0, L_max)
+        if adaptive:
+            tau, l_hat, fb = controller.adaptive_tau(res["grad"], g_prev, tau_prev, p["err_sam"], W.hc3, tau0)
+        else:
+            tau, l_hat, fb = tau0, float("nan"), False
+        z = z - tau * res["grad"]
+        hist.append(dict(tau=tau, l_hat=l_hat, fallback=fb, grad_norm=res["grad_norm"], risk=res["risk"],
+                         err_sam=p["err_sam"], counts=list(counts), plan=p,
+                         rates=controller.rates(stats, shifts, W.theta, W.hc3)))
+        g_prev, tau_prev = res["grad"], tau
+        if adapt_counts:
+            counts = p["M"]
+    return z, hist

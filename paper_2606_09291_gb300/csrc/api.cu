@@ -573,12 +573,28 @@ mlsgd_status mlsgd_level_gradient(mlsgd_ctx* ctx, int iter, int level, int64_t f
   return MLSGD_OK;
 }
 
-mlsgd_status mlsgd_step(mlsgd_ctx* ctx, const mlsgd_level_stats* stats, int n_levels, double tau, double eta,
-                        int max_levels, double* z_dev, double* grad_dev, mlsgd_step_report* rep, void* stream) {
-  if (!ctx) return MLSGD_EINVAL;
-  cudaStream_t st = (cudaStream_t)stream;
+namespace {
+// slope of a least-squares line through (l, y_l), l = 1..L-1; NaN with fewer than two points
+double diff_level_slope(const std::vector<double>& y) {
+  if (y.size() < 3) return NAN;
+  std::vector<double> x, v;
+  for (size_t l = 1; l < y.size(); ++l) { x.push_back((double)l); v.push_back(y[l]); }
+  return ls_slope(x, v);
+}
+}  // namespace
+
+// Shared body of mlsgd_step and mlsgd_step_adaptive.  Fixed: one pass computes the
+// gradient and takes the step with `tau`.  Adaptive: the first pass computes the
+// gradient into scratch together with ||grad - grad_prev|| (read only when
+// tau_prev > 0), the host evaluates eq:adaptive-step-size, and a second pass takes
+// the step and stores the gradient into grad_prev.
+static mlsgd_status step_core(mlsgd_ctx* ctx, const mlsgd_level_stats* stats, int n_levels, double eta,
+                              int max_levels, double* z_dev, double* grad_dev, bool adaptive, double tau,
+                              double tau_prev, double* grad_prev_dev, mlsgd_step_report* rep, cudaStream_t st) {
   if (!stats || n_levels < 1 || n_levels > 16 || !z_dev || !rep || n_levels > ctx->cfg.n_levels)
     return fail(ctx, MLSGD_EINVAL, "mlsgd_step: bad arguments");
+  if (adaptive && (!grad_prev_dev || !(tau > 0) || !std::isfinite(tau_prev)))
+    return fail(ctx, MLSGD_EINVAL, "mlsgd_step_adaptive: needs grad_prev_dev, tau0 > 0 and a finite tau_prev");
   for (int l = 0; l < n_levels; ++l)
     if (stats[l].level != l || !stats[l].field_dev || !stats[l].scalars_dev)
       return fail(ctx, MLSGD_EINVAL, "mlsgd_step: stats[l] must hold level l");
@@ -608,21 +624,25 @@ mlsgd_status mlsgd_step(mlsgd_ctx* ctx, const mlsgd_level_stats* stats, int n_le
   if (!std::isfinite(denom) || !std::isfinite(cstar)) return fail(ctx, MLSGD_ENONFINITE, "mlsgd_step: non-finite shift");
   const long long nc = cells_of(ctx->Nc());
   const int nblk = (int)((nc + 255) / 256);
-  const int rows = n_levels + 2;
-  mlsgd_status s = ensure_ws(ctx, al((size_t)(rows + 1) * nblk * 8 + 64 * 8) + al(16 * 8), st);
+  const int rows = n_levels + 4;
+  const size_t part_bytes = al((size_t)(rows + 1) * nblk * 8 + 64 * 8);
+  mlsgd_status s = ensure_ws(ctx, part_bytes + al(16 * 8) + (adaptive ? al((size_t)nc * 8) : 0), st);
   if (s != MLSGD_OK) return s;
   double* partial = (double*)ctx->ws;
-  double* dfac = (double*)(ctx->ws + al((size_t)(rows + 1) * nblk * 8 + 64 * 8));
+  double* dfac = (double*)(ctx->ws + part_bytes);
+  double* gnew = adaptive ? (double*)(ctx->ws + part_bytes + al(16 * 8)) : nullptr;
+  const double* gprev = (adaptive && tau_prev > 0) ? grad_prev_dev : nullptr;
   CK(cudaMemcpyAsync(dfac, fac.data(), n_levels * sizeof(double), cudaMemcpyHostToDevice, st));
   std::vector<const double*> fields(n_levels);
   for (int l = 0; l < n_levels; ++l) fields[l] = stats[l].field_dev;
-  launch_combine_step(fields.data(), dfac, n_levels, nc, denom, ctx->cfg.alpha, tau, z_dev, grad_dev, partial, nblk,
-                      st);
+  launch_combine_step(fields.data(), dfac, n_levels, nc, denom, ctx->cfg.alpha, tau, !adaptive, z_dev,
+                      adaptive ? gnew : grad_dev, gprev, partial, nblk, st);
   CK(cudaGetLastError());
   CK(cudaMemcpyAsync(hb, partial + (size_t)rows * nblk, rows * sizeof(double), cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
   const double hc = 1.0 / ctx->Nc(), hc3 = hc * hc * hc;
-  const double g2 = hb[0] * hc3, ex2 = hb[1] * hc3;
+  const double g2 = hb[0] * hc3, ex2 = hb[1] * hc3, diff2 = hb[2] * hc3, gp2 = hb[3] * hc3;
+  const double* ml = hb + 4;
   std::memset(rep, 0, sizeof(*rep));
   rep->grad_norm = std::sqrt(g2);
   rep->ey = ey;
@@ -639,7 +659,7 @@ mlsgd_status mlsgd_step(mlsgd_ctx* ctx, const mlsgd_level_stats* stats, int n_le
     const double* q = &sc[l * MLSGD_NSCALARS];
     const double f = std::exp(2.0 * theta * q[MLSGD_S_SHIFT]);
     v2[l] = f * (q[MLSGD_S_S2_DX] + C_hat * q[MLSGD_S_S2_DY]);
-    bias2[l] = f * (hb[2 + l] * hc3 + C_hat * q[MLSGD_S_MEAN_DY] * q[MLSGD_S_MEAN_DY]);
+    bias2[l] = f * (ml[l] * hc3 + C_hat * q[MLSGD_S_MEAN_DY] * q[MLSGD_S_MEAN_DY]);
     M[l] = q[MLSGD_S_COUNT];
   }
   double err_sam = 0.0;
@@ -673,7 +693,7 @@ mlsgd_status mlsgd_step(mlsgd_ctx* ctx, const mlsgd_level_stats* stats, int n_le
   rep->ex_norm2 = ex2;
   rep->c_hat = C_hat;
   for (int l = 0; l < L; ++l) {
-    rep->mean_dx_norm2[l] = hb[2 + l] * hc3;
+    rep->mean_dx_norm2[l] = ml[l] * hc3;
     rep->v2[l] = v2[l];
   }
   rep->err_sam = err_sam;
@@ -685,7 +705,62 @@ mlsgd_status mlsgd_step(mlsgd_ctx* ctx, const mlsgd_level_stats* stats, int n_le
     const double m = std::ceil(2.0 / eps2 * std::sqrt(V[l] / C[l]) * total);
     rep->next_counts[l] = (int64_t)std::max(2.0, std::min(m, 9.0e15));
   }
+  // ---- rate diagnostics (eq:decayNum, eq:decayDenom, eq:weakerror2, eq:weakerror), log2 in the
+  // shifted domain plus the shift so that large theta c does not overflow
+  std::vector<double> lx(L), ly(L), lmx(L), lmy(L);
+  const double log2e = 1.0 / std::log(2.0);
+  for (int l = 0; l < L; ++l) {
+    const double* q = &sc[l * MLSGD_NSCALARS];
+    const double tc = theta * q[MLSGD_S_SHIFT] * log2e;  // log2 exp(theta c_l)
+    const double sx = q[MLSGD_S_S2_DX] / M[l] + ml[l] * hc3;
+    const double sy = q[MLSGD_S_S2_DY] / M[l] + q[MLSGD_S_MEAN_DY] * q[MLSGD_S_MEAN_DY];
+    lx[l] = std::log2(sx) + 2.0 * tc;
+    ly[l] = std::log2(sy) + 2.0 * tc;
+    lmx[l] = 0.5 * std::log2(ml[l] * hc3) + tc;
+    lmy[l] = std::log2(std::fabs(q[MLSGD_S_MEAN_DY])) + tc;
+    rep->m2_dx[l] = std::exp2(lx[l]);
+    rep->m2_dy[l] = std::exp2(ly[l]);
+    rep->mean_dx_norm[l] = std::exp2(lmx[l]);
+    rep->mean_dy_abs[l] = std::exp2(lmy[l]);
+  }
+  rep->beta_x = -diff_level_slope(lx);
+  rep->beta_y = -diff_level_slope(ly);
+  rep->alpha_x = -diff_level_slope(lmx);
+  rep->alpha_y = -diff_level_slope(lmy);
+  // ---- step size
+  rep->l_hat = NAN;
+  rep->tau = tau;
+  if (adaptive) {
+    if (gprev) {
+      rep->l_hat = std::sqrt(diff2) / (tau_prev * std::sqrt(gp2));
+      const double t = (g2 - err_sam) / (rep->l_hat * g2);
+      if (std::isfinite(t) && t > 0) {
+        rep->tau = t;
+      } else {
+        rep->tau = tau_prev;
+        rep->tau_fallback = 1;
+      }
+    }
+    launch_step_apply(nc, rep->tau, gnew, z_dev, grad_prev_dev, st);
+    CK(cudaGetLastError());
+    CK(cudaStreamSynchronize(st));
+  }
   return MLSGD_OK;
+}
+
+mlsgd_status mlsgd_step(mlsgd_ctx* ctx, const mlsgd_level_stats* stats, int n_levels, double tau, double eta,
+                        int max_levels, double* z_dev, double* grad_dev, mlsgd_step_report* rep, void* stream) {
+  if (!ctx) return MLSGD_EINVAL;
+  return step_core(ctx, stats, n_levels, eta, max_levels, z_dev, grad_dev, false, tau, 0.0, nullptr, rep,
+                   (cudaStream_t)stream);
+}
+
+mlsgd_status mlsgd_step_adaptive(mlsgd_ctx* ctx, const mlsgd_level_stats* stats, int n_levels, double tau0,
+                                 double tau_prev, double eta, int max_levels, double* z_dev, double* grad_prev_dev,
+                                 mlsgd_step_report* rep, void* stream) {
+  if (!ctx) return MLSGD_EINVAL;
+  return step_core(ctx, stats, n_levels, eta, max_levels, z_dev, nullptr, true, tau0, tau_prev, grad_prev_dev, rep,
+                   (cudaStream_t)stream);
 }
 
 }  // extern "C"

@@ -334,15 +334,17 @@ void launch_stats_merge(double* dfield, double* dsc, const double* sfield, const
 
 // ---------------------------------------------------------------- combine and step
 // EX = sum_l f_l mean_l (f_l = exp(theta (c_l - c*))), grad = EX / denom + alpha z,
-// z <- z - tau grad.  partial rows: 0 = ||grad||^2, 1 = ||EX||^2, 2+l = ||mean_l||^2
+// z <- z - tau grad when `update`.  partial rows: 0 = ||grad||^2, 1 = ||EX||^2,
+// 2 = ||grad - gprev||^2, 3 = ||gprev||^2 (0 without gprev), 4+l = ||mean_l||^2
 // (unscaled, counted without h_c^3).
 struct FieldList { const double* f[16]; };
 
 __global__ void k_combine_step(FieldList fl, const double* __restrict__ factors, int L, long long n, double denom,
-                               double alpha, double tau, double* __restrict__ z, double* __restrict__ grad,
+                               double alpha, double tau, int update, double* __restrict__ z,
+                               double* __restrict__ grad, const double* __restrict__ gprev,
                                double* __restrict__ partial, int nblk) {
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  double ex = 0.0, g = 0.0;
+  double ex = 0.0, g = 0.0, d = 0.0, gp = 0.0;
   double ml[16];
   for (int l = 0; l < L; ++l) ml[l] = 0.0;
   if (i < n) {
@@ -353,19 +355,34 @@ __global__ void k_combine_step(FieldList fl, const double* __restrict__ factors,
     }
     const double zi = z[i];
     g = ex / denom + alpha * zi;
+    if (gprev) {
+      gp = gprev[i];
+      d = g - gp;
+    }
     if (grad) grad[i] = g;
-    z[i] = zi - tau * g;
+    if (update) z[i] = zi - tau * g;
   }
-  double v = block_sum(g * g);
-  if (threadIdx.x == 0) partial[blockIdx.x] = v;
-  __syncthreads();
-  v = block_sum(ex * ex);
-  if (threadIdx.x == 0) partial[(long long)nblk + blockIdx.x] = v;
+  const double rowv[4] = {g * g, ex * ex, d * d, gp * gp};
+  for (int r = 0; r < 4; ++r) {
+    if (r) __syncthreads();
+    const double v = block_sum(rowv[r]);
+    if (threadIdx.x == 0) partial[(long long)r * nblk + blockIdx.x] = v;
+  }
   for (int l = 0; l < L; ++l) {
     __syncthreads();
-    v = block_sum(ml[l]);
-    if (threadIdx.x == 0) partial[(long long)(2 + l) * nblk + blockIdx.x] = v;
+    const double v = block_sum(ml[l]);
+    if (threadIdx.x == 0) partial[(long long)(4 + l) * nblk + blockIdx.x] = v;
   }
+}
+
+// z <- z - tau g, and gout <- g (the gradient kept for the next step size)
+__global__ void k_step_apply(long long n, double tau, const double* __restrict__ g, double* __restrict__ z,
+                             double* __restrict__ gout) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const double gi = g[i];
+  z[i] -= tau * gi;
+  gout[i] = gi;
 }
 
 __global__ void k_rows_finish(const double* __restrict__ partial, int nblk, int rows, double* __restrict__ out) {
@@ -379,15 +396,21 @@ __global__ void k_rows_finish(const double* __restrict__ partial, int nblk, int 
 }
 
 void launch_combine_step(const double* const* fields, const double* factors, int L, long long ncells, double denom,
-                         double alpha, double tau, double* z, double* grad, double* partial, int nblk,
-                         cudaStream_t st) {
+                         double alpha, double tau, bool update, double* z, double* grad, const double* gprev,
+                         double* partial, int nblk, cudaStream_t st) {
   FieldList fl;
   for (int l = 0; l < L && l < 16; ++l) fl.f[l] = fields[l];
-  launch("combine", (double)ncells * 8 * (L + 2 + (grad ? 1 : 0)), k_combine_step, dim3(nblk), kBlock, 0, st, fl,
-         factors, L, ncells, denom, alpha, tau, z, grad, partial, nblk);
-  const int rows = L + 2;
+  const double bytes = (double)ncells * 8 * (L + 1 + (update ? 1 : 0) + (grad ? 1 : 0) + (gprev ? 1 : 0));
+  launch("combine", bytes, k_combine_step, dim3(nblk), kBlock, 0, st, fl, factors, L, ncells, denom, alpha, tau,
+         update ? 1 : 0, z, grad, gprev, partial, nblk);
+  const int rows = L + 4;
   launch("combine_finish", 0.0, k_rows_finish, dim3((rows + 7) / 8), 256, 0, st, (const double*)partial, nblk, rows,
          partial + (long long)rows * nblk);
+}
+
+void launch_step_apply(long long ncells, double tau, const double* g, double* z, double* gout, cudaStream_t st) {
+  const int nblk = (int)((ncells + kBlock - 1) / kBlock);
+  launch("step_apply", (double)ncells * 32, k_step_apply, dim3(nblk), kBlock, 0, st, ncells, tau, g, z, gout);
 }
 
 }  // namespace mlsgd

@@ -4,9 +4,13 @@ Orchestration only: each iteration calls mlsgd_level_gradient for every
 level with the current batch sizes (fresh draws per iteration, sample
 identity (seed, iteration, level, index)) and mlsgd_step, which combines the
 levels, takes the projected gradient step and plans the next level count
-and batch sizes (eq:optimal-level, eq:optimal-batch-size).  All arithmetic
-runs in libmlsgd.
+and batch sizes (eq:optimal-level, eq:optimal-batch-size), with a fixed or
+the adaptive step size (eq:adaptive-step-size).  All arithmetic of the method
+runs in libmlsgd; the host only fits the exponent of the measured cost per
+sample when asked to time the levels.
 """
+import math
+
 import torch
 
 from . import mlsgd
@@ -19,21 +23,58 @@ def fixed_step(alpha):
     return 0.5 / (alpha + (3.0 * math.pi ** 2) ** -2)
 
 
-def run_mlsgd(ctx, z, counts, iterations, tau, eta=0.9, max_levels=None, adapt=True, stream=None, log=None):
+def _slope(ls, vals):
+    """Least-squares slope of log2(vals) against ls (NaN with fewer than two points)."""
+    if len(ls) < 2:
+        return float("nan")
+    x = [float(l) for l in ls]
+    y = [math.log2(v) if v > 0 else float("nan") for v in vals]
+    xm, ym = sum(x) / len(x), sum(y) / len(y)
+    return sum((a - xm) * (b - ym) for a, b in zip(x, y)) / sum((a - xm) ** 2 for a in x)
+
+
+def run_mlsgd(ctx, z, counts, iterations, tau, eta=0.9, max_levels=None, adapt=True, stream=None, log=None,
+              step="fixed", time_levels=False):
     """Run `iterations` MLSGD steps from control z (device FP64 tensor, updated in
     place).  counts: initial per-level batch sizes (levels 0..len-1).
+    step: "fixed" (tau every iteration) or "adaptive" (eq:adaptive-step-size with
+    tau_0 = tau; mlsgd_step_adaptive keeps the previous gradient in a device buffer).
+    time_levels: time each level's batch with CUDA events and report the cost per
+    sample and its exponent gamma_hat (eq:assumption_gamma, cost ~ h_l^-gamma,
+    fitted over l >= 1; this synchronises after every level).
     Returns the list of per-iteration reports (host dicts)."""
+    assert step in ("fixed", "adaptive")
     max_levels = ctx.cfg["n_levels"] if max_levels is None else max_levels
     counts = list(counts)
     history = []
     stats = [ctx.new_stats(l) for l in range(ctx.cfg["n_levels"])]
+    g_prev = torch.zeros_like(z) if step == "adaptive" else None
+    tau_prev = 0.0
+    strm = stream if stream is not None else torch.cuda.current_stream()
     for k in range(iterations):
+        level_ms = []
         for l, m in enumerate(counts):
             ctx.mlsgd_stats_reset(stats[l], stream=stream)
+            if time_levels:
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(strm)
             ctx.mlsgd_level_gradient(k, l, 0, m, z, stats[l], stream=stream)
-        rep = ctx.mlsgd_step(stats[:len(counts)], tau, z, eta=eta, max_levels=max_levels, stream=stream)
+            if time_levels:
+                e1.record(strm)
+                e1.synchronize()
+                level_ms.append(e0.elapsed_time(e1))
+        if step == "adaptive":
+            rep = ctx.mlsgd_step_adaptive(stats[:len(counts)], tau, tau_prev, z, g_prev, eta=eta,
+                                          max_levels=max_levels, stream=stream)
+            tau_prev = rep["tau"]
+        else:
+            rep = ctx.mlsgd_step(stats[:len(counts)], tau, z, eta=eta, max_levels=max_levels, stream=stream)
         rep["iteration"] = k
         rep["counts"] = list(counts)
+        if time_levels:
+            rep["level_ms"] = level_ms
+            rep["cost_per_sample_ms"] = [t / m for t, m in zip(level_ms, counts)]
+            rep["gamma_hat"] = _slope(range(1, len(counts)), rep["cost_per_sample_ms"][1:])
         history.append(rep)
         if log is not None:
             log(rep)

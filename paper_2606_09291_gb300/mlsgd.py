@@ -38,7 +38,14 @@ class StepReport(ctypes.Structure):
                 ("err_num", ctypes.c_double), ("alpha_hat", ctypes.c_double), ("eps2", ctypes.c_double),
                 ("next_levels", ctypes.c_int), ("next_counts", ctypes.c_int64 * 16),
                 ("ex_norm2", ctypes.c_double), ("c_hat", ctypes.c_double),
-                ("mean_dx_norm2", ctypes.c_double * 16), ("v2", ctypes.c_double * 16)]
+                ("mean_dx_norm2", ctypes.c_double * 16), ("v2", ctypes.c_double * 16),
+                ("tau", ctypes.c_double), ("l_hat", ctypes.c_double), ("tau_fallback", ctypes.c_int),
+                ("m2_dx", ctypes.c_double * 16), ("m2_dy", ctypes.c_double * 16),
+                ("mean_dx_norm", ctypes.c_double * 16), ("mean_dy_abs", ctypes.c_double * 16),
+                ("beta_x", ctypes.c_double), ("beta_y", ctypes.c_double), ("alpha_x", ctypes.c_double),
+                ("alpha_y", ctypes.c_double)]
+
+_PER_LEVEL = ("mean_dx_norm2", "v2", "m2_dx", "m2_dy", "mean_dx_norm", "mean_dy_abs")
 
 
 class ProfileEntry(ctypes.Structure):
@@ -50,7 +57,7 @@ EXPORTS = ["mlsgd_create", "mlsgd_destroy", "mlsgd_last_error", "mlsgd_status_st
            "mlsgd_workspace_bytes", "mlsgd_mode_table", "mlsgd_sample_field", "mlsgd_solve_state_adjoint",
            "mlsgd_level_gradient", "mlsgd_stats_reset", "mlsgd_stats_merge", "mlsgd_step",
            "mlsgd_launch_count", "mlsgd_profile_start", "mlsgd_profile_stop", "mlsgd_solve_state_adjoint_noalloc",
-           "mlsgd_sample_field_tc"]
+           "mlsgd_sample_field_tc", "mlsgd_step_adaptive"]
 
 _lib = None
 
@@ -82,6 +89,8 @@ def load(path=LIB_PATH):
     L.mlsgd_stats_reset.argtypes = [vp, ctypes.POINTER(LevelStats), vp]
     L.mlsgd_stats_merge.argtypes = [vp, ctypes.POINTER(LevelStats), ctypes.POINTER(LevelStats), vp]
     L.mlsgd_step.argtypes = [vp, ctypes.POINTER(LevelStats), i32, dbl, dbl, i32, vp, vp, ctypes.POINTER(StepReport), vp]
+    L.mlsgd_step_adaptive.argtypes = [vp, ctypes.POINTER(LevelStats), i32, dbl, dbl, dbl, i32, vp, vp,
+                                      ctypes.POINTER(StepReport), vp]
     L.mlsgd_sample_field_tc.argtypes = [vp, i32, i32, i32, i64, i32, vp, vp, vp]
     L.mlsgd_solve_state_adjoint_noalloc.argtypes = [vp, i32, i32, vp, vp, vp, vp, vp, vp, vp, vp]
     L.mlsgd_launch_count.argtypes = []
@@ -220,18 +229,30 @@ class Context:
         ml = self.cfg["n_levels"] if max_levels is None else max_levels
         self._check(self.L.mlsgd_step(self.h, arr, n, tau, eta, ml, _ptr(z), _ptr(grad), ctypes.byref(rep),
                                       _stream(stream)))
-        out = {k: getattr(rep, k) for k, _ in StepReport._fields_
-               if k not in ("next_counts", "mean_dx_norm2", "v2")}
-        out["next_counts"] = [int(rep.next_counts[l]) for l in range(rep.next_levels)]
-        out["mean_dx_norm2"] = [rep.mean_dx_norm2[l] for l in range(n)]
-        out["v2"] = [rep.v2[l] for l in range(n)]
-        return out
+        return _report(rep, n)
+
+    def mlsgd_step_adaptive(self, stats_list, tau0, tau_prev, z, grad_prev, eta=0.9, max_levels=None, stream=None):
+        n = len(stats_list)
+        arr = (LevelStats * n)(*[s.c for s in stats_list])
+        rep = StepReport()
+        ml = self.cfg["n_levels"] if max_levels is None else max_levels
+        self._check(self.L.mlsgd_step_adaptive(self.h, arr, n, tau0, tau_prev, eta, ml, _ptr(z), _ptr(grad_prev),
+                                               ctypes.byref(rep), _stream(stream)))
+        return _report(rep, n)
 
     # --- helpers (allocation only) --------------------------------------
     def new_stats(self, level, device="cuda"):
         s = Stats(level, self.n_ctrl, device)
         self.mlsgd_stats_reset(s)
         return s
+
+
+def _report(rep, n):
+    out = {k: getattr(rep, k) for k, _ in StepReport._fields_ if k != "next_counts" and k not in _PER_LEVEL}
+    out["next_counts"] = [int(rep.next_counts[l]) for l in range(rep.next_levels)]
+    for k in _PER_LEVEL:
+        out[k] = [getattr(rep, k)[l] for l in range(n)]
+    return out
 
 
 class Stats:

@@ -177,3 +177,71 @@ def test_alpha_fit_and_level_update():
     assert p["L"] == 5 and len(p["M"]) == 5
     p = controller.plan(infos, EX_norm2=1.0, EY=1.0, grad_norm=1e-3, eta=0.9, n0=8, L_max=4)
     assert p["L"] == 4
+
+
+def inputs_z_test(Nc):
+    from paper_2606_09291_gb300 import inputs
+    return inputs.z_test(Nc)
+
+
+def test_adaptive_tau_quadratic_closed_form():
+    """J(u) = lam/2 ||u||^2 with exact gradients (err_sam = 0): L_hat = lam and the
+    adaptive step is 1/lam, which lands on the minimiser in one step."""
+    from oracle import controller
+    rng = np.random.default_rng(1)
+    lam, hc3 = 7.5, 1.0 / 64
+    u0 = rng.standard_normal(64)
+    tau0 = 0.01
+    g0 = lam * u0
+    u1 = u0 - tau0 * g0
+    g1 = lam * u1
+    tau, l_hat, fb = controller.adaptive_tau(g1, g0, tau0, 0.0, hc3, tau0)
+    assert not fb and abs(l_hat - lam) <= 1e-12 * lam and abs(tau - 1.0 / lam) <= 1e-12 / lam
+    assert np.abs(u1 - tau * g1).max() <= 1e-13 * np.abs(u0).max()
+    # sampling error shortens the step by (1 - err_sam / ||g||^2)
+    g2 = hc3 * float(g1 @ g1)
+    tau_e, _, _ = controller.adaptive_tau(g1, g0, tau0, 0.25 * g2, hc3, tau0)
+    assert abs(tau_e - 0.75 / lam) <= 1e-12 / lam
+    # no positive step: keep tau_prev
+    tau_f, _, fb = controller.adaptive_tau(g1, g0, tau0, 2.0 * g2, hc3, tau0)
+    assert fb and tau_f == tau0
+    # first iteration
+    assert controller.adaptive_tau(g1, None, 0.0, 0.0, hc3, 0.3)[0] == 0.3
+
+
+def test_adaptive_mlsgd_sigma0_lipschitz_bounds():
+    """sigma = 0: every sample is the deterministic a = 1 problem, err_sam = 0 and
+    the gradient u -> S*(S u - g) + alpha u is affine with symmetric Hessian
+    H = S*S + alpha, so L_hat is a Rayleigh-type quotient ||H d|| / ||d|| inside
+    [alpha, alpha + ||S||^2] with ||S|| <= 1/lambda_1 <= 1/(3 pi^2) (Q1 Ritz values
+    lie above the continuous ones); the steps drive the gradient to rounding level."""
+    W = mlmc.Workload(n0=4, n_levels=2, n_modes=8, corr_len=0.3, sigma=0.0, theta=3.0, alpha=1e-3, seed=0)
+    z0 = inputs_z_test(8)
+    tau0 = 50.0
+    z, hist = mlmc.mlsgd(W, z0, (3, 2), 4, tau0, adaptive=True)
+    top = W.alpha + (3 * np.pi ** 2) ** -2
+    for h in hist[1:]:
+        assert abs(h["err_sam"]) <= 1e-20
+        assert W.alpha * (1 - 1e-9) <= h["l_hat"] <= top * (1 + 1e-9)
+        assert not h["fallback"] and abs(h["tau"] - 1.0 / h["l_hat"]) <= 1e-12 * h["tau"]
+    assert hist[-1]["grad_norm"] <= 1e-8 * hist[0]["grad_norm"]
+
+
+def test_rates_second_moment_definition():
+    """The rate diagnostics' second moments equal (1/M) sum of the per-sample
+    squared norms, recomputed from the unshifted per-sample records."""
+    from oracle import controller
+    W = mlmc.Workload(n0=4, n_levels=3, n_modes=8, corr_len=0.3, sigma=1.0, theta=4.0, alpha=1e-4, seed=2)
+    z = inputs_z_test(16)
+    recs = [mlmc.level_batch(W, 0, l, range(4), z) for l in range(3)]
+    r = controller.rates([x["stats"] for x in recs], [x["shift"] for x in recs], W.theta, W.hc3)
+    for l, rec in enumerate(recs):
+        dX = [ps["dX"] * np.exp(W.theta * rec["shift"]) for ps in rec["per_sample"]]
+        dY = [ps["dY"] * np.exp(W.theta * rec["shift"]) for ps in rec["per_sample"]]
+        m2x = np.mean([W.hc3 * float(d @ d) for d in dX])
+        m2y = np.mean([d * d for d in dY])
+        assert abs(r["m2_dx"][l] - m2x) <= 1e-12 * m2x
+        assert abs(r["m2_dy"][l] - m2y) <= 1e-12 * m2y
+        mx = np.mean(dX, axis=0)
+        assert abs(r["mean_dx_norm"][l] - np.sqrt(W.hc3 * float(mx @ mx))) <= 1e-12 * r["mean_dx_norm"][l]
+    assert np.isfinite(r["beta_x"]) and np.isfinite(r["alpha_y"])
