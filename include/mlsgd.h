@@ -18,7 +18,9 @@
  * g = sin(pi x) sin(pi y) sin(pi z); Phi = 1/2 ||y - g||^2_{L2} (eq:cost).
  * Discretisation: Q1 hexahedra on level l with N_l = n0 * 2^l cells per side,
  * coefficient constant per cell (value at the cell centre); the control z is
- * constant per cell of the control grid (level ctrl_level).
+ * constant per cell of the control grid (level ctrl_level).  B z is exactly
+ * int z phi_n dx (<Bu, v> = int u v, Sec. 5) and (B*q)_c is the average of q over
+ * control cell c, for levels finer as well as coarser than the control grid.
  *
  * Conventions shared by every entry point
  *   - Every *_dev pointer is DEVICE memory owned by the caller (for example a
@@ -62,7 +64,8 @@ typedef enum { MLSGD_FP64 = 0, MLSGD_MIXED = 1 } mlsgd_precision;
 typedef struct {
   int n_levels;     /* levels 0..n_levels-1                                          */
   int n0;           /* cells per side on level 0 (8 in every preset)                 */
-  int ctrl_level;   /* level whose cells carry z; must be >= every level solved      */
+  int ctrl_level;   /* level whose cells carry z (any level; solves on finer and
+                       coarser grids both integrate z exactly)                      */
   int n_modes;      /* K, number of KL modes (even)                                  */
   double corr_len;  /* correlation length of the 1D exponential covariance           */
   double sigma;     /* standard-deviation factor of log a                           */
@@ -136,7 +139,7 @@ typedef struct {
   double tau;              /* the step taken                                              */
   double l_hat;            /* L^ of eq:adaptive-step-size (NaN for a fixed or first step)  */
   int tau_fallback;        /* 1: the adaptive rule gave a non-positive or non-finite step
-                              and tau_prev was taken instead                              */
+                              and min(tau_prev, 1/L^) was taken instead                   */
   /* rate diagnostics of this batch, unshifted, per level l (the difference samples) */
   double m2_dx[16];        /* (1/M_l) sum_m ||dX_l^(m)||_U^2, left side of eq:decayNum     */
   double m2_dy[16];        /* (1/M_l) sum_m |dY_l^(m)|^2, left side of eq:decayDenom       */
@@ -146,6 +149,8 @@ typedef struct {
      m2 ~ h_l^beta, means ~ h_l^alpha with h_l = h_0 2^-l (NaN with fewer than two
      difference levels) */
   double beta_x, beta_y, alpha_x, alpha_y;
+  double z_norm;           /* ||u_k||_U, the control before the step                      */
+  double objective;        /* J^ML(u_k) = risk + alpha/2 ||u_k||_U^2 (eq:cost)            */
 } mlsgd_step_report;
 
 /* Create a context on the current CUDA device.  Builds the KL mode table on
@@ -201,7 +206,7 @@ mlsgd_status mlsgd_solve_state_adjoint(mlsgd_ctx* ctx, int grid, int n_samples, 
 
 /* a1..a9 for one level: samples first_sample .. first_sample+n_samples-1 of
  * step `iter` on `level` (and level-1 on the same draw when level > 0):
- * fields, state and adjoint solves, B*q at the control-cell centres, shifted
+ * fields, state and adjoint solves, B*q as control-cell averages, shifted
  * weights, dX~ = X~_l - X~_{l-1}, dY~, and the Chan merge of this batch into
  * *stats (which must have been reset with mlsgd_stats_reset or hold earlier
  * batches of the same level).  The shift becomes max(old shift, max Phi of the
@@ -254,8 +259,8 @@ mlsgd_status mlsgd_step(mlsgd_ctx* ctx, const mlsgd_level_stats* stats, int n_le
  *   L^    = ||g_k - g_{k-1}||_U / ||tau_{k-1} g_{k-1}||_U,
  * g_k = grad J^ML(u_k) and err_sam_k as in *rep (the printed "t_{k-1}" is read as
  * tau_{k-1}).  Reading where the rule gives no positive finite step (sampling
- * error above ||g_k||^2, or g_k = g_{k-1}): keep tau_{k-1} and set
- * rep->tau_fallback.
+ * error at or above ||g_k||^2, or g_k = g_{k-1}): tau_k = min(tau_{k-1}, 1/L^)
+ * (tau_{k-1} if L^ is not positive and finite), and rep->tau_fallback = 1.
  *   tau0           step of the first iteration (> 0), used when tau_prev <= 0
  *   tau_prev       tau_{k-1} (<= 0 on the first iteration: grad_prev_dev is not read)
  *   grad_prev_dev  [n_ctrl_cells] FP64 device, IN g_{k-1}, OUT g_k (caller-owned,

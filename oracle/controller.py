@@ -94,7 +94,10 @@ def adaptive_tau(grad, grad_prev, tau_prev, err_sam, hc3, tau0):
     tau_k = (||g_k||^2 - err_sam_k) / (L_hat ||g_k||^2) with
     L_hat = ||g_k - g_{k-1}||_U / ||tau_{k-1} g_{k-1}||_U; the printed t_{k-1} is
     read as tau_{k-1}.  First iteration (grad_prev None): tau0.  Reading where
-    the rule gives no positive finite step: keep tau_{k-1}.
+    the rule gives no positive finite step (sampling error estimate at or above
+    ||g_k||^2): min(tau_{k-1}, 1 / L_hat), the rule without its sampling
+    correction but never longer than the last step; tau_{k-1} if L_hat is not
+    positive and finite.
     Returns (tau, L_hat, fell_back)."""
     if grad_prev is None:
         return tau0, float("nan"), False
@@ -104,6 +107,8 @@ def adaptive_tau(grad, grad_prev, tau_prev, err_sam, hc3, tau0):
     with np.errstate(all="ignore"):
         tau = (g2 - err_sam) / (l_hat * g2) if l_hat > 0 and g2 > 0 else float("nan")
     if not (math.isfinite(tau) and tau > 0):
+        if math.isfinite(l_hat) and l_hat > 0:
+            return min(tau_prev, 1.0 / l_hat), l_hat, True
         return tau_prev, l_hat, True
     return tau, l_hat, False
 

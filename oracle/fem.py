@@ -125,24 +125,45 @@ class Level:
         return g
 
     def interpolation(self, Nc):
-        """Matrix I [Nc^3, nodes] with I[c, n] = phi_n(x_c) for control-cell centres x_c."""
-        assert Nc % self.N == 0, "control grid must refine the level grid"
-        r = Nc // self.N
-        c = np.arange(Nc ** 3)
-        ci, cj, ck = c % Nc, (c // Nc) % Nc, c // (Nc * Nc)
+        """Matrix I [Nc^3, nodes] with I[c, n] = (1/|c|) int_c phi_n dx, the average of the
+        hat function phi_n over control cell c.  Then B z = h_c^3 I^T z is exactly
+        int z phi_n dx for a cellwise-constant control z (<Bu, v> = int u v, Sec. 5)
+        and B* q = I q is the cell average of q.
+
+        Control grid at least as fine as the level (Nc = r N): phi_n is trilinear on
+        each control cell, so its average is its value at the cell centre.
+        Control grid coarser (N = r Nc): per axis the average of a 1D hat over a
+        control interval of r fine cells is 1/r at the r - 1 inner nodes and 1/(2r)
+        at the two end nodes (each end node's hat lies half inside)."""
         rows, cols, vals = [], [], []
         n1 = self.N + 1
-        # position of the centre inside its level cell
-        ex, ey, ez = ci // r, cj // r, ck // r
-        tx = ((ci % r) + 0.5) / r
-        ty = ((cj % r) + 0.5) / r
-        tz = ((ck % r) + 0.5) / r
-        for a in range(8):
-            dx, dy, dz = a & 1, (a >> 1) & 1, (a >> 2) & 1
-            w = (tx if dx else 1 - tx) * (ty if dy else 1 - ty) * (tz if dz else 1 - tz)
-            node = (ex + dx) + n1 * ((ey + dy) + n1 * (ez + dz))
-            rows.append(c)
-            cols.append(node)
-            vals.append(w)
+        c = np.arange(Nc ** 3)
+        ci, cj, ck = c % Nc, (c // Nc) % Nc, c // (Nc * Nc)
+        if Nc % self.N == 0:
+            r = Nc // self.N
+            # position of the centre inside its level cell
+            ex, ey, ez = ci // r, cj // r, ck // r
+            tx = ((ci % r) + 0.5) / r
+            ty = ((cj % r) + 0.5) / r
+            tz = ((ck % r) + 0.5) / r
+            for a in range(8):
+                dx, dy, dz = a & 1, (a >> 1) & 1, (a >> 2) & 1
+                w = (tx if dx else 1 - tx) * (ty if dy else 1 - ty) * (tz if dz else 1 - tz)
+                node = (ex + dx) + n1 * ((ey + dy) + n1 * (ez + dz))
+                rows.append(c)
+                cols.append(node)
+                vals.append(w)
+        else:
+            assert self.N % Nc == 0, "one grid must refine the other"
+            r = self.N // Nc
+            w1 = np.full(r + 1, 1.0 / r)
+            w1[0] = w1[-1] = 0.5 / r
+            for a in range(r + 1):
+                for b in range(r + 1):
+                    for d in range(r + 1):
+                        node = (r * ci + a) + n1 * ((r * cj + b) + n1 * (r * ck + d))
+                        rows.append(c)
+                        cols.append(node)
+                        vals.append(np.full(c.shape, w1[a] * w1[b] * w1[d]))
         return sp.coo_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))),
                              shape=(Nc ** 3, self.nn)).tocsr()

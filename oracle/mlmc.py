@@ -216,8 +216,10 @@ def mlsgd(W, z, counts, iterations, tau0, adaptive=False, eta=0.9, L_max=None, a
             tau, l_hat, fb = controller.adaptive_tau(res["grad"], g_prev, tau_prev, p["err_sam"], W.hc3, tau0)
         else:
             tau, l_hat, fb = tau0, float("nan"), False
+        objective = res["risk"] + 0.5 * W.alpha * W.hc3 * float(z @ z)  # J^ML(u_k), eq:cost
         z = z - tau * res["grad"]
         hist.append(dict(tau=tau, l_hat=l_hat, fallback=fb, grad_norm=res["grad_norm"], risk=res["risk"],
+                         objective=objective,
                          err_sam=p["err_sam"], counts=list(counts), plan=p,
                          rates=controller.rates(stats, shifts, W.theta, W.hc3)))
         g_prev, tau_prev = res["grad"], tau

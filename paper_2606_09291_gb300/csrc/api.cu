@@ -404,7 +404,7 @@ mlsgd_status mlsgd_solve_state_adjoint(mlsgd_ctx* ctx, int grid, int n_samples, 
                                        int* iters_dev, int* status_dev, void* stream) {
   if (!ctx) return MLSGD_EINVAL;
   cudaStream_t st = (cudaStream_t)stream;
-  if (grid < 0 || grid >= ctx->cfg.n_levels || grid > ctx->cfg.ctrl_level || n_samples < 0)
+  if (grid < 0 || grid >= ctx->cfg.n_levels || n_samples < 0)
     return fail(ctx, MLSGD_EINVAL, "mlsgd_solve_state_adjoint: bad grid or sample count");
   if (n_samples == 0) return MLSGD_OK;
   if (!log_a_dev || !z_dev || !y_dev || !q_dev || !phi_dev || !iters_dev || !status_dev)
@@ -469,7 +469,7 @@ mlsgd_status mlsgd_solve_state_adjoint_noalloc(mlsgd_ctx* ctx, int grid, int n_s
                                                int* iters_dev, int* status_dev, void* stream) {
   if (!ctx) return MLSGD_EINVAL;
   cudaStream_t st = (cudaStream_t)stream;
-  if (grid < 0 || grid >= ctx->cfg.n_levels || grid > ctx->cfg.ctrl_level || n_samples < 0)
+  if (grid < 0 || grid >= ctx->cfg.n_levels || n_samples < 0)
     return fail(ctx, MLSGD_EINVAL, "mlsgd_solve_state_adjoint_noalloc: bad grid or sample count");
   if (n_samples == 0) return MLSGD_OK;
   if (!log_a_dev || !z_dev || !y_dev || !q_dev || !phi_dev || !iters_dev || !status_dev)
@@ -526,7 +526,7 @@ mlsgd_status mlsgd_level_gradient(mlsgd_ctx* ctx, int iter, int level, int64_t f
                                   const double* z_dev, mlsgd_level_stats* stats, void* stream) {
   if (!ctx) return MLSGD_EINVAL;
   cudaStream_t st = (cudaStream_t)stream;
-  if (level < 0 || level >= ctx->cfg.n_levels || level > ctx->cfg.ctrl_level || n_samples < 0 || first_sample < 0 ||
+  if (level < 0 || level >= ctx->cfg.n_levels || n_samples < 0 || first_sample < 0 ||
       iter < 0 || !z_dev || !stats || !stats->field_dev || !stats->scalars_dev || stats->level != level)
     return fail(ctx, MLSGD_EINVAL, "mlsgd_level_gradient: bad arguments");
   if (n_samples == 0) return MLSGD_OK;
@@ -624,7 +624,7 @@ static mlsgd_status step_core(mlsgd_ctx* ctx, const mlsgd_level_stats* stats, in
   if (!std::isfinite(denom) || !std::isfinite(cstar)) return fail(ctx, MLSGD_ENONFINITE, "mlsgd_step: non-finite shift");
   const long long nc = cells_of(ctx->Nc());
   const int nblk = (int)((nc + 255) / 256);
-  const int rows = n_levels + 4;
+  const int rows = n_levels + 5;
   const size_t part_bytes = al((size_t)(rows + 1) * nblk * 8 + 64 * 8);
   mlsgd_status s = ensure_ws(ctx, part_bytes + al(16 * 8) + (adaptive ? al((size_t)nc * 8) : 0), st);
   if (s != MLSGD_OK) return s;
@@ -641,14 +641,16 @@ static mlsgd_status step_core(mlsgd_ctx* ctx, const mlsgd_level_stats* stats, in
   CK(cudaMemcpyAsync(hb, partial + (size_t)rows * nblk, rows * sizeof(double), cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
   const double hc = 1.0 / ctx->Nc(), hc3 = hc * hc * hc;
-  const double g2 = hb[0] * hc3, ex2 = hb[1] * hc3, diff2 = hb[2] * hc3, gp2 = hb[3] * hc3;
-  const double* ml = hb + 4;
+  const double g2 = hb[0] * hc3, ex2 = hb[1] * hc3, diff2 = hb[2] * hc3, gp2 = hb[3] * hc3, z2 = hb[4] * hc3;
+  const double* ml = hb + 5;
   std::memset(rep, 0, sizeof(*rep));
   rep->grad_norm = std::sqrt(g2);
   rep->ey = ey;
   rep->shift = cstar;
   rep->truncated = ey < floor_y ? 1 : 0;
   rep->risk = ey > 0 ? cstar + std::log(ey) / theta : NAN;
+  rep->z_norm = std::sqrt(z2);
+  rep->objective = rep->risk + 0.5 * ctx->cfg.alpha * z2;
   if (!std::isfinite(rep->grad_norm)) return fail(ctx, MLSGD_ENONFINITE, "mlsgd_step: non-finite gradient");
   // ---- adaptive plan (eq:sec-order-sum .. eq:mse-estimate-mlmc; see the readings in the header)
   const int L = n_levels;
@@ -737,7 +739,8 @@ static mlsgd_status step_core(mlsgd_ctx* ctx, const mlsgd_level_stats* stats, in
       if (std::isfinite(t) && t > 0) {
         rep->tau = t;
       } else {
-        rep->tau = tau_prev;
+        const bool lh = std::isfinite(rep->l_hat) && rep->l_hat > 0;
+        rep->tau = lh ? std::min(tau_prev, 1.0 / rep->l_hat) : tau_prev;
         rep->tau_fallback = 1;
       }
     }

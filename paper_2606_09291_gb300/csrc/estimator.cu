@@ -19,7 +19,17 @@ __global__ void k_rhs_state(const double* __restrict__ z, int Nc, int N, double*
   int i, j, k;
   node_ijk(n, n1, i, j, k);
   double acc = 0.0;
-  if (interior(i, j, k, N)) {
+  if (interior(i, j, k, N) && N > Nc) {
+    // control coarser than the grid: each of the 8 cells around the node lies in one
+    // control cell (its parent) and int_e phi_n = h^3 / 8
+    const int r = N / Nc;
+    for (int dz = -1; dz <= 0; ++dz)
+      for (int dy = -1; dy <= 0; ++dy)
+        for (int dx = -1; dx <= 0; ++dx)
+          acc += z[(i + dx) / r + (long long)Nc * ((j + dy) / r + (long long)Nc * ((k + dz) / r))];
+    const double h = 1.0 / N;
+    acc *= 0.125 * h * h * h;
+  } else if (interior(i, j, k, N)) {
     const int r = Nc / N;
     const double inv_r = 1.0 / r;
     for (int cz = r * (k - 1); cz < r * (k + 1); ++cz) {
@@ -188,9 +198,30 @@ __global__ void k_level_scalars(const double* __restrict__ phif, const double* _
   }
 }
 
-// value of the nodal function q (grid N) at the centre of control cell (cx, cy, cz)
-__device__ __forceinline__ double eval_at_ctrl(const double* __restrict__ q, int N, int r, int cx, int cy, int cz) {
+// Average of the nodal function q (grid N) over control cell (cx, cy, cz) of the
+// Nc grid.  N <= Nc (r = Nc / N): q is trilinear on the control cell, so the
+// average is its value at the cell centre.  N > Nc (r = N / Nc): trapezoid
+// weights per axis over the r + 1 grid nodes of the cell, 1/r inside and
+// 1/(2r) at the two ends.
+__device__ __forceinline__ double eval_at_ctrl(const double* __restrict__ q, int N, int Nc, int cx, int cy, int cz) {
   const int n1 = N + 1;
+  if (N > Nc) {
+    const int r = N / Nc;
+    const double wi = 1.0 / r, we = 0.5 / r;
+    double acc = 0.0;
+    for (int c = 0; c <= r; ++c) {
+      const double wz = (c == 0 || c == r) ? we : wi;
+      for (int b = 0; b <= r; ++b) {
+        const double wy = (b == 0 || b == r) ? we : wi;
+        const double* row = q + (long long)r * cx + (long long)n1 * ((long long)r * cy + b + (long long)n1 * ((long long)r * cz + c));
+        double rs = 0.5 * (row[0] + row[r]);
+        for (int a = 1; a < r; ++a) rs += row[a];
+        acc += wz * wy * rs * wi;
+      }
+    }
+    return acc;
+  }
+  const int r = Nc / N;
   const int ex = cx / r, ey = cy / r, ez = cz / r;
   const double tx = ((cx % r) + 0.5) / r, ty = ((cy % r) + 0.5) / r, tz = ((cz % r) + 0.5) / r;
   const double* b = q + ex + (long long)n1 * (ey + (long long)n1 * ez);
@@ -202,8 +233,8 @@ __device__ __forceinline__ double eval_at_ctrl(const double* __restrict__ q, int
   return (c00 * (1 - ty) + c10 * ty) * (1 - tz) + (c01 * (1 - ty) + c11 * ty) * tz;
 }
 
-// One thread per control cell: B*q at the cell centre for both grids
-// ((B*q)_c = q(x_c)), dX~_s = w_f[s] B*q_f[s] - w_c[s] B*q_c[s], Welford over
+// One thread per control cell: B*q as the cell average for both grids
+// (eval_at_ctrl), dX~_s = w_f[s] B*q_f[s] - w_c[s] B*q_c[s], Welford over
 // the batch, Chan merge with the rescaled old mean; block partials of
 // h_c^3 (M2_batch + delta^2 n_old S / n).
 __global__ void k_level_field(const double* __restrict__ qf, int Nf, const double* __restrict__ qc, int Ncs, int S,
@@ -215,13 +246,12 @@ __global__ void k_level_field(const double* __restrict__ qf, int Nf, const doubl
   if (c < ncell) {
     const int cx = (int)(c % Nc), cy = (int)((c / Nc) % Nc), cz = (int)(c / ((long long)Nc * Nc));
     const long long nf = nodes_of(Nf), ncn = qc ? nodes_of(Ncs) : 0;
-    const int rf = Nc / Nf, rc = qc ? Nc / Ncs : 1;
     const double* wf = work + 4;
     const double* wc = work + 4 + S;
     double mean = 0.0, m2 = 0.0;
     for (int s = 0; s < S; ++s) {
-      double v = wf[s] * eval_at_ctrl(qf + s * nf, Nf, rf, cx, cy, cz);
-      if (qc) v -= wc[s] * eval_at_ctrl(qc + s * ncn, Ncs, rc, cx, cy, cz);
+      double v = wf[s] * eval_at_ctrl(qf + s * nf, Nf, Nc, cx, cy, cz);
+      if (qc) v -= wc[s] * eval_at_ctrl(qc + s * ncn, Ncs, Nc, cx, cy, cz);
       const double d = v - mean;
       mean += d / (s + 1);
       m2 += d * (v - mean);
@@ -335,7 +365,8 @@ void launch_stats_merge(double* dfield, double* dsc, const double* sfield, const
 // ---------------------------------------------------------------- combine and step
 // EX = sum_l f_l mean_l (f_l = exp(theta (c_l - c*))), grad = EX / denom + alpha z,
 // z <- z - tau grad when `update`.  partial rows: 0 = ||grad||^2, 1 = ||EX||^2,
-// 2 = ||grad - gprev||^2, 3 = ||gprev||^2 (0 without gprev), 4+l = ||mean_l||^2
+// 2 = ||grad - gprev||^2, 3 = ||gprev||^2 (0 without gprev), 4 = ||z||^2 (before the
+// step), 5+l = ||mean_l||^2
 // (unscaled, counted without h_c^3).
 struct FieldList { const double* f[16]; };
 
@@ -344,7 +375,7 @@ __global__ void k_combine_step(FieldList fl, const double* __restrict__ factors,
                                double* __restrict__ grad, const double* __restrict__ gprev,
                                double* __restrict__ partial, int nblk) {
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  double ex = 0.0, g = 0.0, d = 0.0, gp = 0.0;
+  double ex = 0.0, g = 0.0, d = 0.0, gp = 0.0, zz = 0.0;
   double ml[16];
   for (int l = 0; l < L; ++l) ml[l] = 0.0;
   if (i < n) {
@@ -354,6 +385,7 @@ __global__ void k_combine_step(FieldList fl, const double* __restrict__ factors,
       ex += factors[l] * m;
     }
     const double zi = z[i];
+    zz = zi * zi;
     g = ex / denom + alpha * zi;
     if (gprev) {
       gp = gprev[i];
@@ -362,8 +394,8 @@ __global__ void k_combine_step(FieldList fl, const double* __restrict__ factors,
     if (grad) grad[i] = g;
     if (update) z[i] = zi - tau * g;
   }
-  const double rowv[4] = {g * g, ex * ex, d * d, gp * gp};
-  for (int r = 0; r < 4; ++r) {
+  const double rowv[5] = {g * g, ex * ex, d * d, gp * gp, zz};
+  for (int r = 0; r < 5; ++r) {
     if (r) __syncthreads();
     const double v = block_sum(rowv[r]);
     if (threadIdx.x == 0) partial[(long long)r * nblk + blockIdx.x] = v;
@@ -371,7 +403,7 @@ __global__ void k_combine_step(FieldList fl, const double* __restrict__ factors,
   for (int l = 0; l < L; ++l) {
     __syncthreads();
     const double v = block_sum(ml[l]);
-    if (threadIdx.x == 0) partial[(long long)(4 + l) * nblk + blockIdx.x] = v;
+    if (threadIdx.x == 0) partial[(long long)(5 + l) * nblk + blockIdx.x] = v;
   }
 }
 
@@ -403,7 +435,7 @@ void launch_combine_step(const double* const* fields, const double* factors, int
   const double bytes = (double)ncells * 8 * (L + 1 + (update ? 1 : 0) + (grad ? 1 : 0) + (gprev ? 1 : 0));
   launch("combine", bytes, k_combine_step, dim3(nblk), kBlock, 0, st, fl, factors, L, ncells, denom, alpha, tau,
          update ? 1 : 0, z, grad, gprev, partial, nblk);
-  const int rows = L + 4;
+  const int rows = L + 5;
   launch("combine_finish", 0.0, k_rows_finish, dim3((rows + 7) / 8), 256, 0, st, (const double*)partial, nblk, rows,
          partial + (long long)rows * nblk);
 }

@@ -138,8 +138,8 @@ void launch_level_stats(const double* qf, const double* phif, int Nf, const doub
 void launch_stats_reset(double* field, double* scalars, long long ncells, cudaStream_t st);
 void launch_stats_merge(double* dfield, double* dsc, const double* sfield, const double* ssc, long long ncells,
                         double hc3, double theta, double* partial, cudaStream_t st);
-// combine levels and (when `update`) step; partial gets [L + 4][blocks] sums and
-// then the L + 4 totals; gprev (optional) is the previous gradient
+// combine levels and (when `update`) step; partial gets [L + 5][blocks] sums and
+// then the L + 5 totals; gprev (optional) is the previous gradient
 void launch_combine_step(const double* const* fields, const double* factors, int L, long long ncells,
                          double denom, double alpha, double tau, bool update, double* z, double* grad,
                          const double* gprev, double* partial, int nblk, cudaStream_t st);

@@ -10,6 +10,7 @@ runs in libmlsgd; the host only fits the exponent of the measured cost per
 sample when asked to time the levels.
 """
 import math
+import time
 
 import torch
 
@@ -34,7 +35,7 @@ def _slope(ls, vals):
 
 
 def run_mlsgd(ctx, z, counts, iterations, tau, eta=0.9, max_levels=None, adapt=True, stream=None, log=None,
-              step="fixed", time_levels=False):
+              step="fixed", time_levels=False, grad_tol=None, budget_s=None, count_cap=None):
     """Run `iterations` MLSGD steps from control z (device FP64 tensor, updated in
     place).  counts: initial per-level batch sizes (levels 0..len-1).
     step: "fixed" (tau every iteration) or "adaptive" (eq:adaptive-step-size with
@@ -42,8 +43,20 @@ def run_mlsgd(ctx, z, counts, iterations, tau, eta=0.9, max_levels=None, adapt=T
     time_levels: time each level's batch with CUDA events and report the cost per
     sample and its exponent gamma_hat (eq:assumption_gamma, cost ~ h_l^-gamma,
     fitted over l >= 1; this synchronises after every level).
+    Stops after `iterations` steps, or earlier once the gradient norm of an
+    iteration is <= grad_tol (the loop condition of Algorithm 1, MLSGD; that
+    iteration's step is still taken, so the result is u_{k+1}), or once budget_s
+    wall-clock seconds have passed at the end of an iteration (a plain time budget:
+    the budgeting scheme the paper cites for choosing its tolerance is not restated).
+    count_cap: optional upper bound on every planned batch size.
+    With budget_s and adapt, the planned batches of the next iteration are scaled
+    down together (keeping their ratios, at least 2 each) when their estimated
+    time, from this iteration's measured cost per sample (a new level: 8 times the
+    last), exceeds the budget left; this turns on time_levels.
     Returns the list of per-iteration reports (host dicts)."""
     assert step in ("fixed", "adaptive")
+    if budget_s is not None and adapt:
+        time_levels = True
     max_levels = ctx.cfg["n_levels"] if max_levels is None else max_levels
     counts = list(counts)
     history = []
@@ -51,6 +64,7 @@ def run_mlsgd(ctx, z, counts, iterations, tau, eta=0.9, max_levels=None, adapt=T
     g_prev = torch.zeros_like(z) if step == "adaptive" else None
     tau_prev = 0.0
     strm = stream if stream is not None else torch.cuda.current_stream()
+    t0 = time.perf_counter()
     for k in range(iterations):
         level_ms = []
         for l, m in enumerate(counts):
@@ -78,6 +92,22 @@ def run_mlsgd(ctx, z, counts, iterations, tau, eta=0.9, max_levels=None, adapt=T
         history.append(rep)
         if log is not None:
             log(rep)
+        rep["elapsed_s"] = time.perf_counter() - t0
         if adapt:
             counts = list(rep["next_counts"])
+            if count_cap is not None:
+                counts = [min(m, count_cap) for m in counts]
+            if budget_s is not None:
+                cps = list(rep["cost_per_sample_ms"])
+                while len(cps) < len(counts):
+                    cps.append(8.0 * cps[-1])
+                left_ms = 1000.0 * (budget_s - rep["elapsed_s"])
+                est_ms = sum(m * c for m, c in zip(counts, cps))
+                if left_ms > 0 and est_ms > left_ms:
+                    f = left_ms / est_ms
+                    counts = [max(2, int(m * f)) for m in counts]
+        if grad_tol is not None and rep["grad_norm"] <= grad_tol:
+            break
+        if budget_s is not None and rep["elapsed_s"] >= budget_s:
+            break
     return history

@@ -21,9 +21,12 @@ PRESETS = {
     "c4": dict(n_levels=6, n0=8, n_modes=128, corr_len=0.2, sigma=1.0, theta=10.0, alpha=1e-4, seed=0,
                mix=(1024, 256, 64, 16, 4, 1), precision="mixed"),
     # the paper's Sec. 5 setting: cos-product KL, 125 modes, rho = 0.15, xi ~ U(-4, 4),
-    # target prod sin(2 pi x_i); theta swept over {1, 8, 16, ..., 72}
-    "paper": dict(n_levels=4, n0=8, n_modes=125, corr_len=0.15, sigma=1.0, theta=8.0, alpha=1e-4, seed=0,
-                  field_model=1, target_freq=2, counts=(128, 16, 2), thetas=(1, 8, 16, 24, 32, 40, 48, 56, 64, 72)),
+    # target prod sin(2 pi x_i); initial batches {128, 16, 2} on the cube refined 4, 5
+    # and 6 times (16^3, 32^3, 64^3), one further refinement (128^3) allowed; the
+    # control lives on the 64^3 grid; theta swept over {1, 8, 16, ..., 72}
+    "paper": dict(n_levels=4, n0=16, ctrl_level=2, n_modes=125, corr_len=0.15, sigma=1.0, theta=8.0, alpha=1e-4,
+                  seed=0, field_model=1, target_freq=2, counts=(128, 16, 2),
+                  thetas=(1, 8, 16, 24, 32, 40, 48, 56, 64, 72)),
     # large risk aversion, levels 0..5, 512 modes
     "c5": dict(n_levels=6, n0=8, n_modes=512, corr_len=0.1, sigma=1.5, theta=100.0, alpha=1e-4, seed=0,
                precision="mixed"),

@@ -43,7 +43,7 @@ class StepReport(ctypes.Structure):
                 ("m2_dx", ctypes.c_double * 16), ("m2_dy", ctypes.c_double * 16),
                 ("mean_dx_norm", ctypes.c_double * 16), ("mean_dy_abs", ctypes.c_double * 16),
                 ("beta_x", ctypes.c_double), ("beta_y", ctypes.c_double), ("alpha_x", ctypes.c_double),
-                ("alpha_y", ctypes.c_double)]
+                ("alpha_y", ctypes.c_double), ("z_norm", ctypes.c_double), ("objective", ctypes.c_double)]
 
 _PER_LEVEL = ("mean_dx_norm2", "v2", "m2_dx", "m2_dy", "mean_dx_norm", "mean_dy_abs")
 

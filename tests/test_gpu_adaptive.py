@@ -48,6 +48,7 @@ def test_adaptive_steps_match_oracle(lib, workload):
     assert hist[0]["tau"] == tau0 and math.isnan(hist[0]["l_hat"])
     for g, r in zip(hist, ref):
         assert rel(g["grad_norm"], r["grad_norm"]) <= TOL64
+        assert rel(g["objective"], r["objective"]) <= TOL64
         assert g["tau_fallback"] == int(r["fallback"])
         assert rel(g["tau"], r["tau"]) <= TOL64
         if not math.isnan(r["l_hat"]):
@@ -78,4 +79,21 @@ def test_fixed_step_reports_tau(lib):
     g = torch.zeros_like(z)
     with pytest.raises(lib.MlsgdError):
         ctx.mlsgd_step_adaptive(st, -1.0, 0.0, z, g)
+    ctx.close()
+
+
+def test_stop_rules_and_count_cap(lib):
+    from paper_2606_09291_gb300 import driver
+    ctx = lib.Context(n_levels=3, n0=4, n_modes=16, corr_len=0.3, sigma=1.0, theta=2.0, alpha=1e-4, seed=0,
+                      rtol=1e-8, precision="mixed")
+    z = torch.zeros(16 ** 3, dtype=torch.float64, device="cuda")
+    # gradient tolerance above any gradient: one iteration, its step taken
+    h = driver.run_mlsgd(ctx, z, (4, 2), 5, 100.0, grad_tol=float("inf"))
+    assert len(h) == 1 and torch.any(z != 0)
+    # zero budget: one iteration
+    h = driver.run_mlsgd(ctx, z, (4, 2), 5, 100.0, budget_s=0.0, step="adaptive")
+    assert len(h) == 1
+    # planned batches capped
+    h = driver.run_mlsgd(ctx, z, (4, 2), 3, 100.0, count_cap=3, step="adaptive")
+    assert all(m <= 3 for r in h[1:] for m in r["counts"])
     ctx.close()

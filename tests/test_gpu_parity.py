@@ -253,3 +253,22 @@ def test_iteration_cap_reports_noconv(lib):
     assert st == 3  # MLSGD_ENOCONV
     assert np.all(stt.cpu().numpy() == 1) and np.all(it.cpu().numpy() == 4)
     ctx.close()
+
+
+@pytest.mark.parametrize("ctrl_level", [0, 1])
+def test_control_coarser_than_grid(lib, ctrl_level):
+    """Solves and level statistics on grids finer than the control grid: B z by
+    exact integration of the cellwise control, B*q as control-cell averages."""
+    y, q, phi, it, st, refs = _solve_both(lib, "fp64", 2, 2, 1e-13, z_kind="rand", ctrl_level=ctrl_level)
+    assert np.all(st == 0)
+    for s in range(2):
+        assert rel_err(y[s], refs[s]["y"]) <= TOL64 and rel_err(q[s], refs[s]["q"]) <= TOL64
+        assert abs(phi[s] - refs[s]["phi"]) <= TOL64 * abs(refs[s]["phi"])
+    ctx = lib.Context(**dict(CFG, rtol=1e-13, max_iter=400, theta=5.0, ctrl_level=ctrl_level))
+    W = oracle_workload(theta=5.0, ctrl_level=ctrl_level)
+    z = inputs.z_random(8 << ctrl_level, 3, 20.0)
+    zt = cuda(z)
+    for level, n in ((2, 3), (1, 4)):
+        st_ = _gpu_level(ctx, level, n, zt)
+        _compare_stats(st_, _oracle_level(W, level, n, z), W, TOL64)
+    ctx.close()

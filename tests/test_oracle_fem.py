@@ -126,3 +126,26 @@ def test_solvers_agree():
         assert np.abs(x - xd).max() <= 1e-10 * np.abs(xd).max()
     x0, it0 = solve.solve(A, np.zeros_like(b), 16, method="mg")
     assert it0 == 0 and not np.any(x0)
+
+
+@pytest.mark.parametrize("N,Nc", [(8, 4), (8, 2), (4, 8), (4, 4)])
+def test_control_cell_averages(N, Nc):
+    """I[c, n] = average of phi_n over control cell c, both when the control grid is
+    finer and when it is coarser than the level: partition of unity, exact averages
+    of the Q1-represented functions x and x y z, the trapezoid identity for x^2
+    (mean over the cell + h^2/6 for a coarse control), and B 1 = int phi_n = h^3."""
+    lev = fem.Level(N)
+    I = lev.interpolation(Nc)
+    x, y, z = lev.node_coords()
+    c = np.arange(Nc ** 3)
+    xc, yc, zc = (c % Nc + 0.5) / Nc, ((c // Nc) % Nc + 0.5) / Nc, (c // Nc ** 2 + 0.5) / Nc
+    assert np.abs(I @ np.ones(lev.nn) - 1).max() < 1e-14
+    assert np.abs(I @ x - xc).max() < 1e-14
+    assert np.abs(I @ (x * y * z) - xc * yc * zc).max() < 1e-14
+    if N > Nc:
+        H, h = 1.0 / Nc, 1.0 / N
+        a0 = xc - H / 2
+        mean_x2 = ((a0 + H) ** 3 - a0 ** 3) / (3 * H)
+        assert np.abs(I @ (x * x) - (mean_x2 + h * h / 6)).max() < 1e-14
+    b = (1.0 / Nc) ** 3 * (I.T @ np.ones(Nc ** 3))
+    assert np.abs(b[lev.interior] - (1.0 / N) ** 3).max() < 1e-17

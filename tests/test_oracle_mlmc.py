@@ -202,9 +202,14 @@ def test_adaptive_tau_quadratic_closed_form():
     g2 = hc3 * float(g1 @ g1)
     tau_e, _, _ = controller.adaptive_tau(g1, g0, tau0, 0.25 * g2, hc3, tau0)
     assert abs(tau_e - 0.75 / lam) <= 1e-12 / lam
-    # no positive step: keep tau_prev
+    # no positive step: min(tau_prev, 1 / L_hat)
     tau_f, _, fb = controller.adaptive_tau(g1, g0, tau0, 2.0 * g2, hc3, tau0)
     assert fb and tau_f == tau0
+    big = 0.5  # a previous step longer than 1 / lam: u1' = u0 - big lam u0
+    u1b = u0 - big * g0
+    tau_b, l_b, fb = controller.adaptive_tau(lam * u1b, g0, big, 2.0 * hc3 * float((lam * u1b) @ (lam * u1b)),
+                                             hc3, big)
+    assert fb and abs(l_b - lam) <= 1e-12 * lam and abs(tau_b - 1.0 / lam) <= 1e-12 / lam
     # first iteration
     assert controller.adaptive_tau(g1, None, 0.0, 0.0, hc3, 0.3)[0] == 0.3
 
