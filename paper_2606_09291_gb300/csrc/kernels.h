@@ -61,6 +61,7 @@ struct SolverBufs {
   void* vx[8];               // V-cycle iterate per level
   void* vt[8];               // V-cycle temporary / output per level
   void* vr[8];               // restricted residual (j >= 1)
+  void* dinv[8];             // D^{-1} of levels run with the tiled passes (0 at boundary nodes), else null
   // Krylov vectors
   void* x;                   // solution / correction
   void* r;                   // residual
@@ -103,13 +104,14 @@ template <typename T, typename TA>
 void tiled_apply(const T* z, const T* pold, T* pnew, const TA* a, T* q, double* partial, const SolveScalars* sc, int N,
                  int S, int first, cudaStream_t st);
 template <typename T, typename TA>
-void tiled_pre(const T* r, const TA* a, T* t, const SolveScalars* sc, int N, int S, double omega, cudaStream_t st);
+void tiled_pre(const T* r, const TA* a, const T* dinv, T* t, const SolveScalars* sc, int N, int S, double omega,
+               cudaStream_t st);
 template <typename T, typename TA>
-void tiled_post(const T* r, const TA* a, const T* ec, T* z, double* partial, const SolveScalars* sc, int N, int S,
-                double omega, cudaStream_t st);
+void tiled_post(const T* r, const TA* a, const T* dinv, const T* ec, T* z, double* partial, const SolveScalars* sc,
+                int N, int S, double omega, cudaStream_t st);
 void tiled_apply_x(const float* z, const float* pold, float* pnew, const float* a, float* q, float* x, double* partial,
                    const SolveScalars* sc, int N, int S, cudaStream_t st);
-void tiled_pre_update(const float* r, const float* q, const __nv_bfloat16* a, float* t, float* rnew,
+void tiled_pre_update(const float* r, const float* q, const __nv_bfloat16* a, const float* dinv, float* t, float* rnew,
                       const SolveScalars* sc, int N, int S, double omega, cudaStream_t st);
 void tiled_res64(const double* b, long long bstride, const double* x, const float* a, double* r, double* partial,
                  const SolveScalars* sc, int N, int S, cudaStream_t st);

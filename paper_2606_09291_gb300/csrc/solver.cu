@@ -363,6 +363,9 @@ static int mg_levels(int N) {
   return J;
 }
 
+// levels whose smoothing runs in the tiled passes (they read a precomputed D^{-1})
+static bool tiled_level(int N, int j) { return N >= kTiledMinN && mg_levels(N) >= 1 && (N >> j) >= kTiledMinN; }
+
 size_t solver_bytes(int N, int S, int elem) {
   size_t b = 0;
   const int J = mg_levels(N);
@@ -371,6 +374,8 @@ size_t solver_bytes(int N, int S, int elem) {
     const int Nj = N >> j;
     b += 3 * align_up((size_t)S * nodes_of(Nj) * elem) + align_up((size_t)S * cells_of(Nj) * elem);
   }
+  for (int j = 0; j <= J; ++j)
+    if (tiled_level(N, j)) b += align_up((size_t)S * nodes_of(N >> j) * elem);
   b += align_up((size_t)S * node_blocks(N) * sizeof(double));
   b += 2 * align_up((size_t)S * sizeof(SolveScalars));
   b += align_up(sizeof(int));
@@ -391,6 +396,9 @@ void carve_solver(SolverBufs& B, int N, int S, int elem, char*& ptr) {
     B.vx[j] = take(vj); B.vt[j] = take(vj); B.vr[j] = take(vj);
     B.acoef[j] = take((size_t)S * cells_of(Nj) * elem);
   }
+  for (int j = 0; j < 8; ++j) B.dinv[j] = nullptr;
+  for (int j = 0; j <= B.J; ++j)
+    if (tiled_level(N, j)) B.dinv[j] = take((size_t)S * nodes_of(N >> j) * elem);
   B.partial = (double*)take((size_t)S * node_blocks(N) * sizeof(double));
   B.sc = (SolveScalars*)take((size_t)2 * S * sizeof(SolveScalars));
   B.count = (int*)take(sizeof(int));
@@ -412,6 +420,40 @@ static const char* cls(const char* base, bool fine) {
   return buf;
 }
 
+// D^{-1} = 1 / ((h/3) sum_8 a) at interior nodes, 0 on the boundary (computed once per
+// coefficient hierarchy; the tiled smoothing passes stage it like a vector)
+template <typename T, typename TA>
+__global__ void k_dinv(const TA* __restrict__ a, T* __restrict__ dinv, int N) {
+  const int s = blockIdx.y;
+  const int n1 = N + 1;
+  const long long nodes = (long long)n1 * n1 * n1;
+  const int n = blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= nodes) return;
+  int i, j, k;
+  node_ijk(n, n1, i, j, k);
+  T v = T(0);
+  if (interior(i, j, k, N)) {
+    Cells8<T, TA> C;
+    C.load(a + s * (long long)N * N * N, i, j, k, N);
+    v = T(1) / (T(1.0 / (3.0 * N)) * C.sum);
+  }
+  dinv[s * nodes + n] = v;
+}
+
+template <typename T, typename TA0>
+static void build_dinv(SolverBufs& B, const TA0* a0, cudaStream_t st) {
+  for (int j = 0; j <= B.J; ++j) {
+    if (!B.dinv[j]) continue;
+    const int Nj = B.N >> j;
+    if (j == 0)
+      launch("dinv", nbytes<T, TA0>(Nj, B.S, 1, 1), k_dinv<T, TA0>, grid_nodes(Nj, B.S), kBlock, 0, st, a0,
+             (T*)B.dinv[0], Nj);
+    else
+      launch("dinv", nbytes<T, T>(Nj, B.S, 1, 1), k_dinv<T, T>, grid_nodes(Nj, B.S), kBlock, 0, st,
+             (const T*)B.acoef[j], (T*)B.dinv[j], Nj);
+  }
+}
+
 template <typename TI, typename TO>
 static void coarsen_all(SolverBufs& B, const TI* a0, cudaStream_t st) {
   for (int j = 1; j <= B.J; ++j) {
@@ -426,9 +468,13 @@ static void coarsen_all(SolverBufs& B, const TI* a0, cudaStream_t st) {
              (TO*)B.acoef[j], Nc, B.S);
   }
 }
-void build_hierarchy_fp64(SolverBufs& B, const double* a64, cudaStream_t st) { coarsen_all<double, double>(B, a64, st); }
+void build_hierarchy_fp64(SolverBufs& B, const double* a64, cudaStream_t st) {
+  coarsen_all<double, double>(B, a64, st);
+  build_dinv<double, double>(B, a64, st);
+}
 void build_hierarchy_mixed(SolverBufs& B, const __nv_bfloat16* abf, cudaStream_t st) {
   coarsen_all<__nv_bfloat16, float>(B, abf, st);
+  build_dinv<float, __nv_bfloat16>(B, abf, st);
 }
 
 // One V(1,1)-cycle on r0 (level-0 coefficient a0); the result is left in vt[0].
@@ -450,11 +496,11 @@ static int vcycle(SolverBufs& B, const T* r0, const TA0* a0, const SolveScalars*
     const bool fine = j == 0;
     if (fine && tiled && fuse_q) {
       if constexpr (std::is_same<T, float>::value && std::is_same<TA0, __nv_bfloat16>::value)
-        tiled_pre_update(r0, fuse_q, a0, (T*)B.vt[0], r_new, sc, Nj, S, (double)omega, st);
+        tiled_pre_update(r0, fuse_q, a0, (const T*)B.dinv[0], (T*)B.vt[0], r_new, sc, Nj, S, (double)omega, st);
     } else if (fine && tiled) {
-      tiled_pre<T, TA0>(r0, a0, (T*)B.vt[0], sc, Nj, S, (double)omega, st);
+      tiled_pre<T, TA0>(r0, a0, (const T*)B.dinv[0], (T*)B.vt[0], sc, Nj, S, (double)omega, st);
     } else if (!fine && tiled && Nj >= kTiledMinN) {
-      tiled_pre<T, T>(rin(j), (const T*)B.acoef[j], (T*)B.vt[j], sc, Nj, S, (double)omega, st);
+      tiled_pre<T, T>(rin(j), (const T*)B.acoef[j], (const T*)B.dinv[j], (T*)B.vt[j], sc, Nj, S, (double)omega, st);
     } else if (fine) {
       launch(cls<T>("jacobi0", true), nbytes<T, TA0>(Nj, S, 2, 1), k_jacobi0<T, TA0>, grid_nodes(Nj, S), kBlock, 0,
              st, rin(0), a0, (T*)B.vx[0], sc, Nj, omega);
@@ -479,13 +525,14 @@ static int vcycle(SolverBufs& B, const T* r0, const TA0* a0, const SolveScalars*
     const int Nj = B.N >> j;
     const bool fine = j == 0;
     if (fine && tiled) {
-      tiled_post<T, TA0>(rfine, a0, (const T*)B.vt[1], (T*)B.vt[0], B.partial, sc, Nj, S, (double)omega, st);
+      tiled_post<T, TA0>(rfine, a0, (const T*)B.dinv[0], (const T*)B.vt[1], (T*)B.vt[0], B.partial, sc, Nj, S,
+                         (double)omega, st);
       return tiled_blocks_per_sample(Nj, S, (int)sizeof(T));
     }
     if (!fine && tiled && Nj >= kTiledMinN) {
       // the r.z partial sums of a coarse level are overwritten by the fine level's POST
-      tiled_post<T, T>(rin(j), (const T*)B.acoef[j], (const T*)B.vt[j + 1], (T*)B.vt[j], B.partial, sc, Nj, S,
-                       (double)omega, st);
+      tiled_post<T, T>(rin(j), (const T*)B.acoef[j], (const T*)B.dinv[j], (const T*)B.vt[j + 1], (T*)B.vt[j],
+                       B.partial, sc, Nj, S, (double)omega, st);
       continue;
     }
     launch(cls<T>("prolong", fine), nbytes<T, T>(Nj, S, 2, 0) + nbytes<T, T>(Nj / 2, S, 1, 0), k_prolong_add<T>,

@@ -11,7 +11,8 @@
 // global node (x0 - 1 + lx, y0 - 1 + ly); its eight surrounding cells are the
 // staged cells (lx + p, ly + q), p, q in {0, 1}, of two cell planes.
 //
-// Fused passes (FE operator A: see q1_row in internal.cuh; D = (h/3) sum_8 a):
+// Fused passes (FE operator A: see q1_row in internal.cuh; D = (h/3) sum_8 a, whose
+// inverse is precomputed per coefficient hierarchy and staged like a vector):
 //   APPLY : pn = z + beta p (pn = z on the first iteration); q = A pn;
 //           writes p = pn, q; partial p.q
 //   PRE   : x1 = omega D^{-1} r computed on the fly; t = r - A x1
@@ -42,6 +43,7 @@ struct TiledArgs {
   const void* in1;   // APPLY: p (old)                RES64: b (FP64)
   const void* ec;    // POST: coarse correction (grid N/2)
   const void* a;     // cell coefficient
+  const void* dinv;  // PRE/PREU/POST: D^{-1} per node (0 on the boundary)
   void* out0;        // APPLY: q   PRE: t   POST: z   RES64: r
   void* out1;        // APPLY: p (new)   PREU: r (new)
   const void* q;     // PREU: A p of the current iteration
@@ -98,14 +100,12 @@ struct TiledSmem {
   static constexpr size_t raw0 = 0;
   static constexpr size_t raw1 = raw0 + sizeof(T) * RING * G::NPL;
   static constexpr size_t xs = raw1 + (kRaw1 ? sizeof(T) * RING * G::NPL : 0);
-  static constexpr size_t s4 = xs + sizeof(T) * 3 * G::NPL;
-  static constexpr size_t ec = s4 + (kPre ? sizeof(T) * 3 * G::NPL : 0);
+  static constexpr size_t dv = xs + sizeof(T) * 3 * G::NPL;
+  static constexpr size_t ec = dv + (kPre ? sizeof(T) * RING * G::NPL : 0);
   static constexpr size_t cells = ec + (MODE == TM_POST ? sizeof(T) * ERING * G::EPL : 0);
   static constexpr size_t total = cells + sizeof(TA) * RING * G::CPL;
 };
 
-template <typename T> __device__ __forceinline__ T fdiv(T a, T b) { return a / b; }
-template <> __device__ __forceinline__ float fdiv<float>(float a, float b) { return __fdividef(a, b); }
 
 // ---- error-free FP32 arithmetic for the refinement residual (TM_RES64)
 // two_sum: s + e == a + b exactly (Knuth); products use the FMA to split
@@ -142,7 +142,7 @@ __global__ void __launch_bounds__(NT) k_tiled(TiledArgs A) {
   T* raw0 = (T*)(smraw + L::raw0);
   T* raw1 = (T*)(smraw + L::raw1);
   T* xs = (T*)(smraw + L::xs);
-  T* s4 = (T*)(smraw + L::s4);
+  T* dvs = (T*)(smraw + L::dv);
   T* ecs = (T*)(smraw + L::ec);
   TA* cs = (TA*)(smraw + L::cells);
   const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * TX + tx;
@@ -154,13 +154,13 @@ __global__ void __launch_bounds__(NT) k_tiled(TiledArgs A) {
   const int kbeg = 1 + chunk * A.zc;
   const int kend = min(N - 1, kbeg + A.zc - 1);
   const T scale = T(1.0 / (12.0 * N));
-  const T dscale = T(4) * scale;  // D = (h/3) sum_8 a = dscale * sum_8 a
   const T omega = (T)A.omega;
   const T* in0 = (const T*)A.in0 + s * nodes;
   constexpr bool kApply = L::kApply;
   const T* in1 = kApply ? (const T*)A.in1 + s * nodes : (MODE == TM_PREU ? (const T*)A.q + s * nodes : in0);
   const bool stage1 = (kApply && !A.first) || MODE == TM_PREU;  // raw1 holds p_old or q
   const TA* a = (const TA*)A.a + s * cells;
+  const T* dvg = kPre ? (const T*)A.dinv + s * nodes : in0;
   const int nc1 = N / 2 + 1;
   const T* e0 = (MODE == TM_POST) ? (const T*)A.ec + s * (long long)nc1 * nc1 * nc1 : in0;
   const int ex0 = (x0 - 1) / 2, ey0 = (y0 - 1) / 2;  // coarse tile origin
@@ -170,7 +170,7 @@ __global__ void __launch_bounds__(NT) k_tiled(TiledArgs A) {
   if (MODE == TM_APPLYX || MODE == TM_PREU) alpha = (T)A.sc[s].alpha;  // APPLYX: previous iteration's
 
   // ---- per-thread staging entries, fixed for the whole march (only the plane offset moves)
-  int noff[MN], dcb[MN], deb[MN];
+  int noff[MN], deb[MN];
   unsigned char nflag[MN];  // bit0: entry exists, bit1: inside grid, bit2: interior (x,y), bit3/4: gi/gj odd
 #pragma unroll
   for (int j = 0; j < MN; ++j) {
@@ -181,7 +181,6 @@ __global__ void __launch_bounds__(NT) k_tiled(TiledArgs A) {
     const bool inter = has && gi > 0 && gj > 0 && gi < N && gj < N;
     nflag[j] = (has ? 1 : 0) | (in ? 2 : 0) | (inter ? 4 : 0) | ((gi & 1) ? 8 : 0) | ((gj & 1) ? 16 : 0);
     noff[j] = in ? gi + n1 * gj : 0;
-    dcb[j] = lx + 1 + CW * ly;
     deb[j] = ((gi >> 1) - ex0) + EWX * ((gj >> 1) - ey0);
   }
   int coff[MC], cdst[MC];
@@ -220,6 +219,7 @@ __global__ void __launch_bounds__(NT) k_tiled(TiledArgs A) {
       const bool ok = mok && (nflag[j] & 2);
       cp_async<sizeof(T)>(raw0 + slot * NPL + e, in0 + (ok ? mo + noff[j] : 0), ok);
       if (stage1) cp_async<sizeof(T)>(raw1 + slot * NPL + e, in1 + (ok ? mo + noff[j] : 0), ok);
+      if (kPre) cp_async<sizeof(T)>(dvs + slot * NPL + e, dvg + (ok ? mo + noff[j] : 0), ok);
     }
     const bool cmok = m >= 0 && m < N;
     const long long cmo = cmok ? (long long)m * pc : 0;
@@ -270,9 +270,7 @@ __global__ void __launch_bounds__(NT) k_tiled(TiledArgs A) {
           xp2[tid + j * NT] = make_float2(hi, __double2float_rn(xd - (double)hi));
         }
     } else {
-      const T* sprev = s4 + ring3(m - 1) * NPL;
-      T* scur = s4 + ring3(m) * NPL;
-      const TA* cpl = cs + slot * CPL;
+      const T* dvp = dvs + slot * NPL;
       const bool mint = m > 0 && m < N;
       const int dk = m & 1;
       const T* c0p = ecs + ((m >> 1) % ERING) * EPL;
@@ -281,13 +279,10 @@ __global__ void __launch_bounds__(NT) k_tiled(TiledArgs A) {
       for (int j = 0; j < MN; ++j) {
         if (!(nflag[j] & 1)) continue;
         const int e = tid + j * NT;
-        const TA* cb = cpl + dcb[j];
-        const T sum = (smem_coef<T>(cb[0]) + smem_coef<T>(cb[1])) + (smem_coef<T>(cb[CW]) + smem_coef<T>(cb[CW + 1]));
-        scur[e] = sum;
         T v = T(0);
         if (mint && (nflag[j] & 4)) {
           const T rn = (MODE == TM_PREU) ? r0[e] - alpha * raw1[slot * NPL + e] : r0[e];
-          v = fdiv<T>(omega * rn, dscale * (sprev[e] + sum));
+          v = omega * rn * dvp[e];
           if (MODE == TM_POST) {
             const int b = deb[j];
             const bool di = nflag[j] & 8, dj = nflag[j] & 16;
@@ -480,7 +475,8 @@ __global__ void __launch_bounds__(NT) k_tiled(TiledArgs A) {
           out1[o] = rn;
         } else if (MODE == TM_POST) {
           const T rv = rk[NPX * t];
-          const T zv = X[1][1][t + 1] + fdiv<T>(omega * (rv - ax), dscale * sum8);
+          const T dk = dvs[((k + 2 * RING) % RING) * NPL + xb + 1 + NPX * (t + 1)];
+          const T zv = X[1][1][t + 1] + omega * (rv - ax) * dk;
           out0[o] = zv;
           red += rv * zv;
         }
@@ -619,25 +615,27 @@ void tiled_apply_x(const float* z, const float* pold, float* pnew, const float* 
   A.in0 = z; A.in1 = pold; A.a = a; A.out0 = q; A.out1 = pnew; A.x = x; A.partial = partial; A.sc = sc; A.N = N;
   run_tiled<float, float, TM_APPLYX>("apply_f32", vbytes<float, float>(N, S, 6, 1), A, S, st);
 }
-void tiled_pre_update(const float* r, const float* q, const __nv_bfloat16* a, float* t, float* rnew,
+void tiled_pre_update(const float* r, const float* q, const __nv_bfloat16* a, const float* dinv, float* t, float* rnew,
                       const SolveScalars* sc, int N, int S, double omega, cudaStream_t st) {
   TiledArgs A{};
-  A.in0 = r; A.q = q; A.a = a; A.out0 = t; A.out1 = rnew; A.sc = sc; A.N = N; A.omega = omega;
-  run_tiled<float, __nv_bfloat16, TM_PREU>("pre_f32", vbytes<float, __nv_bfloat16>(N, S, 4, 1), A, S, st);
+  A.in0 = r; A.q = q; A.a = a; A.dinv = dinv; A.out0 = t; A.out1 = rnew; A.sc = sc; A.N = N; A.omega = omega;
+  run_tiled<float, __nv_bfloat16, TM_PREU>("pre_f32", vbytes<float, __nv_bfloat16>(N, S, 5, 1), A, S, st);
 }
 
 template <typename T, typename TA>
-void tiled_pre(const T* r, const TA* a, T* t, const SolveScalars* sc, int N, int S, double omega, cudaStream_t st) {
+void tiled_pre(const T* r, const TA* a, const T* dinv, T* t, const SolveScalars* sc, int N, int S, double omega,
+               cudaStream_t st) {
   TiledArgs A{};
-  A.in0 = r; A.a = a; A.out0 = t; A.sc = sc; A.N = N; A.omega = omega;
-  run_tiled<T, TA, TM_PRE>(name("pre", tag<T>()), vbytes<T, TA>(N, S, 2, 1), A, S, st);
+  A.in0 = r; A.a = a; A.dinv = dinv; A.out0 = t; A.sc = sc; A.N = N; A.omega = omega;
+  run_tiled<T, TA, TM_PRE>(name("pre", tag<T>()), vbytes<T, TA>(N, S, 3, 1), A, S, st);
 }
 template <typename T, typename TA>
-void tiled_post(const T* r, const TA* a, const T* ec, T* z, double* partial, const SolveScalars* sc, int N, int S,
-                double omega, cudaStream_t st) {
+void tiled_post(const T* r, const TA* a, const T* dinv, const T* ec, T* z, double* partial, const SolveScalars* sc,
+                int N, int S, double omega, cudaStream_t st) {
   TiledArgs A{};
-  A.in0 = r; A.a = a; A.ec = ec; A.out0 = z; A.partial = partial; A.sc = sc; A.N = N; A.omega = omega;
-  run_tiled<T, TA, TM_POST>(name("post", tag<T>()), vbytes<T, TA>(N, S, 2, 1) + vbytes<T, T>(N / 2, S, 1, 0), A, S,
+  A.in0 = r; A.a = a; A.dinv = dinv; A.ec = ec; A.out0 = z; A.partial = partial; A.sc = sc; A.N = N;
+  A.omega = omega;
+  run_tiled<T, TA, TM_POST>(name("post", tag<T>()), vbytes<T, TA>(N, S, 3, 1) + vbytes<T, T>(N / 2, S, 1, 0), A, S,
                             st);
 }
 void tiled_res64(const double* b, long long bstride, const double* x, const float* a, double* r, double* partial,
@@ -660,17 +658,17 @@ template void tiled_apply<float, float>(const float*, const float*, float*, cons
                                         const SolveScalars*, int, int, int, cudaStream_t);
 template void tiled_apply<double, double>(const double*, const double*, double*, const double*, double*, double*,
                                           const SolveScalars*, int, int, int, cudaStream_t);
-template void tiled_pre<float, __nv_bfloat16>(const float*, const __nv_bfloat16*, float*, const SolveScalars*, int, int,
-                                              double, cudaStream_t);
-template void tiled_pre<float, float>(const float*, const float*, float*, const SolveScalars*, int, int, double,
-                                      cudaStream_t);
-template void tiled_post<float, float>(const float*, const float*, const float*, float*, double*, const SolveScalars*,
-                                       int, int, double, cudaStream_t);
-template void tiled_pre<double, double>(const double*, const double*, double*, const SolveScalars*, int, int, double,
-                                        cudaStream_t);
-template void tiled_post<float, __nv_bfloat16>(const float*, const __nv_bfloat16*, const float*, float*, double*,
-                                               const SolveScalars*, int, int, double, cudaStream_t);
-template void tiled_post<double, double>(const double*, const double*, const double*, double*, double*,
+template void tiled_pre<float, __nv_bfloat16>(const float*, const __nv_bfloat16*, const float*, float*,
+                                              const SolveScalars*, int, int, double, cudaStream_t);
+template void tiled_pre<float, float>(const float*, const float*, const float*, float*, const SolveScalars*, int, int,
+                                      double, cudaStream_t);
+template void tiled_post<float, float>(const float*, const float*, const float*, const float*, float*, double*,
+                                       const SolveScalars*, int, int, double, cudaStream_t);
+template void tiled_pre<double, double>(const double*, const double*, const double*, double*, const SolveScalars*, int,
+                                        int, double, cudaStream_t);
+template void tiled_post<float, __nv_bfloat16>(const float*, const __nv_bfloat16*, const float*, const float*, float*,
+                                               double*, const SolveScalars*, int, int, double, cudaStream_t);
+template void tiled_post<double, double>(const double*, const double*, const double*, const double*, double*, double*,
                                          const SolveScalars*, int, int, double, cudaStream_t);
 
 }  // namespace mlsgd
