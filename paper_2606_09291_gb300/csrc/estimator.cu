@@ -233,10 +233,40 @@ __device__ __forceinline__ double eval_at_ctrl(const double* __restrict__ q, int
   return (c00 * (1 - ty) + c10 * ty) * (1 - tz) + (c01 * (1 - ty) + c11 * ty) * tz;
 }
 
-// One thread per control cell: B*q as the cell average for both grids
-// (eval_at_ctrl), dX~_s = w_f[s] B*q_f[s] - w_c[s] B*q_c[s], Welford over
-// the batch, Chan merge with the rescaled old mean; block partials of
-// h_c^3 (M2_batch + delta^2 n_old S / n).
+// The eight trilinear weights of a control-cell centre inside a level cell
+// (level no finer than the control grid), set up once per control cell.
+struct CellInterp {
+  long long base;  // node (ex, ey, ez) of the level cell holding the control cell
+  long long sy, sz;
+  double w[8];     // weight of node (ex + a, ey + b, ez + c) at index a + 2b + 4c
+  __device__ void setup(int N, int Nc, int cx, int cy, int cz) {
+    const int n1 = N + 1, r = Nc / N;
+    const double tx = ((cx % r) + 0.5) / r, ty = ((cy % r) + 0.5) / r, tz = ((cz % r) + 0.5) / r;
+    base = (cx / r) + (long long)n1 * ((cy / r) + (long long)n1 * (cz / r));
+    sy = n1;
+    sz = (long long)n1 * n1;
+#pragma unroll
+    for (int e = 0; e < 8; ++e)
+      w[e] = ((e & 1) ? tx : 1.0 - tx) * ((e & 2) ? ty : 1.0 - ty) * ((e & 4) ? tz : 1.0 - tz);
+  }
+  __device__ __forceinline__ double eval(const double* __restrict__ q) const {
+    const double* b = q + base;
+    double v = w[0] * b[0];
+    v = fma(w[1], b[1], v);
+    v = fma(w[2], b[sy], v);
+    v = fma(w[3], b[sy + 1], v);
+    v = fma(w[4], b[sz], v);
+    v = fma(w[5], b[sz + 1], v);
+    v = fma(w[6], b[sz + sy], v);
+    return fma(w[7], b[sz + sy + 1], v);
+  }
+};
+
+// One thread per control cell: B*q as the cell average for both grids,
+// dX~_s = w_f[s] B*q_f[s] - w_c[s] B*q_c[s]; batch mean and M2 by the
+// shifted-data sums (deviations from the first sample: no division per
+// sample, stable when the first sample is typical), then the Chan merge with
+// the rescaled old mean; block partials of h_c^3 (M2_batch + delta^2 n_old S / n).
 __global__ void k_level_field(const double* __restrict__ qf, int Nf, const double* __restrict__ qc, int Ncs, int S,
                               int Nc, const double* __restrict__ work, double* __restrict__ field,
                               double* __restrict__ partial) {
@@ -248,14 +278,26 @@ __global__ void k_level_field(const double* __restrict__ qf, int Nf, const doubl
     const long long nf = nodes_of(Nf), ncn = qc ? nodes_of(Ncs) : 0;
     const double* wf = work + 4;
     const double* wc = work + 4 + S;
-    double mean = 0.0, m2 = 0.0;
+    // level grids no finer than the control grid: weights hoisted out of the sample loop
+    const bool fast_f = Nf <= Nc, fast_c = !qc || Ncs <= Nc;
+    CellInterp If{}, Ic{};
+    if (fast_f) If.setup(Nf, Nc, cx, cy, cz);
+    if (qc && fast_c) Ic.setup(Ncs, Nc, cx, cy, cz);
+    double ref = 0.0, sd = 0.0, sd2 = 0.0;
     for (int s = 0; s < S; ++s) {
-      double v = wf[s] * eval_at_ctrl(qf + s * nf, Nf, Nc, cx, cy, cz);
-      if (qc) v -= wc[s] * eval_at_ctrl(qc + s * ncn, Ncs, Nc, cx, cy, cz);
-      const double d = v - mean;
-      mean += d / (s + 1);
-      m2 += d * (v - mean);
+      const double* qfs = qf + s * nf;
+      double v = wf[s] * (fast_f ? If.eval(qfs) : eval_at_ctrl(qfs, Nf, Nc, cx, cy, cz));
+      if (qc) {
+        const double* qcs = qc + s * ncn;
+        v -= wc[s] * (fast_c ? Ic.eval(qcs) : eval_at_ctrl(qcs, Ncs, Nc, cx, cy, cz));
+      }
+      if (s == 0) ref = v;
+      const double d = v - ref;
+      sd += d;
+      sd2 = fma(d, d, sd2);
     }
+    const double mean = ref + sd / S;
+    const double m2 = fmax(sd2 - sd * (sd / S), 0.0);
     const double n_old = work[2], scale = work[1];
     const double n = n_old + S;
     const double mo = (n_old > 0.0) ? field[c] * scale : 0.0;
