@@ -62,6 +62,7 @@ struct SolverBufs {
   void* vt[8];               // V-cycle temporary / output per level
   void* vr[8];               // restricted residual (j >= 1)
   void* dinv[8];             // D^{-1} of levels run with the tiled passes (0 at boundary nodes), else null
+  float2* bdf;               // mixed tiled solves: b as FP32 (hi, lo) pairs [S][nodes] (or [nodes] if shared)
   // Krylov vectors
   void* x;                   // solution / correction
   void* r;                   // residual
@@ -110,10 +111,12 @@ template <typename T, typename TA>
 void tiled_post(const T* r, const TA* a, const T* dinv, const T* ec, T* z, double* partial, const SolveScalars* sc,
                 int N, int S, double omega, cudaStream_t st);
 void tiled_apply_x(const float* z, const float* pold, float* pnew, const float* a, float* q, float* x, double* partial,
-                   const SolveScalars* sc, int N, int S, cudaStream_t st);
+                   const SolveScalars* sc, int N, int S, cudaStream_t st, bool x_first);
 void tiled_pre_update(const float* r, const float* q, const __nv_bfloat16* a, const float* dinv, float* t, float* rnew,
                       const SolveScalars* sc, int N, int S, double omega, cudaStream_t st);
-void tiled_res64(const double* b, long long bstride, const double* x, const float* a, double* r, double* partial,
+// r32 = (float)(b - A x) to FP64 accuracy with x, b as FP32 (hi, lo) pairs and error-free
+// FP32 products and sums; partial r.r
+void tiled_res64(const float2* b, long long bstride, const float2* x, const float* a, float* r32, double* partial,
                  const SolveScalars* sc, int N, int S, cudaStream_t st);
 // Phi and the adjoint right-hand side; returns the partial-sum blocks per sample
 int tiled_phi(const double* y, int N, int S, const double* gtab, const double* mgtab, double* badj, double* partial,

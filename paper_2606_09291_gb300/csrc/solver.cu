@@ -344,6 +344,66 @@ __global__ void k_demote(const double* __restrict__ r64, float* __restrict__ r32
   }
 }
 
+// r32 = (float) b (shared or per sample), bdf = b as an FP32 (hi, lo) pair (written
+// once when b is shared), partial = b.b  (not masked).  Each thread takes kInitPer
+// nodes so that the FP64 block reduction is amortised.
+constexpr int kInitPer = 8;
+static inline int init_blocks(int N) { return (int)((nodes_of(N) + kBlock * kInitPer - 1) / (kBlock * kInitPer)); }
+__global__ void k_init32(const double* __restrict__ b, long long bstride, float* __restrict__ r32,
+                         float2* __restrict__ bdf, double* __restrict__ partial, long long nodes) {
+  const int s = blockIdx.y;
+  const long long n0 = (long long)blockIdx.x * blockDim.x * kInitPer + threadIdx.x;
+  const bool write_pair = bstride != 0 || s == 0;
+  double contrib = 0.0;
+#pragma unroll
+  for (int i = 0; i < kInitPer; ++i) {
+    const long long n = n0 + (long long)i * blockDim.x;
+    if (n < nodes) {
+      const double bv = b[s * bstride + n];
+      const float hi = (float)bv;
+      r32[s * nodes + n] = hi;
+      if (write_pair) bdf[s * bstride + n] = make_float2(hi, (float)(bv - (double)hi));
+      contrib = fma(bv, bv, contrib);
+    }
+  }
+  const double bs = block_sum(contrib);
+  if (threadIdx.x == 0) partial[(long long)s * gridDim.x + blockIdx.x] = bs;
+}
+
+// the inner solve's last update fused with the refinement step: the solution is
+// kept as an FP32 (hi, lo) pair x, x (+)= d + alpha p (pair addition: two-sum and
+// renormalisation, about 48 significant bits), d taken as 0 when never written
+__global__ void k_finish_step(float2* __restrict__ x, const float* __restrict__ d, const float* __restrict__ p,
+                              const SolveScalars* __restrict__ sci, const SolveScalars* __restrict__ sco,
+                              long long nodes, int assign, int d_zero) {
+  SAMPLE_GUARD(sco);
+  const int n = blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= nodes) return;
+  const long long o = s * nodes + n;
+  const float dv = d_zero ? 0.0f : d[o];
+  const float inc = dv + (float)sci[s].alpha * p[o];
+  if (assign) {
+    x[o] = make_float2(inc, 0.0f);
+    return;
+  }
+  const float2 xv = x[o];
+  const float sh = xv.x + inc;  // two-sum of hi and inc
+  const float bb = sh - xv.x;
+  const float se = (xv.x - (sh - bb)) + (inc - bb);
+  const float lo = xv.y + se;
+  const float h = sh + lo;      // renormalise
+  x[o] = make_float2(h, lo - (h - sh));
+}
+
+// x64 = hi + lo of the FP32 pair solution (every sample, after the refinement)
+__global__ void k_store_pair(double* __restrict__ x, const float2* __restrict__ xp, long long nodes) {
+  const int s = blockIdx.y;
+  const int n = blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= nodes) return;
+  const float2 v = xp[s * nodes + n];
+  x[s * nodes + n] = (double)v.x + (double)v.y;
+}
+
 // x64 += d
 __global__ void k_accumulate(double* __restrict__ x, const float* __restrict__ d, const SolveScalars* __restrict__ sc,
                              long long nodes) {
@@ -376,6 +436,7 @@ size_t solver_bytes(int N, int S, int elem) {
   }
   for (int j = 0; j <= J; ++j)
     if (tiled_level(N, j)) b += align_up((size_t)S * nodes_of(N >> j) * elem);
+  if (elem == 4 && tiled_level(N, 0)) b += align_up((size_t)S * nodes_of(N) * sizeof(float2));
   b += align_up((size_t)S * node_blocks(N) * sizeof(double));
   b += 2 * align_up((size_t)S * sizeof(SolveScalars));
   b += align_up(sizeof(int));
@@ -399,6 +460,7 @@ void carve_solver(SolverBufs& B, int N, int S, int elem, char*& ptr) {
   for (int j = 0; j < 8; ++j) B.dinv[j] = nullptr;
   for (int j = 0; j <= B.J; ++j)
     if (tiled_level(N, j)) B.dinv[j] = take((size_t)S * nodes_of(N >> j) * elem);
+  B.bdf = (elem == 4 && tiled_level(N, 0)) ? (float2*)take((size_t)S * nodes_of(N) * sizeof(float2)) : nullptr;
   B.partial = (double*)take((size_t)S * node_blocks(N) * sizeof(double));
   B.sc = (SolveScalars*)take((size_t)2 * S * sizeof(SolveScalars));
   B.count = (int*)take(sizeof(int));
@@ -421,7 +483,11 @@ static const char* cls(const char* base, bool fine) {
 }
 
 // D^{-1} = 1 / ((h/3) sum_8 a) at interior nodes, 0 on the boundary (computed once per
-// coefficient hierarchy; the tiled smoothing passes stage it like a vector)
+// coefficient hierarchy; the tiled smoothing passes stage it like a vector).  FP32:
+// the fast approximate reciprocal (the diagonal only scales the smoother; pre- and
+// post-smoothing read the same values, so the V-cycle stays symmetric).
+__device__ __forceinline__ double recip(double x) { return 1.0 / x; }
+__device__ __forceinline__ float recip(float x) { return __fdividef(1.0f, x); }
 template <typename T, typename TA>
 __global__ void k_dinv(const TA* __restrict__ a, T* __restrict__ dinv, int N) {
   const int s = blockIdx.y;
@@ -435,7 +501,7 @@ __global__ void k_dinv(const TA* __restrict__ a, T* __restrict__ dinv, int N) {
   if (interior(i, j, k, N)) {
     Cells8<T, TA> C;
     C.load(a + s * (long long)N * N * N, i, j, k, N);
-    v = T(1) / (T(1.0 / (3.0 * N)) * C.sum);
+    v = recip(T(1.0 / (3.0 * N)) * C.sum);
   }
   dinv[s * nodes + n] = v;
 }
@@ -634,8 +700,12 @@ static cudaError_t pcg_loop(SolverBufs& B, const TAop* aop, const TA0* a0, T* x,
 // updates fused into the stencil passes: x += alpha_prev p_old happens inside the
 // next A p pass, r -= alpha q inside the next fine pre-smoothing pass; r and p are
 // double-buffered (neighbouring tiles read the old values in their halos).
+// x need not be initialised: the first iteration that updates it assigns.  Instead
+// of the last x += alpha p, the final update is fused with the refinement step into
+// x_out (+)= x + alpha p (k_finish_step; assign on the first refinement step).
 static cudaError_t pcg_inner_fused(SolverBufs& B, const float* a32, const __nv_bfloat16* abf, float* x, float* r,
-                                   SolveScalars* sc, const PcgParams& prm, int iters, cudaStream_t st) {
+                                   SolveScalars* sc, const PcgParams& prm, int iters, cudaStream_t st,
+                                   float2* x_out, const SolveScalars* sco, bool assign_out) {
   const int S = B.S, N = B.N;
   const long long nodes = nodes_of(N);
   const float omega = (float)prm.omega;
@@ -653,12 +723,13 @@ static cudaError_t pcg_inner_fused(SolverBufs& B, const float* a32, const __nv_b
     if (it == 0)
       tiled_apply<float, float>(z, pold, pnew, a32, q, B.partial, sc, N, S, 1, st);
     else
-      tiled_apply_x(z, pold, pnew, a32, q, x, B.partial, sc, N, S, st);
+      tiled_apply_x(z, pold, pnew, a32, q, x, B.partial, sc, N, S, st, it == 1);
     pc ^= 1;
     scalar(B, sc, SM_ALPHA, 0, 0, st, napply);
     if (it == iters - 1) {
-      launch("axpy_f32", (double)S * nodes * 12, k_axpy<float>, grid_nodes(N, S), kBlock, 0, st, x, (const float*)pnew,
-             (const SolveScalars*)sc, nodes);
+      launch("finish_step", (double)S * nodes * ((iters > 1 ? 4 : 0) + 4 + (assign_out ? 8 : 16)), k_finish_step,
+             grid_nodes(N, S), kBlock, 0, st, x_out, (const float*)x, (const float*)pnew, (const SolveScalars*)sc,
+             sco, nodes, assign_out ? 1 : 0, iters > 1 ? 0 : 1);
       break;
     }
     nrz = vcycle<float, __nv_bfloat16>(B, rb[rc], abf, sc, omega, st, q, rb[rc ^ 1]);
@@ -670,20 +741,57 @@ static cudaError_t pcg_inner_fused(SolverBufs& B, const float* a32, const __nv_b
 
 // Buffers the tiled passes write only on interior nodes must hold zero
 // boundary nodes: clear them once per solve.
+// zero the boundary nodes (2 (N+1)^2 + 4 N (N-1) per sample) of up to 6 vectors
+struct ZeroList { void* v[6]; };
+template <typename T>
+__global__ void k_zero_boundary(ZeroList zl, int nv, int N) {
+  const int s = blockIdx.y;
+  const int n1 = N + 1;
+  const long long plane = (long long)n1 * n1;
+  const long long nb = 2 * plane + 4LL * N * (N - 1);
+  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= nb) return;
+  long long o;
+  if (idx < 2 * plane) {
+    o = (idx < plane ? 0 : (long long)N * plane) + idx % plane;  // planes z = 0 and z = N
+  } else {
+    const long long r = idx - 2 * plane;
+    const int k = 1 + (int)(r / (4 * N));
+    const int p = (int)(r % (4 * N));
+    int i, j;
+    if (p < n1) { i = p; j = 0; }                       // row y = 0
+    else if (p < 2 * n1) { i = p - n1; j = N; }         // row y = N
+    else if (p < 2 * n1 + N - 1) { i = 0; j = p - 2 * n1 + 1; }  // column x = 0
+    else { i = N; j = p - (2 * n1 + N - 1) + 1; }       // column x = N
+    o = i + (long long)n1 * j + plane * k;
+  }
+  const long long so = (long long)s * plane * n1 + o;
+  for (int t = 0; t < nv; ++t) ((T*)zl.v[t])[so] = T(0);
+}
+
+template <typename T>
+static void zero_boundary(void* const* bufs, int nv, int N, int S, cudaStream_t st) {
+  ZeroList zl{};
+  for (int t = 0; t < nv; ++t) zl.v[t] = bufs[t];
+  const long long nb = 2LL * (N + 1) * (N + 1) + 4LL * N * (N - 1);
+  launch("zero_boundary", (double)S * nb * nv * sizeof(T), k_zero_boundary<T>,
+         dim3((unsigned)((nb + kBlock - 1) / kBlock), (unsigned)S), kBlock, 0, st, zl, nv, N);
+}
+
+// The tiled passes write interior nodes only: the vectors they produce (and the
+// inner solve's correction, which is first assigned by a tiled pass) get zero
+// boundary nodes once per solve.
 static cudaError_t clear_tiled(SolverBufs& B, int elem, cudaStream_t st) {
   if (!(B.N >= kTiledMinN && B.J >= 1)) return cudaSuccess;
-  const size_t v = (size_t)B.S * nodes_of(B.N) * elem;
-  void* bufs[5] = {B.p, B.vx[0], B.q, B.vt[0], B.r2};
-  for (void* b : bufs) {
-    cudaError_t e = cudaMemsetAsync(b, 0, v, st);
-    if (e != cudaSuccess) return e;
-  }
-  for (int j = 1; j < B.J; ++j)  // coarse levels run by the tiled passes write interior nodes only
+  void* bufs[6] = {B.p, B.vx[0], B.q, B.vt[0], B.r2, B.x};
+  if (elem == 4) zero_boundary<float>(bufs, 6, B.N, B.S, st);
+  else zero_boundary<double>(bufs, 5, B.N, B.S, st);
+  for (int j = 1; j < B.J; ++j)  // coarse levels run by the tiled passes
     if ((B.N >> j) >= kTiledMinN) {
-      cudaError_t e = cudaMemsetAsync(B.vt[j], 0, (size_t)B.S * nodes_of(B.N >> j) * elem, st);
-      if (e != cudaSuccess) return e;
+      if (elem == 4) zero_boundary<float>(&B.vt[j], 1, B.N >> j, B.S, st);
+      else zero_boundary<double>(&B.vt[j], 1, B.N >> j, B.S, st);
     }
-  return cudaSuccess;
+  return cudaGetLastError();
 }
 
 cudaError_t pcg_fp64(SolverBufs& B, const double* a64, const double* b, long long bstride, double* x_out,
@@ -715,14 +823,25 @@ cudaError_t ir_mixed(SolverBufs& B, const float* a32, const __nv_bfloat16* abf, 
   const double bb = (double)(bstride ? S : 1) * nodes * 8;
   cudaError_t e = clear_tiled(B, 4, st);
   if (e != cudaSuccess) return e;
-  launch("init_f64", bb + nbytes<double, double>(N, S, 2, 0), k_init<double>, g, kBlock, 0, st, b, bstride, r64,
-         x_out, B.partial, nodes);
-  scalar(B, sco, SM_INIT, 0, 0, st, nb);
+  // tiled grids: the FP32 residual is written directly (first from b, then by the
+  // refinement residual pass), b and the solution are kept as FP32 (hi, lo) pairs
+  // (the solution in r64's storage, assigned by the first step and stored to x_out
+  // in FP64 at the end), so the refinement loop executes no FP64 arithmetic.
+  float2* xdf = (float2*)r64;
+  if (tiled) {
+    launch("init_f32", bb + nbytes<float, float>(N, S, 1, 0) + (double)(bstride ? S : 1) * nodes * 8, k_init32,
+           dim3((unsigned)init_blocks(N), (unsigned)S), kBlock, 0, st, b, bstride, r32, B.bdf, B.partial, nodes);
+    scalar(B, sco, SM_INIT, 0, 0, st, init_blocks(N));
+  } else {
+    launch("init_f64", bb + nbytes<double, double>(N, S, 2, 0), k_init<double>, g, kBlock, 0, st, b, bstride, r64,
+           x_out, B.partial, nodes);
+    scalar(B, sco, SM_INIT, 0, 0, st, nb);
+  }
   for (int step = 0;; ++step) {
     if (step > 0) {
       const int cap = fixed_steps > 0 ? fixed_steps : prm.max_iter;
       if (tiled) {
-        tiled_res64(b, bstride, x_out, a32, r64, B.partial, sco, N, S, st);
+        tiled_res64(B.bdf, bstride, xdf, a32, r32, B.partial, sco, N, S, st);
         scalar(B, sco, SM_OUTER_CONV, tol2, cap, st, tiled_blocks_per_sample(N, S, 8));
       } else {
         launch("resid64", bb + nbytes<double, float>(N, S, 2, 1), k_residual64<float>, g, kBlock, 0, st, b, bstride,
@@ -738,16 +857,23 @@ cudaError_t ir_mixed(SolverBufs& B, const float* a32, const __nv_bfloat16* abf, 
       if (e != cudaSuccess) return e;
       if (n == 0) break;
     }
-    launch("demote", (double)S * nodes * 16, k_demote, g, kBlock, 0, st, (const double*)r64, r32, d,
-           (const SolveScalars*)sco, nodes);
+    if (!tiled)
+      launch("demote", (double)S * nodes * 16, k_demote, g, kBlock, 0, st, (const double*)r64, r32, d,
+             (const SolveScalars*)sco, nodes);
     scalar(B, sci, SM_INNER_BEGIN, 0, 0, st, nb, 0, sco);
-    e = tiled ? pcg_inner_fused(B, a32, abf, d, r32, sci, prm, inner_iters, st)
-              : pcg_loop<float, float, __nv_bfloat16>(B, a32, abf, d, r32, sci, prm, inner_iters, st);
-    if (e != cudaSuccess) return e;
-    launch("accum", (double)S * nodes * 20, k_accumulate, g, kBlock, 0, st, x_out, (const float*)d,
-           (const SolveScalars*)sco, nodes);
+    if (tiled) {
+      e = pcg_inner_fused(B, a32, abf, d, r32, sci, prm, inner_iters, st, xdf, sco, step == 0);
+      if (e != cudaSuccess) return e;
+    } else {
+      e = pcg_loop<float, float, __nv_bfloat16>(B, a32, abf, d, r32, sci, prm, inner_iters, st);
+      if (e != cudaSuccess) return e;
+      launch("accum", (double)S * nodes * 20, k_accumulate, g, kBlock, 0, st, x_out, (const float*)d,
+             (const SolveScalars*)sco, nodes);
+    }
     scalar(B, sco, SM_OUTER_STEP, 0, 0, st, nb, inner_iters);
   }
+  if (tiled)
+    launch("store_x", (double)S * nodes * 16, k_store_pair, g, kBlock, 0, st, x_out, (const float2*)xdf, nodes);
   return cudaGetLastError();
 }
 

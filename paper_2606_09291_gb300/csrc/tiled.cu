@@ -18,7 +18,9 @@
 //   PRE   : x1 = omega D^{-1} r computed on the fly; t = r - A x1
 //   POST  : x2 = omega D^{-1} r + P e_c on the fly;
 //           z = x2 + omega D^{-1} (r - A x2); partial r.z
-//   RES64 : r = b - A x in FP64 (x FP64, a FP32), partial r.r
+//   RES64 : r = b - A x to FP64 accuracy in FP32 arithmetic: x and b are FP32 (hi, lo)
+//           pairs (staged as 8-byte words), a is FP32; writes r rounded to FP32 and the
+//           partial r.r
 // Vectors keep zero boundary nodes; only interior nodes are written.
 #include <cstdio>
 
@@ -55,6 +57,7 @@ struct TiledArgs {
   int nzc;           // z chunks per sample
   int zc;            // planes per chunk
   int first;         // APPLY: first iteration (pn = z)
+  int xfirst;        // APPLYX: x not yet written (x = alpha_prev p_old)
   double omega;
 };
 
@@ -102,7 +105,8 @@ struct TiledSmem {
   static constexpr size_t xs = raw1 + (kRaw1 ? sizeof(T) * RING * G::NPL : 0);
   static constexpr size_t dv = xs + sizeof(T) * 3 * G::NPL;
   static constexpr size_t ec = dv + (kPre ? sizeof(T) * RING * G::NPL : 0);
-  static constexpr size_t cells = ec + (MODE == TM_POST ? sizeof(T) * ERING * G::EPL : 0);
+  static constexpr size_t ep = ec + (MODE == TM_POST ? sizeof(T) * ERING * G::EPL : 0);
+  static constexpr size_t cells = ep + (MODE == TM_POST ? sizeof(T) * 2 * G::NPL : 0);
   static constexpr size_t total = cells + sizeof(TA) * RING * G::CPL;
 };
 
@@ -144,6 +148,7 @@ __global__ void __launch_bounds__(NT) k_tiled(TiledArgs A) {
   T* xs = (T*)(smraw + L::xs);
   T* dvs = (T*)(smraw + L::dv);
   T* ecs = (T*)(smraw + L::ec);
+  T* eps = (T*)(smraw + L::ep);  // POST: two coarse planes interpolated in x and y to this tile's nodes
   TA* cs = (TA*)(smraw + L::cells);
   const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * TX + tx;
   const int N = A.N, n1 = N + 1;
@@ -208,8 +213,7 @@ __global__ void __launch_bounds__(NT) k_tiled(TiledArgs A) {
   }
   int coarse_issued = -1000;
 
-  auto issue = [&](int m) {
-    const int slot = (m + 2 * RING) % RING;
+  auto issue = [&](int m, int slot) {
     const bool mok = m >= 0 && m <= N;
     const long long mo = mok ? (long long)m * pn : 0;
 #pragma unroll
@@ -238,18 +242,35 @@ __global__ void __launch_bounds__(NT) k_tiled(TiledArgs A) {
         for (int j = 0; j < ME; ++j) {
           if (!ehas[j]) continue;
           const bool ok = cok2 && eok[j];
-          cp_async<sizeof(T)>(ecs + ((c + 4 * ERING) % ERING) * EPL + tid + j * NT, e0 + (ok ? c * pe + eoff[j] : 0),
-                              ok);
+          cp_async<sizeof(T)>(ecs + (c & (ERING - 1)) * EPL + tid + j * NT, e0 + (ok ? c * pe + eoff[j] : 0), ok);
         }
       }
     }
     cp_async_commit();
   };
 
-  // operand plane m from its staged raw plane (plus 4-cell sums for PRE/POST)
-  auto derive = [&](int m) {
-    const int slot = (m + 2 * RING) % RING;
-    T* xp = xs + ring3(m) * NPL;
+  // POST: eps[c & 1] holds coarse plane c interpolated bilinearly in x and y at this
+  // tile's staged nodes (each thread writes and reads only its own entries, so no
+  // barrier); a fine plane m takes plane m/2 (m even) or the mean of planes (m-1)/2
+  // and (m+1)/2 (m odd), so each coarse plane is interpolated once for two fine planes.
+  int e_have0 = -1000, e_have1 = -1000;  // coarse plane held by eps[0], eps[1]
+  auto interp_xy = [&](int c) {
+    const T* cp = ecs + (c & (ERING - 1)) * EPL;
+    T* ed = eps + (c & 1) * NPL;
+#pragma unroll
+    for (int j = 0; j < MN; ++j) {
+      if (!(nflag[j] & 4)) continue;
+      const int b = deb[j];
+      const bool di = nflag[j] & 8, dj = nflag[j] & 16;
+      const T acc = cp[b] + (di ? cp[b + 1] : T(0)) + (dj ? cp[b + EWX] : T(0)) + ((di && dj) ? cp[b + EWX + 1] : T(0));
+      ed[tid + j * NT] = (di ? T(0.5) : T(1)) * (dj ? T(0.5) : T(1)) * acc;
+    }
+    if (c & 1) e_have1 = c; else e_have0 = c;
+  };
+
+  // operand plane m from its staged raw plane (slot: its raw ring slot, r3: its xs slot)
+  auto derive = [&](int m, int slot, int r3) {
+    T* xp = xs + r3 * NPL;
     const T* r0 = raw0 + slot * NPL;
     if (kApply) {
       const T* r1 = raw1 + slot * NPL;
@@ -260,21 +281,20 @@ __global__ void __launch_bounds__(NT) k_tiled(TiledArgs A) {
         xp[e] = A.first ? r0[e] : r0[e] + beta * r1[e];
       }
     } else if (MODE == TM_RES64) {
-      // x = hi + lo with hi, lo FP32 (one FP64 subtraction per staged value)
-      float2* xp2 = reinterpret_cast<float2*>(xp);
+      // x is already an (hi, lo) pair: copy the 8-byte word
 #pragma unroll
       for (int j = 0; j < MN; ++j)
-        if (nflag[j] & 1) {
-          const double xd = (double)r0[tid + j * NT];
-          const float hi = __double2float_rn(xd);
-          xp2[tid + j * NT] = make_float2(hi, __double2float_rn(xd - (double)hi));
-        }
+        if (nflag[j] & 1) xp[tid + j * NT] = r0[tid + j * NT];
     } else {
       const T* dvp = dvs + slot * NPL;
       const bool mint = m > 0 && m < N;
-      const int dk = m & 1;
-      const T* c0p = ecs + ((m >> 1) % ERING) * EPL;
-      const T* c1p = ecs + (((m >> 1) + dk) % ERING) * EPL;
+      const int dk = m & 1, c0 = m >> 1;
+      if (MODE == TM_POST && mint) {
+        if (((c0 & 1) ? e_have1 : e_have0) != c0) interp_xy(c0);
+        if (dk && (((c0 + 1) & 1) ? e_have1 : e_have0) != c0 + 1) interp_xy(c0 + 1);
+      }
+      const T* e0p = eps + (c0 & 1) * NPL;
+      const T* e1p = eps + ((c0 + 1) & 1) * NPL;
 #pragma unroll
       for (int j = 0; j < MN; ++j) {
         if (!(nflag[j] & 1)) continue;
@@ -283,14 +303,7 @@ __global__ void __launch_bounds__(NT) k_tiled(TiledArgs A) {
         if (mint && (nflag[j] & 4)) {
           const T rn = (MODE == TM_PREU) ? r0[e] - alpha * raw1[slot * NPL + e] : r0[e];
           v = omega * rn * dvp[e];
-          if (MODE == TM_POST) {
-            const int b = deb[j];
-            const bool di = nflag[j] & 8, dj = nflag[j] & 16;
-            T acc = c0p[b] + (di ? c0p[b + 1] : T(0)) + (dj ? c0p[b + EWX] : T(0)) + ((di && dj) ? c0p[b + EWX + 1] : T(0));
-            if (dk) acc += c1p[b] + (di ? c1p[b + 1] : T(0)) + (dj ? c1p[b + EWX] : T(0)) + ((di && dj) ? c1p[b + EWX + 1] : T(0));
-            const T w = (di ? T(0.5) : T(1)) * (dj ? T(0.5) : T(1)) * (dk ? T(0.5) : T(1));
-            v += w * acc;
-          }
+          if (MODE == TM_POST) v += dk ? T(0.5) * (e0p[e] + e1p[e]) : e0p[e];
         }
         xp[e] = v;
       }
@@ -299,11 +312,12 @@ __global__ void __launch_bounds__(NT) k_tiled(TiledArgs A) {
 
   // prologue: derive the planes before kbeg, keep two planes in flight
   const int first_plane = kPre ? kbeg - 2 : kbeg - 1;
-  for (int m = first_plane; m <= kbeg + 2; ++m) issue(m);
+  auto mod5 = [](int m) { return (m + 2 * RING) % RING; };
+  for (int m = first_plane; m <= kbeg + 2; ++m) issue(m, mod5(m));
   cp_async_wait<2>();
   __syncthreads();
   for (int m = first_plane; m <= kbeg; ++m) {
-    derive(m);
+    derive(m, mod5(m), ring3(m));
     __syncthreads();
   }
 
@@ -318,29 +332,44 @@ __global__ void __launch_bounds__(NT) k_tiled(TiledArgs A) {
   T* out1 = (kApply || MODE == TM_PREU) ? (T*)A.out1 + s * nodes + gi + (long long)n1 * gj0 : nullptr;
   T* xio = (MODE == TM_APPLYX) ? (T*)A.x + s * nodes + gi + (long long)n1 * gj0 : nullptr;
   const T* bptr = (MODE == TM_RES64) ? (const T*)A.in1 + s * A.bstride + gi + (long long)n1 * gj0 : nullptr;
+  float* r32o = (MODE == TM_RES64) ? (float*)A.out0 + s * nodes + gi + (long long)n1 * gj0 : nullptr;
+  float redf = 0.f;  // RES64: r.r of this thread in FP32
+  const double scd = 1.0 / (12.0 * N);
+  const float sch = (float)scd, scl = (float)(scd - (double)sch);  // h/12 as an FP32 pair
+  // ring slots of plane k, maintained incrementally: s5 in the RING-plane raw/cell
+  // rings, r3 in the three-plane operand ring
+  int s5 = mod5(kbeg), r3 = ring3(kbeg);
   for (int k = kbeg; k <= kend; ++k) {
+    const int s5p1 = s5 + 1 == RING ? 0 : s5 + 1;
+    const int s5p3 = s5 + 3 >= RING ? s5 + 3 - RING : s5 + 3;
+    const int s5m1 = s5 == 0 ? RING - 1 : s5 - 1;
+    const int r3p1 = r3 == 2 ? 0 : r3 + 1;
+    const int r3m1 = r3 == 0 ? 2 : r3 - 1;
+    const int r3s[3] = {r3m1, r3, r3p1};
+    const int c5s[2] = {s5m1, s5};
     // APPLYX: fetch this plane's x early so the load overlaps the staging below
     T xv[RY];
     if (MODE == TM_APPLYX) {
 #pragma unroll
       for (int t = 0; t < RY; ++t)
-        xv[t] = (colok && gj0 + t < N) ? xio[(long long)n1 * n1 * k + (long long)n1 * t] : T(0);
+        xv[t] = (colok && gj0 + t < N && !A.xfirst) ? xio[(long long)n1 * n1 * k + (long long)n1 * t] : T(0);
     }
-    issue(k + 3);
+    issue(k + 3, s5p3);
     cp_async_wait<2>();
     __syncthreads();
-    derive(k + 1);
+    derive(k + 1, s5p1, r3p1);
     __syncthreads();
     if constexpr (MODE == TM_RES64) {
       if (colok) {
         // b - A x with x = hi + lo (FP32 pairs) and FP32 cells, error-free products and
         // compensated sums: exact pair sums of cells, exact products, one rounding of the
-        // unevaluated sum (S, comp) per term; the result is assembled in FP64.
+        // unevaluated sum (S, comp) per term; the scale h/12 and the subtraction from b are
+        // done in the same pair arithmetic, so no FP64 instruction is executed.
         float2 X[3][3][RY + 2];
         float C[2][2][RY + 1];
 #pragma unroll
         for (int pl = 0; pl < 3; ++pl) {
-          const float2* xp = reinterpret_cast<const float2*>(xs + ring3(k - 1 + pl) * NPL) + xb;
+          const float2* xp = reinterpret_cast<const float2*>(xs + r3s[pl] * NPL) + xb;
 #pragma unroll
           for (int c = 0; c < 3; ++c)
 #pragma unroll
@@ -348,7 +377,7 @@ __global__ void __launch_bounds__(NT) k_tiled(TiledArgs A) {
         }
 #pragma unroll
         for (int r = 0; r < 2; ++r) {
-          const TA* cp = cs + ((k - 1 + r + 2 * RING) % RING) * CPL + cbn;
+          const TA* cp = cs + c5s[r] * CPL + cbn;
 #pragma unroll
           for (int p = 0; p < 2; ++p)
 #pragma unroll
@@ -394,11 +423,16 @@ __global__ void __launch_bounds__(NT) k_tiled(TiledArgs A) {
 #pragma unroll
               for (int p = 0; p < 2; ++p) df_term<true>(S, comp, F2{C[r][p][t + q], 0.f}, X[pl][2 * p][t + 2 * q]);
           }
-          const double ax = ((double)S + (double)comp) * (1.0 / (12.0 * N));
+          // ax = (S + comp) (sch + scl), a pair (p, pe)
+          const F2 axs = two_sum(S, comp);
+          const float p = axs.h * sch;
+          const float pe = __fmaf_rn(axs.h, scl, __fmaf_rn(axs.l, sch, __fmaf_rn(axs.h, sch, -p)));
           const long long o = (long long)n1 * n1 * k + (long long)n1 * t;
-          const double rv = (double)bptr[o] - ax;
-          out0[o] = (T)rv;
-          red += (T)(rv * rv);
+          const float2 bv = reinterpret_cast<const float2*>(bptr)[o];
+          const F2 d = two_sum(bv.x, -p);
+          const float rv = d.h + (d.l + (bv.y - pe));
+          r32o[o] = rv;  // the inner solve's FP32 residual
+          redf = __fmaf_rn(rv, rv, redf);
         }
       }
     } else if (colok) {
@@ -407,7 +441,7 @@ __global__ void __launch_bounds__(NT) k_tiled(TiledArgs A) {
       T C[2][2][RY + 1];
 #pragma unroll
       for (int pl = 0; pl < 3; ++pl) {
-        const T* xp = xs + ring3(k - 1 + pl) * NPL + xb;
+        const T* xp = xs + r3s[pl] * NPL + xb;
 #pragma unroll
         for (int c = 0; c < 3; ++c)
 #pragma unroll
@@ -415,13 +449,13 @@ __global__ void __launch_bounds__(NT) k_tiled(TiledArgs A) {
       }
 #pragma unroll
       for (int r = 0; r < 2; ++r) {
-        const TA* cp = cs + ((k - 1 + r + 2 * RING) % RING) * CPL + cbn;
+        const TA* cp = cs + c5s[r] * CPL + cbn;
 #pragma unroll
         for (int p = 0; p < 2; ++p)
 #pragma unroll
           for (int cr = 0; cr < RY + 1; ++cr) C[r][p][cr] = smem_coef<T>(cp[p + CW * cr]);
       }
-      const T* rk = raw0 + ((k + 2 * RING) % RING) * NPL + xb + 1 + NPX;
+      const T* rk = raw0 + s5 * NPL + xb + 1 + NPX;
 #pragma unroll
       for (int t = 0; t < RY; ++t) {
         if (gj0 + t >= N) break;
@@ -466,16 +500,16 @@ __global__ void __launch_bounds__(NT) k_tiled(TiledArgs A) {
           out0[o] = ax;
           out1[o] = pv;
           red += pv * ax;
-          if (MODE == TM_APPLYX) xio[o] = xv[t] + alpha * raw1[((k + 2 * RING) % RING) * NPL + xb + 1 + NPX * (t + 1)];
+          if (MODE == TM_APPLYX) xio[o] = xv[t] + alpha * raw1[s5 * NPL + xb + 1 + NPX * (t + 1)];  // xv = 0 when A.xfirst
         } else if (MODE == TM_PRE) {
           out0[o] = rk[NPX * t] - ax;
         } else if (MODE == TM_PREU) {
-          const T rn = rk[NPX * t] - alpha * raw1[((k + 2 * RING) % RING) * NPL + xb + 1 + NPX * (t + 1)];
+          const T rn = rk[NPX * t] - alpha * raw1[s5 * NPL + xb + 1 + NPX * (t + 1)];
           out0[o] = rn - ax;
           out1[o] = rn;
         } else if (MODE == TM_POST) {
           const T rv = rk[NPX * t];
-          const T dk = dvs[((k + 2 * RING) % RING) * NPL + xb + 1 + NPX * (t + 1)];
+          const T dk = dvs[s5 * NPL + xb + 1 + NPX * (t + 1)];
           const T zv = X[1][1][t + 1] + omega * (rv - ax) * dk;
           out0[o] = zv;
           red += rv * zv;
@@ -483,8 +517,11 @@ __global__ void __launch_bounds__(NT) k_tiled(TiledArgs A) {
       }
     }
     __syncthreads();
+    s5 = s5p1;
+    r3 = r3p1;
   }
   cp_async_wait<0>();
+  if (MODE == TM_RES64) red = (T)redf;
   if (MODE != TM_PRE && MODE != TM_PREU) {
     const T b = block_sum(red);
     if (tid == 0) {
@@ -610,10 +647,11 @@ void tiled_apply(const T* z, const T* pold, T* pnew, const TA* a, T* q, double* 
 }
 // fused variants of the mixed inner solve (see TM_PREU / TM_APPLYX)
 void tiled_apply_x(const float* z, const float* pold, float* pnew, const float* a, float* q, float* x, double* partial,
-                   const SolveScalars* sc, int N, int S, cudaStream_t st) {
+                   const SolveScalars* sc, int N, int S, cudaStream_t st, bool x_first) {
   TiledArgs A{};
   A.in0 = z; A.in1 = pold; A.a = a; A.out0 = q; A.out1 = pnew; A.x = x; A.partial = partial; A.sc = sc; A.N = N;
-  run_tiled<float, float, TM_APPLYX>("apply_f32", vbytes<float, float>(N, S, 6, 1), A, S, st);
+  A.xfirst = x_first ? 1 : 0;
+  run_tiled<float, float, TM_APPLYX>("apply_f32", vbytes<float, float>(N, S, x_first ? 5 : 6, 1), A, S, st);
 }
 void tiled_pre_update(const float* r, const float* q, const __nv_bfloat16* a, const float* dinv, float* t, float* rnew,
                       const SolveScalars* sc, int N, int S, double omega, cudaStream_t st) {
@@ -638,12 +676,13 @@ void tiled_post(const T* r, const TA* a, const T* dinv, const T* ec, T* z, doubl
   run_tiled<T, TA, TM_POST>(name("post", tag<T>()), vbytes<T, TA>(N, S, 3, 1) + vbytes<T, T>(N / 2, S, 1, 0), A, S,
                             st);
 }
-void tiled_res64(const double* b, long long bstride, const double* x, const float* a, double* r, double* partial,
+void tiled_res64(const float2* b, long long bstride, const float2* x, const float* a, float* r32, double* partial,
                  const SolveScalars* sc, int N, int S, cudaStream_t st) {
   TiledArgs A{};
-  A.in0 = x; A.in1 = b; A.bstride = bstride; A.a = a; A.out0 = r; A.partial = partial; A.sc = sc; A.N = N;
+  A.in0 = x; A.in1 = b; A.bstride = bstride; A.a = a; A.out0 = r32; A.partial = partial; A.sc = sc; A.N = N;
   const double bb = (double)(bstride ? S : 1) * nodes_of(N) * 8;
-  run_tiled<double, float, TM_RES64>("resid64", bb + vbytes<double, float>(N, S, 2, 1), A, S, st);
+  run_tiled<double, float, TM_RES64>("resid64", bb + vbytes<double, float>(N, S, 1, 1) + (double)S * nodes_of(N) * 4, A,
+                                     S, st);
 }
 
 int tiled_phi(const double* y, int N, int S, const double* gtab, const double* mgtab, double* badj, double* partial,
