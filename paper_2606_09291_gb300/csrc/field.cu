@@ -98,6 +98,86 @@ __global__ void k_field(const double* __restrict__ xi, int K, const ModeTable mt
   }
 }
 
+// FP32-coefficient synthesis (the mixed path needs only a = exp(log a) rounded to
+// FP32 and BF16): stage 1 (T2) as in k_field in FP64, stored as FP32 (hi, lo) pairs;
+// stage 2 contracts over i in pair arithmetic (exact products by FMA, two-sum
+// accumulation: about 44 significant bits, far below the FP32 rounding of a), four
+// consecutive cells in x per thread; exp by a Cody-Waite reduction against ln 2 split
+// into a 16-bit head (exact multiples for |k| < 256) and its remainder, then expf.
+// Dynamic shared memory: c[K rounded up to even], phi[n1d][N] (doubles), then T2
+// hi/lo [n1x][N] and phi hi/lo [n1x][N] (floats; 16-byte aligned for the float4
+// reads since N % 4 == 0 is required).
+constexpr float kLn2Hi = 0.693145751953125f;        // ln 2 truncated to 16 bits
+constexpr float kLn2Lo = 1.4286068202862268e-06f;   // ln 2 - kLn2Hi
+__global__ void k_field_df(const double* __restrict__ xi, int K, const ModeTable mt, const double* __restrict__ phi,
+                           int N, float* __restrict__ a32, __nv_bfloat16* __restrict__ abf) {
+  extern __shared__ __align__(16) unsigned char smf[];
+  double* c = reinterpret_cast<double*>(smf);
+  double* ph = c + ((K + 1) & ~1);
+  float* T2h = (float*)(ph + mt.n1d * N);
+  float* T2l = T2h + mt.n1x * N;
+  float* Ph = T2l + mt.n1x * N;
+  float* Pl = Ph + mt.n1x * N;
+  const int z = blockIdx.x, s = blockIdx.y;
+  for (int k = threadIdx.x; k < K; k += blockDim.x) c[k] = mt.scale[k] * xi[(long long)s * K + k];
+  for (int e = threadIdx.x; e < mt.n1d * N; e += blockDim.x) {
+    const double v = phi[e];
+    ph[e] = v;
+    if (e < mt.n1x * N) {
+      const float h = (float)v;
+      Ph[e] = h;
+      Pl[e] = (float)(v - (double)h);
+    }
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < mt.n1x * N; e += blockDim.x) {
+    const int i = e / N, y = e % N;
+    double acc = 0.0;
+    for (int t = mt.offs[i]; t < mt.offs[i + 1]; ++t) {
+      const int k = mt.order[t];
+      acc += c[k] * ph[mt.iy[k] * N + y] * ph[mt.iz[k] * N + z];
+    }
+    const float h = (float)acc;
+    T2h[e] = h;
+    T2l[e] = (float)(acc - (double)h);
+  }
+  __syncthreads();
+  const long long base = (long long)s * N * N * N + (long long)z * N * N;
+  const int nq = N / 4;
+  for (int e = threadIdx.x; e < N * nq; e += blockDim.x) {
+    const int x0 = 4 * (e % nq), y = e / nq;
+    float S[4] = {0.f, 0.f, 0.f, 0.f}, C[4] = {0.f, 0.f, 0.f, 0.f};
+    for (int i = 0; i < mt.n1x; ++i) {
+      const float th = T2h[i * N + y], tl = T2l[i * N + y];
+      const float4 phv = *reinterpret_cast<const float4*>(Ph + i * N + x0);
+      const float4 plv = *reinterpret_cast<const float4*>(Pl + i * N + x0);
+      const float pv[4] = {phv.x, phv.y, phv.z, phv.w}, lv[4] = {plv.x, plv.y, plv.z, plv.w};
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const float p = th * pv[q];
+        const float pe = __fmaf_rn(th, lv[q], __fmaf_rn(tl, pv[q], __fmaf_rn(th, pv[q], -p)));
+        const float sum = S[q] + p;  // two-sum of S and p
+        const float bb = sum - S[q];
+        C[q] += ((S[q] - (sum - bb)) + (p - bb)) + pe;
+        S[q] = sum;
+      }
+    }
+    float av[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const float kf = rintf(S[q] * 1.44269504f);
+      const float r = ((S[q] - kf * kLn2Hi) - kf * kLn2Lo) + C[q];
+      av[q] = ldexpf(expf(r), (int)kf);
+    }
+    const long long o = base + (long long)y * N + x0;
+    if (a32) *reinterpret_cast<float4*>(a32 + o) = make_float4(av[0], av[1], av[2], av[3]);
+    if (abf) {
+#pragma unroll
+      for (int q = 0; q < 4; ++q) abf[o + q] = __float2bfloat16_rn(av[q]);
+    }
+  }
+}
+
 size_t field_smem_bytes(const ModeTable& mt, int K, int N) {
   return sizeof(double) * ((size_t)K + (size_t)mt.n1d * N + (size_t)mt.n1x * N);
 }
@@ -105,6 +185,21 @@ size_t field_smem_bytes(const ModeTable& mt, int K, int N) {
 cudaError_t launch_field(const double* xi, int K, const ModeTable& mt, const double* phi, int N, int S,
                          const FieldOut& out, cudaStream_t st) {
   if (S == 0) return cudaSuccess;
+  if (!out.log_a && !out.a64 && (out.a32 || out.abf) && N % 4 == 0) {
+    const size_t smem =
+        sizeof(double) * ((size_t)((K + 1) & ~1) + (size_t)mt.n1d * N) + sizeof(float) * 4 * (size_t)mt.n1x * N;
+    static size_t smem_df = 48 * 1024;
+    if (smem > smem_df) {
+      cudaError_t e = cudaFuncSetAttribute(k_field_df, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e != cudaSuccess) return e;
+      smem_df = smem;
+    }
+    const double cells = (double)S * N * N * N;
+    launch_flops("field", (double)S * K * 8 + cells * ((out.a32 ? 4 : 0) + (out.abf ? 2 : 0)),
+                 2.0 * cells * mt.n1x + 2.0 * (double)S * K * N * N, k_field_df, dim3(N, S), kBlock, smem, st, xi, K,
+                 mt, phi, N, out.a32, out.abf);
+    return cudaGetLastError();
+  }
   const size_t smem = field_smem_bytes(mt, K, N);
   static size_t smem_set = 48 * 1024;  // raised once per size (not on every enqueue: capture-friendly)
   if (smem > smem_set) {
