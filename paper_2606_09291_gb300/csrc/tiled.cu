@@ -211,7 +211,17 @@ __global__ void __launch_bounds__(NT) k_tiled(TiledArgs A) {
     eok[j] = ehas[j] && ci < nc1 && cj < nc1;
     eoff[j] = eok[j] ? ci + nc1 * cj : 0;
   }
-  int coarse_issued = -1000;
+  // POST: coarse plane c is staged once, by issue(2c - 1) (the first fine plane that
+  // needs it is 2c - 1), plus the first derived plane's own coarse plane in the prologue
+  auto stage_coarse = [&](int c) {
+    const bool cok2 = c >= 0 && c < nc1;
+#pragma unroll
+    for (int j = 0; j < ME; ++j) {
+      if (!ehas[j]) continue;
+      const bool ok = cok2 && eok[j];
+      cp_async<sizeof(T)>(ecs + (c & (ERING - 1)) * EPL + tid + j * NT, e0 + (ok ? c * pe + eoff[j] : 0), ok);
+    }
+  };
 
   auto issue = [&](int m, int slot) {
     const bool mok = m >= 0 && m <= N;
@@ -233,19 +243,7 @@ __global__ void __launch_bounds__(NT) k_tiled(TiledArgs A) {
       const bool ok = cmok && cok[j];
       cp_async<kPairs ? 4 : sizeof(TA)>(cs + slot * CPL + cdst[j], a + (ok ? cmo + coff[j] : 0), ok);
     }
-    if (MODE == TM_POST) {
-      for (int c = (m >= 0 ? m / 2 : -1); c <= (m + 1) / 2; ++c) {
-        if (c <= coarse_issued) continue;
-        coarse_issued = c;
-        const bool cok2 = c >= 0 && c < nc1;
-#pragma unroll
-        for (int j = 0; j < ME; ++j) {
-          if (!ehas[j]) continue;
-          const bool ok = cok2 && eok[j];
-          cp_async<sizeof(T)>(ecs + (c & (ERING - 1)) * EPL + tid + j * NT, e0 + (ok ? c * pe + eoff[j] : 0), ok);
-        }
-      }
-    }
+    if (MODE == TM_POST && (m & 1)) stage_coarse((m + 1) >> 1);
     cp_async_commit();
   };
 
@@ -260,10 +258,14 @@ __global__ void __launch_bounds__(NT) k_tiled(TiledArgs A) {
 #pragma unroll
     for (int j = 0; j < MN; ++j) {
       if (!(nflag[j] & 4)) continue;
+      // bilinear weights from the node's parities (odd: halfway between two coarse
+      // nodes); the neighbour loads stay inside the staged coarse tile
       const int b = deb[j];
-      const bool di = nflag[j] & 8, dj = nflag[j] & 16;
-      const T acc = cp[b] + (di ? cp[b + 1] : T(0)) + (dj ? cp[b + EWX] : T(0)) + ((di && dj) ? cp[b + EWX + 1] : T(0));
-      ed[tid + j * NT] = (di ? T(0.5) : T(1)) * (dj ? T(0.5) : T(1)) * acc;
+      const T wx1 = (nflag[j] & 8) ? T(0.5) : T(0), wy1 = (nflag[j] & 16) ? T(0.5) : T(0);
+      const T wx0 = T(1) - wx1, wy0 = T(1) - wy1;
+      const T r0 = cp[b] * wx0 + cp[b + 1] * wx1;
+      const T r1 = cp[b + EWX] * wx0 + cp[b + EWX + 1] * wx1;
+      ed[tid + j * NT] = r0 * wy0 + r1 * wy1;
     }
     if (c & 1) e_have1 = c; else e_have0 = c;
   };
@@ -313,6 +315,7 @@ __global__ void __launch_bounds__(NT) k_tiled(TiledArgs A) {
   // prologue: derive the planes before kbeg, keep two planes in flight
   const int first_plane = kPre ? kbeg - 2 : kbeg - 1;
   auto mod5 = [](int m) { return (m + 2 * RING) % RING; };
+  if (MODE == TM_POST) stage_coarse(first_plane >> 1);  // committed with the first issue below
   for (int m = first_plane; m <= kbeg + 2; ++m) issue(m, mod5(m));
   cp_async_wait<2>();
   __syncthreads();
