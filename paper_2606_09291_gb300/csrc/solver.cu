@@ -488,22 +488,36 @@ static const char* cls(const char* base, bool fine) {
 // post-smoothing read the same values, so the V-cycle stays symmetric).
 __device__ __forceinline__ double recip(double x) { return 1.0 / x; }
 __device__ __forceinline__ float recip(float x) { return __fdividef(1.0f, x); }
+// One thread per node column (i, j) marching in z: the four cells of the column
+// below a node are summed once and reused by the node above.
 template <typename T, typename TA>
 __global__ void k_dinv(const TA* __restrict__ a, T* __restrict__ dinv, int N) {
   const int s = blockIdx.y;
   const int n1 = N + 1;
-  const long long nodes = (long long)n1 * n1 * n1;
-  const int n = blockIdx.x * blockDim.x + threadIdx.x;
-  if (n >= nodes) return;
-  int i, j, k;
-  node_ijk(n, n1, i, j, k);
-  T v = T(0);
-  if (interior(i, j, k, N)) {
-    Cells8<T, TA> C;
-    C.load(a + s * (long long)N * N * N, i, j, k, N);
-    v = recip(T(1.0 / (3.0 * N)) * C.sum);
+  const int col = blockIdx.x * blockDim.x + threadIdx.x;
+  if (col >= n1 * n1) return;
+  const int i = col % n1, j = col / n1;
+  const long long plane = (long long)n1 * n1;
+  T* out = dinv + s * plane * n1 + col;
+  out[0] = T(0);
+  out[N * plane] = T(0);
+  if (i == 0 || j == 0 || i == N || j == N) {
+    for (int k = 1; k < N; ++k) out[k * plane] = T(0);
+    return;
   }
-  dinv[s * nodes + n] = v;
+  const long long cpl = (long long)N * N;
+  const TA* ac = a + s * cpl * N + (i - 1) + (long long)N * (j - 1);
+  auto sum4 = [&](int c) {
+    const TA* p = ac + cpl * c;
+    return (load_coef<T>(p) + load_coef<T>(p + 1)) + (load_coef<T>(p + N) + load_coef<T>(p + N + 1));
+  };
+  const T h3 = T(1.0 / (3.0 * N));
+  T below = sum4(0);
+  for (int k = 1; k < N; ++k) {
+    const T above = sum4(k);
+    out[k * plane] = recip(h3 * (below + above));
+    below = above;
+  }
 }
 
 template <typename T, typename TA0>
@@ -511,12 +525,12 @@ static void build_dinv(SolverBufs& B, const TA0* a0, cudaStream_t st) {
   for (int j = 0; j <= B.J; ++j) {
     if (!B.dinv[j]) continue;
     const int Nj = B.N >> j;
+    const dim3 g((unsigned)(((Nj + 1) * (Nj + 1) + kBlock - 1) / kBlock), (unsigned)B.S);
     if (j == 0)
-      launch("dinv", nbytes<T, TA0>(Nj, B.S, 1, 1), k_dinv<T, TA0>, grid_nodes(Nj, B.S), kBlock, 0, st, a0,
-             (T*)B.dinv[0], Nj);
+      launch("dinv", nbytes<T, TA0>(Nj, B.S, 1, 1), k_dinv<T, TA0>, g, kBlock, 0, st, a0, (T*)B.dinv[0], Nj);
     else
-      launch("dinv", nbytes<T, T>(Nj, B.S, 1, 1), k_dinv<T, T>, grid_nodes(Nj, B.S), kBlock, 0, st,
-             (const T*)B.acoef[j], (T*)B.dinv[j], Nj);
+      launch("dinv", nbytes<T, T>(Nj, B.S, 1, 1), k_dinv<T, T>, g, kBlock, 0, st, (const T*)B.acoef[j],
+             (T*)B.dinv[j], Nj);
   }
 }
 
