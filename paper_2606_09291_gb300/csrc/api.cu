@@ -33,6 +33,7 @@ struct mlsgd_ctx {
   std::vector<double*> d_phi;  // per level: [n1d][N] at cell centres
   std::vector<double*> d_gtab;   // per level: [N+1] sin(pi i / N), 0 at i = 0, N (nodal interpolant of g)
   std::vector<double*> d_mgtab;  // per level: [N+1] (h/6)(g[i-1] + 4 g[i] + g[i+1]) (1D mass times g)
+  std::vector<float2*> d_gtab2, d_mgtab2;  // the same tables as FP32 (hi, lo) pairs
   char* ws = nullptr;
   size_t ws_size = 0;
   std::vector<__nv_bfloat16*> d_phiT;  // per level: tensor-core B operand [N^3][K] (built on first use)
@@ -104,7 +105,7 @@ size_t level_bytes(const mlsgd_ctx* ctx, int level, int S) {
   b += al(kl_gemm_a_bytes(S, ctx->cfg.n_modes));
   b += solve_scratch_bytes(ctx, N, S);
   const long long ncell = cells_of(ctx->Nc());
-  b += al((4 + 2 * (size_t)S) * 8) + al(((ncell + 255) / 256) * 8 + 64 * 8);
+  b += al((4 + 4 * (size_t)S) * 8) + al(((ncell + 255) / 256) * 8 + 64 * 8);
   return b;
 }
 
@@ -147,9 +148,13 @@ __global__ void k_record(const SolveScalars* __restrict__ sc, int S, int mixed, 
   status[s] = accumulate ? (status[s] | stv) : stv;
 }
 
-// state + Phi + adjoint for S samples on grid N; scratch carved from bp (not kept)
+// state + Phi + adjoint for S samples on grid N; scratch carved from bp (not kept).
+// want_pairs (internal callers): on tiled grids of the mixed path, y stays and q is
+// returned as FP32 (hi, lo) pairs in the FP64 buffers' storage (*pairs_out = true),
+// and Phi / the adjoint right-hand side are formed in pair arithmetic.
 mlsgd_status solve_grid(mlsgd_ctx* ctx, int N, int S, const GridFields& f, const double* z, double* y, double* q,
-                        double* phi, int* iters, int* status, char* scratch, cudaStream_t st) {
+                        double* phi, int* iters, int* status, char* scratch, cudaStream_t st,
+                        bool want_pairs = false, bool* pairs_out = nullptr) {
   const size_t nodes = (size_t)nodes_of(N);
   char* p = scratch;
   SolverBufs B;
@@ -166,7 +171,9 @@ mlsgd_status solve_grid(mlsgd_ctx* ctx, int N, int S, const GridFields& f, const
   else build_hierarchy_fp64(B, f.a64, st);
   launch_rhs_state(z, ctx->Nc(), N, b, st);
   const int fixed = ctx->cfg.ir_steps > 0 ? ctx->cfg.ir_steps : 0;
-  cudaError_t e = ctx->mixed() ? ir_mixed(B, f.a32, f.abf, b, 0, ytmp, r64, prm, inner, st, fixed)
+  const bool pairs = want_pairs && ctx->mixed() && N >= kTiledMinN && B.J >= 1;
+  if (pairs_out) *pairs_out = pairs;
+  cudaError_t e = ctx->mixed() ? ir_mixed(B, f.a32, f.abf, b, 0, ytmp, r64, prm, inner, st, fixed, nullptr, pairs)
                                : pcg_fp64(B, f.a64, b, 0, ytmp, prm, st);
   CK(e);
   launch("record", 0.0, k_record, dim3((S + 127) / 128), 128, 0, st, (const SolveScalars*)B.sc, S, (int)ctx->mixed(),
@@ -174,9 +181,15 @@ mlsgd_status solve_grid(mlsgd_ctx* ctx, int N, int S, const GridFields& f, const
   int lev = 0;
   while ((ctx->cfg.n0 << lev) < N) ++lev;
   CK(cudaMemsetAsync(badj, 0, S * nodes * sizeof(double), st));  // boundary rows stay 0
-  launch_phi_adjrhs(ytmp, N, S, badj, phi, B.partial, ctx->d_gtab[lev], ctx->d_mgtab[lev], st, ctx->freq());
-  e = ctx->mixed() ? ir_mixed(B, f.a32, f.abf, badj, (long long)nodes, q, r64, prm, inner, st, fixed)
-                   : pcg_fp64(B, f.a64, badj, (long long)nodes, q, prm, st);
+  if (pairs) {
+    launch_phi_adjrhs_df((const float2*)ytmp, N, S, (float2*)badj, phi, B.partial, ctx->d_gtab2[lev],
+                         ctx->d_mgtab2[lev], st);
+    e = ir_mixed(B, f.a32, f.abf, nullptr, (long long)nodes, q, r64, prm, inner, st, fixed, (const float2*)badj, true);
+  } else {
+    launch_phi_adjrhs(ytmp, N, S, badj, phi, B.partial, ctx->d_gtab[lev], ctx->d_mgtab[lev], st, ctx->freq());
+    e = ctx->mixed() ? ir_mixed(B, f.a32, f.abf, badj, (long long)nodes, q, r64, prm, inner, st, fixed)
+                     : pcg_fp64(B, f.a64, badj, (long long)nodes, q, prm, st);
+  }
   CK(e);
   launch("record", 0.0, k_record, dim3((S + 127) / 128), 128, 0, st, (const SolveScalars*)B.sc, S, (int)ctx->mixed(),
          iters, status, 1);
@@ -305,6 +318,14 @@ mlsgd_status mlsgd_create(const mlsgd_config* cfg, mlsgd_ctx** out) {
     ok = ok && up((void**)&dg, g.data(), g.size() * sizeof(double)) && up((void**)&dmg, mg.data(), mg.size() * sizeof(double));
     ctx->d_gtab.push_back(dg);
     ctx->d_mgtab.push_back(dmg);
+    std::vector<float2> g2(N + 1), mg2(N + 1);
+    auto split = [](double v) { const float h = (float)v; return make_float2(h, (float)(v - (double)h)); };
+    for (int i = 0; i <= N; ++i) { g2[i] = split(g[i]); mg2[i] = split(mg[i]); }
+    float2 *dg2 = nullptr, *dmg2 = nullptr;
+    ok = ok && up((void**)&dg2, g2.data(), g2.size() * sizeof(float2)) &&
+         up((void**)&dmg2, mg2.data(), mg2.size() * sizeof(float2));
+    ctx->d_gtab2.push_back(dg2);
+    ctx->d_mgtab2.push_back(dmg2);
   }
   ok = ok && cudaHostAlloc((void**)&ctx->count_host, sizeof(int), cudaHostAllocDefault) == cudaSuccess;
   ok = ok && cudaHostAlloc((void**)&ctx->host_buf, 4096 * sizeof(double), cudaHostAllocDefault) == cudaSuccess;
@@ -325,6 +346,8 @@ void mlsgd_destroy(mlsgd_ctx* ctx) {
   for (double* d : ctx->d_phi) cudaFree(d);
   for (double* d : ctx->d_gtab) cudaFree(d);
   for (double* d : ctx->d_mgtab) cudaFree(d);
+  for (float2* d : ctx->d_gtab2) cudaFree(d);
+  for (float2* d : ctx->d_mgtab2) cudaFree(d);
   if (ctx->ws) cudaFree(ctx->ws);
   if (ctx->count_host) cudaFreeHost(ctx->count_host);
   if (ctx->host_buf) cudaFreeHost(ctx->host_buf);
@@ -551,23 +574,24 @@ mlsgd_status mlsgd_level_gradient(mlsgd_ctx* ctx, int iter, int level, int64_t f
     int* iters = bp.take<int>(2 * (size_t)S);
     int* status = bp.take<int>(2 * (size_t)S);
     __nv_bfloat16* gemm_a = bp.take<__nv_bfloat16>((size_t)S * K);
-    double* work = bp.take<double>(4 + 2 * (size_t)S);
+    double* work = bp.take<double>(4 + 4 * (size_t)S);
     const long long ncell = cells_of(ctx->Nc());
     double* spartial = bp.take<double>((size_t)((ncell + 255) / 256) + 64);
     char* scratch = bp.p;
     launch_draw_xi(ctx->cfg.seed, iter, level, first_sample + done, S, K, xi, st, ctx->xi_half_width());
     s = make_field(ctx, xi, level, S, ff, nullptr, st, gemm_a);
     if (s != MLSGD_OK) return s;
-    s = solve_grid(ctx, N, S, ff, z_dev, nullptr, qf, phif, iters, status, scratch, st);
+    bool pf = false, pc = false;
+    s = solve_grid(ctx, N, S, ff, z_dev, nullptr, qf, phif, iters, status, scratch, st, true, &pf);
     if (s != MLSGD_OK) return s;
     if (level > 0) {
       s = make_field(ctx, xi, level - 1, S, fc, nullptr, st, gemm_a);
       if (s != MLSGD_OK) return s;
-      s = solve_grid(ctx, N / 2, S, fc, z_dev, nullptr, qc, phic, iters + S, status + S, scratch, st);
+      s = solve_grid(ctx, N / 2, S, fc, z_dev, nullptr, qc, phic, iters + S, status + S, scratch, st, true, &pc);
       if (s != MLSGD_OK) return s;
     }
     launch_level_stats(qf, phif, N, qc, phic, N / 2, S, ctx->Nc(), ctx->cfg.theta, stats->field_dev,
-                       stats->scalars_dev, work, spartial, iters, status, st);
+                       stats->scalars_dev, work, spartial, iters, status, st, pf, pc);
     CK(cudaGetLastError());
   }
   return MLSGD_OK;

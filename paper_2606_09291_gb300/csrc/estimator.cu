@@ -2,6 +2,8 @@
 // differences, Chan statistics and the multilevel step (rows a3, a5, a7-a10).
 #include <math.h>
 
+#include <type_traits>
+
 #include "internal.cuh"
 #include "kernels.h"
 #include "launch.h"
@@ -114,6 +116,14 @@ __global__ void k_phi_finish(const double* __restrict__ partial, int nblk, int S
   if (lane == 0) phi[s] = 0.5 * v;
 }
 
+// the state as FP32 pairs on a tiled grid: M e written as pairs (tables as pairs)
+void launch_phi_adjrhs_df(const float2* y, int N, int S, float2* badj, double* phi, double* partial,
+                          const float2* gtab, const float2* mgtab, cudaStream_t st) {
+  if (S == 0) return;
+  const int nb = tiled_phi_df(y, N, S, gtab, mgtab, badj, partial, st);
+  launch("phi_finish", 0.0, k_phi_finish, dim3((S + 7) / 8), 256, 0, st, (const double*)partial, nb, S, phi);
+}
+
 void launch_phi_adjrhs(const double* y, int N, int S, double* badj, double* phi, double* partial, const double* gtab,
                        const double* mgtab, cudaStream_t st, int freq) {
   if (S == 0) return;
@@ -130,7 +140,8 @@ void launch_phi_adjrhs(const double* y, int N, int S, double* badj, double* phi,
 
 // ---------------------------------------------------------------- level statistics
 // work layout: [0] shift_new, [1] scale_old = exp(theta (shift_old - shift_new)),
-// [2] n_old, [3] n_batch, [4..4+S) w_fine, [4+S..4+2S) w_coarse.
+// [2] n_old, [3] n_batch, [4..4+S) w_fine, [4+S..4+2S) w_coarse, then the same
+// 2S weights as FP32 pairs (one 8-byte slot each).
 //
 // Single block: shift, per-sample weights Y~ = exp(theta (Phi - shift)), and
 // the scalar statistics of dY~ = Y~_l - Y~_{l-1} (Welford over the batch,
@@ -160,9 +171,14 @@ __global__ void k_level_scalars(const double* __restrict__ phif, const double* _
   }
   __syncthreads();
   const double shift = work[0];
+  float2* wpair = reinterpret_cast<float2*>(work + 4 + 2 * S);  // the same weights as FP32 pairs
   for (int s = threadIdx.x; s < S; s += blockDim.x) {
-    work[4 + s] = exp(theta * (phif[s] - shift));
-    work[4 + S + s] = phic ? exp(theta * (phic[s] - shift)) : 0.0;
+    const double wf = exp(theta * (phif[s] - shift));
+    const double wc = phic ? exp(theta * (phic[s] - shift)) : 0.0;
+    work[4 + s] = wf;
+    work[4 + S + s] = wc;
+    wpair[s] = df_split(wf);
+    wpair[S + s] = df_split(wc);
   }
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -239,6 +255,7 @@ struct CellInterp {
   long long base;  // node (ex, ey, ez) of the level cell holding the control cell
   long long sy, sz;
   double w[8];     // weight of node (ex + a, ey + b, ez + c) at index a + 2b + 4c
+  float w32[8];    // the same weights (exact in FP32: r is a power of two)
   __device__ void setup(int N, int Nc, int cx, int cy, int cz) {
     const int n1 = N + 1, r = Nc / N;
     const double tx = ((cx % r) + 0.5) / r, ty = ((cy % r) + 0.5) / r, tz = ((cz % r) + 0.5) / r;
@@ -248,6 +265,24 @@ struct CellInterp {
 #pragma unroll
     for (int e = 0; e < 8; ++e)
       w[e] = ((e & 1) ? tx : 1.0 - tx) * ((e & 2) ? ty : 1.0 - ty) * ((e & 4) ? tz : 1.0 - tz);
+#pragma unroll
+    for (int e = 0; e < 8; ++e) w32[e] = (float)w[e];
+  }
+  // the same average of an FP32 pair field, in pair arithmetic
+  __device__ __forceinline__ DF eval(const float2* __restrict__ q) const {
+    const float2* b = q + base;
+    const float2 v[8] = {b[0], b[1], b[sy], b[sy + 1], b[sz], b[sz + 1], b[sz + sy], b[sz + sy + 1]};
+    float s = 0.f, c = 0.f;
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+      const float p = w32[e] * v[e].x;
+      const float pe = __fmaf_rn(w32[e], v[e].y, __fmaf_rn(w32[e], v[e].x, -p));
+      const float t = s + p;
+      const float bb = t - s;
+      c += ((s - (t - bb)) + (p - bb)) + pe;
+      s = t;
+    }
+    return df_norm(s, c);
   }
   __device__ __forceinline__ double eval(const double* __restrict__ q) const {
     const double* b = q + base;
@@ -262,14 +297,41 @@ struct CellInterp {
   }
 };
 
+// eval_at_ctrl for an FP32 pair field, in pair arithmetic (trapezoid weights are
+// exact in FP32 since r is a power of two)
+__device__ DF eval_at_ctrl(const float2* __restrict__ q, int N, int Nc, int cx, int cy, int cz) {
+  const int n1 = N + 1;
+  const int r = N / Nc;
+  const float wi = 1.0f / r, we = 0.5f / r;
+  DF acc{0.f, 0.f};
+  for (int c = 0; c <= r; ++c) {
+    const float wz = (c == 0 || c == r) ? we : wi;
+    for (int b = 0; b <= r; ++b) {
+      const float wy = (b == 0 || b == r) ? we : wi;
+      const float2* row = q + (long long)r * cx + (long long)n1 * ((long long)r * cy + b + (long long)n1 * ((long long)r * cz + c));
+      DF rs = df_mulf(df_add(df_make(row[0]), df_make(row[r])), 0.5f);
+      for (int a = 1; a < r; ++a) rs = df_add(rs, df_make(row[a]));
+      acc = df_add(acc, df_mulf(rs, wz * wy * wi));
+    }
+  }
+  return acc;
+}
+
 // One thread per control cell: B*q as the cell average for both grids,
 // dX~_s = w_f[s] B*q_f[s] - w_c[s] B*q_c[s]; batch mean and M2 by the
 // shifted-data sums (deviations from the first sample: no division per
 // sample, stable when the first sample is typical), then the Chan merge with
 // the rescaled old mean; block partials of h_c^3 (M2_batch + delta^2 n_old S / n).
-__global__ void k_level_field(const double* __restrict__ qf, int Nf, const double* __restrict__ qc, int Ncs, int S,
+// PF / PC: the fine / coarse adjoint solutions are FP32 (hi, lo) pairs (the mixed
+// path on tiled grids); those samples then run in pair arithmetic.
+template <bool PF, bool PC>
+__global__ void k_level_field(const void* __restrict__ qf_, int Nf, const void* __restrict__ qc_, int Ncs, int S,
                               int Nc, const double* __restrict__ work, double* __restrict__ field,
                               double* __restrict__ partial) {
+  using QF = typename std::conditional<PF, float2, double>::type;
+  using QC = typename std::conditional<PC, float2, double>::type;
+  const QF* qf = (const QF*)qf_;
+  const QC* qc = (const QC*)qc_;
   const long long ncell = (long long)Nc * Nc * Nc;
   const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   double contrib = 0.0;
@@ -283,21 +345,51 @@ __global__ void k_level_field(const double* __restrict__ qf, int Nf, const doubl
     CellInterp If{}, Ic{};
     if (fast_f) If.setup(Nf, Nc, cx, cy, cz);
     if (qc && fast_c) Ic.setup(Ncs, Nc, cx, cy, cz);
-    double ref = 0.0, sd = 0.0, sd2 = 0.0;
-    for (int s = 0; s < S; ++s) {
-      const double* qfs = qf + s * nf;
-      double v = wf[s] * (fast_f ? If.eval(qfs) : eval_at_ctrl(qfs, Nf, Nc, cx, cy, cz));
-      if (qc) {
-        const double* qcs = qc + s * ncn;
-        v -= wc[s] * (fast_c ? Ic.eval(qcs) : eval_at_ctrl(qcs, Ncs, Nc, cx, cy, cz));
+    double mean, m2;
+    if constexpr (PF) {
+      // all in FP32 pairs: v = w_f X_f - w_c X_c, sums of deviations from the first sample
+      const float2* wpf = reinterpret_cast<const float2*>(work + 4 + 2 * S);
+      const float2* wpc = wpf + S;
+      DF ref{0.f, 0.f}, sd{0.f, 0.f}, sd2{0.f, 0.f};
+      for (int s = 0; s < S; ++s) {
+        const float2* qfs = (const float2*)qf + s * nf;
+        DF v = df_mul(df_make(wpf[s]), fast_f ? If.eval(qfs) : eval_at_ctrl(qfs, Nf, Nc, cx, cy, cz));
+        if (qc) {
+          DF xc;
+          if constexpr (PC) {
+            const float2* qcs = (const float2*)qc + s * ncn;
+            xc = fast_c ? Ic.eval(qcs) : eval_at_ctrl(qcs, Ncs, Nc, cx, cy, cz);
+          } else {
+            const double* qcs = (const double*)qc + s * ncn;
+            xc = df_make(df_split(fast_c ? Ic.eval(qcs) : eval_at_ctrl(qcs, Ncs, Nc, cx, cy, cz)));
+          }
+          v = df_add(v, df_neg(df_mul(df_make(wpc[s]), xc)));
+        }
+        if (s == 0) ref = v;
+        const DF d = df_add(v, df_neg(ref));
+        sd = df_add(sd, d);
+        sd2 = df_add(sd2, df_mul(d, d));
       }
-      if (s == 0) ref = v;
-      const double d = v - ref;
-      sd += d;
-      sd2 = fma(d, d, sd2);
+      const double sdd = df_to_double(sd);
+      mean = df_to_double(ref) + sdd / S;
+      m2 = fmax(df_to_double(sd2) - sdd * (sdd / S), 0.0);
+    } else {
+      double ref = 0.0, sd = 0.0, sd2 = 0.0;
+      for (int s = 0; s < S; ++s) {
+        const double* qfs = (const double*)qf + s * nf;
+        double v = wf[s] * (fast_f ? If.eval(qfs) : eval_at_ctrl(qfs, Nf, Nc, cx, cy, cz));
+        if (qc) {
+          const double* qcs = (const double*)qc + s * ncn;
+          v -= wc[s] * (fast_c ? Ic.eval(qcs) : eval_at_ctrl(qcs, Ncs, Nc, cx, cy, cz));
+        }
+        if (s == 0) ref = v;
+        const double d = v - ref;
+        sd += d;
+        sd2 = fma(d, d, sd2);
+      }
+      mean = ref + sd / S;
+      m2 = fmax(sd2 - sd * (sd / S), 0.0);
     }
-    const double mean = ref + sd / S;
-    const double m2 = fmax(sd2 - sd * (sd / S), 0.0);
     const double n_old = work[2], scale = work[1];
     const double n = n_old + S;
     const double mo = (n_old > 0.0) ? field[c] * scale : 0.0;
@@ -325,15 +417,19 @@ __global__ void k_level_finish(const double* __restrict__ partial, int nblk, con
 
 void launch_level_stats(const double* qf, const double* phif, int Nf, const double* qc, const double* phic,
                         int Ncoarse, int S, int Nc, double theta, double* field, double* scalars, double* work,
-                        double* partial, const int* iters, const int* status, cudaStream_t st) {
+                        double* partial, const int* iters, const int* status, cudaStream_t st, bool qf_pairs,
+                        bool qc_pairs) {
   if (S == 0) return;
   launch("level_scalars", 0.0, k_level_scalars, dim3(1), kBlock, 0, st, phif, phic, S, theta, scalars, work, iters,
          status);
   const long long ncell = (long long)Nc * Nc * Nc;
   const int nblk = (int)((ncell + kBlock - 1) / kBlock);
   const double qbytes = (double)S * 8 * (nodes_of(Nf) + (qc ? nodes_of(Ncoarse) : 0));
-  launch("level_field", qbytes + (double)ncell * 16, k_level_field, dim3(nblk), kBlock, 0, st, qf, Nf, qc, Ncoarse, S,
-         Nc, (const double*)work, field, partial);
+  // pairs on the coarse grid only come with pairs on the fine grid (it is at least as large)
+  auto lf = qf_pairs ? (qc_pairs ? k_level_field<true, true> : k_level_field<true, false>)
+                     : k_level_field<false, false>;
+  launch("level_field", qbytes + (double)ncell * 16, lf, dim3(nblk), kBlock, 0, st, (const void*)qf, Nf,
+         (const void*)qc, Ncoarse, S, Nc, (const double*)work, field, partial);
   launch("level_finish", 0.0, k_level_finish, dim3(1), 32, 0, st, (const double*)partial, nblk, (const double*)work,
          scalars);
 }

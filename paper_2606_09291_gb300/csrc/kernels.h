@@ -86,9 +86,12 @@ cudaError_t pcg_fp64(SolverBufs& B, const double* a64, const double* b, long lon
                      const PcgParams& prm, cudaStream_t st);
 // mixed: FP64 refinement around FP32 PCG (operator a32, V-cycle on abf)
 // fixed_steps > 0: exactly that many refinement steps, no host synchronisation
+// b_pair (tiled grids only): b given as FP32 (hi, lo) pairs instead of b (FP64)
+// pair_out (tiled grids only): x_out's storage receives the solution as FP32 (hi, lo)
+//   pairs (8 bytes per node, as the FP64 layout) instead of FP64 values
 cudaError_t ir_mixed(SolverBufs& B, const float* a32, const __nv_bfloat16* abf, const double* b,
                      long long bstride, double* x_out, double* r64, const PcgParams& prm, int inner_iters,
-                     cudaStream_t st, int fixed_steps = 0);
+                     cudaStream_t st, int fixed_steps = 0, const float2* b_pair = nullptr, bool pair_out = false);
 // coefficient hierarchy for the V-cycle from the level-0 coefficient
 void build_hierarchy_fp64(SolverBufs& B, const double* a64, cudaStream_t st);
 void build_hierarchy_mixed(SolverBufs& B, const __nv_bfloat16* abf, cudaStream_t st);
@@ -119,6 +122,8 @@ void tiled_pre_update(const float* r, const float* q, const __nv_bfloat16* a, co
 void tiled_res64(const float2* b, long long bstride, const float2* x, const float* a, float* r32, double* partial,
                  const SolveScalars* sc, int N, int S, cudaStream_t st);
 // Phi and the adjoint right-hand side; returns the partial-sum blocks per sample
+int tiled_phi_df(const float2* y, int N, int S, const float2* gtab, const float2* mgtab, float2* badj,
+                 double* partial, cudaStream_t st);
 int tiled_phi(const double* y, int N, int S, const double* gtab, const double* mgtab, double* badj, double* partial,
               cudaStream_t st);
 constexpr int kTiledMinN = 16;  // grids with at least this many cells per side use the tiled kernels
@@ -136,10 +141,16 @@ void launch_rhs_state(const double* z, int Nc, int N, double* b, cudaStream_t st
 // Phi = 1/2 e^T M e, badj = M e (interior rows), e = y - g_h
 void launch_phi_adjrhs(const double* y, int N, int S, double* badj, double* phi, double* partial,
                        const double* gtab, const double* mgtab, cudaStream_t st, int freq = 1);
+// the same for a state stored as FP32 pairs on a tiled grid (tables and M e as pairs)
+void launch_phi_adjrhs_df(const float2* y, int N, int S, float2* badj, double* phi, double* partial,
+                          const float2* gtab, const float2* mgtab, cudaStream_t st);
 // batch statistics of one level merged into stats (see mlsgd_level_stats)
+// qf_pairs / qc_pairs: the adjoint solutions are stored as FP32 (hi, lo) pairs;
+// work holds 4 + 4 S doubles
 void launch_level_stats(const double* qf, const double* phif, int Nf, const double* qc, const double* phic,
                         int Ncoarse, int S, int Nc, double theta, double* field, double* scalars,
-                        double* work, double* partial, const int* iters, const int* status, cudaStream_t st);
+                        double* work, double* partial, const int* iters, const int* status, cudaStream_t st,
+                        bool qf_pairs = false, bool qc_pairs = false);
 void launch_stats_reset(double* field, double* scalars, long long ncells, cudaStream_t st);
 void launch_stats_merge(double* dfield, double* dsc, const double* sfield, const double* ssc, long long ncells,
                         double hc3, double theta, double* partial, cudaStream_t st);

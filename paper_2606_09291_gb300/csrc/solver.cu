@@ -349,23 +349,34 @@ __global__ void k_demote(const double* __restrict__ r64, float* __restrict__ r32
 // nodes so that the FP64 block reduction is amortised.
 constexpr int kInitPer = 8;
 static inline int init_blocks(int N) { return (int)((nodes_of(N) + kBlock * kInitPer - 1) / (kBlock * kInitPer)); }
-__global__ void k_init32(const double* __restrict__ b, long long bstride, float* __restrict__ r32,
-                         float2* __restrict__ bdf, double* __restrict__ partial, long long nodes) {
+// PAIR_B: b is already given as FP32 pairs (bp; nothing to split, b.b from the heads).
+template <bool PAIR_B>
+__global__ void k_init32(const double* __restrict__ b, const float2* __restrict__ bp, long long bstride,
+                         float* __restrict__ r32, float2* __restrict__ bdf, double* __restrict__ partial,
+                         long long nodes) {
   const int s = blockIdx.y;
   const long long n0 = (long long)blockIdx.x * blockDim.x * kInitPer + threadIdx.x;
   const bool write_pair = bstride != 0 || s == 0;
   double contrib = 0.0;
+  float contrib32 = 0.0f;
 #pragma unroll
   for (int i = 0; i < kInitPer; ++i) {
     const long long n = n0 + (long long)i * blockDim.x;
     if (n < nodes) {
-      const double bv = b[s * bstride + n];
-      const float hi = (float)bv;
-      r32[s * nodes + n] = hi;
-      if (write_pair) bdf[s * bstride + n] = make_float2(hi, (float)(bv - (double)hi));
-      contrib = fma(bv, bv, contrib);
+      if constexpr (PAIR_B) {
+        const float hi = bp[s * bstride + n].x;
+        r32[s * nodes + n] = hi;
+        contrib32 = __fmaf_rn(hi, hi, contrib32);
+      } else {
+        const double bv = b[s * bstride + n];
+        const float hi = (float)bv;
+        r32[s * nodes + n] = hi;
+        if (write_pair) bdf[s * bstride + n] = make_float2(hi, (float)(bv - (double)hi));
+        contrib = fma(bv, bv, contrib);
+      }
     }
   }
+  if (PAIR_B) contrib = (double)contrib32;
   const double bs = block_sum(contrib);
   if (threadIdx.x == 0) partial[(long long)s * gridDim.x + blockIdx.x] = bs;
 }
@@ -823,7 +834,7 @@ cudaError_t pcg_fp64(SolverBufs& B, const double* a64, const double* b, long lon
 
 cudaError_t ir_mixed(SolverBufs& B, const float* a32, const __nv_bfloat16* abf, const double* b, long long bstride,
                      double* x_out, double* r64, const PcgParams& prm, int inner_iters, cudaStream_t st,
-                     int fixed_steps) {
+                     int fixed_steps, const float2* b_pair, bool pair_out) {
   const int N = B.N, S = B.S;
   const long long nodes = nodes_of(N);
   const dim3 g = grid_nodes(N, S);
@@ -841,10 +852,17 @@ cudaError_t ir_mixed(SolverBufs& B, const float* a32, const __nv_bfloat16* abf, 
   // refinement residual pass), b and the solution are kept as FP32 (hi, lo) pairs
   // (the solution in r64's storage, assigned by the first step and stored to x_out
   // in FP64 at the end), so the refinement loop executes no FP64 arithmetic.
-  float2* xdf = (float2*)r64;
+  if (!tiled && (b_pair || pair_out)) return cudaErrorInvalidValue;  // pairs only on tiled grids
+  float2* xdf = pair_out ? (float2*)x_out : (float2*)r64;
+  const float2* bdf = b_pair ? b_pair : B.bdf;
   if (tiled) {
-    launch("init_f32", bb + nbytes<float, float>(N, S, 1, 0) + (double)(bstride ? S : 1) * nodes * 8, k_init32,
-           dim3((unsigned)init_blocks(N), (unsigned)S), kBlock, 0, st, b, bstride, r32, B.bdf, B.partial, nodes);
+    const dim3 gi((unsigned)init_blocks(N), (unsigned)S);
+    if (b_pair)
+      launch("init_f32", bb + nbytes<float, float>(N, S, 1, 0), k_init32<true>, gi, kBlock, 0, st, b, b_pair,
+             bstride, r32, B.bdf, B.partial, nodes);
+    else
+      launch("init_f32", bb + nbytes<float, float>(N, S, 1, 0) + (double)(bstride ? S : 1) * nodes * 8,
+             k_init32<false>, gi, kBlock, 0, st, b, b_pair, bstride, r32, B.bdf, B.partial, nodes);
     scalar(B, sco, SM_INIT, 0, 0, st, init_blocks(N));
   } else {
     launch("init_f64", bb + nbytes<double, double>(N, S, 2, 0), k_init<double>, g, kBlock, 0, st, b, bstride, r64,
@@ -855,7 +873,7 @@ cudaError_t ir_mixed(SolverBufs& B, const float* a32, const __nv_bfloat16* abf, 
     if (step > 0) {
       const int cap = fixed_steps > 0 ? fixed_steps : prm.max_iter;
       if (tiled) {
-        tiled_res64(B.bdf, bstride, xdf, a32, r32, B.partial, sco, N, S, st);
+        tiled_res64(bdf, bstride, xdf, a32, r32, B.partial, sco, N, S, st);
         scalar(B, sco, SM_OUTER_CONV, tol2, cap, st, tiled_blocks_per_sample(N, S, 8));
       } else {
         launch("resid64", bb + nbytes<double, float>(N, S, 2, 1), k_residual64<float>, g, kBlock, 0, st, b, bstride,
@@ -886,7 +904,7 @@ cudaError_t ir_mixed(SolverBufs& B, const float* a32, const __nv_bfloat16* abf, 
     }
     scalar(B, sco, SM_OUTER_STEP, 0, 0, st, nb, inner_iters);
   }
-  if (tiled)
+  if (tiled && !pair_out)
     launch("store_x", (double)S * nodes * 16, k_store_pair, g, kBlock, 0, st, x_out, (const float2*)xdf, nodes);
   return cudaGetLastError();
 }

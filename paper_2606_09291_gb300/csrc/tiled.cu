@@ -594,6 +594,70 @@ __global__ void __launch_bounds__(NT) k_phi_tiled(const double* __restrict__ y, 
                         blockIdx.x] = b;
 }
 
+// k_phi_tiled for a state given as FP32 (hi, lo) pairs (the mixed level gradient):
+// the same separable sums in pair arithmetic (no FP64 instruction), the 1D tables as
+// pairs, M e written as pairs (the adjoint solve's right-hand side), the partial
+// e.M e of each block returned in FP64.
+__global__ void __launch_bounds__(NT) k_phi_tiled_df(const float2* __restrict__ y, int N, const float2* __restrict__ gtab,
+                                                     const float2* __restrict__ mgtab, float2* __restrict__ badj,
+                                                     double* __restrict__ partial, int nzc, int zc) {
+  __shared__ float2 ys[NP];
+  __shared__ float2 xsum[NPY][TX];
+  __shared__ float2 mxy[3][NT];
+  const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * TX + tx;
+  const int n1 = N + 1;
+  const int s = blockIdx.z / nzc, chunk = blockIdx.z % nzc;
+  const int x0 = 1 + TX * blockIdx.x, y0 = 1 + TY * blockIdx.y;
+  const long long nodes = (long long)n1 * n1 * n1;
+  const float2* yb = y + s * nodes;
+  const int kbeg = 1 + chunk * zc;
+  const int kend = min(N - 1, kbeg + zc - 1);
+  const int gi = x0 + tx, gj = y0 + ty;
+  const bool mine = gi < N && gj < N;
+  DF ycen[3] = {DF{0.f, 0.f}, DF{0.f, 0.f}, DF{0.f, 0.f}};
+  auto four = [](DF a) { return DF{4.f * a.h, 4.f * a.l}; };  // exact
+  auto advance = [&](int m) {
+    for (int e = tid; e < NP; e += NT) {
+      const int lx = e % NPX, ly = e / NPX;
+      const int i = x0 - 1 + lx, j = y0 - 1 + ly;
+      ys[e] = (m >= 0 && m <= N && i <= N && j <= N) ? yb[i + (long long)n1 * (j + (long long)n1 * m)]
+                                                      : make_float2(0.f, 0.f);
+    }
+    __syncthreads();
+    for (int e = tid; e < NPY * TX; e += NT) {
+      const int ly = e / TX, lx = e % TX;
+      const float2* row = ys + NPX * ly + lx;
+      xsum[ly][lx] = df_f2(df_add(df_add(df_make(row[0]), df_make(row[2])), four(df_make(row[1]))));
+    }
+    ycen[(m + 3) % 3] = df_make(ys[(tx + 1) + NPX * (ty + 1)]);
+    __syncthreads();
+    mxy[(m + 3) % 3][tid] =
+        df_f2(df_add(df_add(df_make(xsum[ty][tx]), df_make(xsum[ty + 2][tx])), four(df_make(xsum[ty + 1][tx]))));
+    __syncthreads();
+  };
+  const double h6 = 1.0 / (6.0 * N);
+  const DF h63 = df_make(df_split(h6 * h6 * h6));
+  DF red{0.f, 0.f};
+  advance(kbeg - 1);
+  advance(kbeg);
+  for (int k = kbeg; k <= kend; ++k) {
+    advance(k + 1);
+    if (mine) {
+      const DF my = df_add(df_add(df_make(mxy[(k + 2) % 3][tid]), df_make(mxy[(k + 1) % 3][tid])),
+                           four(df_make(mxy[k % 3][tid])));
+      const DF mg3 = df_mul(df_mul(df_make(mgtab[gi]), df_make(mgtab[gj])), df_make(mgtab[k]));
+      const DF g3 = df_mul(df_mul(df_make(gtab[gi]), df_make(gtab[gj])), df_make(gtab[k]));
+      const DF me = df_add(df_mul(h63, my), df_neg(mg3));
+      const DF e = df_add(ycen[k % 3], df_neg(g3));
+      badj[s * nodes + gi + (long long)n1 * (gj + (long long)n1 * k)] = df_f2(me);
+      red = df_add(red, df_mul(e, me));
+    }
+  }
+  const double b = block_sum(df_to_double(red));
+  if (tid == 0) partial[(long long)s * (gridDim.x * gridDim.y * nzc) + (chunk * gridDim.y + blockIdx.y) * gridDim.x +
+                        blockIdx.x] = b;
+}
+
 // ---------------------------------------------------------------- host side
 
 TiledShape tiled_shape(int N, int S, int ry) {
@@ -686,6 +750,14 @@ void tiled_res64(const float2* b, long long bstride, const float2* x, const floa
   const double bb = (double)(bstride ? S : 1) * nodes_of(N) * 8;
   run_tiled<double, float, TM_RES64>("resid64", bb + vbytes<double, float>(N, S, 1, 1) + (double)S * nodes_of(N) * 4, A,
                                      S, st);
+}
+
+int tiled_phi_df(const float2* y, int N, int S, const float2* gtab, const float2* mgtab, float2* badj,
+                 double* partial, cudaStream_t st) {
+  const TiledShape t = tiled_shape(N, S, 1);
+  launch("phi_adjrhs", (double)S * nodes_of(N) * 16, k_phi_tiled_df, dim3(t.bx, t.by, (unsigned)(S * t.nzc)),
+         dim3(TX, TY), 0, st, y, N, gtab, mgtab, badj, partial, t.nzc, t.zc);
+  return t.blocks_per_sample;
 }
 
 int tiled_phi(const double* y, int N, int S, const double* gtab, const double* mgtab, double* badj, double* partial,
