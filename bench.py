@@ -25,6 +25,12 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "sample-gradients/s (state+adjoint) at rtol 1e-8 vs plain FP64; p99 latency"
+# DRAM bytes (read + write) over algorithmic bytes of the dominant kernel class, from
+# one ncu capture of its 64^3 fine launch on 256 samples of this workload (inputs
+# larger than L2); a full launch processes more samples of the same grid, so its
+# traffic is this ratio times its algorithmic bytes.  Only valid for the kernel as
+# captured: update it with each change of that kernel.
+TRAFFIC_RATIO = {"post_f32": 1.026}
 UNIT = "sample-gradients/s"
 
 
@@ -267,7 +273,10 @@ def run_gpu(args, rank, world):
         else:
             ach = prof["bytes"] / (prof["total_ms"] / 1e3) / 1e9
             roof = {"bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                    "frac": ach / peaks["hbm_gbs"], "traffic": args.traffic_bytes,
+                    "frac": ach / peaks["hbm_gbs"],
+                    "traffic": args.traffic_bytes if args.traffic_bytes is not None else (
+                        TRAFFIC_RATIO[dominant] * prof["bytes"] / prof["launches"] if dominant in TRAFFIC_RATIO
+                        else None),
                     "kernel": dominant, "peak_kind": peak_kind, "launches": prof["launches"],
                     "avg_launch_ms": per_launch_ms, "alg_bytes_per_launch": prof["bytes"] / prof["launches"],
                     "share_of_step": prof_all[dominant]["total_ms"] / total_prof}
