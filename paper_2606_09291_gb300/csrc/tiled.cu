@@ -257,9 +257,10 @@ __global__ void __launch_bounds__(NT) k_tiled(TiledArgs A) {
     T* ed = eps + (c & 1) * NPL;
 #pragma unroll
     for (int j = 0; j < MN; ++j) {
-      if (!(nflag[j] & 4)) continue;
-      // bilinear weights from the node's parities (odd: halfway between two coarse
-      // nodes); the neighbour loads stay inside the staged coarse tile
+      if (!(nflag[j] & 1)) continue;
+      // every staged entry (halo too, discarded later): bilinear weights from the
+      // node's parities (odd: halfway between two coarse nodes); the neighbour loads
+      // stay inside the staged coarse tile
       const int b = deb[j];
       const T wx1 = (nflag[j] & 8) ? T(0.5) : T(0), wy1 = (nflag[j] & 16) ? T(0.5) : T(0);
       const T wx0 = T(1) - wx1, wy0 = T(1) - wy1;
@@ -297,21 +298,26 @@ __global__ void __launch_bounds__(NT) k_tiled(TiledArgs A) {
       }
       const T* e0p = eps + (c0 & 1) * NPL;
       const T* e1p = eps + ((c0 + 1) & 1) * NPL;
+      const T w0 = dk ? T(0.5) : T(1), w1 = dk ? T(0.5) : T(0);
 #pragma unroll
       for (int j = 0; j < MN; ++j) {
         if (!(nflag[j] & 1)) continue;
         const int e = tid + j * NT;
-        T v = T(0);
-        if (mint && (nflag[j] & 4)) {
-          const T rn = (MODE == TM_PREU) ? r0[e] - alpha * raw1[slot * NPL + e] : r0[e];
-          v = omega * rn * dvp[e];
-          if (MODE == TM_POST) v += dk ? T(0.5) * (e0p[e] + e1p[e]) : e0p[e];
+        // branch-free: D^-1 is 0 on the boundary and zero-filled outside the grid (and
+        // so is r outside 0 < m < N), so only the coarse correction needs a mask
+        const T rn = (MODE == TM_PREU) ? r0[e] - alpha * raw1[slot * NPL + e] : r0[e];
+        T v = omega * rn * dvp[e];
+        if (MODE == TM_POST) {
+          const T mk = (mint && (nflag[j] & 4)) ? T(1) : T(0);
+          v += mk * (w0 * e0p[e] + w1 * e1p[e]);
         }
         xp[e] = v;
       }
     }
   };
 
+  if (MODE == TM_POST)  // every E entry is finite before it is first read (masked reads included)
+    for (int e = tid; e < 2 * NPL; e += NT) eps[e] = T(0);
   // prologue: derive the planes before kbeg, keep two planes in flight
   const int first_plane = kPre ? kbeg - 2 : kbeg - 1;
   auto mod5 = [](int m) { return (m + 2 * RING) % RING; };
