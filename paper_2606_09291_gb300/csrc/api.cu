@@ -105,7 +105,8 @@ size_t level_bytes(const mlsgd_ctx* ctx, int level, int S) {
   b += al(kl_gemm_a_bytes(S, ctx->cfg.n_modes));
   b += solve_scratch_bytes(ctx, N, S);
   const long long ncell = cells_of(ctx->Nc());
-  b += al((4 + 4 * (size_t)S) * 8) + al(((ncell + 255) / 256) * 8 + 64 * 8);
+  b += al((4 + 4 * (size_t)S) * 8) + al((((ncell + 255) / 256) + ((cells_of(N) + 255) / 256)) * 8 + 64 * 8);
+  b += al(2 * (size_t)nodes_of(N) * 8);
   return b;
 }
 
@@ -576,7 +577,8 @@ mlsgd_status mlsgd_level_gradient(mlsgd_ctx* ctx, int iter, int level, int64_t f
     __nv_bfloat16* gemm_a = bp.take<__nv_bfloat16>((size_t)S * K);
     double* work = bp.take<double>(4 + 4 * (size_t)S);
     const long long ncell = cells_of(ctx->Nc());
-    double* spartial = bp.take<double>((size_t)((ncell + 255) / 256) + 64);
+    double* spartial = bp.take<double>((size_t)((ncell + 255) / 256) + (size_t)((cells_of(N) + 255) / 256) + 64);
+    double* lvl_nodes = bp.take<double>(2 * (size_t)nodes_of(N));
     char* scratch = bp.p;
     launch_draw_xi(ctx->cfg.seed, iter, level, first_sample + done, S, K, xi, st, ctx->xi_half_width());
     s = make_field(ctx, xi, level, S, ff, nullptr, st, gemm_a);
@@ -591,7 +593,7 @@ mlsgd_status mlsgd_level_gradient(mlsgd_ctx* ctx, int iter, int level, int64_t f
       if (s != MLSGD_OK) return s;
     }
     launch_level_stats(qf, phif, N, qc, phic, N / 2, S, ctx->Nc(), ctx->cfg.theta, stats->field_dev,
-                       stats->scalars_dev, work, spartial, iters, status, st, pf, pc);
+                       stats->scalars_dev, work, spartial, iters, status, st, pf, pc, lvl_nodes);
     CK(cudaGetLastError());
   }
   return MLSGD_OK;

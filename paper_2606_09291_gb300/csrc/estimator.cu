@@ -402,6 +402,164 @@ __global__ void k_level_field(const void* __restrict__ qf_, int Nf, const void* 
   if (threadIdx.x == 0) partial[blockIdx.x] = bs;
 }
 
+// ---- statistics of a level whose grids are coarser than the control grid (Nc = r Nf,
+// r >= 2).  Interpolation to the control grid is linear, so with the nodal values
+// x_s = w_f[s] q_f[s] - w_c[s] P q_c[s] on the level's fine grid (P q_c: the coarse
+// trilinear function at the fine nodes, which interpolation to the control cells
+// reproduces exactly) the batch mean field is the interpolation of the nodal mean,
+// and ||I x||_U^2 = sum over level cells e of x_e^T G x_e with the fixed 8 x 8 Gram
+// matrix G = h_f^3 (g x g x g), g = (1/r) sum_m w(t_m) w(t_m)^T, w(t) = (1 - t, t),
+// t_m = (m + 1/2)/r (the midpoint rule over the r^3 control cells of a level cell is
+// exact for the integrand of these trilinear weights).  M2 of the batch is then
+// sum_s ||d_s||_G^2 - S ||mean d||_G^2 with d_s = x_s - x_0 (deviations from the
+// first sample, as in k_level_field).  Work per sample: the level's nodes and cells,
+// not the control cells.
+__device__ __forceinline__ double ldq(const double* p, long long i) { return p[i]; }
+__device__ __forceinline__ double ldq(const float2* p, long long i) {
+  const float2 v = p[i];
+  return (double)v.x + (double)v.y;
+}
+template <typename QF, typename QC>
+__device__ __forceinline__ double lvl_x(const QF* qfs, const QC* qcs, int Nf, int i, int j, int k, double wf,
+                                        double wc) {
+  const int n1 = Nf + 1;
+  double v = wf * ldq(qfs, i + (long long)n1 * (j + (long long)n1 * k));
+  if (qcs) {
+    const int c1 = Nf / 2 + 1;
+    const int di = i & 1, dj = j & 1, dk = k & 1;
+    const long long b = (i >> 1) + (long long)c1 * ((j >> 1) + (long long)c1 * (k >> 1));
+    double acc = 0.0;
+    for (int c = 0; c <= dk; ++c)
+      for (int bb = 0; bb <= dj; ++bb)
+        for (int a = 0; a <= di; ++a) acc += ldq(qcs, b + a + (long long)c1 * (bb + (long long)c1 * c));
+    v -= wc * acc * (1.0 / (double)(1 << (di + dj + dk)));
+  }
+  return v;
+}
+// nodal x_0 and sum_s (x_s - x_0)
+template <typename QF, typename QC>
+__global__ void k_lvl_nodes(const QF* __restrict__ qf, int Nf, const QC* __restrict__ qc, int S,
+                            const double* __restrict__ work, double* __restrict__ x0, double* __restrict__ dsum) {
+  const int n1 = Nf + 1;
+  const long long nodes = (long long)n1 * n1 * n1;
+  const long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= nodes) return;
+  const int i = (int)(n % n1), j = (int)((n / n1) % n1), k = (int)(n / ((long long)n1 * n1));
+  const long long ncn = qc ? nodes_of(Nf / 2) : 0;
+  const double* wf = work + 4;
+  const double* wc = work + 4 + S;
+  double xr = 0.0, ds = 0.0;
+  for (int s = 0; s < S; ++s) {
+    const double x = lvl_x(qf + s * nodes, qc ? qc + s * ncn : (const QC*)nullptr, Nf, i, j, k, wf[s], wc[s]);
+    if (s == 0) xr = x;
+    ds += x - xr;
+  }
+  x0[n] = xr;
+  dsum[n] = ds;
+}
+// d^T G d for the 8 nodal values of a level cell (index a + 2b + 4c)
+__device__ __forceinline__ double gram8(const double* d, double A, double B) {
+  double t[8], u[8];
+#pragma unroll
+  for (int e = 0; e < 8; e += 2) { t[e] = A * d[e] + B * d[e + 1]; t[e + 1] = B * d[e] + A * d[e + 1]; }
+#pragma unroll
+  for (int e = 0; e < 8; ++e) {
+    if (e & 2) continue;
+    u[e] = A * t[e] + B * t[e + 2];
+    u[e + 2] = B * t[e] + A * t[e + 2];
+  }
+  double q = 0.0;
+#pragma unroll
+  for (int e = 0; e < 4; ++e) q += d[e] * (A * u[e] + B * u[e + 4]) + d[e + 4] * (B * u[e] + A * u[e + 4]);
+  return q;
+}
+// per level cell: sum_s ||d_s||^2 - S ||mean d||^2 over the cell, block partials
+template <typename QF, typename QC>
+__global__ void k_lvl_cells(const QF* __restrict__ qf, int Nf, const QC* __restrict__ qc, int S,
+                            const double* __restrict__ work, const double* __restrict__ x0,
+                            const double* __restrict__ dsum, double A, double B, double hf3,
+                            double* __restrict__ partial) {
+  const long long cells = (long long)Nf * Nf * Nf;
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  double contrib = 0.0;
+  if (e < cells) {
+    const int ci = (int)(e % Nf), cj = (int)((e / Nf) % Nf), ck = (int)(e / ((long long)Nf * Nf));
+    const int n1 = Nf + 1;
+    const long long nodes = (long long)n1 * n1 * n1;
+    const long long ncn = qc ? nodes_of(Nf / 2) : 0;
+    const double* wf = work + 4;
+    const double* wc = work + 4 + S;
+    double xr[8], db[8];
+#pragma unroll
+    for (int v = 0; v < 8; ++v) {
+      const long long n = (ci + (v & 1)) + (long long)n1 * ((cj + ((v >> 1) & 1)) + (long long)n1 * (ck + (v >> 2)));
+      xr[v] = x0[n];
+      db[v] = dsum[n] / S;
+    }
+    double acc = 0.0;
+    for (int s = 0; s < S; ++s) {
+      const QF* qfs = qf + s * nodes;
+      const QC* qcs = qc ? qc + s * ncn : (const QC*)nullptr;
+      double d[8];
+#pragma unroll
+      for (int v = 0; v < 8; ++v)
+        d[v] = lvl_x(qfs, qcs, Nf, ci + (v & 1), cj + ((v >> 1) & 1), ck + (v >> 2), wf[s], wc[s]) - xr[v];
+      acc += gram8(d, A, B);
+    }
+    contrib = hf3 * (acc - S * gram8(db, A, B));
+  }
+  const double bs = block_sum(contrib);
+  if (threadIdx.x == 0) partial[blockIdx.x] = bs;
+}
+// per control cell: batch mean = interpolated nodal mean; Chan merge with the old
+// field; block partials of h_c^3 delta^2 n_old S / n
+__global__ void k_lvl_field(const double* __restrict__ x0, const double* __restrict__ dsum, int Nf, int Nc, int S,
+                            const double* __restrict__ work, double* __restrict__ field, double* __restrict__ partial) {
+  const long long ncell = (long long)Nc * Nc * Nc;
+  const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  double contrib = 0.0;
+  if (c < ncell) {
+    const int cx = (int)(c % Nc), cy = (int)((c / Nc) % Nc), cz = (int)(c / ((long long)Nc * Nc));
+    CellInterp I{};
+    I.setup(Nf, Nc, cx, cy, cz);
+    const double mean = I.eval(x0) + I.eval(dsum) / S;
+    const double n_old = work[2], scale = work[1];
+    const double n = n_old + S;
+    const double mo = (n_old > 0.0) ? field[c] * scale : 0.0;
+    const double delta = mo - mean;
+    field[c] = mean + (n_old / n) * delta;
+    const double hc = 1.0 / Nc;
+    contrib = hc * hc * hc * delta * delta * n_old * S / n;
+  }
+  const double bs = block_sum(contrib);
+  if (threadIdx.x == 0) partial[blockIdx.x] = bs;
+}
+
+template <typename QF, typename QC>
+static void launch_lvl(const void* qf, int Nf, const void* qc, int S, int Nc, const double* work, double* field,
+                       double* partial, double* nodebuf, cudaStream_t st) {
+  const long long nodes = nodes_of(Nf), cells = cells_of(Nf), ncell = cells_of(Nc);
+  double* x0 = nodebuf;
+  double* dsum = nodebuf + nodes;
+  const int r = Nc / Nf;
+  double A = 0.0, B = 0.0;
+  for (int m = 0; m < r; ++m) {
+    const double t = (m + 0.5) / r;
+    A += (1.0 - t) * (1.0 - t) / r;
+    B += t * (1.0 - t) / r;
+  }
+  const double hf = 1.0 / Nf;
+  const double qb = (double)S * sizeof(QF) * (nodes + (qc ? nodes_of(Nf / 2) : 0));
+  launch("level_nodes", qb + (double)nodes * 16, k_lvl_nodes<QF, QC>, dim3((unsigned)((nodes + kBlock - 1) / kBlock)),
+         kBlock, 0, st, (const QF*)qf, Nf, (const QC*)qc, S, work, x0, dsum);
+  const int nbc = (int)((ncell + kBlock - 1) / kBlock);
+  launch("level_field", (double)nodes * 16 + (double)ncell * 16, k_lvl_field, dim3(nbc), kBlock, 0, st,
+         (const double*)x0, (const double*)dsum, Nf, Nc, S, work, field, partial);
+  launch("level_cells", qb + (double)nodes * 16, k_lvl_cells<QF, QC>,
+         dim3((unsigned)((cells + kBlock - 1) / kBlock)), kBlock, 0, st, (const QF*)qf, Nf, (const QC*)qc, S, work,
+         (const double*)x0, (const double*)dsum, A, B, hf * hf * hf, partial + nbc);
+}
+
 // s2_dx = old * scale^2 + sum of partials (fixed order, one warp)
 __global__ void k_level_finish(const double* __restrict__ partial, int nblk, const double* __restrict__ work,
                                double* __restrict__ sc) {
@@ -418,10 +576,19 @@ __global__ void k_level_finish(const double* __restrict__ partial, int nblk, con
 void launch_level_stats(const double* qf, const double* phif, int Nf, const double* qc, const double* phic,
                         int Ncoarse, int S, int Nc, double theta, double* field, double* scalars, double* work,
                         double* partial, const int* iters, const int* status, cudaStream_t st, bool qf_pairs,
-                        bool qc_pairs) {
+                        bool qc_pairs, double* nodebuf) {
   if (S == 0) return;
   launch("level_scalars", 0.0, k_level_scalars, dim3(1), kBlock, 0, st, phif, phic, S, theta, scalars, work, iters,
          status);
+  if (nodebuf && Nf < Nc) {  // the level's grids are coarser than the control grid
+    if (qf_pairs && qc_pairs) launch_lvl<float2, float2>(qf, Nf, qc, S, Nc, work, field, partial, nodebuf, st);
+    else if (qf_pairs) launch_lvl<float2, double>(qf, Nf, qc, S, Nc, work, field, partial, nodebuf, st);
+    else launch_lvl<double, double>(qf, Nf, qc, S, Nc, work, field, partial, nodebuf, st);
+    const int nb = (int)((cells_of(Nc) + kBlock - 1) / kBlock) + (int)((cells_of(Nf) + kBlock - 1) / kBlock);
+    launch("level_finish", 0.0, k_level_finish, dim3(1), 32, 0, st, (const double*)partial, nb, (const double*)work,
+           scalars);
+    return;
+  }
   const long long ncell = (long long)Nc * Nc * Nc;
   const int nblk = (int)((ncell + kBlock - 1) / kBlock);
   const double qbytes = (double)S * 8 * (nodes_of(Nf) + (qc ? nodes_of(Ncoarse) : 0));

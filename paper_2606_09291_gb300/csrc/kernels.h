@@ -146,11 +146,13 @@ void launch_phi_adjrhs_df(const float2* y, int N, int S, float2* badj, double* p
                           const float2* gtab, const float2* mgtab, cudaStream_t st);
 // batch statistics of one level merged into stats (see mlsgd_level_stats)
 // qf_pairs / qc_pairs: the adjoint solutions are stored as FP32 (hi, lo) pairs;
-// work holds 4 + 4 S doubles
+// work holds 4 + 4 S doubles; nodebuf (2 (Nf+1)^3 doubles, optional): when the
+// level's grids are coarser than the control grid the statistics are formed on the
+// level grid (partial then needs cells(Nc)/256 + cells(Nf)/256 + 2 entries)
 void launch_level_stats(const double* qf, const double* phif, int Nf, const double* qc, const double* phic,
                         int Ncoarse, int S, int Nc, double theta, double* field, double* scalars,
                         double* work, double* partial, const int* iters, const int* status, cudaStream_t st,
-                        bool qf_pairs = false, bool qc_pairs = false);
+                        bool qf_pairs = false, bool qc_pairs = false, double* nodebuf = nullptr);
 void launch_stats_reset(double* field, double* scalars, long long ncells, cudaStream_t st);
 void launch_stats_merge(double* dfield, double* dsc, const double* sfield, const double* ssc, long long ncells,
                         double hc3, double theta, double* partial, cudaStream_t st);
