@@ -436,24 +436,30 @@ __device__ __forceinline__ double lvl_x(const QF* qfs, const QC* qcs, int Nf, in
   }
   return v;
 }
-// nodal x_0 and sum_s (x_s - x_0)
+// x_s at every node of the level grid, written over q_f (same 8-byte slots; q_f is
+// not needed after the statistics)
 template <typename QF, typename QC>
-__global__ void k_lvl_nodes(const QF* __restrict__ qf, int Nf, const QC* __restrict__ qc, int S,
-                            const double* __restrict__ work, double* __restrict__ x0, double* __restrict__ dsum) {
+__global__ void k_lvl_x(QF* __restrict__ qf, int Nf, const QC* __restrict__ qc, int S,
+                        const double* __restrict__ work) {
+  const int s = blockIdx.y;
   const int n1 = Nf + 1;
   const long long nodes = (long long)n1 * n1 * n1;
   const long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (n >= nodes) return;
   const int i = (int)(n % n1), j = (int)((n / n1) % n1), k = (int)(n / ((long long)n1 * n1));
   const long long ncn = qc ? nodes_of(Nf / 2) : 0;
-  const double* wf = work + 4;
-  const double* wc = work + 4 + S;
-  double xr = 0.0, ds = 0.0;
-  for (int s = 0; s < S; ++s) {
-    const double x = lvl_x(qf + s * nodes, qc ? qc + s * ncn : (const QC*)nullptr, Nf, i, j, k, wf[s], wc[s]);
-    if (s == 0) xr = x;
-    ds += x - xr;
-  }
+  const double x = lvl_x(qf + s * nodes, qc ? qc + s * ncn : (const QC*)nullptr, Nf, i, j, k, work[4 + s],
+                         work[4 + S + s]);
+  reinterpret_cast<double*>(qf)[s * nodes + n] = x;
+}
+// nodal x_0 and sum_s (x_s - x_0)
+__global__ void k_lvl_nodes(const double* __restrict__ x, long long nodes, int S, double* __restrict__ x0,
+                            double* __restrict__ dsum) {
+  const long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= nodes) return;
+  const double xr = x[n];
+  double ds = 0.0;
+  for (int s = 1; s < S; ++s) ds += x[s * nodes + n] - xr;
   x0[n] = xr;
   dsum[n] = ds;
 }
@@ -474,9 +480,7 @@ __device__ __forceinline__ double gram8(const double* d, double A, double B) {
   return q;
 }
 // per level cell: sum_s ||d_s||^2 - S ||mean d||^2 over the cell, block partials
-template <typename QF, typename QC>
-__global__ void k_lvl_cells(const QF* __restrict__ qf, int Nf, const QC* __restrict__ qc, int S,
-                            const double* __restrict__ work, const double* __restrict__ x0,
+__global__ void k_lvl_cells(const double* __restrict__ x, int Nf, int S, const double* __restrict__ x0,
                             const double* __restrict__ dsum, double A, double B, double hf3,
                             double* __restrict__ partial) {
   const long long cells = (long long)Nf * Nf * Nf;
@@ -486,24 +490,20 @@ __global__ void k_lvl_cells(const QF* __restrict__ qf, int Nf, const QC* __restr
     const int ci = (int)(e % Nf), cj = (int)((e / Nf) % Nf), ck = (int)(e / ((long long)Nf * Nf));
     const int n1 = Nf + 1;
     const long long nodes = (long long)n1 * n1 * n1;
-    const long long ncn = qc ? nodes_of(Nf / 2) : 0;
-    const double* wf = work + 4;
-    const double* wc = work + 4 + S;
+    long long nv[8];
     double xr[8], db[8];
 #pragma unroll
     for (int v = 0; v < 8; ++v) {
-      const long long n = (ci + (v & 1)) + (long long)n1 * ((cj + ((v >> 1) & 1)) + (long long)n1 * (ck + (v >> 2)));
-      xr[v] = x0[n];
-      db[v] = dsum[n] / S;
+      nv[v] = (ci + (v & 1)) + (long long)n1 * ((cj + ((v >> 1) & 1)) + (long long)n1 * (ck + (v >> 2)));
+      xr[v] = x0[nv[v]];
+      db[v] = dsum[nv[v]] / S;
     }
     double acc = 0.0;
     for (int s = 0; s < S; ++s) {
-      const QF* qfs = qf + s * nodes;
-      const QC* qcs = qc ? qc + s * ncn : (const QC*)nullptr;
+      const double* xs = x + s * nodes;
       double d[8];
 #pragma unroll
-      for (int v = 0; v < 8; ++v)
-        d[v] = lvl_x(qfs, qcs, Nf, ci + (v & 1), cj + ((v >> 1) & 1), ck + (v >> 2), wf[s], wc[s]) - xr[v];
+      for (int v = 0; v < 8; ++v) d[v] = xs[nv[v]] - xr[v];
       acc += gram8(d, A, B);
     }
     contrib = hf3 * (acc - S * gram8(db, A, B));
@@ -550,14 +550,18 @@ static void launch_lvl(const void* qf, int Nf, const void* qc, int S, int Nc, co
   }
   const double hf = 1.0 / Nf;
   const double qb = (double)S * sizeof(QF) * (nodes + (qc ? nodes_of(Nf / 2) : 0));
-  launch("level_nodes", qb + (double)nodes * 16, k_lvl_nodes<QF, QC>, dim3((unsigned)((nodes + kBlock - 1) / kBlock)),
-         kBlock, 0, st, (const QF*)qf, Nf, (const QC*)qc, S, work, x0, dsum);
+  const unsigned nbn = (unsigned)((nodes + kBlock - 1) / kBlock);
+  launch("level_x", qb + (double)S * nodes * 8, k_lvl_x<QF, QC>, dim3(nbn, (unsigned)S), kBlock, 0, st,
+         (QF*)const_cast<void*>(qf), Nf, (const QC*)qc, S, work);
+  const double* x = (const double*)qf;
+  launch("level_nodes", (double)S * nodes * 8 + (double)nodes * 16, k_lvl_nodes, dim3(nbn), kBlock, 0, st, x, nodes,
+         S, x0, dsum);
   const int nbc = (int)((ncell + kBlock - 1) / kBlock);
   launch("level_field", (double)nodes * 16 + (double)ncell * 16, k_lvl_field, dim3(nbc), kBlock, 0, st,
          (const double*)x0, (const double*)dsum, Nf, Nc, S, work, field, partial);
-  launch("level_cells", qb + (double)nodes * 16, k_lvl_cells<QF, QC>,
-         dim3((unsigned)((cells + kBlock - 1) / kBlock)), kBlock, 0, st, (const QF*)qf, Nf, (const QC*)qc, S, work,
-         (const double*)x0, (const double*)dsum, A, B, hf * hf * hf, partial + nbc);
+  launch("level_cells", (double)S * nodes * 8 + (double)nodes * 16, k_lvl_cells,
+         dim3((unsigned)((cells + kBlock - 1) / kBlock)), kBlock, 0, st, x, Nf, S, (const double*)x0,
+         (const double*)dsum, A, B, hf * hf * hf, partial + nbc);
 }
 
 // s2_dx = old * scale^2 + sum of partials (fixed order, one warp)
@@ -580,7 +584,10 @@ void launch_level_stats(const double* qf, const double* phif, int Nf, const doub
   if (S == 0) return;
   launch("level_scalars", 0.0, k_level_scalars, dim3(1), kBlock, 0, st, phif, phic, S, theta, scalars, work, iters,
          status);
-  if (nodebuf && Nf < Nc) {  // the level's grids are coarser than the control grid
+  // levels at least 4x coarser than the control grid (per axis): statistics on the level
+  // grid (cost ~ level nodes and cells per sample instead of control cells per sample;
+  // at 2x the control-cell path in pair arithmetic is cheaper).  q_f is overwritten.
+  if (nodebuf && 4 * Nf <= Nc) {
     if (qf_pairs && qc_pairs) launch_lvl<float2, float2>(qf, Nf, qc, S, Nc, work, field, partial, nodebuf, st);
     else if (qf_pairs) launch_lvl<float2, double>(qf, Nf, qc, S, Nc, work, field, partial, nodebuf, st);
     else launch_lvl<double, double>(qf, Nf, qc, S, Nc, work, field, partial, nodebuf, st);

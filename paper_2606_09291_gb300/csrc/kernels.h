@@ -147,8 +147,9 @@ void launch_phi_adjrhs_df(const float2* y, int N, int S, float2* badj, double* p
 // batch statistics of one level merged into stats (see mlsgd_level_stats)
 // qf_pairs / qc_pairs: the adjoint solutions are stored as FP32 (hi, lo) pairs;
 // work holds 4 + 4 S doubles; nodebuf (2 (Nf+1)^3 doubles, optional): when the
-// level's grids are coarser than the control grid the statistics are formed on the
-// level grid (partial then needs cells(Nc)/256 + cells(Nf)/256 + 2 entries)
+// level's grids are at least 4x coarser than the control grid the statistics are
+// formed on the level grid (qf is then overwritten; partial needs cells(Nc)/256 +
+// cells(Nf)/256 + 2 entries)
 void launch_level_stats(const double* qf, const double* phif, int Nf, const double* qc, const double* phic,
                         int Ncoarse, int S, int Nc, double theta, double* field, double* scalars,
                         double* work, double* partial, const int* iters, const int* status, cudaStream_t st,
