@@ -181,7 +181,7 @@ mlsgd_status solve_grid(mlsgd_ctx* ctx, int N, int S, const GridFields& f, const
          iters, status, 0);
   int lev = 0;
   while ((ctx->cfg.n0 << lev) < N) ++lev;
-  CK(cudaMemsetAsync(badj, 0, S * nodes * sizeof(double), st));  // boundary rows stay 0
+  if (!pairs) CK(cudaMemsetAsync(badj, 0, S * nodes * sizeof(double), st));  // boundary rows stay 0
   if (pairs) {
     launch_phi_adjrhs_df((const float2*)ytmp, N, S, (float2*)badj, phi, B.partial, ctx->d_gtab2[lev],
                          ctx->d_mgtab2[lev], st);

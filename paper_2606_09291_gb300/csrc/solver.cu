@@ -350,10 +350,11 @@ __global__ void k_demote(const double* __restrict__ r64, float* __restrict__ r32
 constexpr int kInitPer = 8;
 static inline int init_blocks(int N) { return (int)((nodes_of(N) + kBlock * kInitPer - 1) / (kBlock * kInitPer)); }
 // PAIR_B: b is already given as FP32 pairs (bp; nothing to split, b.b from the heads).
+// Boundary rows of b are taken as 0 whatever the buffer holds there.
 template <bool PAIR_B>
 __global__ void k_init32(const double* __restrict__ b, const float2* __restrict__ bp, long long bstride,
                          float* __restrict__ r32, float2* __restrict__ bdf, double* __restrict__ partial,
-                         long long nodes) {
+                         long long nodes, int N) {
   const int s = blockIdx.y;
   const long long n0 = (long long)blockIdx.x * blockDim.x * kInitPer + threadIdx.x;
   const bool write_pair = bstride != 0 || s == 0;
@@ -363,6 +364,13 @@ __global__ void k_init32(const double* __restrict__ b, const float2* __restrict_
   for (int i = 0; i < kInitPer; ++i) {
     const long long n = n0 + (long long)i * blockDim.x;
     if (n < nodes) {
+      int ii, jj, kk;
+      node_ijk((int)n, N + 1, ii, jj, kk);
+      if (!interior(ii, jj, kk, N)) {
+        r32[s * nodes + n] = 0.0f;
+        if (!PAIR_B && write_pair) bdf[s * bstride + n] = make_float2(0.0f, 0.0f);
+        continue;
+      }
       if constexpr (PAIR_B) {
         const float hi = bp[s * bstride + n].x;
         r32[s * nodes + n] = hi;
@@ -386,11 +394,17 @@ __global__ void k_init32(const double* __restrict__ b, const float2* __restrict_
 // renormalisation, about 48 significant bits), d taken as 0 when never written
 __global__ void k_finish_step(float2* __restrict__ x, const float* __restrict__ d, const float* __restrict__ p,
                               const SolveScalars* __restrict__ sci, const SolveScalars* __restrict__ sco,
-                              long long nodes, int assign, int d_zero) {
+                              long long nodes, int N, int assign, int d_zero) {
   SAMPLE_GUARD(sco);
   const int n = blockIdx.x * blockDim.x + threadIdx.x;
   if (n >= nodes) return;
   const long long o = s * nodes + n;
+  int i, j, k;
+  node_ijk(n, N + 1, i, j, k);
+  if (!interior(i, j, k, N)) {  // d and p are never written on the boundary
+    x[o] = make_float2(0.0f, 0.0f);
+    return;
+  }
   const float dv = d_zero ? 0.0f : d[o];
   const float inc = dv + (float)sci[s].alpha * p[o];
   if (assign) {
@@ -754,7 +768,7 @@ static cudaError_t pcg_inner_fused(SolverBufs& B, const float* a32, const __nv_b
     if (it == iters - 1) {
       launch("finish_step", (double)S * nodes * ((iters > 1 ? 4 : 0) + 4 + (assign_out ? 8 : 16)), k_finish_step,
              grid_nodes(N, S), kBlock, 0, st, x_out, (const float*)x, (const float*)pnew, (const SolveScalars*)sc,
-             sco, nodes, assign_out ? 1 : 0, iters > 1 ? 0 : 1);
+             sco, nodes, N, assign_out ? 1 : 0, iters > 1 ? 0 : 1);
       break;
     }
     nrz = vcycle<float, __nv_bfloat16>(B, rb[rc], abf, sc, omega, st, q, rb[rc ^ 1]);
@@ -806,8 +820,11 @@ static void zero_boundary(void* const* bufs, int nv, int N, int S, cudaStream_t 
 // The tiled passes write interior nodes only: the vectors they produce (and the
 // inner solve's correction, which is first assigned by a tiled pass) get zero
 // boundary nodes once per solve.
+// The mixed path needs none of this: its tiled passes zero-fill boundary nodes when
+// staging, and the kernels that read whole vectors (the refinement's init and
+// accumulation) take the boundary as 0 themselves.
 static cudaError_t clear_tiled(SolverBufs& B, int elem, cudaStream_t st) {
-  if (!(B.N >= kTiledMinN && B.J >= 1)) return cudaSuccess;
+  if (!(B.N >= kTiledMinN && B.J >= 1) || elem == 4) return cudaSuccess;
   void* bufs[6] = {B.p, B.vx[0], B.q, B.vt[0], B.r2, B.x};
   if (elem == 4) zero_boundary<float>(bufs, 6, B.N, B.S, st);
   else zero_boundary<double>(bufs, 5, B.N, B.S, st);
@@ -859,10 +876,10 @@ cudaError_t ir_mixed(SolverBufs& B, const float* a32, const __nv_bfloat16* abf, 
     const dim3 gi((unsigned)init_blocks(N), (unsigned)S);
     if (b_pair)
       launch("init_f32", bb + nbytes<float, float>(N, S, 1, 0), k_init32<true>, gi, kBlock, 0, st, b, b_pair,
-             bstride, r32, B.bdf, B.partial, nodes);
+             bstride, r32, B.bdf, B.partial, nodes, N);
     else
       launch("init_f32", bb + nbytes<float, float>(N, S, 1, 0) + (double)(bstride ? S : 1) * nodes * 8,
-             k_init32<false>, gi, kBlock, 0, st, b, b_pair, bstride, r32, B.bdf, B.partial, nodes);
+             k_init32<false>, gi, kBlock, 0, st, b, b_pair, bstride, r32, B.bdf, B.partial, nodes, N);
     scalar(B, sco, SM_INIT, 0, 0, st, init_blocks(N));
   } else {
     launch("init_f64", bb + nbytes<double, double>(N, S, 2, 0), k_init<double>, g, kBlock, 0, st, b, bstride, r64,

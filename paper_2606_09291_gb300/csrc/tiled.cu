@@ -208,13 +208,13 @@ __global__ void __launch_bounds__(NT) k_tiled(TiledArgs A) {
     const int e = tid + j * NT;
     const int ci = ex0 + e % EWX, cj = ey0 + e / EWX;
     ehas[j] = (MODE == TM_POST) && e < EPL;
-    eok[j] = ehas[j] && ci < nc1 && cj < nc1;
+    eok[j] = ehas[j] && ci > 0 && cj > 0 && ci < nc1 - 1 && cj < nc1 - 1;  // coarse interior
     eoff[j] = eok[j] ? ci + nc1 * cj : 0;
   }
   // POST: coarse plane c is staged once, by issue(2c - 1) (the first fine plane that
   // needs it is 2c - 1), plus the first derived plane's own coarse plane in the prologue
   auto stage_coarse = [&](int c) {
-    const bool cok2 = c >= 0 && c < nc1;
+    const bool cok2 = c > 0 && c < nc1 - 1;
 #pragma unroll
     for (int j = 0; j < ME; ++j) {
       if (!ehas[j]) continue;
@@ -224,13 +224,15 @@ __global__ void __launch_bounds__(NT) k_tiled(TiledArgs A) {
   };
 
   auto issue = [&](int m, int slot) {
-    const bool mok = m >= 0 && m <= N;
+    // every node vector here is zero on the Dirichlet boundary: boundary nodes are
+    // zero-filled like nodes outside the grid, so no buffer's boundary is ever read
+    const bool mok = m > 0 && m < N;
     const long long mo = mok ? (long long)m * pn : 0;
 #pragma unroll
     for (int j = 0; j < MN; ++j) {
       if (!(nflag[j] & 1)) continue;
       const int e = tid + j * NT;
-      const bool ok = mok && (nflag[j] & 2);
+      const bool ok = mok && (nflag[j] & 4);
       cp_async<sizeof(T)>(raw0 + slot * NPL + e, in0 + (ok ? mo + noff[j] : 0), ok);
       if (stage1) cp_async<sizeof(T)>(raw1 + slot * NPL + e, in1 + (ok ? mo + noff[j] : 0), ok);
       if (kPre) cp_async<sizeof(T)>(dvs + slot * NPL + e, dvg + (ok ? mo + noff[j] : 0), ok);
