@@ -22,7 +22,11 @@
 
 namespace mlsgd {
 
-constexpr int GBM = 128, GBN = 128, GBK = 64, GSTAGES = 4;
+// K is short here (the mode count, 256 for the workload: four chunks), so two stages
+// suffice; 66 KB of shared memory and 128 TMEM columns per CTA let three CTAs share
+// an SM, so one CTA's epilogue (exp, BF16 stores) overlaps the others' loads and MMAs.
+constexpr int GBM = 128, GBN = 128, GBK = 64, GSTAGES = 2;
+constexpr int kGemmCtasPerSm = 3;
 constexpr uint32_t GSTAGE_A = GBM * GBK * 2;  // 16 KB
 constexpr uint32_t GSTAGE_B = GBN * GBK * 2;  // 16 KB
 constexpr uint32_t kWaitLimit = 1u << 22;  // bounded polls of mbarrier.try_wait
@@ -75,7 +79,7 @@ constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(GBN
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory"); }
 
-__global__ void __launch_bounds__(128, 1)
+__global__ void __launch_bounds__(128, kGemmCtasPerSm)
     k_kl_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, int S, int cells, int K,
               __nv_bfloat16* __restrict__ abf, float* __restrict__ loga, int* __restrict__ err) {
   extern __shared__ unsigned char gsm_raw[];
