@@ -181,15 +181,38 @@ __global__ void k_level_scalars(const double* __restrict__ phif, const double* _
     wpair[S + s] = df_split(wc);
   }
   __syncthreads();
-  if (threadIdx.x == 0) {
-    // Welford over the batch in sample order
-    double mean = 0.0, s2 = 0.0;
-    for (int s = 0; s < S; ++s) {
-      const double v = work[4 + s] - work[4 + S + s];
-      const double d = v - mean;
-      mean += d / (s + 1);
-      s2 += d * (v - mean);
+  // batch mean and M2 of dY~ by shifted sums over the block (deviations from the
+  // first sample), and the sample-wise maxima / counts, all in parallel
+  const double ref = work[4] - work[4 + S];
+  double sd = 0.0, sd2 = 0.0, pm = -INFINITY, itp = 0.0, ncp = 0.0;
+  for (int s = threadIdx.x; s < S; s += blockDim.x) {
+    const double d = (work[4 + s] - work[4 + S + s]) - ref;
+    sd += d;
+    sd2 = fma(d, d, sd2);
+    pm = fmax(pm, fmax(phif[s], phic ? phic[s] : -INFINITY));
+  }
+  if (iters) {
+    const int nsolve = phic ? 2 * S : S;
+    for (int t = threadIdx.x; t < nsolve; t += blockDim.x) {
+      itp += iters[t];
+      ncp += (status[t] != 0) ? 1.0 : 0.0;
     }
+  }
+  sd = block_sum(sd);
+  __syncthreads();
+  sd2 = block_sum(sd2);
+  __syncthreads();
+  itp = block_sum(itp);
+  __syncthreads();
+  ncp = block_sum(ncp);
+  for (int o = 16; o > 0; o >>= 1) pm = fmax(pm, __shfl_xor_sync(0xffffffffu, pm, o));
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) smax[threadIdx.x >> 5] = pm;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int w = 1; w < kBlock / 32; ++w) pm = fmax(pm, smax[w]);
+    const double mean = ref + sd / S;
+    const double s2 = fmax(sd2 - sd * (sd / S), 0.0);
     const double n_old = work[2], scale = work[1];
     const double n = n_old + S;
     const double mo = sc[MLSGD_S_MEAN_DY] * scale;
@@ -199,18 +222,9 @@ __global__ void k_level_scalars(const double* __restrict__ phif, const double* _
     sc[MLSGD_S_S2_DY] = so + s2 + delta * delta * n_old * S / n;
     sc[MLSGD_S_COUNT] = n;
     sc[MLSGD_S_SHIFT] = shift;
-    double pmax = sc[MLSGD_S_PHI_MAX];
-    double it = 0.0, nc = 0.0;
-    for (int s = 0; s < S; ++s) {
-      pmax = fmax(pmax, fmax(phif[s], phic ? phic[s] : -INFINITY));
-    }
-    if (iters) {
-      const int nsolve = phic ? 2 * S : S;
-      for (int t = 0; t < nsolve; ++t) { it += iters[t]; nc += (status[t] != 0) ? 1.0 : 0.0; }
-    }
-    sc[MLSGD_S_PHI_MAX] = pmax;
-    sc[MLSGD_S_ITERS] += it;
-    sc[MLSGD_S_NOCONV] += nc;
+    sc[MLSGD_S_PHI_MAX] = fmax(sc[MLSGD_S_PHI_MAX], pm);
+    sc[MLSGD_S_ITERS] += itp;
+    sc[MLSGD_S_NOCONV] += ncp;
   }
 }
 

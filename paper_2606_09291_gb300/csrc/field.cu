@@ -99,47 +99,47 @@ __global__ void k_field(const double* __restrict__ xi, int K, const ModeTable mt
 }
 
 // FP32-coefficient synthesis (the mixed path needs only a = exp(log a) rounded to
-// FP32 and BF16): stage 1 (T2) as in k_field in FP64, stored as FP32 (hi, lo) pairs;
+// FP32 and BF16): stage 1 (T2) in FP32 pair arithmetic from c_k phi_{iz_k}(z)
+// (formed in FP64 once per block and split) and the pair tables;
 // stage 2 contracts over i in pair arithmetic (exact products by FMA, two-sum
 // accumulation: about 44 significant bits, far below the FP32 rounding of a), four
 // consecutive cells in x per thread; exp by a Cody-Waite reduction against ln 2 split
 // into a 16-bit head (exact multiples for |k| < 256) and its remainder, then expf.
-// Dynamic shared memory: c[K rounded up to even], phi[n1d][N] (doubles), then T2
-// hi/lo [n1x][N] and phi hi/lo [n1x][N] (floats; 16-byte aligned for the float4
-// reads since N % 4 == 0 is required).
+// Dynamic shared memory: c_k phi(z) pairs [K rounded up to even], then T2 hi/lo
+// [n1x][N] and phi hi/lo [n1d][N] (floats; 16-byte aligned for the float4 reads
+// since N % 4 == 0 is required).
 constexpr float kLn2Hi = 0.693145751953125f;        // ln 2 truncated to 16 bits
 constexpr float kLn2Lo = 1.4286068202862268e-06f;   // ln 2 - kLn2Hi
 __global__ void k_field_df(const double* __restrict__ xi, int K, const ModeTable mt, const double* __restrict__ phi,
                            int N, float* __restrict__ a32, __nv_bfloat16* __restrict__ abf) {
   extern __shared__ __align__(16) unsigned char smf[];
-  double* c = reinterpret_cast<double*>(smf);
-  double* ph = c + ((K + 1) & ~1);
-  float* T2h = (float*)(ph + mt.n1d * N);
+  float2* cz = reinterpret_cast<float2*>(smf);  // c_k phi_{iz_k}(z) as pairs
+  float* T2h = reinterpret_cast<float*>(cz + ((K + 1) & ~1));
   float* T2l = T2h + mt.n1x * N;
-  float* Ph = T2l + mt.n1x * N;
-  float* Pl = Ph + mt.n1x * N;
+  float* Ph = T2l + mt.n1x * N;  // all 1D tables as pairs
+  float* Pl = Ph + mt.n1d * N;
   const int z = blockIdx.x, s = blockIdx.y;
-  for (int k = threadIdx.x; k < K; k += blockDim.x) c[k] = mt.scale[k] * xi[(long long)s * K + k];
+  for (int k = threadIdx.x; k < K; k += blockDim.x) {
+    const double v = mt.scale[k] * xi[(long long)s * K + k] * phi[mt.iz[k] * N + z];
+    cz[k] = df_split(v);
+  }
   for (int e = threadIdx.x; e < mt.n1d * N; e += blockDim.x) {
     const double v = phi[e];
-    ph[e] = v;
-    if (e < mt.n1x * N) {
-      const float h = (float)v;
-      Ph[e] = h;
-      Pl[e] = (float)(v - (double)h);
-    }
+    const float h = (float)v;
+    Ph[e] = h;
+    Pl[e] = (float)(v - (double)h);
   }
   __syncthreads();
   for (int e = threadIdx.x; e < mt.n1x * N; e += blockDim.x) {
     const int i = e / N, y = e % N;
-    double acc = 0.0;
+    DF acc{0.f, 0.f};
     for (int t = mt.offs[i]; t < mt.offs[i + 1]; ++t) {
       const int k = mt.order[t];
-      acc += c[k] * ph[mt.iy[k] * N + y] * ph[mt.iz[k] * N + z];
+      const int o = mt.iy[k] * N + y;
+      acc = df_add(acc, df_mul(df_make(cz[k]), DF{Ph[o], Pl[o]}));
     }
-    const float h = (float)acc;
-    T2h[e] = h;
-    T2l[e] = (float)(acc - (double)h);
+    T2h[e] = acc.h;
+    T2l[e] = acc.l;
   }
   __syncthreads();
   const long long base = (long long)s * N * N * N + (long long)z * N * N;
@@ -186,8 +186,8 @@ cudaError_t launch_field(const double* xi, int K, const ModeTable& mt, const dou
                          const FieldOut& out, cudaStream_t st) {
   if (S == 0) return cudaSuccess;
   if (!out.log_a && !out.a64 && (out.a32 || out.abf) && N % 4 == 0) {
-    const size_t smem =
-        sizeof(double) * ((size_t)((K + 1) & ~1) + (size_t)mt.n1d * N) + sizeof(float) * 4 * (size_t)mt.n1x * N;
+    const size_t smem = sizeof(float2) * (size_t)((K + 1) & ~1) +
+                        sizeof(float) * (2 * (size_t)mt.n1x * N + 2 * (size_t)mt.n1d * N);
     static size_t smem_df = 48 * 1024;
     if (smem > smem_df) {
       cudaError_t e = cudaFuncSetAttribute(k_field_df, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
