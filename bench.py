@@ -163,7 +163,14 @@ def run_gpu(args, rank, world):
     import __graft_entry__
     from paper_2606_09291_gb300 import inputs, mlsgd
 
-    __graft_entry__.build()
+    if world > 1:  # one rank compiles (in-tree outputs are shared), the others load after it
+        if rank == 0:
+            __graft_entry__.build()
+        dist.barrier()
+        if rank != 0:
+            __graft_entry__.build()
+    else:
+        __graft_entry__.build()
     dev = int(os.environ.get("LOCAL_RANK", 0))
     torch.cuda.set_device(dev)
     stream = torch.cuda.current_stream()
