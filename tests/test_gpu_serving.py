@@ -51,3 +51,35 @@ def test_fifo_latency_closed_forms():
     assert all(abs(x - 10.0) < 1e-9 for x in lat)
     lat = serving.fifo_latency([10.0] * 50, rate_per_s=1e6)
     assert lat[-1] > 490.0
+
+
+@pytest.mark.gpu
+def test_continuous_batching_same_alone_and_in_mix(lib):
+    """Requests of several estimates admitted while others run: each level record
+    equals the one computed alone, bit for bit; the requests overlap on the device;
+    a tight HBM budget keeps the large requests from running together."""
+    from paper_2606_09291_gb300 import serving
+    z = torch.tensor(inputs.z_test(32), dtype=torch.float64, device="cuda")
+    reqs = serving.poisson_mix_requests(MIX, 3, 0.0, first_estimate=40)  # 9 requests at t = 0
+    big = [(l, m) for l, m in enumerate(MIX)]
+    srv = serving.ContinuousServer(CFG, 3, big)
+    mixed = srv.run(reqs, z, keep=True)
+    overlap = any(a["start"] < b["done"] and b["start"] < a["done"]
+                  for i, a in enumerate(mixed) for b in mixed[i + 1:])
+    assert overlap
+    srv.close()
+    alone = serving.ContinuousServer(CFG, 1, big)
+    for r, req in zip(mixed, reqs):
+        one = alone.run([(0.0,) + tuple(req[1:])], z, keep=True)[0]
+        assert torch.equal(r["field"], one["field"]) and torch.equal(r["scalars"], one["scalars"])
+    alone.close()
+    # budget = the largest request's scratch: two level-2 requests never run together
+    tight = serving.ContinuousServer(CFG, 3, big)
+    tight.budget = max(tight.footprint(l, m) for l, m in big)
+    res = tight.run(reqs, z)
+    l2 = [r for r in res if r["level"] == 2]
+    assert len(l2) == 3
+    for i, a in enumerate(l2):
+        for b in l2[i + 1:]:
+            assert not (a["start"] < b["done"] and b["start"] < a["done"])
+    tight.close()
