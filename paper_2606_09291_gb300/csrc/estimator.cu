@@ -50,9 +50,46 @@ __global__ void k_rhs_state(const double* __restrict__ z, int Nc, int N, double*
   b[n] = acc;
 }
 
+// The same integral for a grid much coarser than the control grid (r = Nc / N >= 8):
+// one block per node reduces over the (2r)^3 control cells of the node's support,
+// cx fastest so a warp reads contiguous control rows.  On cell c of a support the
+// hat weight along one axis is 1 - |(c + 1/2) / r - 1|, c = 0 .. 2r-1.
+__global__ void __launch_bounds__(kBlock) k_rhs_state_wide(const double* __restrict__ z, int Nc, int N,
+                                                           double* __restrict__ b) {
+  const int n1 = N + 1;
+  const int n = blockIdx.x;
+  int i, j, k;
+  node_ijk(n, n1, i, j, k);
+  if (!interior(i, j, k, N)) {
+    if (threadIdx.x == 0) b[n] = 0.0;
+    return;
+  }
+  const int r = Nc / N, w2 = 2 * r;
+  const double inv_r = 1.0 / r;
+  const long long cnt = (long long)w2 * w2 * w2;
+  const long long x0 = (long long)r * (i - 1), y0 = (long long)r * (j - 1), z0 = (long long)r * (k - 1);
+  double acc = 0.0;
+  for (long long e = threadIdx.x; e < cnt; e += blockDim.x) {
+    const int cx = (int)(e % w2);
+    const long long t = e / w2;
+    const int cy = (int)(t % w2), cz = (int)(t / w2);
+    const double w = (1.0 - fabs((cx + 0.5) * inv_r - 1.0)) * (1.0 - fabs((cy + 0.5) * inv_r - 1.0)) *
+                     (1.0 - fabs((cz + 0.5) * inv_r - 1.0));
+    acc += w * z[(x0 + cx) + Nc * ((y0 + cy) + Nc * (z0 + cz))];
+  }
+  acc = block_sum(acc);
+  if (threadIdx.x == 0) {
+    const double hc = 1.0 / Nc;
+    b[n] = acc * (hc * hc * hc);
+  }
+}
+
 void launch_rhs_state(const double* z, int Nc, int N, double* b, cudaStream_t st) {
-  launch("rhs", (double)cells_of(Nc) * 8 + (double)nodes_of(N) * 8, k_rhs_state, dim3(node_blocks(N)), kBlock, 0, st,
-         z, Nc, N, b);
+  const double bytes = (double)cells_of(Nc) * 8 + (double)nodes_of(N) * 8;
+  if (Nc >= 8 * N)
+    launch("rhs", bytes, k_rhs_state_wide, dim3((unsigned)nodes_of(N)), kBlock, 0, st, z, Nc, N, b);
+  else
+    launch("rhs", bytes, k_rhs_state, dim3(node_blocks(N)), kBlock, 0, st, z, Nc, N, b);
 }
 
 // e = y - g_h with g_h the nodal interpolant of sin(pi x) sin(pi y) sin(pi z);

@@ -272,3 +272,16 @@ def test_control_coarser_than_grid(lib, ctrl_level):
         st_ = _gpu_level(ctx, level, n, zt)
         _compare_stats(st_, _oracle_level(W, level, n, z), W, TOL64)
     ctx.close()
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", TOL64), ("mixed", TOLMIX)])
+def test_control_much_finer_than_grid(lib, precision, tol):
+    """Grid 8 (r = 8) and 16 (r = 4) under a 64^3 control grid: B z summed over the
+    (2r)^3 control cells of each node's support, one block per node for r >= 8."""
+    rtol = 1e-13 if precision == "fp64" else 1e-8
+    for grid, S in ((0, 3), (1, 2)):
+        y, q, phi, it, st, refs = _solve_both(lib, precision, grid, S, rtol, z_kind="rand", n_levels=4, ctrl_level=3)
+        assert np.all(st == 0)
+        for s in range(S):
+            assert rel_err(y[s], refs[s]["y"]) <= tol and rel_err(q[s], refs[s]["q"]) <= tol
+            assert abs(phi[s] - refs[s]["phi"]) <= tol * abs(refs[s]["phi"])
