@@ -104,8 +104,7 @@ size_t level_bytes(const mlsgd_ctx* ctx, int level, int S) {
   b += 2 * al((size_t)2 * S * 4);
   b += al(kl_gemm_a_bytes(S, ctx->cfg.n_modes));
   b += solve_scratch_bytes(ctx, N, S);
-  const long long ncell = cells_of(ctx->Nc());
-  b += al((4 + 4 * (size_t)S) * 8) + al((((ncell + 255) / 256) + ((cells_of(N) + 255) / 256)) * 8 + 64 * 8);
+  b += al((4 + 4 * (size_t)S) * 8) + al((size_t)level_partial_cap(ctx->Nc(), N) * 8);
   b += al(2 * (size_t)nodes_of(N) * 8);
   return b;
 }
@@ -576,8 +575,7 @@ mlsgd_status mlsgd_level_gradient(mlsgd_ctx* ctx, int iter, int level, int64_t f
     int* status = bp.take<int>(2 * (size_t)S);
     __nv_bfloat16* gemm_a = bp.take<__nv_bfloat16>((size_t)S * K);
     double* work = bp.take<double>(4 + 4 * (size_t)S);
-    const long long ncell = cells_of(ctx->Nc());
-    double* spartial = bp.take<double>((size_t)((ncell + 255) / 256) + (size_t)((cells_of(N) + 255) / 256) + 64);
+    double* spartial = bp.take<double>((size_t)level_partial_cap(ctx->Nc(), N));
     double* lvl_nodes = bp.take<double>(2 * (size_t)nodes_of(N));
     char* scratch = bp.p;
     launch_draw_xi(ctx->cfg.seed, iter, level, first_sample + done, S, K, xi, st, ctx->xi_half_width());

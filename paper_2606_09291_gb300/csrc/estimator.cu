@@ -2,6 +2,8 @@
 // differences, Chan statistics and the multilevel step (rows a3, a5, a7-a10).
 #include <math.h>
 
+#include <algorithm>
+
 #include <type_traits>
 
 #include "internal.cuh"
@@ -51,9 +53,10 @@ __global__ void k_rhs_state(const double* __restrict__ z, int Nc, int N, double*
 }
 
 // The same integral for a grid much coarser than the control grid (r = Nc / N >= 8):
-// one block per node reduces over the (2r)^3 control cells of the node's support,
-// cx fastest so a warp reads contiguous control rows.  On cell c of a support the
+// one block per node reduces over the (2r)^3 control cells of the node's support, a
+// warp per control row (cy, cz) with its lanes along cx.  On cell c of a support the
 // hat weight along one axis is 1 - |(c + 1/2) / r - 1|, c = 0 .. 2r-1.
+__device__ __forceinline__ double hat_w(int c, double inv_r) { return 1.0 - fabs((c + 0.5) * inv_r - 1.0); }
 __global__ void __launch_bounds__(kBlock) k_rhs_state_wide(const double* __restrict__ z, int Nc, int N,
                                                            double* __restrict__ b) {
   const int n1 = N + 1;
@@ -66,16 +69,23 @@ __global__ void __launch_bounds__(kBlock) k_rhs_state_wide(const double* __restr
   }
   const int r = Nc / N, w2 = 2 * r;
   const double inv_r = 1.0 / r;
-  const long long cnt = (long long)w2 * w2 * w2;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
   const long long x0 = (long long)r * (i - 1), y0 = (long long)r * (j - 1), z0 = (long long)r * (k - 1);
+  // x weights of this lane's first two columns (w2 <= 64 covers every column)
+  const double wa = lane < w2 ? hat_w(lane, inv_r) : 0.0;
+  const double wb = lane + 32 < w2 ? hat_w(lane + 32, inv_r) : 0.0;
   double acc = 0.0;
-  for (long long e = threadIdx.x; e < cnt; e += blockDim.x) {
-    const int cx = (int)(e % w2);
-    const long long t = e / w2;
-    const int cy = (int)(t % w2), cz = (int)(t / w2);
-    const double w = (1.0 - fabs((cx + 0.5) * inv_r - 1.0)) * (1.0 - fabs((cy + 0.5) * inv_r - 1.0)) *
-                     (1.0 - fabs((cz + 0.5) * inv_r - 1.0));
-    acc += w * z[(x0 + cx) + Nc * ((y0 + cy) + Nc * (z0 + cz))];
+  for (int row = warp; row < w2 * w2; row += nwarp) {
+    const int cy = row % w2, cz = row / w2;
+    const double* zr = z + x0 + Nc * ((y0 + cy) + Nc * (z0 + cz));
+    double rs = 0.0;
+    if (w2 <= 64) {
+      if (lane < w2) rs = wa * zr[lane];
+      if (lane + 32 < w2) rs = fma(wb, zr[lane + 32], rs);
+    } else {
+      for (int cx = lane; cx < w2; cx += 32) rs = fma(hat_w(cx, inv_r), zr[cx], rs);
+    }
+    acc = fma(hat_w(cy, inv_r) * hat_w(cz, inv_r), rs, acc);
   }
   acc = block_sum(acc);
   if (threadIdx.x == 0) {
@@ -530,7 +540,8 @@ __device__ __forceinline__ double gram8(const double* d, double A, double B) {
   for (int e = 0; e < 4; ++e) q += d[e] * (A * u[e] + B * u[e + 4]) + d[e + 4] * (B * u[e] + A * u[e + 4]);
   return q;
 }
-// per level cell: sum_s ||d_s||^2 - S ||mean d||^2 over the cell, block partials
+// per level cell: sum_s ||d_s||^2 - S ||mean d||^2 over the cell, block partials;
+// blockIdx.y takes samples y, y + gridDim.y, ... (the mean term goes with y = 0)
 __global__ void k_lvl_cells(const double* __restrict__ x, int Nf, int S, const double* __restrict__ x0,
                             const double* __restrict__ dsum, double A, double B, double hf3,
                             double* __restrict__ partial) {
@@ -542,53 +553,86 @@ __global__ void k_lvl_cells(const double* __restrict__ x, int Nf, int S, const d
     const int n1 = Nf + 1;
     const long long nodes = (long long)n1 * n1 * n1;
     long long nv[8];
-    double xr[8], db[8];
+    double xr[8];
 #pragma unroll
     for (int v = 0; v < 8; ++v) {
       nv[v] = (ci + (v & 1)) + (long long)n1 * ((cj + ((v >> 1) & 1)) + (long long)n1 * (ck + (v >> 2)));
       xr[v] = x0[nv[v]];
-      db[v] = dsum[nv[v]] / S;
     }
     double acc = 0.0;
-    for (int s = 0; s < S; ++s) {
+    for (int s = blockIdx.y; s < S; s += gridDim.y) {
       const double* xs = x + s * nodes;
       double d[8];
 #pragma unroll
       for (int v = 0; v < 8; ++v) d[v] = xs[nv[v]] - xr[v];
       acc += gram8(d, A, B);
     }
-    contrib = hf3 * (acc - S * gram8(db, A, B));
+    if (blockIdx.y == 0) {
+      double db[8];
+#pragma unroll
+      for (int v = 0; v < 8; ++v) db[v] = dsum[nv[v]] / S;
+      acc -= S * gram8(db, A, B);
+    }
+    contrib = hf3 * acc;
   }
   const double bs = block_sum(contrib);
-  if (threadIdx.x == 0) partial[blockIdx.x] = bs;
+  if (threadIdx.x == 0) partial[blockIdx.x + (long long)gridDim.x * blockIdx.y] = bs;
 }
 // per control cell: batch mean = interpolated nodal mean; Chan merge with the old
-// field; block partials of h_c^3 delta^2 n_old S / n
-__global__ void k_lvl_field(const double* __restrict__ x0, const double* __restrict__ dsum, int Nf, int Nc, int S,
-                            const double* __restrict__ work, double* __restrict__ field, double* __restrict__ partial) {
-  const long long ncell = (long long)Nc * Nc * Nc;
-  const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+// field; block partials of h_c^3 delta^2 n_old S / n.  A block takes kLvlRows rows
+// (cy, cz) of control cells, 256 cells of a row per block in x; per row the
+// level-node columns are first interpolated in (y, z) into shared memory, then each
+// cell interpolates linearly in x between the two columns of its level cell.
+constexpr int kLvlRows = 16;
+__global__ void __launch_bounds__(kBlock) k_lvl_field(const double* __restrict__ x0, const double* __restrict__ dsum,
+                                                      int Nf, int Nc, int S, const double* __restrict__ work,
+                                                      double* __restrict__ field, double* __restrict__ partial) {
+  extern __shared__ double col[];  // [2][Nf + 1]: x0 and dsum interpolated in (y, z)
+  const int n1 = Nf + 1, r = Nc / Nf;
+  const long long sz = (long long)n1 * n1;
+  const double inv_r = 1.0 / r;
+  const double n_old = work[2], scale = work[1];
+  const double n = n_old + S;
+  const double inv_s = 1.0 / S, a = n_old / n;
+  const int cx = blockIdx.x * blockDim.x + threadIdx.x;
+  const int ex = cx / r;
+  const double tx = (cx - ex * r + 0.5) * inv_r;
+  const long long rows = (long long)Nc * Nc;
   double contrib = 0.0;
-  if (c < ncell) {
-    const int cx = (int)(c % Nc), cy = (int)((c / Nc) % Nc), cz = (int)(c / ((long long)Nc * Nc));
-    CellInterp I{};
-    I.setup(Nf, Nc, cx, cy, cz);
-    const double mean = I.eval(x0) + I.eval(dsum) / S;
-    const double n_old = work[2], scale = work[1];
-    const double n = n_old + S;
-    const double mo = (n_old > 0.0) ? field[c] * scale : 0.0;
-    const double delta = mo - mean;
-    field[c] = mean + (n_old / n) * delta;
-    const double hc = 1.0 / Nc;
-    contrib = hc * hc * hc * delta * delta * n_old * S / n;
+  for (long long row = (long long)blockIdx.y * kLvlRows; row < rows && row < (long long)(blockIdx.y + 1) * kLvlRows;
+       ++row) {
+    const int cy = (int)(row % Nc), cz = (int)(row / Nc);
+    const int ey = cy / r, ez = cz / r;
+    const double ty = (cy - ey * r + 0.5) * inv_r, tz = (cz - ez * r + 0.5) * inv_r;
+    __syncthreads();  // the previous row's columns are no longer read
+    for (int c = threadIdx.x; c < n1; c += blockDim.x) {
+      const long long b = c + (long long)n1 * ey + sz * ez;
+      const double w00 = (1.0 - ty) * (1.0 - tz), w10 = ty * (1.0 - tz), w01 = (1.0 - ty) * tz, w11 = ty * tz;
+      col[c] = w00 * x0[b] + w10 * x0[b + n1] + w01 * x0[b + sz] + w11 * x0[b + sz + n1];
+      col[n1 + c] = w00 * dsum[b] + w10 * dsum[b + n1] + w01 * dsum[b + sz] + w11 * dsum[b + sz + n1];
+    }
+    __syncthreads();
+    if (cx < Nc) {
+      const double xv = fma(tx, col[ex + 1] - col[ex], col[ex]);
+      const double dv = fma(tx, col[n1 + ex + 1] - col[n1 + ex], col[n1 + ex]);
+      const double mean = fma(dv, inv_s, xv);
+      const long long c = cx + row * Nc;
+      const double mo = (n_old > 0.0) ? field[c] * scale : 0.0;
+      const double delta = mo - mean;
+      field[c] = fma(a, delta, mean);
+      contrib = fma(delta, delta, contrib);
+    }
   }
+  const double hc = 1.0 / Nc;
+  contrib *= hc * hc * hc * n_old * S / n;
   const double bs = block_sum(contrib);
-  if (threadIdx.x == 0) partial[blockIdx.x] = bs;
+  if (threadIdx.x == 0) partial[blockIdx.x + (long long)gridDim.x * blockIdx.y] = bs;
 }
 
+// returns the number of block partials written (at most level_partial_cap(Nc, Nf))
 template <typename QF, typename QC>
-static void launch_lvl(const void* qf, int Nf, const void* qc, int S, int Nc, const double* work, double* field,
-                       double* partial, double* nodebuf, cudaStream_t st) {
+static int launch_lvl(const void* qf, int Nf, const void* qc, int S, int Nc, const double* work, double* field,
+                      double* partial, double* nodebuf, cudaStream_t st) {
   const long long nodes = nodes_of(Nf), cells = cells_of(Nf), ncell = cells_of(Nc);
   double* x0 = nodebuf;
   double* dsum = nodebuf + nodes;
@@ -607,12 +651,19 @@ static void launch_lvl(const void* qf, int Nf, const void* qc, int S, int Nc, co
   const double* x = (const double*)qf;
   launch("level_nodes", (double)S * nodes * 8 + (double)nodes * 16, k_lvl_nodes, dim3(nbn), kBlock, 0, st, x, nodes,
          S, x0, dsum);
-  const int nbc = (int)((ncell + kBlock - 1) / kBlock);
-  launch("level_field", (double)nodes * 16 + (double)ncell * 16, k_lvl_field, dim3(nbc), kBlock, 0, st,
-         (const double*)x0, (const double*)dsum, Nf, Nc, S, work, field, partial);
-  launch("level_cells", (double)S * nodes * 8 + (double)nodes * 16, k_lvl_cells,
-         dim3((unsigned)((cells + kBlock - 1) / kBlock)), kBlock, 0, st, x, Nf, S, (const double*)x0,
-         (const double*)dsum, A, B, hf * hf * hf, partial + nbc);
+  const unsigned fx = (unsigned)((Nc + kBlock - 1) / kBlock);
+  const unsigned fy = (unsigned)(((long long)Nc * Nc + kLvlRows - 1) / kLvlRows);
+  const long long nf = (long long)fx * fy;
+  launch("level_field", (double)nodes * 16 + (double)ncell * 16, k_lvl_field, dim3(fx, fy), kBlock,
+         (size_t)2 * (Nf + 1) * sizeof(double), st, (const double*)x0, (const double*)dsum, Nf, Nc, S, work, field,
+         partial);
+  // samples spread over blockIdx.y: about 4 blocks per SM, within the partial buffer
+  const long long cb = (cells + kBlock - 1) / kBlock;
+  long long g = std::min<long long>((level_partial_cap(Nc, Nf) - nf) / cb, (4LL * 152 + cb - 1) / cb);
+  g = std::max<long long>(1, std::min<long long>(g, S));
+  launch("level_cells", (double)S * nodes * 8 + (double)nodes * 16, k_lvl_cells, dim3((unsigned)cb, (unsigned)g),
+         kBlock, 0, st, x, Nf, S, (const double*)x0, (const double*)dsum, A, B, hf * hf * hf, partial + nf);
+  return (int)(nf + cb * g);
 }
 
 // s2_dx = old * scale^2 + sum of partials (fixed order, one warp)
@@ -639,10 +690,9 @@ void launch_level_stats(const double* qf, const double* phif, int Nf, const doub
   // grid (cost ~ level nodes and cells per sample instead of control cells per sample;
   // at 2x the control-cell path in pair arithmetic is cheaper).  q_f is overwritten.
   if (nodebuf && 4 * Nf <= Nc) {
-    if (qf_pairs && qc_pairs) launch_lvl<float2, float2>(qf, Nf, qc, S, Nc, work, field, partial, nodebuf, st);
-    else if (qf_pairs) launch_lvl<float2, double>(qf, Nf, qc, S, Nc, work, field, partial, nodebuf, st);
-    else launch_lvl<double, double>(qf, Nf, qc, S, Nc, work, field, partial, nodebuf, st);
-    const int nb = (int)((cells_of(Nc) + kBlock - 1) / kBlock) + (int)((cells_of(Nf) + kBlock - 1) / kBlock);
+    const int nb = (qf_pairs && qc_pairs) ? launch_lvl<float2, float2>(qf, Nf, qc, S, Nc, work, field, partial, nodebuf, st)
+                   : qf_pairs             ? launch_lvl<float2, double>(qf, Nf, qc, S, Nc, work, field, partial, nodebuf, st)
+                                          : launch_lvl<double, double>(qf, Nf, qc, S, Nc, work, field, partial, nodebuf, st);
     launch("level_finish", 0.0, k_level_finish, dim3(1), 32, 0, st, (const double*)partial, nb, (const double*)work,
            scalars);
     return;

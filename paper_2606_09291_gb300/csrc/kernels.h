@@ -51,6 +51,11 @@ struct SolveScalars {
 __host__ __device__ inline long long nodes_of(int N) { return (long long)(N + 1) * (N + 1) * (N + 1); }
 __host__ __device__ inline long long cells_of(int N) { return (long long)N * N * N; }
 inline int node_blocks(int N) { return (int)((nodes_of(N) + 255) / 256); }
+// block partials one level's statistics may write (control-cell blocks + level-cell
+// blocks + slack); the buffer is sized with this and the kernels stay within it
+inline long long level_partial_cap(int Nc, int Nf) {
+  return (cells_of(Nc) + 255) / 256 + (cells_of(Nf) + 255) / 256 + 64;
+}
 
 // Buffers of one batched solve on a grid with N cells per side.  Vectors are
 // [S][nodes] (stride nodes_of(N)), coefficients [S][cells].

@@ -285,3 +285,10 @@ def test_control_much_finer_than_grid(lib, precision, tol):
         for s in range(S):
             assert rel_err(y[s], refs[s]["y"]) <= tol and rel_err(q[s], refs[s]["q"]) <= tol
             assert abs(phi[s] - refs[s]["phi"]) <= tol * abs(refs[s]["phi"])
+    ctx = lib.Context(**dict(CFG, rtol=rtol, max_iter=400, theta=5.0, n_levels=4, ctrl_level=3, precision=precision))
+    W = oracle_workload(theta=5.0, n_levels=4, ctrl_level=3)
+    z = inputs.z_random(64, 3, 20.0)
+    zt = cuda(z)
+    for level, n in ((0, 6), (1, 3)):
+        _compare_stats(_gpu_level(ctx, level, n, zt), _oracle_level(W, level, n, z), W, tol)
+    ctx.close()
