@@ -12,9 +12,11 @@
 
 namespace mlsgd {
 
-// (B z)_n = int z phi_n = h_c^3 sum_c z_c phi_n(x_c) over the control cells c in
-// the support of phi_n (<B u, v> = int u v, Sec. 5; the midpoint rule is exact
-// for the multilinear phi_n on a control cell).  Control grid Nc = N * r.
+// (B z)_n = int z phi_n (<B u, v> = int u v, Sec. 5) for a cellwise-constant control
+// z on the control grid Nc.
+//
+// Control coarser than the grid (N = r Nc): each of the 8 cells around node n lies in
+// one control cell (its parent) and int_e phi_n = h^3 / 8.
 __global__ void k_rhs_state(const double* __restrict__ z, int Nc, int N, double* __restrict__ b) {
   const int n1 = N + 1;
   const long long nodes = (long long)n1 * n1 * n1;
@@ -23,9 +25,7 @@ __global__ void k_rhs_state(const double* __restrict__ z, int Nc, int N, double*
   int i, j, k;
   node_ijk(n, n1, i, j, k);
   double acc = 0.0;
-  if (interior(i, j, k, N) && N > Nc) {
-    // control coarser than the grid: each of the 8 cells around the node lies in one
-    // control cell (its parent) and int_e phi_n = h^3 / 8
+  if (interior(i, j, k, N)) {
     const int r = N / Nc;
     for (int dz = -1; dz <= 0; ++dz)
       for (int dy = -1; dy <= 0; ++dy)
@@ -33,73 +33,65 @@ __global__ void k_rhs_state(const double* __restrict__ z, int Nc, int N, double*
           acc += z[(i + dx) / r + (long long)Nc * ((j + dy) / r + (long long)Nc * ((k + dz) / r))];
     const double h = 1.0 / N;
     acc *= 0.125 * h * h * h;
-  } else if (interior(i, j, k, N)) {
-    const int r = Nc / N;
-    const double inv_r = 1.0 / r;
-    for (int cz = r * (k - 1); cz < r * (k + 1); ++cz) {
-      const double wz = 1.0 - fabs((cz + 0.5) * inv_r - k);
-      for (int cy = r * (j - 1); cy < r * (j + 1); ++cy) {
-        const double wy = 1.0 - fabs((cy + 0.5) * inv_r - j);
-        const double* zr = z + (long long)Nc * (cy + (long long)Nc * cz);
-        double row = 0.0;
-        for (int cx = r * (i - 1); cx < r * (i + 1); ++cx) row += zr[cx] * (1.0 - fabs((cx + 0.5) * inv_r - i));
-        acc += wz * wy * row;
-      }
-    }
-    const double hc = 1.0 / Nc;
-    acc *= hc * hc * hc;
   }
   b[n] = acc;
 }
 
-// The same integral for a grid much coarser than the control grid (r = Nc / N >= 8):
-// one block per node reduces over the (2r)^3 control cells of the node's support, a
-// warp per control row (cy, cz) with its lanes along cx.  On cell c of a support the
-// hat weight along one axis is 1 - |(c + 1/2) / r - 1|, c = 0 .. 2r-1.
-__device__ __forceinline__ double hat_w(int c, double inv_r) { return 1.0 - fabs((c + 0.5) * inv_r - 1.0); }
-__global__ void __launch_bounds__(kBlock) k_rhs_state_wide(const double* __restrict__ z, int Nc, int N,
-                                                           double* __restrict__ b) {
-  const int n1 = N + 1;
-  const int n = blockIdx.x;
-  int i, j, k;
-  node_ijk(n, n1, i, j, k);
-  if (!interior(i, j, k, N)) {
-    if (threadIdx.x == 0) b[n] = 0.0;
+// Control grid at least as fine as the grid (Nc = r N): the midpoint rule on each
+// control cell c is exact for the multilinear phi_n, so (B z)_n = h_c^3 sum_c z_c
+// phi_n(x_c) over the (2r)^3 control cells of the support.  phi_n(x_c) is a product of
+// one hat weight per axis, w(m) = 1 - |(m + 1/2) / r - 1| for the m-th of the 2r control
+// cells along that axis.  One block per node row (j, k): threads along cx contract
+// the (2r)^2 control rows (cy, cz) of the row's support with w(y) w(z) into a column
+// sum per cx, then each node i of the row contracts its 2r columns with w(x).
+__global__ void __launch_bounds__(kBlock) k_rhs_rows(const double* __restrict__ z, int Nc, int N,
+                                                     double* __restrict__ b) {
+  extern __shared__ double sm[];  // w[2r], col[Nc]
+  const int n1 = N + 1, r = Nc / N, w2 = 2 * r;
+  const int j = blockIdx.x, k = blockIdx.y;
+  double* brow = b + (long long)n1 * (j + (long long)n1 * k);
+  if (j == 0 || j == N || k == 0 || k == N) {
+    for (int i = threadIdx.x; i < n1; i += blockDim.x) brow[i] = 0.0;
     return;
   }
-  const int r = Nc / N, w2 = 2 * r;
+  double* w = sm;
+  double* col = sm + w2;
   const double inv_r = 1.0 / r;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
-  const long long x0 = (long long)r * (i - 1), y0 = (long long)r * (j - 1), z0 = (long long)r * (k - 1);
-  // x weights of this lane's first two columns (w2 <= 64 covers every column)
-  const double wa = lane < w2 ? hat_w(lane, inv_r) : 0.0;
-  const double wb = lane + 32 < w2 ? hat_w(lane + 32, inv_r) : 0.0;
-  double acc = 0.0;
-  for (int row = warp; row < w2 * w2; row += nwarp) {
-    const int cy = row % w2, cz = row / w2;
-    const double* zr = z + x0 + Nc * ((y0 + cy) + Nc * (z0 + cz));
-    double rs = 0.0;
-    if (w2 <= 64) {
-      if (lane < w2) rs = wa * zr[lane];
-      if (lane + 32 < w2) rs = fma(wb, zr[lane + 32], rs);
-    } else {
-      for (int cx = lane; cx < w2; cx += 32) rs = fma(hat_w(cx, inv_r), zr[cx], rs);
+  for (int m = threadIdx.x; m < w2; m += blockDim.x) w[m] = 1.0 - fabs((m + 0.5) * inv_r - 1.0);
+  __syncthreads();
+  const long long y0 = (long long)r * (j - 1), z0 = (long long)r * (k - 1);
+  for (int cx = threadIdx.x; cx < Nc; cx += blockDim.x) {
+    double acc = 0.0;
+    for (int mz = 0; mz < w2; ++mz) {
+      const double* zp = z + cx + (long long)Nc * (y0 + (long long)Nc * (z0 + mz));
+      double accz = 0.0;
+      for (int my = 0; my < w2; ++my) accz = fma(w[my], zp[(long long)Nc * my], accz);
+      acc = fma(w[mz], accz, acc);
     }
-    acc = fma(hat_w(cy, inv_r) * hat_w(cz, inv_r), rs, acc);
+    col[cx] = acc;
   }
-  acc = block_sum(acc);
-  if (threadIdx.x == 0) {
-    const double hc = 1.0 / Nc;
-    b[n] = acc * (hc * hc * hc);
+  __syncthreads();
+  const double hc = 1.0 / Nc;
+  const double hc3 = hc * hc * hc;
+  for (int i = threadIdx.x; i < n1; i += blockDim.x) {
+    double v = 0.0;
+    if (i > 0 && i < N) {
+      const double* cp = col + r * (i - 1);
+      for (int m = 0; m < w2; ++m) v = fma(w[m], cp[m], v);
+      v *= hc3;
+    }
+    brow[i] = v;
   }
 }
 
 void launch_rhs_state(const double* z, int Nc, int N, double* b, cudaStream_t st) {
   const double bytes = (double)cells_of(Nc) * 8 + (double)nodes_of(N) * 8;
-  if (Nc >= 8 * N)
-    launch("rhs", bytes, k_rhs_state_wide, dim3((unsigned)nodes_of(N)), kBlock, 0, st, z, Nc, N, b);
-  else
+  if (N > Nc) {
     launch("rhs", bytes, k_rhs_state, dim3(node_blocks(N)), kBlock, 0, st, z, Nc, N, b);
+  } else {
+    const size_t smem = (size_t)(2 * (Nc / N) + Nc) * sizeof(double);
+    launch("rhs", bytes, k_rhs_rows, dim3((unsigned)(N + 1), (unsigned)(N + 1)), kBlock, smem, st, z, Nc, N, b);
+  }
 }
 
 // e = y - g_h with g_h the nodal interpolant of sin(pi x) sin(pi y) sin(pi z);
