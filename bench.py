@@ -124,6 +124,60 @@ def oracle_rate(n_samples, it0=0):
     return n_samples / dt, dt
 
 
+# all host cores: the unchanged oracle over disjoint sample ranges, one process per
+# core (started with spawn: nothing is forked from a process that has used the GPU);
+# each worker builds the operators' static parts before the timed map
+_POOL_STATE = {}
+
+
+def _oracle_worker_init():
+    os.environ["OMP_NUM_THREADS"] = "1"
+    from oracle import mlmc
+    from paper_2606_09291_gb300 import inputs
+    p = inputs.PRESETS["c3"]
+    W = mlmc.Workload(n0=p["n0"], n_levels=p["n_levels"], n_modes=p["n_modes"], corr_len=p["corr_len"],
+                      sigma=p["sigma"], theta=p["theta"], alpha=p["alpha"], seed=p["seed"], rtol=1e-8)
+    W.level(3), W.level(2)
+    _POOL_STATE.update(W=W, z=inputs.z_test(64), mlmc=mlmc)
+
+
+def _oracle_worker_batch(task):
+    it, first, count = task
+    st = _POOL_STATE
+    st["mlmc"].level_batch(st["W"], it, 3, range(first, first + count), st["z"])
+    return count
+
+
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+class OraclePool:
+    """A spawn-started pool of oracle processes, one per host core."""
+
+    def __init__(self, procs):
+        import multiprocessing as mp
+        os.environ.setdefault("OMP_NUM_THREADS", "1")
+        self.procs = procs
+        self.pool = mp.get_context("spawn").Pool(procs, initializer=_oracle_worker_init)
+        self.pool.map(_oracle_worker_batch, [(0, 10 ** 6 + i, 1) for i in range(procs)], chunksize=1)
+
+    def rate(self, per_proc, it0):
+        """Sample-gradients/s over procs * per_proc level-3 samples (wall time of the map)."""
+        tasks = [(it0, i * per_proc, per_proc) for i in range(self.procs)]
+        t = time.perf_counter()
+        n = sum(self.pool.map(_oracle_worker_batch, tasks, chunksize=1))
+        dt = time.perf_counter() - t
+        return n / dt, dt, n
+
+    def close(self):
+        self.pool.close()
+        self.pool.join()
+
+
 def cpu_threads():
     try:
         import numpy  # noqa: F401
@@ -136,20 +190,24 @@ def cpu_threads():
 def run_reference(args, rank):
     if rank != 0:
         return
-    rates, times = [], []
-    for _ in range(args.warmup):
-        oracle_rate(1)
+    procs = host_cores()
+    pool = OraclePool(procs)
+    for k in range(args.warmup):
+        pool.rate(1, it0=1000 + k)
+    times, count = [], 0
     for k in range(args.steps):
-        r, dt = oracle_rate(args.ref_samples, it0=k + 1)
-        rates.append(r)
+        _, dt, n = pool.rate(args.ref_samples, it0=k + 1)
         times.append(dt)
-    value = args.ref_samples * args.steps / sum(times)
-    sample = "%d level-3 samples (+ level-2 partners) of the c3 workload per step, rtol 1e-8" % args.ref_samples
+        count += n
+    pool.close()
+    value = count / sum(times)
+    sample = ("%d level-3 samples (+ level-2 partners) of the c3 workload per step, %d per process on %d "
+              "processes (one per host core), rtol 1e-8" % (args.ref_samples * procs, args.ref_samples, procs))
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": workload_name(args), "reference": "CPU FP64 oracle (numpy/scipy), bounded sample"},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cpu_threads(), "kind": "oracle", "sample": sample},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": procs, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -299,10 +357,19 @@ def run_gpu(args, rank, world):
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        r, dt = oracle_rate(args.cpu_samples)
-        cpu = {"value": r, "unit": UNIT, "cores": cpu_threads(), "kind": "oracle",
-               "sample": "%d level-3 samples (+ level-2 partners) of this workload, rtol 1e-8, %.1f s" % (
-                   args.cpu_samples, dt)}
+        r1, dt1 = oracle_rate(args.cpu_samples)
+        single = {"value": r1, "cores": cpu_threads(),
+                  "sample": "%d level-3 samples (+ level-2 partners) of this workload, rtol 1e-8, %.1f s" % (
+                      args.cpu_samples, dt1)}
+        procs = host_cores()
+        pool = OraclePool(procs)
+        r, dt, n = pool.rate(args.cpu_pool_samples, it0=1)
+        pool.close()
+        cpu = {"value": r, "unit": UNIT, "cores": procs, "kind": "oracle",
+               "sample": "%d level-3 samples (+ level-2 partners) of this workload, %d per process on %d processes "
+                         "(one per host core; batches merged within each process), rtol 1e-8, %.1f s" % (
+                             n, args.cpu_pool_samples, procs, dt),
+               "single_thread": single}
 
     if rank == 0:
         sm = sorted(step_ms)
@@ -338,7 +405,8 @@ def main():
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--fp64-samples", type=int, default=256)
     ap.add_argument("--cpu-samples", type=int, default=6)
-    ap.add_argument("--ref-samples", type=int, default=2)
+    ap.add_argument("--ref-samples", type=int, default=1, help="oracle samples per process per reference step")
+    ap.add_argument("--cpu-pool-samples", type=int, default=2, help="oracle samples per process, all-cores leg")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ir-steps", type=int, default=3,
                     help="mixed path: fixed refinement steps per solve (masked, no host sync); 0 = adaptive")
