@@ -211,8 +211,10 @@ __global__ void __launch_bounds__(NT) k_tiled(TiledArgs A) {
     eok[j] = ehas[j] && ci > 0 && cj > 0 && ci < nc1 - 1 && cj < nc1 - 1;  // coarse interior
     eoff[j] = eok[j] ? ci + nc1 * cj : 0;
   }
-  // POST: coarse plane c is staged once, by issue(2c - 1) (the first fine plane that
-  // needs it is 2c - 1), plus the first derived plane's own coarse plane in the prologue
+  // POST: coarse plane c is staged once, by issue(2c - 2), and interpolated in x and y
+  // by derive(2c - 2), one fine plane before derive(2c - 1) first reads it (the
+  // barrier after each derive separates the two); the prologue stages and
+  // interpolates the planes of the first derived plane
   auto stage_coarse = [&](int c) {
     const bool cok2 = c > 0 && c < nc1 - 1;
 #pragma unroll
@@ -245,32 +247,37 @@ __global__ void __launch_bounds__(NT) k_tiled(TiledArgs A) {
       const bool ok = cmok && cok[j];
       cp_async<kPairs ? 4 : sizeof(TA)>(cs + slot * CPL + cdst[j], a + (ok ? cmo + coff[j] : 0), ok);
     }
-    if (MODE == TM_POST && (m & 1)) stage_coarse((m + 1) >> 1);
+    if (MODE == TM_POST && !(m & 1)) stage_coarse((m >> 1) + 1);
     cp_async_commit();
   };
 
   // POST: eps[c & 1] holds coarse plane c interpolated bilinearly in x and y at this
-  // tile's staged nodes (each thread writes and reads only its own entries, so no
-  // barrier); a fine plane m takes plane m/2 (m even) or the mean of planes (m-1)/2
-  // and (m+1)/2 (m odd), so each coarse plane is interpolated once for two fine planes.
-  int e_have0 = -1000, e_have1 = -1000;  // coarse plane held by eps[0], eps[1]
+  // tile's staged nodes; a fine plane m takes plane m/2 (m even) or the mean of planes
+  // (m-1)/2 and (m+1)/2 (m odd), so each coarse plane is interpolated once for two
+  // fine planes.  The tile origin is even (x0 - 1 = 32 bx, y0 - 1 = TYT by), so staged
+  // node (2a + p, 2b + q) lies in coarse cell (a, b) of the staged coarse tile: one
+  // work item per coarse cell writes its four nodes (odd index: halfway between two
+  // coarse nodes), every staged entry included.
   auto interp_xy = [&](int c) {
     const T* cp = ecs + (c & (ERING - 1)) * EPL;
     T* ed = eps + (c & 1) * NPL;
+    constexpr int AX = EWX - 1, AY = G::EWYT - 1;  // 17 x (TYT/2 + 1) cells cover 34 x (TYT+2) nodes
+    // items NT.. go to the last threads (their warps stage one entry fewer in derive)
+    static_assert(AX * AY <= 2 * NT, "two rounds at most");
 #pragma unroll
-    for (int j = 0; j < MN; ++j) {
-      if (!(nflag[j] & 1)) continue;
-      // every staged entry (halo too, discarded later): bilinear weights from the
-      // node's parities (odd: halfway between two coarse nodes); the neighbour loads
-      // stay inside the staged coarse tile
-      const int b = deb[j];
-      const T wx1 = (nflag[j] & 8) ? T(0.5) : T(0), wy1 = (nflag[j] & 16) ? T(0.5) : T(0);
-      const T wx0 = T(1) - wx1, wy0 = T(1) - wy1;
-      const T r0 = cp[b] * wx0 + cp[b + 1] * wx1;
-      const T r1 = cp[b + EWX] * wx0 + cp[b + EWX + 1] * wx1;
-      ed[tid + j * NT] = r0 * wy0 + r1 * wy1;
+    for (int rd = 0; rd < 2; ++rd) {
+      const int wi = rd == 0 ? tid : 2 * NT - 1 - tid;
+      if (wi >= AX * AY || (rd == 1 && wi < NT)) continue;
+      const int ca = wi % AX, cb = wi / AX;
+      const T* q = cp + ca + EWX * cb;
+      const T e00 = q[0], e10 = q[1], e01 = q[EWX], e11 = q[EWX + 1];
+      const T r0 = (e00 + e10) * T(0.5), r1 = (e01 + e11) * T(0.5);
+      T* o = ed + 2 * ca + NPX * (2 * cb);
+      o[0] = e00;
+      o[1] = r0;
+      o[NPX] = (e00 + e01) * T(0.5);
+      o[NPX + 1] = (r0 + r1) * T(0.5);
     }
-    if (c & 1) e_have1 = c; else e_have0 = c;
   };
 
   // operand plane m from its staged raw plane (slot: its raw ring slot, r3: its xs slot)
@@ -294,13 +301,10 @@ __global__ void __launch_bounds__(NT) k_tiled(TiledArgs A) {
       const T* dvp = dvs + slot * NPL;
       const bool mint = m > 0 && m < N;
       const int dk = m & 1, c0 = m >> 1;
-      if (MODE == TM_POST && mint) {
-        if (((c0 & 1) ? e_have1 : e_have0) != c0) interp_xy(c0);
-        if (dk && (((c0 + 1) & 1) ? e_have1 : e_have0) != c0 + 1) interp_xy(c0 + 1);
-      }
+      // even m: coarse plane m/2 + 1 for the next (odd) plane, into the other eps slot
+      if (MODE == TM_POST && !dk) interp_xy(c0 + 1);
       const T* e0p = eps + (c0 & 1) * NPL;
       const T* e1p = eps + ((c0 + 1) & 1) * NPL;
-      const T w0 = dk ? T(0.5) : T(1), w1 = dk ? T(0.5) : T(0);
 #pragma unroll
       for (int j = 0; j < MN; ++j) {
         if (!(nflag[j] & 1)) continue;
@@ -311,22 +315,28 @@ __global__ void __launch_bounds__(NT) k_tiled(TiledArgs A) {
         T v = omega * rn * dvp[e];
         if (MODE == TM_POST) {
           const T mk = (mint && (nflag[j] & 4)) ? T(1) : T(0);
-          v += mk * (w0 * e0p[e] + w1 * e1p[e]);
+          v += mk * (dk ? (e0p[e] + e1p[e]) * T(0.5) : e0p[e]);
         }
         xp[e] = v;
       }
     }
   };
 
-  if (MODE == TM_POST)  // every E entry is finite before it is first read (masked reads included)
-    for (int e = tid; e < 2 * NPL; e += NT) eps[e] = T(0);
   // prologue: derive the planes before kbeg, keep two planes in flight
   const int first_plane = kPre ? kbeg - 2 : kbeg - 1;
   auto mod5 = [](int m) { return (m + 2 * RING) % RING; };
-  if (MODE == TM_POST) stage_coarse(first_plane >> 1);  // committed with the first issue below
+  if (MODE == TM_POST) {  // committed with the first issue below
+    stage_coarse(first_plane >> 1);
+    if (first_plane & 1) stage_coarse((first_plane >> 1) + 1);
+  }
   for (int m = first_plane; m <= kbeg + 2; ++m) issue(m, mod5(m));
   cp_async_wait<2>();
   __syncthreads();
+  if (MODE == TM_POST) {
+    interp_xy(first_plane >> 1);
+    if (first_plane & 1) interp_xy((first_plane >> 1) + 1);
+    __syncthreads();
+  }
   for (int m = first_plane; m <= kbeg; ++m) {
     derive(m, mod5(m), ring3(m));
     __syncthreads();
