@@ -217,11 +217,11 @@ __global__ void __launch_bounds__(NT) k_tiled(TiledArgs A) {
   // interpolates the planes of the first derived plane
   auto stage_coarse = [&](int c) {
     const bool cok2 = c > 0 && c < nc1 - 1;
+    const T* eb = e0 + (cok2 ? c * pe : 0);  // a plane inside the buffer; invalid entries are zero-filled
 #pragma unroll
     for (int j = 0; j < ME; ++j) {
       if (!ehas[j]) continue;
-      const bool ok = cok2 && eok[j];
-      cp_async<sizeof(T)>(ecs + (c & (ERING - 1)) * EPL + tid + j * NT, e0 + (ok ? c * pe + eoff[j] : 0), ok);
+      cp_async<sizeof(T)>(ecs + (c & (ERING - 1)) * EPL + tid + j * NT, eb + eoff[j], cok2 && eok[j]);
     }
   };
 
@@ -229,23 +229,28 @@ __global__ void __launch_bounds__(NT) k_tiled(TiledArgs A) {
     // every node vector here is zero on the Dirichlet boundary: boundary nodes are
     // zero-filled like nodes outside the grid, so no buffer's boundary is ever read
     const bool mok = m > 0 && m < N;
+    // plane bases inside the buffers (plane 0 when m is outside); every staged offset
+    // lies inside a plane, so each source address is valid and the flag alone decides
+    // between a copy and a zero fill
     const long long mo = mok ? (long long)m * pn : 0;
+    const T* b0 = in0 + mo;
+    const T* b1 = in1 + mo;
+    const T* bd = dvg + mo;
 #pragma unroll
     for (int j = 0; j < MN; ++j) {
       if (!(nflag[j] & 1)) continue;
       const int e = tid + j * NT;
       const bool ok = mok && (nflag[j] & 4);
-      cp_async<sizeof(T)>(raw0 + slot * NPL + e, in0 + (ok ? mo + noff[j] : 0), ok);
-      if (stage1) cp_async<sizeof(T)>(raw1 + slot * NPL + e, in1 + (ok ? mo + noff[j] : 0), ok);
-      if (kPre) cp_async<sizeof(T)>(dvs + slot * NPL + e, dvg + (ok ? mo + noff[j] : 0), ok);
+      cp_async<sizeof(T)>(raw0 + slot * NPL + e, b0 + noff[j], ok);
+      if (stage1) cp_async<sizeof(T)>(raw1 + slot * NPL + e, b1 + noff[j], ok);
+      if (kPre) cp_async<sizeof(T)>(dvs + slot * NPL + e, bd + noff[j], ok);
     }
     const bool cmok = m >= 0 && m < N;
-    const long long cmo = cmok ? (long long)m * pc : 0;
+    const TA* ab = a + (cmok ? (long long)m * pc : 0);
 #pragma unroll
     for (int j = 0; j < MC; ++j) {
       if (!chas[j]) continue;
-      const bool ok = cmok && cok[j];
-      cp_async<kPairs ? 4 : sizeof(TA)>(cs + slot * CPL + cdst[j], a + (ok ? cmo + coff[j] : 0), ok);
+      cp_async<kPairs ? 4 : sizeof(TA)>(cs + slot * CPL + cdst[j], ab + coff[j], cmok && cok[j]);
     }
     if (MODE == TM_POST && !(m & 1)) stage_coarse((m >> 1) + 1);
     cp_async_commit();
