@@ -142,6 +142,8 @@ __global__ void __launch_bounds__(NT) k_tiled(TiledArgs A) {
   constexpr bool kPairs = sizeof(TA) == 2;                 // BF16 cells staged as 4-byte pairs
   constexpr int NCE = kPairs ? CPL / 2 : CPL;              // cell staging entries per plane
   constexpr int MN = (NPL + NT - 1) / NT, MC = (NCE + NT - 1) / NT, ME = (EPL + NT - 1) / NT;
+  // staging entries j < M - 1 always exist (only the last one per thread may not)
+  static_assert((MN - 1) * NT < NPL && (MC - 1) * NT < NCE && (ME - 1) * NT < EPL, "staging entries");
   extern __shared__ __align__(16) unsigned char smraw[];
   T* raw0 = (T*)(smraw + L::raw0);
   T* raw1 = (T*)(smraw + L::raw1);
@@ -220,7 +222,7 @@ __global__ void __launch_bounds__(NT) k_tiled(TiledArgs A) {
     const T* eb = e0 + (cok2 ? c * pe : 0);  // a plane inside the buffer; invalid entries are zero-filled
 #pragma unroll
     for (int j = 0; j < ME; ++j) {
-      if (!ehas[j]) continue;
+      if (j == ME - 1 && !ehas[j]) continue;
       cp_async<sizeof(T)>(ecs + (c & (ERING - 1)) * EPL + tid + j * NT, eb + eoff[j], cok2 && eok[j]);
     }
   };
@@ -238,7 +240,7 @@ __global__ void __launch_bounds__(NT) k_tiled(TiledArgs A) {
     const T* bd = dvg + mo;
 #pragma unroll
     for (int j = 0; j < MN; ++j) {
-      if (!(nflag[j] & 1)) continue;
+      if (j == MN - 1 && !(nflag[j] & 1)) continue;
       const int e = tid + j * NT;
       const bool ok = mok && (nflag[j] & 4);
       cp_async<sizeof(T)>(raw0 + slot * NPL + e, b0 + noff[j], ok);
@@ -249,7 +251,7 @@ __global__ void __launch_bounds__(NT) k_tiled(TiledArgs A) {
     const TA* ab = a + (cmok ? (long long)m * pc : 0);
 #pragma unroll
     for (int j = 0; j < MC; ++j) {
-      if (!chas[j]) continue;
+      if (j == MC - 1 && !chas[j]) continue;
       cp_async<kPairs ? 4 : sizeof(TA)>(cs + slot * CPL + cdst[j], ab + coff[j], cmok && cok[j]);
     }
     if (MODE == TM_POST && !(m & 1)) stage_coarse((m >> 1) + 1);
@@ -293,7 +295,7 @@ __global__ void __launch_bounds__(NT) k_tiled(TiledArgs A) {
       const T* r1 = raw1 + slot * NPL;
 #pragma unroll
       for (int j = 0; j < MN; ++j) {
-        if (!(nflag[j] & 1)) continue;
+        if (j == MN - 1 && !(nflag[j] & 1)) continue;
         const int e = tid + j * NT;
         xp[e] = A.first ? r0[e] : r0[e] + beta * r1[e];
       }
@@ -301,7 +303,7 @@ __global__ void __launch_bounds__(NT) k_tiled(TiledArgs A) {
       // x is already an (hi, lo) pair: copy the 8-byte word
 #pragma unroll
       for (int j = 0; j < MN; ++j)
-        if (nflag[j] & 1) xp[tid + j * NT] = r0[tid + j * NT];
+        if (j < MN - 1 || (nflag[j] & 1)) xp[tid + j * NT] = r0[tid + j * NT];
     } else {
       const T* dvp = dvs + slot * NPL;
       const bool mint = m > 0 && m < N;
@@ -312,7 +314,7 @@ __global__ void __launch_bounds__(NT) k_tiled(TiledArgs A) {
       const T* e1p = eps + ((c0 + 1) & 1) * NPL;
 #pragma unroll
       for (int j = 0; j < MN; ++j) {
-        if (!(nflag[j] & 1)) continue;
+        if (j == MN - 1 && !(nflag[j] & 1)) continue;
         const int e = tid + j * NT;
         // branch-free: D^-1 is 0 on the boundary and zero-filled outside the grid (and
         // so is r outside 0 < m < N), so only the coarse correction needs a mask
@@ -378,7 +380,7 @@ __global__ void __launch_bounds__(NT) k_tiled(TiledArgs A) {
     if (MODE == TM_APPLYX) {
 #pragma unroll
       for (int t = 0; t < RY; ++t)
-        xv[t] = (colok && gj0 + t < N && !A.xfirst) ? xio[(long long)n1 * n1 * k + (long long)n1 * t] : T(0);
+        xv[t] = (colok && gj0 + t < N && !A.xfirst) ? xio[pn * k + n1 * t] : T(0);
     }
     issue(k + 3, s5p3);
     cp_async_wait<2>();
@@ -453,7 +455,7 @@ __global__ void __launch_bounds__(NT) k_tiled(TiledArgs A) {
           const F2 axs = two_sum(S, comp);
           const float p = axs.h * sch;
           const float pe = __fmaf_rn(axs.h, scl, __fmaf_rn(axs.l, sch, __fmaf_rn(axs.h, sch, -p)));
-          const long long o = (long long)n1 * n1 * k + (long long)n1 * t;
+          const long long o = pn * k + n1 * t;
           const float2 bv = reinterpret_cast<const float2*>(bptr)[o];
           const F2 d = two_sum(bv.x, -p);
           const float rv = d.h + (d.l + (bv.y - pe));
@@ -520,7 +522,7 @@ __global__ void __launch_bounds__(NT) k_tiled(TiledArgs A) {
           accp[pl] = a2;
         }
         const T ax = scale * (accp[1] + (accp[0] + accp[2]));
-        const long long o = (long long)n1 * n1 * k + (long long)n1 * t;
+        const long long o = pn * k + n1 * t;
         if (kApply) {
           const T pv = X[1][1][t + 1];
           out0[o] = ax;
