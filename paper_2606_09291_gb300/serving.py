@@ -117,6 +117,10 @@ class ContinuousServer:
         # limit beyond the slots, whose scratch is already reserved)
         self.budget = float("inf") if hbm_budget is None else hbm_budget
 
+    @staticmethod
+    def _new_event():
+        return torch.cuda.Event(enable_timing=True)
+
     def close(self):
         for s in self.slots:
             s["ctx"].close()
@@ -127,9 +131,14 @@ class ContinuousServer:
     def run(self, requests, z, keep=False):
         """requests: list of (arrival_s, estimate_id, level, n), sorted by arrival.
         Returns one dict per request (arrival, start, done, latency_ms, service_ms) and,
-        with keep, copies of the level records (field, scalars)."""
+        with keep, copies of the level records (field, scalars).  A request whose
+        workspace alone exceeds the HBM budget could never be admitted: ValueError."""
         import collections
         import time
+        for (a, eid, level, n) in requests:
+            if self.footprint(level, n) > self.budget:
+                raise ValueError("request (estimate %d, level %d, %d samples) needs %d workspace bytes, over the "
+                                 "budget of %d" % (eid, level, n, self.footprint(level, n), self.budget))
         pending = collections.deque(range(len(requests)))
         queue = collections.deque()
         out = [None] * len(requests)
@@ -164,11 +173,11 @@ class ContinuousServer:
                 queue.popleft()
                 in_flight += fp
                 st = s["stats"][level]
-                s["e0"] = torch.cuda.Event(enable_timing=True)
+                s["e0"] = self._new_event()
                 s["e0"].record(s["stream"])
                 s["ctx"].mlsgd_stats_reset(st, stream=s["stream"])
                 s["ctx"].mlsgd_level_gradient(eid, level, 0, n, z, st, stream=s["stream"])
-                s["ev"] = torch.cuda.Event(enable_timing=True)
+                s["ev"] = self._new_event()
                 s["ev"].record(s["stream"])
                 s["req"], s["t0"] = i, now
             if not queue or all(s["req"] is not None for s in self.slots):
