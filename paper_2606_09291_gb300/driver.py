@@ -24,6 +24,10 @@ def fixed_step(alpha):
     return 0.5 / (alpha + (3.0 * math.pi ** 2) ** -2)
 
 
+def _event():
+    return torch.cuda.Event(enable_timing=True)
+
+
 def _slope(ls, vals):
     """Least-squares slope of log2(vals) against ls (NaN with fewer than two points)."""
     if len(ls) < 2:
@@ -63,14 +67,14 @@ def run_mlsgd(ctx, z, counts, iterations, tau, eta=0.9, max_levels=None, adapt=T
     stats = [ctx.new_stats(l) for l in range(ctx.cfg["n_levels"])]
     g_prev = torch.zeros_like(z) if step == "adaptive" else None
     tau_prev = 0.0
-    strm = stream if stream is not None else torch.cuda.current_stream()
+    strm = stream if stream is not None or not time_levels else torch.cuda.current_stream()
     t0 = time.perf_counter()
     for k in range(iterations):
         level_ms = []
         for l, m in enumerate(counts):
             ctx.mlsgd_stats_reset(stats[l], stream=stream)
             if time_levels:
-                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0, e1 = _event(), _event()
                 e0.record(strm)
             ctx.mlsgd_level_gradient(k, l, 0, m, z, stats[l], stream=stream)
             if time_levels:
