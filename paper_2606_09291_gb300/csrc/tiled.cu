@@ -813,5 +813,7 @@ template void tiled_post<double, double>(const double*, const double*, const dou
 }  // namespace mlsgd
 
 namespace mlsgd {
-int tiled_blocks_per_sample(int N, int S, int elem) { return tiled_shape(N, S, elem == 8 ? 2 : 4).blocks_per_sample; }
+int tiled_blocks_per_sample(int N, int S, int elem) {
+  return tiled_shape(N, S, elem == 8 ? RowsPerThread<double>::value : RowsPerThread<float>::value).blocks_per_sample;
+}
 }  // namespace mlsgd
