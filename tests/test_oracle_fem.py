@@ -128,7 +128,7 @@ def test_solvers_agree():
     assert it0 == 0 and not np.any(x0)
 
 
-@pytest.mark.parametrize("N,Nc", [(8, 4), (8, 2), (4, 8), (4, 4)])
+@pytest.mark.parametrize("N,Nc", [(8, 4), (8, 2), (4, 8), (4, 4), (4, 16), (2, 16)])
 def test_control_cell_averages(N, Nc):
     """I[c, n] = average of phi_n over control cell c, both when the control grid is
     finer and when it is coarser than the level: partition of unity, exact averages
@@ -149,3 +149,22 @@ def test_control_cell_averages(N, Nc):
         assert np.abs(I @ (x * x) - (mean_x2 + h * h / 6)).max() < 1e-14
     b = (1.0 / Nc) ** 3 * (I.T @ np.ones(Nc ** 3))
     assert np.abs(b[lev.interior] - (1.0 / N) ** 3).max() < 1e-17
+
+
+@pytest.mark.parametrize("N,Nc", [(4, 4), (4, 8), (4, 16), (4, 32), (2, 16)])
+def test_rhs_closed_form_fine_control(N, Nc):
+    """(B z)_n = h_c^3 sum_c z_c phi_n(x_c) for a control r = Nc / N times finer than
+    the grid.  The hat weights of a node's 2r control cells per axis sum to r and are
+    symmetric about the node, so for z_c = x_c y_c z_c (cell centres) every interior
+    node gets exactly h^3 x_i y_j z_k, and for z_c = 1 exactly h^3."""
+    lev = fem.Level(N)
+    I = lev.interpolation(Nc)
+    c = np.arange(Nc ** 3)
+    xc, yc, zc = (c % Nc + 0.5) / Nc, ((c // Nc) % Nc + 0.5) / Nc, (c // Nc ** 2 + 0.5) / Nc
+    x, y, z = lev.node_coords()
+    hc3, h3 = (1.0 / Nc) ** 3, (1.0 / N) ** 3
+    b = hc3 * (I.T @ (xc * yc * zc))
+    assert np.abs(b[lev.interior] - h3 * (x * y * z)[lev.interior]).max() < 1e-16
+    b1 = hc3 * (I.T @ np.ones(Nc ** 3))
+    assert np.abs(b1[lev.interior] - h3).max() < 1e-17
+
