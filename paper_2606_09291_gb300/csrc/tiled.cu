@@ -1,15 +1,18 @@
 // tiled.cu - z-marching shared-memory kernels for the fine-grid passes of the
 // solver (rows a4, a6) and for Phi / the adjoint right-hand side (row a5).
 //
-// Layout: a block of 32 x 8 threads owns a 32 x 8 tile of interior nodes
-// (x0 = 1 + 32 bx, y0 = 1 + 8 by) and marches along z over a chunk of interior
-// planes.  Each node plane of an input vector is staged once into shared
-// memory with a one-node halo (34 x 10), each cell plane with a two-cell halo
-// (35 x 11); three planes of each are kept in a ring.  So every value is read
-// from HBM about once per pass (halos come from L2) and there is no integer
-// division in the index arithmetic.  Node (lx, ly) of the staged plane is the
-// global node (x0 - 1 + lx, y0 - 1 + ly); its eight surrounding cells are the
-// staged cells (lx + p, ly + q), p, q in {0, 1}, of two cell planes.
+// Layout: a block of 32 x 8 threads owns a 32 x 8 RY tile of interior nodes (RY
+// rows per thread: 4 for FP32 vectors, 2 for FP64; x0 = 1 + 32 bx, y0 = 1 + 8 RY by)
+// and marches along z over a chunk of interior planes.  Each node plane of an
+// input vector is staged once into shared memory with a one-node halo
+// (34 x (8 RY + 2)), each cell plane with a two-cell halo (36 x (8 RY + 3), from an
+// even x start), with cp.async into a five-plane ring that keeps two planes in
+// flight ahead of the stencil; the operand planes derived from them (three
+// planes) are kept in their own ring.  So every value is read from HBM about
+// once per pass (halos come from L2) and there is no integer division in the
+// index arithmetic.  Node (lx, ly) of the staged plane is the global node
+// (x0 - 1 + lx, y0 - 1 + ly); its eight surrounding cells are the staged cells
+// (lx + p, ly + q), p, q in {0, 1}, of two cell planes.
 //
 // Fused passes (FE operator A: see q1_row in internal.cuh; D = (h/3) sum_8 a, whose
 // inverse is precomputed per coefficient hierarchy and staged like a vector):
@@ -21,7 +24,8 @@
 //   RES64 : r = b - A x to FP64 accuracy in FP32 arithmetic: x and b are FP32 (hi, lo)
 //           pairs (staged as 8-byte words), a is FP32; writes r rounded to FP32 and the
 //           partial r.r
-// Vectors keep zero boundary nodes; only interior nodes are written.
+// The fused passes write only interior nodes and zero-fill boundary nodes at staging
+// (like nodes outside the grid), so they never read a buffer's boundary values.
 #include <cstdio>
 
 #include "internal.cuh"
@@ -31,8 +35,8 @@
 namespace mlsgd {
 
 constexpr int TX = 32, TY = 8;
-constexpr int NPX = TX + 2, NPY = TY + 2, NP = NPX * NPY;  // node plane 34 x 10
-constexpr int CPX = TX + 3, CPY = TY + 3, CP = CPX * CPY;  // cell plane 35 x 11
+constexpr int NPX = TX + 2;                     // staged node row: 34 nodes
+constexpr int NPY = TY + 2, NP = NPX * NPY;      // the Phi kernels' staged plane (one row per thread): 34 x 10
 constexpr int NT = TX * TY;
 
 enum TiledMode { TM_APPLY = 0, TM_PRE = 1, TM_POST = 2, TM_RES64 = 3, TM_PREU = 4, TM_APPLYX = 5 };
