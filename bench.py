@@ -26,11 +26,11 @@ sys.path.insert(0, ROOT)
 
 METRIC = "sample-gradients/s (state+adjoint) at rtol 1e-8 vs plain FP64; p99 latency"
 # DRAM bytes (read + write) over algorithmic bytes of the dominant kernel class, from
-# one ncu capture of its 64^3 fine launch on 256 samples of this workload (inputs
+# one ncu capture of its 64^3 fine launch on a smaller batch of this workload (inputs
 # larger than L2); a full launch processes more samples of the same grid, so its
 # traffic is this ratio times its algorithmic bytes.  Only valid for the kernel as
-# captured: update it with each change of that kernel.
-TRAFFIC_RATIO = {"post_f32": 0.983}
+# captured: emptied with each change of that kernel until it is captured again.
+TRAFFIC_RATIO = {}
 UNIT = "sample-gradients/s"
 
 
@@ -308,23 +308,31 @@ def run_gpu(args, rank, world):
         e2e_ms = float(t.item())
     e2e_value = S * world * e2e_steps / (e2e_ms / 1e3)
 
-    # plain FP64 path on a subset of the same workload (the metric's comparison)
+    # plain FP64 path on the same batch (the metric's "vs plain FP64"): same sample
+    # count per step, one warm-up step, then fp64_steps timed steps between barriers
     fp64 = None
     if args.fp64_samples > 0 and args.precision == "mixed":
-        c64 = dict(cfg, precision="fp64", max_batch=args.fp64_samples, max_iter=200)
+        c64 = dict(cfg, precision="fp64", max_batch=min(args.fp64_chunk, args.fp64_samples), max_iter=200)
         ctx64 = mlsgd.Context(**c64)
         st64 = ctx64.new_stats(level)
         ctx64.mlsgd_level_gradient(0, level, first, args.fp64_samples, z, st64)  # warm-up
-        torch.cuda.synchronize()
-        f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        f0.record(stream)
-        ctx64.mlsgd_stats_reset(st64)
-        ctx64.mlsgd_level_gradient(1, level, first, args.fp64_samples, z, st64)
-        f1.record(stream)
-        torch.cuda.synchronize()
-        ms64 = f0.elapsed_time(f1)
-        fp64 = {"value": args.fp64_samples / (ms64 / 1e3), "unit": UNIT, "samples": args.fp64_samples,
-                "ms": ms64, "iters_per_sample": st64.host()["iters"] / args.fp64_samples}
+        barrier()
+        fev = [torch.cuda.Event(enable_timing=True) for _ in range(args.fp64_steps + 1)]
+        fev[0].record(stream)
+        for k in range(args.fp64_steps):
+            ctx64.mlsgd_stats_reset(st64)
+            ctx64.mlsgd_level_gradient(1 + k, level, first, args.fp64_samples, z, st64)
+            fev[k + 1].record(stream)
+        barrier()
+        ms64 = fev[0].elapsed_time(fev[-1])
+        if world > 1:
+            t = torch.tensor([ms64], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms64 = float(t.item())
+        fp64 = {"value": args.fp64_samples * world * args.fp64_steps / (ms64 / 1e3), "unit": UNIT,
+                "samples_per_step": args.fp64_samples, "steps": args.fp64_steps, "chunk": c64["max_batch"],
+                "ms_per_step": ms64 / args.fp64_steps,
+                "iters_per_sample": st64.host()["iters"] / args.fp64_samples}
         ctx64.close()
 
     peaks, peak_kind = load_peaks()
@@ -388,14 +396,14 @@ def run_gpu(args, rank, world):
                 "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": z.numel() * 8,
                         "d2h_bytes_per_step": (stats.field.numel() + mlsgd.NSCALARS) * 8},
                 "gpu_launches": gpu_launches, "clocks": clocks, "fp64_path": fp64,
-                "mixed_over_fp64": (value / world / fp64["value"]) if fp64 else None,
+                "mixed_over_fp64": (value / fp64["value"]) if fp64 else None,
                 "kernel_shares": {k: round(v["total_ms"] / total_prof, 4) for k, v in
                                   sorted(prof_all.items(), key=lambda kv: -kv[1]["total_ms"])[:8]}}
         print(json.dumps(line), flush=True)
     ctx.close()
 
 
-def main():
+def parser():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
@@ -403,16 +411,24 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--samples", type=int, default=4096)
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
-    ap.add_argument("--fp64-samples", type=int, default=256)
+    ap.add_argument("--fp64-samples", type=int, default=4096,
+                    help="samples per step of the plain FP64 leg (same batch as the mixed arm by default)")
+    ap.add_argument("--fp64-steps", type=int, default=3)
+    ap.add_argument("--fp64-chunk", type=int, default=1024, help="FP64 leg: samples per internal chunk")
     ap.add_argument("--cpu-samples", type=int, default=6)
     ap.add_argument("--ref-samples", type=int, default=1, help="oracle samples per process per reference step")
     ap.add_argument("--cpu-pool-samples", type=int, default=2, help="oracle samples per process, all-cores leg")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--ir-steps", type=int, default=3,
-                    help="mixed path: fixed refinement steps per solve (masked, no host sync); 0 = adaptive")
+    ap.add_argument("--ir-steps", type=int, default=0,
+                    help="mixed path: 0 = refine until converged, launching only the samples still above rtol "
+                         "(host check per step); k > 0 = exactly k masked steps (no host sync)")
     ap.add_argument("--traffic-bytes", type=float, default=None,
                     help="ncu dram read+write bytes per launch of the dominant kernel, if captured")
-    args = ap.parse_args()
+    return ap
+
+
+def main():
+    args = parser().parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     if world > 1:

@@ -80,7 +80,9 @@ typedef struct {
                        tensor cores (tcgen05 GEMM, BF16 in / FP32 accumulate); 0 = rounded
                        from the FP64 synthesis                                        */
   int ir_steps;     /* MIXED only: 0 = refine until converged, checking on the host after
-                       each step; k > 0 = exactly k refinement steps per solve with no host
+                       each step (the samples still above rtol are compacted into a list and
+                       only they are launched in the next step; the FP64 path does the same
+                       at its host checks); k > 0 = exactly k refinement steps per solve with no host
                        synchronisation (per-sample masks; a sample still above rtol after k
                        steps gets status 1).  With k > 0 and the scratch already sized (one
                        earlier call of the same size), mlsgd_level_gradient enqueues only
@@ -198,8 +200,10 @@ mlsgd_status mlsgd_sample_field_tc(mlsgd_ctx* ctx, int iter, int level, int grid
  * Inputs: log_a_dev [n_samples][N^3], z_dev [n_ctrl_cells].
  * Outputs: y_dev, q_dev [n_samples][(N+1)^3]; phi_dev [n_samples];
  * iters_dev [n_samples] PCG iterations (FP64) or inner iterations (MIXED),
- * state + adjoint; status_dev [n_samples] 0 = converged, 1 = hit max_iter.
- * Returns MLSGD_ENOCONV (after writing every output) if any solve hit max_iter. */
+ * state + adjoint; status_dev [n_samples] 0 = converged, bit 0 (1) = a solve hit
+ * max_iter, bit 1 (2) = a solve went non-finite (NaN/Inf in z or the coefficient).
+ * After writing every output, returns MLSGD_ENONFINITE if any sample has bit 1,
+ * else MLSGD_ENOCONV if any has bit 0.  SYNCHRONOUS (reads the flags back). */
 mlsgd_status mlsgd_solve_state_adjoint(mlsgd_ctx* ctx, int grid, int n_samples, const double* log_a_dev,
                                        const double* z_dev, double* y_dev, double* q_dev, double* phi_dev,
                                        int* iters_dev, int* status_dev, void* stream);
@@ -214,22 +218,25 @@ mlsgd_status mlsgd_solve_state_adjoint(mlsgd_ctx* ctx, int grid, int n_samples, 
 mlsgd_status mlsgd_level_gradient(mlsgd_ctx* ctx, int iter, int level, int64_t first_sample, int n_samples,
                                   const double* z_dev, mlsgd_level_stats* stats, void* stream);
 
-/* Allocation-free variant of mlsgd_solve_state_adjoint (the paper has no
- * counterpart; it exists for callers that must not allocate device memory,
- * for example code in a host callback or real-time loop where cudaMalloc's
- * implicit synchronisation is forbidden, or an application whose own pool owns
- * all device memory).  Same arguments, layouts and results as
- * mlsgd_solve_state_adjoint, but every scratch buffer comes from one static
- * device array of MLSGD_NOALLOC_SCRATCH_BYTES compiled into the library, which
- * each GPU that loads the library holds until the process exits; the call
- * makes no cudaMalloc/cudaFree.  A batch whose scratch would not fit is
- * rejected with MLSGD_EINVAL and a message giving the bytes it needs (about
- * 6 samples of a 32^3 grid or 40 of a 16^3 grid in FP64).  The first call on
- * each device looks up the array's device address (cudaGetSymbolAddress) with
- * that device current; make that first call before any stream capture.  All
- * calls share the array and it keeps the last call's contents: calls that
- * overlap on the GPU (other streams, other threads, other contexts) race, so
- * serialise them.  Nothing in the array needs to start at zero. */
+/* Allocation-free variant of mlsgd_solve_state_adjoint.  The paper has no
+ * counterpart: it exists for callers that cannot allocate device memory when they
+ * need a solve, for example a latency-critical loop in which cudaMalloc's implicit
+ * device-wide synchronisation is not acceptable, or an application whose own
+ * allocator has reserved the device memory and does not let libraries call the
+ * CUDA allocator.  Same arguments, layouts, results and status codes as
+ * mlsgd_solve_state_adjoint, but every scratch buffer comes from one static device
+ * array of MLSGD_NOALLOC_SCRATCH_BYTES compiled into the library, which each GPU
+ * that loads the library holds until the process exits; the call makes no
+ * cudaMalloc/cudaFree and calls no allocating library routine.  A batch whose
+ * scratch would not fit is rejected with MLSGD_EINVAL and a message giving the
+ * bytes it needs (about 6 samples of a 32^3 grid or 40 of a 16^3 grid in FP64).
+ * The first call on each device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call before
+ * any stream capture.  The call waits for its stream before it returns (it reads
+ * back one status word).  All calls share the array and it keeps the last call's
+ * contents: calls that overlap on the GPU (other streams, other threads, other
+ * contexts) race, so serialise them.  Nothing in the array needs to start at
+ * zero: the solve writes every buffer before it reads it. */
 #define MLSGD_NOALLOC_SCRATCH_BYTES (16u << 20)
 mlsgd_status mlsgd_solve_state_adjoint_noalloc(mlsgd_ctx* ctx, int grid, int n_samples, const double* log_a_dev,
                                                const double* z_dev, double* y_dev, double* q_dev, double* phi_dev,

@@ -145,6 +145,21 @@ def pairwise_reduce(items, hc3):
     return items[0]
 
 
+def merge_shifted(records, theta, hc3):
+    """Merge level records kept at different shifts (each a dict(stats, shift) as
+    level_batch returns): every record is rescaled to the largest shift c* (means by
+    exp(theta (c - c*)), second-order sums by its square; X~ and Y~ carry the factor
+    exp(-theta c)) and the rescaled records are merged pairwise (Algorithm 1,
+    PairwiseUpdate).  Returns dict(stats, shift)."""
+    cstar = max(r["shift"] for r in records)
+    items = []
+    for r in records:
+        f = np.exp(theta * (r["shift"] - cstar))
+        S = r["stats"]
+        items.append(Stats(S.n, S.mean_x * f, S.s2_x * f * f, S.mean_y * f, S.s2_y * f * f))
+    return dict(stats=pairwise_reduce(items, hc3), shift=cstar)
+
+
 def level_batch(W, iteration, level, samples, z, shift=None, xi_level=None):
     """Samples of one level: per-sample records and their merged statistics.
 

@@ -104,7 +104,7 @@ size_t level_bytes(const mlsgd_ctx* ctx, int level, int S) {
   b += 2 * al((size_t)2 * S * 4);
   b += al(kl_gemm_a_bytes(S, ctx->cfg.n_modes));
   b += solve_scratch_bytes(ctx, N, S);
-  b += al((4 + 4 * (size_t)S) * 8) + al((size_t)level_partial_cap(ctx->Nc(), N) * 8);
+  b += al((4 + 2 * (size_t)S) * 8) + al((size_t)level_partial_cap(ctx->Nc(), N) * 8);
   b += al(2 * (size_t)nodes_of(N) * 8);
   return b;
 }
@@ -138,6 +138,9 @@ GridFields carve_fields(const mlsgd_ctx* ctx, int N, int S, Bump& bp) {
   return f;
 }
 
+// Per-sample status flags: 1 = a solve hit its iteration cap, 2 = a solve went
+// non-finite (NaN/Inf right-hand side or iterate); the state and adjoint flags of a
+// sample are OR-ed.
 __global__ void k_record(const SolveScalars* __restrict__ sc, int S, int mixed, int* __restrict__ iters,
                          int* __restrict__ status, int accumulate) {
   const int s = blockIdx.x * blockDim.x + threadIdx.x;
@@ -146,6 +149,28 @@ __global__ void k_record(const SolveScalars* __restrict__ sc, int S, int mixed, 
   const int stv = sc[s].status;
   iters[s] = accumulate ? iters[s] + it : it;
   status[s] = accumulate ? (status[s] | stv) : stv;
+}
+
+// OR of the S per-sample status flags into *out (one block of kAnyBlock threads)
+constexpr int kAnyBlock = 256;
+__global__ void k_status_any(const int* __restrict__ status, int S, int* __restrict__ out) {
+  int v = 0;
+  for (int s = threadIdx.x; s < S; s += blockDim.x) v |= status[s];
+  for (int o = 16; o > 0; o >>= 1) v |= __shfl_xor_sync(0xffffffffu, v, o);
+  __shared__ int w[kAnyBlock / 32];
+  if ((threadIdx.x & 31) == 0) w[threadIdx.x >> 5] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int i = 1; i < kAnyBlock / 32; ++i) v |= w[i];
+    *out = v;
+  }
+}
+
+// status of a solve call from the OR of its per-sample flags
+mlsgd_status solve_verdict(mlsgd_ctx* ctx, int flags, const char* who) {
+  if (flags & 2) return fail(ctx, MLSGD_ENONFINITE, std::string(who) + ": a solve went non-finite (NaN/Inf input?)");
+  if (flags & 1) return fail(ctx, MLSGD_ENOCONV, std::string(who) + ": a solve hit max_iter");
+  return MLSGD_OK;
 }
 
 // state + Phi + adjoint for S samples on grid N; scratch carved from bp (not kept).
@@ -443,24 +468,24 @@ mlsgd_status mlsgd_solve_state_adjoint(mlsgd_ctx* ctx, int grid, int n_samples, 
   launch_exp_field(log_a_dev, o, (long long)S * cells_of(N), st);
   s = solve_grid(ctx, N, S, f, z_dev, y_dev, q_dev, phi_dev, iters_dev, status_dev, bp.p, st);
   if (s != MLSGD_OK) return s;
-  // report non-convergence (synchronous check of the status flags)
+  // report non-convergence / non-finite solves (synchronous check of the status flags)
   std::vector<int> h(S);
   CK(cudaMemcpyAsync(h.data(), status_dev, S * sizeof(int), cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
-  for (int v : h)
-    if (v) return fail(ctx, MLSGD_ENOCONV, "mlsgd_solve_state_adjoint: a solve hit max_iter or went non-finite");
-  return MLSGD_OK;
+  int flags = 0;
+  for (int v : h) flags |= v;
+  return solve_verdict(ctx, flags, "mlsgd_solve_state_adjoint");
 }
 
 // ---------------------------------------------------------------- allocation-free solve
-// Some callers cannot allocate device memory at the time they need a solve:
-// code running inside a host callback or a real-time loop where cudaMalloc's
-// implicit device synchronisation is not allowed, or a host application that
-// owns all device memory through its own pool and forbids libraries from
-// calling the CUDA allocator.  For them the solve below takes its scratch from
-// a fixed array compiled into the library instead of the context's growable
-// workspace.  The array is MLSGD_NOALLOC_SCRATCH_BYTES large and every GPU
-// that loads the library holds it until the process exits.
+// Some callers cannot allocate device memory at the time they need a solve: a
+// latency-critical loop where cudaMalloc's implicit device-wide synchronisation is
+// not acceptable, or a host application whose own allocator has reserved the
+// device memory and forbids libraries to call the CUDA allocator.  For them the
+// solve below takes its scratch from a fixed array compiled into the library
+// instead of the context's growable workspace.  The array is
+// MLSGD_NOALLOC_SCRATCH_BYTES large and every GPU that loads the library holds it
+// until the process exits.
 static __device__ __align__(256) char g_noalloc_scratch[MLSGD_NOALLOC_SCRATCH_BYTES];
 
 namespace {
@@ -469,7 +494,8 @@ char* g_noalloc_addr[kMaxDevices] = {};
 std::mutex g_noalloc_mu;
 
 // Device address of the static array on the current device, looked up once per
-// device (host code only sees a host-side stand-in under that name).
+// device with that device current (host code only sees a host-side stand-in under
+// the array's name, never a device address).
 mlsgd_status noalloc_scratch(mlsgd_ctx* ctx, char** out) {
   int dev = -1;
   CK(cudaGetDevice(&dev));
@@ -499,7 +525,7 @@ mlsgd_status mlsgd_solve_state_adjoint_noalloc(mlsgd_ctx* ctx, int grid, int n_s
     return fail(ctx, MLSGD_EINVAL, "mlsgd_solve_state_adjoint_noalloc: null pointer");
   const int N = ctx->N(grid);
   const int S = n_samples;
-  const size_t need = field_bytes(ctx, N, S) + solve_scratch_bytes(ctx, N, S);
+  const size_t need = al(sizeof(int)) + field_bytes(ctx, N, S) + solve_scratch_bytes(ctx, N, S);
   if (need > (size_t)MLSGD_NOALLOC_SCRATCH_BYTES)
     return fail(ctx, MLSGD_EINVAL,
                 "mlsgd_solve_state_adjoint_noalloc: " + std::to_string(S) + " samples on a " + std::to_string(N) +
@@ -511,18 +537,19 @@ mlsgd_status mlsgd_solve_state_adjoint_noalloc(mlsgd_ctx* ctx, int grid, int n_s
   // Nothing in the scratch has to start at zero: every kernel of the solve writes
   // a buffer (all nodes, boundary included) before any kernel reads it.
   Bump bp{scratch};
+  int* flags_dev = bp.take<int>(1);
   GridFields f = carve_fields(ctx, N, S, bp);
   FieldOut o{nullptr, f.a64, f.a32, f.abf};
   launch_exp_field(log_a_dev, o, (long long)S * cells_of(N), st);
   s = solve_grid(ctx, N, S, f, z_dev, y_dev, q_dev, phi_dev, iters_dev, status_dev, bp.p, st);
   if (s != MLSGD_OK) return s;
-  // non-convergence check through the context's pinned host buffer (no allocation)
-  int* h = (int*)ctx->host_buf;
-  CK(cudaMemcpyAsync(h, status_dev, S * sizeof(int), cudaMemcpyDeviceToHost, st));
+  // the OR of the per-sample flags is formed on the device and one int read back
+  // through the context's pinned word (no allocation, any batch size)
+  launch("status_any", (double)S * sizeof(int), k_status_any, dim3(1), kAnyBlock, 0, st, (const int*)status_dev, S,
+         flags_dev);
+  CK(cudaMemcpyAsync(ctx->count_host, flags_dev, sizeof(int), cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
-  for (int i = 0; i < S; ++i)
-    if (h[i]) return fail(ctx, MLSGD_ENOCONV, "mlsgd_solve_state_adjoint_noalloc: a solve hit max_iter");
-  return MLSGD_OK;
+  return solve_verdict(ctx, *ctx->count_host, "mlsgd_solve_state_adjoint_noalloc");
 }
 
 mlsgd_status mlsgd_stats_reset(mlsgd_ctx* ctx, mlsgd_level_stats* stats, void* stream) {
@@ -574,7 +601,7 @@ mlsgd_status mlsgd_level_gradient(mlsgd_ctx* ctx, int iter, int level, int64_t f
     int* iters = bp.take<int>(2 * (size_t)S);
     int* status = bp.take<int>(2 * (size_t)S);
     __nv_bfloat16* gemm_a = bp.take<__nv_bfloat16>((size_t)S * K);
-    double* work = bp.take<double>(4 + 4 * (size_t)S);
+    double* work = bp.take<double>(4 + 2 * (size_t)S);
     double* spartial = bp.take<double>((size_t)level_partial_cap(ctx->Nc(), N));
     double* lvl_nodes = bp.take<double>(2 * (size_t)nodes_of(N));
     char* scratch = bp.p;

@@ -179,8 +179,7 @@ void launch_phi_adjrhs(const double* y, int N, int S, double* badj, double* phi,
 
 // ---------------------------------------------------------------- level statistics
 // work layout: [0] shift_new, [1] scale_old = exp(theta (shift_old - shift_new)),
-// [2] n_old, [3] n_batch, [4..4+S) w_fine, [4+S..4+2S) w_coarse, then the same
-// 2S weights as FP32 pairs (one 8-byte slot each).
+// [2] n_old, [3] n_batch, [4..4+S) w_fine, [4+S..4+2S) w_coarse.
 //
 // Single block: shift, per-sample weights Y~ = exp(theta (Phi - shift)), and
 // the scalar statistics of dY~ = Y~_l - Y~_{l-1} (Welford over the batch,
@@ -210,14 +209,12 @@ __global__ void k_level_scalars(const double* __restrict__ phif, const double* _
   }
   __syncthreads();
   const double shift = work[0];
-  float2* wpair = reinterpret_cast<float2*>(work + 4 + 2 * S);  // the same weights as FP32 pairs
+  // a sample whose solve went non-finite (status bit 1) gets NaN weights, so the
+  // record, and the step that reads it, report the failure instead of using it
   for (int s = threadIdx.x; s < S; s += blockDim.x) {
-    const double wf = exp(theta * (phif[s] - shift));
-    const double wc = phic ? exp(theta * (phic[s] - shift)) : 0.0;
-    work[4 + s] = wf;
-    work[4 + S + s] = wc;
-    wpair[s] = df_split(wf);
-    wpair[S + s] = df_split(wc);
+    const bool bad = status != nullptr && ((status[s] | (phic ? status[S + s] : 0)) & 2);
+    work[4 + s] = bad ? NAN : exp(theta * (phif[s] - shift));
+    work[4 + S + s] = bad ? NAN : (phic ? exp(theta * (phic[s] - shift)) : 0.0);
   }
   __syncthreads();
   // batch mean and M2 of dY~ by shifted sums over the block (deviations from the
@@ -376,7 +373,21 @@ __device__ DF eval_at_ctrl(const float2* __restrict__ q, int N, int Nc, int cx, 
 // sample, stable when the first sample is typical), then the Chan merge with
 // the rescaled old mean; block partials of h_c^3 (M2_batch + delta^2 n_old S / n).
 // PF / PC: the fine / coarse adjoint solutions are FP32 (hi, lo) pairs (the mixed
-// path on tiled grids); those samples then run in pair arithmetic.
+// path on tiled grids); their control-cell averages are then formed in pair
+// arithmetic (exact weights, about 48 significant bits, a function of the sample
+// alone).  The weighting, the cancelling difference w_f X_f - w_c X_c and its sums
+// are FP64 in every case (eq:delta-notation, eq:sec-order-sum): the only values
+// that depend on the batch (through the shift) are formed and accumulated in FP64,
+// so a record does not depend on how the samples were split into calls beyond
+// FP64 rounding.
+__device__ __forceinline__ double ctrl_avg(const CellInterp& I, bool fast, const double* q, int N, int Nc, int cx,
+                                           int cy, int cz) {
+  return fast ? I.eval(q) : eval_at_ctrl(q, N, Nc, cx, cy, cz);
+}
+__device__ __forceinline__ double ctrl_avg(const CellInterp& I, bool fast, const float2* q, int N, int Nc, int cx,
+                                           int cy, int cz) {
+  return df_to_double(fast ? I.eval(q) : eval_at_ctrl(q, N, Nc, cx, cy, cz));
+}
 template <bool PF, bool PC>
 __global__ void k_level_field(const void* __restrict__ qf_, int Nf, const void* __restrict__ qc_, int Ncs, int S,
                               int Nc, const double* __restrict__ work, double* __restrict__ field,
@@ -398,51 +409,17 @@ __global__ void k_level_field(const void* __restrict__ qf_, int Nf, const void* 
     CellInterp If{}, Ic{};
     if (fast_f) If.setup(Nf, Nc, cx, cy, cz);
     if (qc && fast_c) Ic.setup(Ncs, Nc, cx, cy, cz);
-    double mean, m2;
-    if constexpr (PF) {
-      // all in FP32 pairs: v = w_f X_f - w_c X_c, sums of deviations from the first sample
-      const float2* wpf = reinterpret_cast<const float2*>(work + 4 + 2 * S);
-      const float2* wpc = wpf + S;
-      DF ref{0.f, 0.f}, sd{0.f, 0.f}, sd2{0.f, 0.f};
-      for (int s = 0; s < S; ++s) {
-        const float2* qfs = (const float2*)qf + s * nf;
-        DF v = df_mul(df_make(wpf[s]), fast_f ? If.eval(qfs) : eval_at_ctrl(qfs, Nf, Nc, cx, cy, cz));
-        if (qc) {
-          DF xc;
-          if constexpr (PC) {
-            const float2* qcs = (const float2*)qc + s * ncn;
-            xc = fast_c ? Ic.eval(qcs) : eval_at_ctrl(qcs, Ncs, Nc, cx, cy, cz);
-          } else {
-            const double* qcs = (const double*)qc + s * ncn;
-            xc = df_make(df_split(fast_c ? Ic.eval(qcs) : eval_at_ctrl(qcs, Ncs, Nc, cx, cy, cz)));
-          }
-          v = df_add(v, df_neg(df_mul(df_make(wpc[s]), xc)));
-        }
-        if (s == 0) ref = v;
-        const DF d = df_add(v, df_neg(ref));
-        sd = df_add(sd, d);
-        sd2 = df_add(sd2, df_mul(d, d));
-      }
-      const double sdd = df_to_double(sd);
-      mean = df_to_double(ref) + sdd / S;
-      m2 = fmax(df_to_double(sd2) - sdd * (sdd / S), 0.0);
-    } else {
-      double ref = 0.0, sd = 0.0, sd2 = 0.0;
-      for (int s = 0; s < S; ++s) {
-        const double* qfs = (const double*)qf + s * nf;
-        double v = wf[s] * (fast_f ? If.eval(qfs) : eval_at_ctrl(qfs, Nf, Nc, cx, cy, cz));
-        if (qc) {
-          const double* qcs = (const double*)qc + s * ncn;
-          v -= wc[s] * (fast_c ? Ic.eval(qcs) : eval_at_ctrl(qcs, Ncs, Nc, cx, cy, cz));
-        }
-        if (s == 0) ref = v;
-        const double d = v - ref;
-        sd += d;
-        sd2 = fma(d, d, sd2);
-      }
-      mean = ref + sd / S;
-      m2 = fmax(sd2 - sd * (sd / S), 0.0);
+    double ref = 0.0, sd = 0.0, sd2 = 0.0;
+    for (int s = 0; s < S; ++s) {
+      double v = wf[s] * ctrl_avg(If, fast_f, qf + s * nf, Nf, Nc, cx, cy, cz);
+      if (qc) v = fma(-wc[s], ctrl_avg(Ic, fast_c, qc + s * ncn, Ncs, Nc, cx, cy, cz), v);
+      if (s == 0) ref = v;
+      const double d = v - ref;
+      sd += d;
+      sd2 = fma(d, d, sd2);
     }
+    const double mean = ref + sd / S;
+    const double m2 = fmax(sd2 - sd * (sd / S), 0.0);
     const double n_old = work[2], scale = work[1];
     const double n = n_old + S;
     const double mo = (n_old > 0.0) ? field[c] * scale : 0.0;

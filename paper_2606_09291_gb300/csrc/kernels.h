@@ -57,10 +57,24 @@ inline long long level_partial_cap(int Nc, int Nf) {
   return (cells_of(Nc) + 255) / 256 + (cells_of(Nf) + 255) / 256 + 64;
 }
 
+// The samples one launch processes: a batch of S samples (the tile shapes and the
+// per-sample partial-sum layout follow S), of which n are launched, sample act[t] for
+// t < n (act null: samples 0..n-1, n == S).  The solver's host-checked modes compact
+// the still-active samples into act, so retired samples start no blocks.
+struct Batch {
+  int S;
+  int n;
+  const int* act;
+};
+
 // Buffers of one batched solve on a grid with N cells per side.  Vectors are
 // [S][nodes] (stride nodes_of(N)), coefficients [S][cells].
 struct SolverBufs {
   int N, S, J;               // MG levels j = 0..J, N_j = N >> j, N_J = 2
+  int n_act = 0;             // samples launched by the masked kernels (host-known)
+  const int* actp = nullptr; // their indices (null: all S)
+  int* act = nullptr;        // [S] device list the compaction writes
+  Batch batch() const { return Batch{S, n_act, actp}; }
   // MG hierarchy (j >= 1 coarse; j = 0 uses the caller's operator coefficient)
   void* acoef[8];            // coefficient per MG level (j = 0: the V-cycle's own copy, may alias)
   void* vx[8];               // V-cycle iterate per level
@@ -111,21 +125,21 @@ TiledShape tiled_shape(int N, int S, int rows_per_thread);
 int tiled_blocks_per_sample(int N, int S, int elem);
 template <typename T, typename TA>
 void tiled_apply(const T* z, const T* pold, T* pnew, const TA* a, T* q, double* partial, const SolveScalars* sc, int N,
-                 int S, int first, cudaStream_t st);
+                 const Batch& bt, int first, cudaStream_t st);
 template <typename T, typename TA>
-void tiled_pre(const T* r, const TA* a, const T* dinv, T* t, const SolveScalars* sc, int N, int S, double omega,
-               cudaStream_t st);
+void tiled_pre(const T* r, const TA* a, const T* dinv, T* t, const SolveScalars* sc, int N, const Batch& bt,
+               double omega, cudaStream_t st);
 template <typename T, typename TA>
 void tiled_post(const T* r, const TA* a, const T* dinv, const T* ec, T* z, double* partial, const SolveScalars* sc,
-                int N, int S, double omega, cudaStream_t st);
+                int N, const Batch& bt, double omega, cudaStream_t st);
 void tiled_apply_x(const float* z, const float* pold, float* pnew, const float* a, float* q, float* x, double* partial,
-                   const SolveScalars* sc, int N, int S, cudaStream_t st, bool x_first);
+                   const SolveScalars* sc, int N, const Batch& bt, cudaStream_t st, bool x_first);
 void tiled_pre_update(const float* r, const float* q, const __nv_bfloat16* a, const float* dinv, float* t, float* rnew,
-                      const SolveScalars* sc, int N, int S, double omega, cudaStream_t st);
+                      const SolveScalars* sc, int N, const Batch& bt, double omega, cudaStream_t st);
 // r32 = (float)(b - A x) to FP64 accuracy with x, b as FP32 (hi, lo) pairs and error-free
 // FP32 products and sums; partial r.r
 void tiled_res64(const float2* b, long long bstride, const float2* x, const float* a, float* r32, double* partial,
-                 const SolveScalars* sc, int N, int S, cudaStream_t st);
+                 const SolveScalars* sc, int N, const Batch& bt, cudaStream_t st);
 // Phi and the adjoint right-hand side; returns the partial-sum blocks per sample
 int tiled_phi_df(const float2* y, int N, int S, const float2* gtab, const float2* mgtab, float2* badj,
                  double* partial, cudaStream_t st);
@@ -151,7 +165,7 @@ void launch_phi_adjrhs_df(const float2* y, int N, int S, float2* badj, double* p
                           const float2* gtab, const float2* mgtab, cudaStream_t st);
 // batch statistics of one level merged into stats (see mlsgd_level_stats)
 // qf_pairs / qc_pairs: the adjoint solutions are stored as FP32 (hi, lo) pairs;
-// work holds 4 + 4 S doubles; nodebuf (2 (Nf+1)^3 doubles, optional): when the
+// work holds 4 + 2 S doubles; nodebuf (2 (Nf+1)^3 doubles, optional): when the
 // level's grids are at least 4x coarser than the control grid the statistics are
 // formed on the level grid (qf is then overwritten; partial needs cells(Nc)/256 +
 // cells(Nf)/256 + 2 entries)

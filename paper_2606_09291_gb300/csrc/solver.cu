@@ -26,13 +26,16 @@ namespace mlsgd {
 enum ScalarMode { SM_INIT = 0, SM_RZ0, SM_ALPHA, SM_CONV, SM_BETA, SM_OUTER_CONV, SM_INNER_BEGIN, SM_OUTER_STEP };
 
 // ---------------------------------------------------------------- vector kernels
-#define SAMPLE_GUARD(sc)                         \
-  const int s = blockIdx.y;                      \
+// blockIdx.y indexes the launched samples: act[blockIdx.y] when the active samples
+// have been compacted into a list, else blockIdx.y itself
+#define SAMPLE_GUARD(sc)                                                     \
+  const int s = act != nullptr ? act[blockIdx.y] : (int)blockIdx.y;          \
   if ((sc) != nullptr && !(sc)[s].active) return;
 
 template <typename T, typename TA>
 __global__ void k_apply_dot(const T* __restrict__ x, const TA* __restrict__ a, T* __restrict__ y,
-                            double* __restrict__ partial, const SolveScalars* __restrict__ sc, int N) {
+                            double* __restrict__ partial, const SolveScalars* __restrict__ sc, int N,
+                            const int* __restrict__ act) {
   SAMPLE_GUARD(sc);
   const int n1 = N + 1;
   const long long nodes = (long long)n1 * n1 * n1;
@@ -57,7 +60,7 @@ __global__ void k_apply_dot(const T* __restrict__ x, const TA* __restrict__ a, T
 
 template <typename T>
 __global__ void k_dot(const T* __restrict__ u, const T* __restrict__ v, double* __restrict__ partial,
-                      const SolveScalars* __restrict__ sc, long long nodes) {
+                      const SolveScalars* __restrict__ sc, long long nodes, const int* __restrict__ act) {
   SAMPLE_GUARD(sc);
   const int n = blockIdx.x * blockDim.x + threadIdx.x;
   T contrib = T(0);
@@ -69,7 +72,8 @@ __global__ void k_dot(const T* __restrict__ u, const T* __restrict__ v, double* 
 // x += alpha p; r -= alpha q; partial = r.r
 template <typename T, bool REDUCE>
 __global__ void k_update_xr(T* __restrict__ x, T* __restrict__ r, const T* __restrict__ p, const T* __restrict__ q,
-                            double* __restrict__ partial, const SolveScalars* __restrict__ sc, long long nodes) {
+                            double* __restrict__ partial, const SolveScalars* __restrict__ sc, long long nodes,
+                            const int* __restrict__ act) {
   SAMPLE_GUARD(sc);
   const int n = blockIdx.x * blockDim.x + threadIdx.x;
   const T al = (T)sc[s].alpha;
@@ -89,21 +93,13 @@ __global__ void k_update_xr(T* __restrict__ x, T* __restrict__ r, const T* __res
 
 template <typename T>
 __global__ void k_p_update(T* __restrict__ p, const T* __restrict__ z, const SolveScalars* __restrict__ sc,
-                           long long nodes, int first) {
+                           long long nodes, int first, const int* __restrict__ act) {
   SAMPLE_GUARD(sc);
   const int n = blockIdx.x * blockDim.x + threadIdx.x;
   if (n < nodes) {
     const long long o = s * nodes + n;
     p[o] = first ? z[o] : z[o] + (T)sc[s].beta * p[o];
   }
-}
-
-// x += alpha p (the last update of a fused inner solve)
-template <typename T>
-__global__ void k_axpy(T* __restrict__ x, const T* __restrict__ p, const SolveScalars* __restrict__ sc, long long nodes) {
-  SAMPLE_GUARD(sc);
-  const int n = blockIdx.x * blockDim.x + threadIdx.x;
-  if (n < nodes) x[s * nodes + n] += (T)sc[s].alpha * p[s * nodes + n];
 }
 
 // r = b (shared or per sample), x = 0, partial = b.b  (not masked)
@@ -123,12 +119,15 @@ __global__ void k_init(const double* __restrict__ b, long long bstride, T* __res
   if (threadIdx.x == 0) partial[(long long)s * gridDim.x + blockIdx.x] = bs;
 }
 
-// one warp per sample: sum the block partials in a fixed order, then the scalar update
-__global__ void k_scalar(const double* __restrict__ partial, int nblk, SolveScalars* __restrict__ sc, int S,
-                         int mode, double tol2, int max_iter, int inner_iters, const SolveScalars* __restrict__ outer) {
-  const int s = blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
+// one warp per launched sample: sum the block partials in a fixed order, then the
+// scalar update
+__global__ void k_scalar(const double* __restrict__ partial, int nblk, SolveScalars* __restrict__ sc, int n,
+                         const int* __restrict__ act, int mode, double tol2, int max_iter, int inner_iters,
+                         const SolveScalars* __restrict__ outer) {
+  const int t = blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
   const int lane = threadIdx.x & 31;
-  if (s >= S) return;
+  if (t >= n) return;
+  const int s = act != nullptr ? act[t] : t;
   SolveScalars& c = sc[s];
   if (mode == SM_INNER_BEGIN) {
     if (lane == 0) c.active = outer[s].active;
@@ -167,18 +166,34 @@ __global__ void k_scalar(const double* __restrict__ partial, int nblk, SolveScal
   }
 }
 
-__global__ void k_count_active(const SolveScalars* __restrict__ sc, int S, int* __restrict__ count) {
-  int v = 0;
-  for (int s = threadIdx.x; s < S; s += blockDim.x) v += sc[s].active;
-  v = block_sum(v);
-  if (threadIdx.x == 0) *count = v;
+// Ordered compaction of the active samples: act[0..count) = the indices s with
+// sc[s].active, ascending.  One block of kBlock threads walks the batch in chunks;
+// each chunk's offsets come from warp ballots and a scan of the warp counts.
+__global__ void __launch_bounds__(kBlock) k_compact(const SolveScalars* __restrict__ sc, int S, int* __restrict__ act,
+                                                    int* __restrict__ count) {
+  __shared__ int wcount[kBlock / 32];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  int base = 0;
+  for (int s0 = 0; s0 < S; s0 += kBlock) {
+    const int s = s0 + threadIdx.x;
+    const bool a = s < S && sc[s].active;
+    const unsigned m = __ballot_sync(0xffffffffu, a);
+    if (lane == 0) wcount[w] = __popc(m);
+    __syncthreads();
+    int off = base;
+    for (int v = 0; v < w; ++v) off += wcount[v];
+    if (a) act[off + __popc(m & ((1u << lane) - 1u))] = s;
+    for (int v = 0; v < kBlock / 32; ++v) base += wcount[v];
+    __syncthreads();  // wcount is rewritten by the next chunk
+  }
+  if (threadIdx.x == 0) *count = base;
 }
 
 // ---------------------------------------------------------------- multigrid kernels
 // x = omega D^{-1} r  (pre-smoothing from a zero initial guess), D = (h/3) sum_8 a
 template <typename T, typename TA>
 __global__ void k_jacobi0(const T* __restrict__ r, const TA* __restrict__ a, T* __restrict__ x,
-                          const SolveScalars* __restrict__ sc, int N, T omega) {
+                          const SolveScalars* __restrict__ sc, int N, T omega, const int* __restrict__ act) {
   SAMPLE_GUARD(sc);
   const int n1 = N + 1;
   const long long nodes = (long long)n1 * n1 * n1;
@@ -198,7 +213,8 @@ __global__ void k_jacobi0(const T* __restrict__ r, const TA* __restrict__ a, T* 
 // t = r - A x   (mode 0)   or   t = x + omega D^{-1} (r - A x)   (mode 1, smoothing)
 template <typename T, typename TA, int MODE>
 __global__ void k_resid_smooth(const T* __restrict__ r, const T* __restrict__ x, const TA* __restrict__ a,
-                               T* __restrict__ t, const SolveScalars* __restrict__ sc, int N, T omega) {
+                               T* __restrict__ t, const SolveScalars* __restrict__ sc, int N, T omega,
+                               const int* __restrict__ act) {
   SAMPLE_GUARD(sc);
   const int n1 = N + 1;
   const long long nodes = (long long)n1 * n1 * n1;
@@ -220,7 +236,7 @@ __global__ void k_resid_smooth(const T* __restrict__ r, const T* __restrict__ x,
 // coarse = P^T fine: weights 1, 1/2 per axis around (2I, 2J, 2K)
 template <typename T>
 __global__ void k_restrict(const T* __restrict__ tf, T* __restrict__ rc, const SolveScalars* __restrict__ sc,
-                           int Nc) {
+                           int Nc, const int* __restrict__ act) {
   SAMPLE_GUARD(sc);
   const int n1c = Nc + 1, Nf = 2 * Nc, n1f = Nf + 1;
   const long long nc = (long long)n1c * n1c * n1c, nf = (long long)n1f * n1f * n1f;
@@ -247,7 +263,7 @@ __global__ void k_restrict(const T* __restrict__ tf, T* __restrict__ rc, const S
 // fine += P coarse (trilinear)
 template <typename T>
 __global__ void k_prolong_add(T* __restrict__ xf, const T* __restrict__ ec, const SolveScalars* __restrict__ sc,
-                              int Nf) {
+                              int Nf, const int* __restrict__ act) {
   SAMPLE_GUARD(sc);
   const int n1f = Nf + 1, Nc = Nf / 2, n1c = Nc + 1;
   const long long nf = (long long)n1f * n1f * n1f, nc = (long long)n1c * n1c * n1c;
@@ -277,9 +293,11 @@ __global__ void k_prolong_add(T* __restrict__ xf, const T* __restrict__ ec, cons
 // 2^3 cells: the single interior unknown, x = r / D; all other nodes 0
 template <typename T, typename TA>
 __global__ void k_coarsest(const T* __restrict__ r, const TA* __restrict__ a, T* __restrict__ x,
-                           const SolveScalars* __restrict__ sc, int S) {
-  const int s = blockIdx.x * blockDim.x + threadIdx.x;
-  if (s >= S || (sc != nullptr && !sc[s].active)) return;
+                           const SolveScalars* __restrict__ sc, int n, const int* __restrict__ act) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n) return;
+  const int s = act != nullptr ? act[t] : t;
+  if (sc != nullptr && !sc[s].active) return;
   T* xs = x + (long long)s * 27;
   for (int n = 0; n < 27; ++n) xs[n] = T(0);
   Cells8<T, TA> C;
@@ -311,7 +329,7 @@ __global__ void k_coarsen_coef(const TI* __restrict__ af, TO* __restrict__ ac, i
 template <typename TA>
 __global__ void k_residual64(const double* __restrict__ b, long long bstride, const double* __restrict__ x,
                              const TA* __restrict__ a, double* __restrict__ r, double* __restrict__ partial,
-                             const SolveScalars* __restrict__ sc, int N) {
+                             const SolveScalars* __restrict__ sc, int N, const int* __restrict__ act) {
   SAMPLE_GUARD(sc);
   const int n1 = N + 1;
   const long long nodes = (long long)n1 * n1 * n1;
@@ -335,7 +353,7 @@ __global__ void k_residual64(const double* __restrict__ b, long long bstride, co
 
 // r32 = (float) r64, d = 0
 __global__ void k_demote(const double* __restrict__ r64, float* __restrict__ r32, float* __restrict__ d,
-                         const SolveScalars* __restrict__ sc, long long nodes) {
+                         const SolveScalars* __restrict__ sc, long long nodes, const int* __restrict__ act) {
   SAMPLE_GUARD(sc);
   const int n = blockIdx.x * blockDim.x + threadIdx.x;
   if (n < nodes) {
@@ -391,17 +409,21 @@ __global__ void k_init32(const double* __restrict__ b, const float2* __restrict_
 
 // the inner solve's last update fused with the refinement step: the solution is
 // kept as an FP32 (hi, lo) pair x, x (+)= d + alpha p (pair addition: two-sum and
-// renormalisation, about 48 significant bits), d taken as 0 when never written
+// renormalisation, about 48 significant bits), d taken as 0 when never written.
+// The first step (assign) launches every sample and writes x = 0 for the samples that
+// take no step (b = 0, or a non-finite b), so every sample's solution is defined.
 __global__ void k_finish_step(float2* __restrict__ x, const float* __restrict__ d, const float* __restrict__ p,
                               const SolveScalars* __restrict__ sci, const SolveScalars* __restrict__ sco,
-                              long long nodes, int N, int assign, int d_zero) {
-  SAMPLE_GUARD(sco);
+                              long long nodes, int N, int assign, int d_zero, const int* __restrict__ act) {
+  const int s = act != nullptr ? act[blockIdx.y] : (int)blockIdx.y;
+  const bool on = sco[s].active != 0;
+  if (!on && !assign) return;
   const int n = blockIdx.x * blockDim.x + threadIdx.x;
   if (n >= nodes) return;
   const long long o = s * nodes + n;
   int i, j, k;
   node_ijk(n, N + 1, i, j, k);
-  if (!interior(i, j, k, N)) {  // d and p are never written on the boundary
+  if (!on || !interior(i, j, k, N)) {  // d and p are never written on the boundary
     x[o] = make_float2(0.0f, 0.0f);
     return;
   }
@@ -431,7 +453,7 @@ __global__ void k_store_pair(double* __restrict__ x, const float2* __restrict__ 
 
 // x64 += d
 __global__ void k_accumulate(double* __restrict__ x, const float* __restrict__ d, const SolveScalars* __restrict__ sc,
-                             long long nodes) {
+                             long long nodes, const int* __restrict__ act) {
   SAMPLE_GUARD(sc);
   const int n = blockIdx.x * blockDim.x + threadIdx.x;
   if (n < nodes) x[s * nodes + n] += (double)d[s * nodes + n];
@@ -464,7 +486,7 @@ size_t solver_bytes(int N, int S, int elem) {
   if (elem == 4 && tiled_level(N, 0)) b += align_up((size_t)S * nodes_of(N) * sizeof(float2));
   b += align_up((size_t)S * node_blocks(N) * sizeof(double));
   b += 2 * align_up((size_t)S * sizeof(SolveScalars));
-  b += align_up(sizeof(int));
+  b += align_up(sizeof(int)) + align_up((size_t)S * sizeof(int));
   return b;
 }
 
@@ -489,6 +511,9 @@ void carve_solver(SolverBufs& B, int N, int S, int elem, char*& ptr) {
   B.partial = (double*)take((size_t)S * node_blocks(N) * sizeof(double));
   B.sc = (SolveScalars*)take((size_t)2 * S * sizeof(SolveScalars));
   B.count = (int*)take(sizeof(int));
+  B.act = (int*)take((size_t)S * sizeof(int));
+  B.n_act = S;
+  B.actp = nullptr;
 }
 
 // algorithmic bytes of a node kernel: `vec` vectors of T over S samples of grid N
@@ -593,6 +618,9 @@ template <typename T, typename TA0>
 static int vcycle(SolverBufs& B, const T* r0, const TA0* a0, const SolveScalars* sc, T omega, cudaStream_t st,
                   const T* fuse_q = nullptr, T* r_new = nullptr) {
   const int S = B.S, J = B.J;
+  const int n = B.n_act;            // samples launched (the active ones when compacted)
+  const int* act = B.actp;
+  const Batch bt = B.batch();
   const bool tiled = B.N >= kTiledMinN && J >= 1;
   const T* rfine = fuse_q ? r_new : r0;  // residual the V-cycle works on after the fused update
   auto rin = [&](int j) { return j == 0 ? rfine : (const T*)B.vr[j]; };
@@ -601,53 +629,54 @@ static int vcycle(SolverBufs& B, const T* r0, const TA0* a0, const SolveScalars*
     const bool fine = j == 0;
     if (fine && tiled && fuse_q) {
       if constexpr (std::is_same<T, float>::value && std::is_same<TA0, __nv_bfloat16>::value)
-        tiled_pre_update(r0, fuse_q, a0, (const T*)B.dinv[0], (T*)B.vt[0], r_new, sc, Nj, S, (double)omega, st);
+        tiled_pre_update(r0, fuse_q, a0, (const T*)B.dinv[0], (T*)B.vt[0], r_new, sc, Nj, bt, (double)omega, st);
     } else if (fine && tiled) {
-      tiled_pre<T, TA0>(r0, a0, (const T*)B.dinv[0], (T*)B.vt[0], sc, Nj, S, (double)omega, st);
+      tiled_pre<T, TA0>(r0, a0, (const T*)B.dinv[0], (T*)B.vt[0], sc, Nj, bt, (double)omega, st);
     } else if (!fine && tiled && Nj >= kTiledMinN) {
-      tiled_pre<T, T>(rin(j), (const T*)B.acoef[j], (const T*)B.dinv[j], (T*)B.vt[j], sc, Nj, S, (double)omega, st);
+      tiled_pre<T, T>(rin(j), (const T*)B.acoef[j], (const T*)B.dinv[j], (T*)B.vt[j], sc, Nj, bt, (double)omega, st);
     } else if (fine) {
-      launch(cls<T>("jacobi0", true), nbytes<T, TA0>(Nj, S, 2, 1), k_jacobi0<T, TA0>, grid_nodes(Nj, S), kBlock, 0,
-             st, rin(0), a0, (T*)B.vx[0], sc, Nj, omega);
-      launch(cls<T>("resid", true), nbytes<T, TA0>(Nj, S, 3, 1), k_resid_smooth<T, TA0, 0>, grid_nodes(Nj, S), kBlock,
-             0, st, rin(0), (const T*)B.vx[0], a0, (T*)B.vt[0], sc, Nj, omega);
+      launch(cls<T>("jacobi0", true), nbytes<T, TA0>(Nj, n, 2, 1), k_jacobi0<T, TA0>, grid_nodes(Nj, n), kBlock, 0,
+             st, rin(0), a0, (T*)B.vx[0], sc, Nj, omega, act);
+      launch(cls<T>("resid", true), nbytes<T, TA0>(Nj, n, 3, 1), k_resid_smooth<T, TA0, 0>, grid_nodes(Nj, n), kBlock,
+             0, st, rin(0), (const T*)B.vx[0], a0, (T*)B.vt[0], sc, Nj, omega, act);
     } else {
       const T* aj = (const T*)B.acoef[j];
-      launch(cls<T>("jacobi0", false), nbytes<T, T>(Nj, S, 2, 1), k_jacobi0<T, T>, grid_nodes(Nj, S), kBlock, 0, st,
-             rin(j), aj, (T*)B.vx[j], sc, Nj, omega);
-      launch(cls<T>("resid", false), nbytes<T, T>(Nj, S, 3, 1), k_resid_smooth<T, T, 0>, grid_nodes(Nj, S), kBlock, 0,
-             st, rin(j), (const T*)B.vx[j], aj, (T*)B.vt[j], sc, Nj, omega);
+      launch(cls<T>("jacobi0", false), nbytes<T, T>(Nj, n, 2, 1), k_jacobi0<T, T>, grid_nodes(Nj, n), kBlock, 0, st,
+             rin(j), aj, (T*)B.vx[j], sc, Nj, omega, act);
+      launch(cls<T>("resid", false), nbytes<T, T>(Nj, n, 3, 1), k_resid_smooth<T, T, 0>, grid_nodes(Nj, n), kBlock, 0,
+             st, rin(j), (const T*)B.vx[j], aj, (T*)B.vt[j], sc, Nj, omega, act);
     }
-    launch(cls<T>("restrict", fine), nbytes<T, T>(Nj, S, 1, 0) + nbytes<T, T>(Nj / 2, S, 1, 0), k_restrict<T>,
-           grid_nodes(Nj / 2, S), kBlock, 0, st, (const T*)B.vt[j], (T*)B.vr[j + 1], sc, Nj / 2);
+    launch(cls<T>("restrict", fine), nbytes<T, T>(Nj, n, 1, 0) + nbytes<T, T>(Nj / 2, n, 1, 0), k_restrict<T>,
+           grid_nodes(Nj / 2, n), kBlock, 0, st, (const T*)B.vt[j], (T*)B.vr[j + 1], sc, Nj / 2, act);
   }
   if (J == 0)
-    launch("coarsest", 0.0, k_coarsest<T, TA0>, dim3((S + 127) / 128), 128, 0, st, rin(0), a0, (T*)B.vt[0], sc, S);
+    launch("coarsest", 0.0, k_coarsest<T, TA0>, dim3((n + 127) / 128), 128, 0, st, rin(0), a0, (T*)B.vt[0], sc, n,
+           act);
   else
-    launch("coarsest", 0.0, k_coarsest<T, T>, dim3((S + 127) / 128), 128, 0, st, rin(J), (const T*)B.acoef[J],
-           (T*)B.vt[J], sc, S);
+    launch("coarsest", 0.0, k_coarsest<T, T>, dim3((n + 127) / 128), 128, 0, st, rin(J), (const T*)B.acoef[J],
+           (T*)B.vt[J], sc, n, act);
   for (int j = J - 1; j >= 0; --j) {
     const int Nj = B.N >> j;
     const bool fine = j == 0;
     if (fine && tiled) {
-      tiled_post<T, TA0>(rfine, a0, (const T*)B.dinv[0], (const T*)B.vt[1], (T*)B.vt[0], B.partial, sc, Nj, S,
+      tiled_post<T, TA0>(rfine, a0, (const T*)B.dinv[0], (const T*)B.vt[1], (T*)B.vt[0], B.partial, sc, Nj, bt,
                          (double)omega, st);
       return tiled_blocks_per_sample(Nj, S, (int)sizeof(T));
     }
     if (!fine && tiled && Nj >= kTiledMinN) {
       // the r.z partial sums of a coarse level are overwritten by the fine level's POST
       tiled_post<T, T>(rin(j), (const T*)B.acoef[j], (const T*)B.dinv[j], (const T*)B.vt[j + 1], (T*)B.vt[j],
-                       B.partial, sc, Nj, S, (double)omega, st);
+                       B.partial, sc, Nj, bt, (double)omega, st);
       continue;
     }
-    launch(cls<T>("prolong", fine), nbytes<T, T>(Nj, S, 2, 0) + nbytes<T, T>(Nj / 2, S, 1, 0), k_prolong_add<T>,
-           grid_nodes(Nj, S), kBlock, 0, st, (T*)B.vx[j], (const T*)B.vt[j + 1], sc, Nj);
+    launch(cls<T>("prolong", fine), nbytes<T, T>(Nj, n, 2, 0) + nbytes<T, T>(Nj / 2, n, 1, 0), k_prolong_add<T>,
+           grid_nodes(Nj, n), kBlock, 0, st, (T*)B.vx[j], (const T*)B.vt[j + 1], sc, Nj, act);
     if (fine)
-      launch(cls<T>("smooth", true), nbytes<T, TA0>(Nj, S, 3, 1), k_resid_smooth<T, TA0, 1>, grid_nodes(Nj, S), kBlock,
-             0, st, rin(0), (const T*)B.vx[0], a0, (T*)B.vt[0], sc, Nj, omega);
+      launch(cls<T>("smooth", true), nbytes<T, TA0>(Nj, n, 3, 1), k_resid_smooth<T, TA0, 1>, grid_nodes(Nj, n), kBlock,
+             0, st, rin(0), (const T*)B.vx[0], a0, (T*)B.vt[0], sc, Nj, omega, act);
     else
-      launch(cls<T>("smooth", false), nbytes<T, T>(Nj, S, 3, 1), k_resid_smooth<T, T, 1>, grid_nodes(Nj, S), kBlock, 0,
-             st, rin(j), (const T*)B.vx[j], (const T*)B.acoef[j], (T*)B.vt[j], sc, Nj, omega);
+      launch(cls<T>("smooth", false), nbytes<T, T>(Nj, n, 3, 1), k_resid_smooth<T, T, 1>, grid_nodes(Nj, n), kBlock, 0,
+             st, rin(j), (const T*)B.vx[j], (const T*)B.acoef[j], (T*)B.vt[j], sc, Nj, omega, act);
   }
   return 0;
 }
@@ -655,27 +684,43 @@ static int vcycle(SolverBufs& B, const T* r0, const TA0* a0, const SolveScalars*
 static void scalar(SolverBufs& B, SolveScalars* sc, int mode, double tol2, int max_iter, cudaStream_t st, int nblk,
                    int inner_iters = 0, const SolveScalars* outer = nullptr) {
   const int warps = 8;
-  launch("scalar", 0.0, k_scalar, dim3((B.S + warps - 1) / warps), 32 * warps, 0, st, (const double*)B.partial, nblk,
-         sc, B.S, mode, tol2, max_iter, inner_iters, outer);
+  launch("scalar", 0.0, k_scalar, dim3((B.n_act + warps - 1) / warps), 32 * warps, 0, st, (const double*)B.partial,
+         nblk, sc, B.n_act, B.actp, mode, tol2, max_iter, inner_iters, outer);
 }
 
-static cudaError_t count_active(SolverBufs& B, const SolveScalars* sc, cudaStream_t st, int& n) {
-  launch("count", 0.0, k_count_active, dim3(1), kBlock, 0, st, sc, B.S, B.count);
+// All samples launched again (the start of a solve).
+static void launch_all(SolverBufs& B) {
+  B.n_act = B.S;
+  B.actp = nullptr;
+}
+
+// Host-checked modes: compact the active samples of `sc` into B.act, read their
+// count back (one synchronisation) and launch only them from now on, so retired
+// samples start no blocks and are credited with no bytes.
+static cudaError_t compact_active(SolverBufs& B, const SolveScalars* sc, cudaStream_t st, int& n) {
+  launch("compact", (double)B.S * (sizeof(SolveScalars) + sizeof(int)), k_compact, dim3(1), kBlock, 0, st, sc, B.S,
+         B.act, B.count);
   cudaError_t e = cudaMemcpyAsync(B.count_host, B.count, sizeof(int), cudaMemcpyDeviceToHost, st);
   if (e != cudaSuccess) return e;
   e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return e;
   n = *B.count_host;
-  return e;
+  if (n < 0 || n > B.S) return cudaErrorInvalidValue;
+  B.n_act = n;
+  B.actp = n < B.S ? B.act : nullptr;
+  return cudaSuccess;
 }
 
 // Krylov loop shared by the FP64 solve and the FP32 inner solve.
-// fixed_iters > 0: run exactly that many iterations without a stop test.
+// fixed_iters > 0: run exactly that many iterations without a stop test (over the
+// samples the caller's compaction left active).  Otherwise the stop test runs every
+// iteration on the device and every prm.check_every iterations on the host, which
+// then compacts the still-active samples.
 template <typename T, typename TAop, typename TA0>
 static cudaError_t pcg_loop(SolverBufs& B, const TAop* aop, const TA0* a0, T* x, T* r, SolveScalars* sc,
                             const PcgParams& prm, int fixed_iters, cudaStream_t st) {
   const int S = B.S, N = B.N;
   const long long nodes = nodes_of(N);
-  const dim3 g = grid_nodes(N, S);
   const int nb = node_blocks(N);
   const T omega = (T)prm.omega;
   const bool tiled = N >= kTiledMinN && B.J >= 1;
@@ -683,11 +728,12 @@ static cudaError_t pcg_loop(SolverBufs& B, const TAop* aop, const TA0* a0, T* x,
   int cur = 0;
   T* q = (T*)B.q;
   const T* z = (const T*)B.vt[0];
+  auto g = [&]() { return grid_nodes(N, B.n_act); };
   auto precondition = [&](int mode) {
     const int nrz = vcycle<T, TA0>(B, r, a0, sc, omega, st);
     if (nrz == 0) {
-      launch(cls<T>("dot", true), nbytes<T, T>(N, S, 2, 0), k_dot<T>, g, kBlock, 0, st, (const T*)r, z, B.partial,
-             (const SolveScalars*)sc, nodes);
+      launch(cls<T>("dot", true), nbytes<T, T>(N, B.n_act, 2, 0), k_dot<T>, g(), kBlock, 0, st, (const T*)r, z,
+             B.partial, (const SolveScalars*)sc, nodes, B.actp);
       scalar(B, sc, mode, 0, 0, st, nb);
     } else {
       scalar(B, sc, mode, 0, 0, st, nrz);
@@ -695,8 +741,8 @@ static cudaError_t pcg_loop(SolverBufs& B, const TAop* aop, const TA0* a0, T* x,
   };
   precondition(SM_RZ0);
   if (!tiled)
-    launch(cls<T>("pupdate", true), nbytes<T, T>(N, S, 2, 0), k_p_update<T>, g, kBlock, 0, st, pbuf[0], z,
-           (const SolveScalars*)sc, nodes, 1);
+    launch(cls<T>("pupdate", true), nbytes<T, T>(N, B.n_act, 2, 0), k_p_update<T>, g(), kBlock, 0, st, pbuf[0], z,
+           (const SolveScalars*)sc, nodes, 1, B.actp);
   const double tol2 = prm.rtol * prm.rtol;
   const int nit = fixed_iters > 0 ? fixed_iters : prm.max_iter;
   const int napply = tiled ? tiled_blocks_per_sample(N, S, (int)sizeof(T)) : nb;
@@ -704,33 +750,33 @@ static cudaError_t pcg_loop(SolverBufs& B, const TAop* aop, const TA0* a0, T* x,
     T* p;
     if (tiled) {
       p = pbuf[cur ^ 1];
-      tiled_apply<T, TAop>(z, pbuf[cur], p, aop, q, B.partial, sc, N, S, it == 0, st);
+      tiled_apply<T, TAop>(z, pbuf[cur], p, aop, q, B.partial, sc, N, B.batch(), it == 0, st);
       cur ^= 1;
     } else {
       p = pbuf[0];
-      launch(cls<T>("apply", true), nbytes<T, TAop>(N, S, 2, 1), k_apply_dot<T, TAop>, g, kBlock, 0, st, (const T*)p,
-             aop, q, B.partial, (const SolveScalars*)sc, N);
+      launch(cls<T>("apply", true), nbytes<T, TAop>(N, B.n_act, 2, 1), k_apply_dot<T, TAop>, g(), kBlock, 0, st,
+             (const T*)p, aop, q, B.partial, (const SolveScalars*)sc, N, B.actp);
     }
     scalar(B, sc, SM_ALPHA, 0, 0, st, napply);
     if (fixed_iters > 0) {
-      launch(cls<T>("update", true), nbytes<T, T>(N, S, 6, 0), k_update_xr<T, false>, g, kBlock, 0, st, x, r,
-             (const T*)p, (const T*)q, B.partial, (const SolveScalars*)sc, nodes);
+      launch(cls<T>("update", true), nbytes<T, T>(N, B.n_act, 6, 0), k_update_xr<T, false>, g(), kBlock, 0, st, x, r,
+             (const T*)p, (const T*)q, B.partial, (const SolveScalars*)sc, nodes, B.actp);
       if (it == nit - 1) break;
     } else {
-      launch(cls<T>("update", true), nbytes<T, T>(N, S, 6, 0), k_update_xr<T, true>, g, kBlock, 0, st, x, r,
-             (const T*)p, (const T*)q, B.partial, (const SolveScalars*)sc, nodes);
+      launch(cls<T>("update", true), nbytes<T, T>(N, B.n_act, 6, 0), k_update_xr<T, true>, g(), kBlock, 0, st, x, r,
+             (const T*)p, (const T*)q, B.partial, (const SolveScalars*)sc, nodes, B.actp);
       scalar(B, sc, SM_CONV, tol2, prm.max_iter, st, nb);
       if ((it + 1) % prm.check_every == 0 || it + 1 == nit) {
         int n = 0;
-        cudaError_t e = count_active(B, sc, st, n);
+        cudaError_t e = compact_active(B, sc, st, n);
         if (e != cudaSuccess) return e;
         if (n == 0) break;
       }
     }
     precondition(SM_BETA);
     if (!tiled)
-      launch(cls<T>("pupdate", true), nbytes<T, T>(N, S, 3, 0), k_p_update<T>, g, kBlock, 0, st, pbuf[0], z,
-             (const SolveScalars*)sc, nodes, 0);
+      launch(cls<T>("pupdate", true), nbytes<T, T>(N, B.n_act, 3, 0), k_p_update<T>, g(), kBlock, 0, st, pbuf[0], z,
+             (const SolveScalars*)sc, nodes, 0, B.actp);
   }
   return cudaGetLastError();
 }
@@ -742,10 +788,12 @@ static cudaError_t pcg_loop(SolverBufs& B, const TAop* aop, const TA0* a0, T* x,
 // x need not be initialised: the first iteration that updates it assigns.  Instead
 // of the last x += alpha p, the final update is fused with the refinement step into
 // x_out (+)= x + alpha p (k_finish_step; assign on the first refinement step).
+// Runs over the samples the refinement left active (B.n_act, B.actp).
 static cudaError_t pcg_inner_fused(SolverBufs& B, const float* a32, const __nv_bfloat16* abf, float* x, float* r,
                                    SolveScalars* sc, const PcgParams& prm, int iters, cudaStream_t st,
                                    float2* x_out, const SolveScalars* sco, bool assign_out) {
-  const int S = B.S, N = B.N;
+  const int S = B.S, N = B.N, n = B.n_act;
+  const Batch bt = B.batch();
   const long long nodes = nodes_of(N);
   const float omega = (float)prm.omega;
   float* rb[2] = {r, (float*)B.r2};
@@ -760,15 +808,15 @@ static cudaError_t pcg_inner_fused(SolverBufs& B, const float* a32, const __nv_b
     float* pold = pb[pc];
     float* pnew = pb[pc ^ 1];
     if (it == 0)
-      tiled_apply<float, float>(z, pold, pnew, a32, q, B.partial, sc, N, S, 1, st);
+      tiled_apply<float, float>(z, pold, pnew, a32, q, B.partial, sc, N, bt, 1, st);
     else
-      tiled_apply_x(z, pold, pnew, a32, q, x, B.partial, sc, N, S, st, it == 1);
+      tiled_apply_x(z, pold, pnew, a32, q, x, B.partial, sc, N, bt, st, it == 1);
     pc ^= 1;
     scalar(B, sc, SM_ALPHA, 0, 0, st, napply);
     if (it == iters - 1) {
-      launch("finish_step", (double)S * nodes * ((iters > 1 ? 4 : 0) + 4 + (assign_out ? 8 : 16)), k_finish_step,
-             grid_nodes(N, S), kBlock, 0, st, x_out, (const float*)x, (const float*)pnew, (const SolveScalars*)sc,
-             sco, nodes, N, assign_out ? 1 : 0, iters > 1 ? 0 : 1);
+      launch("finish_step", (double)n * nodes * ((iters > 1 ? 4 : 0) + 4 + (assign_out ? 8 : 16)), k_finish_step,
+             grid_nodes(N, n), kBlock, 0, st, x_out, (const float*)x, (const float*)pnew, (const SolveScalars*)sc,
+             sco, nodes, N, assign_out ? 1 : 0, iters > 1 ? 0 : 1, B.actp);
       break;
     }
     nrz = vcycle<float, __nv_bfloat16>(B, rb[rc], abf, sc, omega, st, q, rb[rc ^ 1]);
@@ -838,6 +886,7 @@ static cudaError_t clear_tiled(SolverBufs& B, int elem, cudaStream_t st) {
 
 cudaError_t pcg_fp64(SolverBufs& B, const double* a64, const double* b, long long bstride, double* x_out,
                      const PcgParams& prm, cudaStream_t st) {
+  launch_all(B);
   const dim3 g = grid_nodes(B.N, B.S);
   double* r = (double*)B.r;
   cudaError_t e = clear_tiled(B, 8, st);
@@ -854,7 +903,6 @@ cudaError_t ir_mixed(SolverBufs& B, const float* a32, const __nv_bfloat16* abf, 
                      int fixed_steps, const float2* b_pair, bool pair_out) {
   const int N = B.N, S = B.S;
   const long long nodes = nodes_of(N);
-  const dim3 g = grid_nodes(N, S);
   const int nb = node_blocks(N);
   const bool tiled = N >= kTiledMinN && B.J >= 1;
   SolveScalars* sco = B.sc;
@@ -863,6 +911,8 @@ cudaError_t ir_mixed(SolverBufs& B, const float* a32, const __nv_bfloat16* abf, 
   float* r32 = (float*)B.r;
   const double tol2 = prm.rtol * prm.rtol;
   const double bb = (double)(bstride ? S : 1) * nodes * 8;
+  launch_all(B);
+  auto g = [&]() { return grid_nodes(N, B.n_act); };
   cudaError_t e = clear_tiled(B, 4, st);
   if (e != cudaSuccess) return e;
   // tiled grids: the FP32 residual is written directly (first from b, then by the
@@ -882,7 +932,7 @@ cudaError_t ir_mixed(SolverBufs& B, const float* a32, const __nv_bfloat16* abf, 
              k_init32<false>, gi, kBlock, 0, st, b, b_pair, bstride, r32, B.bdf, B.partial, nodes, N);
     scalar(B, sco, SM_INIT, 0, 0, st, init_blocks(N));
   } else {
-    launch("init_f64", bb + nbytes<double, double>(N, S, 2, 0), k_init<double>, g, kBlock, 0, st, b, bstride, r64,
+    launch("init_f64", bb + nbytes<double, double>(N, S, 2, 0), k_init<double>, g(), kBlock, 0, st, b, bstride, r64,
            x_out, B.partial, nodes);
     scalar(B, sco, SM_INIT, 0, 0, st, nb);
   }
@@ -890,25 +940,28 @@ cudaError_t ir_mixed(SolverBufs& B, const float* a32, const __nv_bfloat16* abf, 
     if (step > 0) {
       const int cap = fixed_steps > 0 ? fixed_steps : prm.max_iter;
       if (tiled) {
-        tiled_res64(bdf, bstride, xdf, a32, r32, B.partial, sco, N, S, st);
+        tiled_res64(bdf, bstride, xdf, a32, r32, B.partial, sco, N, B.batch(), st);
         scalar(B, sco, SM_OUTER_CONV, tol2, cap, st, tiled_blocks_per_sample(N, S, 8));
       } else {
-        launch("resid64", bb + nbytes<double, float>(N, S, 2, 1), k_residual64<float>, g, kBlock, 0, st, b, bstride,
-               (const double*)x_out, a32, r64, B.partial, (const SolveScalars*)sco, N);
+        launch("resid64", (double)(bstride ? B.n_act : 1) * nodes * 8 + nbytes<double, float>(N, B.n_act, 2, 1),
+               k_residual64<float>, g(), kBlock, 0, st, b, bstride, (const double*)x_out, a32, r64, B.partial,
+               (const SolveScalars*)sco, N, B.actp);
         scalar(B, sco, SM_OUTER_CONV, tol2, cap, st, nb);
       }
     }
     if (fixed_steps > 0) {
       if (step == fixed_steps) break;  // masked steps: no host round trip
-    } else {
+    } else if (step > 0) {
+      // host-checked: only the samples still above rtol take the next step (the first
+      // step launches every sample: it also defines x of those that take no step)
       int n = 0;
-      e = count_active(B, sco, st, n);
+      e = compact_active(B, sco, st, n);
       if (e != cudaSuccess) return e;
       if (n == 0) break;
     }
     if (!tiled)
-      launch("demote", (double)S * nodes * 16, k_demote, g, kBlock, 0, st, (const double*)r64, r32, d,
-             (const SolveScalars*)sco, nodes);
+      launch("demote", (double)B.n_act * nodes * 16, k_demote, g(), kBlock, 0, st, (const double*)r64, r32, d,
+             (const SolveScalars*)sco, nodes, B.actp);
     scalar(B, sci, SM_INNER_BEGIN, 0, 0, st, nb, 0, sco);
     if (tiled) {
       e = pcg_inner_fused(B, a32, abf, d, r32, sci, prm, inner_iters, st, xdf, sco, step == 0);
@@ -916,13 +969,15 @@ cudaError_t ir_mixed(SolverBufs& B, const float* a32, const __nv_bfloat16* abf, 
     } else {
       e = pcg_loop<float, float, __nv_bfloat16>(B, a32, abf, d, r32, sci, prm, inner_iters, st);
       if (e != cudaSuccess) return e;
-      launch("accum", (double)S * nodes * 20, k_accumulate, g, kBlock, 0, st, x_out, (const float*)d,
-             (const SolveScalars*)sco, nodes);
+      launch("accum", (double)B.n_act * nodes * 20, k_accumulate, g(), kBlock, 0, st, x_out, (const float*)d,
+             (const SolveScalars*)sco, nodes, B.actp);
     }
     scalar(B, sco, SM_OUTER_STEP, 0, 0, st, nb, inner_iters);
   }
+  launch_all(B);
   if (tiled && !pair_out)
-    launch("store_x", (double)S * nodes * 16, k_store_pair, g, kBlock, 0, st, x_out, (const float2*)xdf, nodes);
+    launch("store_x", (double)S * nodes * 16, k_store_pair, grid_nodes(N, S), kBlock, 0, st, x_out,
+           (const float2*)xdf, nodes);
   return cudaGetLastError();
 }
 

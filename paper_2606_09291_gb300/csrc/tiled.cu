@@ -56,6 +56,7 @@ struct TiledArgs {
   void* x;           // APPLYX: solution updated in place with alpha_prev * p_old
   double* partial;   // [S][blocks per sample]
   const SolveScalars* sc;
+  const int* act;    // launched samples (null: blockIdx.z / nzc itself)
   long long bstride; // RES64: b stride per sample (0 = shared)
   int N;
   int nzc;           // z chunks per sample
@@ -158,7 +159,8 @@ __global__ void __launch_bounds__(NT) k_tiled(TiledArgs A) {
   TA* cs = (TA*)(smraw + L::cells);
   const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * TX + tx;
   const int N = A.N, n1 = N + 1;
-  const int s = blockIdx.z / A.nzc, chunk = blockIdx.z % A.nzc;
+  const int chunk = blockIdx.z % A.nzc;
+  const int s = A.act != nullptr ? A.act[blockIdx.z / A.nzc] : (int)(blockIdx.z / A.nzc);
   if (A.sc != nullptr && !A.sc[s].active) return;
   const int x0 = 1 + TX * blockIdx.x, y0 = 1 + G::TYT * blockIdx.y;
   const long long nodes = (long long)n1 * n1 * n1, cells = (long long)N * N * N;
@@ -703,18 +705,22 @@ TiledShape tiled_shape(int N, int S, int ry) {
   return t;
 }
 
+// The tile shape follows the batch size bt.S (not the number of samples launched),
+// so a sample's partial sums, and with them its iterates, do not depend on how many
+// other samples are still active.
 template <typename T, typename TA, int MODE>
-static void run_tiled(const char* cls, double bytes, TiledArgs args, int S, cudaStream_t st) {
-  const TiledShape t = tiled_shape(args.N, S, RowsPerThread<T>::value);
+static void run_tiled(const char* cls, double bytes, TiledArgs args, const Batch& bt, cudaStream_t st) {
+  const TiledShape t = tiled_shape(args.N, bt.S, RowsPerThread<T>::value);
   args.nzc = t.nzc;
   args.zc = t.zc;
+  args.act = bt.act;
   const size_t smem = TiledSmem<T, TA, MODE>::total;  // up to ~91 KB (FP64): opt in above 48 KB
   static bool smem_set = false;  // once per instantiation (capture-friendly)
   if (smem > 48 * 1024 && !smem_set) {
     cudaFuncSetAttribute(k_tiled<T, TA, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     smem_set = true;
   }
-  launch(cls, bytes, k_tiled<T, TA, MODE>, dim3(t.bx, t.by, (unsigned)(S * t.nzc)), dim3(TX, TY), smem, st, args);
+  launch(cls, bytes, k_tiled<T, TA, MODE>, dim3(t.bx, t.by, (unsigned)(bt.n * t.nzc)), dim3(TX, TY), smem, st, args);
 }
 
 template <typename T, typename TA>
@@ -735,50 +741,50 @@ static const char* name(const char* base, const char* t) {
 // this tile writes the new one.
 template <typename T, typename TA>
 void tiled_apply(const T* z, const T* pold, T* pnew, const TA* a, T* q, double* partial, const SolveScalars* sc, int N,
-                 int S, int first, cudaStream_t st) {
+                 const Batch& bt, int first, cudaStream_t st) {
   TiledArgs A{};
   A.in0 = z; A.in1 = pold; A.a = a; A.out0 = q; A.out1 = pnew; A.partial = partial; A.sc = sc; A.N = N;
   A.first = first;
-  run_tiled<T, TA, TM_APPLY>(name("apply", tag<T>()), vbytes<T, TA>(N, S, first ? 3 : 4, 1), A, S, st);
+  run_tiled<T, TA, TM_APPLY>(name("apply", tag<T>()), vbytes<T, TA>(N, bt.n, first ? 3 : 4, 1), A, bt, st);
 }
 // fused variants of the mixed inner solve (see TM_PREU / TM_APPLYX)
 void tiled_apply_x(const float* z, const float* pold, float* pnew, const float* a, float* q, float* x, double* partial,
-                   const SolveScalars* sc, int N, int S, cudaStream_t st, bool x_first) {
+                   const SolveScalars* sc, int N, const Batch& bt, cudaStream_t st, bool x_first) {
   TiledArgs A{};
   A.in0 = z; A.in1 = pold; A.a = a; A.out0 = q; A.out1 = pnew; A.x = x; A.partial = partial; A.sc = sc; A.N = N;
   A.xfirst = x_first ? 1 : 0;
-  run_tiled<float, float, TM_APPLYX>("apply_f32", vbytes<float, float>(N, S, x_first ? 5 : 6, 1), A, S, st);
+  run_tiled<float, float, TM_APPLYX>("apply_f32", vbytes<float, float>(N, bt.n, x_first ? 5 : 6, 1), A, bt, st);
 }
 void tiled_pre_update(const float* r, const float* q, const __nv_bfloat16* a, const float* dinv, float* t, float* rnew,
-                      const SolveScalars* sc, int N, int S, double omega, cudaStream_t st) {
+                      const SolveScalars* sc, int N, const Batch& bt, double omega, cudaStream_t st) {
   TiledArgs A{};
   A.in0 = r; A.q = q; A.a = a; A.dinv = dinv; A.out0 = t; A.out1 = rnew; A.sc = sc; A.N = N; A.omega = omega;
-  run_tiled<float, __nv_bfloat16, TM_PREU>("pre_f32", vbytes<float, __nv_bfloat16>(N, S, 5, 1), A, S, st);
+  run_tiled<float, __nv_bfloat16, TM_PREU>("pre_f32", vbytes<float, __nv_bfloat16>(N, bt.n, 5, 1), A, bt, st);
 }
 
 template <typename T, typename TA>
-void tiled_pre(const T* r, const TA* a, const T* dinv, T* t, const SolveScalars* sc, int N, int S, double omega,
-               cudaStream_t st) {
+void tiled_pre(const T* r, const TA* a, const T* dinv, T* t, const SolveScalars* sc, int N, const Batch& bt,
+               double omega, cudaStream_t st) {
   TiledArgs A{};
   A.in0 = r; A.a = a; A.dinv = dinv; A.out0 = t; A.sc = sc; A.N = N; A.omega = omega;
-  run_tiled<T, TA, TM_PRE>(name("pre", tag<T>()), vbytes<T, TA>(N, S, 3, 1), A, S, st);
+  run_tiled<T, TA, TM_PRE>(name("pre", tag<T>()), vbytes<T, TA>(N, bt.n, 3, 1), A, bt, st);
 }
 template <typename T, typename TA>
 void tiled_post(const T* r, const TA* a, const T* dinv, const T* ec, T* z, double* partial, const SolveScalars* sc,
-                int N, int S, double omega, cudaStream_t st) {
+                int N, const Batch& bt, double omega, cudaStream_t st) {
   TiledArgs A{};
   A.in0 = r; A.a = a; A.dinv = dinv; A.ec = ec; A.out0 = z; A.partial = partial; A.sc = sc; A.N = N;
   A.omega = omega;
-  run_tiled<T, TA, TM_POST>(name("post", tag<T>()), vbytes<T, TA>(N, S, 3, 1) + vbytes<T, T>(N / 2, S, 1, 0), A, S,
-                            st);
+  run_tiled<T, TA, TM_POST>(name("post", tag<T>()), vbytes<T, TA>(N, bt.n, 3, 1) + vbytes<T, T>(N / 2, bt.n, 1, 0), A,
+                            bt, st);
 }
 void tiled_res64(const float2* b, long long bstride, const float2* x, const float* a, float* r32, double* partial,
-                 const SolveScalars* sc, int N, int S, cudaStream_t st) {
+                 const SolveScalars* sc, int N, const Batch& bt, cudaStream_t st) {
   TiledArgs A{};
   A.in0 = x; A.in1 = b; A.bstride = bstride; A.a = a; A.out0 = r32; A.partial = partial; A.sc = sc; A.N = N;
-  const double bb = (double)(bstride ? S : 1) * nodes_of(N) * 8;
-  run_tiled<double, float, TM_RES64>("resid64", bb + vbytes<double, float>(N, S, 1, 1) + (double)S * nodes_of(N) * 4, A,
-                                     S, st);
+  const double bb = (double)(bstride ? bt.n : 1) * nodes_of(N) * 8;
+  run_tiled<double, float, TM_RES64>("resid64", bb + vbytes<double, float>(N, bt.n, 1, 1) + (double)bt.n * nodes_of(N) * 4,
+                                     A, bt, st);
 }
 
 int tiled_phi_df(const float2* y, int N, int S, const float2* gtab, const float2* mgtab, float2* badj,
@@ -798,21 +804,21 @@ int tiled_phi(const double* y, int N, int S, const double* gtab, const double* m
 }
 
 template void tiled_apply<float, float>(const float*, const float*, float*, const float*, float*, double*,
-                                        const SolveScalars*, int, int, int, cudaStream_t);
+                                        const SolveScalars*, int, const Batch&, int, cudaStream_t);
 template void tiled_apply<double, double>(const double*, const double*, double*, const double*, double*, double*,
-                                          const SolveScalars*, int, int, int, cudaStream_t);
+                                          const SolveScalars*, int, const Batch&, int, cudaStream_t);
 template void tiled_pre<float, __nv_bfloat16>(const float*, const __nv_bfloat16*, const float*, float*,
-                                              const SolveScalars*, int, int, double, cudaStream_t);
-template void tiled_pre<float, float>(const float*, const float*, const float*, float*, const SolveScalars*, int, int,
-                                      double, cudaStream_t);
+                                              const SolveScalars*, int, const Batch&, double, cudaStream_t);
+template void tiled_pre<float, float>(const float*, const float*, const float*, float*, const SolveScalars*, int,
+                                      const Batch&, double, cudaStream_t);
 template void tiled_post<float, float>(const float*, const float*, const float*, const float*, float*, double*,
-                                       const SolveScalars*, int, int, double, cudaStream_t);
+                                       const SolveScalars*, int, const Batch&, double, cudaStream_t);
 template void tiled_pre<double, double>(const double*, const double*, const double*, double*, const SolveScalars*, int,
-                                        int, double, cudaStream_t);
+                                        const Batch&, double, cudaStream_t);
 template void tiled_post<float, __nv_bfloat16>(const float*, const __nv_bfloat16*, const float*, const float*, float*,
-                                               double*, const SolveScalars*, int, int, double, cudaStream_t);
+                                               double*, const SolveScalars*, int, const Batch&, double, cudaStream_t);
 template void tiled_post<double, double>(const double*, const double*, const double*, const double*, double*, double*,
-                                         const SolveScalars*, int, int, double, cudaStream_t);
+                                         const SolveScalars*, int, const Batch&, double, cudaStream_t);
 
 }  // namespace mlsgd
 

@@ -1,22 +1,27 @@
 """Parity at the full size of the benchmark workload, in the configuration the
-benchmark times (bench.workload_cfg): 4096 level-3 samples (64^3 cells), 256 KL
-modes, mixed precision at rtol 1e-8, one batch of 4096 per call.
+benchmark times (bench.workload_cfg with the benchmark's default arguments):
+4096 level-3 samples (64^3 cells) with their level-2 partners, 256 KL modes,
+mixed precision at rtol 1e-8, one batch of 4096 per call.
 
-The oracle cannot process 4096 samples in seconds, so:
-(a) one full-batch field and solve through the C ABI is compared with the oracle
-    on sampled samples (first, middle, last): xi and log a to rounding; the state
-    and adjoint solutions through the solver's contract, ||b - A y|| <= rtol ||b||
-    with the oracle's assembled operator on the coefficient the mixed path solves
-    with (exp(log a) rounded to FP32), and against the oracle's own solutions at the
-    mixed path's bar (1e-6; an oracle solve at rtol 5e-9 on the FP32-rounded
-    coefficient is 2e-9..4e-9 from them at this size); Phi = 1/2 e^T M e from the
-    returned state;
-(b) the full-batch level record equals the Chan merge of the records of its two
-    halves (each sample's contribution depends only on its identity), a property
-    that holds at any size.
+(a) The timed call itself, mlsgd_level_gradient over samples 0..4095 of step 0,
+    against the oracle's record of the same samples (tests/golden/
+    c3_level3_record.npz, written by tests/golden/make_c3_record.py, which calls
+    only oracle/; oracle solves at rtol 1e-13): count bit-exact, the mean of dX~
+    element by element, the mean of dY~ and both second-order sums within the
+    mixed path's bar 1e-6, compared in unshifted units.
+(b) The same full-batch field and solve through mlsgd_solve_state_adjoint against
+    the oracle on sampled samples (first, middle, last): xi and log a to rounding;
+    the state and adjoint solutions through the solver's contract,
+    ||b - A y|| <= rtol ||b|| with the oracle's assembled operator on the
+    coefficient the mixed path solves with (exp(log a) rounded to FP32), and
+    against the oracle's own solutions at the mixed path's bar (1e-6); Phi from
+    the returned state.
+(c) The full-batch level record equals the Chan merge of the records of its two
+    halves (each sample's contribution depends only on its identity; the level
+    differences are accumulated in FP64), a property that holds at any size.
 Named to run after the other GPU tests (they are cheaper and say more when they
 fail); the allocation-free entry point's test stays last."""
-import types
+import os
 
 import numpy as np
 import pytest
@@ -43,8 +48,36 @@ def lib():
     return mlsgd
 
 
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "c3_level3_record.npz")
+
+
 def bench_cfg():
-    return bench.workload_cfg(types.SimpleNamespace(precision="mixed", samples=S, ir_steps=3))
+    args = bench.parser().parse_args([])
+    assert args.samples == S and args.precision == "mixed"
+    return bench.workload_cfg(args)
+
+
+def test_timed_call_matches_oracle_record(lib):
+    ref = np.load(GOLDEN)
+    assert int(ref["count"]) == S and int(ref["level"]) == LEVEL and int(ref["first_sample"]) == 0
+    cfg = bench_cfg()
+    ctx = lib.Context(**cfg)
+    zt = torch.tensor(inputs.z_test(8 << LEVEL), dtype=torch.float64, device="cuda")
+    st = ctx.new_stats(LEVEL)
+    ctx.mlsgd_level_gradient(int(ref["iteration"]), LEVEL, 0, S, zt, st)
+    h = st.host()
+    field = st.field.cpu().numpy()
+    ctx.close()
+    assert h["count"] == S and h["noconv"] == 0
+    theta = cfg["theta"]
+    fg, fo = np.exp(theta * h["shift"]), np.exp(theta * float(ref["shift"]))
+    assert abs(h["shift"] - float(ref["shift"])) <= TOLMIX * abs(float(ref["shift"]))
+    assert rel_err(field * fg, ref["mean_x"] * fo) <= TOLMIX
+    my = float(ref["mean_y"]) * fo
+    assert abs(h["mean_dy"] * fg - my) <= TOLMIX * abs(my)
+    for k_gpu, k_ref in (("s2_dx", "s2_x"), ("s2_dy", "s2_y")):
+        r = float(ref[k_ref]) * fo ** 2
+        assert abs(h[k_gpu] * fg ** 2 - r) <= TOLMIX * r, (k_gpu, h[k_gpu] * fg ** 2, r)
 
 
 def oracle_workload():

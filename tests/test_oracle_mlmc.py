@@ -137,6 +137,22 @@ def test_chan_merge_matches_two_pass(n):
             assert abs(AB.s2_x - S.s2_x) < 1e-11 and abs(AB.s2_y - S.s2_y) < 1e-11
 
 
+def test_merge_of_records_at_different_shifts():
+    """Records of disjoint sample ranges, each at its own shift (the largest Phi of
+    its own samples), merge into the record of the whole range at its shift."""
+    W = _small(n_levels=2, theta=40.0)
+    z = _ctrl_field(W.Nc, "test") + 3.0 * _ctrl_field(W.Nc, "rand", 2)
+    whole = mlmc.level_batch(W, 1, 1, range(7), z)
+    parts = [mlmc.level_batch(W, 1, 1, r, z) for r in (range(0, 2), range(2, 3), range(3, 7))]
+    assert len({p["shift"] for p in parts}) > 1  # the parts' shifts differ
+    m = mlmc.merge_shifted(parts, W.theta, W.hc3)
+    a, b = m["stats"], whole["stats"]
+    assert m["shift"] == whole["shift"] and a.n == b.n == 7
+    assert np.abs(a.mean_x - b.mean_x).max() <= 1e-13 * np.abs(b.mean_x).max()
+    assert abs(a.mean_y - b.mean_y) <= 1e-13 * abs(b.mean_y)
+    assert abs(a.s2_x - b.s2_x) <= 1e-11 * b.s2_x and abs(a.s2_y - b.s2_y) <= 1e-11 * b.s2_y
+
+
 def test_truncation_of_denominator():
     W = _small(theta=2.0)
     S = mlmc.Stats(4, np.ones(W.Nc ** 3), 0.0, 1e-6, 0.0)  # E^ML[Y~] far below exp(-theta c)
@@ -177,6 +193,44 @@ def test_alpha_fit_and_level_update():
     assert p["L"] == 5 and len(p["M"]) == 5
     p = controller.plan(infos, EX_norm2=1.0, EY=1.0, grad_norm=1e-3, eta=0.9, n0=8, L_max=4)
     assert p["L"] == 4
+
+
+def test_plan_undoes_the_shift():
+    """v^2, err_sam and the plan are in unshifted units (eq:sec-order-sum,
+    eq:mse-estimate-mlmc, eq:optimal-batch-size): records kept with nonzero shifts
+    c_l (X~ = exp(-theta c_l) X) must give the plan that the unshifted per-sample data
+    give, and v^2 must equal the second-order sums formed directly from the unshifted
+    data.  Converting back with exp(theta c) instead of exp(2 theta c) fails this."""
+    rng = np.random.default_rng(11)
+    theta, hc3, ncell = 7.0, 1.0 / 512, 512
+    shifts = [0.31, 0.27, 0.33]
+    counts = [40, 12, 5]
+    raw, shifted = [], []
+    for l, (c, n) in enumerate(zip(shifts, counts)):
+        dX = rng.standard_normal((n, ncell)) * 2.0 ** -l + 0.3 * 4.0 ** -l
+        dY = rng.standard_normal(n) * 0.1 * 2.0 ** -l + 4.0 ** -l
+        mx, my = dX.mean(0), dY.mean()
+        s2x = hc3 * float(((dX - mx) ** 2).sum())  # sum_m ||dX_m - mean||_U^2, two passes
+        s2y = float(((dY - my) ** 2).sum())
+        raw.append(dict(n=n, mx=mx, my=my, s2x=s2x, s2y=s2y))
+        f = np.exp(-theta * c)
+        shifted.append(_info(n, s2x * f * f, s2y * f * f, hc3 * float(mx @ mx) * f * f, my * f, shift=c,
+                             theta=theta))
+    EX = sum(r["mx"] for r in raw)
+    EY = sum(r["my"] for r in raw)
+    cstar = max(shifts)
+    g = 0.05
+    p = controller.plan(shifted, EX_norm2=hc3 * float(EX @ EX) * np.exp(-2 * theta * cstar),
+                        EY=EY * np.exp(-theta * cstar), grad_norm=g, eta=0.9, n0=8, L_max=4)
+    C_hat = hc3 * float(EX @ EX) / EY ** 2
+    v2 = [r["s2x"] + C_hat * r["s2y"] for r in raw]
+    assert np.allclose(p["v2"], v2, rtol=1e-12, atol=0)
+    err_sam = sum(v / (r["n"] * (r["n"] - 1)) for v, r in zip(v2, raw))
+    assert abs(p["err_sam"] - err_sam) <= 1e-12 * err_sam
+    q = controller.plan([_info(r["n"], r["s2x"], r["s2y"], hc3 * float(r["mx"] @ r["mx"]), r["my"], theta=theta)
+                         for r in raw], EX_norm2=hc3 * float(EX @ EX), EY=EY, grad_norm=g, eta=0.9, n0=8, L_max=4)
+    assert p["M"] == q["M"] and p["L"] == q["L"]
+    assert abs(p["err_num"] - q["err_num"]) <= 1e-12 * q["err_num"]
 
 
 def inputs_z_test(Nc):
