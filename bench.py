@@ -35,12 +35,19 @@ UNIT = "sample-gradients/s"
 
 
 def workload_cfg(args):
-    from paper_2606_09291_gb300 import inputs
+    """The c3 configuration; the mixed path takes the autotuner's knobs for this batch
+    from the committed cache (paper_2606_09291_gb300/tuned.json) when it has them."""
+    from paper_2606_09291_gb300 import autotune, inputs
     p = dict(inputs.PRESETS["c3"])
-    return dict(n_levels=p["n_levels"], n0=p["n0"], n_modes=p["n_modes"], corr_len=p["corr_len"], sigma=p["sigma"],
-                theta=p["theta"], alpha=p["alpha"], seed=p["seed"], rtol=1e-8, max_iter=50,
-                precision=args.precision, max_batch=args.samples, ctrl_level=p["n_levels"] - 1,
-                field_tc=1 if args.precision == "mixed" else 0, ir_steps=args.ir_steps)
+    cfg = dict(n_levels=p["n_levels"], n0=p["n0"], n_modes=p["n_modes"], corr_len=p["corr_len"], sigma=p["sigma"],
+               theta=p["theta"], alpha=p["alpha"], seed=p["seed"], rtol=1e-8, max_iter=50,
+               precision=args.precision, max_batch=args.samples, ctrl_level=p["n_levels"] - 1,
+               field_tc=1 if args.precision == "mixed" else 0, ir_steps=args.ir_steps)
+    if args.precision == "mixed" and not getattr(args, "no_tuned", False):
+        knobs = autotune.lookup(cfg, p["level"], args.samples)
+        if knobs:
+            cfg.update(knobs)
+    return cfg
 
 
 def workload_name(args):
@@ -219,7 +226,7 @@ def run_gpu(args, rank, world):
     import torch.distributed as dist
 
     import __graft_entry__
-    from paper_2606_09291_gb300 import inputs, mlsgd
+    from paper_2606_09291_gb300 import distributed, inputs, mlsgd
 
     if world > 1:  # one rank compiles (in-tree outputs are shared), the others load after it
         if rank == 0:
@@ -245,6 +252,8 @@ def run_gpu(args, rank, world):
     def step(k):
         ctx.mlsgd_stats_reset(stats)
         ctx.mlsgd_level_gradient(k, level, first, S, z, stats)
+        if world > 1:  # the level record of all ranks' samples (all-gather + the library's Chan merge)
+            distributed.allgather_merge(ctx, stats)
 
     def barrier():
         if world > 1:
@@ -280,6 +289,7 @@ def run_gpu(args, rank, world):
     prof = mlsgd.mlsgd_profile_stop().get(dominant)
     gpu_launches = mlsgd.mlsgd_launch_count() - launches0
     clocks = sampler.stop() if sampler else None
+    ws_bytes = ctx.mlsgd_workspace_bytes(level, S)
     if world > 1:
         t = torch.tensor([total_ms], device="cuda")
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
@@ -335,6 +345,15 @@ def run_gpu(args, rank, world):
                 "iters_per_sample": st64.host()["iters"] / args.fp64_samples}
         ctx64.close()
 
+    # serving: the C4 mix (levels 0..5) through the continuous-batching server with its
+    # HBM arena; estimates arrive all at once (saturation) and as a Poisson stream at
+    # half that rate; latency from arrival to the last level's completion
+    serve = None
+    if args.serving and rank == 0 and world == 1:
+        ctx.close()
+        torch.cuda.empty_cache()
+        serve = serving_leg(args)
+
     peaks, peak_kind = load_peaks()
     roof = None
     if prof and prof["launches"] > 0:
@@ -388,19 +407,53 @@ def run_gpu(args, rank, world):
                 "dtype": "f32+f64 (bf16 coefficient)" if args.precision == "mixed" else "f64", "data": "synthetic",
                 "config": {"workload": workload_name(args), "samples_per_step_per_gpu": S, "level": level,
                            "partner_level": level - 1, "n_modes": 256, "l2": "inputs larger than L2 (batch working "
-                           "set %.0f GB)" % (ctx.mlsgd_workspace_bytes(level, S) / 1e9),
-                           "parallelism": "replicas" if world > 1 else "single GPU"},
+                           "set %.0f GB)" % (ws_bytes / 1e9),
+                           "parallelism": ("samples sharded over ranks, records all-gathered and merged "
+                                           "every step") if world > 1 else "single GPU",
+                           "knobs": {k: cfg.get(k) for k in ("stencil", "z_chunks", "inner_iters", "omega",
+                                                             "ir_steps", "max_batch")},
+                           "knobs_source": "autotuner cache" if any(k in cfg for k in ("inner_iters", "omega"))
+                           else "defaults"},
                 "latency_ms": {"p50": statistics.median(step_ms), "p99": p99, "per": "step (one batch)"},
                 "solver_iters_per_sample": iters_per_sample,
                 "roofline": roof, "roofline_kl_gemm": roof_gemm, "cpu_baseline": cpu,
                 "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": z.numel() * 8,
                         "d2h_bytes_per_step": (stats.field.numel() + mlsgd.NSCALARS) * 8},
-                "gpu_launches": gpu_launches, "clocks": clocks, "fp64_path": fp64,
+                "gpu_launches": gpu_launches, "clocks": clocks, "fp64_path": fp64, "serving": serve,
                 "mixed_over_fp64": (value / fp64["value"]) if fp64 else None,
                 "kernel_shares": {k: round(v["total_ms"] / total_prof, 4) for k, v in
                                   sorted(prof_all.items(), key=lambda kv: -kv[1]["total_ms"])[:8]}}
         print(json.dumps(line), flush=True)
     ctx.close()
+
+
+def serving_leg(args):
+    import numpy as np
+    import torch
+
+    from paper_2606_09291_gb300 import inputs, serving
+    cfg, mix = serving.mix_config("c4")
+    Nc = cfg["n0"] << (cfg["n_levels"] - 1)
+    z = torch.tensor(inputs.z_test(Nc), dtype=torch.float64, device="cuda")
+    srv = serving.ContinuousServer(cfg, args.serve_slots, [(l, m) for l, m in enumerate(mix)])
+    srv.run(serving.poisson_mix_requests(mix, 2, 0.0, first_estimate=50000), z)  # warm-up
+    sat = srv.run(serving.poisson_mix_requests(mix, args.serve_estimates, 0.0, first_estimate=60000), z)
+    span = max(r["done"] for r in sat) - min(r["start"] for r in sat)
+    cap = args.serve_estimates / span
+    res = srv.run(serving.poisson_mix_requests(mix, args.serve_estimates, 0.5 * cap, seed=3, first_estimate=70000), z)
+    est = {}
+    for r in res:
+        est.setdefault(r["estimate"], []).append(r)
+    lat = [1e3 * (max(x["done"] for x in v) - v[0]["arrival"]) for v in est.values()]
+    out = {"workload": "c4 mix %s over levels 0..5 (8^3 .. 256^3), K=128, theta 10, mixed, rtol 1e-8" % (list(mix),),
+           "slots": args.serve_slots, "hbm_budget_bytes": srv.budget,
+           "saturated_sample_gradients_per_s": cap * sum(mix), "saturated_estimates_per_s": cap,
+           "device_overlap_saturated": serving.device_overlap(sat),
+           "at_half_load": {"estimates_per_s": 0.5 * cap, "estimate_p50_ms": float(np.median(lat)),
+                            "estimate_p99_ms": serving.pct(lat, 0.99), "deferred_by_hbm": srv.deferred},
+           "estimates": args.serve_estimates}
+    srv.close()
+    return out
 
 
 def parser():
@@ -422,6 +475,10 @@ def parser():
     ap.add_argument("--ir-steps", type=int, default=0,
                     help="mixed path: 0 = refine until converged, launching only the samples still above rtol "
                          "(host check per step); k > 0 = exactly k masked steps (no host sync)")
+    ap.add_argument("--no-tuned", action="store_true", help="default kernel and smoother knobs, not the tuned ones")
+    ap.add_argument("--serving", type=int, default=1, help="1: also time the C4 serving mix (continuous batching)")
+    ap.add_argument("--serve-slots", type=int, default=6)
+    ap.add_argument("--serve-estimates", type=int, default=16)
     ap.add_argument("--traffic-bytes", type=float, default=None,
                     help="ncu dram read+write bytes per launch of the dominant kernel, if captured")
     return ap

@@ -93,6 +93,13 @@ typedef struct {
                        lambda = exp(-pi (j+k+l) corr_len), xi ~ U(-4, 4), not normalised */
   int target_freq;  /* g = prod_i sin(f pi x_i): 1 for the workload, 2 for the paper (0 = 1) */
   uint64_t seed;
+  /* kernel and smoother choices (none changes what a converged solve returns beyond
+     the solver tolerance; an autotuner picks them per grid and batch) */
+  int stencil;      /* MIXED only: 0 = whole-row slab passes on 32^3 and 64^3 grids,
+                       z-marching tile passes elsewhere; 1 = z-marching tile passes only  */
+  int z_chunks;     /* z chunks the fused passes split a sample into (0 = chosen from the
+                       batch size); results do not depend on it                          */
+  double omega;     /* damping of the Jacobi smoother in the V-cycle (0 = 0.6; (0, 1))    */
 } mlsgd_config;
 
 typedef struct mlsgd_ctx mlsgd_ctx;
@@ -170,6 +177,19 @@ int64_t mlsgd_n_ctrl_cells(const mlsgd_ctx* ctx);
 /* Bytes of library scratch one chunk of n_samples at `level` needs (both
  * grids of the level difference); used for admission by HBM footprint. */
 size_t mlsgd_workspace_bytes(const mlsgd_ctx* ctx, int level, int n_samples);
+
+/* Scratch owned by the caller: the context takes [ws_dev, ws_dev + bytes) (device
+ * memory, 256-byte aligned, kept valid while the context uses it) as its workspace
+ * instead of allocating its own, frees its own scratch if it had any (synchronising
+ * the device first), and never grows, frees or reallocates the caller's range: a
+ * call whose batch needs more (mlsgd_workspace_bytes) fails with MLSGD_ENOMEM.
+ * Every call of the context until the next mlsgd_set_workspace reads and writes the
+ * range, so a caller that hands disjoint ranges of one arena to several contexts can
+ * run them concurrently on different streams and admit work by memory footprint.
+ * ws_dev NULL with bytes 0 returns the context to allocating its own scratch.  The
+ * per-level tensor-core mode tables are still allocated by the context on the first
+ * call that needs them. */
+mlsgd_status mlsgd_set_workspace(mlsgd_ctx* ctx, void* ws_dev, size_t bytes);
 
 /* Copy the KL mode table to host arrays (each may be NULL):
  * idx [3*n_modes] 1D mode indices (x, y, z) of each 3D mode, lam [n_modes]

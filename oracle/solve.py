@@ -71,8 +71,10 @@ class GalerkinMG:
         return self._vcycle(0, r)
 
 
-def pcg(A, b, rtol, max_iter=100000, precond=None):
-    """Preconditioned CG; returns (x, iterations).  Raises if not converged."""
+def pcg(A, b, rtol, max_iter=100000, precond=None, max_restarts=50):
+    """Preconditioned CG; returns (x, iterations).  Raises if not converged, or when
+    the true residual stalls above rtol ||b|| (more than max_restarts restarts from the
+    true residual: rtol is below the residual FP64 can attain for this system)."""
     bn = np.linalg.norm(b)
     if bn == 0.0:
         return np.zeros_like(b), 0
@@ -84,6 +86,7 @@ def pcg(A, b, rtol, max_iter=100000, precond=None):
     z = precond(r)
     p = z.copy()
     rz = r @ z
+    restarts = 0
     for it in range(1, max_iter + 1):
         q = A @ p
         alpha = rz / (p @ q)
@@ -92,7 +95,18 @@ def pcg(A, b, rtol, max_iter=100000, precond=None):
         if np.linalg.norm(r) <= rtol * bn:
             if np.linalg.norm(b - A @ x) <= rtol * bn:
                 return x, it
-            r = b - A @ x  # recursive residual drifted: restart from the true one
+            # the recursive residual drifted below the true one: restart CG from the
+            # true residual (a fresh search direction; the old one belongs to the
+            # drifted recursion)
+            restarts += 1
+            if restarts > max_restarts:
+                raise RuntimeError("oracle PCG: true residual stalls at %.3g ||b|| above rtol %.3g" %
+                                   (np.linalg.norm(b - A @ x) / bn, rtol))
+            r = b - A @ x
+            z = precond(r)
+            p = z.copy()
+            rz = r @ z
+            continue
         z = precond(r)
         rz_new = r @ z
         p = z + (rz_new / rz) * p

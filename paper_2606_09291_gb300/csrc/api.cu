@@ -36,6 +36,7 @@ struct mlsgd_ctx {
   std::vector<float2*> d_gtab2, d_mgtab2;  // the same tables as FP32 (hi, lo) pairs
   char* ws = nullptr;
   size_t ws_size = 0;
+  bool ws_external = false;  // ws belongs to the caller (mlsgd_set_workspace): never grown or freed
   std::vector<__nv_bfloat16*> d_phiT;  // per level: tensor-core B operand [N^3][K] (built on first use)
   int* d_err = nullptr;                // device error flag of the tensor-core kernel
   int* count_host = nullptr;
@@ -111,6 +112,9 @@ size_t level_bytes(const mlsgd_ctx* ctx, int level, int S) {
 
 mlsgd_status ensure_ws(mlsgd_ctx* ctx, size_t bytes, cudaStream_t st) {
   if (bytes <= ctx->ws_size) return MLSGD_OK;
+  if (ctx->ws_external)
+    return fail(ctx, MLSGD_ENOMEM, "the caller's workspace holds " + std::to_string(ctx->ws_size) + " bytes, " +
+                                       std::to_string(bytes) + " needed");
   CK(cudaStreamSynchronize(st));
   if (ctx->ws) CK(cudaFree(ctx->ws));
   ctx->ws = nullptr;
@@ -185,12 +189,15 @@ mlsgd_status solve_grid(mlsgd_ctx* ctx, int N, int S, const GridFields& f, const
   SolverBufs B;
   carve_solver(B, N, S, ctx->mixed() ? 4 : 8, p);
   B.count_host = ctx->count_host;
+  B.err = ctx->d_err;
+  B.stencil = ctx->cfg.stencil;
+  B.zchunks = ctx->cfg.z_chunks;
   Bump bp{p};
   double* badj = bp.take<double>(S * nodes);
   double* b = bp.take<double>(nodes);
   double* r64 = ctx->mixed() ? bp.take<double>(S * nodes) : nullptr;
   double* ytmp = y ? y : bp.take<double>(S * nodes);
-  PcgParams prm{ctx->cfg.rtol, ctx->cfg.max_iter, 0.6, 4};
+  PcgParams prm{ctx->cfg.rtol, ctx->cfg.max_iter, ctx->cfg.omega > 0 ? ctx->cfg.omega : 0.6, 4};
   const int inner = ctx->cfg.inner_iters > 0 ? ctx->cfg.inner_iters : 6;
   if (ctx->mixed()) build_hierarchy_mixed(B, f.abf, st);
   else build_hierarchy_fp64(B, f.a64, st);
@@ -292,7 +299,8 @@ mlsgd_status mlsgd_create(const mlsgd_config* cfg, mlsgd_ctx** out) {
   if (c.n_levels < 1 || c.n_levels > 16 || c.n0 < 2 || (c.n0 & (c.n0 - 1)) != 0 || c.ctrl_level < 0 ||
       c.ctrl_level >= c.n_levels || c.n_modes < 2 || (c.field_model == 0 && (c.n_modes % 2) != 0) || c.n_modes > 4096 ||
       !(c.corr_len > 0) || !(c.rtol > 0) || c.max_iter < 1 || (c.precision != MLSGD_FP64 && c.precision != MLSGD_MIXED) ||
-      (c.n0 << (c.n_levels - 1)) > 1024 || c.field_model < 0 || c.field_model > 1 || c.target_freq < 0)
+      (c.n0 << (c.n_levels - 1)) > 1024 || c.field_model < 0 || c.field_model > 1 || c.target_freq < 0 ||
+      c.stencil < 0 || c.stencil > 1 || c.z_chunks < 0 || !(c.omega >= 0.0 && c.omega < 1.0))
     return MLSGD_EINVAL;
   int mcube = 0;
   if (c.field_model == 1) {
@@ -373,13 +381,26 @@ void mlsgd_destroy(mlsgd_ctx* ctx) {
   for (double* d : ctx->d_mgtab) cudaFree(d);
   for (float2* d : ctx->d_gtab2) cudaFree(d);
   for (float2* d : ctx->d_mgtab2) cudaFree(d);
-  if (ctx->ws) cudaFree(ctx->ws);
+  if (ctx->ws && !ctx->ws_external) cudaFree(ctx->ws);
   if (ctx->count_host) cudaFreeHost(ctx->count_host);
   if (ctx->host_buf) cudaFreeHost(ctx->host_buf);
   delete ctx;
 }
 
 int64_t mlsgd_n_ctrl_cells(const mlsgd_ctx* ctx) { return ctx ? cells_of(ctx->Nc()) : 0; }
+
+mlsgd_status mlsgd_set_workspace(mlsgd_ctx* ctx, void* ws_dev, size_t bytes) {
+  if (!ctx || (ws_dev == nullptr) != (bytes == 0) || ((uintptr_t)ws_dev & 255) != 0)
+    return fail(ctx, MLSGD_EINVAL, "mlsgd_set_workspace: a 256-byte aligned device range, or NULL and 0");
+  if (ctx->ws && !ctx->ws_external) {
+    cudaDeviceSynchronize();  // the context's own scratch may still be in use
+    cudaFree(ctx->ws);
+  }
+  ctx->ws = (char*)ws_dev;
+  ctx->ws_size = bytes;
+  ctx->ws_external = ws_dev != nullptr;
+  return MLSGD_OK;
+}
 
 size_t mlsgd_workspace_bytes(const mlsgd_ctx* ctx, int level, int n_samples) {
   if (!ctx || level < 0 || level >= ctx->cfg.n_levels || n_samples < 0) return 0;
@@ -471,7 +492,9 @@ mlsgd_status mlsgd_solve_state_adjoint(mlsgd_ctx* ctx, int grid, int n_samples, 
   // report non-convergence / non-finite solves (synchronous check of the status flags)
   std::vector<int> h(S);
   CK(cudaMemcpyAsync(h.data(), status_dev, S * sizeof(int), cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(ctx->count_host, ctx->d_err, sizeof(int), cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
+  if (*ctx->count_host != 0) return fail(ctx, MLSGD_ECUDA, "mlsgd_solve_state_adjoint: a kernel timed out on a barrier");
   int flags = 0;
   for (int v : h) flags |= v;
   return solve_verdict(ctx, flags, "mlsgd_solve_state_adjoint");
@@ -548,7 +571,10 @@ mlsgd_status mlsgd_solve_state_adjoint_noalloc(mlsgd_ctx* ctx, int grid, int n_s
   launch("status_any", (double)S * sizeof(int), k_status_any, dim3(1), kAnyBlock, 0, st, (const int*)status_dev, S,
          flags_dev);
   CK(cudaMemcpyAsync(ctx->count_host, flags_dev, sizeof(int), cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(ctx->host_buf, ctx->d_err, sizeof(int), cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
+  if (*(const int*)ctx->host_buf != 0)
+    return fail(ctx, MLSGD_ECUDA, "mlsgd_solve_state_adjoint_noalloc: a kernel timed out on a barrier");
   return solve_verdict(ctx, *ctx->count_host, "mlsgd_solve_state_adjoint_noalloc");
 }
 
@@ -656,7 +682,7 @@ static mlsgd_status step_core(mlsgd_ctx* ctx, const mlsgd_level_stats* stats, in
                        cudaMemcpyDeviceToHost, st));
   CK(cudaMemcpyAsync(ctx->count_host, ctx->d_err, sizeof(int), cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
-  if (*ctx->count_host != 0) return fail(ctx, MLSGD_ECUDA, "tensor-core KL synthesis timed out on a barrier");
+  if (*ctx->count_host != 0) return fail(ctx, MLSGD_ECUDA, "a kernel timed out on a barrier");
   std::vector<double> sc(hb, hb + n_levels * MLSGD_NSCALARS);
   double cstar = -INFINITY;
   for (int l = 0; l < n_levels; ++l) {

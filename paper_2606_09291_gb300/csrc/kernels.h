@@ -65,6 +65,9 @@ struct Batch {
   int S;
   int n;
   const int* act;
+  int* err;      // device flag a kernel sets when one of its bounded waits runs out
+  int stencil;   // 0: slab passes where supported, 1: z-marching tiles only
+  int zchunks;   // z chunks per sample (0: chosen from S)
 };
 
 // Buffers of one batched solve on a grid with N cells per side.  Vectors are
@@ -74,7 +77,10 @@ struct SolverBufs {
   int n_act = 0;             // samples launched by the masked kernels (host-known)
   const int* actp = nullptr; // their indices (null: all S)
   int* act = nullptr;        // [S] device list the compaction writes
-  Batch batch() const { return Batch{S, n_act, actp}; }
+  int* err = nullptr;        // device error flag (bounded waits that ran out)
+  int stencil = 0;           // see Batch
+  int zchunks = 0;
+  Batch batch() const { return Batch{S, n_act, actp, err, stencil, zchunks}; }
   // MG hierarchy (j >= 1 coarse; j = 0 uses the caller's operator coefficient)
   void* acoef[8];            // coefficient per MG level (j = 0: the V-cycle's own copy, may alias)
   void* vx[8];               // V-cycle iterate per level
@@ -118,11 +124,13 @@ void build_hierarchy_mixed(SolverBufs& B, const __nv_bfloat16* abf, cudaStream_t
 size_t solver_bytes(int N, int S, int elem);
 void carve_solver(SolverBufs& B, int N, int S, int elem, char*& ptr);
 
-// tiled fine-grid kernels (tiled.cu); partial sums land in [S][blocks_per_sample]
-struct TiledShape { int bx, by, nzc, zc, blocks_per_sample; };
-TiledShape tiled_shape(int N, int S, int rows_per_thread);
-// partial-sum blocks per sample of the solver passes for elements of `elem` bytes
-int tiled_blocks_per_sample(int N, int S, int elem);
+// tiled fine-grid kernels (tiled.cu); partial sums land in [S][blocks_per_sample], one
+// entry per (xy tile, segment of 8 interior planes), independent of the z chunking
+struct TiledShape { int bx, by, nzc, zc, nseg, blocks_per_sample; };
+TiledShape tiled_shape(int N, int S, int rows_per_thread, int zchunks = 0);
+// partial-sum entries per sample of the solver passes for elements of `elem` bytes
+// (slab: the whole-row slab passes' geometry)
+int tiled_blocks_per_sample(int N, int S, int elem, bool slab);
 template <typename T, typename TA>
 void tiled_apply(const T* z, const T* pold, T* pnew, const TA* a, T* q, double* partial, const SolveScalars* sc, int N,
                  const Batch& bt, int first, cudaStream_t st);
@@ -146,6 +154,19 @@ int tiled_phi_df(const float2* y, int N, int S, const float2* gtab, const float2
 int tiled_phi(const double* y, int N, int S, const double* gtab, const double* mgtab, double* badj, double* partial,
               cudaStream_t st);
 constexpr int kTiledMinN = 16;  // grids with at least this many cells per side use the tiled kernels
+
+// whole-row slab passes (slab.cu) for the mixed path's FP32 vectors on 32^3 and 64^3
+// grids; they need every staged node vector to hold zero boundary nodes
+bool slab_supported(int N);
+TiledShape slab_shape(int N, int S, int zchunks = 0);
+void slab_apply(const float* z, const float* pold, float* pnew, const float* a, float* q, float* x, double* partial,
+                const SolveScalars* sc, int N, const Batch& bt, bool first, bool with_x, bool x_first, cudaStream_t st);
+template <typename TA>
+void slab_pre(const float* r, const float* q, const TA* a, const float* dinv, float* t, float* rnew,
+              const SolveScalars* sc, int N, const Batch& bt, double omega, cudaStream_t st);
+template <typename TA>
+void slab_post(const float* r, const TA* a, const float* dinv, const float* ec, float* z, double* partial,
+               const SolveScalars* sc, int N, const Batch& bt, double omega, cudaStream_t st);
 
 // tensor-core KL synthesis (kl_gemm.cu)
 size_t kl_gemm_b_bytes(int N, int K);

@@ -1,0 +1,551 @@
+// slab.cu - fused fine-grid passes of the mixed-precision solver on 32^3 and 64^3
+// grids, staged as whole-row slabs by bulk asynchronous copies (rows a4, a6).
+//
+// The passes compute what the z-marching passes of tiled.cu compute (APPLY,
+// APPLYX, PRE, PREU, POST; FP32 vectors, BF16 or FP32 cell coefficient) with a
+// layout chosen for fewer instructions per node:
+//   * a block owns every node of TYT = 8 RY consecutive interior rows (all x) and
+//     marches along z over a chunk of interior planes; warp w takes rows
+//     RY w .. RY w + RY - 1 of the block, lane l the RX = N/32 nodes
+//     x = 1 + RX l .. RX l + RX;
+//   * node plane m of a staged vector, rows y0-1 .. y0+TYT (clamped to N), is one
+//     contiguous span of memory (x fastest), so one thread copies it with a single
+//     cp.async.bulk into a ring slot (the span is widened to 16-byte boundaries;
+//     node (x, row) sits at delta + row (N+1) + x, delta = the span's offset modulo
+//     4 floats); cell planes (rows y0-1 .. y0+TYT-1) and, for POST, the coarse
+//     correction's planes are copied the same way; an mbarrier per ring slot counts
+//     the bytes in;
+//   * every staged node vector has zero boundary nodes in memory (the solver clears
+//     them once per solve and the passes write interior nodes only), so the operand
+//     plane is derived branch-free for every staged entry;
+//   * the derived operand plane has an even row stride N + 2, so a lane's window of
+//     RX + 2 columns is read with 8-byte loads when RX = 2.
+// Partial sums (APPLY p.q, POST r.z) are formed per segment of kZSeg interior planes
+// exactly as in tiled.cu (entry seg * by + tile_y per sample).
+//
+// Every wait on an mbarrier is bounded (about a second of SM clock); a wait that
+// runs out sets *err, and the thread then skips its remaining waits and memory work
+// but still reaches every block barrier, so the kernel ends and the host reads the
+// flag.
+#include <cstdio>
+
+#include "internal.cuh"
+#include "kernels.h"
+#include "launch.h"
+
+namespace mlsgd {
+
+namespace {
+
+enum SlabMode { SL_APPLY = 0, SL_PRE = 1, SL_POST = 2, SL_PREU = 4, SL_APPLYX = 5 };
+constexpr int kSegPlanes = 8;  // partial-sum segment (the same as tiled.cu's kZSeg)
+// Raw plane slots per ring: 4 (iteration k copies plane k + 3 into the slot of plane
+// k - 1); 3 for PREU, which stages three node vectors, so that its shared memory
+// still admits three blocks per SM.
+constexpr int ring_of(int mode) { return mode == 4 ? 3 : 4; }
+
+struct SlabArgs {
+  const float* in0;   // APPLY/APPLYX: z     PRE/PREU/POST: r
+  const float* in1;   // APPLY/APPLYX: p_old PREU: q
+  const float* dinv;  // PRE/PREU/POST: D^-1 (0 on the boundary)
+  const float* ec;    // POST: coarse correction on grid N/2
+  const void* a;      // cell coefficient (TA)
+  float* out0;        // APPLY: q   PRE/PREU: t   POST: z
+  float* out1;        // APPLY: p_new   PREU: r_new
+  float* x;           // APPLYX: solution updated with alpha_prev p_old
+  double* partial;    // [S][by * nseg]
+  const SolveScalars* sc;
+  const int* act;
+  int* err;           // set when a wait runs out
+  int nzc, zc, nseg;
+  int first, xfirst;
+  float omega, scale;
+};
+
+template <int N>
+struct SlabGeo {
+  static constexpr int RX = N / 32;           // x nodes per lane
+  static constexpr int RY = N == 64 ? 2 : 4;  // rows per warp
+  static constexpr int TYT = 8 * RY;          // interior rows per block
+  static constexpr int N1 = N + 1;
+  static constexpr int NR = TYT + 2;          // staged node rows
+  static constexpr int XS = N + 2;            // operand-plane row stride (even)
+  static constexpr int RAWF = (NR * N1 + 3 + 3) / 4 * 4;  // raw node slab (floats), shift included
+  static constexpr int XPL = NR * XS;         // operand plane (floats)
+  static constexpr int CROWS = TYT + 1;       // staged cell rows
+  static constexpr int NC = N / 2, NC1 = NC + 1;
+  static constexpr int CNR = TYT / 2 + 2;     // staged coarse node rows
+  static constexpr int CRAWF = (CNR * NC1 + 3 + 3) / 4 * 4;
+  static constexpr int NE = (NR * N1 + 255) / 256;  // derived entries per thread
+  static constexpr int NI = (NC1 * (CNR - 1) + 255) / 256;  // coarse interpolation items per thread
+};
+
+template <int N, typename TA, int MODE>
+struct SlabSmem {
+  using G = SlabGeo<N>;
+  static constexpr int NV = (MODE == SL_PREU) ? 3 : 2;  // staged node vectors
+  static constexpr bool kPost = MODE == SL_POST;
+  static constexpr int kRing = ring_of(MODE);
+  static constexpr size_t raw = 0;
+  static constexpr size_t cells = raw + sizeof(float) * NV * kRing * G::RAWF;
+  static constexpr size_t cellb = (size_t)G::CROWS * N * sizeof(TA);  // one cell slab (a multiple of 16)
+  static constexpr size_t craw = cells + kRing * cellb;
+  static constexpr size_t xs = craw + (kPost ? sizeof(float) * 3 * G::CRAWF : 0);
+  static constexpr size_t eps = xs + sizeof(float) * 3 * G::XPL;
+  static constexpr size_t bar = eps + (kPost ? sizeof(float) * 2 * G::XPL : 0);
+  static constexpr size_t total = bar + 8 * kRing;
+  static_assert(cells % 16 == 0 && craw % 16 == 0 && cellb % 16 == 0 && xs % 16 == 0 && bar % 8 == 0, "align");
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint32_t bar) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ void mbar_expect(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(bar), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void bulk_copy(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(dst),
+               "l"(src), "r"(bytes), "r"(bar)
+               : "memory");
+}
+// bounded wait for phase `parity` of the barrier; false after about a second
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+  const long long t0 = clock64();
+  for (;;) {
+    uint32_t done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    if (done) return true;
+    if (clock64() - t0 > (2LL << 30)) return false;
+  }
+}
+
+__device__ __forceinline__ float ld_cell(const float* c, int i) { return c[i]; }
+__device__ __forceinline__ float ld_cell(const __nv_bfloat16* c, int i) { return __bfloat162float(c[i]); }
+
+template <int N, typename TA, int MODE>
+__global__ void __launch_bounds__(256, 3) k_slab(SlabArgs A) {
+  using G = SlabGeo<N>;
+  using L = SlabSmem<N, TA, MODE>;
+  constexpr int RX = G::RX, RY = G::RY, TYT = G::TYT, N1 = G::N1, NR = G::NR, XS = G::XS;
+  constexpr bool kApply = MODE == SL_APPLY || MODE == SL_APPLYX;
+  constexpr bool kPost = MODE == SL_POST;
+  constexpr int NV = L::NV;
+  constexpr int kRing = L::kRing, kAhead = kRing - 1;
+  extern __shared__ __align__(16) unsigned char sm[];
+  float* raw = (float*)(sm + L::raw);  // [NV][kRing][RAWF]
+  TA* cs = (TA*)(sm + L::cells);       // [kRing][CROWS * N]
+  float* craw = (float*)(sm + L::craw);  // [3][CRAWF]
+  float* xs = (float*)(sm + L::xs);    // [3][XPL]
+  float* eps = (float*)(sm + L::eps);  // [2][XPL]
+  const uint32_t bar0 = smem_u32(sm + L::bar);
+
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int chunk = blockIdx.z % A.nzc;
+  const int s = A.act != nullptr ? A.act[blockIdx.z / A.nzc] : (int)(blockIdx.z / A.nzc);
+  if (A.sc != nullptr && !A.sc[s].active) return;
+  if (*(volatile int*)A.err != 0) return;  // an earlier wait ran out: the results are void anyway
+  const int y0 = 1 + TYT * blockIdx.y;  // first interior row of the block
+  const int kbeg = 1 + chunk * A.zc;
+  const int kend = min(N - 1, kbeg + A.zc - 1);
+  constexpr long long kNodes = (long long)N1 * N1 * N1;
+  constexpr long long kCells = (long long)N * N * N;
+  constexpr long long kCNodes = (long long)G::NC1 * G::NC1 * G::NC1;
+  // node rows y0-1 .. y0+TYT and cell rows y0-1 .. y0+TYT-1 that exist
+  const int rows = min(NR, N + 2 - y0);
+  const int crows = min(G::CROWS, N + 1 - y0);
+  const int cy0 = (y0 - 1) >> 1;  // first staged coarse row
+  const int crows_c = min(G::CNR, G::NC1 - cy0);
+  const float omega = A.omega, scale = A.scale;
+  float beta = 0.f, alpha = 0.f;
+  if (kApply && !A.first) beta = (float)A.sc[s].beta;
+  if (MODE == SL_APPLYX || MODE == SL_PREU) alpha = (float)A.sc[s].alpha;
+  const float* vin[3] = {A.in0, MODE == SL_PREU || kApply ? A.in1 : A.dinv, A.dinv};
+  bool dead = false;  // a wait of this thread ran out: skip the remaining work
+
+  // ---- producer (thread 0): plane m into ring slot (m - first) % kRing
+  const int first = kbeg - 1;
+  auto span = [&](long long off, int len, int& delta) {  // 16-byte aligned span covering [off, off + len)
+    delta = (int)(off & 3);
+    return (uint32_t)(4 * ((delta + len + 3) & ~3));
+  };
+  auto issue = [&](int m, bool extra_coarse) {
+    const int j = m - first, slot = j % kRing;
+    const uint32_t bar = bar0 + 8 * slot;
+    const long long noff = (long long)s * kNodes + (long long)m * N1 * N1 + (long long)(y0 - 1) * N1;
+    int d;
+    const uint32_t nb = span(noff, rows * N1, d);
+    const bool cell = m < N;
+    const uint32_t cb = cell ? (uint32_t)(crows * N * sizeof(TA)) : 0u;
+    const int nv = (kApply && A.first) ? 1 : NV;  // the first APPLY reads no old p
+    uint32_t total = nv * nb + cb;
+    // POST: coarse plane m/2 + 1 with every even fine plane (interpolated in derive(m)),
+    // plane (kbeg-1)/2 as well with the first plane of the chunk
+    int cplanes[2], nc = 0;
+    if (kPost) {
+      if (extra_coarse) cplanes[nc++] = m >> 1;
+      if (!(m & 1) && (m >> 1) + 1 <= G::NC) cplanes[nc++] = (m >> 1) + 1;
+    }
+    uint32_t cbytes[2] = {0u, 0u};
+    long long coff[2] = {0, 0};
+    for (int q = 0; q < nc; ++q) {
+      coff[q] = (long long)s * kCNodes + (long long)cplanes[q] * G::NC1 * G::NC1 + (long long)cy0 * G::NC1;
+      int dc;
+      cbytes[q] = span(coff[q], crows_c * G::NC1, dc);
+      total += cbytes[q];
+    }
+    mbar_expect(bar, total);
+    for (int v = 0; v < nv; ++v)
+      bulk_copy(smem_u32(raw + (v * kRing + slot) * G::RAWF), vin[v] + (noff & ~3LL), nb, bar);
+    if (cell) {
+      const long long coff_c = (long long)s * kCells + (long long)m * N * N + (long long)(y0 - 1) * N;
+      bulk_copy(smem_u32((unsigned char*)cs + slot * L::cellb), (const TA*)A.a + coff_c, cb, bar);
+    }
+    for (int q = 0; q < nc; ++q)
+      bulk_copy(smem_u32(craw + (cplanes[q] % 3) * G::CRAWF), A.ec + (coff[q] & ~3LL), cbytes[q], bar);
+  };
+  auto wait_plane = [&](int m) {
+    const int j = m - first;
+    if (!dead && !mbar_wait(bar0 + 8 * (j % kRing), (uint32_t)((j / kRing) & 1))) {
+      dead = true;
+      atomicOr(A.err, 1);
+    }
+  };
+  auto delta_of = [&](int m) { return (int)(((long long)s * kNodes + (long long)m * N1 * N1 + (long long)(y0 - 1) * N1) & 3); };
+
+  // ---- entries this thread derives: e = tid + 256 j, operand index e + e / N1 (stride N + 2)
+  int xo[G::NE];
+#pragma unroll
+  for (int j = 0; j < G::NE; ++j) {
+    const int e = tid + 256 * j;
+    xo[j] = e + e / N1;
+  }
+
+  // POST: interpolate staged coarse plane c (xy-bilinear) into eps[c & 1]: item
+  // (a, b) of the coarse tile writes fine nodes (2a + p, 2b + q)
+  auto interp = [&](int c) {
+    if (dead) return;
+    const float* cp = craw + (c % 3) * G::CRAWF +
+                      (int)(((long long)s * kCNodes + (long long)c * G::NC1 * G::NC1 + (long long)cy0 * G::NC1) & 3);
+    float* ed = eps + (c & 1) * G::XPL;
+#pragma unroll
+    for (int j = 0; j < G::NI; ++j) {
+      const int it = tid + 256 * j;
+      if (it >= G::NC1 * (G::CNR - 1)) break;
+      const int a = it % G::NC1, b = it / G::NC1;
+      const float* q = cp + a + G::NC1 * b;
+      const float e00 = q[0], e01 = q[G::NC1];
+      float* o = ed + 2 * a + XS * (2 * b);
+      o[0] = e00;
+      o[XS] = 0.5f * (e00 + e01);
+      if (a < G::NC) {
+        const float e10 = q[1], e11 = q[G::NC1 + 1];
+        const float r0 = 0.5f * (e00 + e10), r1 = 0.5f * (e01 + e11);
+        o[1] = r0;
+        o[XS + 1] = 0.5f * (r0 + r1);
+      }
+    }
+  };
+
+  // derive operand plane m (ring slot of m, operand slot m % 3)
+  auto derive = [&](int m, bool interp_next) {
+    if (dead) return;
+    const int slot = (m - first) % kRing;
+    const int dl = delta_of(m);
+    const float* r0 = raw + (0 * kRing + slot) * G::RAWF + dl;
+    const float* r1 = raw + (1 * kRing + slot) * G::RAWF + dl;
+    const float* r2 = raw + (2 * kRing + slot) * G::RAWF + dl;
+    float* xp = xs + (m % 3) * G::XPL;
+    if (kPost && interp_next && !(m & 1) && (m >> 1) + 1 <= G::NC) interp((m >> 1) + 1);
+    const float* e0 = eps + ((m >> 1) & 1) * G::XPL;
+    const float* e1 = eps + (((m + 1) >> 1) & 1) * G::XPL;
+#pragma unroll
+    for (int j = 0; j < G::NE; ++j) {
+      const int e = tid + 256 * j;
+      if (j == G::NE - 1 && e >= NR * N1) break;
+      float v;
+      if (kApply) {
+        v = A.first ? r0[e] : fmaf(beta, r1[e], r0[e]);
+      } else if (MODE == SL_PREU) {
+        v = omega * fmaf(-alpha, r1[e], r0[e]) * r2[e];
+      } else {
+        v = omega * r0[e] * r1[e];
+        if (kPost) v += (m & 1) ? 0.5f * (e0[xo[j]] + e1[xo[j]]) : e0[xo[j]];
+      }
+      xp[xo[j]] = v;
+    }
+  };
+
+  // ---- prologue
+  if (tid == 0) {
+#pragma unroll
+    for (int q = 0; q < kRing; ++q) mbar_init(bar0 + 8 * q);
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+  }
+  __syncthreads();
+  // planes first .. first+kAhead fill the fresh slots; iteration k then refills the slot
+  // of plane k-1 with plane k+kAhead (raw k-1 was last read by compute(k-1), its cells
+  // by compute(k))
+  if (tid == 0)
+    for (int m = first; m <= min(first + kAhead, kend + 1); ++m) issue(m, kPost && m == first);
+  wait_plane(first);
+  if (kPost) {
+    interp(first >> 1);
+    interp((first >> 1) + 1);
+    __syncthreads();
+  }
+  derive(first, false);
+  wait_plane(kbeg);
+  derive(kbeg, false);
+  __syncthreads();
+
+  // ---- this thread's nodes: x = 1 + RX lane + i, rows y = y0 + RY warp + t
+  const int ly0 = RY * warp;                // staged row of the window's first row
+  const int xw = RX * lane;                 // window's first column
+  const int own0 = (ly0 + 1) * N1 + xw + 1;  // raw index of node (i = 0, t = 0) without the shift
+  const int cwin = ly0 * N + xw;             // cell slab index of the window's first cell
+  float* out0 = A.out0 + s * kNodes;
+  float* out1 = (kApply || MODE == SL_PREU) ? A.out1 + s * kNodes : nullptr;
+  float* xg = (MODE == SL_APPLYX) ? A.x + s * kNodes : nullptr;
+  bool xok[RX], yok[RY];
+#pragma unroll
+  for (int i = 0; i < RX; ++i) xok[i] = xw + 1 + i <= N - 1;
+#pragma unroll
+  for (int t = 0; t < RY; ++t) yok[t] = y0 + ly0 + t <= N - 1;
+  float red = 0.f;
+
+  for (int k = kbeg; k <= kend; ++k) {
+    // APPLYX: this plane's x of the thread's nodes, loaded before the waits so the
+    // global latency overlaps the derive step
+    float xv[RY][RX];
+    if (MODE == SL_APPLYX) {
+#pragma unroll
+      for (int t = 0; t < RY; ++t)
+#pragma unroll
+        for (int i = 0; i < RX; ++i)
+          xv[t][i] = (!A.xfirst && xok[i] && yok[t]) ? xg[k * N1 * N1 + (y0 + ly0 + t) * N1 + xw + 1 + i] : 0.f;
+    }
+    if (k + 1 <= kend + 1) {
+      wait_plane(k + 1);
+      derive(k + 1, true);
+    }
+    __syncthreads();
+    if (!dead) {
+      // cells of the two cell planes around plane k: C[r][cc][cr], cell (xw + cc, row ly0 + cr)
+      float C[2][RX + 1][RY + 1];
+#pragma unroll
+      for (int r = 0; r < 2; ++r) {
+        const TA* cp = cs + ((k - 1 + r - first) % kRing) * (L::cellb / sizeof(TA)) + cwin;
+#pragma unroll
+        for (int cr = 0; cr < RY + 1; ++cr)
+#pragma unroll
+          for (int cc = 0; cc < RX + 1; ++cc) C[r][cc][cr] = ld_cell(cp, cr * N + cc);
+      }
+      // the operator plane by plane (k-1, k, k+1): one window of (RX+2) x (RY+2) operand
+      // values live at a time; node (i, t) has cells c[p][q][r] = C[r][i + p][t + q] and
+      // neighbour (du, dv) of the plane at window (i + 1 + du, t + 1 + dv)
+      float acc[RY][RX], ctr[RY][RX];
+#pragma unroll
+      for (int pl = 0; pl < 3; ++pl) {
+        const int order = pl == 0 ? 1 : (pl == 1 ? 0 : 2);  // centre plane first
+        const float* xp = xs + ((k - 1 + order) % 3) * G::XPL + ly0 * XS + xw;
+        float W[RX + 2][RY + 2];
+#pragma unroll
+        for (int rr = 0; rr < RY + 2; ++rr) {
+          if constexpr (RX == 2) {
+            const float2 a0 = *reinterpret_cast<const float2*>(xp + rr * XS);
+            const float2 a1 = *reinterpret_cast<const float2*>(xp + rr * XS + 2);
+            W[0][rr] = a0.x;
+            W[1][rr] = a0.y;
+            W[2][rr] = a1.x;
+            W[3][rr] = a1.y;
+          } else {
+#pragma unroll
+            for (int c = 0; c < RX + 2; ++c) W[c][rr] = xp[rr * XS + c];
+          }
+        }
+#pragma unroll
+        for (int t = 0; t < RY; ++t)
+#pragma unroll
+          for (int i = 0; i < RX; ++i) {
+            if (order == 1) {
+              // in-plane face diagonals: pair sums over the two cell planes
+              float pxy[2][2];
+#pragma unroll
+              for (int v = 0; v < 2; ++v)
+#pragma unroll
+                for (int u = 0; u < 2; ++u) pxy[v][u] = C[0][i + u][t + v] + C[1][i + u][t + v];
+              const float sum8 = (pxy[0][0] + pxy[0][1]) + (pxy[1][0] + pxy[1][1]);
+              ctr[t][i] = W[i + 1][t + 1];
+              float a1 = 4.f * sum8 * W[i + 1][t + 1];
+#pragma unroll
+              for (int v = 0; v < 2; ++v)
+#pragma unroll
+                for (int u = 0; u < 2; ++u) a1 -= pxy[v][u] * W[i + 2 * u][t + 2 * v];
+              acc[t][i] = a1;
+            } else {
+              const int r = order >> 1;  // plane k-1: cells below (r = 0); k+1: above (r = 1)
+              float a2 = acc[t][i];
+#pragma unroll
+              for (int u = 0; u < 2; ++u) {
+                a2 -= (C[r][i + u][t] + C[r][i + u][t + 1]) * W[i + 2 * u][t + 1];  // xz face diagonals
+                a2 -= (C[r][i][t + u] + C[r][i + 1][t + u]) * W[i + 1][t + 2 * u];  // yz face diagonals
+              }
+#pragma unroll
+              for (int q = 0; q < 2; ++q)
+#pragma unroll
+                for (int p = 0; p < 2; ++p) a2 -= C[r][i + p][t + q] * W[i + 2 * p][t + 2 * q];  // body diagonals
+              acc[t][i] = a2;
+            }
+          }
+      }
+      const int dl = delta_of(k);
+      const int slot = (k - first) % kRing;
+      const float* o0 = raw + (0 * kRing + slot) * G::RAWF + dl + own0;
+      const float* o1 = raw + (1 * kRing + slot) * G::RAWF + dl + own0;
+#pragma unroll
+      for (int t = 0; t < RY; ++t) {
+#pragma unroll
+        for (int i = 0; i < RX; ++i) {
+          const float ax = scale * acc[t][i];
+          if (!(xok[i] && yok[t])) continue;
+          const int own = t * N1 + i;
+          const int g = k * N1 * N1 + (y0 + ly0 + t) * N1 + xw + 1 + i;
+          if (kApply) {
+            const float pv = ctr[t][i];
+            out0[g] = ax;
+            out1[g] = pv;
+            red = fmaf(pv, ax, red);
+            if (MODE == SL_APPLYX) xg[g] = xv[t][i] + alpha * o1[own];
+          } else if (MODE == SL_PRE) {
+            out0[g] = o0[own] - ax;
+          } else if (MODE == SL_PREU) {
+            const float rn = fmaf(-alpha, o1[own], o0[own]);
+            out0[g] = rn - ax;
+            out1[g] = rn;
+          } else {  // POST
+            const float rv = o0[own];
+            const float zv = ctr[t][i] + omega * (rv - ax) * o1[own];
+            out0[g] = zv;
+            red = fmaf(rv, zv, red);
+          }
+        }
+      }
+    }
+    if ((kApply || kPost) && (k == kend || (k - 1) % kSegPlanes == kSegPlanes - 1)) {
+      const float b = block_sum(red);
+      if (tid == 0) {
+        const int per = gridDim.y * A.nseg;
+        A.partial[(long long)s * per + ((k - 1) / kSegPlanes) * gridDim.y + blockIdx.y] = (double)b;
+      }
+      red = 0.f;
+    }
+    __syncthreads();
+    if (tid == 0 && !dead && k + kAhead <= kend + 1) issue(k + kAhead, false);
+  }
+  // the last copies of the chunk have been waited for (every issued plane is derived)
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------- host side
+bool slab_supported(int N) { return N == 32 || N == 64; }
+
+TiledShape slab_shape(int N, int S, int zchunks) {
+  TiledShape t;
+  const int tyt = N == 64 ? 16 : 32;
+  t.bx = 1;
+  t.by = (N - 1 + tyt - 1) / tyt;
+  const int nseg = (N - 1 + kSegPlanes - 1) / kSegPlanes;
+  const long long base = (long long)t.by * S;
+  int nzc = 1;
+  if (zchunks > 0) nzc = zchunks < nseg ? zchunks : nseg;
+  else
+    while (base * nzc < 3 * 152 * 4 && 2 * nzc <= nseg) nzc *= 2;
+  const int spc = (nseg + nzc - 1) / nzc;
+  t.nzc = (nseg + spc - 1) / spc;
+  t.zc = spc * kSegPlanes;
+  t.nseg = nseg;
+  t.blocks_per_sample = t.by * nseg;
+  return t;
+}
+
+template <int N, typename TA, int MODE>
+static void run_slab(const char* cls, double bytes, SlabArgs args, const Batch& bt, cudaStream_t st) {
+  const TiledShape t = slab_shape(N, bt.S, bt.zchunks);
+  args.nzc = t.nzc;
+  args.zc = t.zc;
+  args.nseg = t.nseg;
+  args.act = bt.act;
+  args.scale = (float)(1.0 / (12.0 * N));
+  const size_t smem = SlabSmem<N, TA, MODE>::total;
+  static bool smem_set = false;  // once per instantiation (capture-friendly)
+  if (!smem_set) {
+    cudaFuncSetAttribute(k_slab<N, TA, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaFuncSetAttribute(k_slab<N, TA, MODE>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                         cudaSharedmemCarveoutMaxShared);
+    smem_set = true;
+  }
+  launch(cls, bytes, k_slab<N, TA, MODE>, dim3(1, t.by, (unsigned)(bt.n * t.nzc)), dim3(256), smem, st, args);
+}
+
+template <typename TA, int MODE>
+static void dispatch(int N, const char* cls, double bytes, SlabArgs args, const Batch& bt, cudaStream_t st) {
+  if (N == 64) run_slab<64, TA, MODE>(cls, bytes, args, bt, st);
+  else run_slab<32, TA, MODE>(cls, bytes, args, bt, st);
+}
+
+static double sbytes(int N, int n, double vec, double coef, size_t ta) {
+  return (double)n * (vec * (double)nodes_of(N) * 4 + coef * (double)cells_of(N) * ta);
+}
+
+void slab_apply(const float* z, const float* pold, float* pnew, const float* a, float* q, float* x, double* partial,
+                const SolveScalars* sc, int N, const Batch& bt, bool first, bool with_x, bool x_first, cudaStream_t st) {
+  SlabArgs A{};
+  A.in0 = z; A.in1 = pold; A.a = a; A.out0 = q; A.out1 = pnew; A.x = x; A.partial = partial; A.sc = sc;
+  A.err = bt.err;
+  A.first = first ? 1 : 0;
+  A.xfirst = x_first ? 1 : 0;
+  if (with_x)
+    dispatch<float, SL_APPLYX>(N, "apply_f32", sbytes(N, bt.n, x_first ? 5 : 6, 1, 4), A, bt, st);
+  else
+    dispatch<float, SL_APPLY>(N, "apply_f32", sbytes(N, bt.n, first ? 3 : 4, 1, 4), A, bt, st);
+}
+
+template <typename TA>
+void slab_pre(const float* r, const float* q, const TA* a, const float* dinv, float* t, float* rnew,
+              const SolveScalars* sc, int N, const Batch& bt, double omega, cudaStream_t st) {
+  SlabArgs A{};
+  A.in0 = r; A.in1 = q; A.a = a; A.dinv = dinv; A.out0 = t; A.out1 = rnew; A.sc = sc; A.err = bt.err;
+  A.omega = (float)omega;
+  if (q)
+    dispatch<TA, SL_PREU>(N, "pre_f32", sbytes(N, bt.n, 5, 1, sizeof(TA)), A, bt, st);
+  else
+    dispatch<TA, SL_PRE>(N, "pre_f32", sbytes(N, bt.n, 3, 1, sizeof(TA)), A, bt, st);
+}
+
+template <typename TA>
+void slab_post(const float* r, const TA* a, const float* dinv, const float* ec, float* z, double* partial,
+               const SolveScalars* sc, int N, const Batch& bt, double omega, cudaStream_t st) {
+  SlabArgs A{};
+  A.in0 = r; A.a = a; A.dinv = dinv; A.ec = ec; A.out0 = z; A.partial = partial; A.sc = sc; A.err = bt.err;
+  A.omega = (float)omega;
+  dispatch<TA, SL_POST>(N, "post_f32", sbytes(N, bt.n, 3, 1, sizeof(TA)) + (double)bt.n * nodes_of(N / 2) * 4, A, bt,
+                        st);
+}
+
+template void slab_pre<__nv_bfloat16>(const float*, const float*, const __nv_bfloat16*, const float*, float*, float*,
+                                      const SolveScalars*, int, const Batch&, double, cudaStream_t);
+template void slab_pre<float>(const float*, const float*, const float*, const float*, float*, float*,
+                              const SolveScalars*, int, const Batch&, double, cudaStream_t);
+template void slab_post<__nv_bfloat16>(const float*, const __nv_bfloat16*, const float*, const float*, float*,
+                                       double*, const SolveScalars*, int, const Batch&, double, cudaStream_t);
+template void slab_post<float>(const float*, const float*, const float*, const float*, float*, double*,
+                               const SolveScalars*, int, const Batch&, double, cudaStream_t);
+
+}  // namespace mlsgd

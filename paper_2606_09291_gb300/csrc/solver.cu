@@ -463,6 +463,9 @@ __global__ void k_accumulate(double* __restrict__ x, const float* __restrict__ d
 static inline dim3 grid_nodes(int N, int S) { return dim3((unsigned)node_blocks(N), (unsigned)S); }
 
 static size_t align_up(size_t v) { return (v + 255) & ~(size_t)255; }
+// bytes after every node vector: the slab passes copy 16-byte aligned spans that may
+// reach up to 12 bytes past a vector's last node
+constexpr size_t kVecSlack = 64;
 
 static int mg_levels(int N) {
   int J = 0;
@@ -470,19 +473,22 @@ static int mg_levels(int N) {
   return J;
 }
 
+// the whole-row slab passes run the FP32 fused passes of grid N
+static bool uses_slab(const SolverBufs& B, int N, int elem) { return elem == 4 && B.stencil == 0 && slab_supported(N); }
+
 // levels whose smoothing runs in the tiled passes (they read a precomputed D^{-1})
 static bool tiled_level(int N, int j) { return N >= kTiledMinN && mg_levels(N) >= 1 && (N >> j) >= kTiledMinN; }
 
 size_t solver_bytes(int N, int S, int elem) {
   size_t b = 0;
   const int J = mg_levels(N);
-  b += 7 * align_up((size_t)S * nodes_of(N) * elem);
+  b += 7 * align_up((size_t)S * nodes_of(N) * elem + kVecSlack);
   for (int j = 1; j <= J; ++j) {
     const int Nj = N >> j;
-    b += 3 * align_up((size_t)S * nodes_of(Nj) * elem) + align_up((size_t)S * cells_of(Nj) * elem);
+    b += 3 * align_up((size_t)S * nodes_of(Nj) * elem + kVecSlack) + align_up((size_t)S * cells_of(Nj) * elem);
   }
   for (int j = 0; j <= J; ++j)
-    if (tiled_level(N, j)) b += align_up((size_t)S * nodes_of(N >> j) * elem);
+    if (tiled_level(N, j)) b += align_up((size_t)S * nodes_of(N >> j) * elem + kVecSlack);
   if (elem == 4 && tiled_level(N, 0)) b += align_up((size_t)S * nodes_of(N) * sizeof(float2));
   b += align_up((size_t)S * node_blocks(N) * sizeof(double));
   b += 2 * align_up((size_t)S * sizeof(SolveScalars));
@@ -495,18 +501,18 @@ void carve_solver(SolverBufs& B, int N, int S, int elem, char*& ptr) {
   B.N = N;
   B.S = S;
   B.J = mg_levels(N);
-  const size_t v0 = (size_t)S * nodes_of(N) * elem;
+  const size_t v0 = (size_t)S * nodes_of(N) * elem + kVecSlack;
   B.x = take(v0); B.r = take(v0); B.r2 = take(v0); B.p = take(v0); B.q = take(v0);
   B.vx[0] = take(v0); B.vt[0] = take(v0); B.vr[0] = nullptr; B.acoef[0] = nullptr;
   for (int j = 1; j <= B.J; ++j) {
     const int Nj = N >> j;
-    const size_t vj = (size_t)S * nodes_of(Nj) * elem;
+    const size_t vj = (size_t)S * nodes_of(Nj) * elem + kVecSlack;
     B.vx[j] = take(vj); B.vt[j] = take(vj); B.vr[j] = take(vj);
     B.acoef[j] = take((size_t)S * cells_of(Nj) * elem);
   }
   for (int j = 0; j < 8; ++j) B.dinv[j] = nullptr;
   for (int j = 0; j <= B.J; ++j)
-    if (tiled_level(N, j)) B.dinv[j] = take((size_t)S * nodes_of(N >> j) * elem);
+    if (tiled_level(N, j)) B.dinv[j] = take((size_t)S * nodes_of(N >> j) * elem + kVecSlack);
   B.bdf = (elem == 4 && tiled_level(N, 0)) ? (float2*)take((size_t)S * nodes_of(N) * sizeof(float2)) : nullptr;
   B.partial = (double*)take((size_t)S * node_blocks(N) * sizeof(double));
   B.sc = (SolveScalars*)take((size_t)2 * S * sizeof(SolveScalars));
@@ -661,7 +667,7 @@ static int vcycle(SolverBufs& B, const T* r0, const TA0* a0, const SolveScalars*
     if (fine && tiled) {
       tiled_post<T, TA0>(rfine, a0, (const T*)B.dinv[0], (const T*)B.vt[1], (T*)B.vt[0], B.partial, sc, Nj, bt,
                          (double)omega, st);
-      return tiled_blocks_per_sample(Nj, S, (int)sizeof(T));
+      return tiled_blocks_per_sample(Nj, S, (int)sizeof(T), uses_slab(B, Nj, (int)sizeof(T)));
     }
     if (!fine && tiled && Nj >= kTiledMinN) {
       // the r.z partial sums of a coarse level are overwritten by the fine level's POST
@@ -745,7 +751,7 @@ static cudaError_t pcg_loop(SolverBufs& B, const TAop* aop, const TA0* a0, T* x,
            (const SolveScalars*)sc, nodes, 1, B.actp);
   const double tol2 = prm.rtol * prm.rtol;
   const int nit = fixed_iters > 0 ? fixed_iters : prm.max_iter;
-  const int napply = tiled ? tiled_blocks_per_sample(N, S, (int)sizeof(T)) : nb;
+  const int napply = tiled ? tiled_blocks_per_sample(N, S, (int)sizeof(T), uses_slab(B, N, (int)sizeof(T))) : nb;
   for (int it = 0; it < nit; ++it) {
     T* p;
     if (tiled) {
@@ -801,7 +807,7 @@ static cudaError_t pcg_inner_fused(SolverBufs& B, const float* a32, const __nv_b
   int rc = 0, pc = 0;
   float* q = (float*)B.q;
   const float* z = (const float*)B.vt[0];
-  const int napply = tiled_blocks_per_sample(N, S, 4);
+  const int napply = tiled_blocks_per_sample(N, S, 4, uses_slab(B, N, 4));
   int nrz = vcycle<float, __nv_bfloat16>(B, rb[rc], abf, sc, omega, st);
   scalar(B, sc, SM_RZ0, 0, 0, st, nrz);
   for (int it = 0; it < iters; ++it) {
@@ -871,16 +877,27 @@ static void zero_boundary(void* const* bufs, int nv, int N, int S, cudaStream_t 
 // The mixed path needs none of this: its tiled passes zero-fill boundary nodes when
 // staging, and the kernels that read whole vectors (the refinement's init and
 // accumulation) take the boundary as 0 themselves.
+// The mixed path's z-marching passes zero-fill boundary nodes when staging and need
+// none of this; its slab passes (32^3, 64^3 grids) copy whole rows, boundary nodes
+// included, so the vectors they read get zero boundaries here: p (both buffers), q,
+// z and the second residual on the fine level, the V-cycle outputs on the coarse
+// levels (the other inputs, r, D^-1 and the restricted residuals, are written with
+// zero boundaries by their producers).
 static cudaError_t clear_tiled(SolverBufs& B, int elem, cudaStream_t st) {
-  if (!(B.N >= kTiledMinN && B.J >= 1) || elem == 4) return cudaSuccess;
-  void* bufs[6] = {B.p, B.vx[0], B.q, B.vt[0], B.r2, B.x};
-  if (elem == 4) zero_boundary<float>(bufs, 6, B.N, B.S, st);
-  else zero_boundary<double>(bufs, 5, B.N, B.S, st);
-  for (int j = 1; j < B.J; ++j)  // coarse levels run by the tiled passes
-    if ((B.N >> j) >= kTiledMinN) {
-      if (elem == 4) zero_boundary<float>(&B.vt[j], 1, B.N >> j, B.S, st);
-      else zero_boundary<double>(&B.vt[j], 1, B.N >> j, B.S, st);
+  if (!(B.N >= kTiledMinN && B.J >= 1)) return cudaSuccess;
+  if (elem == 4) {
+    if (uses_slab(B, B.N, 4)) {
+      void* bufs[5] = {B.p, B.vx[0], B.q, B.vt[0], B.r2};
+      zero_boundary<float>(bufs, 5, B.N, B.S, st);
     }
+    for (int j = 1; j < B.J; ++j)
+      if ((B.N >> j) >= kTiledMinN) zero_boundary<float>(&B.vt[j], 1, B.N >> j, B.S, st);
+    return cudaGetLastError();
+  }
+  void* bufs[5] = {B.p, B.vx[0], B.q, B.vt[0], B.r2};
+  zero_boundary<double>(bufs, 5, B.N, B.S, st);
+  for (int j = 1; j < B.J; ++j)  // coarse levels run by the tiled passes
+    if ((B.N >> j) >= kTiledMinN) zero_boundary<double>(&B.vt[j], 1, B.N >> j, B.S, st);
   return cudaGetLastError();
 }
 
@@ -941,7 +958,7 @@ cudaError_t ir_mixed(SolverBufs& B, const float* a32, const __nv_bfloat16* abf, 
       const int cap = fixed_steps > 0 ? fixed_steps : prm.max_iter;
       if (tiled) {
         tiled_res64(bdf, bstride, xdf, a32, r32, B.partial, sco, N, B.batch(), st);
-        scalar(B, sco, SM_OUTER_CONV, tol2, cap, st, tiled_blocks_per_sample(N, S, 8));
+        scalar(B, sco, SM_OUTER_CONV, tol2, cap, st, tiled_blocks_per_sample(N, S, 8, false));
       } else {
         launch("resid64", (double)(bstride ? B.n_act : 1) * nodes * 8 + nbytes<double, float>(N, B.n_act, 2, 1),
                k_residual64<float>, g(), kBlock, 0, st, b, bstride, (const double*)x_out, a32, r64, B.partial,

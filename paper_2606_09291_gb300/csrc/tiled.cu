@@ -27,6 +27,7 @@
 // The fused passes write only interior nodes and zero-fill boundary nodes at staging
 // (like nodes outside the grid), so they never read a buffer's boundary values.
 #include <cstdio>
+#include <type_traits>
 
 #include "internal.cuh"
 #include "kernels.h"
@@ -60,7 +61,8 @@ struct TiledArgs {
   long long bstride; // RES64: b stride per sample (0 = shared)
   int N;
   int nzc;           // z chunks per sample
-  int zc;            // planes per chunk
+  int zc;            // planes per chunk (a multiple of kZSeg)
+  int nseg;          // partial-sum segments per sample column
   int first;         // APPLY: first iteration (pn = z)
   int xfirst;        // APPLYX: x not yet written (x = alpha_prev p_old)
   double omega;
@@ -80,6 +82,13 @@ __device__ __forceinline__ void cp_async(void* smem, const void* gmem, bool vali
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+
+// Partial sums (dot products of the fused passes, Phi) are formed per segment of
+// kZSeg interior planes, whatever z chunk the block marches: partial entry
+// (seg * by + tile_y) * bx + tile_x of a sample holds the segment's block sum, so
+// the reduction order, and with it every sample's iterates, is independent of the
+// batch size that chose the z chunking.
+constexpr int kZSeg = 8;
 
 constexpr int RING = 5;   // raw planes resident: k-1, k, k+1 + two in flight
 constexpr int ERING = 4;  // coarse planes
@@ -550,20 +559,22 @@ __global__ void __launch_bounds__(NT) k_tiled(TiledArgs A) {
         }
       }
     }
+    if (MODE != TM_PRE && MODE != TM_PREU && (k == kend || (k - 1) % kZSeg == kZSeg - 1)) {
+      // end of a partial-sum segment (block-uniform condition)
+      const T b = block_sum(MODE == TM_RES64 ? (T)redf : red);
+      if (tid == 0) {
+        const int per = gridDim.x * gridDim.y * A.nseg;
+        const int bid = (((k - 1) / kZSeg) * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
+        A.partial[(long long)s * per + bid] = (double)b;
+      }
+      red = T(0);
+      redf = 0.f;
+    }
     __syncthreads();
     s5 = s5p1;
     r3 = r3p1;
   }
   cp_async_wait<0>();
-  if (MODE == TM_RES64) red = (T)redf;
-  if (MODE != TM_PRE && MODE != TM_PREU) {
-    const T b = block_sum(red);
-    if (tid == 0) {
-      const int per = gridDim.x * gridDim.y * A.nzc;
-      const int bid = (chunk * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
-      A.partial[(long long)s * per + bid] = (double)b;
-    }
-  }
 }
 
 // Phi = 1/2 e^T M e and badj = M e on interior rows, e = y - g_h (row a5).
@@ -574,7 +585,7 @@ __global__ void __launch_bounds__(NT) k_tiled(TiledArgs A) {
 // mgtab[i] = (h/6)(g[i-1] + 4 g[i] + g[i+1]).
 __global__ void __launch_bounds__(NT) k_phi_tiled(const double* __restrict__ y, int N, const double* __restrict__ gtab,
                                                   const double* __restrict__ mgtab, double* __restrict__ badj,
-                                                  double* __restrict__ partial, int nzc, int zc) {
+                                                  double* __restrict__ partial, int nzc, int zc, int nseg) {
   __shared__ double ys[NP];
   __shared__ double xsum[NPY][TX];
   __shared__ double mxy[3][NT];
@@ -619,10 +630,15 @@ __global__ void __launch_bounds__(NT) k_phi_tiled(const double* __restrict__ y, 
       badj[s * nodes + gi + (long long)n1 * (gj + (long long)n1 * k)] = me;
       red += e * me;
     }
+    if (k == kend || (k - 1) % kZSeg == kZSeg - 1) {  // end of a partial-sum segment
+      const double b = block_sum(red);
+      if (tid == 0)
+        partial[(long long)s * (gridDim.x * gridDim.y * nseg) + (((k - 1) / kZSeg) * gridDim.y + blockIdx.y) * gridDim.x +
+                blockIdx.x] = b;
+      red = 0.0;
+      __syncthreads();
+    }
   }
-  const double b = block_sum(red);
-  if (tid == 0) partial[(long long)s * (gridDim.x * gridDim.y * nzc) + (chunk * gridDim.y + blockIdx.y) * gridDim.x +
-                        blockIdx.x] = b;
 }
 
 // k_phi_tiled for a state given as FP32 (hi, lo) pairs (the mixed level gradient):
@@ -631,7 +647,7 @@ __global__ void __launch_bounds__(NT) k_phi_tiled(const double* __restrict__ y, 
 // e.M e of each block returned in FP64.
 __global__ void __launch_bounds__(NT) k_phi_tiled_df(const float2* __restrict__ y, int N, const float2* __restrict__ gtab,
                                                      const float2* __restrict__ mgtab, float2* __restrict__ badj,
-                                                     double* __restrict__ partial, int nzc, int zc) {
+                                                     double* __restrict__ partial, int nzc, int zc, int nseg) {
   __shared__ float2 ys[NP];
   __shared__ float2 xsum[NPY][TX];
   __shared__ float2 mxy[3][NT];
@@ -683,25 +699,36 @@ __global__ void __launch_bounds__(NT) k_phi_tiled_df(const float2* __restrict__ 
       badj[s * nodes + gi + (long long)n1 * (gj + (long long)n1 * k)] = df_f2(me);
       red = df_add(red, df_mul(e, me));
     }
+    if (k == kend || (k - 1) % kZSeg == kZSeg - 1) {  // end of a partial-sum segment
+      const double b = block_sum(df_to_double(red));
+      if (tid == 0)
+        partial[(long long)s * (gridDim.x * gridDim.y * nseg) + (((k - 1) / kZSeg) * gridDim.y + blockIdx.y) * gridDim.x +
+                blockIdx.x] = b;
+      red = DF{0.f, 0.f};
+      __syncthreads();
+    }
   }
-  const double b = block_sum(df_to_double(red));
-  if (tid == 0) partial[(long long)s * (gridDim.x * gridDim.y * nzc) + (chunk * gridDim.y + blockIdx.y) * gridDim.x +
-                        blockIdx.x] = b;
 }
 
 // ---------------------------------------------------------------- host side
 
-TiledShape tiled_shape(int N, int S, int ry) {
+TiledShape tiled_shape(int N, int S, int ry, int zchunks) {
   TiledShape t;
   t.bx = (N - 1 + TX - 1) / TX;
   t.by = (N - 1 + TY * ry - 1) / (TY * ry);
-  // enough blocks to fill the GPU: split z when the batch is small
+  // enough blocks to fill the GPU: split z into chunks of whole partial-sum segments
+  // when the batch is small (the partial-sum layout does not depend on the split)
+  const int nseg = (N - 1 + kZSeg - 1) / kZSeg;
   const long long base = (long long)t.bx * t.by * S;
   int nzc = 1;
-  while (base * nzc < 4 * 152 * 4 && nzc * 8 < N - 1) nzc *= 2;
-  t.nzc = nzc;
-  t.zc = (N - 1 + nzc - 1) / nzc;
-  t.blocks_per_sample = t.bx * t.by * t.nzc;
+  if (zchunks > 0) nzc = zchunks < nseg ? zchunks : nseg;
+  else
+    while (base * nzc < 4 * 152 * 4 && 2 * nzc <= nseg) nzc *= 2;
+  const int spc = (nseg + nzc - 1) / nzc;  // segments per chunk
+  t.nzc = (nseg + spc - 1) / spc;
+  t.zc = spc * kZSeg;
+  t.nseg = nseg;
+  t.blocks_per_sample = t.bx * t.by * nseg;  // partial-sum entries per sample
   return t;
 }
 
@@ -710,9 +737,10 @@ TiledShape tiled_shape(int N, int S, int ry) {
 // other samples are still active.
 template <typename T, typename TA, int MODE>
 static void run_tiled(const char* cls, double bytes, TiledArgs args, const Batch& bt, cudaStream_t st) {
-  const TiledShape t = tiled_shape(args.N, bt.S, RowsPerThread<T>::value);
+  const TiledShape t = tiled_shape(args.N, bt.S, RowsPerThread<T>::value, bt.zchunks);
   args.nzc = t.nzc;
   args.zc = t.zc;
+  args.nseg = t.nseg;
   args.act = bt.act;
   const size_t smem = TiledSmem<T, TA, MODE>::total;  // up to ~91 KB (FP64): opt in above 48 KB
   static bool smem_set = false;  // once per instantiation (capture-friendly)
@@ -739,9 +767,16 @@ static const char* name(const char* base, const char* t) {
 
 // p is double-buffered: neighbouring tiles read the old p in their halos while
 // this tile writes the new one.
+// FP32 vectors on 32^3 and 64^3 grids go to the whole-row slab passes (slab.cu)
 template <typename T, typename TA>
 void tiled_apply(const T* z, const T* pold, T* pnew, const TA* a, T* q, double* partial, const SolveScalars* sc, int N,
                  const Batch& bt, int first, cudaStream_t st) {
+  if constexpr (std::is_same<T, float>::value && std::is_same<TA, float>::value) {
+    if (bt.stencil == 0 && slab_supported(N)) {
+      slab_apply(z, pold, pnew, a, q, nullptr, partial, sc, N, bt, first != 0, false, false, st);
+      return;
+    }
+  }
   TiledArgs A{};
   A.in0 = z; A.in1 = pold; A.a = a; A.out0 = q; A.out1 = pnew; A.partial = partial; A.sc = sc; A.N = N;
   A.first = first;
@@ -750,6 +785,10 @@ void tiled_apply(const T* z, const T* pold, T* pnew, const TA* a, T* q, double* 
 // fused variants of the mixed inner solve (see TM_PREU / TM_APPLYX)
 void tiled_apply_x(const float* z, const float* pold, float* pnew, const float* a, float* q, float* x, double* partial,
                    const SolveScalars* sc, int N, const Batch& bt, cudaStream_t st, bool x_first) {
+  if (bt.stencil == 0 && slab_supported(N)) {
+    slab_apply(z, pold, pnew, a, q, x, partial, sc, N, bt, false, true, x_first, st);
+    return;
+  }
   TiledArgs A{};
   A.in0 = z; A.in1 = pold; A.a = a; A.out0 = q; A.out1 = pnew; A.x = x; A.partial = partial; A.sc = sc; A.N = N;
   A.xfirst = x_first ? 1 : 0;
@@ -757,6 +796,10 @@ void tiled_apply_x(const float* z, const float* pold, float* pnew, const float* 
 }
 void tiled_pre_update(const float* r, const float* q, const __nv_bfloat16* a, const float* dinv, float* t, float* rnew,
                       const SolveScalars* sc, int N, const Batch& bt, double omega, cudaStream_t st) {
+  if (bt.stencil == 0 && slab_supported(N)) {
+    slab_pre<__nv_bfloat16>(r, q, a, dinv, t, rnew, sc, N, bt, omega, st);
+    return;
+  }
   TiledArgs A{};
   A.in0 = r; A.q = q; A.a = a; A.dinv = dinv; A.out0 = t; A.out1 = rnew; A.sc = sc; A.N = N; A.omega = omega;
   run_tiled<float, __nv_bfloat16, TM_PREU>("pre_f32", vbytes<float, __nv_bfloat16>(N, bt.n, 5, 1), A, bt, st);
@@ -765,6 +808,12 @@ void tiled_pre_update(const float* r, const float* q, const __nv_bfloat16* a, co
 template <typename T, typename TA>
 void tiled_pre(const T* r, const TA* a, const T* dinv, T* t, const SolveScalars* sc, int N, const Batch& bt,
                double omega, cudaStream_t st) {
+  if constexpr (std::is_same<T, float>::value) {
+    if (bt.stencil == 0 && slab_supported(N)) {
+      slab_pre<TA>(r, nullptr, a, dinv, t, nullptr, sc, N, bt, omega, st);
+      return;
+    }
+  }
   TiledArgs A{};
   A.in0 = r; A.a = a; A.dinv = dinv; A.out0 = t; A.sc = sc; A.N = N; A.omega = omega;
   run_tiled<T, TA, TM_PRE>(name("pre", tag<T>()), vbytes<T, TA>(N, bt.n, 3, 1), A, bt, st);
@@ -772,6 +821,12 @@ void tiled_pre(const T* r, const TA* a, const T* dinv, T* t, const SolveScalars*
 template <typename T, typename TA>
 void tiled_post(const T* r, const TA* a, const T* dinv, const T* ec, T* z, double* partial, const SolveScalars* sc,
                 int N, const Batch& bt, double omega, cudaStream_t st) {
+  if constexpr (std::is_same<T, float>::value) {
+    if (bt.stencil == 0 && slab_supported(N)) {
+      slab_post<TA>(r, a, dinv, ec, z, partial, sc, N, bt, omega, st);
+      return;
+    }
+  }
   TiledArgs A{};
   A.in0 = r; A.a = a; A.dinv = dinv; A.ec = ec; A.out0 = z; A.partial = partial; A.sc = sc; A.N = N;
   A.omega = omega;
@@ -791,7 +846,7 @@ int tiled_phi_df(const float2* y, int N, int S, const float2* gtab, const float2
                  double* partial, cudaStream_t st) {
   const TiledShape t = tiled_shape(N, S, 1);
   launch("phi_adjrhs", (double)S * nodes_of(N) * 16, k_phi_tiled_df, dim3(t.bx, t.by, (unsigned)(S * t.nzc)),
-         dim3(TX, TY), 0, st, y, N, gtab, mgtab, badj, partial, t.nzc, t.zc);
+         dim3(TX, TY), 0, st, y, N, gtab, mgtab, badj, partial, t.nzc, t.zc, t.nseg);
   return t.blocks_per_sample;
 }
 
@@ -799,7 +854,7 @@ int tiled_phi(const double* y, int N, int S, const double* gtab, const double* m
               cudaStream_t st) {
   const TiledShape t = tiled_shape(N, S, 1);
   launch("phi_adjrhs", (double)S * nodes_of(N) * 16, k_phi_tiled, dim3(t.bx, t.by, (unsigned)(S * t.nzc)),
-         dim3(TX, TY), 0, st, y, N, gtab, mgtab, badj, partial, t.nzc, t.zc);
+         dim3(TX, TY), 0, st, y, N, gtab, mgtab, badj, partial, t.nzc, t.zc, t.nseg);
   return t.blocks_per_sample;
 }
 
@@ -823,7 +878,8 @@ template void tiled_post<double, double>(const double*, const double*, const dou
 }  // namespace mlsgd
 
 namespace mlsgd {
-int tiled_blocks_per_sample(int N, int S, int elem) {
+int tiled_blocks_per_sample(int N, int S, int elem, bool slab) {
+  if (elem == 4 && slab && slab_supported(N)) return slab_shape(N, S).blocks_per_sample;
   return tiled_shape(N, S, elem == 8 ? RowsPerThread<double>::value : RowsPerThread<float>::value).blocks_per_sample;
 }
 }  // namespace mlsgd

@@ -4,19 +4,15 @@ Samples are independent (Sec. 2.2: the draws xi^(m,l) are iid over m and l), so
 a level's batch shards by sample index with no exchange on the data path; each
 rank merges its samples into its own level record with mlsgd_level_gradient.
 The only exchange is the merge of the records (Algorithm 1, PairwiseUpdate;
-Sec. 4.2 b): every rank gathers all records (count, shift, mean of dY~,
-second-order sums, mean dX~ field) and merges them pairwise in rank order
-with the Chan update after rescaling to the largest shift.  The collective is
-an all-gather (NCCL/gloo have no custom reduction operator).  Host-side FP64
-arithmetic on gathered records; the per-rank record itself is produced on the
-GPU.
+Sec. 4.2 b): every rank all-gathers the records (mean dX~ field and the eight
+scalars) and merges them pairwise in a fixed order with mlsgd_stats_merge, the
+library's Chan update with rescaling to the larger shift, so every rank ends
+with the same record.  The collective is an all-gather (NCCL and gloo have no
+custom reduction operator); with gloo the records travel through host memory.
+No merge arithmetic lives here: the Chan update exists once, in the library.
 """
-import numpy as np
 import torch
 import torch.distributed as dist
-
-# record layout (matches mlsgd_level_stats scalars)
-COUNT, SHIFT, MEAN_DY, S2_DY, S2_DX, PHI_MAX, ITERS, NOCONV = range(8)
 
 
 def shard_range(n_samples, rank, world):
@@ -26,47 +22,41 @@ def shard_range(n_samples, rank, world):
     return first, base + (1 if rank < extra else 0)
 
 
-def merge_records(a_field, a_sc, b_field, b_sc, theta, hc3):
-    """Chan merge of two level records (FP64 numpy); returns (field, scalars)."""
-    na, nb = a_sc[COUNT], b_sc[COUNT]
-    if nb == 0:
-        return a_field.copy(), a_sc.copy()
-    if na == 0:
-        return b_field.copy(), b_sc.copy()
-    shift = max(a_sc[SHIFT], b_sc[SHIFT])
-    fa, fb = np.exp(theta * (a_sc[SHIFT] - shift)), np.exp(theta * (b_sc[SHIFT] - shift))
-    n = na + nb
-    xa, xb = a_field * fa, b_field * fb
-    dx = xa - xb
-    field = xb + (na / n) * dx
-    ya, yb = a_sc[MEAN_DY] * fa, b_sc[MEAN_DY] * fb
-    dy = ya - yb
-    sc = np.zeros_like(a_sc)
-    sc[COUNT] = n
-    sc[SHIFT] = shift
-    sc[MEAN_DY] = yb + (na / n) * dy
-    sc[S2_DY] = a_sc[S2_DY] * fa * fa + b_sc[S2_DY] * fb * fb + dy * dy * na * nb / n
-    sc[S2_DX] = a_sc[S2_DX] * fa * fa + b_sc[S2_DX] * fb * fb + hc3 * float(dx @ dx) * na * nb / n
-    sc[PHI_MAX] = max(a_sc[PHI_MAX], b_sc[PHI_MAX])
-    sc[ITERS] = a_sc[ITERS] + b_sc[ITERS]
-    sc[NOCONV] = a_sc[NOCONV] + b_sc[NOCONV]
-    return field, sc
-
-
-def allgather_merge(field, scalars, theta, hc3, group=None):
-    """Gather every rank's record (CPU tensors or numpy) and merge pairwise in rank
-    order (distance-doubling tree over ranks).  Returns (field, scalars) as numpy."""
+def gather_records(field, scalars, group=None):
+    """Every rank's (field, scalars) tensors, in rank order.  NCCL gathers device
+    tensors; other backends gather host copies."""
     world = dist.get_world_size(group)
-    f = torch.as_tensor(np.asarray(field, dtype=np.float64))
-    s = torch.as_tensor(np.asarray(scalars, dtype=np.float64))
+    dev = field.device if dist.get_backend(group) == "nccl" else torch.device("cpu")
+    f, s = field.to(dev).contiguous(), scalars.to(dev).contiguous()
     fs = [torch.empty_like(f) for _ in range(world)]
     ss = [torch.empty_like(s) for _ in range(world)]
     dist.all_gather(fs, f, group=group)
     dist.all_gather(ss, s, group=group)
-    recs = [(fs[r].numpy(), ss[r].numpy()) for r in range(world)]
-    d = 1
-    while d < world:
-        for i in range(0, world - d, 2 * d):
-            recs[i] = merge_records(recs[i][0], recs[i][1], recs[i + d][0], recs[i + d][1], theta, hc3)
+    return fs, ss
+
+
+def tree_merge(items, merge):
+    """Merge items pairwise at distances 1, 2, 4, ... (item i takes item i + d for i a
+    multiple of 2d, the pairing of Algorithm 1's PairwiseUpdate); merge(dst, src)
+    merges src into dst in place.  Returns items[0], the merge of all."""
+    n, d = len(items), 1
+    while d < n:
+        for i in range(0, n - d, 2 * d):
+            merge(items[i], items[i + d])
         d *= 2
-    return recs[0]
+    return items[0]
+
+
+def allgather_merge(ctx, stats, group=None):
+    """The merge of every rank's level record `stats` (an mlsgd.Stats of ctx's
+    workload), formed on this rank's device with ctx.mlsgd_stats_merge.  Returns a
+    new mlsgd.Stats; `stats` is left unchanged."""
+    from .mlsgd import Stats
+    fs, ss = gather_records(stats.field, stats.scalars, group)
+    recs = []
+    for f, s in zip(fs, ss):
+        r = Stats(stats.level, stats.field.numel(), device=stats.field.device)
+        r.field.copy_(f)
+        r.scalars.copy_(s)
+        recs.append(r)
+    return tree_merge(recs, ctx.mlsgd_stats_merge)

@@ -11,6 +11,10 @@ steps, the total samples per level, when the extra level was added, and the
 rate exponents of the last batch.
 
     python -m paper_2606_09291_gb300.experiments --budget 30 --precision mixed
+
+The same module runs the full FP64 MLSGD workload (run_c2):
+
+    python -m paper_2606_09291_gb300.experiments --workload c2 --iterations 100 --log c2.jsonl
 """
 import argparse
 import json
@@ -57,8 +61,46 @@ def run_theta(theta, budget_s, precision="mixed", max_iters=10000, count_cap=1 <
                 gamma=last.get("gamma_hat", math.nan), cost_per_sample_ms=last.get("cost_per_sample_ms"))
 
 
+def run_c2(iterations=100, log_path=None, checkpoint=None, resume=None, count_cap=1 << 14, precision="fp64"):
+    """The full MLSGD workload c2: levels 0..4 (8^3 .. 128^3 cells), 128 KL modes of
+    the exponential covariance (corr length 0.2, sigma 1), theta 10, alpha 1e-4,
+    control on the 128^3 grid from u_0 = 0, the fixed step driver.fixed_step(alpha),
+    adaptive level count and batch sizes (eq:optimal-level, eq:optimal-batch-size,
+    eta = 0.9) from {128, 16, 2} on levels 0..2, `iterations` iterations, plain FP64.
+    Writes one JSON line per iteration to log_path (driver.log_line); returns a
+    summary of the history."""
+    p = dict(inputs.PRESETS["c2"])
+    counts = p.pop("counts")
+    p.pop("iterations")
+    p.update(precision=precision, rtol=1e-8, max_iter=400)
+    ctx = mlsgd.Context(**p)
+    try:
+        Nc = p["n0"] << (p["n_levels"] - 1)
+        z = torch.zeros(Nc ** 3, dtype=torch.float64, device="cuda")
+        hist = driver.run_mlsgd(ctx, z, counts, iterations, driver.fixed_step(p["alpha"]), eta=0.9,
+                                max_levels=p["n_levels"], adapt=True, step="fixed", time_levels=True,
+                                count_cap=count_cap, log_path=log_path, checkpoint=checkpoint, resume=resume)
+    finally:
+        ctx.close()
+    totals = [0] * p["n_levels"]
+    for h in hist:
+        for l, m in enumerate(h["counts"]):
+            totals[l] += m
+    pick = lambda h: dict(iteration=h["iteration"], objective=h["objective"], grad_norm=h["grad_norm"],  # noqa: E731
+                          levels=len(h["counts"]), counts=h["counts"],
+                          sqrt_mse=math.sqrt(max(h["err_sam"] + h["err_num"], 0.0)), elapsed_s=h["elapsed_s"])
+    return dict(workload="c2", iterations=len(hist), count_cap=count_cap, precision=precision,
+                total_samples=totals, first=pick(hist[0]), last=pick(hist[-1]),
+                every_10th=[pick(h) for h in hist[::10]], elapsed_s=hist[-1]["elapsed_s"],
+                levels_added_at=[h["iteration"] for a, h in zip(hist, hist[1:]) if len(h["counts"]) > len(a["counts"])])
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--workload", default="sweep", choices=("sweep", "c2"),
+                    help="sweep: the theta sweep of the paper's workload; c2: the full FP64 MLSGD run")
+    ap.add_argument("--iterations", type=int, default=100, help="c2: MLSGD iterations")
+    ap.add_argument("--log", default=None, help="c2: JSON-lines iteration log")
     ap.add_argument("--thetas", default=",".join(str(t) for t in inputs.PRESETS["paper"]["thetas"]))
     ap.add_argument("--budget", type=float, default=30.0, help="wall-clock seconds per theta")
     ap.add_argument("--precision", default="mixed", choices=("mixed", "fp64"))
@@ -70,6 +112,9 @@ def main(argv=None):
     a = ap.parse_args(argv)
     from . import build
     build.build()
+    if a.workload == "c2":
+        print(json.dumps(run_c2(a.iterations, log_path=a.log, count_cap=a.count_cap)), flush=True)
+        return 0
     for t in [float(x) for x in a.thetas.split(",")]:
         r = run_theta(t, a.budget, a.precision, a.max_iters, a.count_cap, a.seed, tau0=a.tau0)
         print(json.dumps(r), flush=True)

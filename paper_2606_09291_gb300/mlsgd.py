@@ -25,7 +25,8 @@ class Config(ctypes.Structure):
                 ("theta", ctypes.c_double), ("alpha", ctypes.c_double), ("rtol", ctypes.c_double),
                 ("max_iter", ctypes.c_int), ("precision", ctypes.c_int), ("inner_iters", ctypes.c_int),
                 ("max_batch", ctypes.c_int), ("field_tc", ctypes.c_int), ("ir_steps", ctypes.c_int),
-                ("field_model", ctypes.c_int), ("target_freq", ctypes.c_int), ("seed", ctypes.c_uint64)]
+                ("field_model", ctypes.c_int), ("target_freq", ctypes.c_int), ("seed", ctypes.c_uint64),
+                ("stencil", ctypes.c_int), ("z_chunks", ctypes.c_int), ("omega", ctypes.c_double)]
 
 
 class LevelStats(ctypes.Structure):
@@ -57,7 +58,7 @@ EXPORTS = ["mlsgd_create", "mlsgd_destroy", "mlsgd_last_error", "mlsgd_status_st
            "mlsgd_workspace_bytes", "mlsgd_mode_table", "mlsgd_sample_field", "mlsgd_solve_state_adjoint",
            "mlsgd_level_gradient", "mlsgd_stats_reset", "mlsgd_stats_merge", "mlsgd_step",
            "mlsgd_launch_count", "mlsgd_profile_start", "mlsgd_profile_stop", "mlsgd_solve_state_adjoint_noalloc",
-           "mlsgd_sample_field_tc", "mlsgd_step_adaptive"]
+           "mlsgd_sample_field_tc", "mlsgd_step_adaptive", "mlsgd_set_workspace"]
 
 _lib = None
 
@@ -92,6 +93,7 @@ def load(path=LIB_PATH):
     L.mlsgd_step_adaptive.argtypes = [vp, ctypes.POINTER(LevelStats), i32, dbl, dbl, dbl, i32, vp, vp,
                                       ctypes.POINTER(StepReport), vp]
     L.mlsgd_sample_field_tc.argtypes = [vp, i32, i32, i32, i64, i32, vp, vp, vp]
+    L.mlsgd_set_workspace.argtypes = [vp, vp, ctypes.c_size_t]
     L.mlsgd_solve_state_adjoint_noalloc.argtypes = [vp, i32, i32, vp, vp, vp, vp, vp, vp, vp, vp]
     L.mlsgd_launch_count.argtypes = []
     L.mlsgd_launch_count.restype = i64
@@ -151,7 +153,7 @@ class Context:
         defaults = dict(n_levels=3, n0=8, ctrl_level=None, n_modes=64, corr_len=0.3, sigma=1.0, theta=1.0,
                         alpha=1e-4, rtol=1e-8, max_iter=200, precision=MLSGD_FP64, inner_iters=0,
                         max_batch=256, field_tc=0, ir_steps=0, field_model=0,
-                        target_freq=1, seed=0)
+                        target_freq=1, seed=0, stencil=0, z_chunks=0, omega=0.0)
         defaults.update(cfg)
         if defaults["ctrl_level"] is None:
             defaults["ctrl_level"] = defaults["n_levels"] - 1
@@ -186,6 +188,11 @@ class Context:
     # --- C entry points -------------------------------------------------
     def mlsgd_workspace_bytes(self, level, n_samples):
         return int(self.L.mlsgd_workspace_bytes(self.h, level, n_samples))
+
+    def mlsgd_set_workspace(self, ptr, nbytes):
+        """Use [ptr, ptr + nbytes) of caller-owned device memory as scratch (ptr an int
+        device address, 0 with nbytes 0 to return to the context's own scratch)."""
+        self._check(self.L.mlsgd_set_workspace(self.h, ctypes.c_void_p(ptr) if ptr else None, nbytes))
 
     def mlsgd_mode_table(self):
         K = self.cfg["n_modes"]

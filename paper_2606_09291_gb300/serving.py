@@ -84,6 +84,60 @@ class MixServer:
         return times
 
 
+class FirstFit:
+    """First-fit allocator of byte ranges in [0, size) in granules of `granule`
+    bytes (256: the library's workspace alignment), the HBM arena of the
+    continuous-batching server."""
+
+    def __init__(self, size, granule=256):
+        self.size, self.granule = int(size), int(granule)
+        self.free = [(0, self.size)]  # sorted, coalesced (offset, length)
+
+    def round(self, n):
+        g = self.granule
+        return (int(n) + g - 1) // g * g
+
+    def alloc(self, n):
+        n = self.round(n)
+        for i, (off, ln) in enumerate(self.free):
+            if ln >= n:
+                self.free[i:i + 1] = [(off + n, ln - n)] if ln > n else []
+                return off
+        return None
+
+    def release(self, off, n):
+        n = self.round(n)
+        self.free.append((off, n))
+        self.free.sort()
+        merged = []
+        for o, ln in self.free:
+            if merged and merged[-1][0] + merged[-1][1] == o:
+                merged[-1] = (merged[-1][0], merged[-1][1] + ln)
+            else:
+                merged.append((o, ln))
+        self.free = merged
+
+
+def device_overlap(records):
+    """From device timestamps (dev_start_ms, dev_end_ms per request): the time some
+    request ran, the time at least two ran together, and the most that ran at once."""
+    ev = sorted([(r["dev_start_ms"], 1) for r in records] + [(r["dev_end_ms"], -1) for r in records])
+    busy = multi = 0.0
+    depth = peak = 0
+    last = None
+    for t, d in ev:
+        if last is not None:
+            if depth >= 1:
+                busy += t - last
+            if depth >= 2:
+                multi += t - last
+        depth += d
+        peak = max(peak, depth)
+        last = t
+    return dict(busy_ms=busy, overlapped_ms=multi, overlap_fraction=multi / busy if busy > 0 else 0.0,
+                max_concurrent=peak)
+
+
 class ContinuousServer:
     """Continuous batching of per-level sample-solve requests.
 
@@ -91,13 +145,17 @@ class ContinuousServer:
     multilevel estimate, computed by mlsgd_level_gradient into its own level record
     (sample identity (seed, estimate id, level, index), so a request's result does
     not depend on what else runs).  The server owns n_slots slots, each a library
-    context with its own scratch and its own CUDA stream.  Requests wait in arrival
-    order; the head of the queue is admitted to a free slot as soon as one frees up
-    and the workspace bytes of the requests in flight plus its own fit the HBM
-    budget, so work arriving while the GPU is busy starts without waiting for the
-    running requests to end and overlaps them on the device.  Every slot's scratch
-    is sized once for the largest request before serving (no allocation, hence no
-    device synchronisation, while serving)."""
+    context with its own CUDA stream, and one HBM arena of `budget` bytes: a request
+    runs in a range of the arena that it holds from launch to completion (handed to
+    its slot's context with mlsgd_set_workspace, so the library allocates no
+    scratch while serving).  Requests wait in arrival order; the head of the queue
+    is admitted as soon as a slot is free and the arena has room for its workspace
+    bytes (mlsgd_workspace_bytes), so work arriving while the GPU is busy starts
+    without waiting for the running requests to end and overlaps them on the
+    device.  The budget defaults to the smaller of half the device memory free at
+    construction and n_slots times the largest request's workspace.  Each request's
+    start and end are also recorded as device events, so overlap is measured on the
+    GPU's own clock."""
 
     def __init__(self, cfg, n_slots, largest_requests, hbm_budget=None):
         self.cfg = dict(cfg)
@@ -105,24 +163,43 @@ class ContinuousServer:
         L = self.cfg["n_levels"]
         Nc = self.cfg["n0"] << self.cfg.get("ctrl_level", L - 1)
         zwarm = torch.zeros(Nc ** 3, dtype=torch.float64, device="cuda")
+        probe = mlsgd.Context(**self.cfg)
+        largest = max(probe.mlsgd_workspace_bytes(l, n) for l, n in largest_requests)
+        probe.close()
+        if hbm_budget is None:
+            hbm_budget = min(int(0.5 * torch.cuda.mem_get_info()[0]), n_slots * FirstFit(0).round(largest))
+        self.arena = torch.empty(int(hbm_budget), dtype=torch.uint8, device="cuda")
+        self.base = self.arena.data_ptr()
+        self.set_budget(hbm_budget)
         for _ in range(n_slots):
             ctx = mlsgd.Context(**self.cfg)
             stream = torch.cuda.Stream()
             stats = [ctx.new_stats(l) for l in range(L)]
-            for (level, n) in largest_requests:  # size the scratch and build the per-grid tables
-                ctx.mlsgd_level_gradient(0, level, 0, n, zwarm, stats[level], stream=stream)
+            for (level, n) in largest_requests:  # build the per-grid tables (arena start as scratch)
+                fp = ctx.mlsgd_workspace_bytes(level, n)
+                if fp <= self.budget:
+                    ctx.mlsgd_set_workspace(self.base, fp)
+                    ctx.mlsgd_level_gradient(0, level, 0, n, zwarm, stats[level], stream=stream)
+                    stream.synchronize()
             self.slots.append(dict(ctx=ctx, stream=stream, stats=stats, req=None, ev=None, t0=None))
         torch.cuda.synchronize()
-        # bytes of library scratch the requests in flight may need together (None: no
-        # limit beyond the slots, whose scratch is already reserved)
-        self.budget = float("inf") if hbm_budget is None else hbm_budget
+
+    def set_budget(self, nbytes):
+        """Admit by at most nbytes of the arena from now on (at most the arena's size)."""
+        self.budget = min(int(nbytes), self.arena.numel())
+        self.alloc = FirstFit(self.budget)
 
     @staticmethod
     def _new_event():
         return torch.cuda.Event(enable_timing=True)
 
+    @staticmethod
+    def _ref_stream():
+        return torch.cuda.current_stream()
+
     def close(self):
         for s in self.slots:
+            s["ctx"].mlsgd_set_workspace(0, 0)
             s["ctx"].close()
 
     def footprint(self, level, n):
@@ -130,19 +207,24 @@ class ContinuousServer:
 
     def run(self, requests, z, keep=False):
         """requests: list of (arrival_s, estimate_id, level, n), sorted by arrival.
-        Returns one dict per request (arrival, start, done, latency_ms, service_ms) and,
-        with keep, copies of the level records (field, scalars).  A request whose
-        workspace alone exceeds the HBM budget could never be admitted: ValueError."""
+        Returns one dict per request (arrival, start, done, latency_ms, service_ms,
+        dev_start_ms / dev_end_ms on the device clock from the start of the run) and,
+        with keep, copies of the level records (field, scalars).  self.deferred counts
+        the polls in which the queue head waited for arena room while a slot was free.
+        A request whose workspace alone exceeds the budget could never be admitted:
+        ValueError."""
         import collections
         import time
         for (a, eid, level, n) in requests:
-            if self.footprint(level, n) > self.budget:
+            if self.alloc.round(self.footprint(level, n)) > self.budget:
                 raise ValueError("request (estimate %d, level %d, %d samples) needs %d workspace bytes, over the "
                                  "budget of %d" % (eid, level, n, self.footprint(level, n), self.budget))
         pending = collections.deque(range(len(requests)))
         queue = collections.deque()
         out = [None] * len(requests)
-        in_flight = 0
+        self.deferred = 0
+        ref = self._new_event()
+        ref.record(self._ref_stream())
         t_start = time.perf_counter()
         while pending or queue or any(s["req"] is not None for s in self.slots):
             now = time.perf_counter() - t_start
@@ -153,12 +235,13 @@ class ContinuousServer:
                     i = s["req"]
                     a, eid, level, n = requests[i]
                     rec = dict(arrival=a, start=s["t0"], done=now, latency_ms=1e3 * (now - a),
-                               service_ms=s["e0"].elapsed_time(s["ev"]), level=level, n=n, estimate=eid)
+                               service_ms=s["e0"].elapsed_time(s["ev"]), level=level, n=n, estimate=eid,
+                               dev_start_ms=ref.elapsed_time(s["e0"]), dev_end_ms=ref.elapsed_time(s["ev"]))
                     if keep:
                         st = s["stats"][level]
                         rec["field"], rec["scalars"] = st.field.clone(), st.scalars.clone()
                     out[i] = rec
-                    in_flight -= self.footprint(level, n)
+                    self.alloc.release(s["off"], self.footprint(level, n))
                     s["req"] = None
             for s in self.slots:  # admissions, in arrival order
                 if not queue:
@@ -168,18 +251,20 @@ class ContinuousServer:
                 i = queue[0]
                 a, eid, level, n = requests[i]
                 fp = self.footprint(level, n)
-                if in_flight + fp > self.budget:
+                off = self.alloc.alloc(fp)
+                if off is None:
+                    self.deferred += 1
                     break
                 queue.popleft()
-                in_flight += fp
                 st = s["stats"][level]
+                s["ctx"].mlsgd_set_workspace(self.base + off, self.alloc.round(fp))
                 s["e0"] = self._new_event()
                 s["e0"].record(s["stream"])
                 s["ctx"].mlsgd_stats_reset(st, stream=s["stream"])
                 s["ctx"].mlsgd_level_gradient(eid, level, 0, n, z, st, stream=s["stream"])
                 s["ev"] = self._new_event()
                 s["ev"].record(s["stream"])
-                s["req"], s["t0"] = i, now
+                s["req"], s["t0"], s["off"] = i, now, off
             if not queue or all(s["req"] is not None for s in self.slots):
                 time.sleep(1e-4)
         return out
@@ -268,8 +353,9 @@ def main(argv=None):
     sat = srv.run(poisson_mix_requests(mix, a.requests, 0.0, first_estimate=20000), z)  # all at t = 0
     span = max(r["done"] for r in sat) - min(r["start"] for r in sat)
     cap = a.requests / span  # estimates per second at saturation
-    out["continuous"] = {"slots": a.slots, "saturated_estimates_per_s": cap,
-                         "saturated_sample_gradients_per_s": cap * sum(mix), "load": []}
+    out["continuous"] = {"slots": a.slots, "hbm_budget_bytes": srv.budget, "saturated_estimates_per_s": cap,
+                         "saturated_sample_gradients_per_s": cap * sum(mix), "device_overlap": device_overlap(sat),
+                         "deferred_by_hbm": srv.deferred, "load": []}
     for f in (0.25, 0.5, 0.75, 0.9):
         res = srv.run(poisson_mix_requests(mix, a.requests, f * cap, seed=2, first_estimate=30000), z)
         est = {}

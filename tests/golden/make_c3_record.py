@@ -9,13 +9,17 @@ eq:delta-notation, eq:sec-order-sum): sample count, shift c = max Phi, the
 mean of dX~ = X~_3 - X~_2 on the control grid, the mean of dY~ and both
 second-order sums, all at the shift c.
 
-The oracle solves every sample to rtol 1e-13 (sparse direct below 32^3,
-Galerkin-MG-PCG above).  The 4096 samples are spread over one spawn-started
+The oracle solves every sample to rtol 1e-12 (sparse direct below 32^3,
+Galerkin-MG-PCG above; at 64^3 with this coefficient contrast the true residual
+FP64 can attain lies near 1e-13 ||b||, so rtol 1e-13 stalls for some samples,
+while 1e-12 is six orders below the mixed path's bar of 1e-6).  The 4096 samples are spread over one spawn-started
 process per host core in chunks; each chunk's record is kept at its own shift
 and the chunks are merged with oracle.mlmc.merge_shifted.  Only oracle/ and the
-seeded input module are called.  About 15 minutes on 8 cores:
+seeded input module are called.  The sparse solves are memory-bound, so the rate
+depends on the host's memory bandwidth: about 10 minutes on 16 Grace cores,
+hours on a small x86 host.
 
-    python tests/golden/make_c3_record.py
+    python tests/golden/make_c3_record.py [output.npz]
 """
 import multiprocessing as mp
 import os
@@ -37,7 +41,7 @@ def _workload():
     from paper_2606_09291_gb300 import inputs
     p = inputs.PRESETS["c3"]
     return mlmc.Workload(n0=p["n0"], n_levels=p["n_levels"], n_modes=p["n_modes"], corr_len=p["corr_len"],
-                         sigma=p["sigma"], theta=p["theta"], alpha=p["alpha"], seed=p["seed"])
+                         sigma=p["sigma"], theta=p["theta"], alpha=p["alpha"], seed=p["seed"], rtol=1e-12)
 
 
 def _init():
@@ -68,9 +72,10 @@ def main():
     rec = mlmc.merge_shifted(parts, W.theta, W.hc3)
     S = rec["stats"]
     assert S.n == SAMPLES
-    np.savez_compressed(OUT, count=S.n, shift=rec["shift"], mean_x=S.mean_x, s2_x=S.s2_x, mean_y=S.mean_y,
+    out = sys.argv[1] if len(sys.argv) > 1 else OUT
+    np.savez_compressed(out, count=S.n, shift=rec["shift"], mean_x=S.mean_x, s2_x=S.s2_x, mean_y=S.mean_y,
                         s2_y=S.s2_y, iteration=ITERATION, level=LEVEL, first_sample=0, oracle_rtol=W.rtol)
-    print("wrote %s: %d samples in %.0f s on %d processes, shift %.15g" % (OUT, S.n, time.time() - t, procs,
+    print("wrote %s: %d samples in %.0f s on %d processes, shift %.15g" % (out, S.n, time.time() - t, procs,
                                                                            rec["shift"]))
 
 

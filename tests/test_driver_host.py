@@ -123,3 +123,67 @@ def test_time_budget_scales_the_next_batches(monkeypatch):
     got = hist[1]["counts"]
     assert got == [max(2, int(m * f)) for m in planned]
     assert sum(m * c for m, c in zip(got, cost + [128.0])) <= 1000.0 * budget
+
+
+class StepCtx(FakeCtx):
+    """A fake whose step moves z by an amount that depends on the iteration, the batch
+    sizes and the previous step size, and whose plan depends on the iteration, so
+    that any state lost at a checkpoint changes the continuation."""
+
+    def __init__(self, n_levels, seed=3):
+        super().__init__(n_levels, [])
+        self.cfg["seed"] = seed
+
+    def _report(self, stats_list):
+        it = self.launches[-1][0]
+        n = [m for (i, l, m) in self.launches if i == it]
+        return dict(grad_norm=1.0 / (it + 1), tau=0.1 + 0.01 * it, next_counts=[8 + it + l for l in range(len(n))],
+                    err_sam=0.01 * it, err_num=1e-4, objective=0.5 + it, risk=0.4)
+
+    def mlsgd_step(self, stats_list, tau, z, eta=0.9, max_levels=None, grad=None, stream=None):
+        self.steps.append(("fixed", len(stats_list), tau, None))
+        rep = self._report(stats_list)
+        it = self.launches[-1][0]
+        z += tau * (it + 1) * torch.arange(z.numel(), dtype=z.dtype) + sum(m for (i, l, m) in self.launches if i == it)
+        return rep
+
+    def mlsgd_step_adaptive(self, stats_list, tau0, tau_prev, z, grad_prev, eta=0.9, max_levels=None, stream=None):
+        self.steps.append(("adaptive", len(stats_list), tau0, tau_prev))
+        rep = self._report(stats_list)
+        z -= (tau_prev + 1.0) * grad_prev
+        grad_prev += 0.5 * z
+        return rep
+
+
+@pytest.mark.parametrize("step", ["fixed", "adaptive"])
+def test_checkpoint_resume_is_bit_exact(tmp_path, step):
+    ck = str(tmp_path / "ck.npz")
+    a = StepCtx(3)
+    za = torch.linspace(0, 1, 16, dtype=torch.float64)
+    ha = driver.run_mlsgd(a, za, [6, 2], 5, tau=0.3, step=step)
+    b = StepCtx(3)
+    zb = torch.linspace(0, 1, 16, dtype=torch.float64)
+    hb = driver.run_mlsgd(b, zb, [6, 2], 3, tau=0.3, step=step, checkpoint=ck)
+    c = StepCtx(3)
+    zc = torch.zeros(16, dtype=torch.float64)  # overwritten from the checkpoint
+    hc = driver.run_mlsgd(c, zc, [99], 5, tau=0.3, step=step, resume=ck)
+    assert torch.equal(zc, za)
+    assert b.launches + c.launches == a.launches and b.steps + c.steps == a.steps
+    assert [h["counts"] for h in hb + hc] == [h["counts"] for h in ha]
+    assert [h["iteration"] for h in hc] == [3, 4]
+    with pytest.raises(ValueError):
+        driver.run_mlsgd(StepCtx(3, seed=4), torch.zeros(16, dtype=torch.float64), [6], 5, tau=0.3, step=step,
+                         resume=ck)
+
+
+def test_iteration_log_lines(tmp_path):
+    import json
+    log = str(tmp_path / "log.jsonl")
+    ctx = StepCtx(2)
+    driver.run_mlsgd(ctx, torch.zeros(4, dtype=torch.float64), [6, 2], 3, tau=0.3, log_path=log)
+    lines = [json.loads(x) for x in open(log)]
+    assert [d["iteration"] for d in lines] == [0, 1, 2]
+    assert [d["counts"] for d in lines] == [[6, 2], [8, 9], [9, 10]]
+    for d in lines:
+        assert d["sqrt_mse"] == pytest.approx(math.sqrt(d["err_sam"] + d["err_num"]))
+        assert {"objective", "grad_norm", "tau", "elapsed_s"} <= set(d)

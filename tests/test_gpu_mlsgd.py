@@ -126,3 +126,29 @@ def test_large_risk_aversion_levels_0_to_2(lib):
     assert rel_err(grad.cpu().numpy(), out["grad"]) <= 1e-6
     assert abs(rep["risk"] - out["risk"]) <= 1e-6 * abs(out["risk"])
     ctx.close()
+
+
+@pytest.mark.parametrize("step", ["fixed", "adaptive"])
+def test_resume_from_checkpoint_is_bit_exact(lib, tmp_path, step):
+    """Four MLSGD iterations against two, a checkpoint, and two more from it: the
+    counter-based draws make the resumed run repeat the uninterrupted one bit for bit
+    (control, gradient norms, batch sizes and plans)."""
+    from paper_2606_09291_gb300 import driver
+    cfg = dict(n_levels=3, n0=8, n_modes=32, corr_len=0.3, sigma=1.0, theta=5.0, alpha=1e-4, seed=4, rtol=1e-10,
+               max_iter=300, precision="fp64")
+    tau = 0.5 if step == "adaptive" else driver.fixed_step(1e-4)
+    runs = []
+    for plan in (dict(iterations=4), dict(iterations=2, checkpoint=str(tmp_path / "ck.npz"))):
+        ctx = lib.Context(**cfg)
+        z = torch.tensor(inputs.z_test(32), dtype=torch.float64, device="cuda")
+        runs.append((driver.run_mlsgd(ctx, z, [8, 4, 2], tau=tau, step=step, count_cap=16, **plan), z))
+        ctx.close()
+    ctx = lib.Context(**cfg)
+    z = torch.zeros(32 ** 3, dtype=torch.float64, device="cuda")
+    tail = driver.run_mlsgd(ctx, z, [8], 4, tau=tau, step=step, count_cap=16, resume=str(tmp_path / "ck.npz"))
+    ctx.close()
+    (full, zf), (head, _) = runs
+    assert torch.equal(z, zf)
+    for a, b in zip(full, head + tail):
+        assert a["iteration"] == b["iteration"] and a["counts"] == b["counts"]
+        assert a["grad_norm"] == b["grad_norm"] and a["next_counts"] == b["next_counts"] and a["tau"] == b["tau"]

@@ -138,6 +138,31 @@ def test_batch_composition_is_bitwise_irrelevant(lib):
     assert np.array_equal(y1[:2], y2) and np.array_equal(q1[:2], q2) and np.array_equal(p1[:2], p2)
 
 
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_batch_size_does_not_change_a_sample(lib, precision):
+    """Small batches split the tiled passes' z march into more chunks than large
+    ones; the partial sums are formed per fixed 8-plane segment, so a sample's
+    solution is bitwise the same in a batch of 2 and in a batch of 2600 (32^3 grid:
+    4 chunks against 1)."""
+    cfg = dict(CFG, rtol=1e-8 if precision == "mixed" else 1e-12, max_iter=200, precision=precision,
+               max_batch=4096)
+    ctx = lib.Context(**cfg)
+    zt = cuda(inputs.z_test(32))
+    outs = []
+    for S in (2, 2600):
+        la = torch.zeros(S, 32 ** 3, dtype=torch.float64, device="cuda")
+        ctx.mlsgd_sample_field(3, 2, 2, 0, S, log_a=la)
+        y = torch.zeros(S, 33 ** 3, dtype=torch.float64, device="cuda")
+        q, phi = torch.zeros_like(y), torch.zeros(S, dtype=torch.float64, device="cuda")
+        it, stt = torch.zeros(S, dtype=torch.int32, device="cuda"), torch.zeros(S, dtype=torch.int32, device="cuda")
+        assert ctx.mlsgd_solve_state_adjoint(2, S, la, zt, y, q, phi, it, stt) == 0, ctx.L.mlsgd_last_error(ctx.h)
+        outs.append((y[:2].cpu().numpy(), q[:2].cpu().numpy(), phi[:2].cpu().numpy(), it[:2].cpu().numpy()))
+        del la, y, q
+    ctx.close()
+    for a, b in zip(*outs):
+        assert np.array_equal(a, b)
+
+
 def _oracle_level(W, level, n, z, it=0):
     r = mlmc.level_batch(W, it, level, range(n), z)
     return r

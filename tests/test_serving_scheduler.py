@@ -6,13 +6,15 @@ completes when that time has passed.  What is checked is the scheduling policy
 alone: requests are launched in arrival order, never before they arrive, each
 exactly once; the workspace bytes of the requests running at any launch plus the
 launched one stay within the HBM budget; a request larger than the budget is
-rejected instead of waiting forever."""
+rejected instead of waiting forever; the arena's first-fit allocator hands out
+disjoint ranges and coalesces what comes back; the device-clock overlap summary
+counts time with two or more requests running."""
 import time
 
 import pytest
 
 pytest.importorskip("torch")
-from paper_2606_09291_gb300.serving import ContinuousServer, poisson_mix_requests  # noqa: E402
+from paper_2606_09291_gb300.serving import ContinuousServer, FirstFit, device_overlap, poisson_mix_requests  # noqa: E402
 
 
 class FakeStream:
@@ -42,6 +44,9 @@ class FakeCtx:
     def mlsgd_workspace_bytes(self, level, n):
         return self.fp(level, n)
 
+    def mlsgd_set_workspace(self, ptr, nbytes):
+        self.ws = (ptr, nbytes)
+
     def mlsgd_stats_reset(self, st, stream=None):
         pass
 
@@ -56,8 +61,11 @@ def make_server(n_slots, n_levels, budget, service_s, footprint):
     log = []
     srv = object.__new__(ContinuousServer)
     srv.cfg = dict(n_levels=n_levels)
-    srv.budget = float("inf") if budget is None else budget
+    srv.budget = 10 ** 12 if budget is None else budget
+    srv.alloc = FirstFit(srv.budget, granule=1)
+    srv.base = 0
     srv._new_event = FakeEvent
+    srv._ref_stream = FakeStream
 
     def check(now, fp):  # requests still running at this launch, by their simulated end
         running = sum(footprint(r["level"], r["n"]) for r in log if r["until"] > now)
@@ -116,3 +124,23 @@ def test_request_over_budget_is_rejected():
     with pytest.raises(ValueError):
         srv.run([(0.0, 0, 0, 1)], z=None)
     assert log == []
+
+
+def test_first_fit_arena():
+    a = FirstFit(4096)
+    x, y, z = a.alloc(100), a.alloc(1000), a.alloc(256)
+    assert (x, y, z) == (0, 256, 1280)  # 256-byte granules
+    assert a.alloc(4096) is None
+    a.release(y, 1000)
+    assert a.alloc(700) == 256          # first fit reuses the hole
+    a.release(x, 100)
+    a.release(z, 256)
+    a.release(256, 700)
+    assert a.free == [(0, 4096)]        # coalesced back to one range
+
+
+def test_device_overlap_summary():
+    recs = [dict(dev_start_ms=0.0, dev_end_ms=4.0), dict(dev_start_ms=1.0, dev_end_ms=3.0),
+            dict(dev_start_ms=6.0, dev_end_ms=7.0)]
+    o = device_overlap(recs)
+    assert o["busy_ms"] == 5.0 and o["overlapped_ms"] == 2.0 and o["max_concurrent"] == 2
