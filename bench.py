@@ -28,9 +28,10 @@ METRIC = "sample-gradients/s (state+adjoint) at rtol 1e-8 vs plain FP64; p99 lat
 # DRAM bytes (read + write) over algorithmic bytes of the dominant kernel class, from
 # one ncu capture of its 64^3 fine launch on a smaller batch of this workload (inputs
 # larger than L2); a full launch processes more samples of the same grid, so its
-# traffic is this ratio times its algorithmic bytes.  Only valid for the kernel as
+# traffic is this ratio times its algorithmic bytes (ncu on the 64^3 slab launches of a
+# 256-sample batch, profiles/slab_passes_c3_ncu.md).  Only valid for the kernel as
 # captured: emptied with each change of that kernel until it is captured again.
-TRAFFIC_RATIO = {}
+TRAFFIC_RATIO = {"apply_f32": 1.001, "pre_f32": 1.025, "post_f32": 1.017}
 UNIT = "sample-gradients/s"
 
 

@@ -39,10 +39,15 @@ namespace {
 
 enum SlabMode { SL_APPLY = 0, SL_PRE = 1, SL_POST = 2, SL_PREU = 4, SL_APPLYX = 5 };
 constexpr int kSegPlanes = 8;  // partial-sum segment (the same as tiled.cu's kZSeg)
-// Raw plane slots per ring: 4 (iteration k copies plane k + 3 into the slot of plane
-// k - 1); 3 for PREU, which stages three node vectors, so that its shared memory
-// still admits three blocks per SM.
-constexpr int ring_of(int mode) { return mode == 4 ? 3 : 4; }
+// Raw plane slots: plane m of a chunk (j = m - (kbeg-1)) lives in slot j % 4 of the
+// node vectors whose own-node values the epilogue reads, and in slot j % 3 of D^-1 in
+// PRE and PREU (read only when deriving plane m, so three slots suffice: iteration k
+// copies plane k + 3, whose D^-1 replaces that of plane k, derived one iteration
+// earlier).  The shorter ring keeps PREU, which stages three node vectors, at three
+// blocks per SM.
+constexpr int kRing = 4;
+constexpr int kAhead = 3;
+constexpr int short_vec(int mode) { return mode == 1 ? 1 : (mode == 4 ? 2 : -1); }
 
 struct SlabArgs {
   const float* in0;   // APPLY/APPLYX: z     PRE/PREU/POST: r
@@ -85,9 +90,11 @@ struct SlabSmem {
   using G = SlabGeo<N>;
   static constexpr int NV = (MODE == SL_PREU) ? 3 : 2;  // staged node vectors
   static constexpr bool kPost = MODE == SL_POST;
-  static constexpr int kRing = ring_of(MODE);
+  static constexpr int SV = short_vec(MODE);             // the vector with a 3-slot ring (or -1)
+  static constexpr int slots(int v) { return v == SV ? kRing - 1 : kRing; }
+  static constexpr int first_slot(int v) { return v == 0 ? 0 : first_slot(v - 1) + slots(v - 1); }
   static constexpr size_t raw = 0;
-  static constexpr size_t cells = raw + sizeof(float) * NV * kRing * G::RAWF;
+  static constexpr size_t cells = raw + sizeof(float) * first_slot(NV) * G::RAWF;
   static constexpr size_t cellb = (size_t)G::CROWS * N * sizeof(TA);  // one cell slab (a multiple of 16)
   static constexpr size_t craw = cells + kRing * cellb;
   static constexpr size_t xs = craw + (kPost ? sizeof(float) * 3 * G::CRAWF : 0);
@@ -127,6 +134,17 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
 
 __device__ __forceinline__ float ld_cell(const float* c, int i) { return c[i]; }
 __device__ __forceinline__ float ld_cell(const __nv_bfloat16* c, int i) { return __bfloat162float(c[i]); }
+// two neighbouring cells from an 8-byte (FP32) or 4-byte (BF16) aligned address
+__device__ __forceinline__ void ld_cell_pair(const float* c, float& a, float& b) {
+  const float2 v = *reinterpret_cast<const float2*>(c);
+  a = v.x;
+  b = v.y;
+}
+__device__ __forceinline__ void ld_cell_pair(const __nv_bfloat16* c, float& a, float& b) {
+  const uint32_t v = *reinterpret_cast<const uint32_t*>(c);
+  a = __uint_as_float(v << 16);           // BF16 is the upper half of an FP32
+  b = __uint_as_float(v & 0xffff0000u);
+}
 
 template <int N, typename TA, int MODE>
 __global__ void __launch_bounds__(256, 3) k_slab(SlabArgs A) {
@@ -136,9 +154,9 @@ __global__ void __launch_bounds__(256, 3) k_slab(SlabArgs A) {
   constexpr bool kApply = MODE == SL_APPLY || MODE == SL_APPLYX;
   constexpr bool kPost = MODE == SL_POST;
   constexpr int NV = L::NV;
-  constexpr int kRing = L::kRing, kAhead = kRing - 1;
+  static_assert(N1 % 4 == 1 && G::NC1 % 4 == 1, "shift arithmetic assumes N + 1 = 1 mod 4");
   extern __shared__ __align__(16) unsigned char sm[];
-  float* raw = (float*)(sm + L::raw);  // [NV][kRing][RAWF]
+  float* raw = (float*)(sm + L::raw);  // vector v, plane j: slot L::first_slot(v) + j % L::slots(v)
   TA* cs = (TA*)(sm + L::cells);       // [kRing][CROWS * N]
   float* craw = (float*)(sm + L::craw);  // [3][CRAWF]
   float* xs = (float*)(sm + L::xs);    // [3][XPL]
@@ -201,7 +219,7 @@ __global__ void __launch_bounds__(256, 3) k_slab(SlabArgs A) {
     }
     mbar_expect(bar, total);
     for (int v = 0; v < nv; ++v)
-      bulk_copy(smem_u32(raw + (v * kRing + slot) * G::RAWF), vin[v] + (noff & ~3LL), nb, bar);
+      bulk_copy(smem_u32(raw + (L::first_slot(v) + j % L::slots(v)) * G::RAWF), vin[v] + (noff & ~3LL), nb, bar);
     if (cell) {
       const long long coff_c = (long long)s * kCells + (long long)m * N * N + (long long)(y0 - 1) * N;
       bulk_copy(smem_u32((unsigned char*)cs + slot * L::cellb), (const TA*)A.a + coff_c, cb, bar);
@@ -216,7 +234,8 @@ __global__ void __launch_bounds__(256, 3) k_slab(SlabArgs A) {
       atomicOr(A.err, 1);
     }
   };
-  auto delta_of = [&](int m) { return (int)(((long long)s * kNodes + (long long)m * N1 * N1 + (long long)(y0 - 1) * N1) & 3); };
+  // offset modulo 4 of node (0, y0-1, m) of sample s: N+1, (N+1)^2 and (N+1)^3 are 1 mod 4
+  auto delta_of = [&](int m) { return (s + m + y0 - 1) & 3; };
 
   // ---- entries this thread derives: e = tid + 256 j, operand index e + e / N1 (stride N + 2)
   int xo[G::NE];
@@ -230,8 +249,7 @@ __global__ void __launch_bounds__(256, 3) k_slab(SlabArgs A) {
   // (a, b) of the coarse tile writes fine nodes (2a + p, 2b + q)
   auto interp = [&](int c) {
     if (dead) return;
-    const float* cp = craw + (c % 3) * G::CRAWF +
-                      (int)(((long long)s * kCNodes + (long long)c * G::NC1 * G::NC1 + (long long)cy0 * G::NC1) & 3);
+    const float* cp = craw + (c % 3) * G::CRAWF + ((s + c + cy0) & 3);
     float* ed = eps + (c & 1) * G::XPL;
 #pragma unroll
     for (int j = 0; j < G::NI; ++j) {
@@ -255,29 +273,33 @@ __global__ void __launch_bounds__(256, 3) k_slab(SlabArgs A) {
   // derive operand plane m (ring slot of m, operand slot m % 3)
   auto derive = [&](int m, bool interp_next) {
     if (dead) return;
-    const int slot = (m - first) % kRing;
+    const int jm = m - first;
     const int dl = delta_of(m);
-    const float* r0 = raw + (0 * kRing + slot) * G::RAWF + dl;
-    const float* r1 = raw + (1 * kRing + slot) * G::RAWF + dl;
-    const float* r2 = raw + (2 * kRing + slot) * G::RAWF + dl;
+    const float* r0 = raw + (L::first_slot(0) + jm % L::slots(0)) * G::RAWF + dl;
+    const float* r1 = raw + (L::first_slot(1) + jm % L::slots(1)) * G::RAWF + dl;
+    const float* r2 = raw + (L::first_slot(NV - 1) + jm % L::slots(NV - 1)) * G::RAWF + dl;
     float* xp = xs + (m % 3) * G::XPL;
     if (kPost && interp_next && !(m & 1) && (m >> 1) + 1 <= G::NC) interp((m >> 1) + 1);
     const float* e0 = eps + ((m >> 1) & 1) * G::XPL;
     const float* e1 = eps + (((m + 1) >> 1) & 1) * G::XPL;
+    auto each = [&](auto f) {
 #pragma unroll
-    for (int j = 0; j < G::NE; ++j) {
-      const int e = tid + 256 * j;
-      if (j == G::NE - 1 && e >= NR * N1) break;
-      float v;
-      if (kApply) {
-        v = A.first ? r0[e] : fmaf(beta, r1[e], r0[e]);
-      } else if (MODE == SL_PREU) {
-        v = omega * fmaf(-alpha, r1[e], r0[e]) * r2[e];
-      } else {
-        v = omega * r0[e] * r1[e];
-        if (kPost) v += (m & 1) ? 0.5f * (e0[xo[j]] + e1[xo[j]]) : e0[xo[j]];
+      for (int j = 0; j < G::NE; ++j) {
+        const int e = tid + 256 * j;
+        if (j == G::NE - 1 && e >= NR * N1) break;
+        xp[xo[j]] = f(e, xo[j]);
       }
-      xp[xo[j]] = v;
+    };
+    if (kApply) {
+      if (A.first) each([&](int e, int) { return r0[e]; });
+      else each([&](int e, int) { return fmaf(beta, r1[e], r0[e]); });
+    } else if (MODE == SL_PREU) {
+      each([&](int e, int) { return omega * fmaf(-alpha, r1[e], r0[e]) * r2[e]; });
+    } else if (kPost) {  // coarse correction: one interpolated coarse plane (m even) or the mean of two
+      if (m & 1) each([&](int e, int x) { return fmaf(omega * r0[e], r1[e], 0.5f * (e0[x] + e1[x])); });
+      else each([&](int e, int x) { return fmaf(omega * r0[e], r1[e], e0[x]); });
+    } else {
+      each([&](int e, int) { return omega * r0[e] * r1[e]; });
     }
   };
 
@@ -288,11 +310,11 @@ __global__ void __launch_bounds__(256, 3) k_slab(SlabArgs A) {
     asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
   }
   __syncthreads();
-  // planes first .. first+kAhead fill the fresh slots; iteration k then refills the slot
-  // of plane k-1 with plane k+kAhead (raw k-1 was last read by compute(k-1), its cells
-  // by compute(k))
+  // planes first .. first+2 now, first+3 once the prologue has derived plane first
+  // (whose D^-1 slot it may reuse); iteration k then copies plane k+3 into the slots of
+  // plane k-1 (raw k-1 was last read by compute(k-1), its cells by compute(k))
   if (tid == 0)
-    for (int m = first; m <= min(first + kAhead, kend + 1); ++m) issue(m, kPost && m == first);
+    for (int m = first; m <= min(first + kAhead - 1, kend + 1); ++m) issue(m, kPost && m == first);
   wait_plane(first);
   if (kPost) {
     interp(first >> 1);
@@ -303,6 +325,7 @@ __global__ void __launch_bounds__(256, 3) k_slab(SlabArgs A) {
   wait_plane(kbeg);
   derive(kbeg, false);
   __syncthreads();
+  if (tid == 0 && !dead && first + kAhead <= kend + 1) issue(first + kAhead, false);
 
   // ---- this thread's nodes: x = 1 + RX lane + i, rows y = y0 + RY warp + t
   const int ly0 = RY * warp;                // staged row of the window's first row
@@ -342,9 +365,15 @@ __global__ void __launch_bounds__(256, 3) k_slab(SlabArgs A) {
       for (int r = 0; r < 2; ++r) {
         const TA* cp = cs + ((k - 1 + r - first) % kRing) * (L::cellb / sizeof(TA)) + cwin;
 #pragma unroll
-        for (int cr = 0; cr < RY + 1; ++cr)
+        for (int cr = 0; cr < RY + 1; ++cr) {
+          if constexpr (RX == 2) {  // cells xw, xw+1 as one aligned pair (xw and N even), then xw+2
+            ld_cell_pair(cp + cr * N, C[r][0][cr], C[r][1][cr]);
+            C[r][2][cr] = ld_cell(cp, cr * N + 2);
+          } else {
 #pragma unroll
-          for (int cc = 0; cc < RX + 1; ++cc) C[r][cc][cr] = ld_cell(cp, cr * N + cc);
+            for (int cc = 0; cc < RX + 1; ++cc) C[r][cc][cr] = ld_cell(cp, cr * N + cc);
+          }
+        }
       }
       // the operator plane by plane (k-1, k, k+1): one window of (RX+2) x (RY+2) operand
       // values live at a time; node (i, t) has cells c[p][q][r] = C[r][i + p][t + q] and
@@ -405,9 +434,9 @@ __global__ void __launch_bounds__(256, 3) k_slab(SlabArgs A) {
           }
       }
       const int dl = delta_of(k);
-      const int slot = (k - first) % kRing;
-      const float* o0 = raw + (0 * kRing + slot) * G::RAWF + dl + own0;
-      const float* o1 = raw + (1 * kRing + slot) * G::RAWF + dl + own0;
+      const int jk = k - first;
+      const float* o0 = raw + (L::first_slot(0) + jk % L::slots(0)) * G::RAWF + dl + own0;
+      const float* o1 = raw + (L::first_slot(1) + jk % L::slots(1)) * G::RAWF + dl + own0;
 #pragma unroll
       for (int t = 0; t < RY; ++t) {
 #pragma unroll
