@@ -31,7 +31,7 @@ METRIC = "sample-gradients/s (state+adjoint) at rtol 1e-8 vs plain FP64; p99 lat
 # traffic is this ratio times its algorithmic bytes (ncu on the 64^3 slab launches of a
 # 256-sample batch, profiles/slab_passes_c3_ncu.md).  Only valid for the kernel as
 # captured: emptied with each change of that kernel until it is captured again.
-TRAFFIC_RATIO = {"apply_f32": 1.001, "pre_f32": 1.025, "post_f32": 1.017}
+TRAFFIC_RATIO = {}
 UNIT = "sample-gradients/s"
 
 
@@ -423,7 +423,14 @@ def run_gpu(args, rank, world):
                 "gpu_launches": gpu_launches, "clocks": clocks, "fp64_path": fp64, "serving": serve,
                 "mixed_over_fp64": (value / fp64["value"]) if fp64 else None,
                 "kernel_shares": {k: round(v["total_ms"] / total_prof, 4) for k, v in
-                                  sorted(prof_all.items(), key=lambda kv: -kv[1]["total_ms"])[:8]}}
+                                  sorted(prof_all.items(), key=lambda kv: -kv[1]["total_ms"])[:8]},
+                # every class of the last warm-up step over 1% of it: algorithmic bytes per
+                # second of its launches (CUDA events around each launch) against the HBM peak
+                "kernel_roofline": {k: {"share": round(v["total_ms"] / total_prof, 4), "launches": v["launches"],
+                                        "gbs": round(v["bytes"] / (v["total_ms"] / 1e3) / 1e9, 1),
+                                        "frac": round(v["bytes"] / (v["total_ms"] / 1e3) / 1e9 / peaks["hbm_gbs"], 3)}
+                                    for k, v in sorted(prof_all.items(), key=lambda kv: -kv[1]["total_ms"])
+                                    if v["total_ms"] > 0.01 * total_prof and v["bytes"] > 0}}
         print(json.dumps(line), flush=True)
     ctx.close()
 

@@ -156,7 +156,7 @@ int tiled_phi(const double* y, int N, int S, const double* gtab, const double* m
 constexpr int kTiledMinN = 16;  // grids with at least this many cells per side use the tiled kernels
 
 // whole-row slab passes (slab.cu) for the mixed path's FP32 vectors on 32^3 and 64^3
-// grids; they need every staged node vector to hold zero boundary nodes
+// grids; boundary nodes of the staged vectors are taken as 0 whatever they hold
 bool slab_supported(int N);
 TiledShape slab_shape(int N, int S, int zchunks = 0);
 void slab_apply(const float* z, const float* pold, float* pnew, const float* a, float* q, float* x, double* partial,
@@ -167,6 +167,14 @@ void slab_pre(const float* r, const float* q, const TA* a, const float* dinv, fl
 template <typename TA>
 void slab_post(const float* r, const TA* a, const float* dinv, const float* ec, float* z, double* partial,
                const SolveScalars* sc, int N, const Batch& bt, double omega, cudaStream_t st);
+
+// the V-cycle from a coarse 16^3 level (j >= 1 of a grid with N cells) down to 2^3 in one
+// launch, one block per launched sample (coarse.cu): r16 the restricted residual, a the
+// coefficients of the levels 16^3 .. 2^3, z16 the correction
+bool coarse_vcycle_applies(int N, int j);
+template <typename T>
+void coarse_vcycle(const T* r16, const T* const a[4], T* z16, const SolveScalars* sc, const Batch& bt, double omega,
+                   cudaStream_t st);
 
 // tensor-core KL synthesis (kl_gemm.cu)
 size_t kl_gemm_b_bytes(int N, int K);

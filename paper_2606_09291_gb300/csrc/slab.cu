@@ -15,17 +15,20 @@
 //     4 floats); cell planes (rows y0-1 .. y0+TYT-1) and, for POST, the coarse
 //     correction's planes are copied the same way; an mbarrier per ring slot counts
 //     the bytes in;
-//   * every staged node vector has zero boundary nodes in memory (the solver clears
-//     them once per solve and the passes write interior nodes only), so the operand
-//     plane is derived branch-free for every staged entry;
+//   * the operand plane is derived branch-free for every staged entry, boundary nodes
+//     (and boundary values of the coarse correction) taken as 0 by a per-thread mask
+//     whatever the staged vectors hold there, so the passes need no cleared
+//     boundaries; they write the interior nodes and, branch-free, the nodes x = N and
+//     y = N of a lane's window (as 0), never x = 0, y = 0 or the planes 0 and N;
 //   * the derived operand plane has an even row stride N + 2, so a lane's window of
 //     RX + 2 columns is read with 8-byte loads when RX = 2.
 // Partial sums (APPLY p.q, POST r.z) are formed per segment of kZSeg interior planes
 // exactly as in tiled.cu (entry seg * by + tile_y per sample).
 //
 // Every wait on an mbarrier is bounded (about a second of SM clock); a wait that
-// runs out sets *err, and the thread then skips its remaining waits and memory work
-// but still reaches every block barrier, so the kernel ends and the host reads the
+// runs out sets *err, and the thread then skips its remaining waits and copies but
+// still reaches every block barrier (its shared-memory work stays in bounds whatever
+// the slots hold; its results are void), so the kernel ends and the host reads the
 // flag.
 #include <cstdio>
 
@@ -183,8 +186,8 @@ __global__ void __launch_bounds__(256, 3) k_slab(SlabArgs A) {
   float beta = 0.f, alpha = 0.f;
   if (kApply && !A.first) beta = (float)A.sc[s].beta;
   if (MODE == SL_APPLYX || MODE == SL_PREU) alpha = (float)A.sc[s].alpha;
-  const float* vin[3] = {A.in0, MODE == SL_PREU || kApply ? A.in1 : A.dinv, A.dinv};
-  bool dead = false;  // a wait of this thread ran out: skip the remaining work
+  auto vin = [&](int v) { return v == 0 ? A.in0 : (v == 1 && (MODE == SL_PREU || kApply) ? A.in1 : A.dinv); };
+  bool dead = false;  // a wait of this thread ran out: skip the remaining waits and copies
 
   // ---- producer (thread 0): plane m into ring slot (m - first) % kRing
   const int first = kbeg - 1;
@@ -204,28 +207,25 @@ __global__ void __launch_bounds__(256, 3) k_slab(SlabArgs A) {
     uint32_t total = nv * nb + cb;
     // POST: coarse plane m/2 + 1 with every even fine plane (interpolated in derive(m)),
     // plane (kbeg-1)/2 as well with the first plane of the chunk
-    int cplanes[2], nc = 0;
-    if (kPost) {
-      if (extra_coarse) cplanes[nc++] = m >> 1;
-      if (!(m & 1) && (m >> 1) + 1 <= G::NC) cplanes[nc++] = (m >> 1) + 1;
-    }
-    uint32_t cbytes[2] = {0u, 0u};
-    long long coff[2] = {0, 0};
-    for (int q = 0; q < nc; ++q) {
-      coff[q] = (long long)s * kCNodes + (long long)cplanes[q] * G::NC1 * G::NC1 + (long long)cy0 * G::NC1;
-      int dc;
-      cbytes[q] = span(coff[q], crows_c * G::NC1, dc);
-      total += cbytes[q];
-    }
+    const bool c0 = kPost && extra_coarse, c1 = kPost && !(m & 1) && (m >> 1) + 1 <= G::NC;
+    const long long cbase = (long long)s * kCNodes + (long long)cy0 * G::NC1;
+    const long long coff0 = cbase + (long long)(m >> 1) * G::NC1 * G::NC1;
+    const long long coff1 = coff0 + (long long)G::NC1 * G::NC1;
+    int dc;
+    const uint32_t cb0 = c0 ? span(coff0, crows_c * G::NC1, dc) : 0u;  // spans differ with the offset mod 4
+    const uint32_t cb1 = c1 ? span(coff1, crows_c * G::NC1, dc) : 0u;
+    total += cb0 + cb1;
     mbar_expect(bar, total);
-    for (int v = 0; v < nv; ++v)
-      bulk_copy(smem_u32(raw + (L::first_slot(v) + j % L::slots(v)) * G::RAWF), vin[v] + (noff & ~3LL), nb, bar);
+#pragma unroll
+    for (int v = 0; v < NV; ++v)
+      if (v < nv)
+        bulk_copy(smem_u32(raw + (L::first_slot(v) + j % L::slots(v)) * G::RAWF), vin(v) + (noff & ~3LL), nb, bar);
     if (cell) {
       const long long coff_c = (long long)s * kCells + (long long)m * N * N + (long long)(y0 - 1) * N;
       bulk_copy(smem_u32((unsigned char*)cs + slot * L::cellb), (const TA*)A.a + coff_c, cb, bar);
     }
-    for (int q = 0; q < nc; ++q)
-      bulk_copy(smem_u32(craw + (cplanes[q] % 3) * G::CRAWF), A.ec + (coff[q] & ~3LL), cbytes[q], bar);
+    if (c0) bulk_copy(smem_u32(craw + ((m >> 1) % 3) * G::CRAWF), A.ec + (coff0 & ~3LL), cb0, bar);
+    if (c1) bulk_copy(smem_u32(craw + (((m >> 1) + 1) % 3) * G::CRAWF), A.ec + (coff1 & ~3LL), cb1, bar);
   };
   auto wait_plane = [&](int m) {
     const int j = m - first;
@@ -238,56 +238,85 @@ __global__ void __launch_bounds__(256, 3) k_slab(SlabArgs A) {
   auto delta_of = [&](int m) { return (s + m + y0 - 1) & 3; };
 
   // ---- entries this thread derives: e = tid + 256 j, operand index e + e / N1 (stride N + 2)
+  // bnd bit j: entry j is a boundary node (x or y on the boundary; the planes 0 and N
+  // are handled per plane), derived as 0 whatever the staged vector holds there
   int xo[G::NE];
+  unsigned bnd = 0;
 #pragma unroll
   for (int j = 0; j < G::NE; ++j) {
     const int e = tid + 256 * j;
-    xo[j] = e + e / N1;
+    const int ly = e / N1, x = e - ly * N1, y = y0 - 1 + ly;
+    xo[j] = e + ly;
+    if (x == 0 || x == N || y == 0 || y >= N) bnd |= 1u << j;
+  }
+  // the same for the coarse interpolation items (a, b): bit 4j + (p + 2q) for coarse
+  // node (a + p, cy0 + b + q) on the coarse boundary
+  unsigned cbnd = 0;
+  if (kPost) {
+#pragma unroll
+    for (int j = 0; j < G::NI; ++j) {
+      const int it = tid + 256 * j;
+      const int a = it % G::NC1, b = it / G::NC1;
+#pragma unroll
+      for (int q = 0; q < 2; ++q)
+#pragma unroll
+        for (int p = 0; p < 2; ++p) {
+          const int ca = a + p, cb = cy0 + b + q;
+          if (ca == 0 || ca >= G::NC || cb == 0 || cb >= G::NC) cbnd |= 1u << (4 * j + p + 2 * q);
+        }
+    }
   }
 
   // POST: interpolate staged coarse plane c (xy-bilinear) into eps[c & 1]: item
   // (a, b) of the coarse tile writes fine nodes (2a + p, 2b + q)
+  // (coarse boundary values are taken as 0 whatever the staged vector holds there)
+  // Every load stays inside the staged slot (its last item a = NC reads one value past
+  // the row, still inside the slot), and the item a = NC writes column N + 1 of the
+  // row, the padding of the even row stride; only items past the tile are skipped.
   auto interp = [&](int c) {
-    if (dead) return;
     const float* cp = craw + (c % 3) * G::CRAWF + ((s + c + cy0) & 3);
     float* ed = eps + (c & 1) * G::XPL;
+    const unsigned all = (c == 0 || c == G::NC) ? ~0u : cbnd;
 #pragma unroll
     for (int j = 0; j < G::NI; ++j) {
       const int it = tid + 256 * j;
-      if (it >= G::NC1 * (G::CNR - 1)) break;
+      if (j == G::NI - 1 && it >= G::NC1 * (G::CNR - 1)) break;
       const int a = it % G::NC1, b = it / G::NC1;
       const float* q = cp + a + G::NC1 * b;
-      const float e00 = q[0], e01 = q[G::NC1];
+      const unsigned mk = all >> (4 * j);
+      const float e00 = (mk & 1u) ? 0.f : q[0], e10 = (mk & 2u) ? 0.f : q[1];
+      const float e01 = (mk & 4u) ? 0.f : q[G::NC1], e11 = (mk & 8u) ? 0.f : q[G::NC1 + 1];
       float* o = ed + 2 * a + XS * (2 * b);
+      const float r0 = 0.5f * (e00 + e10), r1 = 0.5f * (e01 + e11);
       o[0] = e00;
+      o[1] = r0;
       o[XS] = 0.5f * (e00 + e01);
-      if (a < G::NC) {
-        const float e10 = q[1], e11 = q[G::NC1 + 1];
-        const float r0 = 0.5f * (e00 + e10), r1 = 0.5f * (e01 + e11);
-        o[1] = r0;
-        o[XS + 1] = 0.5f * (r0 + r1);
-      }
+      o[XS + 1] = 0.5f * (r0 + r1);
     }
   };
 
-  // derive operand plane m (ring slot of m, operand slot m % 3)
-  auto derive = [&](int m, bool interp_next) {
-    if (dead) return;
-    const int jm = m - first;
-    const int dl = delta_of(m);
-    const float* r0 = raw + (L::first_slot(0) + jm % L::slots(0)) * G::RAWF + dl;
-    const float* r1 = raw + (L::first_slot(1) + jm % L::slots(1)) * G::RAWF + dl;
-    const float* r2 = raw + (L::first_slot(NV - 1) + jm % L::slots(NV - 1)) * G::RAWF + dl;
-    float* xp = xs + (m % 3) * G::XPL;
+  // derive operand plane m into operand slot x3 = m % 3 (j3 = (m - first) % 3: the
+  // slot of m in a 3-slot ring)
+  auto raw_of = [&](int v, int m, int j3) {
+    const int j = m - first;
+    return raw + (L::first_slot(v) + (L::slots(v) == kRing ? (j & (kRing - 1)) : j3)) * G::RAWF + delta_of(m);
+  };
+  auto derive = [&](int m, int x3, int j3, bool interp_next) {
+    const float* r0 = raw_of(0, m, j3);
+    const float* r1 = raw_of(1, m, j3);
+    const float* r2 = raw_of(NV - 1, m, j3);
+    float* xp = xs + x3 * G::XPL;
     if (kPost && interp_next && !(m & 1) && (m >> 1) + 1 <= G::NC) interp((m >> 1) + 1);
     const float* e0 = eps + ((m >> 1) & 1) * G::XPL;
     const float* e1 = eps + (((m + 1) >> 1) & 1) * G::XPL;
+    const unsigned mask = (m == 0 || m == N) ? ~0u : bnd;  // boundary entries of this plane
     auto each = [&](auto f) {
 #pragma unroll
       for (int j = 0; j < G::NE; ++j) {
         const int e = tid + 256 * j;
         if (j == G::NE - 1 && e >= NR * N1) break;
-        xp[xo[j]] = f(e, xo[j]);
+        const float v = f(e, xo[j]);
+        xp[xo[j]] = ((mask >> j) & 1u) ? 0.f : v;
       }
     };
     if (kApply) {
@@ -321,9 +350,12 @@ __global__ void __launch_bounds__(256, 3) k_slab(SlabArgs A) {
     interp((first >> 1) + 1);
     __syncthreads();
   }
-  derive(first, false);
+  // rotating slots of plane k: xk = k % 3 (operand ring), jk3 = (k - first) % 3
+  int xk = kbeg % 3, jk3 = 1;
+  const int xfirst3 = xk == 0 ? 2 : xk - 1;
+  derive(first, xfirst3, 0, false);
   wait_plane(kbeg);
-  derive(kbeg, false);
+  derive(kbeg, xk, 1, false);
   __syncthreads();
   if (tid == 0 && !dead && first + kAhead <= kend + 1) issue(first + kAhead, false);
 
@@ -335,35 +367,41 @@ __global__ void __launch_bounds__(256, 3) k_slab(SlabArgs A) {
   float* out0 = A.out0 + s * kNodes;
   float* out1 = (kApply || MODE == SL_PREU) ? A.out1 + s * kNodes : nullptr;
   float* xg = (MODE == SL_APPLYX) ? A.x + s * kNodes : nullptr;
-  bool xok[RX], yok[RY];
+  // bit t RX + i: node (i, t) is interior (the others, x = N or y = N, are written 0)
+  unsigned okb = 0;
 #pragma unroll
-  for (int i = 0; i < RX; ++i) xok[i] = xw + 1 + i <= N - 1;
+  for (int t = 0; t < RY; ++t)
 #pragma unroll
-  for (int t = 0; t < RY; ++t) yok[t] = y0 + ly0 + t <= N - 1;
+    for (int i = 0; i < RX; ++i)
+      if (xw + 1 + i <= N - 1 && y0 + ly0 + t <= N - 1) okb |= 1u << (t * RX + i);
+  const long long gown = (long long)(y0 + ly0) * N1 + xw + 1;  // node (i = 0, t = 0) of plane 0
   float red = 0.f;
 
   for (int k = kbeg; k <= kend; ++k) {
     // APPLYX: this plane's x of the thread's nodes, loaded before the waits so the
     // global latency overlaps the derive step
+    const long long gk = (long long)k * N1 * N1 + gown;
+    const int xkp = xk == 2 ? 0 : xk + 1, xkm = xk == 0 ? 2 : xk - 1;
+    const int jk3p = jk3 == 2 ? 0 : jk3 + 1;
     float xv[RY][RX];
     if (MODE == SL_APPLYX) {
 #pragma unroll
       for (int t = 0; t < RY; ++t)
 #pragma unroll
         for (int i = 0; i < RX; ++i)
-          xv[t][i] = (!A.xfirst && xok[i] && yok[t]) ? xg[k * N1 * N1 + (y0 + ly0 + t) * N1 + xw + 1 + i] : 0.f;
+          xv[t][i] = (!A.xfirst && ((okb >> (t * RX + i)) & 1u)) ? xg[gk + t * N1 + i] : 0.f;
     }
     if (k + 1 <= kend + 1) {
       wait_plane(k + 1);
-      derive(k + 1, true);
+      derive(k + 1, xkp, jk3p, true);
     }
     __syncthreads();
-    if (!dead) {
+    {
       // cells of the two cell planes around plane k: C[r][cc][cr], cell (xw + cc, row ly0 + cr)
       float C[2][RX + 1][RY + 1];
 #pragma unroll
       for (int r = 0; r < 2; ++r) {
-        const TA* cp = cs + ((k - 1 + r - first) % kRing) * (L::cellb / sizeof(TA)) + cwin;
+        const TA* cp = cs + ((k - 1 + r - first) & (kRing - 1)) * (L::cellb / sizeof(TA)) + cwin;
 #pragma unroll
         for (int cr = 0; cr < RY + 1; ++cr) {
           if constexpr (RX == 2) {  // cells xw, xw+1 as one aligned pair (xw and N even), then xw+2
@@ -382,7 +420,7 @@ __global__ void __launch_bounds__(256, 3) k_slab(SlabArgs A) {
 #pragma unroll
       for (int pl = 0; pl < 3; ++pl) {
         const int order = pl == 0 ? 1 : (pl == 1 ? 0 : 2);  // centre plane first
-        const float* xp = xs + ((k - 1 + order) % 3) * G::XPL + ly0 * XS + xw;
+        const float* xp = xs + (order == 0 ? xkm : (order == 1 ? xk : xkp)) * G::XPL + ly0 * XS + xw;
         float W[RX + 2][RY + 2];
 #pragma unroll
         for (int rr = 0; rr < RY + 2; ++rr) {
@@ -433,33 +471,34 @@ __global__ void __launch_bounds__(256, 3) k_slab(SlabArgs A) {
             }
           }
       }
-      const int dl = delta_of(k);
-      const int jk = k - first;
-      const float* o0 = raw + (L::first_slot(0) + jk % L::slots(0)) * G::RAWF + dl + own0;
-      const float* o1 = raw + (L::first_slot(1) + jk % L::slots(1)) * G::RAWF + dl + own0;
+      // every node of the window is written (nodes x = N or y = N with 0), so the
+      // stores and the partial sum are branch-free
+      const float* o0 = raw_of(0, k, jk3) + own0;
+      const float* o1 = raw_of(1, k, jk3) + own0;
 #pragma unroll
       for (int t = 0; t < RY; ++t) {
 #pragma unroll
         for (int i = 0; i < RX; ++i) {
+          const bool ok = (okb >> (t * RX + i)) & 1u;
           const float ax = scale * acc[t][i];
-          if (!(xok[i] && yok[t])) continue;
           const int own = t * N1 + i;
-          const int g = k * N1 * N1 + (y0 + ly0 + t) * N1 + xw + 1 + i;
+          const long long g = gk + t * N1 + i;
           if (kApply) {
-            const float pv = ctr[t][i];
-            out0[g] = ax;
+            const float pv = ctr[t][i];  // 0 off the interior (derived with the mask)
+            const float qv = ok ? ax : 0.f;
+            out0[g] = qv;
             out1[g] = pv;
-            red = fmaf(pv, ax, red);
-            if (MODE == SL_APPLYX) xg[g] = xv[t][i] + alpha * o1[own];
+            red = fmaf(pv, qv, red);
+            if (MODE == SL_APPLYX) xg[g] = ok ? xv[t][i] + alpha * o1[own] : 0.f;
           } else if (MODE == SL_PRE) {
-            out0[g] = o0[own] - ax;
+            out0[g] = ok ? o0[own] - ax : 0.f;
           } else if (MODE == SL_PREU) {
-            const float rn = fmaf(-alpha, o1[own], o0[own]);
-            out0[g] = rn - ax;
+            const float rn = ok ? fmaf(-alpha, o1[own], o0[own]) : 0.f;
+            out0[g] = ok ? rn - ax : 0.f;
             out1[g] = rn;
           } else {  // POST
-            const float rv = o0[own];
-            const float zv = ctr[t][i] + omega * (rv - ax) * o1[own];
+            const float rv = ok ? o0[own] : 0.f;
+            const float zv = ok ? ctr[t][i] + omega * (rv - ax) * o1[own] : 0.f;
             out0[g] = zv;
             red = fmaf(rv, zv, red);
           }
@@ -476,6 +515,8 @@ __global__ void __launch_bounds__(256, 3) k_slab(SlabArgs A) {
     }
     __syncthreads();
     if (tid == 0 && !dead && k + kAhead <= kend + 1) issue(k + kAhead, false);
+    xk = xkp;
+    jk3 = jk3p;
   }
   // the last copies of the chunk have been waited for (every issued plane is derived)
 }

@@ -234,10 +234,11 @@ __global__ void k_resid_smooth(const T* __restrict__ r, const T* __restrict__ x,
 }
 
 // coarse = P^T fine: weights 1, 1/2 per axis around (2I, 2J, 2K)
-template <typename T>
+template <typename T, int NCC = 0>
 __global__ void k_restrict(const T* __restrict__ tf, T* __restrict__ rc, const SolveScalars* __restrict__ sc,
-                           int Nc, const int* __restrict__ act) {
+                           int Nc_, const int* __restrict__ act) {
   SAMPLE_GUARD(sc);
+  const int Nc = NCC ? NCC : Nc_;  // a compile-time grid makes the index divisions multiplications
   const int n1c = Nc + 1, Nf = 2 * Nc, n1f = Nf + 1;
   const long long nc = (long long)n1c * n1c * n1c, nf = (long long)n1f * n1f * n1f;
   const int n = blockIdx.x * blockDim.x + threadIdx.x;
@@ -369,10 +370,11 @@ constexpr int kInitPer = 8;
 static inline int init_blocks(int N) { return (int)((nodes_of(N) + kBlock * kInitPer - 1) / (kBlock * kInitPer)); }
 // PAIR_B: b is already given as FP32 pairs (bp; nothing to split, b.b from the heads).
 // Boundary rows of b are taken as 0 whatever the buffer holds there.
-template <bool PAIR_B>
+template <bool PAIR_B, int NN = 0>
 __global__ void k_init32(const double* __restrict__ b, const float2* __restrict__ bp, long long bstride,
                          float* __restrict__ r32, float2* __restrict__ bdf, double* __restrict__ partial,
-                         long long nodes, int N) {
+                         long long nodes, int N_) {
+  const int N = NN ? NN : N_;
   const int s = blockIdx.y;
   const long long n0 = (long long)blockIdx.x * blockDim.x * kInitPer + threadIdx.x;
   const bool write_pair = bstride != 0 || s == 0;
@@ -412,9 +414,11 @@ __global__ void k_init32(const double* __restrict__ b, const float2* __restrict_
 // renormalisation, about 48 significant bits), d taken as 0 when never written.
 // The first step (assign) launches every sample and writes x = 0 for the samples that
 // take no step (b = 0, or a non-finite b), so every sample's solution is defined.
+template <int NN = 0>
 __global__ void k_finish_step(float2* __restrict__ x, const float* __restrict__ d, const float* __restrict__ p,
                               const SolveScalars* __restrict__ sci, const SolveScalars* __restrict__ sco,
-                              long long nodes, int N, int assign, int d_zero, const int* __restrict__ act) {
+                              long long nodes, int N_, int assign, int d_zero, const int* __restrict__ act) {
+  const int N = NN ? NN : N_;
   const int s = act != nullptr ? act[blockIdx.y] : (int)blockIdx.y;
   const bool on = sco[s].active != 0;
   if (!on && !assign) return;
@@ -461,6 +465,20 @@ __global__ void k_accumulate(double* __restrict__ x, const float* __restrict__ d
 
 // ---------------------------------------------------------------- host side
 static inline dim3 grid_nodes(int N, int S) { return dim3((unsigned)node_blocks(N), (unsigned)S); }
+
+// f(std::integral_constant<int, N>) for the grids of the hierarchies (N a power of two,
+// 16 .. 256), f(std::integral_constant<int, 0>) (N at run time) otherwise
+template <typename F>
+static void with_grid(int N, F&& f) {
+  switch (N) {
+    case 16: f(std::integral_constant<int, 16>()); break;
+    case 32: f(std::integral_constant<int, 32>()); break;
+    case 64: f(std::integral_constant<int, 64>()); break;
+    case 128: f(std::integral_constant<int, 128>()); break;
+    case 256: f(std::integral_constant<int, 256>()); break;
+    default: f(std::integral_constant<int, 0>()); break;
+  }
+}
 
 static size_t align_up(size_t v) { return (v + 255) & ~(size_t)255; }
 // bytes after every node vector: the slab passes copy 16-byte aligned spans that may
@@ -630,7 +648,13 @@ static int vcycle(SolverBufs& B, const T* r0, const TA0* a0, const SolveScalars*
   const bool tiled = B.N >= kTiledMinN && J >= 1;
   const T* rfine = fuse_q ? r_new : r0;  // residual the V-cycle works on after the fused update
   auto rin = [&](int j) { return j == 0 ? rfine : (const T*)B.vr[j]; };
-  for (int j = 0; j < J; ++j) {
+  // the levels from a coarse 16^3 level down to 2^3 run as one fused launch; jc is
+  // the first of them (J: none)
+  int jc = J;
+  if (tiled)
+    for (int j = 1; j < J; ++j)
+      if (coarse_vcycle_applies(B.N, j) && J - j == 3) jc = j;
+  for (int j = 0; j < jc; ++j) {
     const int Nj = B.N >> j;
     const bool fine = j == 0;
     if (fine && tiled && fuse_q) {
@@ -652,16 +676,24 @@ static int vcycle(SolverBufs& B, const T* r0, const TA0* a0, const SolveScalars*
       launch(cls<T>("resid", false), nbytes<T, T>(Nj, n, 3, 1), k_resid_smooth<T, T, 0>, grid_nodes(Nj, n), kBlock, 0,
              st, rin(j), (const T*)B.vx[j], aj, (T*)B.vt[j], sc, Nj, omega, act);
     }
-    launch(cls<T>("restrict", fine), nbytes<T, T>(Nj, n, 1, 0) + nbytes<T, T>(Nj / 2, n, 1, 0), k_restrict<T>,
-           grid_nodes(Nj / 2, n), kBlock, 0, st, (const T*)B.vt[j], (T*)B.vr[j + 1], sc, Nj / 2, act);
+    with_grid(Nj / 2, [&](auto c) {
+      launch(cls<T>("restrict", fine), nbytes<T, T>(Nj, n, 1, 0) + nbytes<T, T>(Nj / 2, n, 1, 0),
+             k_restrict<T, decltype(c)::value>, grid_nodes(Nj / 2, n), kBlock, 0, st, (const T*)B.vt[j],
+             (T*)B.vr[j + 1], sc, Nj / 2, act);
+    });
   }
-  if (J == 0)
+  if (jc < J) {
+    const T* const al[4] = {(const T*)B.acoef[jc], (const T*)B.acoef[jc + 1], (const T*)B.acoef[jc + 2],
+                            (const T*)B.acoef[jc + 3]};
+    coarse_vcycle<T>(rin(jc), al, (T*)B.vt[jc], sc, bt, (double)omega, st);
+  } else if (J == 0) {
     launch("coarsest", 0.0, k_coarsest<T, TA0>, dim3((n + 127) / 128), 128, 0, st, rin(0), a0, (T*)B.vt[0], sc, n,
            act);
-  else
+  } else {
     launch("coarsest", 0.0, k_coarsest<T, T>, dim3((n + 127) / 128), 128, 0, st, rin(J), (const T*)B.acoef[J],
            (T*)B.vt[J], sc, n, act);
-  for (int j = J - 1; j >= 0; --j) {
+  }
+  for (int j = jc - 1; j >= 0; --j) {
     const int Nj = B.N >> j;
     const bool fine = j == 0;
     if (fine && tiled) {
@@ -820,9 +852,12 @@ static cudaError_t pcg_inner_fused(SolverBufs& B, const float* a32, const __nv_b
     pc ^= 1;
     scalar(B, sc, SM_ALPHA, 0, 0, st, napply);
     if (it == iters - 1) {
-      launch("finish_step", (double)n * nodes * ((iters > 1 ? 4 : 0) + 4 + (assign_out ? 8 : 16)), k_finish_step,
-             grid_nodes(N, n), kBlock, 0, st, x_out, (const float*)x, (const float*)pnew, (const SolveScalars*)sc,
-             sco, nodes, N, assign_out ? 1 : 0, iters > 1 ? 0 : 1, B.actp);
+      with_grid(N, [&](auto c) {
+        launch("finish_step", (double)n * nodes * ((iters > 1 ? 4 : 0) + 4 + (assign_out ? 8 : 16)),
+               k_finish_step<decltype(c)::value>, grid_nodes(N, n), kBlock, 0, st, x_out, (const float*)x,
+               (const float*)pnew, (const SolveScalars*)sc, sco, nodes, N, assign_out ? 1 : 0, iters > 1 ? 0 : 1,
+               B.actp);
+      });
       break;
     }
     nrz = vcycle<float, __nv_bfloat16>(B, rb[rc], abf, sc, omega, st, q, rb[rc ^ 1]);
@@ -871,29 +906,15 @@ static void zero_boundary(void* const* bufs, int nv, int N, int S, cudaStream_t 
          dim3((unsigned)((nb + kBlock - 1) / kBlock), (unsigned)S), kBlock, 0, st, zl, nv, N);
 }
 
-// The tiled passes write interior nodes only: the vectors they produce (and the
+// The FP64 tiled passes write interior nodes only: the vectors they produce (and the
 // inner solve's correction, which is first assigned by a tiled pass) get zero
 // boundary nodes once per solve.
-// The mixed path needs none of this: its tiled passes zero-fill boundary nodes when
-// staging, and the kernels that read whole vectors (the refinement's init and
-// accumulation) take the boundary as 0 themselves.
-// The mixed path's z-marching passes zero-fill boundary nodes when staging and need
-// none of this; its slab passes (32^3, 64^3 grids) copy whole rows, boundary nodes
-// included, so the vectors they read get zero boundaries here: p (both buffers), q,
-// z and the second residual on the fine level, the V-cycle outputs on the coarse
-// levels (the other inputs, r, D^-1 and the restricted residuals, are written with
-// zero boundaries by their producers).
+// The mixed path needs none of this: its z-marching passes zero-fill boundary nodes
+// when staging, its slab passes take them as 0 when deriving the operand plane and
+// interpolating the coarse correction, and the kernels that read whole vectors (the
+// refinement's init and accumulation) take the boundary as 0 themselves.
 static cudaError_t clear_tiled(SolverBufs& B, int elem, cudaStream_t st) {
-  if (!(B.N >= kTiledMinN && B.J >= 1)) return cudaSuccess;
-  if (elem == 4) {
-    if (uses_slab(B, B.N, 4)) {
-      void* bufs[5] = {B.p, B.vx[0], B.q, B.vt[0], B.r2};
-      zero_boundary<float>(bufs, 5, B.N, B.S, st);
-    }
-    for (int j = 1; j < B.J; ++j)
-      if ((B.N >> j) >= kTiledMinN) zero_boundary<float>(&B.vt[j], 1, B.N >> j, B.S, st);
-    return cudaGetLastError();
-  }
+  if (!(B.N >= kTiledMinN && B.J >= 1) || elem == 4) return cudaSuccess;
   void* bufs[5] = {B.p, B.vx[0], B.q, B.vt[0], B.r2};
   zero_boundary<double>(bufs, 5, B.N, B.S, st);
   for (int j = 1; j < B.J; ++j)  // coarse levels run by the tiled passes
@@ -941,12 +962,15 @@ cudaError_t ir_mixed(SolverBufs& B, const float* a32, const __nv_bfloat16* abf, 
   const float2* bdf = b_pair ? b_pair : B.bdf;
   if (tiled) {
     const dim3 gi((unsigned)init_blocks(N), (unsigned)S);
-    if (b_pair)
-      launch("init_f32", bb + nbytes<float, float>(N, S, 1, 0), k_init32<true>, gi, kBlock, 0, st, b, b_pair,
-             bstride, r32, B.bdf, B.partial, nodes, N);
-    else
-      launch("init_f32", bb + nbytes<float, float>(N, S, 1, 0) + (double)(bstride ? S : 1) * nodes * 8,
-             k_init32<false>, gi, kBlock, 0, st, b, b_pair, bstride, r32, B.bdf, B.partial, nodes, N);
+    with_grid(N, [&](auto c) {
+      constexpr int NN = decltype(c)::value;
+      if (b_pair)
+        launch("init_f32", bb + nbytes<float, float>(N, S, 1, 0), k_init32<true, NN>, gi, kBlock, 0, st, b, b_pair,
+               bstride, r32, B.bdf, B.partial, nodes, N);
+      else
+        launch("init_f32", bb + nbytes<float, float>(N, S, 1, 0) + (double)(bstride ? S : 1) * nodes * 8,
+               k_init32<false, NN>, gi, kBlock, 0, st, b, b_pair, bstride, r32, B.bdf, B.partial, nodes, N);
+    });
     scalar(B, sco, SM_INIT, 0, 0, st, init_blocks(N));
   } else {
     launch("init_f64", bb + nbytes<double, double>(N, S, 2, 0), k_init<double>, g(), kBlock, 0, st, b, bstride, r64,

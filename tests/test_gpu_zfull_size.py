@@ -71,13 +71,17 @@ def test_timed_call_matches_oracle_record(lib):
     assert h["count"] == S and h["noconv"] == 0
     theta = cfg["theta"]
     fg, fo = np.exp(theta * h["shift"]), np.exp(theta * float(ref["shift"]))
-    assert abs(h["shift"] - float(ref["shift"])) <= TOLMIX * abs(float(ref["shift"]))
-    assert rel_err(field * fg, ref["mean_x"] * fo) <= TOLMIX
     my = float(ref["mean_y"]) * fo
-    assert abs(h["mean_dy"] * fg - my) <= TOLMIX * abs(my)
+    err = {"shift": abs(h["shift"] - float(ref["shift"])) / abs(float(ref["shift"])),
+           "mean_dx": rel_err(field * fg, ref["mean_x"] * fo),
+           "mean_dy": abs(h["mean_dy"] * fg - my) / abs(my)}
     for k_gpu, k_ref in (("s2_dx", "s2_x"), ("s2_dy", "s2_y")):
         r = float(ref[k_ref]) * fo ** 2
-        assert abs(h[k_gpu] * fg ** 2 - r) <= TOLMIX * r, (k_gpu, h[k_gpu] * fg ** 2, r)
+        err[k_gpu] = abs(h[k_gpu] * fg ** 2 - r) / r
+    print("measured relative error per result (4096-sample timed call vs oracle):",
+          {k: "%.2e" % v for k, v in err.items()})
+    for k, v in err.items():
+        assert v <= TOLMIX, (k, v)
 
 
 def oracle_workload():
@@ -124,6 +128,7 @@ def test_full_batch_solve_on_sampled_samples(lib):
     b = W.rhs_state(z, LEVEL)
     ref_xi = philox.normals(W.seed, 0, LEVEL, np.array(SAMPLED), K)
     assert np.abs(xs - ref_xi).max() <= 4e-15 * np.abs(ref_xi).max()
+    err = {"y": 0.0, "q": 0.0, "phi": 0.0, "res_y/rtol": 0.0, "res_q/rtol": 0.0}
     for k, m in enumerate(SAMPLED):
         assert rel_err(las[k], W.log_a(ref_xi[k][None], LEVEL)[0]) <= 1e-12
         # the operator the mixed path solves with: the coefficient rounded to FP32
@@ -138,9 +143,13 @@ def test_full_batch_solve_on_sampled_samples(lib):
         assert np.linalg.norm(rq) <= 1.05 * RTOL * np.linalg.norm(Me[I])
         # against the oracle's own solutions (FP64 coefficient, rtol 1e-12)
         ref = W.solve_state_adjoint(las[k], z, LEVEL)
-        assert rel_err(ys[k], ref["y"]) <= TOLMIX
-        assert rel_err(qs[k], ref["q"]) <= TOLMIX
-        assert abs(phis[k] - ref["phi"]) <= TOLMIX * abs(ref["phi"])
+        e_k = {"y": rel_err(ys[k], ref["y"]), "q": rel_err(qs[k], ref["q"]),
+               "phi": abs(phis[k] - ref["phi"]) / abs(ref["phi"]),
+               "res_y/rtol": np.linalg.norm(ry) / (RTOL * np.linalg.norm(b[I])),
+               "res_q/rtol": np.linalg.norm(rq) / (RTOL * np.linalg.norm(Me[I]))}
+        err = {key: max(err[key], v) for key, v in e_k.items()}
+        assert e_k["y"] <= TOLMIX and e_k["q"] <= TOLMIX and e_k["phi"] <= TOLMIX
+    print("measured error per result over the sampled samples (max):", {k: "%.2e" % v for k, v in err.items()})
 
 
 def test_full_batch_record_equals_merged_halves(lib):
