@@ -31,7 +31,12 @@ METRIC = "sample-gradients/s (state+adjoint) at rtol 1e-8 vs plain FP64; p99 lat
 # traffic is this ratio times its algorithmic bytes (ncu on the 64^3 slab launches of a
 # 256-sample batch, profiles/slab_passes_c3_ncu.md).  Only valid for the kernel as
 # captured: emptied with each change of that kernel until it is captured again.
-TRAFFIC_RATIO = {}
+TRAFFIC_RATIO = {"apply_f32": 0.996, "pre_f32": 1.023, "post_f32": 1.018}
+# ALU-bound classes: the operations their launch sites count, against the issue rate of
+# the units that execute them (152 SMs at 2070 MHz: 128 FP32 lanes per SM; FP64 at the
+# nominal 1.25 TFLOP/s, i.e. 0.625 T operations/s)
+ALU_PEAK = {"resid64": (152 * 128 * 2.07e9 / 1e12, "T FP32 ops/s", "FP32 lanes x max SM clock"),
+            "level_field": (0.625, "T FP64 ops/s", "nominal FP64 rate")}
 UNIT = "sample-gradients/s"
 
 
@@ -359,10 +364,11 @@ def run_gpu(args, rank, world):
     roof = None
     if prof and prof["launches"] > 0:
         per_launch_ms = prof["total_ms"] / prof["launches"]
-        if dominant in ("resid64", "apply_f64", "smooth_f64", "resid_f64", "jacobi0_f64") and prof["flops"] > 0:
+        if dominant in ALU_PEAK and prof["flops"] > 0:
+            peak, unit, kind = ALU_PEAK[dominant]
             ach = prof["flops"] / (prof["total_ms"] / 1e3) / 1e12
-            roof = {"bound": "alu", "achieved": ach, "peak": 1.25, "unit": "TFLOP/s", "frac": ach / 1.25,
-                    "traffic": None, "kernel": dominant, "peak_kind": "nominal FP64 dense"}
+            roof = {"bound": "alu", "achieved": ach, "peak": peak, "unit": unit, "frac": ach / peak,
+                    "traffic": None, "kernel": dominant, "peak_kind": kind}
         else:
             ach = prof["bytes"] / (prof["total_ms"] / 1e3) / 1e9
             roof = {"bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
@@ -426,9 +432,15 @@ def run_gpu(args, rank, world):
                                   sorted(prof_all.items(), key=lambda kv: -kv[1]["total_ms"])[:8]},
                 # every class of the last warm-up step over 1% of it: algorithmic bytes per
                 # second of its launches (CUDA events around each launch) against the HBM peak
-                "kernel_roofline": {k: {"share": round(v["total_ms"] / total_prof, 4), "launches": v["launches"],
-                                        "gbs": round(v["bytes"] / (v["total_ms"] / 1e3) / 1e9, 1),
-                                        "frac": round(v["bytes"] / (v["total_ms"] / 1e3) / 1e9 / peaks["hbm_gbs"], 3)}
+                "kernel_roofline": {k: dict({"share": round(v["total_ms"] / total_prof, 4), "launches": v["launches"],
+                                             "gbs": round(v["bytes"] / (v["total_ms"] / 1e3) / 1e9, 1),
+                                             "frac": round(v["bytes"] / (v["total_ms"] / 1e3) / 1e9 /
+                                                           peaks["hbm_gbs"], 3)},
+                                            **({"alu": {"achieved": round(v["flops"] / (v["total_ms"] / 1e3) / 1e12, 3),
+                                                        "peak": round(ALU_PEAK[k][0], 3), "unit": ALU_PEAK[k][1],
+                                                        "frac": round(v["flops"] / (v["total_ms"] / 1e3) / 1e12 /
+                                                                      ALU_PEAK[k][0], 3)}}
+                                               if k in ALU_PEAK and v["flops"] > 0 else {}))
                                     for k, v in sorted(prof_all.items(), key=lambda kv: -kv[1]["total_ms"])
                                     if v["total_ms"] > 0.01 * total_prof and v["bytes"] > 0}}
         print(json.dumps(line), flush=True)

@@ -105,7 +105,7 @@ size_t level_bytes(const mlsgd_ctx* ctx, int level, int S) {
   b += 2 * al((size_t)2 * S * 4);
   b += al(kl_gemm_a_bytes(S, ctx->cfg.n_modes));
   b += solve_scratch_bytes(ctx, N, S);
-  b += al((4 + 2 * (size_t)S) * 8) + al((size_t)level_partial_cap(ctx->Nc(), N) * 8);
+  b += al((4 + 4 * (size_t)S) * 8) + al((size_t)level_partial_cap(ctx->Nc(), N) * 8);
   b += al(2 * (size_t)nodes_of(N) * 8);
   return b;
 }
@@ -199,8 +199,8 @@ mlsgd_status solve_grid(mlsgd_ctx* ctx, int N, int S, const GridFields& f, const
   double* ytmp = y ? y : bp.take<double>(S * nodes);
   PcgParams prm{ctx->cfg.rtol, ctx->cfg.max_iter, ctx->cfg.omega > 0 ? ctx->cfg.omega : 0.6, 4};
   const int inner = ctx->cfg.inner_iters > 0 ? ctx->cfg.inner_iters : 6;
-  if (ctx->mixed()) build_hierarchy_mixed(B, f.abf, st);
-  else build_hierarchy_fp64(B, f.a64, st);
+  if (ctx->mixed()) build_hierarchy_mixed(B, f.abf, prm.omega, st);
+  else build_hierarchy_fp64(B, f.a64, prm.omega, st);
   launch_rhs_state(z, ctx->Nc(), N, b, st);
   const int fixed = ctx->cfg.ir_steps > 0 ? ctx->cfg.ir_steps : 0;
   const bool pairs = want_pairs && ctx->mixed() && N >= kTiledMinN && B.J >= 1;
@@ -627,7 +627,7 @@ mlsgd_status mlsgd_level_gradient(mlsgd_ctx* ctx, int iter, int level, int64_t f
     int* iters = bp.take<int>(2 * (size_t)S);
     int* status = bp.take<int>(2 * (size_t)S);
     __nv_bfloat16* gemm_a = bp.take<__nv_bfloat16>((size_t)S * K);
-    double* work = bp.take<double>(4 + 2 * (size_t)S);
+    double* work = bp.take<double>(4 + 4 * (size_t)S);
     double* spartial = bp.take<double>((size_t)level_partial_cap(ctx->Nc(), N));
     double* lvl_nodes = bp.take<double>(2 * (size_t)nodes_of(N));
     char* scratch = bp.p;

@@ -179,7 +179,8 @@ void launch_phi_adjrhs(const double* y, int N, int S, double* badj, double* phi,
 
 // ---------------------------------------------------------------- level statistics
 // work layout: [0] shift_new, [1] scale_old = exp(theta (shift_old - shift_new)),
-// [2] n_old, [3] n_batch, [4..4+S) w_fine, [4+S..4+2S) w_coarse.
+// [2] n_old, [3] n_batch, [4..4+S) w_fine, [4+S..4+2S) w_coarse, then the same
+// weights as FP32 (hi, lo) pairs (8 bytes each): [4+2S..4+3S) fine, [4+3S..4+4S) coarse.
 //
 // Single block: shift, per-sample weights Y~ = exp(theta (Phi - shift)), and
 // the scalar statistics of dY~ = Y~_l - Y~_{l-1} (Welford over the batch,
@@ -211,10 +212,15 @@ __global__ void k_level_scalars(const double* __restrict__ phif, const double* _
   const double shift = work[0];
   // a sample whose solve went non-finite (status bit 1) gets NaN weights, so the
   // record, and the step that reads it, report the failure instead of using it
+  float2* wpair = (float2*)(work + 4 + 2 * S);
   for (int s = threadIdx.x; s < S; s += blockDim.x) {
     const bool bad = status != nullptr && ((status[s] | (phic ? status[S + s] : 0)) & 2);
-    work[4 + s] = bad ? NAN : exp(theta * (phif[s] - shift));
-    work[4 + S + s] = bad ? NAN : (phic ? exp(theta * (phic[s] - shift)) : 0.0);
+    const double wf = bad ? NAN : exp(theta * (phif[s] - shift));
+    const double wc = bad ? NAN : (phic ? exp(theta * (phic[s] - shift)) : 0.0);
+    work[4 + s] = wf;
+    work[4 + S + s] = wc;
+    wpair[s] = df_split(wf);
+    wpair[S + s] = df_split(wc);
   }
   __syncthreads();
   // batch mean and M2 of dY~ by shifted sums over the block (deviations from the
@@ -374,19 +380,26 @@ __device__ DF eval_at_ctrl(const float2* __restrict__ q, int N, int Nc, int cx, 
 // the rescaled old mean; block partials of h_c^3 (M2_batch + delta^2 n_old S / n).
 // PF / PC: the fine / coarse adjoint solutions are FP32 (hi, lo) pairs (the mixed
 // path on tiled grids); their control-cell averages are then formed in pair
-// arithmetic (exact weights, about 48 significant bits, a function of the sample
-// alone).  The weighting, the cancelling difference w_f X_f - w_c X_c and its sums
-// are FP64 in every case (eq:delta-notation, eq:sec-order-sum): the only values
-// that depend on the batch (through the shift) are formed and accumulated in FP64,
-// so a record does not depend on how the samples were split into calls beyond
-// FP64 rounding.
+// arithmetic (exact weights, about 48 significant bits), and with both grids in
+// pairs so is the weighted difference w_f X_f - w_c X_c (weights rounded to pairs
+// from their FP64 values; error below 6 u^2 (|w_f X_f| + |w_c X_c|), u = 2^-24), a
+// function of the sample alone.  The sums of the cancelling differences, the
+// deviations from the first sample and the merge are FP64 in every case
+// (eq:delta-notation, eq:sec-order-sum), so a record does not depend on how the
+// samples were split into calls beyond FP64 rounding.  (This part has about 2 FP64
+// operations per FP32 one; GB300 issues FP64 at 1/58 of the FP32 rate, so the FP64
+// count sets the kernel's time.)
 __device__ __forceinline__ double ctrl_avg(const CellInterp& I, bool fast, const double* q, int N, int Nc, int cx,
                                            int cy, int cz) {
   return fast ? I.eval(q) : eval_at_ctrl(q, N, Nc, cx, cy, cz);
 }
+__device__ __forceinline__ DF ctrl_avg_df(const CellInterp& I, bool fast, const float2* q, int N, int Nc, int cx,
+                                          int cy, int cz) {
+  return fast ? I.eval(q) : eval_at_ctrl(q, N, Nc, cx, cy, cz);
+}
 __device__ __forceinline__ double ctrl_avg(const CellInterp& I, bool fast, const float2* q, int N, int Nc, int cx,
                                            int cy, int cz) {
-  return df_to_double(fast ? I.eval(q) : eval_at_ctrl(q, N, Nc, cx, cy, cz));
+  return df_to_double(ctrl_avg_df(I, fast, q, N, Nc, cx, cy, cz));
 }
 template <bool PF, bool PC>
 __global__ void k_level_field(const void* __restrict__ qf_, int Nf, const void* __restrict__ qc_, int Ncs, int S,
@@ -404,6 +417,8 @@ __global__ void k_level_field(const void* __restrict__ qf_, int Nf, const void* 
     const long long nf = nodes_of(Nf), ncn = qc ? nodes_of(Ncs) : 0;
     const double* wf = work + 4;
     const double* wc = work + 4 + S;
+    const float2* wfp = (const float2*)(work + 4 + 2 * S);
+    const float2* wcp = wfp + S;
     // level grids no finer than the control grid: weights hoisted out of the sample loop
     const bool fast_f = Nf <= Nc, fast_c = !qc || Ncs <= Nc;
     CellInterp If{}, Ic{};
@@ -411,8 +426,15 @@ __global__ void k_level_field(const void* __restrict__ qf_, int Nf, const void* 
     if (qc && fast_c) Ic.setup(Ncs, Nc, cx, cy, cz);
     double ref = 0.0, sd = 0.0, sd2 = 0.0;
     for (int s = 0; s < S; ++s) {
-      double v = wf[s] * ctrl_avg(If, fast_f, qf + s * nf, Nf, Nc, cx, cy, cz);
-      if (qc) v = fma(-wc[s], ctrl_avg(Ic, fast_c, qc + s * ncn, Ncs, Nc, cx, cy, cz), v);
+      double v;
+      if constexpr (PF && PC) {
+        const DF vf = df_mul(df_make(wfp[s]), ctrl_avg_df(If, fast_f, qf + s * nf, Nf, Nc, cx, cy, cz));
+        const DF vc = df_mul(df_make(wcp[s]), ctrl_avg_df(Ic, fast_c, qc + s * ncn, Ncs, Nc, cx, cy, cz));
+        v = df_to_double(df_add(vf, df_neg(vc)));
+      } else {
+        v = wf[s] * ctrl_avg(If, fast_f, qf + s * nf, Nf, Nc, cx, cy, cz);
+        if (qc) v = fma(-wc[s], ctrl_avg(Ic, fast_c, qc + s * ncn, Ncs, Nc, cx, cy, cz), v);
+      }
       if (s == 0) ref = v;
       const double d = v - ref;
       sd += d;
@@ -672,8 +694,12 @@ void launch_level_stats(const double* qf, const double* phif, int Nf, const doub
   // pairs on the coarse grid only come with pairs on the fine grid (it is at least as large)
   auto lf = qf_pairs ? (qc_pairs ? k_level_field<true, true> : k_level_field<true, false>)
                      : k_level_field<false, false>;
-  launch("level_field", qbytes + (double)ncell * 16, lf, dim3(nblk), kBlock, 0, st, (const void*)qf, Nf,
-         (const void*)qc, Ncoarse, S, Nc, (const double*)work, field, partial);
+  // FP64 operations per control cell and sample: both grids in pairs, the pair value
+  // to FP64 (2 conversions, 1 add), its deviation and the two sums; otherwise also the
+  // FP64 weighting and, for FP64 fields, the 8-node averages
+  const double f64ops = qf_pairs && qc_pairs ? 6.0 : (qf_pairs ? 16.0 : 21.0);
+  launch_flops("level_field", qbytes + (double)ncell * 16, (double)S * ncell * f64ops, lf, dim3(nblk), kBlock, 0, st,
+               (const void*)qf, Nf, (const void*)qc, Ncoarse, S, Nc, (const double*)work, field, partial);
   launch("level_finish", 0.0, k_level_finish, dim3(1), 32, 0, st, (const double*)partial, nblk, (const double*)work,
          scalars);
 }

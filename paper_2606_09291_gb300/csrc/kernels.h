@@ -118,8 +118,9 @@ cudaError_t ir_mixed(SolverBufs& B, const float* a32, const __nv_bfloat16* abf, 
                      long long bstride, double* x_out, double* r64, const PcgParams& prm, int inner_iters,
                      cudaStream_t st, int fixed_steps = 0, const float2* b_pair = nullptr, bool pair_out = false);
 // coefficient hierarchy for the V-cycle from the level-0 coefficient
-void build_hierarchy_fp64(SolverBufs& B, const double* a64, cudaStream_t st);
-void build_hierarchy_mixed(SolverBufs& B, const __nv_bfloat16* abf, cudaStream_t st);
+// coarse coefficients and, per tiled level, omega D^-1 (omega: the smoother's damping)
+void build_hierarchy_fp64(SolverBufs& B, const double* a64, double omega, cudaStream_t st);
+void build_hierarchy_mixed(SolverBufs& B, const __nv_bfloat16* abf, double omega, cudaStream_t st);
 // bytes the buffers need (elem = 8 for FP64, 4 for FP32 Krylov vectors)
 size_t solver_bytes(int N, int S, int elem);
 void carve_solver(SolverBufs& B, int N, int S, int elem, char*& ptr);
@@ -135,15 +136,15 @@ template <typename T, typename TA>
 void tiled_apply(const T* z, const T* pold, T* pnew, const TA* a, T* q, double* partial, const SolveScalars* sc, int N,
                  const Batch& bt, int first, cudaStream_t st);
 template <typename T, typename TA>
-void tiled_pre(const T* r, const TA* a, const T* dinv, T* t, const SolveScalars* sc, int N, const Batch& bt,
-               double omega, cudaStream_t st);
+void tiled_pre(const T* r, const TA* a, const T* wdinv, T* t, const SolveScalars* sc, int N, const Batch& bt,
+               cudaStream_t st);
 template <typename T, typename TA>
-void tiled_post(const T* r, const TA* a, const T* dinv, const T* ec, T* z, double* partial, const SolveScalars* sc,
-                int N, const Batch& bt, double omega, cudaStream_t st);
+void tiled_post(const T* r, const TA* a, const T* wdinv, const T* ec, T* z, double* partial, const SolveScalars* sc,
+                int N, const Batch& bt, cudaStream_t st);
 void tiled_apply_x(const float* z, const float* pold, float* pnew, const float* a, float* q, float* x, double* partial,
                    const SolveScalars* sc, int N, const Batch& bt, cudaStream_t st, bool x_first);
-void tiled_pre_update(const float* r, const float* q, const __nv_bfloat16* a, const float* dinv, float* t, float* rnew,
-                      const SolveScalars* sc, int N, const Batch& bt, double omega, cudaStream_t st);
+void tiled_pre_update(const float* r, const float* q, const __nv_bfloat16* a, const float* wdinv, float* t,
+                      float* rnew, const SolveScalars* sc, int N, const Batch& bt, cudaStream_t st);
 // r32 = (float)(b - A x) to FP64 accuracy with x, b as FP32 (hi, lo) pairs and error-free
 // FP32 products and sums; partial r.r
 void tiled_res64(const float2* b, long long bstride, const float2* x, const float* a, float* r32, double* partial,
@@ -162,11 +163,11 @@ TiledShape slab_shape(int N, int S, int zchunks = 0);
 void slab_apply(const float* z, const float* pold, float* pnew, const float* a, float* q, float* x, double* partial,
                 const SolveScalars* sc, int N, const Batch& bt, bool first, bool with_x, bool x_first, cudaStream_t st);
 template <typename TA>
-void slab_pre(const float* r, const float* q, const TA* a, const float* dinv, float* t, float* rnew,
-              const SolveScalars* sc, int N, const Batch& bt, double omega, cudaStream_t st);
+void slab_pre(const float* r, const float* q, const TA* a, const float* wdinv, float* t, float* rnew,
+              const SolveScalars* sc, int N, const Batch& bt, cudaStream_t st);
 template <typename TA>
-void slab_post(const float* r, const TA* a, const float* dinv, const float* ec, float* z, double* partial,
-               const SolveScalars* sc, int N, const Batch& bt, double omega, cudaStream_t st);
+void slab_post(const float* r, const TA* a, const float* wdinv, const float* ec, float* z, double* partial,
+               const SolveScalars* sc, int N, const Batch& bt, cudaStream_t st);
 
 // the V-cycle from a coarse 16^3 level (j >= 1 of a grid with N cells) down to 2^3 in one
 // launch, one block per launched sample (coarse.cu): r16 the restricted residual, a the
@@ -194,7 +195,7 @@ void launch_phi_adjrhs_df(const float2* y, int N, int S, float2* badj, double* p
                           const float2* gtab, const float2* mgtab, cudaStream_t st);
 // batch statistics of one level merged into stats (see mlsgd_level_stats)
 // qf_pairs / qc_pairs: the adjoint solutions are stored as FP32 (hi, lo) pairs;
-// work holds 4 + 2 S doubles; nodebuf (2 (Nf+1)^3 doubles, optional): when the
+// work holds 4 + 4 S doubles; nodebuf (2 (Nf+1)^3 doubles, optional): when the
 // level's grids are at least 4x coarser than the control grid the statistics are
 // formed on the level grid (qf is then overwritten; partial needs cells(Nc)/256 +
 // cells(Nf)/256 + 2 entries)

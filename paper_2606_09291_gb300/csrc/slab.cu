@@ -55,7 +55,7 @@ constexpr int short_vec(int mode) { return mode == 1 ? 1 : (mode == 4 ? 2 : -1);
 struct SlabArgs {
   const float* in0;   // APPLY/APPLYX: z     PRE/PREU/POST: r
   const float* in1;   // APPLY/APPLYX: p_old PREU: q
-  const float* dinv;  // PRE/PREU/POST: D^-1 (0 on the boundary)
+  const float* dinv;  // PRE/PREU/POST: omega D^-1 (0 on the boundary)
   const float* ec;    // POST: coarse correction on grid N/2
   const void* a;      // cell coefficient (TA)
   float* out0;        // APPLY: q   PRE/PREU: t   POST: z
@@ -67,7 +67,7 @@ struct SlabArgs {
   int* err;           // set when a wait runs out
   int nzc, zc, nseg;
   int first, xfirst;
-  float omega, scale;
+  float scale;
 };
 
 template <int N>
@@ -182,7 +182,7 @@ __global__ void __launch_bounds__(256, 3) k_slab(SlabArgs A) {
   const int crows = min(G::CROWS, N + 1 - y0);
   const int cy0 = (y0 - 1) >> 1;  // first staged coarse row
   const int crows_c = min(G::CNR, G::NC1 - cy0);
-  const float omega = A.omega, scale = A.scale;
+  const float scale = A.scale;
   float beta = 0.f, alpha = 0.f;
   if (kApply && !A.first) beta = (float)A.sc[s].beta;
   if (MODE == SL_APPLYX || MODE == SL_PREU) alpha = (float)A.sc[s].alpha;
@@ -323,12 +323,12 @@ __global__ void __launch_bounds__(256, 3) k_slab(SlabArgs A) {
       if (A.first) each([&](int e, int) { return r0[e]; });
       else each([&](int e, int) { return fmaf(beta, r1[e], r0[e]); });
     } else if (MODE == SL_PREU) {
-      each([&](int e, int) { return omega * fmaf(-alpha, r1[e], r0[e]) * r2[e]; });
+      each([&](int e, int) { return fmaf(-alpha, r1[e], r0[e]) * r2[e]; });
     } else if (kPost) {  // coarse correction: one interpolated coarse plane (m even) or the mean of two
-      if (m & 1) each([&](int e, int x) { return fmaf(omega * r0[e], r1[e], 0.5f * (e0[x] + e1[x])); });
-      else each([&](int e, int x) { return fmaf(omega * r0[e], r1[e], e0[x]); });
+      if (m & 1) each([&](int e, int x) { return fmaf(r0[e], r1[e], 0.5f * (e0[x] + e1[x])); });
+      else each([&](int e, int x) { return fmaf(r0[e], r1[e], e0[x]); });
     } else {
-      each([&](int e, int) { return omega * r0[e] * r1[e]; });
+      each([&](int e, int) { return r0[e] * r1[e]; });
     }
   };
 
@@ -498,7 +498,7 @@ __global__ void __launch_bounds__(256, 3) k_slab(SlabArgs A) {
             out1[g] = rn;
           } else {  // POST
             const float rv = ok ? o0[own] : 0.f;
-            const float zv = ok ? ctr[t][i] + omega * (rv - ax) * o1[own] : 0.f;
+            const float zv = ok ? fmaf(fmaf(-scale, acc[t][i], rv), o1[own], ctr[t][i]) : 0.f;
             out0[g] = zv;
             red = fmaf(rv, zv, red);
           }
@@ -589,10 +589,9 @@ void slab_apply(const float* z, const float* pold, float* pnew, const float* a, 
 
 template <typename TA>
 void slab_pre(const float* r, const float* q, const TA* a, const float* dinv, float* t, float* rnew,
-              const SolveScalars* sc, int N, const Batch& bt, double omega, cudaStream_t st) {
+              const SolveScalars* sc, int N, const Batch& bt, cudaStream_t st) {
   SlabArgs A{};
   A.in0 = r; A.in1 = q; A.a = a; A.dinv = dinv; A.out0 = t; A.out1 = rnew; A.sc = sc; A.err = bt.err;
-  A.omega = (float)omega;
   if (q)
     dispatch<TA, SL_PREU>(N, "pre_f32", sbytes(N, bt.n, 5, 1, sizeof(TA)), A, bt, st);
   else
@@ -601,21 +600,20 @@ void slab_pre(const float* r, const float* q, const TA* a, const float* dinv, fl
 
 template <typename TA>
 void slab_post(const float* r, const TA* a, const float* dinv, const float* ec, float* z, double* partial,
-               const SolveScalars* sc, int N, const Batch& bt, double omega, cudaStream_t st) {
+               const SolveScalars* sc, int N, const Batch& bt, cudaStream_t st) {
   SlabArgs A{};
   A.in0 = r; A.a = a; A.dinv = dinv; A.ec = ec; A.out0 = z; A.partial = partial; A.sc = sc; A.err = bt.err;
-  A.omega = (float)omega;
   dispatch<TA, SL_POST>(N, "post_f32", sbytes(N, bt.n, 3, 1, sizeof(TA)) + (double)bt.n * nodes_of(N / 2) * 4, A, bt,
                         st);
 }
 
 template void slab_pre<__nv_bfloat16>(const float*, const float*, const __nv_bfloat16*, const float*, float*, float*,
-                                      const SolveScalars*, int, const Batch&, double, cudaStream_t);
+                                      const SolveScalars*, int, const Batch&, cudaStream_t);
 template void slab_pre<float>(const float*, const float*, const float*, const float*, float*, float*,
-                              const SolveScalars*, int, const Batch&, double, cudaStream_t);
+                              const SolveScalars*, int, const Batch&, cudaStream_t);
 template void slab_post<__nv_bfloat16>(const float*, const __nv_bfloat16*, const float*, const float*, float*,
-                                       double*, const SolveScalars*, int, const Batch&, double, cudaStream_t);
+                                       double*, const SolveScalars*, int, const Batch&, cudaStream_t);
 template void slab_post<float>(const float*, const float*, const float*, const float*, float*, double*,
-                               const SolveScalars*, int, const Batch&, double, cudaStream_t);
+                               const SolveScalars*, int, const Batch&, cudaStream_t);
 
 }  // namespace mlsgd

@@ -565,7 +565,7 @@ __device__ __forceinline__ float recip(float x) { return __fdividef(1.0f, x); }
 // One thread per node column (i, j) marching in z: the four cells of the column
 // below a node are summed once and reused by the node above.
 template <typename T, typename TA>
-__global__ void k_dinv(const TA* __restrict__ a, T* __restrict__ dinv, int N) {
+__global__ void k_dinv(const TA* __restrict__ a, T* __restrict__ dinv, int N, T omega) {
   const int s = blockIdx.y;
   const int n1 = N + 1;
   const int col = blockIdx.x * blockDim.x + threadIdx.x;
@@ -589,22 +589,23 @@ __global__ void k_dinv(const TA* __restrict__ a, T* __restrict__ dinv, int N) {
   T below = sum4(0);
   for (int k = 1; k < N; ++k) {
     const T above = sum4(k);
-    out[k * plane] = recip(h3 * (below + above));
+    out[k * plane] = omega * recip(h3 * (below + above));
     below = above;
   }
 }
 
 template <typename T, typename TA0>
-static void build_dinv(SolverBufs& B, const TA0* a0, cudaStream_t st) {
+static void build_dinv(SolverBufs& B, const TA0* a0, double omega, cudaStream_t st) {
   for (int j = 0; j <= B.J; ++j) {
     if (!B.dinv[j]) continue;
     const int Nj = B.N >> j;
     const dim3 g((unsigned)(((Nj + 1) * (Nj + 1) + kBlock - 1) / kBlock), (unsigned)B.S);
     if (j == 0)
-      launch("dinv", nbytes<T, TA0>(Nj, B.S, 1, 1), k_dinv<T, TA0>, g, kBlock, 0, st, a0, (T*)B.dinv[0], Nj);
+      launch("dinv", nbytes<T, TA0>(Nj, B.S, 1, 1), k_dinv<T, TA0>, g, kBlock, 0, st, a0, (T*)B.dinv[0], Nj,
+             (T)omega);
     else
       launch("dinv", nbytes<T, T>(Nj, B.S, 1, 1), k_dinv<T, T>, g, kBlock, 0, st, (const T*)B.acoef[j],
-             (T*)B.dinv[j], Nj);
+             (T*)B.dinv[j], Nj, (T)omega);
   }
 }
 
@@ -622,13 +623,13 @@ static void coarsen_all(SolverBufs& B, const TI* a0, cudaStream_t st) {
              (TO*)B.acoef[j], Nc, B.S);
   }
 }
-void build_hierarchy_fp64(SolverBufs& B, const double* a64, cudaStream_t st) {
+void build_hierarchy_fp64(SolverBufs& B, const double* a64, double omega, cudaStream_t st) {
   coarsen_all<double, double>(B, a64, st);
-  build_dinv<double, double>(B, a64, st);
+  build_dinv<double, double>(B, a64, omega, st);
 }
-void build_hierarchy_mixed(SolverBufs& B, const __nv_bfloat16* abf, cudaStream_t st) {
+void build_hierarchy_mixed(SolverBufs& B, const __nv_bfloat16* abf, double omega, cudaStream_t st) {
   coarsen_all<__nv_bfloat16, float>(B, abf, st);
-  build_dinv<float, __nv_bfloat16>(B, abf, st);
+  build_dinv<float, __nv_bfloat16>(B, abf, omega, st);
 }
 
 // One V(1,1)-cycle on r0 (level-0 coefficient a0); the result is left in vt[0].
@@ -659,11 +660,11 @@ static int vcycle(SolverBufs& B, const T* r0, const TA0* a0, const SolveScalars*
     const bool fine = j == 0;
     if (fine && tiled && fuse_q) {
       if constexpr (std::is_same<T, float>::value && std::is_same<TA0, __nv_bfloat16>::value)
-        tiled_pre_update(r0, fuse_q, a0, (const T*)B.dinv[0], (T*)B.vt[0], r_new, sc, Nj, bt, (double)omega, st);
+        tiled_pre_update(r0, fuse_q, a0, (const T*)B.dinv[0], (T*)B.vt[0], r_new, sc, Nj, bt, st);
     } else if (fine && tiled) {
-      tiled_pre<T, TA0>(r0, a0, (const T*)B.dinv[0], (T*)B.vt[0], sc, Nj, bt, (double)omega, st);
+      tiled_pre<T, TA0>(r0, a0, (const T*)B.dinv[0], (T*)B.vt[0], sc, Nj, bt, st);
     } else if (!fine && tiled && Nj >= kTiledMinN) {
-      tiled_pre<T, T>(rin(j), (const T*)B.acoef[j], (const T*)B.dinv[j], (T*)B.vt[j], sc, Nj, bt, (double)omega, st);
+      tiled_pre<T, T>(rin(j), (const T*)B.acoef[j], (const T*)B.dinv[j], (T*)B.vt[j], sc, Nj, bt, st);
     } else if (fine) {
       launch(cls<T>("jacobi0", true), nbytes<T, TA0>(Nj, n, 2, 1), k_jacobi0<T, TA0>, grid_nodes(Nj, n), kBlock, 0,
              st, rin(0), a0, (T*)B.vx[0], sc, Nj, omega, act);
@@ -697,14 +698,13 @@ static int vcycle(SolverBufs& B, const T* r0, const TA0* a0, const SolveScalars*
     const int Nj = B.N >> j;
     const bool fine = j == 0;
     if (fine && tiled) {
-      tiled_post<T, TA0>(rfine, a0, (const T*)B.dinv[0], (const T*)B.vt[1], (T*)B.vt[0], B.partial, sc, Nj, bt,
-                         (double)omega, st);
+      tiled_post<T, TA0>(rfine, a0, (const T*)B.dinv[0], (const T*)B.vt[1], (T*)B.vt[0], B.partial, sc, Nj, bt, st);
       return tiled_blocks_per_sample(Nj, S, (int)sizeof(T), uses_slab(B, Nj, (int)sizeof(T)));
     }
     if (!fine && tiled && Nj >= kTiledMinN) {
       // the r.z partial sums of a coarse level are overwritten by the fine level's POST
       tiled_post<T, T>(rin(j), (const T*)B.acoef[j], (const T*)B.dinv[j], (const T*)B.vt[j + 1], (T*)B.vt[j],
-                       B.partial, sc, Nj, bt, (double)omega, st);
+                       B.partial, sc, Nj, bt, st);
       continue;
     }
     launch(cls<T>("prolong", fine), nbytes<T, T>(Nj, n, 2, 0) + nbytes<T, T>(Nj / 2, n, 1, 0), k_prolong_add<T>,

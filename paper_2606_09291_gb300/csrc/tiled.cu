@@ -21,6 +21,7 @@
 //   PRE   : x1 = omega D^{-1} r computed on the fly; t = r - A x1
 //   POST  : x2 = omega D^{-1} r + P e_c on the fly;
 //           z = x2 + omega D^{-1} (r - A x2); partial r.z
+//   (omega D^{-1} is precomputed per coefficient hierarchy and staged like a vector)
 //   RES64 : r = b - A x to FP64 accuracy in FP32 arithmetic: x and b are FP32 (hi, lo)
 //           pairs (staged as 8-byte words), a is FP32; writes r rounded to FP32 and the
 //           partial r.r
@@ -50,7 +51,7 @@ struct TiledArgs {
   const void* in1;   // APPLY: p (old)                RES64: b (FP64)
   const void* ec;    // POST: coarse correction (grid N/2)
   const void* a;     // cell coefficient
-  const void* dinv;  // PRE/PREU/POST: D^{-1} per node (0 on the boundary)
+  const void* dinv;  // PRE/PREU/POST: omega D^{-1} per node (0 on the boundary)
   void* out0;        // APPLY: q   PRE: t   POST: z   RES64: r
   void* out1;        // APPLY: p (new)   PREU: r (new)
   const void* q;     // PREU: A p of the current iteration
@@ -65,7 +66,6 @@ struct TiledArgs {
   int nseg;          // partial-sum segments per sample column
   int first;         // APPLY: first iteration (pn = z)
   int xfirst;        // APPLYX: x not yet written (x = alpha_prev p_old)
-  double omega;
 };
 
 __device__ __forceinline__ int ring3(int m) { return (m + 3) % 3; }
@@ -91,6 +91,7 @@ __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_gr
 constexpr int kZSeg = 8;
 
 constexpr int RING = 5;   // raw planes resident: k-1, k, k+1 + two in flight
+constexpr double kRes64OpsPerNode = 12 * 6 + 28 + 21 * 12 + 20;  // = 372 (see tiled_res64)
 constexpr int ERING = 4;  // coarse planes
 constexpr int CW = TX + 4;  // staged cell row: 36 cells from x0 - 3 (even start)
 constexpr int EWX = TX / 2 + 2;
@@ -176,7 +177,6 @@ __global__ void __launch_bounds__(NT) k_tiled(TiledArgs A) {
   const int kbeg = 1 + chunk * A.zc;
   const int kend = min(N - 1, kbeg + A.zc - 1);
   const T scale = T(1.0 / (12.0 * N));
-  const T omega = (T)A.omega;
   const T* in0 = (const T*)A.in0 + s * nodes;
   constexpr bool kApply = L::kApply;
   const T* in1 = kApply ? (const T*)A.in1 + s * nodes : (MODE == TM_PREU ? (const T*)A.q + s * nodes : in0);
@@ -334,7 +334,7 @@ __global__ void __launch_bounds__(NT) k_tiled(TiledArgs A) {
         // branch-free: D^-1 is 0 on the boundary and zero-filled outside the grid (and
         // so is r outside 0 < m < N), so only the coarse correction needs a mask
         const T rn = (MODE == TM_PREU) ? r0[e] - alpha * raw1[slot * NPL + e] : r0[e];
-        T v = omega * rn * dvp[e];
+        T v = rn * dvp[e];
         if (MODE == TM_POST) {
           const T mk = (mint && (nflag[j] & 4)) ? T(1) : T(0);
           v += mk * (dk ? (e0p[e] + e1p[e]) * T(0.5) : e0p[e]);
@@ -553,7 +553,7 @@ __global__ void __launch_bounds__(NT) k_tiled(TiledArgs A) {
         } else if (MODE == TM_POST) {
           const T rv = rk[NPX * t];
           const T dk = dvs[s5 * NPL + xb + 1 + NPX * (t + 1)];
-          const T zv = X[1][1][t + 1] + omega * (rv - ax) * dk;
+          const T zv = X[1][1][t + 1] + (rv - ax) * dk;
           out0[o] = zv;
           red += rv * zv;
         }
@@ -736,7 +736,8 @@ TiledShape tiled_shape(int N, int S, int ry, int zchunks) {
 // so a sample's partial sums, and with them its iterates, do not depend on how many
 // other samples are still active.
 template <typename T, typename TA, int MODE>
-static void run_tiled(const char* cls, double bytes, TiledArgs args, const Batch& bt, cudaStream_t st) {
+static void run_tiled(const char* cls, double bytes, TiledArgs args, const Batch& bt, cudaStream_t st,
+                      double ops = 0.0) {
   const TiledShape t = tiled_shape(args.N, bt.S, RowsPerThread<T>::value, bt.zchunks);
   args.nzc = t.nzc;
   args.zc = t.zc;
@@ -748,7 +749,8 @@ static void run_tiled(const char* cls, double bytes, TiledArgs args, const Batch
     cudaFuncSetAttribute(k_tiled<T, TA, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     smem_set = true;
   }
-  launch(cls, bytes, k_tiled<T, TA, MODE>, dim3(t.bx, t.by, (unsigned)(bt.n * t.nzc)), dim3(TX, TY), smem, st, args);
+  launch_flops(cls, bytes, ops, k_tiled<T, TA, MODE>, dim3(t.bx, t.by, (unsigned)(bt.n * t.nzc)), dim3(TX, TY), smem,
+               st, args);
 }
 
 template <typename T, typename TA>
@@ -794,42 +796,41 @@ void tiled_apply_x(const float* z, const float* pold, float* pnew, const float* 
   A.xfirst = x_first ? 1 : 0;
   run_tiled<float, float, TM_APPLYX>("apply_f32", vbytes<float, float>(N, bt.n, x_first ? 5 : 6, 1), A, bt, st);
 }
-void tiled_pre_update(const float* r, const float* q, const __nv_bfloat16* a, const float* dinv, float* t, float* rnew,
-                      const SolveScalars* sc, int N, const Batch& bt, double omega, cudaStream_t st) {
+void tiled_pre_update(const float* r, const float* q, const __nv_bfloat16* a, const float* dinv, float* t,
+                      float* rnew, const SolveScalars* sc, int N, const Batch& bt, cudaStream_t st) {
   if (bt.stencil == 0 && slab_supported(N)) {
-    slab_pre<__nv_bfloat16>(r, q, a, dinv, t, rnew, sc, N, bt, omega, st);
+    slab_pre<__nv_bfloat16>(r, q, a, dinv, t, rnew, sc, N, bt, st);
     return;
   }
   TiledArgs A{};
-  A.in0 = r; A.q = q; A.a = a; A.dinv = dinv; A.out0 = t; A.out1 = rnew; A.sc = sc; A.N = N; A.omega = omega;
+  A.in0 = r; A.q = q; A.a = a; A.dinv = dinv; A.out0 = t; A.out1 = rnew; A.sc = sc; A.N = N;
   run_tiled<float, __nv_bfloat16, TM_PREU>("pre_f32", vbytes<float, __nv_bfloat16>(N, bt.n, 5, 1), A, bt, st);
 }
 
 template <typename T, typename TA>
 void tiled_pre(const T* r, const TA* a, const T* dinv, T* t, const SolveScalars* sc, int N, const Batch& bt,
-               double omega, cudaStream_t st) {
+               cudaStream_t st) {
   if constexpr (std::is_same<T, float>::value) {
     if (bt.stencil == 0 && slab_supported(N)) {
-      slab_pre<TA>(r, nullptr, a, dinv, t, nullptr, sc, N, bt, omega, st);
+      slab_pre<TA>(r, nullptr, a, dinv, t, nullptr, sc, N, bt, st);
       return;
     }
   }
   TiledArgs A{};
-  A.in0 = r; A.a = a; A.dinv = dinv; A.out0 = t; A.sc = sc; A.N = N; A.omega = omega;
+  A.in0 = r; A.a = a; A.dinv = dinv; A.out0 = t; A.sc = sc; A.N = N;
   run_tiled<T, TA, TM_PRE>(name("pre", tag<T>()), vbytes<T, TA>(N, bt.n, 3, 1), A, bt, st);
 }
 template <typename T, typename TA>
 void tiled_post(const T* r, const TA* a, const T* dinv, const T* ec, T* z, double* partial, const SolveScalars* sc,
-                int N, const Batch& bt, double omega, cudaStream_t st) {
+                int N, const Batch& bt, cudaStream_t st) {
   if constexpr (std::is_same<T, float>::value) {
     if (bt.stencil == 0 && slab_supported(N)) {
-      slab_post<TA>(r, a, dinv, ec, z, partial, sc, N, bt, omega, st);
+      slab_post<TA>(r, a, dinv, ec, z, partial, sc, N, bt, st);
       return;
     }
   }
   TiledArgs A{};
   A.in0 = r; A.a = a; A.dinv = dinv; A.ec = ec; A.out0 = z; A.partial = partial; A.sc = sc; A.N = N;
-  A.omega = omega;
   run_tiled<T, TA, TM_POST>(name("post", tag<T>()), vbytes<T, TA>(N, bt.n, 3, 1) + vbytes<T, T>(N / 2, bt.n, 1, 0), A,
                             bt, st);
 }
@@ -838,8 +839,12 @@ void tiled_res64(const float2* b, long long bstride, const float2* x, const floa
   TiledArgs A{};
   A.in0 = x; A.in1 = b; A.bstride = bstride; A.a = a; A.out0 = r32; A.partial = partial; A.sc = sc; A.N = N;
   const double bb = (double)(bstride ? bt.n : 1) * nodes_of(N) * 8;
+  // FP32 operations per interior node as written (no sharing between nodes): 12 exact
+  // cell-pair sums (6 each), the 8-cell sum (28), 21 compensated product terms (12
+  // each), the scaling, the subtraction from b and r.r (20)
+  const double ops = (double)bt.n * (N - 1) * (N - 1) * (N - 1) * kRes64OpsPerNode;
   run_tiled<double, float, TM_RES64>("resid64", bb + vbytes<double, float>(N, bt.n, 1, 1) + (double)bt.n * nodes_of(N) * 4,
-                                     A, bt, st);
+                                     A, bt, st, ops);
 }
 
 int tiled_phi_df(const float2* y, int N, int S, const float2* gtab, const float2* mgtab, float2* badj,
@@ -863,17 +868,17 @@ template void tiled_apply<float, float>(const float*, const float*, float*, cons
 template void tiled_apply<double, double>(const double*, const double*, double*, const double*, double*, double*,
                                           const SolveScalars*, int, const Batch&, int, cudaStream_t);
 template void tiled_pre<float, __nv_bfloat16>(const float*, const __nv_bfloat16*, const float*, float*,
-                                              const SolveScalars*, int, const Batch&, double, cudaStream_t);
+                                              const SolveScalars*, int, const Batch&, cudaStream_t);
 template void tiled_pre<float, float>(const float*, const float*, const float*, float*, const SolveScalars*, int,
-                                      const Batch&, double, cudaStream_t);
+                                      const Batch&, cudaStream_t);
 template void tiled_post<float, float>(const float*, const float*, const float*, const float*, float*, double*,
-                                       const SolveScalars*, int, const Batch&, double, cudaStream_t);
+                                       const SolveScalars*, int, const Batch&, cudaStream_t);
 template void tiled_pre<double, double>(const double*, const double*, const double*, double*, const SolveScalars*, int,
-                                        const Batch&, double, cudaStream_t);
+                                        const Batch&, cudaStream_t);
 template void tiled_post<float, __nv_bfloat16>(const float*, const __nv_bfloat16*, const float*, const float*, float*,
-                                               double*, const SolveScalars*, int, const Batch&, double, cudaStream_t);
+                                               double*, const SolveScalars*, int, const Batch&, cudaStream_t);
 template void tiled_post<double, double>(const double*, const double*, const double*, const double*, double*, double*,
-                                         const SolveScalars*, int, const Batch&, double, cudaStream_t);
+                                         const SolveScalars*, int, const Batch&, cudaStream_t);
 
 }  // namespace mlsgd
 
