@@ -425,6 +425,7 @@ __global__ void k_level_field(const void* __restrict__ qf_, int Nf, const void* 
     if (fast_f) If.setup(Nf, Nc, cx, cy, cz);
     if (qc && fast_c) Ic.setup(Ncs, Nc, cx, cy, cz);
     double ref = 0.0, sd = 0.0, sd2 = 0.0;
+#pragma unroll 2
     for (int s = 0; s < S; ++s) {
       double v;
       if constexpr (PF && PC) {

@@ -87,7 +87,9 @@ struct SolverBufs {
   void* vt[8];               // V-cycle temporary / output per level
   void* vr[8];               // restricted residual (j >= 1)
   void* dinv[8];             // D^{-1} of levels run with the tiled passes (0 at boundary nodes), else null
-  float2* bdf;               // mixed tiled solves: b as FP32 (hi, lo) pairs [S][nodes] (or [nodes] if shared)
+  float2* bdf;               // mixed tiled solves: b as FP32 (hi, lo) pairs [S][nodes]; with the slab
+                             // refinement step, the residual pairs of the step
+  float2* bsh;               // the same for a b shared by every sample: [nodes]
   // Krylov vectors
   void* x;                   // solution / correction
   void* r;                   // residual
@@ -168,6 +170,14 @@ void slab_pre(const float* r, const float* q, const TA* a, const float* wdinv, f
 template <typename TA>
 void slab_post(const float* r, const TA* a, const float* wdinv, const float* ec, float* z, double* partial,
                const SolveScalars* sc, int N, const Batch& bt, cudaStream_t st);
+// the refinement step in one pass: inc = d + alpha p (alpha p when d_zero; alpha from
+// sci), rr_out = rr_in - A inc and r32 = rr_out rounded (to FP64 accuracy in FP32 pair
+// arithmetic; rr_in stride 0: one vector for every sample), partial r32.r32, and the
+// solution pairs x (+)= inc (x = inc when assign; samples that take no step get x = 0
+// on the first step); interior and x = N / y = N nodes only
+void slab_res(const float* d, const float* p, bool d_zero, const SolveScalars* sci, const float2* rr_in,
+              long long rr_stride, float2* rr_out, float2* x, bool assign, const float* a, float* r32,
+              double* partial, const SolveScalars* sco, int N, const Batch& bt, cudaStream_t st);
 
 // the V-cycle from a coarse 16^3 level (j >= 1 of a grid with N cells) down to 2^3 in one
 // launch, one block per launched sample (coarse.cu): r16 the restricted residual, a the

@@ -22,8 +22,17 @@
 //     y = N of a lane's window (as 0), never x = 0, y = 0 or the planes 0 and N;
 //   * the derived operand plane has an even row stride N + 2, so a lane's window of
 //     RX + 2 columns is read with 8-byte loads when RX = 2.
-// Partial sums (APPLY p.q, POST r.z) are formed per segment of kZSeg interior planes
-// exactly as in tiled.cu (entry seg * by + tile_y per sample).
+// Partial sums (APPLY p.q, POST r.z, RES r.r) are formed per segment of kZSeg interior
+// planes exactly as in tiled.cu (entry seg * by + tile_y per sample).
+//
+// RES is the refinement step of the mixed solver in one pass: the operand is the inner
+// solve's increment inc = d + alpha p, the stencil forms A inc to FP64 accuracy in
+// FP32 arithmetic (exact cell-pair sums and FMA-split products, compensated sums), and
+// each owned node updates the residual pair rr <- rr - A inc (rr = b before the first
+// step), writes it rounded as the next inner solve's FP32 residual and updates the
+// solution pair x (+)= inc.  Neither rr nor x is read at another block's nodes, so both
+// are updated in place; the recursive residual equals b - A x up to the pair
+// arithmetic's rounding (a few u^2 |A||x| per step, u = 2^-24).
 //
 // Every wait on an mbarrier is bounded (about a second of SM clock); a wait that
 // runs out sets *err, and the thread then skips its remaining waits and copies but
@@ -40,7 +49,7 @@ namespace mlsgd {
 
 namespace {
 
-enum SlabMode { SL_APPLY = 0, SL_PRE = 1, SL_POST = 2, SL_PREU = 4, SL_APPLYX = 5 };
+enum SlabMode { SL_APPLY = 0, SL_PRE = 1, SL_POST = 2, SL_PREU = 4, SL_APPLYX = 5, SL_RES = 6 };
 constexpr int kSegPlanes = 8;  // partial-sum segment (the same as tiled.cu's kZSeg)
 // Raw plane slots: plane m of a chunk (j = m - (kbeg-1)) lives in slot j % 4 of the
 // node vectors whose own-node values the epilogue reads, and in slot j % 3 of D^-1 in
@@ -68,7 +77,33 @@ struct SlabArgs {
   int nzc, zc, nseg;
   int first, xfirst;
   float scale;
+  // RES: the refinement step, see k_slab
+  const SolveScalars* sci;  // inner solve's scalars (alpha of its last update)
+  const float2* rr_in;      // residual pairs before the step (b on the first step)
+  long long rr_stride;      // rr_in stride per sample (0: one shared vector)
+  float2* rr_out;           // residual pairs after the step, [S][nodes]
+  float2* xp;               // solution pairs, updated in place, [S][nodes]
+  int assign, dzero;        // first step (x = inc); d never written (inc = alpha p)
 };
+
+// ---- error-free FP32 arithmetic of the refinement step (RES)
+// two_sum: s + e == a + b exactly (Knuth); a coefficient is an unevaluated pair (h, l)
+struct P2 { float h, l; };
+__device__ __forceinline__ P2 two_sum(float a, float b) {
+  const float s = a + b;
+  const float bb = s - a;
+  return P2{s, (a - (s - bb)) + (b - bb)};
+}
+// (S, comp) += sgn (c.h + c.l) x for an FP32 operand x: the product c.h x is split
+// exactly by the FMA, c.l x enters the compensation
+template <bool NEG>
+__device__ __forceinline__ void res_term(float& S, float& comp, P2 c, float x) {
+  const float p = c.h * x;
+  const float low = __fmaf_rn(c.l, x, __fmaf_rn(c.h, x, -p));
+  const P2 t = two_sum(S, NEG ? -p : p);
+  S = t.h;
+  comp += t.l + (NEG ? -low : low);
+}
 
 template <int N>
 struct SlabGeo {
@@ -156,6 +191,7 @@ __global__ void __launch_bounds__(256, 3) k_slab(SlabArgs A) {
   constexpr int RX = G::RX, RY = G::RY, TYT = G::TYT, N1 = G::N1, NR = G::NR, XS = G::XS;
   constexpr bool kApply = MODE == SL_APPLY || MODE == SL_APPLYX;
   constexpr bool kPost = MODE == SL_POST;
+  constexpr bool kRes = MODE == SL_RES;
   constexpr int NV = L::NV;
   static_assert(N1 % 4 == 1 && G::NC1 % 4 == 1, "shift arithmetic assumes N + 1 = 1 mod 4");
   extern __shared__ __align__(16) unsigned char sm[];
@@ -169,12 +205,22 @@ __global__ void __launch_bounds__(256, 3) k_slab(SlabArgs A) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int chunk = blockIdx.z % A.nzc;
   const int s = A.act != nullptr ? A.act[blockIdx.z / A.nzc] : (int)(blockIdx.z / A.nzc);
-  if (A.sc != nullptr && !A.sc[s].active) return;
-  if (*(volatile int*)A.err != 0) return;  // an earlier wait ran out: the results are void anyway
   const int y0 = 1 + TYT * blockIdx.y;  // first interior row of the block
   const int kbeg = 1 + chunk * A.zc;
   const int kend = min(N - 1, kbeg + A.zc - 1);
   constexpr long long kNodes = (long long)N1 * N1 * N1;
+  if (A.sc != nullptr && !A.sc[s].active) {
+    if (kRes && A.assign) {  // a sample that takes no step: its solution is 0 (own nodes)
+      float2* xo = A.xp + s * kNodes;
+      for (int k = kbeg; k <= kend; ++k)
+        for (int e = tid; e < TYT * N; e += 256) {
+          const int y = y0 + e / N;
+          if (y <= N - 1) xo[(long long)k * N1 * N1 + (long long)y * N1 + 1 + e % N] = make_float2(0.f, 0.f);
+        }
+    }
+    return;
+  }
+  if (*(volatile int*)A.err != 0) return;  // an earlier wait ran out: the results are void anyway
   constexpr long long kCells = (long long)N * N * N;
   constexpr long long kCNodes = (long long)G::NC1 * G::NC1 * G::NC1;
   // node rows y0-1 .. y0+TYT and cell rows y0-1 .. y0+TYT-1 that exist
@@ -186,7 +232,10 @@ __global__ void __launch_bounds__(256, 3) k_slab(SlabArgs A) {
   float beta = 0.f, alpha = 0.f;
   if (kApply && !A.first) beta = (float)A.sc[s].beta;
   if (MODE == SL_APPLYX || MODE == SL_PREU) alpha = (float)A.sc[s].alpha;
-  auto vin = [&](int v) { return v == 0 ? A.in0 : (v == 1 && (MODE == SL_PREU || kApply) ? A.in1 : A.dinv); };
+  if (kRes) alpha = (float)A.sci[s].alpha;
+  auto vin = [&](int v) {
+    return v == 0 ? A.in0 : (v == 1 && (MODE == SL_PREU || kApply || kRes) ? A.in1 : A.dinv);
+  };
   bool dead = false;  // a wait of this thread ran out: skip the remaining waits and copies
 
   // ---- producer (thread 0): plane m into ring slot (m - first) % kRing
@@ -203,7 +252,7 @@ __global__ void __launch_bounds__(256, 3) k_slab(SlabArgs A) {
     const uint32_t nb = span(noff, rows * N1, d);
     const bool cell = m < N;
     const uint32_t cb = cell ? (uint32_t)(crows * N * sizeof(TA)) : 0u;
-    const int nv = (kApply && A.first) ? 1 : NV;  // the first APPLY reads no old p
+    const int nv = ((kApply && A.first) || (kRes && A.dzero)) ? 1 : NV;  // the first APPLY reads no old p
     uint32_t total = nv * nb + cb;
     // POST: coarse plane m/2 + 1 with every even fine plane (interpolated in derive(m)),
     // plane (kbeg-1)/2 as well with the first plane of the chunk
@@ -322,6 +371,9 @@ __global__ void __launch_bounds__(256, 3) k_slab(SlabArgs A) {
     if (kApply) {
       if (A.first) each([&](int e, int) { return r0[e]; });
       else each([&](int e, int) { return fmaf(beta, r1[e], r0[e]); });
+    } else if (kRes) {  // the inner solve's increment d + alpha p (alpha p when d is 0)
+      if (A.dzero) each([&](int e, int) { return alpha * r0[e]; });
+      else each([&](int e, int) { return fmaf(alpha, r1[e], r0[e]); });
     } else if (MODE == SL_PREU) {
       each([&](int e, int) { return fmaf(-alpha, r1[e], r0[e]) * r2[e]; });
     } else if (kPost) {  // coarse correction: one interpolated coarse plane (m even) or the mean of two
@@ -413,6 +465,113 @@ __global__ void __launch_bounds__(256, 3) k_slab(SlabArgs A) {
           }
         }
       }
+      // RES: rr_new = rr - A inc to FP64 accuracy in FP32 arithmetic (exact cell-pair
+      // sums and products, compensated sums, the scale h/12 and the subtraction as
+      // pairs), r = rr_new rounded, x (+)= inc; the same plane-by-plane order as below
+      if constexpr (kRes) {
+        float Sa[RY][RX], Ca[RY][RX], ctr[RY][RX];
+#pragma unroll
+        for (int pl = 0; pl < 3; ++pl) {
+          const int order = pl == 0 ? 1 : (pl == 1 ? 0 : 2);  // centre plane first
+          const float* xp = xs + (order == 0 ? xkm : (order == 1 ? xk : xkp)) * G::XPL + ly0 * XS + xw;
+          float W[RX + 2][RY + 2];
+#pragma unroll
+          for (int rr = 0; rr < RY + 2; ++rr) {
+            if constexpr (RX == 2) {
+              const float2 a0 = *reinterpret_cast<const float2*>(xp + rr * XS);
+              const float2 a1 = *reinterpret_cast<const float2*>(xp + rr * XS + 2);
+              W[0][rr] = a0.x;
+              W[1][rr] = a0.y;
+              W[2][rr] = a1.x;
+              W[3][rr] = a1.y;
+            } else {
+#pragma unroll
+              for (int c = 0; c < RX + 2; ++c) W[c][rr] = xp[rr * XS + c];
+            }
+          }
+#pragma unroll
+          for (int t = 0; t < RY; ++t)
+#pragma unroll
+            for (int i = 0; i < RX; ++i) {
+              if (order == 1) {
+                P2 pxy[2][2];
+#pragma unroll
+                for (int v = 0; v < 2; ++v)
+#pragma unroll
+                  for (int u = 0; u < 2; ++u) pxy[v][u] = two_sum(C[0][i + u][t + v], C[1][i + u][t + v]);
+                float S8 = 0.f, E8 = 0.f;
+#pragma unroll
+                for (int v = 0; v < 2; ++v)
+#pragma unroll
+                  for (int u = 0; u < 2; ++u) {
+                    const P2 q = two_sum(S8, pxy[v][u].h);
+                    S8 = q.h;
+                    E8 += q.l + pxy[v][u].l;
+                  }
+                float S = 0.f, cmp = 0.f;
+                ctr[t][i] = W[i + 1][t + 1];
+                res_term<false>(S, cmp, P2{4.f * S8, 4.f * E8}, W[i + 1][t + 1]);
+#pragma unroll
+                for (int v = 0; v < 2; ++v)
+#pragma unroll
+                  for (int u = 0; u < 2; ++u) res_term<true>(S, cmp, pxy[v][u], W[i + 2 * u][t + 2 * v]);
+                Sa[t][i] = S;
+                Ca[t][i] = cmp;
+              } else {
+                const int r = order >> 1;
+                float S = Sa[t][i], cmp = Ca[t][i];
+#pragma unroll
+                for (int u = 0; u < 2; ++u) {
+                  res_term<true>(S, cmp, two_sum(C[r][i + u][t], C[r][i + u][t + 1]), W[i + 2 * u][t + 1]);
+                  res_term<true>(S, cmp, two_sum(C[r][i][t + u], C[r][i + 1][t + u]), W[i + 1][t + 2 * u]);
+                }
+#pragma unroll
+                for (int q = 0; q < 2; ++q)
+#pragma unroll
+                  for (int p = 0; p < 2; ++p) res_term<true>(S, cmp, P2{C[r][i + p][t + q], 0.f}, W[i + 2 * p][t + 2 * q]);
+                Sa[t][i] = S;
+                Ca[t][i] = cmp;
+              }
+            }
+        }
+        constexpr double kH12 = 1.0 / (12.0 * N);
+        const float sch = (float)kH12, scl = (float)(kH12 - (double)(float)kH12);  // h/12 as an FP32 pair
+        const float2* rri = A.rr_in + s * A.rr_stride;
+        float2* rro = A.rr_out + s * kNodes;
+        float2* xo = A.xp + s * kNodes;
+#pragma unroll
+        for (int t = 0; t < RY; ++t) {
+#pragma unroll
+          for (int i = 0; i < RX; ++i) {
+            const bool ok = (okb >> (t * RX + i)) & 1u;
+            const long long g = gk + t * N1 + i;
+            const P2 axs = two_sum(Sa[t][i], Ca[t][i]);
+            const float pp = axs.h * sch;  // (A inc) as a pair (pp, pe)
+            const float pe = __fmaf_rn(axs.h, scl, __fmaf_rn(axs.l, sch, __fmaf_rn(axs.h, sch, -pp)));
+            const float2 bv = ok ? rri[g] : make_float2(0.f, 0.f);
+            const P2 dd = two_sum(bv.x, -pp);
+            const float e = dd.l + (bv.y - pe);
+            const float rh = dd.h + e;  // renormalised pair (rh, rl)
+            const float rl = e - (rh - dd.h);
+            const float rv = ok ? rh : 0.f;
+            out0[g] = rv;  // the next inner solve's FP32 residual
+            rro[g] = ok ? make_float2(rh, rl) : make_float2(0.f, 0.f);
+            red = fmaf(rv, rv, red);
+            const float inc = ctr[t][i];  // 0 off the interior
+            float2 xn = make_float2(inc, 0.f);
+            if (!A.assign) {  // pair addition: two-sum of the head and inc, renormalised
+              const float2 xv = xo[g];
+              const float sh = xv.x + inc;
+              const float bb = sh - xv.x;
+              const float se = (xv.x - (sh - bb)) + (inc - bb);
+              const float lo = xv.y + se;
+              const float h = sh + lo;
+              xn = make_float2(h, lo - (h - sh));
+            }
+            xo[g] = ok ? xn : make_float2(0.f, 0.f);
+          }
+        }
+      } else {
       // the operator plane by plane (k-1, k, k+1): one window of (RX+2) x (RY+2) operand
       // values live at a time; node (i, t) has cells c[p][q][r] = C[r][i + p][t + q] and
       // neighbour (du, dv) of the plane at window (i + 1 + du, t + 1 + dv)
@@ -504,8 +663,9 @@ __global__ void __launch_bounds__(256, 3) k_slab(SlabArgs A) {
           }
         }
       }
+      }  // not RES
     }
-    if ((kApply || kPost) && (k == kend || (k - 1) % kSegPlanes == kSegPlanes - 1)) {
+    if ((kApply || kPost || kRes) && (k == kend || (k - 1) % kSegPlanes == kSegPlanes - 1)) {
       const float b = block_sum(red);
       if (tid == 0) {
         const int per = gridDim.y * A.nseg;
@@ -546,7 +706,8 @@ TiledShape slab_shape(int N, int S, int zchunks) {
 }
 
 template <int N, typename TA, int MODE>
-static void run_slab(const char* cls, double bytes, SlabArgs args, const Batch& bt, cudaStream_t st) {
+static void run_slab(const char* cls, double bytes, SlabArgs args, const Batch& bt, cudaStream_t st,
+                     double ops = 0.0) {
   const TiledShape t = slab_shape(N, bt.S, bt.zchunks);
   args.nzc = t.nzc;
   args.zc = t.zc;
@@ -561,13 +722,15 @@ static void run_slab(const char* cls, double bytes, SlabArgs args, const Batch& 
                          cudaSharedmemCarveoutMaxShared);
     smem_set = true;
   }
-  launch(cls, bytes, k_slab<N, TA, MODE>, dim3(1, t.by, (unsigned)(bt.n * t.nzc)), dim3(256), smem, st, args);
+  launch_flops(cls, bytes, ops, k_slab<N, TA, MODE>, dim3(1, t.by, (unsigned)(bt.n * t.nzc)), dim3(256), smem, st,
+               args);
 }
 
 template <typename TA, int MODE>
-static void dispatch(int N, const char* cls, double bytes, SlabArgs args, const Batch& bt, cudaStream_t st) {
-  if (N == 64) run_slab<64, TA, MODE>(cls, bytes, args, bt, st);
-  else run_slab<32, TA, MODE>(cls, bytes, args, bt, st);
+static void dispatch(int N, const char* cls, double bytes, SlabArgs args, const Batch& bt, cudaStream_t st,
+                     double ops = 0.0) {
+  if (N == 64) run_slab<64, TA, MODE>(cls, bytes, args, bt, st, ops);
+  else run_slab<32, TA, MODE>(cls, bytes, args, bt, st, ops);
 }
 
 static double sbytes(int N, int n, double vec, double coef, size_t ta) {
@@ -585,6 +748,27 @@ void slab_apply(const float* z, const float* pold, float* pnew, const float* a, 
     dispatch<float, SL_APPLYX>(N, "apply_f32", sbytes(N, bt.n, x_first ? 5 : 6, 1, 4), A, bt, st);
   else
     dispatch<float, SL_APPLY>(N, "apply_f32", sbytes(N, bt.n, first ? 3 : 4, 1, 4), A, bt, st);
+}
+
+// FP32 operations per interior node of the refinement step as written (no sharing
+// between nodes): 12 exact cell-pair sums (6 each), the 8-cell sum (28), 21 compensated
+// product terms (11 each), the scaling and subtraction (16), r.r and the pair update of x (10)
+constexpr double kResOpsPerNode = 12 * 6 + 28 + 21 * 11 + 16 + 10;
+
+void slab_res(const float* d, const float* p, bool d_zero, const SolveScalars* sci, const float2* rr_in,
+              long long rr_stride, float2* rr_out, float2* x, bool assign, const float* a, float* r32,
+              double* partial, const SolveScalars* sco, int N, const Batch& bt, cudaStream_t st) {
+  SlabArgs A{};
+  A.in0 = d_zero ? p : d; A.in1 = p; A.a = a; A.out0 = r32; A.partial = partial; A.sc = sco; A.err = bt.err;
+  A.sci = sci; A.rr_in = rr_in; A.rr_stride = rr_stride; A.rr_out = rr_out; A.xp = x;
+  A.assign = assign ? 1 : 0;
+  A.dzero = d_zero ? 1 : 0;
+  const double nodes = (double)nodes_of(N);
+  // d (unless 0), p, the cells; the residual pairs in (once when shared) and out, r; x in (unless
+  // assigned) and out
+  const double bytes = sbytes(N, bt.n, d_zero ? 1 : 2, 1, 4) + (rr_stride ? bt.n : 1) * nodes * 8 +
+                       bt.n * nodes * (8 + 4 + (assign ? 8 : 16));
+  dispatch<float, SL_RES>(N, "resid64", bytes, A, bt, st, (double)bt.n * (N - 1) * (N - 1) * (N - 1) * kResOpsPerNode);
 }
 
 template <typename TA>

@@ -507,7 +507,8 @@ size_t solver_bytes(int N, int S, int elem) {
   }
   for (int j = 0; j <= J; ++j)
     if (tiled_level(N, j)) b += align_up((size_t)S * nodes_of(N >> j) * elem + kVecSlack);
-  if (elem == 4 && tiled_level(N, 0)) b += align_up((size_t)S * nodes_of(N) * sizeof(float2));
+  if (elem == 4 && tiled_level(N, 0)) b += align_up((size_t)S * nodes_of(N) * sizeof(float2)) +
+                                           align_up((size_t)nodes_of(N) * sizeof(float2));
   b += align_up((size_t)S * node_blocks(N) * sizeof(double));
   b += 2 * align_up((size_t)S * sizeof(SolveScalars));
   b += align_up(sizeof(int)) + align_up((size_t)S * sizeof(int));
@@ -532,6 +533,7 @@ void carve_solver(SolverBufs& B, int N, int S, int elem, char*& ptr) {
   for (int j = 0; j <= B.J; ++j)
     if (tiled_level(N, j)) B.dinv[j] = take((size_t)S * nodes_of(N >> j) * elem + kVecSlack);
   B.bdf = (elem == 4 && tiled_level(N, 0)) ? (float2*)take((size_t)S * nodes_of(N) * sizeof(float2)) : nullptr;
+  B.bsh = (elem == 4 && tiled_level(N, 0)) ? (float2*)take((size_t)nodes_of(N) * sizeof(float2)) : nullptr;
   B.partial = (double*)take((size_t)S * node_blocks(N) * sizeof(double));
   B.sc = (SolveScalars*)take((size_t)2 * S * sizeof(SolveScalars));
   B.count = (int*)take(sizeof(int));
@@ -825,11 +827,13 @@ static cudaError_t pcg_loop(SolverBufs& B, const TAop* aop, const TA0* a0, T* x,
 // double-buffered (neighbouring tiles read the old values in their halos).
 // x need not be initialised: the first iteration that updates it assigns.  Instead
 // of the last x += alpha p, the final update is fused with the refinement step into
-// x_out (+)= x + alpha p (k_finish_step; assign on the first refinement step).
+// x_out (+)= x + alpha p (k_finish_step; assign on the first refinement step), or,
+// with p_last, left to the next refinement step's pass (its p is returned there).
 // Runs over the samples the refinement left active (B.n_act, B.actp).
 static cudaError_t pcg_inner_fused(SolverBufs& B, const float* a32, const __nv_bfloat16* abf, float* x, float* r,
                                    SolveScalars* sc, const PcgParams& prm, int iters, cudaStream_t st,
-                                   float2* x_out, const SolveScalars* sco, bool assign_out) {
+                                   float2* x_out, const SolveScalars* sco, bool assign_out,
+                                   const float** p_last = nullptr) {
   const int S = B.S, N = B.N, n = B.n_act;
   const Batch bt = B.batch();
   const long long nodes = nodes_of(N);
@@ -852,6 +856,10 @@ static cudaError_t pcg_inner_fused(SolverBufs& B, const float* a32, const __nv_b
     pc ^= 1;
     scalar(B, sc, SM_ALPHA, 0, 0, st, napply);
     if (it == iters - 1) {
+      if (p_last) {  // the refinement step applies x (+)= x + alpha p itself
+        *p_last = pnew;
+        break;
+      }
       with_grid(N, [&](auto c) {
         launch("finish_step", (double)n * nodes * ((iters > 1 ? 4 : 0) + 4 + (assign_out ? 8 : 16)),
                k_finish_step<decltype(c)::value>, grid_nodes(N, n), kBlock, 0, st, x_out, (const float*)x,
@@ -959,17 +967,29 @@ cudaError_t ir_mixed(SolverBufs& B, const float* a32, const __nv_bfloat16* abf, 
   // in FP64 at the end), so the refinement loop executes no FP64 arithmetic.
   if (!tiled && (b_pair || pair_out)) return cudaErrorInvalidValue;  // pairs only on tiled grids
   float2* xdf = pair_out ? (float2*)x_out : (float2*)r64;
-  const float2* bdf = b_pair ? b_pair : B.bdf;
+  // b as pairs: given, or split by the init pass (per sample, or once when shared)
+  float2* bsplit = bstride ? B.bdf : B.bsh;
+  const float2* bdf = b_pair ? b_pair : bsplit;
+  // 32^3 and 64^3 grids: one slab pass per refinement step applies the inner solve's
+  // last update to x and updates the residual pairs rr (B.bdf; b on the first step) by
+  // rr -= A inc, so x is only written at nodes its block owns; its boundary nodes are
+  // cleared here, once
+  const bool sres = tiled && uses_slab(B, N, 4);
+  const float* p_last = nullptr;
+  if (sres) {
+    void* xb[1] = {xdf};
+    zero_boundary<double>(xb, 1, N, S, st);
+  }
   if (tiled) {
     const dim3 gi((unsigned)init_blocks(N), (unsigned)S);
     with_grid(N, [&](auto c) {
       constexpr int NN = decltype(c)::value;
       if (b_pair)
         launch("init_f32", bb + nbytes<float, float>(N, S, 1, 0), k_init32<true, NN>, gi, kBlock, 0, st, b, b_pair,
-               bstride, r32, B.bdf, B.partial, nodes, N);
+               bstride, r32, bsplit, B.partial, nodes, N);
       else
         launch("init_f32", bb + nbytes<float, float>(N, S, 1, 0) + (double)(bstride ? S : 1) * nodes * 8,
-               k_init32<false, NN>, gi, kBlock, 0, st, b, b_pair, bstride, r32, B.bdf, B.partial, nodes, N);
+               k_init32<false, NN>, gi, kBlock, 0, st, b, b_pair, bstride, r32, bsplit, B.partial, nodes, N);
     });
     scalar(B, sco, SM_INIT, 0, 0, st, init_blocks(N));
   } else {
@@ -980,7 +1000,11 @@ cudaError_t ir_mixed(SolverBufs& B, const float* a32, const __nv_bfloat16* abf, 
   for (int step = 0;; ++step) {
     if (step > 0) {
       const int cap = fixed_steps > 0 ? fixed_steps : prm.max_iter;
-      if (tiled) {
+      if (sres) {
+        slab_res(d, p_last, inner_iters <= 1, sci, step == 1 ? bdf : B.bdf, step == 1 ? bstride : nodes, B.bdf, xdf,
+                 step == 1, a32, r32, B.partial, sco, N, B.batch(), st);
+        scalar(B, sco, SM_OUTER_CONV, tol2, cap, st, tiled_blocks_per_sample(N, S, 4, true));
+      } else if (tiled) {
         tiled_res64(bdf, bstride, xdf, a32, r32, B.partial, sco, N, B.batch(), st);
         scalar(B, sco, SM_OUTER_CONV, tol2, cap, st, tiled_blocks_per_sample(N, S, 8, false));
       } else {
@@ -1005,7 +1029,8 @@ cudaError_t ir_mixed(SolverBufs& B, const float* a32, const __nv_bfloat16* abf, 
              (const SolveScalars*)sco, nodes, B.actp);
     scalar(B, sci, SM_INNER_BEGIN, 0, 0, st, nb, 0, sco);
     if (tiled) {
-      e = pcg_inner_fused(B, a32, abf, d, r32, sci, prm, inner_iters, st, xdf, sco, step == 0);
+      e = pcg_inner_fused(B, a32, abf, d, r32, sci, prm, inner_iters, st, xdf, sco, step == 0,
+                          sres ? &p_last : nullptr);
       if (e != cudaSuccess) return e;
     } else {
       e = pcg_loop<float, float, __nv_bfloat16>(B, a32, abf, d, r32, sci, prm, inner_iters, st);
