@@ -353,6 +353,41 @@ struct CellInterp {
   }
 };
 
+// The same trilinear average for FP32 pair fields with the weights kept as three
+// per-axis pairs (exact dyadic values, so each product equals CellInterp's w32) and a
+// 32-bit node index: fewer registers per thread, so more threads in flight.
+struct PairInterp {
+  int base, sy, sz;
+  float wx[2], wy[2], wz[2];
+  __device__ void setup(int N, int Nc, int cx, int cy, int cz) {
+    const int n1 = N + 1, r = Nc / N;
+    const float ir = 1.0f / (float)r;  // r a power of two: exact
+    const float tx = ((cx % r) + 0.5f) * ir, ty = ((cy % r) + 0.5f) * ir, tz = ((cz % r) + 0.5f) * ir;
+    wx[0] = 1.0f - tx; wx[1] = tx;
+    wy[0] = 1.0f - ty; wy[1] = ty;
+    wz[0] = 1.0f - tz; wz[1] = tz;
+    base = (cx / r) + n1 * ((cy / r) + n1 * (cz / r));
+    sy = n1;
+    sz = n1 * n1;
+  }
+  __device__ __forceinline__ DF eval(const float2* __restrict__ q) const {
+    const float2* b = q + base;
+    float s = 0.f, c = 0.f;
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+      const float w = (wx[e & 1] * wy[(e >> 1) & 1]) * wz[e >> 2];
+      const float2 v = b[(e & 1) + ((e >> 1) & 1) * sy + (e >> 2) * sz];
+      const float p = w * v.x;
+      const float pe = __fmaf_rn(w, v.y, __fmaf_rn(w, v.x, -p));
+      const float t = s + p;
+      const float bb = t - s;
+      c += ((s - (t - bb)) + (p - bb)) + pe;
+      s = t;
+    }
+    return df_norm(s, c);
+  }
+};
+
 // eval_at_ctrl for an FP32 pair field, in pair arithmetic (trapezoid weights are
 // exact in FP32 since r is a power of two)
 __device__ DF eval_at_ctrl(const float2* __restrict__ q, int N, int Nc, int cx, int cy, int cz) {
@@ -393,6 +428,19 @@ __device__ __forceinline__ double ctrl_avg(const CellInterp& I, bool fast, const
                                            int cy, int cz) {
   return fast ? I.eval(q) : eval_at_ctrl(q, N, Nc, cx, cy, cz);
 }
+// FP32 -> FP64 by moving the fields (IEEE 754 binary32 and binary64 layouts), in
+// integer instructions instead of the FP64 conversion: exponent rebiased by
+// 1023 - 127, mantissa shifted into the top of the 52-bit field; 0 and subnormals
+// give a signed 0, Inf and NaN keep their class (a NaN stays a NaN).
+__device__ __forceinline__ double f2d(float f) {
+  const uint32_t u = __float_as_uint(f);
+  const uint32_t e = (u >> 23) & 0xffu, m = u & 0x7fffffu;
+  const uint32_t e11 = e == 0u ? 0u : (e == 0xffu ? 0x7ffu : e + 896u);
+  const uint32_t mh = e == 0u ? 0u : ((m >> 3) | ((e == 0xffu && m != 0u) ? 0x80000u : 0u));
+  const uint32_t hi = (u & 0x80000000u) | (e11 << 20) | mh;
+  const uint32_t lo = e == 0u ? 0u : (m << 29);
+  return __hiloint2double((int)hi, (int)lo);
+}
 __device__ __forceinline__ DF ctrl_avg_df(const CellInterp& I, bool fast, const float2* q, int N, int Nc, int cx,
                                           int cy, int cz) {
   return fast ? I.eval(q) : eval_at_ctrl(q, N, Nc, cx, cy, cz);
@@ -401,7 +449,7 @@ __device__ __forceinline__ double ctrl_avg(const CellInterp& I, bool fast, const
                                            int cy, int cz) {
   return df_to_double(ctrl_avg_df(I, fast, q, N, Nc, cx, cy, cz));
 }
-template <bool PF, bool PC>
+template <bool PF, bool PC, bool FAST = false>
 __global__ void k_level_field(const void* __restrict__ qf_, int Nf, const void* __restrict__ qc_, int Ncs, int S,
                               int Nc, const double* __restrict__ work, double* __restrict__ field,
                               double* __restrict__ partial) {
@@ -421,17 +469,36 @@ __global__ void k_level_field(const void* __restrict__ qf_, int Nf, const void* 
     const float2* wcp = wfp + S;
     // level grids no finer than the control grid: weights hoisted out of the sample loop
     const bool fast_f = Nf <= Nc, fast_c = !qc || Ncs <= Nc;
+    double ref = 0.0, sd = 0.0, sd2 = 0.0;
+    if constexpr (PF && PC && FAST) {  // both grids no finer than the control grid
+      PairInterp Pf{}, Pc{};
+      Pf.setup(Nf, Nc, cx, cy, cz);
+      Pc.setup(Ncs, Nc, cx, cy, cz);
+      // sample pointers advanced by addition: a 64-bit multiply per sample would issue
+      // on the FP64 pipe of this part, the kernel's bottleneck
+      const QF* qfs = qf;
+      const QC* qcs = qc;
+      for (int s = 0; s < S; ++s, qfs += nf, qcs += ncn) {
+        const DF vf = df_mul(df_make(wfp[s]), Pf.eval(qfs));
+        const DF vc = df_mul(df_make(wcp[s]), Pc.eval(qcs));
+        const DF vd = df_add(vf, df_neg(vc));
+        const double v = f2d(vd.h) + f2d(vd.l);
+        if (s == 0) ref = v;
+        const double d = v - ref;
+        sd += d;
+        sd2 = fma(d, d, sd2);
+      }
+    } else {
     CellInterp If{}, Ic{};
     if (fast_f) If.setup(Nf, Nc, cx, cy, cz);
     if (qc && fast_c) Ic.setup(Ncs, Nc, cx, cy, cz);
-    double ref = 0.0, sd = 0.0, sd2 = 0.0;
-#pragma unroll 2
     for (int s = 0; s < S; ++s) {
       double v;
       if constexpr (PF && PC) {
         const DF vf = df_mul(df_make(wfp[s]), ctrl_avg_df(If, fast_f, qf + s * nf, Nf, Nc, cx, cy, cz));
         const DF vc = df_mul(df_make(wcp[s]), ctrl_avg_df(Ic, fast_c, qc + s * ncn, Ncs, Nc, cx, cy, cz));
-        v = df_to_double(df_add(vf, df_neg(vc)));
+        const DF vd = df_add(vf, df_neg(vc));
+        v = f2d(vd.h) + f2d(vd.l);
       } else {
         v = wf[s] * ctrl_avg(If, fast_f, qf + s * nf, Nf, Nc, cx, cy, cz);
         if (qc) v = fma(-wc[s], ctrl_avg(Ic, fast_c, qc + s * ncn, Ncs, Nc, cx, cy, cz), v);
@@ -440,6 +507,7 @@ __global__ void k_level_field(const void* __restrict__ qf_, int Nf, const void* 
       const double d = v - ref;
       sd += d;
       sd2 = fma(d, d, sd2);
+    }
     }
     const double mean = ref + sd / S;
     const double m2 = fmax(sd2 - sd * (sd / S), 0.0);
@@ -693,12 +761,14 @@ void launch_level_stats(const double* qf, const double* phif, int Nf, const doub
   const int nblk = (int)((ncell + kBlock - 1) / kBlock);
   const double qbytes = (double)S * 8 * (nodes_of(Nf) + (qc ? nodes_of(Ncoarse) : 0));
   // pairs on the coarse grid only come with pairs on the fine grid (it is at least as large)
-  auto lf = qf_pairs ? (qc_pairs ? k_level_field<true, true> : k_level_field<true, false>)
+  const bool fast = Nf <= Nc && (!qc || Ncoarse <= Nc);
+  auto lf = qf_pairs ? (qc_pairs ? (fast ? k_level_field<true, true, true> : k_level_field<true, true>)
+                                 : k_level_field<true, false>)
                      : k_level_field<false, false>;
   // FP64 operations per control cell and sample: both grids in pairs, the pair value
   // to FP64 (2 conversions, 1 add), its deviation and the two sums; otherwise also the
   // FP64 weighting and, for FP64 fields, the 8-node averages
-  const double f64ops = qf_pairs && qc_pairs ? 6.0 : (qf_pairs ? 16.0 : 21.0);
+  const double f64ops = qf_pairs && qc_pairs ? (fast ? 4.0 : 6.0) : (qf_pairs ? 16.0 : 21.0);
   launch_flops("level_field", qbytes + (double)ncell * 16, (double)S * ncell * f64ops, lf, dim3(nblk), kBlock, 0, st,
                (const void*)qf, Nf, (const void*)qc, Ncoarse, S, Nc, (const double*)work, field, partial);
   launch("level_finish", 0.0, k_level_finish, dim3(1), 32, 0, st, (const double*)partial, nblk, (const double*)work,

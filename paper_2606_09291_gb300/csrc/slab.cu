@@ -129,7 +129,9 @@ struct SlabSmem {
   static constexpr int NV = (MODE == SL_PREU) ? 3 : 2;  // staged node vectors
   static constexpr bool kPost = MODE == SL_POST;
   static constexpr int SV = short_vec(MODE);             // the vector with a 3-slot ring (or -1)
-  static constexpr int slots(int v) { return v == SV ? kRing - 1 : kRing; }
+  // RES reads its staged vectors only when deriving (its epilogue reads the operand
+  // plane), so both of them take 3-slot rings
+  static constexpr int slots(int v) { return (v == SV || MODE == SL_RES) ? kRing - 1 : kRing; }
   static constexpr int first_slot(int v) { return v == 0 ? 0 : first_slot(v - 1) + slots(v - 1); }
   static constexpr size_t raw = 0;
   static constexpr size_t cells = raw + sizeof(float) * first_slot(NV) * G::RAWF;
@@ -138,7 +140,9 @@ struct SlabSmem {
   static constexpr size_t xs = craw + (kPost ? sizeof(float) * 3 * G::CRAWF : 0);
   static constexpr size_t eps = xs + sizeof(float) * 3 * G::XPL;
   static constexpr size_t bar = eps + (kPost ? sizeof(float) * 2 * G::XPL : 0);
-  static constexpr size_t total = bar + 8 * kRing;
+  // RES: x of the thread's own nodes for the plane being computed, copied ahead
+  static constexpr size_t xpre = (bar + 8 * kRing + 15) / 16 * 16;
+  static constexpr size_t total = xpre + (MODE == SL_RES ? sizeof(float2) * 256 * G::RX * G::RY : 0);
   static_assert(cells % 16 == 0 && craw % 16 == 0 && cellb % 16 == 0 && xs % 16 == 0 && bar % 8 == 0, "align");
 };
 
@@ -155,6 +159,13 @@ __device__ __forceinline__ void bulk_copy(uint32_t dst, const void* src, uint32_
                "l"(src), "r"(bytes), "r"(bar)
                : "memory");
 }
+// 8-byte asynchronous copy into shared memory (the thread waits for its own copies)
+__device__ __forceinline__ void cp_async8(void* dst, const void* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
 // bounded wait for phase `parity` of the barrier; false after about a second
 __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
   const long long t0 = clock64();
@@ -200,6 +211,7 @@ __global__ void __launch_bounds__(256, 3) k_slab(SlabArgs A) {
   float* craw = (float*)(sm + L::craw);  // [3][CRAWF]
   float* xs = (float*)(sm + L::xs);    // [3][XPL]
   float* eps = (float*)(sm + L::eps);  // [2][XPL]
+  float2* xpre = (float2*)(sm + L::xpre) + threadIdx.x * (G::RX * G::RY);  // RES: this thread's nodes
   const uint32_t bar0 = smem_u32(sm + L::bar);
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -435,6 +447,14 @@ __global__ void __launch_bounds__(256, 3) k_slab(SlabArgs A) {
     const long long gk = (long long)k * N1 * N1 + gown;
     const int xkp = xk == 2 ? 0 : xk + 1, xkm = xk == 0 ? 2 : xk - 1;
     const int jk3p = jk3 == 2 ? 0 : jk3 + 1;
+    if (kRes && !A.assign) {  // x of the own nodes, consumed by this plane's epilogue
+      const float2* xs_g = A.xp + s * kNodes + gk;
+#pragma unroll
+      for (int t = 0; t < RY; ++t)
+#pragma unroll
+        for (int i = 0; i < RX; ++i) cp_async8(xpre + t * RX + i, xs_g + t * N1 + i);
+      cp_async_commit();
+    }
     float xv[RY][RX];
     if (MODE == SL_APPLYX) {
 #pragma unroll
@@ -539,6 +559,7 @@ __global__ void __launch_bounds__(256, 3) k_slab(SlabArgs A) {
         const float2* rri = A.rr_in + s * A.rr_stride;
         float2* rro = A.rr_out + s * kNodes;
         float2* xo = A.xp + s * kNodes;
+        if (!A.assign) cp_async_wait_all();
 #pragma unroll
         for (int t = 0; t < RY; ++t) {
 #pragma unroll
@@ -560,7 +581,7 @@ __global__ void __launch_bounds__(256, 3) k_slab(SlabArgs A) {
             const float inc = ctr[t][i];  // 0 off the interior
             float2 xn = make_float2(inc, 0.f);
             if (!A.assign) {  // pair addition: two-sum of the head and inc, renormalised
-              const float2 xv = xo[g];
+              const float2 xv = xpre[t * RX + i];
               const float sh = xv.x + inc;
               const float bb = sh - xv.x;
               const float se = (xv.x - (sh - bb)) + (inc - bb);

@@ -261,6 +261,49 @@ __global__ void k_restrict(const T* __restrict__ tf, T* __restrict__ rc, const S
   rc[s * nc + n] = v;
 }
 
+// The same restriction marching in z: one thread per coarse node column (I, J) and
+// chunk of kRestrictPlanes coarse planes (blockIdx.z); the xy-weighted sum of fine
+// plane 2K+1 serves coarse planes K and K+1, so a coarse node reads 18 fine values
+// instead of 27.  rc holds 0 on the coarse boundary.
+constexpr int kRestrictPlanes = 8;
+template <typename T, int NCC>
+__global__ void k_restrict_zm(const T* __restrict__ tf, T* __restrict__ rc, const SolveScalars* __restrict__ sc,
+                              const int* __restrict__ act) {
+  SAMPLE_GUARD(sc);
+  constexpr int Nc = NCC, n1c = Nc + 1, n1f = 2 * Nc + 1;
+  constexpr long long nc = (long long)n1c * n1c * n1c, nf = (long long)n1f * n1f * n1f;
+  const int col = blockIdx.x * blockDim.x + threadIdx.x;
+  if (col >= n1c * n1c) return;
+  const int I = col % n1c, J = col / n1c;
+  const int K0 = kRestrictPlanes * (int)blockIdx.z, K1 = min(Nc, K0 + kRestrictPlanes - 1);
+  T* out = rc + s * nc + col;
+  if (I == 0 || J == 0 || I == Nc || J == Nc) {
+    for (int K = K0; K <= K1; ++K) out[K * (n1c * n1c)] = T(0);
+    return;
+  }
+  const T* f = tf + s * nf + 2 * I + (long long)n1f * (2 * J);
+  auto rxy = [&](int k) {  // sum over the 3 x 3 fine nodes around (2I, 2J) of fine plane k
+    const T* p = f + (long long)n1f * n1f * k;
+    T v = T(0);
+#pragma unroll
+    for (int u = -1; u <= 1; ++u)
+#pragma unroll
+      for (int q = -1; q <= 1; ++q) v += T((q == 0 ? 1.0 : 0.5) * (u == 0 ? 1.0 : 0.5)) * p[q + n1f * u];
+    return v;
+  };
+  T prev = K0 > 0 ? rxy(2 * K0 - 1) : T(0);
+  for (int K = K0; K <= K1; ++K) {
+    if (K == 0 || K == Nc) {
+      out[K * (n1c * n1c)] = T(0);
+      if (K == 0) prev = rxy(1);
+      continue;
+    }
+    const T mid = rxy(2 * K), up = rxy(2 * K + 1);
+    out[K * (n1c * n1c)] = T(0.5) * prev + mid + T(0.5) * up;
+    prev = up;
+  }
+}
+
 // fine += P coarse (trilinear)
 template <typename T>
 __global__ void k_prolong_add(T* __restrict__ xf, const T* __restrict__ ec, const SolveScalars* __restrict__ sc,
@@ -308,21 +351,28 @@ __global__ void k_coarsest(const T* __restrict__ r, const TA* __restrict__ a, T*
 
 // coarse cell coefficient = mean of the 8 children
 template <typename TI, typename TO>
-__global__ void k_coarsen_coef(const TI* __restrict__ af, TO* __restrict__ ac, int Nc, int S) {
-  const long long cc = (long long)Nc * Nc * Nc;
-  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= cc * S) return;
-  const int s = (int)(idx / cc);
-  const long long c = idx % cc;
-  const int I = (int)(c % Nc), J = (int)((c / Nc) % Nc), K = (int)(c / ((long long)Nc * Nc));
+// (one thread per coarse cell of a sample, blockIdx.y the sample).  The mixed path's
+// FP32 levels sum in FP32: the eight BF16 children of the first coarsening sum exactly
+// (8-bit significands, the coefficient's range spans well under 16 binary orders), and
+// the coarse coefficients only shape the preconditioner; the FP64 path sums in FP64.
+__global__ void k_coarsen_coef(const TI* __restrict__ af, TO* __restrict__ ac, int Nc) {
+  using Acc = typename std::conditional<std::is_same<TO, double>::value, double, float>::type;
+  const int cc = Nc * Nc * Nc;
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= cc) return;
+  const int s = blockIdx.y;
+  const unsigned t = (unsigned)c / (unsigned)Nc;
+  const int I = c - (int)t * Nc, K = (int)(t / (unsigned)Nc), J = (int)t - K * Nc;
   const int Nf = 2 * Nc;
-  const TI* f = af + (long long)s * Nf * Nf * Nf;
-  double acc = 0.0;
+  const TI* f = af + (long long)s * Nf * Nf * Nf + 2 * I + Nf * (2 * J + Nf * 2 * K);
+  Acc acc = Acc(0);
+#pragma unroll
   for (int r = 0; r < 2; ++r)
+#pragma unroll
     for (int q = 0; q < 2; ++q)
-      for (int p = 0; p < 2; ++p)
-        acc += to_double(f[(2 * I + p) + (long long)Nf * ((2 * J + q) + (long long)Nf * (2 * K + r))]);
-  ac[idx] = (TO)(0.125 * acc);
+#pragma unroll
+      for (int p = 0; p < 2; ++p) acc += smem_coef<Acc>(f[p + Nf * (q + Nf * r)]);
+  ac[(long long)s * cc + c] = (TO)(Acc(0.125) * acc);
 }
 
 // ---------------------------------------------------------------- mixed-precision kernels
@@ -564,8 +614,10 @@ static const char* cls(const char* base, bool fine) {
 // post-smoothing read the same values, so the V-cycle stays symmetric).
 __device__ __forceinline__ double recip(double x) { return 1.0 / x; }
 __device__ __forceinline__ float recip(float x) { return __fdividef(1.0f, x); }
-// One thread per node column (i, j) marching in z: the four cells of the column
-// below a node are summed once and reused by the node above.
+// One thread per node column (i, j) and chunk of kDinvPlanes planes (blockIdx.z),
+// marching in z: the four cells of the column below a node are summed once and
+// reused by the node above (the chunk's first node sums both).
+constexpr int kDinvPlanes = 8;
 template <typename T, typename TA>
 __global__ void k_dinv(const TA* __restrict__ a, T* __restrict__ dinv, int N, T omega) {
   const int s = blockIdx.y;
@@ -574,24 +626,28 @@ __global__ void k_dinv(const TA* __restrict__ a, T* __restrict__ dinv, int N, T 
   if (col >= n1 * n1) return;
   const int i = col % n1, j = col / n1;
   const long long plane = (long long)n1 * n1;
+  const int k0 = 1 + kDinvPlanes * (int)blockIdx.z, k1 = min(N - 1, k0 + kDinvPlanes - 1);
   T* out = dinv + s * plane * n1 + col;
-  out[0] = T(0);
-  out[N * plane] = T(0);
+  if (blockIdx.z == 0) out[0] = T(0);
+  if (k1 == N - 1) out[N * plane] = T(0);
   if (i == 0 || j == 0 || i == N || j == N) {
-    for (int k = 1; k < N; ++k) out[k * plane] = T(0);
+    T* o = out + (long long)k0 * plane;
+    for (int k = k0; k <= k1; ++k, o += plane) *o = T(0);
     return;
   }
-  const long long cpl = (long long)N * N;
-  const TA* ac = a + s * cpl * N + (i - 1) + (long long)N * (j - 1);
-  auto sum4 = [&](int c) {
-    const TA* p = ac + cpl * c;
+  const int cpl = N * N;
+  // pointers advanced by addition (64-bit multiplies issue on the FP64 pipe here)
+  const TA* ac = a + (long long)s * cpl * N + (i - 1) + N * (j - 1) + (long long)(k0 - 1) * cpl;
+  auto sum4 = [&](const TA* p) {
     return (load_coef<T>(p) + load_coef<T>(p + 1)) + (load_coef<T>(p + N) + load_coef<T>(p + N + 1));
   };
   const T h3 = T(1.0 / (3.0 * N));
-  T below = sum4(0);
-  for (int k = 1; k < N; ++k) {
-    const T above = sum4(k);
-    out[k * plane] = omega * recip(h3 * (below + above));
+  T below = sum4(ac);
+  T* o = out + (long long)k0 * plane;
+  for (int k = k0; k <= k1; ++k, o += plane) {
+    ac += cpl;
+    const T above = sum4(ac);
+    *o = omega * recip(h3 * (below + above));
     below = above;
   }
 }
@@ -601,7 +657,8 @@ static void build_dinv(SolverBufs& B, const TA0* a0, double omega, cudaStream_t 
   for (int j = 0; j <= B.J; ++j) {
     if (!B.dinv[j]) continue;
     const int Nj = B.N >> j;
-    const dim3 g((unsigned)(((Nj + 1) * (Nj + 1) + kBlock - 1) / kBlock), (unsigned)B.S);
+    const dim3 g((unsigned)(((Nj + 1) * (Nj + 1) + kBlock - 1) / kBlock), (unsigned)B.S,
+                 (unsigned)((Nj - 1 + kDinvPlanes - 1) / kDinvPlanes));
     if (j == 0)
       launch("dinv", nbytes<T, TA0>(Nj, B.S, 1, 1), k_dinv<T, TA0>, g, kBlock, 0, st, a0, (T*)B.dinv[0], Nj,
              (T)omega);
@@ -616,13 +673,13 @@ static void coarsen_all(SolverBufs& B, const TI* a0, cudaStream_t st) {
   for (int j = 1; j <= B.J; ++j) {
     const int Nc = B.N >> j;
     const long long n = cells_of(Nc) * B.S;
-    const dim3 g((unsigned)((n + 255) / 256));
+    const dim3 g((unsigned)((cells_of(Nc) + 255) / 256), (unsigned)B.S);
     if (j == 1)
       launch("coarsen", (double)n * (8 * sizeof(TI) + sizeof(TO)), k_coarsen_coef<TI, TO>, g, 256, 0, st, a0,
-             (TO*)B.acoef[1], Nc, B.S);
+             (TO*)B.acoef[1], Nc);
     else
       launch("coarsen", (double)n * 9 * sizeof(TO), k_coarsen_coef<TO, TO>, g, 256, 0, st, (const TO*)B.acoef[j - 1],
-             (TO*)B.acoef[j], Nc, B.S);
+             (TO*)B.acoef[j], Nc);
   }
 }
 void build_hierarchy_fp64(SolverBufs& B, const double* a64, double omega, cudaStream_t st) {
@@ -680,9 +737,18 @@ static int vcycle(SolverBufs& B, const T* r0, const TA0* a0, const SolveScalars*
              st, rin(j), (const T*)B.vx[j], aj, (T*)B.vt[j], sc, Nj, omega, act);
     }
     with_grid(Nj / 2, [&](auto c) {
-      launch(cls<T>("restrict", fine), nbytes<T, T>(Nj, n, 1, 0) + nbytes<T, T>(Nj / 2, n, 1, 0),
-             k_restrict<T, decltype(c)::value>, grid_nodes(Nj / 2, n), kBlock, 0, st, (const T*)B.vt[j],
-             (T*)B.vr[j + 1], sc, Nj / 2, act);
+      constexpr int NCC = decltype(c)::value;
+      const double rb = nbytes<T, T>(Nj, n, 1, 0) + nbytes<T, T>(Nj / 2, n, 1, 0);
+      if constexpr (NCC >= 32) {  // on smaller grids the per-node kernel has more threads in flight
+        const int n1c = Nj / 2 + 1;
+        const dim3 gr((unsigned)((n1c * n1c + kBlock - 1) / kBlock), (unsigned)n,
+                      (unsigned)((Nj / 2 + kRestrictPlanes) / kRestrictPlanes));
+        launch(cls<T>("restrict", fine), rb, k_restrict_zm<T, NCC>, gr, kBlock, 0, st, (const T*)B.vt[j],
+               (T*)B.vr[j + 1], sc, act);
+      } else {
+        launch(cls<T>("restrict", fine), rb, k_restrict<T, NCC>, grid_nodes(Nj / 2, n), kBlock, 0, st,
+               (const T*)B.vt[j], (T*)B.vr[j + 1], sc, Nj / 2, act);
+      }
     });
   }
   if (jc < J) {
@@ -984,12 +1050,21 @@ cudaError_t ir_mixed(SolverBufs& B, const float* a32, const __nv_bfloat16* abf, 
     const dim3 gi((unsigned)init_blocks(N), (unsigned)S);
     with_grid(N, [&](auto c) {
       constexpr int NN = decltype(c)::value;
-      if (b_pair)
+      if (b_pair) {
         launch("init_f32", bb + nbytes<float, float>(N, S, 1, 0), k_init32<true, NN>, gi, kBlock, 0, st, b, b_pair,
                bstride, r32, bsplit, B.partial, nodes, N);
-      else
-        launch("init_f32", bb + nbytes<float, float>(N, S, 1, 0) + (double)(bstride ? S : 1) * nodes * 8,
-               k_init32<false, NN>, gi, kBlock, 0, st, b, b_pair, bstride, r32, bsplit, B.partial, nodes, N);
+      } else if (bstride) {
+        launch("init_f32", bb + nbytes<float, float>(N, S, 1, 0) + (double)S * nodes * 8, k_init32<false, NN>, gi,
+               kBlock, 0, st, b, b_pair, bstride, r32, bsplit, B.partial, nodes, N);
+      } else {
+        // a b shared by every sample is split into pairs once (sample 0's launch), and
+        // every sample's FP32 residual and b.b then come from the pairs in FP32
+        const dim3 g1((unsigned)init_blocks(N), 1u);
+        launch("init_f32", (double)nodes * 20, k_init32<false, NN>, g1, kBlock, 0, st, b, b_pair, bstride, r32, bsplit,
+               B.partial, nodes, N);
+        launch("init_f32", (double)nodes * 8 + nbytes<float, float>(N, S, 1, 0), k_init32<true, NN>, gi, kBlock, 0, st,
+               b, (const float2*)bsplit, bstride, r32, bsplit, B.partial, nodes, N);
+      }
     });
     scalar(B, sco, SM_INIT, 0, 0, st, init_blocks(N));
   } else {
