@@ -52,7 +52,9 @@ def workload_cfg(args):
     if args.precision == "mixed" and not getattr(args, "no_tuned", False):
         knobs = autotune.lookup(cfg, p["level"], args.samples)
         if knobs:
-            cfg.update(knobs)
+            if args.ir_steps:  # an explicit --ir-steps wins over the tuned schedule
+                knobs["ir_steps"] = args.ir_steps
+            cfg = autotune.context_cfg(cfg, knobs, args.samples)
     return cfg
 
 
@@ -488,9 +490,10 @@ def parser():
                     help="samples per step of the plain FP64 leg (same batch as the mixed arm by default)")
     ap.add_argument("--fp64-steps", type=int, default=3)
     ap.add_argument("--fp64-chunk", type=int, default=1024, help="FP64 leg: samples per internal chunk")
-    ap.add_argument("--cpu-samples", type=int, default=6)
+    ap.add_argument("--cpu-samples", type=int, default=12, help="oracle samples of the one-thread leg (about 11 s)")
     ap.add_argument("--ref-samples", type=int, default=1, help="oracle samples per process per reference step")
-    ap.add_argument("--cpu-pool-samples", type=int, default=2, help="oracle samples per process, all-cores leg")
+    ap.add_argument("--cpu-pool-samples", type=int, default=8,
+                    help="oracle samples per process, all-cores leg (about 10 s)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ir-steps", type=int, default=0,
                     help="mixed path: 0 = refine until converged, launching only the samples still above rtol "

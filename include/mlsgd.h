@@ -100,6 +100,9 @@ typedef struct {
   int z_chunks;     /* z chunks the fused passes split a sample into (0 = chosen from the
                        batch size); results do not depend on it                          */
   double omega;     /* damping of the Jacobi smoother in the V-cycle (0 = 0.6; (0, 1))    */
+  int inner_iters_next; /* MIXED only: FP32 PCG iterations of the refinement steps after the
+                           first, which start from a residual already reduced by it
+                           (0 = inner_iters)                                               */
 } mlsgd_config;
 
 typedef struct mlsgd_ctx mlsgd_ctx;

@@ -5,16 +5,21 @@ converged solve returns beyond the solver tolerance (the level record stays
 within the mixed path's 1e-6 of the oracle for every choice; tests/
 test_gpu_autotune.py checks each one):
 
-* stencil     0 = whole-row slab passes on 32^3 / 64^3 grids, 1 = z-marching tiles
-* z_chunks    z chunks per sample in the fused passes (0 = chosen from the batch)
-* inner_iters FP32 PCG iterations per refinement step
-* omega       damping of the Jacobi smoother of the V-cycle
+* stencil      0 = whole-row slab passes on 32^3 / 64^3 grids, 1 = z-marching tiles
+* z_chunks     z chunks per sample in the fused passes (0 = chosen from the batch)
+* batch_chunks the level batch is solved in this many sequential sub-batches
+               (the context's max_batch = ceil(S / batch_chunks))
+* inner_iters  FP32 PCG iterations per refinement step
+* omega        damping of the Jacobi smoother of the V-cycle
+* ir_steps     0 = refine until every sample converges (host check per step, the
+               still-active samples compacted); k > 0 = exactly k masked steps
+               (no host round trip; rejected when a sample is left unconverged)
 
 Search: time candidate configurations on a probe batch of the level with CUDA
 events (one warm-up call, then `reps` timed calls of mlsgd_level_gradient), keep
 only candidates whose solves all converge, and go coordinate-wise: launch shape
-(stencil x z_chunks) first, then the smoother schedule (inner_iters x omega) at
-the best shape.  The cost is time per converged sample-gradient.  Winners are
+(stencil x z_chunks x batch_chunks) first, then the solver schedule (inner_iters x
+omega x ir_steps) at the best shape.  The cost is time per converged sample-gradient.  Winners are
 stored per (grid, batch size, precision, modes) in a JSON cache; a cached entry is
 returned as is, so a run is deterministic given its cache.  The paper's own
 analogue is choosing the batch width per level by memory and cost (Sec. 4.2,
@@ -32,10 +37,10 @@ import torch
 
 from . import mlsgd
 
-KNOBS = ("stencil", "z_chunks", "inner_iters", "omega")
-DEFAULTS = dict(stencil=0, z_chunks=0, inner_iters=6, omega=0.6)
-SHAPES = dict(stencil=(0, 1), z_chunks=(0, 1, 2, 4))
-SCHEDULES = dict(inner_iters=(4, 5, 6, 7, 8), omega=(0.5, 0.6, 0.7))
+KNOBS = ("stencil", "z_chunks", "batch_chunks", "inner_iters", "omega", "ir_steps")
+DEFAULTS = dict(stencil=0, z_chunks=0, batch_chunks=1, inner_iters=6, omega=0.6, ir_steps=0)
+SHAPES = dict(stencil=(0, 1), z_chunks=(0, 1, 2, 4), batch_chunks=(1, 2, 4))
+SCHEDULES = dict(inner_iters=(4, 5, 6, 7, 8), omega=(0.5, 0.6, 0.7), ir_steps=(0, 2, 3))
 CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "tuned.json")
 
 
@@ -54,18 +59,25 @@ def load_cache(path=CACHE):
         return {}
 
 
+def context_cfg(base_cfg, knobs, n_samples):
+    """The context configuration of base_cfg with the knobs applied to batches of
+    n_samples (knobs missing from an older cache entry take their defaults)."""
+    k = dict(DEFAULTS, **knobs)
+    cfg = dict(base_cfg)
+    cfg.update({name: k[name] for name in KNOBS if name != "batch_chunks"})
+    cfg["max_batch"] = max(1, -(-n_samples // k["batch_chunks"]))
+    return cfg
+
+
 def lookup(cfg, level, n_samples, path=CACHE):
-    """The tuned knobs for this batch, or None (no entry: use DEFAULTS)."""
+    """The tuned knobs for this batch (all of KNOBS), or None (no entry: use DEFAULTS)."""
     e = load_cache(path).get(key(cfg, level, n_samples))
-    return dict(e["knobs"]) if e else None
+    return dict(DEFAULTS, **e["knobs"]) if e else None
 
 
 def measure(base_cfg, knobs, level, n_samples, z, reps=2, it0=1000):
     """ms per sample-gradient of knobs on a batch of n_samples, and whether every solve converged."""
-    cfg = dict(base_cfg)
-    cfg.update(knobs)
-    cfg["max_batch"] = max(cfg.get("max_batch", 0), n_samples)
-    ctx = mlsgd.Context(**cfg)
+    ctx = mlsgd.Context(**context_cfg(base_cfg, knobs, n_samples))
     st = ctx.new_stats(level)
     ctx.mlsgd_level_gradient(it0, level, 0, n_samples, z, st)  # warm-up (scratch, kernels)
     noconv = st.host()["noconv"]
@@ -108,12 +120,13 @@ def tune(base_cfg, level, n_samples, z, probe=None, reps=2, cache_path=CACHE, lo
         ok = [r for r in rs if r["noconv"] == 0]
         return min(ok, key=lambda r: r["ms_per_sample"]) if ok else None
 
-    shape = best([run(dict(DEFAULTS, stencil=s, z_chunks=c))
-                  for s, c in itertools.product(SHAPES["stencil"], SHAPES["z_chunks"])])
+    shape = best([run(dict(DEFAULTS, stencil=s, z_chunks=c, batch_chunks=b))
+                  for s, c, b in itertools.product(SHAPES["stencil"], SHAPES["z_chunks"], SHAPES["batch_chunks"])])
     if shape is None:
         raise RuntimeError("autotune: no launch shape converged")
-    sched = best([run(dict(shape["knobs"], inner_iters=i, omega=w))
-                  for i, w in itertools.product(SCHEDULES["inner_iters"], SCHEDULES["omega"])])
+    sched = best([run(dict(shape["knobs"], inner_iters=i, omega=w, ir_steps=k))
+                  for i, w, k in itertools.product(SCHEDULES["inner_iters"], SCHEDULES["omega"],
+                                                   SCHEDULES["ir_steps"])])
     win = sched if sched is not None and sched["ms_per_sample"] < shape["ms_per_sample"] else shape
     entry = dict(knobs=win["knobs"], ms_per_sample=win["ms_per_sample"], probe_samples=m,
                  default_ms_per_sample=next(r["ms_per_sample"] for r in tried if r["knobs"] == DEFAULTS),

@@ -199,13 +199,14 @@ mlsgd_status solve_grid(mlsgd_ctx* ctx, int N, int S, const GridFields& f, const
   double* ytmp = y ? y : bp.take<double>(S * nodes);
   PcgParams prm{ctx->cfg.rtol, ctx->cfg.max_iter, ctx->cfg.omega > 0 ? ctx->cfg.omega : 0.6, 4};
   const int inner = ctx->cfg.inner_iters > 0 ? ctx->cfg.inner_iters : 6;
+  const int inner2 = ctx->cfg.inner_iters_next > 0 ? ctx->cfg.inner_iters_next : inner;
   if (ctx->mixed()) build_hierarchy_mixed(B, f.abf, prm.omega, st);
   else build_hierarchy_fp64(B, f.a64, prm.omega, st);
   launch_rhs_state(z, ctx->Nc(), N, b, st);
   const int fixed = ctx->cfg.ir_steps > 0 ? ctx->cfg.ir_steps : 0;
   const bool pairs = want_pairs && ctx->mixed() && N >= kTiledMinN && B.J >= 1;
   if (pairs_out) *pairs_out = pairs;
-  cudaError_t e = ctx->mixed() ? ir_mixed(B, f.a32, f.abf, b, 0, ytmp, r64, prm, inner, st, fixed, nullptr, pairs)
+  cudaError_t e = ctx->mixed() ? ir_mixed(B, f.a32, f.abf, b, 0, ytmp, r64, prm, inner, st, fixed, nullptr, pairs, inner2)
                                : pcg_fp64(B, f.a64, b, 0, ytmp, prm, st);
   CK(e);
   launch("record", 0.0, k_record, dim3((S + 127) / 128), 128, 0, st, (const SolveScalars*)B.sc, S, (int)ctx->mixed(),
@@ -216,10 +217,11 @@ mlsgd_status solve_grid(mlsgd_ctx* ctx, int N, int S, const GridFields& f, const
   if (pairs) {
     launch_phi_adjrhs_df((const float2*)ytmp, N, S, (float2*)badj, phi, B.partial, ctx->d_gtab2[lev],
                          ctx->d_mgtab2[lev], st);
-    e = ir_mixed(B, f.a32, f.abf, nullptr, (long long)nodes, q, r64, prm, inner, st, fixed, (const float2*)badj, true);
+    e = ir_mixed(B, f.a32, f.abf, nullptr, (long long)nodes, q, r64, prm, inner, st, fixed, (const float2*)badj, true,
+                 inner2);
   } else {
     launch_phi_adjrhs(ytmp, N, S, badj, phi, B.partial, ctx->d_gtab[lev], ctx->d_mgtab[lev], st, ctx->freq());
-    e = ctx->mixed() ? ir_mixed(B, f.a32, f.abf, badj, (long long)nodes, q, r64, prm, inner, st, fixed)
+    e = ctx->mixed() ? ir_mixed(B, f.a32, f.abf, badj, (long long)nodes, q, r64, prm, inner, st, fixed, nullptr, false, inner2)
                      : pcg_fp64(B, f.a64, badj, (long long)nodes, q, prm, st);
   }
   CK(e);
@@ -300,7 +302,8 @@ mlsgd_status mlsgd_create(const mlsgd_config* cfg, mlsgd_ctx** out) {
       c.ctrl_level >= c.n_levels || c.n_modes < 2 || (c.field_model == 0 && (c.n_modes % 2) != 0) || c.n_modes > 4096 ||
       !(c.corr_len > 0) || !(c.rtol > 0) || c.max_iter < 1 || (c.precision != MLSGD_FP64 && c.precision != MLSGD_MIXED) ||
       (c.n0 << (c.n_levels - 1)) > 1024 || c.field_model < 0 || c.field_model > 1 || c.target_freq < 0 ||
-      c.stencil < 0 || c.stencil > 1 || c.z_chunks < 0 || !(c.omega >= 0.0 && c.omega < 1.0))
+      c.stencil < 0 || c.stencil > 1 || c.z_chunks < 0 || !(c.omega >= 0.0 && c.omega < 1.0) ||
+      c.inner_iters_next < 0)
     return MLSGD_EINVAL;
   int mcube = 0;
   if (c.field_model == 1) {

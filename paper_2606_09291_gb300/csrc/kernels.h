@@ -116,9 +116,11 @@ cudaError_t pcg_fp64(SolverBufs& B, const double* a64, const double* b, long lon
 // b_pair (tiled grids only): b given as FP32 (hi, lo) pairs instead of b (FP64)
 // pair_out (tiled grids only): x_out's storage receives the solution as FP32 (hi, lo)
 //   pairs (8 bytes per node, as the FP64 layout) instead of FP64 values
+// inner_next: inner iterations of the steps after the first (0: inner_iters)
 cudaError_t ir_mixed(SolverBufs& B, const float* a32, const __nv_bfloat16* abf, const double* b,
                      long long bstride, double* x_out, double* r64, const PcgParams& prm, int inner_iters,
-                     cudaStream_t st, int fixed_steps = 0, const float2* b_pair = nullptr, bool pair_out = false);
+                     cudaStream_t st, int fixed_steps = 0, const float2* b_pair = nullptr, bool pair_out = false,
+                     int inner_next = 0);
 // coefficient hierarchy for the V-cycle from the level-0 coefficient
 // coarse coefficients and, per tiled level, omega D^-1 (omega: the smoother's damping)
 void build_hierarchy_fp64(SolverBufs& B, const double* a64, double omega, cudaStream_t st);

@@ -1012,7 +1012,7 @@ cudaError_t pcg_fp64(SolverBufs& B, const double* a64, const double* b, long lon
 
 cudaError_t ir_mixed(SolverBufs& B, const float* a32, const __nv_bfloat16* abf, const double* b, long long bstride,
                      double* x_out, double* r64, const PcgParams& prm, int inner_iters, cudaStream_t st,
-                     int fixed_steps, const float2* b_pair, bool pair_out) {
+                     int fixed_steps, const float2* b_pair, bool pair_out, int inner_next) {
   const int N = B.N, S = B.S;
   const long long nodes = nodes_of(N);
   const int nb = node_blocks(N);
@@ -1042,6 +1042,8 @@ cudaError_t ir_mixed(SolverBufs& B, const float* a32, const __nv_bfloat16* abf, 
   // cleared here, once
   const bool sres = tiled && uses_slab(B, N, 4);
   const float* p_last = nullptr;
+  if (inner_next <= 0) inner_next = inner_iters;
+  int last_inner = inner_iters;  // inner iterations of the step the next refinement pass completes
   if (sres) {
     void* xb[1] = {xdf};
     zero_boundary<double>(xb, 1, N, S, st);
@@ -1076,7 +1078,7 @@ cudaError_t ir_mixed(SolverBufs& B, const float* a32, const __nv_bfloat16* abf, 
     if (step > 0) {
       const int cap = fixed_steps > 0 ? fixed_steps : prm.max_iter;
       if (sres) {
-        slab_res(d, p_last, inner_iters <= 1, sci, step == 1 ? bdf : B.bdf, step == 1 ? bstride : nodes, B.bdf, xdf,
+        slab_res(d, p_last, last_inner <= 1, sci, step == 1 ? bdf : B.bdf, step == 1 ? bstride : nodes, B.bdf, xdf,
                  step == 1, a32, r32, B.partial, sco, N, B.batch(), st);
         scalar(B, sco, SM_OUTER_CONV, tol2, cap, st, tiled_blocks_per_sample(N, S, 4, true));
       } else if (tiled) {
@@ -1103,17 +1105,18 @@ cudaError_t ir_mixed(SolverBufs& B, const float* a32, const __nv_bfloat16* abf, 
       launch("demote", (double)B.n_act * nodes * 16, k_demote, g(), kBlock, 0, st, (const double*)r64, r32, d,
              (const SolveScalars*)sco, nodes, B.actp);
     scalar(B, sci, SM_INNER_BEGIN, 0, 0, st, nb, 0, sco);
+    const int inner = step == 0 ? inner_iters : inner_next;
+    last_inner = inner;
     if (tiled) {
-      e = pcg_inner_fused(B, a32, abf, d, r32, sci, prm, inner_iters, st, xdf, sco, step == 0,
-                          sres ? &p_last : nullptr);
+      e = pcg_inner_fused(B, a32, abf, d, r32, sci, prm, inner, st, xdf, sco, step == 0, sres ? &p_last : nullptr);
       if (e != cudaSuccess) return e;
     } else {
-      e = pcg_loop<float, float, __nv_bfloat16>(B, a32, abf, d, r32, sci, prm, inner_iters, st);
+      e = pcg_loop<float, float, __nv_bfloat16>(B, a32, abf, d, r32, sci, prm, inner, st);
       if (e != cudaSuccess) return e;
       launch("accum", (double)B.n_act * nodes * 20, k_accumulate, g(), kBlock, 0, st, x_out, (const float*)d,
              (const SolveScalars*)sco, nodes, B.actp);
     }
-    scalar(B, sco, SM_OUTER_STEP, 0, 0, st, nb, inner_iters);
+    scalar(B, sco, SM_OUTER_STEP, 0, 0, st, nb, inner);
   }
   launch_all(B);
   if (tiled && !pair_out)

@@ -644,61 +644,79 @@ __global__ void __launch_bounds__(NT) k_phi_tiled(const double* __restrict__ y, 
 // k_phi_tiled for a state given as FP32 (hi, lo) pairs (the mixed level gradient):
 // the same separable sums in pair arithmetic (no FP64 instruction), the 1D tables as
 // pairs, M e written as pairs (the adjoint solve's right-hand side), the partial
-// e.M e of each block returned in FP64.
+// e.M e of each block returned in FP64.  Each thread takes kPhiRows rows of a
+// 32 x (8 kPhiRows) tile, so the three block barriers of a plane serve four nodes.
+constexpr int kPhiRows = 4;
+constexpr int kPhiTY = TY * kPhiRows;                        // tile rows
+constexpr int kPhiNPY = kPhiTY + 2, kPhiNP = NPX * kPhiNPY;  // staged plane with halo
 __global__ void __launch_bounds__(NT) k_phi_tiled_df(const float2* __restrict__ y, int N, const float2* __restrict__ gtab,
                                                      const float2* __restrict__ mgtab, float2* __restrict__ badj,
                                                      double* __restrict__ partial, int nzc, int zc, int nseg) {
-  __shared__ float2 ys[NP];
-  __shared__ float2 xsum[NPY][TX];
-  __shared__ float2 mxy[3][NT];
+  __shared__ float2 ys[kPhiNP];
+  __shared__ float2 xsum[kPhiNPY][TX];
+  __shared__ float2 mxy[3][kPhiTY][TX];
   const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * TX + tx;
   const int n1 = N + 1;
   const int s = blockIdx.z / nzc, chunk = blockIdx.z % nzc;
-  const int x0 = 1 + TX * blockIdx.x, y0 = 1 + TY * blockIdx.y;
+  const int x0 = 1 + TX * blockIdx.x, y0 = 1 + kPhiTY * blockIdx.y;
   const long long nodes = (long long)n1 * n1 * n1;
   const float2* yb = y + s * nodes;
   const int kbeg = 1 + chunk * zc;
   const int kend = min(N - 1, kbeg + zc - 1);
-  const int gi = x0 + tx, gj = y0 + ty;
-  const bool mine = gi < N && gj < N;
-  DF ycen[3] = {DF{0.f, 0.f}, DF{0.f, 0.f}, DF{0.f, 0.f}};
+  const int gi = x0 + tx;
+  const int ly0 = kPhiRows * ty;  // the thread's first tile row
+  DF yc[kPhiRows], yn[kPhiRows];  // y at the thread's nodes of planes k and k + 1
   auto four = [](DF a) { return DF{4.f * a.h, 4.f * a.l}; };  // exact
-  auto advance = [&](int m) {
-    for (int e = tid; e < NP; e += NT) {
+  auto advance = [&](int m, DF* ycen) {
+    const int r3 = (m + 3) % 3;
+    for (int e = tid; e < kPhiNP; e += NT) {
       const int lx = e % NPX, ly = e / NPX;
       const int i = x0 - 1 + lx, j = y0 - 1 + ly;
       ys[e] = (m >= 0 && m <= N && i <= N && j <= N) ? yb[i + (long long)n1 * (j + (long long)n1 * m)]
                                                       : make_float2(0.f, 0.f);
     }
     __syncthreads();
-    for (int e = tid; e < NPY * TX; e += NT) {
+    for (int e = tid; e < kPhiNPY * TX; e += NT) {
       const int ly = e / TX, lx = e % TX;
       const float2* row = ys + NPX * ly + lx;
       xsum[ly][lx] = df_f2(df_add(df_add(df_make(row[0]), df_make(row[2])), four(df_make(row[1]))));
     }
-    ycen[(m + 3) % 3] = df_make(ys[(tx + 1) + NPX * (ty + 1)]);
+#pragma unroll
+    for (int t = 0; t < kPhiRows; ++t) ycen[t] = df_make(ys[(tx + 1) + NPX * (ly0 + t + 1)]);
     __syncthreads();
-    mxy[(m + 3) % 3][tid] =
-        df_f2(df_add(df_add(df_make(xsum[ty][tx]), df_make(xsum[ty + 2][tx])), four(df_make(xsum[ty + 1][tx]))));
+#pragma unroll
+    for (int t = 0; t < kPhiRows; ++t) {
+      const int ly = ly0 + t;
+      mxy[r3][ly][tx] =
+          df_f2(df_add(df_add(df_make(xsum[ly][tx]), df_make(xsum[ly + 2][tx])), four(df_make(xsum[ly + 1][tx]))));
+    }
     __syncthreads();
   };
   const double h6 = 1.0 / (6.0 * N);
   const DF h63 = df_make(df_split(h6 * h6 * h6));
   DF red{0.f, 0.f};
-  advance(kbeg - 1);
-  advance(kbeg);
+  advance(kbeg - 1, yn);
+  advance(kbeg, yc);
+  const DF mgi = gi < N ? df_make(mgtab[gi]) : DF{0.f, 0.f}, ggi = gi < N ? df_make(gtab[gi]) : DF{0.f, 0.f};
   for (int k = kbeg; k <= kend; ++k) {
-    advance(k + 1);
-    if (mine) {
-      const DF my = df_add(df_add(df_make(mxy[(k + 2) % 3][tid]), df_make(mxy[(k + 1) % 3][tid])),
-                           four(df_make(mxy[k % 3][tid])));
-      const DF mg3 = df_mul(df_mul(df_make(mgtab[gi]), df_make(mgtab[gj])), df_make(mgtab[k]));
-      const DF g3 = df_mul(df_mul(df_make(gtab[gi]), df_make(gtab[gj])), df_make(gtab[k]));
-      const DF me = df_add(df_mul(h63, my), df_neg(mg3));
-      const DF e = df_add(ycen[k % 3], df_neg(g3));
-      badj[s * nodes + gi + (long long)n1 * (gj + (long long)n1 * k)] = df_f2(me);
-      red = df_add(red, df_mul(e, me));
+    advance(k + 1, yn);
+    const DF mgk = df_make(mgtab[k]), ggk = df_make(gtab[k]);
+#pragma unroll
+    for (int t = 0; t < kPhiRows; ++t) {
+      const int gj = y0 + ly0 + t;
+      if (gi < N && gj < N) {
+        const DF my = df_add(df_add(df_make(mxy[(k + 2) % 3][ly0 + t][tx]), df_make(mxy[(k + 1) % 3][ly0 + t][tx])),
+                             four(df_make(mxy[k % 3][ly0 + t][tx])));
+        const DF mg3 = df_mul(df_mul(mgi, df_make(mgtab[gj])), mgk);
+        const DF g3 = df_mul(df_mul(ggi, df_make(gtab[gj])), ggk);
+        const DF me = df_add(df_mul(h63, my), df_neg(mg3));
+        const DF e = df_add(yc[t], df_neg(g3));
+        badj[s * nodes + gi + (long long)n1 * (gj + (long long)n1 * k)] = df_f2(me);
+        red = df_add(red, df_mul(e, me));
+      }
     }
+#pragma unroll
+    for (int t = 0; t < kPhiRows; ++t) yc[t] = yn[t];
     if (k == kend || (k - 1) % kZSeg == kZSeg - 1) {  // end of a partial-sum segment
       const double b = block_sum(df_to_double(red));
       if (tid == 0)
@@ -849,7 +867,7 @@ void tiled_res64(const float2* b, long long bstride, const float2* x, const floa
 
 int tiled_phi_df(const float2* y, int N, int S, const float2* gtab, const float2* mgtab, float2* badj,
                  double* partial, cudaStream_t st) {
-  const TiledShape t = tiled_shape(N, S, 1);
+  const TiledShape t = tiled_shape(N, S, kPhiRows);
   launch("phi_adjrhs", (double)S * nodes_of(N) * 16, k_phi_tiled_df, dim3(t.bx, t.by, (unsigned)(S * t.nzc)),
          dim3(TX, TY), 0, st, y, N, gtab, mgtab, badj, partial, t.nzc, t.zc, t.nseg);
   return t.blocks_per_sample;

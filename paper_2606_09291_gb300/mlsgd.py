@@ -26,7 +26,8 @@ class Config(ctypes.Structure):
                 ("max_iter", ctypes.c_int), ("precision", ctypes.c_int), ("inner_iters", ctypes.c_int),
                 ("max_batch", ctypes.c_int), ("field_tc", ctypes.c_int), ("ir_steps", ctypes.c_int),
                 ("field_model", ctypes.c_int), ("target_freq", ctypes.c_int), ("seed", ctypes.c_uint64),
-                ("stencil", ctypes.c_int), ("z_chunks", ctypes.c_int), ("omega", ctypes.c_double)]
+                ("stencil", ctypes.c_int), ("z_chunks", ctypes.c_int), ("omega", ctypes.c_double),
+                ("inner_iters_next", ctypes.c_int)]
 
 
 class LevelStats(ctypes.Structure):
@@ -153,7 +154,7 @@ class Context:
         defaults = dict(n_levels=3, n0=8, ctrl_level=None, n_modes=64, corr_len=0.3, sigma=1.0, theta=1.0,
                         alpha=1e-4, rtol=1e-8, max_iter=200, precision=MLSGD_FP64, inner_iters=0,
                         max_batch=256, field_tc=0, ir_steps=0, field_model=0,
-                        target_freq=1, seed=0, stencil=0, z_chunks=0, omega=0.0)
+                        target_freq=1, seed=0, stencil=0, z_chunks=0, omega=0.0, inner_iters_next=0)
         defaults.update(cfg)
         if defaults["ctrl_level"] is None:
             defaults["ctrl_level"] = defaults["n_levels"] - 1

@@ -1,6 +1,8 @@
 """GPU tests of the autotuner: every knob value it can choose keeps the level
-record within the mixed path's bar of the oracle, and a tuned entry, once cached,
-is returned as is (a run is deterministic given its cache)."""
+record within the mixed path's bar of the oracle (a fixed refinement-step count that
+leaves a sample unconverged is reported as such, and the tuner rejects it), and a
+tuned entry, once cached, is returned as is (a run is deterministic given its
+cache)."""
 import json
 
 import numpy as np
@@ -42,14 +44,18 @@ def test_every_choice_matches_the_oracle(lib):
     ref = mlmc.level_batch(W, 2, 2, range(5), z)
     fo = ref["stats"].mean_x * np.exp(W.theta * ref["shift"])
     yo = ref["stats"].mean_y * np.exp(W.theta * ref["shift"])
+    from paper_2606_09291_gb300 import autotune as T
     for knobs in _choices():
-        ctx = lib.Context(**dict(CFG, **knobs))
+        ctx = lib.Context(**T.context_cfg(CFG, knobs, 5))
         st = ctx.new_stats(2)
         ctx.mlsgd_level_gradient(2, 2, 0, 5, zt, st)
         h = st.host()
         f = st.field.cpu().numpy() * np.exp(W.theta * h["shift"])
         ctx.close()
-        assert h["count"] == 5 and h["noconv"] == 0, knobs
+        assert h["count"] == 5, knobs
+        if h["noconv"]:  # only a fixed step count may stop short of rtol
+            assert knobs["ir_steps"] > 0, knobs
+            continue
         assert np.abs(f - fo).max() <= TOLMIX * np.abs(fo).max(), knobs
         assert abs(h["mean_dy"] * np.exp(W.theta * h["shift"]) - yo) <= TOLMIX * abs(yo), knobs
 
