@@ -419,8 +419,9 @@ def run_gpu(args, rank, world):
                            "set %.0f GB)" % (ws_bytes / 1e9),
                            "parallelism": ("samples sharded over ranks, records all-gathered and merged "
                                            "every step") if world > 1 else "single GPU",
-                           "knobs": {k: cfg.get(k) for k in ("stencil", "z_chunks", "inner_iters", "omega",
-                                                             "ir_steps", "max_batch")},
+                           "knobs": {k: cfg.get(k) for k in ("stencil", "z_chunks", "inner_iters",
+                                                             "inner_iters_next", "omega", "ir_steps",
+                                                             "max_batch")},
                            "knobs_source": "autotuner cache" if any(k in cfg for k in ("inner_iters", "omega"))
                            else "defaults"},
                 "latency_ms": {"p50": statistics.median(step_ms), "p99": p99, "per": "step (one batch)"},

@@ -14,12 +14,14 @@ test_gpu_autotune.py checks each one):
 * ir_steps     0 = refine until every sample converges (host check per step, the
                still-active samples compacted); k > 0 = exactly k masked steps
                (no host round trip; rejected when a sample is left unconverged)
+* inner_iters_next  inner iterations of the refinement steps after the first, which
+               start from a residual the first step has already reduced (0 = inner_iters)
 
 Search: time candidate configurations on a probe batch of the level with CUDA
 events (one warm-up call, then `reps` timed calls of mlsgd_level_gradient), keep
 only candidates whose solves all converge, and go coordinate-wise: launch shape
-(stencil x z_chunks x batch_chunks) first, then the solver schedule (inner_iters x
-omega x ir_steps) at the best shape.  The cost is time per converged sample-gradient.  Winners are
+(stencil x z_chunks x batch_chunks) first, then the smoother schedule (inner_iters x
+omega), then the refinement schedule (ir_steps x inner_iters_next).  The cost is time per converged sample-gradient.  Winners are
 stored per (grid, batch size, precision, modes) in a JSON cache; a cached entry is
 returned as is, so a run is deterministic given its cache.  The paper's own
 analogue is choosing the batch width per level by memory and cost (Sec. 4.2,
@@ -37,10 +39,11 @@ import torch
 
 from . import mlsgd
 
-KNOBS = ("stencil", "z_chunks", "batch_chunks", "inner_iters", "omega", "ir_steps")
-DEFAULTS = dict(stencil=0, z_chunks=0, batch_chunks=1, inner_iters=6, omega=0.6, ir_steps=0)
+KNOBS = ("stencil", "z_chunks", "batch_chunks", "inner_iters", "omega", "ir_steps", "inner_iters_next")
+DEFAULTS = dict(stencil=0, z_chunks=0, batch_chunks=1, inner_iters=6, omega=0.6, ir_steps=0, inner_iters_next=0)
 SHAPES = dict(stencil=(0, 1), z_chunks=(0, 1, 2, 4), batch_chunks=(1, 2, 4))
-SCHEDULES = dict(inner_iters=(4, 5, 6, 7, 8), omega=(0.5, 0.6, 0.7), ir_steps=(0, 2, 3))
+SCHEDULES = dict(inner_iters=(4, 5, 6, 7, 8), omega=(0.5, 0.6, 0.7), ir_steps=(0, 2, 3),
+                 inner_iters_next=(0, 3, 4, 5))
 CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "tuned.json")
 
 
@@ -124,10 +127,13 @@ def tune(base_cfg, level, n_samples, z, probe=None, reps=2, cache_path=CACHE, lo
                   for s, c, b in itertools.product(SHAPES["stencil"], SHAPES["z_chunks"], SHAPES["batch_chunks"])])
     if shape is None:
         raise RuntimeError("autotune: no launch shape converged")
-    sched = best([run(dict(shape["knobs"], inner_iters=i, omega=w, ir_steps=k))
-                  for i, w, k in itertools.product(SCHEDULES["inner_iters"], SCHEDULES["omega"],
-                                                   SCHEDULES["ir_steps"])])
+    sched = best([run(dict(shape["knobs"], inner_iters=i, omega=w))
+                  for i, w in itertools.product(SCHEDULES["inner_iters"], SCHEDULES["omega"])])
     win = sched if sched is not None and sched["ms_per_sample"] < shape["ms_per_sample"] else shape
+    refine = best([run(dict(win["knobs"], ir_steps=k, inner_iters_next=i2))
+                   for k, i2 in itertools.product(SCHEDULES["ir_steps"], SCHEDULES["inner_iters_next"])])
+    if refine is not None and refine["ms_per_sample"] < win["ms_per_sample"]:
+        win = refine
     entry = dict(knobs=win["knobs"], ms_per_sample=win["ms_per_sample"], probe_samples=m,
                  default_ms_per_sample=next(r["ms_per_sample"] for r in tried if r["knobs"] == DEFAULTS),
                  candidates=len(tried), device=torch.cuda.get_device_name())

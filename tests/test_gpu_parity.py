@@ -131,6 +131,18 @@ def test_zero_control_and_rough_control(lib):
         assert rel_err(y[s], refs[s]["y"]) <= TOL64 and rel_err(q[s], refs[s]["q"]) <= TOL64
 
 
+@pytest.mark.parametrize("grid", [2, 3])
+def test_zero_control_mixed(lib, grid):
+    # the mixed path on the slab grids (32^3, 64^3): b = 0 takes no refinement step, the
+    # first step's pass writes y = 0 exactly; the adjoint (b = -M g_h) is solved as usual
+    y, q, phi, it, st, refs = _solve_both(lib, "mixed", grid, 2, 1e-8, z_kind="zero", n_levels=grid + 1)
+    assert not np.any(y)
+    assert np.all(st == 0)
+    for s in range(2):
+        assert abs(phi[s] - refs[s]["phi"]) <= 1e-12 * refs[s]["phi"]
+        assert rel_err(q[s], refs[s]["q"]) <= TOLMIX
+
+
 def test_batch_composition_is_bitwise_irrelevant(lib):
     """A sample's solution does not depend on which batch it is solved in."""
     y1, q1, p1, *_ = _solve_both(lib, "fp64", 1, 5, 1e-10)
