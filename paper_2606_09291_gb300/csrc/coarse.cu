@@ -29,7 +29,7 @@ namespace mlsgd {
 
 namespace {
 
-constexpr int kCT = 512;  // threads per block
+constexpr int kCT = 768;  // threads per block (24 warps: two blocks per SM hide the shared-memory latency)
 
 template <int N>
 struct Lv {

@@ -291,13 +291,12 @@ __global__ void k_restrict_zm(const T* __restrict__ tf, T* __restrict__ rc, cons
       for (int q = -1; q <= 1; ++q) v += T((q == 0 ? 1.0 : 0.5) * (u == 0 ? 1.0 : 0.5)) * p[q + n1f * u];
     return v;
   };
-  T prev = K0 > 0 ? rxy(2 * K0 - 1) : T(0);
-  for (int K = K0; K <= K1; ++K) {
-    if (K == 0 || K == Nc) {
-      out[K * (n1c * n1c)] = T(0);
-      if (K == 0) prev = rxy(1);
-      continue;
-    }
+  if (K0 == 0) out[0] = T(0);
+  if (K1 == Nc) out[Nc * (n1c * n1c)] = T(0);
+  const int Ka = K0 > 1 ? K0 : 1, Kb = K1 < Nc - 1 ? K1 : Nc - 1;  // interior coarse planes
+  T prev = rxy(2 * Ka - 1);
+#pragma unroll 2
+  for (int K = Ka; K <= Kb; ++K) {
     const T mid = rxy(2 * K), up = rxy(2 * K + 1);
     out[K * (n1c * n1c)] = T(0.5) * prev + mid + T(0.5) * up;
     prev = up;
