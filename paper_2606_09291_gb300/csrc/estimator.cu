@@ -331,11 +331,11 @@ struct CellInterp {
     float s = 0.f, c = 0.f;
 #pragma unroll
     for (int e = 0; e < 8; ++e) {
-      const float p = w32[e] * v[e].x;
+      const float p = __fmul_rn(w32[e], v[e].x);
       const float pe = __fmaf_rn(w32[e], v[e].y, __fmaf_rn(w32[e], v[e].x, -p));
-      const float t = s + p;
-      const float bb = t - s;
-      c += ((s - (t - bb)) + (p - bb)) + pe;
+      const float t = __fadd_rn(s, p);  // two-sum (intrinsics: never contracted)
+      const float bb = __fsub_rn(t, s);
+      c = __fadd_rn(c, __fadd_rn(__fadd_rn(__fsub_rn(s, __fsub_rn(t, bb)), __fsub_rn(p, bb)), pe));
       s = t;
     }
     return df_norm(s, c);
@@ -375,13 +375,13 @@ struct PairInterp {
     float s = 0.f, c = 0.f;
 #pragma unroll
     for (int e = 0; e < 8; ++e) {
-      const float w = (wx[e & 1] * wy[(e >> 1) & 1]) * wz[e >> 2];
+      const float w = (wx[e & 1] * wy[(e >> 1) & 1]) * wz[e >> 2];  // exact
       const float2 v = b[(e & 1) + ((e >> 1) & 1) * sy + (e >> 2) * sz];
-      const float p = w * v.x;
+      const float p = __fmul_rn(w, v.x);
       const float pe = __fmaf_rn(w, v.y, __fmaf_rn(w, v.x, -p));
-      const float t = s + p;
-      const float bb = t - s;
-      c += ((s - (t - bb)) + (p - bb)) + pe;
+      const float t = __fadd_rn(s, p);  // two-sum (intrinsics: never contracted)
+      const float bb = __fsub_rn(t, s);
+      c = __fadd_rn(c, __fadd_rn(__fadd_rn(__fsub_rn(s, __fsub_rn(t, bb)), __fsub_rn(p, bb)), pe));
       s = t;
     }
     return df_norm(s, c);

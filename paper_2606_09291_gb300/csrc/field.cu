@@ -154,11 +154,11 @@ __global__ void k_field_df(const double* __restrict__ xi, int K, const ModeTable
       const float pv[4] = {phv.x, phv.y, phv.z, phv.w}, lv[4] = {plv.x, plv.y, plv.z, plv.w};
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
-        const float p = th * pv[q];
+        const float p = __fmul_rn(th, pv[q]);
         const float pe = __fmaf_rn(th, lv[q], __fmaf_rn(tl, pv[q], __fmaf_rn(th, pv[q], -p)));
-        const float sum = S[q] + p;  // two-sum of S and p
-        const float bb = sum - S[q];
-        C[q] += ((S[q] - (sum - bb)) + (p - bb)) + pe;
+        const float sum = __fadd_rn(S[q], p);  // two-sum of S and p (intrinsics: never contracted)
+        const float bb = __fsub_rn(sum, S[q]);
+        C[q] = __fadd_rn(C[q], __fadd_rn(__fadd_rn(__fsub_rn(S[q], __fsub_rn(sum, bb)), __fsub_rn(p, bb)), pe));
         S[q] = sum;
       }
     }

@@ -151,30 +151,33 @@ __device__ __forceinline__ T block_sum(T v) {
 // A value is the unevaluated sum h + l of two FP32 numbers with |l| <= ulp(h)/2
 // (about 48 significant bits).  Sums use Knuth's two-sum, products the FMA to
 // recover the rounding error of h*h'; both renormalise.  No FP64 instruction.
+// The additions and products are the round-to-nearest intrinsics, which the
+// compiler never contracts into an FMA: a contracted "s + a*b" would round once
+// where the error-free transformations count on two roundings.
 struct DF {
   float h, l;
 };
 __device__ __forceinline__ DF df_make(float2 v) { return DF{v.x, v.y}; }
 __device__ __forceinline__ float2 df_f2(DF a) { return make_float2(a.h, a.l); }
 __device__ __forceinline__ DF df_norm(float s, float e) {
-  const float h = s + e;
-  return DF{h, e - (h - s)};
+  const float h = __fadd_rn(s, e);
+  return DF{h, __fsub_rn(e, __fsub_rn(h, s))};
 }
 __device__ __forceinline__ DF df_add(DF a, DF b) {
-  const float s = a.h + b.h;
-  const float bb = s - a.h;
-  const float e = (a.h - (s - bb)) + (b.h - bb);
-  return df_norm(s, e + (a.l + b.l));
+  const float s = __fadd_rn(a.h, b.h);
+  const float bb = __fsub_rn(s, a.h);
+  const float e = __fadd_rn(__fsub_rn(a.h, __fsub_rn(s, bb)), __fsub_rn(b.h, bb));
+  return df_norm(s, __fadd_rn(e, __fadd_rn(a.l, b.l)));
 }
 __device__ __forceinline__ DF df_neg(DF a) { return DF{-a.h, -a.l}; }
 __device__ __forceinline__ DF df_mul(DF a, DF b) {
-  const float p = a.h * b.h;
+  const float p = __fmul_rn(a.h, b.h);
   const float e = __fmaf_rn(a.h, b.l, __fmaf_rn(a.l, b.h, __fmaf_rn(a.h, b.h, -p)));
   return df_norm(p, e);
 }
 // product with an FP32 number
 __device__ __forceinline__ DF df_mulf(DF a, float w) {
-  const float p = a.h * w;
+  const float p = __fmul_rn(a.h, w);
   const float e = __fmaf_rn(a.l, w, __fmaf_rn(a.h, w, -p));
   return df_norm(p, e);
 }

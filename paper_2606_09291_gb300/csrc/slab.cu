@@ -89,20 +89,20 @@ struct SlabArgs {
 // ---- error-free FP32 arithmetic of the refinement step (RES)
 // two_sum: s + e == a + b exactly (Knuth); a coefficient is an unevaluated pair (h, l)
 struct P2 { float h, l; };
-__device__ __forceinline__ P2 two_sum(float a, float b) {
-  const float s = a + b;
-  const float bb = s - a;
-  return P2{s, (a - (s - bb)) + (b - bb)};
+__device__ __forceinline__ P2 two_sum(float a, float b) {  // intrinsics: never contracted
+  const float s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  return P2{s, __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb))};
 }
 // (S, comp) += sgn (c.h + c.l) x for an FP32 operand x: the product c.h x is split
 // exactly by the FMA, c.l x enters the compensation
 template <bool NEG>
 __device__ __forceinline__ void res_term(float& S, float& comp, P2 c, float x) {
-  const float p = c.h * x;
+  const float p = __fmul_rn(c.h, x);
   const float low = __fmaf_rn(c.l, x, __fmaf_rn(c.h, x, -p));
   const P2 t = two_sum(S, NEG ? -p : p);
   S = t.h;
-  comp += t.l + (NEG ? -low : low);
+  comp = __fadd_rn(comp, __fadd_rn(t.l, NEG ? -low : low));
 }
 
 template <int N>
@@ -567,7 +567,7 @@ __global__ void __launch_bounds__(256, 3) k_slab(SlabArgs A) {
             const bool ok = (okb >> (t * RX + i)) & 1u;
             const long long g = gk + t * N1 + i;
             const P2 axs = two_sum(Sa[t][i], Ca[t][i]);
-            const float pp = axs.h * sch;  // (A inc) as a pair (pp, pe)
+            const float pp = __fmul_rn(axs.h, sch);  // (A inc) as a pair (pp, pe)
             const float pe = __fmaf_rn(axs.h, scl, __fmaf_rn(axs.l, sch, __fmaf_rn(axs.h, sch, -pp)));
             const float2 bv = ok ? rri[g] : make_float2(0.f, 0.f);
             const P2 dd = two_sum(bv.x, -pp);

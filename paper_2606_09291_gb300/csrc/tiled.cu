@@ -130,21 +130,21 @@ struct TiledSmem {
 // two_sum: s + e == a + b exactly (Knuth); products use the FMA to split
 // c * x into p + pe exactly.  A coefficient is an unevaluated pair (h, l).
 struct F2 { float h, l; };
-__device__ __forceinline__ F2 two_sum(float a, float b) {
-  const float s = a + b;
-  const float bb = s - a;
-  return F2{s, (a - (s - bb)) + (b - bb)};
+__device__ __forceinline__ F2 two_sum(float a, float b) {  // intrinsics: never contracted
+  const float s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  return F2{s, __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb))};
 }
 // (S, comp) += sgn * (c.h + c.l) * (x.x + x.y), sgn = +1 or -1
 template <bool NEG>
 __device__ __forceinline__ void df_term(float& S, float& comp, F2 c, float2 x) {
-  const float p = c.h * x.x;
+  const float p = __fmul_rn(c.h, x.x);
   const float pe = __fmaf_rn(c.h, x.x, -p);
   const float low = __fmaf_rn(c.h, x.y, __fmaf_rn(c.l, x.x, pe));
   const float q = NEG ? -p : p;
   const F2 t = two_sum(S, q);
   S = t.h;
-  comp += t.l + (NEG ? -low : low);
+  comp = __fadd_rn(comp, __fadd_rn(t.l, NEG ? -low : low));
 }
 
 template <typename T, typename TA, int MODE>
@@ -468,7 +468,7 @@ __global__ void __launch_bounds__(NT) k_tiled(TiledArgs A) {
           }
           // ax = (S + comp) (sch + scl), a pair (p, pe)
           const F2 axs = two_sum(S, comp);
-          const float p = axs.h * sch;
+          const float p = __fmul_rn(axs.h, sch);
           const float pe = __fmaf_rn(axs.h, scl, __fmaf_rn(axs.l, sch, __fmaf_rn(axs.h, sch, -p)));
           const long long o = pn * k + n1 * t;
           const float2 bv = reinterpret_cast<const float2*>(bptr)[o];
