@@ -139,16 +139,19 @@ int tiled_blocks_per_sample(int N, int S, int elem, bool slab);
 template <typename T, typename TA>
 void tiled_apply(const T* z, const T* pold, T* pnew, const TA* a, T* q, double* partial, const SolveScalars* sc, int N,
                  const Batch& bt, int first, cudaStream_t st);
+// PRE (and PREU): t = r - A x1 with x1 = omega D^-1 r (PREU: r <- r - alpha q first, stored
+// in rnew).  True when the pass also restricted t to rc on grid N/2 (the slab passes;
+// t is then not stored), false when t was stored for a separate restriction.
 template <typename T, typename TA>
-void tiled_pre(const T* r, const TA* a, const T* wdinv, T* t, const SolveScalars* sc, int N, const Batch& bt,
+bool tiled_pre(const T* r, const TA* a, const T* wdinv, T* t, T* rc, const SolveScalars* sc, int N, const Batch& bt,
                cudaStream_t st);
 template <typename T, typename TA>
 void tiled_post(const T* r, const TA* a, const T* wdinv, const T* ec, T* z, double* partial, const SolveScalars* sc,
                 int N, const Batch& bt, cudaStream_t st);
 void tiled_apply_x(const float* z, const float* pold, float* pnew, const float* a, float* q, float* x, double* partial,
                    const SolveScalars* sc, int N, const Batch& bt, cudaStream_t st, bool x_first);
-void tiled_pre_update(const float* r, const float* q, const __nv_bfloat16* a, const float* wdinv, float* t,
-                      float* rnew, const SolveScalars* sc, int N, const Batch& bt, cudaStream_t st);
+bool tiled_pre_update(const float* r, const float* q, const __nv_bfloat16* a, const float* wdinv, float* t,
+                      float* rnew, float* rc, const SolveScalars* sc, int N, const Batch& bt, cudaStream_t st);
 // r32 = (float)(b - A x) to FP64 accuracy with x, b as FP32 (hi, lo) pairs and error-free
 // FP32 products and sums; partial r.r
 void tiled_res64(const float2* b, long long bstride, const float2* x, const float* a, float* r32, double* partial,
@@ -166,8 +169,9 @@ bool slab_supported(int N);
 TiledShape slab_shape(int N, int S, int zchunks = 0);
 void slab_apply(const float* z, const float* pold, float* pnew, const float* a, float* q, float* x, double* partial,
                 const SolveScalars* sc, int N, const Batch& bt, bool first, bool with_x, bool x_first, cudaStream_t st);
+// PRE (q null) or PREU with the restriction of t fused: rc on grid N/2 (t not stored)
 template <typename TA>
-void slab_pre(const float* r, const float* q, const TA* a, const float* wdinv, float* t, float* rnew,
+void slab_pre(const float* r, const float* q, const TA* a, const float* wdinv, float* rnew, float* rc,
               const SolveScalars* sc, int N, const Batch& bt, cudaStream_t st);
 template <typename TA>
 void slab_post(const float* r, const TA* a, const float* wdinv, const float* ec, float* z, double* partial,

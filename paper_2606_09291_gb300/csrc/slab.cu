@@ -25,6 +25,17 @@
 // Partial sums (APPLY p.q, POST r.z, RES r.r) are formed per segment of kZSeg interior
 // planes exactly as in tiled.cu (entry seg * by + tile_y per sample).
 //
+// PRE and PREU restrict their residual t = r - A x1 to the coarse grid N/2 in the same
+// pass (t itself is never stored): rc(X, Y, Z) = sum over d in {-1, 0, 1}^3 of
+// w(d_x) w(d_y) w(d_z) t(2X + d_x, 2Y + d_y, 2Z + d_z), w(0) = 1, w(+-1) = 1/2 (the
+// transpose of trilinear interpolation).  A lane sums its rows over x with one shuffle,
+// each warp combines its rows with the first row of the warp above (through shared
+// memory, after the plane's last barrier), and the coarse planes are summed while
+// marching in z.  A chunk computes t on one more plane than it owns (the first plane
+// of the next chunk; nothing of it is stored) so that its last coarse plane is complete; the coarse row at the boundary of
+// two row blocks takes exactly two atomic additions onto a zeroed row (k_zero_seams),
+// so its value does not depend on their order.  Coarse boundary nodes are written 0.
+//
 // RES is the refinement step of the mixed solver in one pass: the operand is the inner
 // solve's increment inc = d + alpha p, the stencil forms A inc to FP64 accuracy in
 // FP32 arithmetic (exact cell-pair sums and FMA-split products, compensated sums), and
@@ -67,7 +78,7 @@ struct SlabArgs {
   const float* dinv;  // PRE/PREU/POST: omega D^-1 (0 on the boundary)
   const float* ec;    // POST: coarse correction on grid N/2
   const void* a;      // cell coefficient (TA)
-  float* out0;        // APPLY: q   PRE/PREU: t   POST: z
+  float* out0;        // APPLY: q   POST: z   RES: r32
   float* out1;        // APPLY: p_new   PREU: r_new
   float* x;           // APPLYX: solution updated with alpha_prev p_old
   double* partial;    // [S][by * nseg]
@@ -84,6 +95,7 @@ struct SlabArgs {
   float2* rr_out;           // residual pairs after the step, [S][nodes]
   float2* xp;               // solution pairs, updated in place, [S][nodes]
   int assign, dzero;        // first step (x = inc); d never written (inc = alpha p)
+  float* rc;                // PRE/PREU: the restricted residual on grid N/2, [S][(N/2+1)^3]
 };
 
 // ---- error-free FP32 arithmetic of the refinement step (RES)
@@ -142,7 +154,10 @@ struct SlabSmem {
   static constexpr size_t bar = eps + (kPost ? sizeof(float) * 2 * G::XPL : 0);
   // RES: x of the thread's own nodes for the plane being computed, copied ahead
   static constexpr size_t xpre = (bar + 8 * kRing + 15) / 16 * 16;
-  static constexpr size_t total = xpre + (MODE == SL_RES ? sizeof(float2) * 256 * G::RX * G::RY : 0);
+  // PRE/PREU: the x-restricted first row of every warp, [8 warps][32 lanes]
+  static constexpr bool kRestr = MODE == SL_PRE || MODE == SL_PREU;
+  static constexpr size_t hx = xpre + (MODE == SL_RES ? sizeof(float2) * 256 * G::RX * G::RY : 0);
+  static constexpr size_t total = hx + (kRestr ? sizeof(float) * 256 : 0);
   static_assert(cells % 16 == 0 && craw % 16 == 0 && cellb % 16 == 0 && xs % 16 == 0 && bar % 8 == 0, "align");
 };
 
@@ -212,6 +227,7 @@ __global__ void __launch_bounds__(256, 3) k_slab(SlabArgs A) {
   float* xs = (float*)(sm + L::xs);    // [3][XPL]
   float* eps = (float*)(sm + L::eps);  // [2][XPL]
   float2* xpre = (float2*)(sm + L::xpre) + threadIdx.x * (G::RX * G::RY);  // RES: this thread's nodes
+  float* hx = (float*)(sm + L::hx);  // PRE/PREU: [warp][lane]
   const uint32_t bar0 = smem_u32(sm + L::bar);
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -219,7 +235,9 @@ __global__ void __launch_bounds__(256, 3) k_slab(SlabArgs A) {
   const int s = A.act != nullptr ? A.act[blockIdx.z / A.nzc] : (int)(blockIdx.z / A.nzc);
   const int y0 = 1 + TYT * blockIdx.y;  // first interior row of the block
   const int kbeg = 1 + chunk * A.zc;
-  const int kend = min(N - 1, kbeg + A.zc - 1);
+  const int kend0 = min(N - 1, kbeg + A.zc - 1);  // the chunk's last plane
+  // PRE/PREU compute one more plane for the restriction (kend0 is even unless it is N-1)
+  const int kend = (L::kRestr && kend0 < N - 1) ? kend0 + 1 : kend0;
   constexpr long long kNodes = (long long)N1 * N1 * N1;
   if (A.sc != nullptr && !A.sc[s].active) {
     if (kRes && A.assign) {  // a sample that takes no step: its solution is 0 (own nodes)
@@ -428,7 +446,7 @@ __global__ void __launch_bounds__(256, 3) k_slab(SlabArgs A) {
   const int xw = RX * lane;                 // window's first column
   const int own0 = (ly0 + 1) * N1 + xw + 1;  // raw index of node (i = 0, t = 0) without the shift
   const int cwin = ly0 * N + xw;             // cell slab index of the window's first cell
-  float* out0 = A.out0 + s * kNodes;
+  float* out0 = L::kRestr ? nullptr : A.out0 + s * kNodes;
   float* out1 = (kApply || MODE == SL_PREU) ? A.out1 + s * kNodes : nullptr;
   float* xg = (MODE == SL_APPLYX) ? A.x + s * kNodes : nullptr;
   // bit t RX + i: node (i, t) is interior (the others, x = N or y = N, are written 0)
@@ -440,6 +458,40 @@ __global__ void __launch_bounds__(256, 3) k_slab(SlabArgs A) {
       if (xw + 1 + i <= N - 1 && y0 + ly0 + t <= N - 1) okb |= 1u << (t * RX + i);
   const long long gown = (long long)(y0 + ly0) * N1 + xw + 1;  // node (i = 0, t = 0) of plane 0
   float red = 0.f;
+
+  // ---- restriction (PRE/PREU): coarse column cx of the lane (RX = 1: odd lanes only),
+  // the warp's coarse rows (y0 + RY warp + 2c + 1) / 2 and, warp 0, row (y0 - 1) / 2
+  float zacc[RY / 2], zlow = 0.f;
+#pragma unroll
+  for (int c = 0; c < RY / 2; ++c) zacc[c] = 0.f;
+  const int cx = RX == 2 ? lane + 1 : (lane + 1) >> 1;
+  const bool has_cx = RX == 2 || (lane & 1);
+  // coarse plane Zc of the block's rows: interior nodes stored (the row shared with
+  // the neighbouring row block by atomic addition onto its zeroed value), boundary
+  // nodes 0; zero: the whole plane is a boundary plane
+  auto store_coarse = [&](int Zc, bool zero) {
+    float* rz = A.rc + s * (long long)G::NC1 * G::NC1 * G::NC1 + (long long)Zc * G::NC1 * G::NC1;
+#pragma unroll
+    for (int c = 0; c < RY / 2; ++c) {
+      const int Yc = (y0 + RY * warp + 2 * c + 1) >> 1;
+      if (Yc > G::NC) continue;
+      float* o = rz + Yc * G::NC1;
+      if (lane == 0) o[0] = 0.f;
+      if (!has_cx) continue;
+      if (zero || cx == G::NC || Yc == G::NC) o[cx] = 0.f;
+      else if (c == RY / 2 - 1 && warp == 7 && blockIdx.y + 1 < gridDim.y) atomicAdd(o + cx, zacc[c]);
+      else o[cx] = zacc[c];
+    }
+    if (warp == 0) {
+      const int Yl = (y0 - 1) >> 1;
+      float* o = rz + Yl * G::NC1;
+      if (lane == 0) o[0] = 0.f;
+      if (has_cx) {
+        if (zero || Yl == 0 || cx == G::NC) o[cx] = 0.f;
+        else atomicAdd(o + cx, zlow);
+      }
+    }
+  };
 
   for (int k = kbeg; k <= kend; ++k) {
     // APPLYX: this plane's x of the thread's nodes, loaded before the waits so the
@@ -456,6 +508,7 @@ __global__ void __launch_bounds__(256, 3) k_slab(SlabArgs A) {
       cp_async_commit();
     }
     float xv[RY][RX];
+    float tv[RY][RX], ux[RY];  // PRE/PREU: t of the own nodes, x-restricted rows
     if (MODE == SL_APPLYX) {
 #pragma unroll
       for (int t = 0; t < RY; ++t)
@@ -671,11 +724,11 @@ __global__ void __launch_bounds__(256, 3) k_slab(SlabArgs A) {
             red = fmaf(pv, qv, red);
             if (MODE == SL_APPLYX) xg[g] = ok ? xv[t][i] + alpha * o1[own] : 0.f;
           } else if (MODE == SL_PRE) {
-            out0[g] = ok ? o0[own] - ax : 0.f;
+            tv[t][i] = ok ? o0[own] - ax : 0.f;
           } else if (MODE == SL_PREU) {
             const float rn = ok ? fmaf(-alpha, o1[own], o0[own]) : 0.f;
-            out0[g] = ok ? rn - ax : 0.f;
-            out1[g] = rn;
+            tv[t][i] = ok ? rn - ax : 0.f;
+            if (k <= kend0) out1[g] = rn;
           } else {  // POST
             const float rv = ok ? o0[own] : 0.f;
             const float zv = ok ? fmaf(fmaf(-scale, acc[t][i], rv), o1[own], ctr[t][i]) : 0.f;
@@ -683,6 +736,20 @@ __global__ void __launch_bounds__(256, 3) k_slab(SlabArgs A) {
             red = fmaf(rv, zv, red);
           }
         }
+      }
+      if constexpr (L::kRestr) {  // x-restriction of the thread's rows at coarse column cx
+#pragma unroll
+        for (int t = 0; t < RY; ++t) {
+          if constexpr (RX == 2) {  // fine x = 2 cx - 1, 2 cx (this lane), 2 cx + 1 (the next)
+            const float nb = __shfl_down_sync(0xffffffffu, tv[t][0], 1);
+            ux[t] = fmaf(0.5f, tv[t][0] + nb, tv[t][1]);
+          } else {  // fine x = lane + 1 (= 2 cx on odd lanes)
+            const float lo = __shfl_up_sync(0xffffffffu, tv[t][0], 1);
+            const float hi = __shfl_down_sync(0xffffffffu, tv[t][0], 1);
+            ux[t] = fmaf(0.5f, lo + hi, tv[t][0]);
+          }
+        }
+        hx[warp * 32 + lane] = ux[0];
       }
       }  // not RES
     }
@@ -696,6 +763,30 @@ __global__ void __launch_bounds__(256, 3) k_slab(SlabArgs A) {
     }
     __syncthreads();
     if (tid == 0 && !dead && k + kAhead <= kend + 1) issue(k + kAhead, false);
+    if constexpr (L::kRestr) {
+      // the coarse rows of this warp (fine rows t = 1, 3, .. of the warp, the last one
+      // with the first row of the warp above) and, warp 0, row y0 for coarse row (y0-1)/2
+      const float hn = warp < 7 ? hx[(warp + 1) * 32 + lane] : 0.f;
+      float sv[RY / 2];
+#pragma unroll
+      for (int c = 0; c < RY / 2; ++c) sv[c] = fmaf(0.5f, ux[2 * c] + (2 * c + 2 < RY ? ux[2 * c + 2] : hn), ux[2 * c + 1]);
+      const float sl = 0.5f * ux[0];
+      if (k & 1) {  // plane k completes coarse plane (k-1)/2 (half weight) and starts (k+1)/2
+#pragma unroll
+        for (int c = 0; c < RY / 2; ++c) zacc[c] = fmaf(0.5f, sv[c], zacc[c]);
+        zlow = fmaf(0.5f, sl, zlow);
+        if (k > kbeg) store_coarse((k - 1) >> 1, false);
+        else if (k == 1) store_coarse(0, true);
+#pragma unroll
+        for (int c = 0; c < RY / 2; ++c) zacc[c] = 0.5f * sv[c];
+        zlow = 0.5f * sl;
+        if (k == N - 1) store_coarse(G::NC, true);
+      } else {
+#pragma unroll
+        for (int c = 0; c < RY / 2; ++c) zacc[c] += sv[c];
+        zlow += sl;
+      }
+    }
     xk = xkp;
     jk3 = jk3p;
   }
@@ -792,15 +883,37 @@ void slab_res(const float* d, const float* p, bool d_zero, const SolveScalars* s
   dispatch<float, SL_RES>(N, "resid64", bytes, A, bt, st, (double)bt.n * (N - 1) * (N - 1) * (N - 1) * kResOpsPerNode);
 }
 
+// the coarse rows shared by two row blocks, 0 before the blocks add their parts
+template <int N>
+__global__ void __launch_bounds__(256) k_zero_seams(float* __restrict__ rc, const int* __restrict__ act,
+                                                    const SolveScalars* __restrict__ sc) {
+  using G = SlabGeo<N>;
+  const int s = act != nullptr ? act[blockIdx.x] : (int)blockIdx.x;
+  if (sc != nullptr && !sc[s].active) return;
+  constexpr int kBy = (N - 1 + G::TYT - 1) / G::TYT;
+  constexpr int kPer = (kBy - 1) * G::NC1 * G::NC1;  // (seam, Z, X)
+  float* r = rc + s * (long long)G::NC1 * G::NC1 * G::NC1;
+  for (int e = threadIdx.x; e < kPer; e += 256) {
+    const int x = e % G::NC1, rest = e / G::NC1, z = rest % G::NC1, b = 1 + rest / G::NC1;
+    r[(long long)z * G::NC1 * G::NC1 + (b * G::TYT / 2) * G::NC1 + x] = 0.f;
+  }
+}
+
 template <typename TA>
-void slab_pre(const float* r, const float* q, const TA* a, const float* dinv, float* t, float* rnew,
+void slab_pre(const float* r, const float* q, const TA* a, const float* dinv, float* rnew, float* rc,
               const SolveScalars* sc, int N, const Batch& bt, cudaStream_t st) {
   SlabArgs A{};
-  A.in0 = r; A.in1 = q; A.a = a; A.dinv = dinv; A.out0 = t; A.out1 = rnew; A.sc = sc; A.err = bt.err;
+  A.in0 = r; A.in1 = q; A.a = a; A.dinv = dinv; A.out1 = rnew; A.rc = rc; A.sc = sc; A.err = bt.err;
+  if (N == 64) {  // four row blocks per sample (32^3: one)
+    const double zb = (double)bt.n * 4.0 * 33 * 33 * 3;
+    launch("seams", zb, k_zero_seams<64>, dim3((unsigned)bt.n), dim3(256), 0, st, rc, bt.act, sc);
+  }
+  // r (and q), omega D^-1 and the cells in; r_new (PREU) and the coarse residual out
+  const double coarse = (double)bt.n * nodes_of(N / 2) * 4;
   if (q)
-    dispatch<TA, SL_PREU>(N, "pre_f32", sbytes(N, bt.n, 5, 1, sizeof(TA)), A, bt, st);
+    dispatch<TA, SL_PREU>(N, "pre_f32", sbytes(N, bt.n, 4, 1, sizeof(TA)) + coarse, A, bt, st);
   else
-    dispatch<TA, SL_PRE>(N, "pre_f32", sbytes(N, bt.n, 3, 1, sizeof(TA)), A, bt, st);
+    dispatch<TA, SL_PRE>(N, "pre_f32", sbytes(N, bt.n, 2, 1, sizeof(TA)) + coarse, A, bt, st);
 }
 
 template <typename TA>

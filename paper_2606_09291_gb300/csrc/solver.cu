@@ -716,13 +716,15 @@ static int vcycle(SolverBufs& B, const T* r0, const TA0* a0, const SolveScalars*
   for (int j = 0; j < jc; ++j) {
     const int Nj = B.N >> j;
     const bool fine = j == 0;
+    T* rc = (T*)B.vr[j + 1];
+    bool restricted = false;  // the pre-smoothing pass restricted its residual itself
     if (fine && tiled && fuse_q) {
       if constexpr (std::is_same<T, float>::value && std::is_same<TA0, __nv_bfloat16>::value)
-        tiled_pre_update(r0, fuse_q, a0, (const T*)B.dinv[0], (T*)B.vt[0], r_new, sc, Nj, bt, st);
+        restricted = tiled_pre_update(r0, fuse_q, a0, (const T*)B.dinv[0], (T*)B.vt[0], r_new, rc, sc, Nj, bt, st);
     } else if (fine && tiled) {
-      tiled_pre<T, TA0>(r0, a0, (const T*)B.dinv[0], (T*)B.vt[0], sc, Nj, bt, st);
+      restricted = tiled_pre<T, TA0>(r0, a0, (const T*)B.dinv[0], (T*)B.vt[0], rc, sc, Nj, bt, st);
     } else if (!fine && tiled && Nj >= kTiledMinN) {
-      tiled_pre<T, T>(rin(j), (const T*)B.acoef[j], (const T*)B.dinv[j], (T*)B.vt[j], sc, Nj, bt, st);
+      restricted = tiled_pre<T, T>(rin(j), (const T*)B.acoef[j], (const T*)B.dinv[j], (T*)B.vt[j], rc, sc, Nj, bt, st);
     } else if (fine) {
       launch(cls<T>("jacobi0", true), nbytes<T, TA0>(Nj, n, 2, 1), k_jacobi0<T, TA0>, grid_nodes(Nj, n), kBlock, 0,
              st, rin(0), a0, (T*)B.vx[0], sc, Nj, omega, act);
@@ -735,6 +737,7 @@ static int vcycle(SolverBufs& B, const T* r0, const TA0* a0, const SolveScalars*
       launch(cls<T>("resid", false), nbytes<T, T>(Nj, n, 3, 1), k_resid_smooth<T, T, 0>, grid_nodes(Nj, n), kBlock, 0,
              st, rin(j), (const T*)B.vx[j], aj, (T*)B.vt[j], sc, Nj, omega, act);
     }
+    if (restricted) continue;
     with_grid(Nj / 2, [&](auto c) {
       constexpr int NCC = decltype(c)::value;
       const double rb = nbytes<T, T>(Nj, n, 1, 0) + nbytes<T, T>(Nj / 2, n, 1, 0);

@@ -814,29 +814,31 @@ void tiled_apply_x(const float* z, const float* pold, float* pnew, const float* 
   A.xfirst = x_first ? 1 : 0;
   run_tiled<float, float, TM_APPLYX>("apply_f32", vbytes<float, float>(N, bt.n, x_first ? 5 : 6, 1), A, bt, st);
 }
-void tiled_pre_update(const float* r, const float* q, const __nv_bfloat16* a, const float* dinv, float* t,
-                      float* rnew, const SolveScalars* sc, int N, const Batch& bt, cudaStream_t st) {
+bool tiled_pre_update(const float* r, const float* q, const __nv_bfloat16* a, const float* dinv, float* t,
+                      float* rnew, float* rc, const SolveScalars* sc, int N, const Batch& bt, cudaStream_t st) {
   if (bt.stencil == 0 && slab_supported(N)) {
-    slab_pre<__nv_bfloat16>(r, q, a, dinv, t, rnew, sc, N, bt, st);
-    return;
+    slab_pre<__nv_bfloat16>(r, q, a, dinv, rnew, rc, sc, N, bt, st);
+    return true;
   }
   TiledArgs A{};
   A.in0 = r; A.q = q; A.a = a; A.dinv = dinv; A.out0 = t; A.out1 = rnew; A.sc = sc; A.N = N;
   run_tiled<float, __nv_bfloat16, TM_PREU>("pre_f32", vbytes<float, __nv_bfloat16>(N, bt.n, 5, 1), A, bt, st);
+  return false;
 }
 
 template <typename T, typename TA>
-void tiled_pre(const T* r, const TA* a, const T* dinv, T* t, const SolveScalars* sc, int N, const Batch& bt,
+bool tiled_pre(const T* r, const TA* a, const T* dinv, T* t, T* rc, const SolveScalars* sc, int N, const Batch& bt,
                cudaStream_t st) {
   if constexpr (std::is_same<T, float>::value) {
     if (bt.stencil == 0 && slab_supported(N)) {
-      slab_pre<TA>(r, nullptr, a, dinv, t, nullptr, sc, N, bt, st);
-      return;
+      slab_pre<TA>(r, nullptr, a, dinv, nullptr, rc, sc, N, bt, st);
+      return true;
     }
   }
   TiledArgs A{};
   A.in0 = r; A.a = a; A.dinv = dinv; A.out0 = t; A.sc = sc; A.N = N;
   run_tiled<T, TA, TM_PRE>(name("pre", tag<T>()), vbytes<T, TA>(N, bt.n, 3, 1), A, bt, st);
+  return false;
 }
 template <typename T, typename TA>
 void tiled_post(const T* r, const TA* a, const T* dinv, const T* ec, T* z, double* partial, const SolveScalars* sc,
@@ -885,14 +887,14 @@ template void tiled_apply<float, float>(const float*, const float*, float*, cons
                                         const SolveScalars*, int, const Batch&, int, cudaStream_t);
 template void tiled_apply<double, double>(const double*, const double*, double*, const double*, double*, double*,
                                           const SolveScalars*, int, const Batch&, int, cudaStream_t);
-template void tiled_pre<float, __nv_bfloat16>(const float*, const __nv_bfloat16*, const float*, float*,
+template bool tiled_pre<float, __nv_bfloat16>(const float*, const __nv_bfloat16*, const float*, float*, float*,
                                               const SolveScalars*, int, const Batch&, cudaStream_t);
-template void tiled_pre<float, float>(const float*, const float*, const float*, float*, const SolveScalars*, int,
-                                      const Batch&, cudaStream_t);
+template bool tiled_pre<float, float>(const float*, const float*, const float*, float*, float*, const SolveScalars*,
+                                      int, const Batch&, cudaStream_t);
 template void tiled_post<float, float>(const float*, const float*, const float*, const float*, float*, double*,
                                        const SolveScalars*, int, const Batch&, cudaStream_t);
-template void tiled_pre<double, double>(const double*, const double*, const double*, double*, const SolveScalars*, int,
-                                        const Batch&, cudaStream_t);
+template bool tiled_pre<double, double>(const double*, const double*, const double*, double*, double*,
+                                        const SolveScalars*, int, const Batch&, cudaStream_t);
 template void tiled_post<float, __nv_bfloat16>(const float*, const __nv_bfloat16*, const float*, const float*, float*,
                                                double*, const SolveScalars*, int, const Batch&, cudaStream_t);
 template void tiled_post<double, double>(const double*, const double*, const double*, const double*, double*, double*,
