@@ -154,10 +154,12 @@ struct SlabSmem {
   static constexpr size_t bar = eps + (kPost ? sizeof(float) * 2 * G::XPL : 0);
   // RES: x of the thread's own nodes for the plane being computed, copied ahead
   static constexpr size_t xpre = (bar + 8 * kRing + 15) / 16 * 16;
-  // PRE/PREU: the x-restricted first row of every warp, [8 warps][32 lanes]
+  // PRE/PREU: the x-restricted first row of every warp, [plane parity][8 warps][32 lanes]
   static constexpr bool kRestr = MODE == SL_PRE || MODE == SL_PREU;
   static constexpr size_t hx = xpre + (MODE == SL_RES ? sizeof(float2) * 256 * G::RX * G::RY : 0);
-  static constexpr size_t total = hx + (kRestr ? sizeof(float) * 256 : 0);
+  static constexpr size_t total = hx + (kRestr ? sizeof(float) * 512 : 0);
+  static_assert((sizeof(TA) == 4 && (MODE == SL_PREU || MODE == SL_POST)) || total + 1024 <= 228 * 1024 / 3,
+                "three blocks per SM");
   static_assert(cells % 16 == 0 && craw % 16 == 0 && cellb % 16 == 0 && xs % 16 == 0 && bar % 8 == 0, "align");
 };
 
@@ -227,7 +229,7 @@ __global__ void __launch_bounds__(256, 3) k_slab(SlabArgs A) {
   float* xs = (float*)(sm + L::xs);    // [3][XPL]
   float* eps = (float*)(sm + L::eps);  // [2][XPL]
   float2* xpre = (float2*)(sm + L::xpre) + threadIdx.x * (G::RX * G::RY);  // RES: this thread's nodes
-  float* hx = (float*)(sm + L::hx);  // PRE/PREU: [warp][lane]
+  float* hx = (float*)(sm + L::hx);  // PRE/PREU: [plane parity][warp][lane]
   const uint32_t bar0 = smem_u32(sm + L::bar);
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -493,6 +495,129 @@ __global__ void __launch_bounds__(256, 3) k_slab(SlabArgs A) {
     }
   };
 
+  // ---- the operator as contributions of one operand plane p (all modes but RES): to
+  // node plane p - 1 and p + 1 through the cell plane between them (off_term), to node
+  // plane p through the cell planes below and above it (centre_term).  Node (i, t) has
+  // cells Cx[i + p][t + q] of a cell plane and operand neighbour (du, dv) of a plane at
+  // window (i + 1 + du, t + 1 + dv).
+  using Win = float[RX + 2][RY + 2];
+  using Cel = float[RX + 1][RY + 1];
+  using Acc = float[RY][RX];
+  auto load_cells = [&](int cpl, Cel& Cx) {  // cell plane cpl, cell (xw + cc, row ly0 + cr)
+    const TA* cp = cs + ((cpl - first) & (kRing - 1)) * (L::cellb / sizeof(TA)) + cwin;
+#pragma unroll
+    for (int cr = 0; cr < RY + 1; ++cr) {
+      if constexpr (RX == 2) {  // cells xw, xw+1 as one aligned pair (xw and N even), then xw+2
+        ld_cell_pair(cp + cr * N, Cx[0][cr], Cx[1][cr]);
+        Cx[2][cr] = ld_cell(cp, cr * N + 2);
+      } else {
+#pragma unroll
+        for (int cc = 0; cc < RX + 1; ++cc) Cx[cc][cr] = ld_cell(cp, cr * N + cc);
+      }
+    }
+  };
+  auto load_win = [&](int x3, Win& W) {  // the lane's (RX+2) x (RY+2) window of operand slot x3
+    const float* xp = xs + x3 * G::XPL + ly0 * XS + xw;
+#pragma unroll
+    for (int rr = 0; rr < RY + 2; ++rr) {
+      if constexpr (RX == 2) {
+        const float2 a0 = *reinterpret_cast<const float2*>(xp + rr * XS);
+        const float2 a1 = *reinterpret_cast<const float2*>(xp + rr * XS + 2);
+        W[0][rr] = a0.x;
+        W[1][rr] = a0.y;
+        W[2][rr] = a1.x;
+        W[3][rr] = a1.y;
+      } else {
+#pragma unroll
+        for (int c = 0; c < RX + 2; ++c) W[c][rr] = xp[rr * XS + c];
+      }
+    }
+  };
+  auto off_term = [&](Acc& acc, const Win& W, const Cel& Cr) {
+#pragma unroll
+    for (int t = 0; t < RY; ++t)
+#pragma unroll
+      for (int i = 0; i < RX; ++i) {
+        float a2 = acc[t][i];
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+          a2 -= (Cr[i + u][t] + Cr[i + u][t + 1]) * W[i + 2 * u][t + 1];  // xz face diagonals
+          a2 -= (Cr[i][t + u] + Cr[i + 1][t + u]) * W[i + 1][t + 2 * u];  // yz face diagonals
+        }
+#pragma unroll
+        for (int q = 0; q < 2; ++q)
+#pragma unroll
+          for (int p = 0; p < 2; ++p) a2 -= Cr[i + p][t + q] * W[i + 2 * p][t + 2 * q];  // body diagonals
+        acc[t][i] = a2;
+      }
+  };
+  auto centre_term = [&](Acc& acc, const Win& W, const Cel& Cl, const Cel& Ch) {
+#pragma unroll
+    for (int t = 0; t < RY; ++t)
+#pragma unroll
+      for (int i = 0; i < RX; ++i) {
+        float pxy[2][2];  // in-plane face diagonals: pair sums over the two cell planes
+#pragma unroll
+        for (int v = 0; v < 2; ++v)
+#pragma unroll
+          for (int u = 0; u < 2; ++u) pxy[v][u] = Cl[i + u][t + v] + Ch[i + u][t + v];
+        const float sum8 = (pxy[0][0] + pxy[0][1]) + (pxy[1][0] + pxy[1][1]);
+        float a1 = fmaf(4.f * sum8, W[i + 1][t + 1], acc[t][i]);
+#pragma unroll
+        for (int v = 0; v < 2; ++v)
+#pragma unroll
+          for (int u = 0; u < 2; ++u) a1 -= pxy[v][u] * W[i + 2 * u][t + 2 * v];
+        acc[t][i] = a1;
+      }
+  };
+  // node planes k and k + 1 summed so far (below, then centre) and the operand of node
+  // plane k at the own nodes, entering iteration k
+  float accB[RY][RX], accC[RY][RX], ctrk[RY][RX];
+  if constexpr (!kRes) {
+    float W[RX + 2][RY + 2], Cl[RX + 1][RY + 1], Ch[RX + 1][RY + 1];
+#pragma unroll
+    for (int t = 0; t < RY; ++t)
+#pragma unroll
+      for (int i = 0; i < RX; ++i) accB[t][i] = accC[t][i] = 0.f;
+    load_cells(first, Cl);
+    load_cells(kbeg, Ch);
+    load_win(xfirst3, W);
+    off_term(accB, W, Cl);
+    load_win(xk, W);
+    centre_term(accB, W, Cl, Ch);
+#pragma unroll
+    for (int t = 0; t < RY; ++t)
+#pragma unroll
+      for (int i = 0; i < RX; ++i) ctrk[t][i] = W[i + 1][t + 1];
+    off_term(accC, W, Ch);
+  }
+  float ux[RY];  // PRE/PREU: x-restricted rows of the last computed plane
+  // PRE/PREU: the coarse rows of this warp from plane k (fine rows t = 1, 3, .. of the
+  // warp, the last one with the first row of the warp above) and, warp 0, row y0 for
+  // coarse row (y0-1)/2; called after the barrier that follows plane k's epilogue
+  auto restrict_plane = [&](int k) {
+    const float hn = warp < 7 ? hx[(k & 1) * 256 + (warp + 1) * 32 + lane] : 0.f;
+    float sv[RY / 2];
+#pragma unroll
+    for (int c = 0; c < RY / 2; ++c) sv[c] = fmaf(0.5f, ux[2 * c] + (2 * c + 2 < RY ? ux[2 * c + 2] : hn), ux[2 * c + 1]);
+    const float sl = 0.5f * ux[0];
+    if (k & 1) {  // plane k completes coarse plane (k-1)/2 (half weight) and starts (k+1)/2
+#pragma unroll
+      for (int c = 0; c < RY / 2; ++c) zacc[c] = fmaf(0.5f, sv[c], zacc[c]);
+      zlow = fmaf(0.5f, sl, zlow);
+      if (k > kbeg) store_coarse((k - 1) >> 1, false);
+      else if (k == 1) store_coarse(0, true);
+#pragma unroll
+      for (int c = 0; c < RY / 2; ++c) zacc[c] = 0.5f * sv[c];
+      zlow = 0.5f * sl;
+      if (k == N - 1) store_coarse(G::NC, true);
+    } else {
+#pragma unroll
+      for (int c = 0; c < RY / 2; ++c) zacc[c] += sv[c];
+      zlow += sl;
+    }
+  };
+
   for (int k = kbeg; k <= kend; ++k) {
     // APPLYX: this plane's x of the thread's nodes, loaded before the waits so the
     // global latency overlaps the derive step
@@ -508,7 +633,7 @@ __global__ void __launch_bounds__(256, 3) k_slab(SlabArgs A) {
       cp_async_commit();
     }
     float xv[RY][RX];
-    float tv[RY][RX], ux[RY];  // PRE/PREU: t of the own nodes, x-restricted rows
+    float tv[RY][RX];  // PRE/PREU: t of the own nodes
     if (MODE == SL_APPLYX) {
 #pragma unroll
       for (int t = 0; t < RY; ++t)
@@ -521,27 +646,24 @@ __global__ void __launch_bounds__(256, 3) k_slab(SlabArgs A) {
       derive(k + 1, xkp, jk3p, true);
     }
     __syncthreads();
+    // One barrier per plane for all modes but RES: compute(k) reads only operand plane
+    // k + 1 (derived before this barrier; derive(k+2) overwrites plane k - 1, last read
+    // by compute(k-2)) and cell planes k, k + 1, so plane k + 3 is copied now into the
+    // slots of plane k - 1 (raw k - 1 was last read by compute(k-1), its cells too; a
+    // 3-slot vector ring reuses the slot of plane k, last read by derive(k)).
+    if constexpr (!kRes) {
+      if (L::kRestr && k > kbeg) restrict_plane(k - 1);
+      if (tid == 0 && !dead && k + kAhead <= kend + 1) issue(k + kAhead, false);
+    }
     {
-      // cells of the two cell planes around plane k: C[r][cc][cr], cell (xw + cc, row ly0 + cr)
-      float C[2][RX + 1][RY + 1];
-#pragma unroll
-      for (int r = 0; r < 2; ++r) {
-        const TA* cp = cs + ((k - 1 + r - first) & (kRing - 1)) * (L::cellb / sizeof(TA)) + cwin;
-#pragma unroll
-        for (int cr = 0; cr < RY + 1; ++cr) {
-          if constexpr (RX == 2) {  // cells xw, xw+1 as one aligned pair (xw and N even), then xw+2
-            ld_cell_pair(cp + cr * N, C[r][0][cr], C[r][1][cr]);
-            C[r][2][cr] = ld_cell(cp, cr * N + 2);
-          } else {
-#pragma unroll
-            for (int cc = 0; cc < RX + 1; ++cc) C[r][cc][cr] = ld_cell(cp, cr * N + cc);
-          }
-        }
-      }
       // RES: rr_new = rr - A inc to FP64 accuracy in FP32 arithmetic (exact cell-pair
       // sums and products, compensated sums, the scale h/12 and the subtraction as
       // pairs), r = rr_new rounded, x (+)= inc; the same plane-by-plane order as below
       if constexpr (kRes) {
+        // cells of the two cell planes around plane k: C[r][cc][cr], cell (xw + cc, row ly0 + cr)
+        float C[2][RX + 1][RY + 1];
+        load_cells(k - 1, C[0]);
+        load_cells(k, C[1]);
         float Sa[RY][RX], Ca[RY][RX], ctr[RY][RX];
 #pragma unroll
         for (int pl = 0; pl < 3; ++pl) {
@@ -646,64 +768,14 @@ __global__ void __launch_bounds__(256, 3) k_slab(SlabArgs A) {
           }
         }
       } else {
-      // the operator plane by plane (k-1, k, k+1): one window of (RX+2) x (RY+2) operand
-      // values live at a time; node (i, t) has cells c[p][q][r] = C[r][i + p][t + q] and
-      // neighbour (du, dv) of the plane at window (i + 1 + du, t + 1 + dv)
-      float acc[RY][RX], ctr[RY][RX];
-#pragma unroll
-      for (int pl = 0; pl < 3; ++pl) {
-        const int order = pl == 0 ? 1 : (pl == 1 ? 0 : 2);  // centre plane first
-        const float* xp = xs + (order == 0 ? xkm : (order == 1 ? xk : xkp)) * G::XPL + ly0 * XS + xw;
-        float W[RX + 2][RY + 2];
-#pragma unroll
-        for (int rr = 0; rr < RY + 2; ++rr) {
-          if constexpr (RX == 2) {
-            const float2 a0 = *reinterpret_cast<const float2*>(xp + rr * XS);
-            const float2 a1 = *reinterpret_cast<const float2*>(xp + rr * XS + 2);
-            W[0][rr] = a0.x;
-            W[1][rr] = a0.y;
-            W[2][rr] = a1.x;
-            W[3][rr] = a1.y;
-          } else {
-#pragma unroll
-            for (int c = 0; c < RX + 2; ++c) W[c][rr] = xp[rr * XS + c];
-          }
-        }
-#pragma unroll
-        for (int t = 0; t < RY; ++t)
-#pragma unroll
-          for (int i = 0; i < RX; ++i) {
-            if (order == 1) {
-              // in-plane face diagonals: pair sums over the two cell planes
-              float pxy[2][2];
-#pragma unroll
-              for (int v = 0; v < 2; ++v)
-#pragma unroll
-                for (int u = 0; u < 2; ++u) pxy[v][u] = C[0][i + u][t + v] + C[1][i + u][t + v];
-              const float sum8 = (pxy[0][0] + pxy[0][1]) + (pxy[1][0] + pxy[1][1]);
-              ctr[t][i] = W[i + 1][t + 1];
-              float a1 = 4.f * sum8 * W[i + 1][t + 1];
-#pragma unroll
-              for (int v = 0; v < 2; ++v)
-#pragma unroll
-                for (int u = 0; u < 2; ++u) a1 -= pxy[v][u] * W[i + 2 * u][t + 2 * v];
-              acc[t][i] = a1;
-            } else {
-              const int r = order >> 1;  // plane k-1: cells below (r = 0); k+1: above (r = 1)
-              float a2 = acc[t][i];
-#pragma unroll
-              for (int u = 0; u < 2; ++u) {
-                a2 -= (C[r][i + u][t] + C[r][i + u][t + 1]) * W[i + 2 * u][t + 1];  // xz face diagonals
-                a2 -= (C[r][i][t + u] + C[r][i + 1][t + u]) * W[i + 1][t + 2 * u];  // yz face diagonals
-              }
-#pragma unroll
-              for (int q = 0; q < 2; ++q)
-#pragma unroll
-                for (int p = 0; p < 2; ++p) a2 -= C[r][i + p][t + q] * W[i + 2 * p][t + 2 * q];  // body diagonals
-              acc[t][i] = a2;
-            }
-          }
-      }
+      // operand plane k + 1: completes node plane k (with cell plane k), adds the centre
+      // part of node plane k + 1 and starts node plane k + 2 (with cell plane k + 1)
+      float W[RX + 2][RY + 2], Cl[RX + 1][RY + 1];
+      load_cells(k, Cl);
+      load_win(xkp, W);
+      off_term(accB, W, Cl);
+      const Acc& acc = accB;
+      const Acc& ctr = ctrk;
       // every node of the window is written (nodes x = N or y = N with 0), so the
       // stores and the partial sum are branch-free
       const float* o0 = raw_of(0, k, jk3) + own0;
@@ -749,7 +821,21 @@ __global__ void __launch_bounds__(256, 3) k_slab(SlabArgs A) {
             ux[t] = fmaf(0.5f, lo + hi, tv[t][0]);
           }
         }
-        hx[warp * 32 + lane] = ux[0];
+        hx[(k & 1) * 256 + warp * 32 + lane] = ux[0];
+      }
+      if (k < kend) {
+        float Ch[RX + 1][RY + 1];
+        load_cells(k + 1, Ch);
+        centre_term(accC, W, Cl, Ch);
+#pragma unroll
+        for (int t = 0; t < RY; ++t)
+#pragma unroll
+          for (int i = 0; i < RX; ++i) {
+            accB[t][i] = accC[t][i];
+            accC[t][i] = 0.f;
+            ctrk[t][i] = W[i + 1][t + 1];
+          }
+        off_term(accC, W, Ch);
       }
       }  // not RES
     }
@@ -761,34 +847,16 @@ __global__ void __launch_bounds__(256, 3) k_slab(SlabArgs A) {
       }
       red = 0.f;
     }
-    __syncthreads();
-    if (tid == 0 && !dead && k + kAhead <= kend + 1) issue(k + kAhead, false);
-    if constexpr (L::kRestr) {
-      // the coarse rows of this warp (fine rows t = 1, 3, .. of the warp, the last one
-      // with the first row of the warp above) and, warp 0, row y0 for coarse row (y0-1)/2
-      const float hn = warp < 7 ? hx[(warp + 1) * 32 + lane] : 0.f;
-      float sv[RY / 2];
-#pragma unroll
-      for (int c = 0; c < RY / 2; ++c) sv[c] = fmaf(0.5f, ux[2 * c] + (2 * c + 2 < RY ? ux[2 * c + 2] : hn), ux[2 * c + 1]);
-      const float sl = 0.5f * ux[0];
-      if (k & 1) {  // plane k completes coarse plane (k-1)/2 (half weight) and starts (k+1)/2
-#pragma unroll
-        for (int c = 0; c < RY / 2; ++c) zacc[c] = fmaf(0.5f, sv[c], zacc[c]);
-        zlow = fmaf(0.5f, sl, zlow);
-        if (k > kbeg) store_coarse((k - 1) >> 1, false);
-        else if (k == 1) store_coarse(0, true);
-#pragma unroll
-        for (int c = 0; c < RY / 2; ++c) zacc[c] = 0.5f * sv[c];
-        zlow = 0.5f * sl;
-        if (k == N - 1) store_coarse(G::NC, true);
-      } else {
-#pragma unroll
-        for (int c = 0; c < RY / 2; ++c) zacc[c] += sv[c];
-        zlow += sl;
-      }
+    if constexpr (kRes) {  // RES reads operand planes k-1 .. k+1: a second barrier
+      __syncthreads();
+      if (tid == 0 && !dead && k + kAhead <= kend + 1) issue(k + kAhead, false);
     }
     xk = xkp;
     jk3 = jk3p;
+  }
+  if constexpr (L::kRestr) {
+    __syncthreads();
+    restrict_plane(kend);
   }
   // the last copies of the chunk have been waited for (every issued plane is derived)
 }
