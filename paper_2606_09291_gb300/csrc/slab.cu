@@ -152,11 +152,13 @@ struct SlabSmem {
   static constexpr size_t xs = craw + (kPost ? sizeof(float) * 3 * G::CRAWF : 0);
   static constexpr size_t eps = xs + sizeof(float) * 3 * G::XPL;
   static constexpr size_t bar = eps + (kPost ? sizeof(float) * 2 * G::XPL : 0);
-  // RES: x of the thread's own nodes for the plane being computed, copied ahead
+  // RES: x (pairs) of the thread's own nodes for the plane being computed, copied ahead;
+  // APPLYX: x of the own nodes of the next plane
   static constexpr size_t xpre = (bar + 8 * kRing + 15) / 16 * 16;
   // PRE/PREU: the x-restricted first row of every warp, [plane parity][8 warps][32 lanes]
   static constexpr bool kRestr = MODE == SL_PRE || MODE == SL_PREU;
-  static constexpr size_t hx = xpre + (MODE == SL_RES ? sizeof(float2) * 256 * G::RX * G::RY : 0);
+  static constexpr size_t hx =
+      xpre + (MODE == SL_RES ? sizeof(float2) : (MODE == SL_APPLYX ? sizeof(float) : 0)) * 256 * G::RX * G::RY;
   static constexpr size_t total = hx + (kRestr ? sizeof(float) * 512 : 0);
   static_assert((sizeof(TA) == 4 && (MODE == SL_PREU || MODE == SL_POST)) || total + 1024 <= 228 * 1024 / 3,
                 "three blocks per SM");
@@ -176,9 +178,12 @@ __device__ __forceinline__ void bulk_copy(uint32_t dst, const void* src, uint32_
                "l"(src), "r"(bytes), "r"(bar)
                : "memory");
 }
-// 8-byte asynchronous copy into shared memory (the thread waits for its own copies)
+// 8- and 4-byte asynchronous copies into shared memory (the thread waits for its own copies)
 __device__ __forceinline__ void cp_async8(void* dst, const void* src) {
   asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async4(void* dst, const void* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(smem_u32(dst)), "l"(src) : "memory");
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
@@ -229,6 +234,7 @@ __global__ void __launch_bounds__(256, 3) k_slab(SlabArgs A) {
   float* xs = (float*)(sm + L::xs);    // [3][XPL]
   float* eps = (float*)(sm + L::eps);  // [2][XPL]
   float2* xpre = (float2*)(sm + L::xpre) + threadIdx.x * (G::RX * G::RY);  // RES: this thread's nodes
+  float* xq = (float*)(sm + L::xpre) + threadIdx.x * (G::RX * G::RY);    // APPLYX: this thread's nodes
   float* hx = (float*)(sm + L::hx);  // PRE/PREU: [plane parity][warp][lane]
   const uint32_t bar0 = smem_u32(sm + L::bar);
 
@@ -618,9 +624,22 @@ __global__ void __launch_bounds__(256, 3) k_slab(SlabArgs A) {
     }
   };
 
+  // APPLYX: x of the own interior nodes of plane m into xq, a plane ahead of its use
+  // (the epilogue of plane m - 1 issues it after its last use of xq)
+  auto prefetch_x = [&](int m) {
+    const float* xm = xg + (long long)m * N1 * N1 + gown;
+#pragma unroll
+    for (int t = 0; t < RY; ++t)
+#pragma unroll
+      for (int i = 0; i < RX; ++i)
+        if ((okb >> (t * RX + i)) & 1u) cp_async4(xq + t * RX + i, xm + t * N1 + i);
+    cp_async_commit();
+  };
+  if (MODE == SL_APPLYX && !A.xfirst) prefetch_x(kbeg);
+
   for (int k = kbeg; k <= kend; ++k) {
-    // APPLYX: this plane's x of the thread's nodes, loaded before the waits so the
-    // global latency overlaps the derive step
+    // RES: this plane's x of the thread's nodes, copied before the waits so the global
+    // latency overlaps the derive step
     const long long gk = (long long)k * N1 * N1 + gown;
     const int xkp = xk == 2 ? 0 : xk + 1, xkm = xk == 0 ? 2 : xk - 1;
     const int jk3p = jk3 == 2 ? 0 : jk3 + 1;
@@ -632,15 +651,7 @@ __global__ void __launch_bounds__(256, 3) k_slab(SlabArgs A) {
         for (int i = 0; i < RX; ++i) cp_async8(xpre + t * RX + i, xs_g + t * N1 + i);
       cp_async_commit();
     }
-    float xv[RY][RX];
     float tv[RY][RX];  // PRE/PREU: t of the own nodes
-    if (MODE == SL_APPLYX) {
-#pragma unroll
-      for (int t = 0; t < RY; ++t)
-#pragma unroll
-        for (int i = 0; i < RX; ++i)
-          xv[t][i] = (!A.xfirst && ((okb >> (t * RX + i)) & 1u)) ? xg[gk + t * N1 + i] : 0.f;
-    }
     if (k + 1 <= kend + 1) {
       wait_plane(k + 1);
       derive(k + 1, xkp, jk3p, true);
@@ -776,6 +787,14 @@ __global__ void __launch_bounds__(256, 3) k_slab(SlabArgs A) {
       off_term(accB, W, Cl);
       const Acc& acc = accB;
       const Acc& ctr = ctrk;
+      float xv[RY][RX];  // APPLYX: x of the own nodes (0 where not interior or not read)
+      if constexpr (MODE == SL_APPLYX) {
+        if (!A.xfirst) cp_async_wait_all();
+#pragma unroll
+        for (int t = 0; t < RY; ++t)
+#pragma unroll
+          for (int i = 0; i < RX; ++i) xv[t][i] = (!A.xfirst && ((okb >> (t * RX + i)) & 1u)) ? xq[t * RX + i] : 0.f;
+      }
       // every node of the window is written (nodes x = N or y = N with 0), so the
       // stores and the partial sum are branch-free
       const float* o0 = raw_of(0, k, jk3) + own0;
@@ -808,6 +827,9 @@ __global__ void __launch_bounds__(256, 3) k_slab(SlabArgs A) {
             red = fmaf(rv, zv, red);
           }
         }
+      }
+      if constexpr (MODE == SL_APPLYX) {  // after the stores that used this plane's xq
+        if (!A.xfirst && k < kend) prefetch_x(k + 1);
       }
       if constexpr (L::kRestr) {  // x-restriction of the thread's rows at coarse column cx
 #pragma unroll
