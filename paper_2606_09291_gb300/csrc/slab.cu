@@ -152,13 +152,13 @@ struct SlabSmem {
   static constexpr size_t xs = craw + (kPost ? sizeof(float) * 3 * G::CRAWF : 0);
   static constexpr size_t eps = xs + sizeof(float) * 3 * G::XPL;
   static constexpr size_t bar = eps + (kPost ? sizeof(float) * 2 * G::XPL : 0);
-  // RES: x (pairs) of the thread's own nodes for the plane being computed, copied ahead;
-  // APPLYX: x of the own nodes of the next plane
+  // RES: x and the residual pairs rr_in of the thread's own nodes for the plane being
+  // computed, copied ahead; APPLYX: x of the own nodes of the next plane
   static constexpr size_t xpre = (bar + 8 * kRing + 15) / 16 * 16;
   // PRE/PREU: the x-restricted first row of every warp, [plane parity][8 warps][32 lanes]
   static constexpr bool kRestr = MODE == SL_PRE || MODE == SL_PREU;
   static constexpr size_t hx =
-      xpre + (MODE == SL_RES ? sizeof(float2) : (MODE == SL_APPLYX ? sizeof(float) : 0)) * 256 * G::RX * G::RY;
+      xpre + (MODE == SL_RES ? 2 * sizeof(float2) : (MODE == SL_APPLYX ? sizeof(float) : 0)) * 256 * G::RX * G::RY;
   static constexpr size_t total = hx + (kRestr ? sizeof(float) * 512 : 0);
   static_assert((sizeof(TA) == 4 && (MODE == SL_PREU || MODE == SL_POST)) || total + 1024 <= 228 * 1024 / 3,
                 "three blocks per SM");
@@ -234,6 +234,7 @@ __global__ void __launch_bounds__(256, 3) k_slab(SlabArgs A) {
   float* xs = (float*)(sm + L::xs);    // [3][XPL]
   float* eps = (float*)(sm + L::eps);  // [2][XPL]
   float2* xpre = (float2*)(sm + L::xpre) + threadIdx.x * (G::RX * G::RY);  // RES: this thread's nodes
+  float2* rpre = (float2*)(sm + L::xpre) + (256 + threadIdx.x) * (G::RX * G::RY);  // RES: rr_in of them
   float* xq = (float*)(sm + L::xpre) + threadIdx.x * (G::RX * G::RY);    // APPLYX: this thread's nodes
   float* hx = (float*)(sm + L::hx);  // PRE/PREU: [plane parity][warp][lane]
   const uint32_t bar0 = smem_u32(sm + L::bar);
@@ -636,21 +637,26 @@ __global__ void __launch_bounds__(256, 3) k_slab(SlabArgs A) {
     cp_async_commit();
   };
   if (MODE == SL_APPLYX && !A.xfirst) prefetch_x(kbeg);
+  // RES: x and rr_in of the own nodes of plane m into xpre, rpre, a plane ahead of their use
+  auto prefetch_res = [&](int m) {
+    const long long gm = (long long)m * N1 * N1 + gown;
+    const float2* xs_g = A.xp + s * kNodes + gm;
+    const float2* rr_g = A.rr_in + s * A.rr_stride + gm;
+#pragma unroll
+    for (int t = 0; t < RY; ++t)
+#pragma unroll
+      for (int i = 0; i < RX; ++i) {
+        if (!A.assign) cp_async8(xpre + t * RX + i, xs_g + t * N1 + i);
+        if ((okb >> (t * RX + i)) & 1u) cp_async8(rpre + t * RX + i, rr_g + t * N1 + i);
+      }
+    cp_async_commit();
+  };
+  if constexpr (kRes) prefetch_res(kbeg);
 
   for (int k = kbeg; k <= kend; ++k) {
-    // RES: this plane's x of the thread's nodes, copied before the waits so the global
-    // latency overlaps the derive step
     const long long gk = (long long)k * N1 * N1 + gown;
     const int xkp = xk == 2 ? 0 : xk + 1, xkm = xk == 0 ? 2 : xk - 1;
     const int jk3p = jk3 == 2 ? 0 : jk3 + 1;
-    if (kRes && !A.assign) {  // x of the own nodes, consumed by this plane's epilogue
-      const float2* xs_g = A.xp + s * kNodes + gk;
-#pragma unroll
-      for (int t = 0; t < RY; ++t)
-#pragma unroll
-        for (int i = 0; i < RX; ++i) cp_async8(xpre + t * RX + i, xs_g + t * N1 + i);
-      cp_async_commit();
-    }
     float tv[RY][RX];  // PRE/PREU: t of the own nodes
     if (k + 1 <= kend + 1) {
       wait_plane(k + 1);
@@ -742,10 +748,10 @@ __global__ void __launch_bounds__(256, 3) k_slab(SlabArgs A) {
         }
         constexpr double kH12 = 1.0 / (12.0 * N);
         const float sch = (float)kH12, scl = (float)(kH12 - (double)(float)kH12);  // h/12 as an FP32 pair
-        const float2* rri = A.rr_in + s * A.rr_stride;
+
         float2* rro = A.rr_out + s * kNodes;
         float2* xo = A.xp + s * kNodes;
-        if (!A.assign) cp_async_wait_all();
+        cp_async_wait_all();
 #pragma unroll
         for (int t = 0; t < RY; ++t) {
 #pragma unroll
@@ -755,7 +761,7 @@ __global__ void __launch_bounds__(256, 3) k_slab(SlabArgs A) {
             const P2 axs = two_sum(Sa[t][i], Ca[t][i]);
             const float pp = __fmul_rn(axs.h, sch);  // (A inc) as a pair (pp, pe)
             const float pe = __fmaf_rn(axs.h, scl, __fmaf_rn(axs.l, sch, __fmaf_rn(axs.h, sch, -pp)));
-            const float2 bv = ok ? rri[g] : make_float2(0.f, 0.f);
+            const float2 bv = ok ? rpre[t * RX + i] : make_float2(0.f, 0.f);
             const P2 dd = two_sum(bv.x, -pp);
             const float e = dd.l + (bv.y - pe);
             const float rh = dd.h + e;  // renormalised pair (rh, rl)
@@ -778,6 +784,7 @@ __global__ void __launch_bounds__(256, 3) k_slab(SlabArgs A) {
             xo[g] = ok ? xn : make_float2(0.f, 0.f);
           }
         }
+        if (k < kend) prefetch_res(k + 1);  // after the last use of xpre and rpre
       } else {
       // operand plane k + 1: completes node plane k (with cell plane k), adds the centre
       // part of node plane k + 1 and starts node plane k + 2 (with cell plane k + 1)
