@@ -99,81 +99,91 @@ __global__ void k_field(const double* __restrict__ xi, int K, const ModeTable mt
 }
 
 // FP32-coefficient synthesis (the mixed path needs only a = exp(log a) rounded to
-// FP32 and BF16): stage 1 (T2) in FP32 pair arithmetic from c_k phi_{iz_k}(z)
-// (formed in FP64 once per block and split) and the pair tables;
+// FP32 and BF16).  One block per (chunk of kFieldPlanes z planes, sample): the 1D
+// tables and c_k are split into FP32 pairs once per block (the only FP64 work),
+// then per plane c_k phi_{iz_k}(z) is a pair product and stage 1 (T2) runs in FP32
+// pair arithmetic;
 // stage 2 contracts over i in pair arithmetic (exact products by FMA, two-sum
 // accumulation: about 44 significant bits, far below the FP32 rounding of a), four
 // consecutive cells in x per thread; exp by a Cody-Waite reduction against ln 2 split
 // into a 16-bit head (exact multiples for |k| < 256) and its remainder, then expf.
-// Dynamic shared memory: c_k phi(z) pairs [K rounded up to even], then T2 hi/lo
-// [n1x][N] and phi hi/lo [n1d][N] (floats; 16-byte aligned for the float4 reads
-// since N % 4 == 0 is required).
+// Dynamic shared memory: c_k phi(z) pairs and c_k pairs [K rounded up to even each],
+// then T2 hi/lo [n1x][N] and phi hi/lo [n1d][N] (floats; 16-byte aligned for the
+// float4 reads since N % 4 == 0 is required).
+constexpr int kFieldPlanes = 16;
 constexpr float kLn2Hi = 0.693145751953125f;        // ln 2 truncated to 16 bits
 constexpr float kLn2Lo = 1.4286068202862268e-06f;   // ln 2 - kLn2Hi
 __global__ void k_field_df(const double* __restrict__ xi, int K, const ModeTable mt, const double* __restrict__ phi,
                            int N, float* __restrict__ a32, __nv_bfloat16* __restrict__ abf) {
   extern __shared__ __align__(16) unsigned char smf[];
   float2* cz = reinterpret_cast<float2*>(smf);  // c_k phi_{iz_k}(z) as pairs
-  float* T2h = reinterpret_cast<float*>(cz + ((K + 1) & ~1));
+  float2* ck = cz + ((K + 1) & ~1);             // c_k as pairs
+  float* T2h = reinterpret_cast<float*>(ck + ((K + 1) & ~1));
   float* T2l = T2h + mt.n1x * N;
   float* Ph = T2l + mt.n1x * N;  // all 1D tables as pairs
   float* Pl = Ph + mt.n1d * N;
-  const int z = blockIdx.x, s = blockIdx.y;
-  for (int k = threadIdx.x; k < K; k += blockDim.x) {
-    const double v = mt.scale[k] * xi[(long long)s * K + k] * phi[mt.iz[k] * N + z];
-    cz[k] = df_split(v);
-  }
+  const int s = blockIdx.y;
+  for (int k = threadIdx.x; k < K; k += blockDim.x) ck[k] = df_split(mt.scale[k] * xi[(long long)s * K + k]);
   for (int e = threadIdx.x; e < mt.n1d * N; e += blockDim.x) {
     const double v = phi[e];
     const float h = (float)v;
     Ph[e] = h;
     Pl[e] = (float)(v - (double)h);
   }
-  __syncthreads();
-  for (int e = threadIdx.x; e < mt.n1x * N; e += blockDim.x) {
-    const int i = e / N, y = e % N;
-    DF acc{0.f, 0.f};
-    for (int t = mt.offs[i]; t < mt.offs[i + 1]; ++t) {
-      const int k = mt.order[t];
-      const int o = mt.iy[k] * N + y;
-      acc = df_add(acc, df_mul(df_make(cz[k]), DF{Ph[o], Pl[o]}));
+  const int z0 = kFieldPlanes * blockIdx.x, z1 = min(N, z0 + kFieldPlanes);
+  for (int z = z0; z < z1; ++z) {
+    __syncthreads();  // the tables (first plane); the previous plane's T2 reads done
+    for (int k = threadIdx.x; k < K; k += blockDim.x) {
+      const int o = mt.iz[k] * N + z;
+      const DF v = df_mul(df_make(ck[k]), DF{Ph[o], Pl[o]});
+      cz[k] = make_float2(v.h, v.l);
     }
-    T2h[e] = acc.h;
-    T2l[e] = acc.l;
-  }
-  __syncthreads();
-  const long long base = (long long)s * N * N * N + (long long)z * N * N;
-  const int nq = N / 4;
-  for (int e = threadIdx.x; e < N * nq; e += blockDim.x) {
-    const int x0 = 4 * (e % nq), y = e / nq;
-    float S[4] = {0.f, 0.f, 0.f, 0.f}, C[4] = {0.f, 0.f, 0.f, 0.f};
-    for (int i = 0; i < mt.n1x; ++i) {
-      const float th = T2h[i * N + y], tl = T2l[i * N + y];
-      const float4 phv = *reinterpret_cast<const float4*>(Ph + i * N + x0);
-      const float4 plv = *reinterpret_cast<const float4*>(Pl + i * N + x0);
-      const float pv[4] = {phv.x, phv.y, phv.z, phv.w}, lv[4] = {plv.x, plv.y, plv.z, plv.w};
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const float p = __fmul_rn(th, pv[q]);
-        const float pe = __fmaf_rn(th, lv[q], __fmaf_rn(tl, pv[q], __fmaf_rn(th, pv[q], -p)));
-        const float sum = __fadd_rn(S[q], p);  // two-sum of S and p (intrinsics: never contracted)
-        const float bb = __fsub_rn(sum, S[q]);
-        C[q] = __fadd_rn(C[q], __fadd_rn(__fadd_rn(__fsub_rn(S[q], __fsub_rn(sum, bb)), __fsub_rn(p, bb)), pe));
-        S[q] = sum;
+    __syncthreads();
+    for (int e = threadIdx.x; e < mt.n1x * N; e += blockDim.x) {
+      const int i = e / N, y = e % N;
+      DF acc{0.f, 0.f};
+      for (int t = mt.offs[i]; t < mt.offs[i + 1]; ++t) {
+        const int k = mt.order[t];
+        const int o = mt.iy[k] * N + y;
+        acc = df_add(acc, df_mul(df_make(cz[k]), DF{Ph[o], Pl[o]}));
       }
+      T2h[e] = acc.h;
+      T2l[e] = acc.l;
     }
-    float av[4];
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const float kf = rintf(S[q] * 1.44269504f);
-      const float r = ((S[q] - kf * kLn2Hi) - kf * kLn2Lo) + C[q];
-      av[q] = ldexpf(expf(r), (int)kf);
-    }
-    const long long o = base + (long long)y * N + x0;
-    if (a32) *reinterpret_cast<float4*>(a32 + o) = make_float4(av[0], av[1], av[2], av[3]);
-    if (abf) {
-#pragma unroll
-      for (int q = 0; q < 4; ++q) abf[o + q] = __float2bfloat16_rn(av[q]);
+    __syncthreads();
+    const long long base = (long long)s * N * N * N + (long long)z * N * N;
+    const int nq = N / 4;
+    for (int e = threadIdx.x; e < N * nq; e += blockDim.x) {
+      const int x0 = 4 * (e % nq), y = e / nq;
+      float S[4] = {0.f, 0.f, 0.f, 0.f}, C[4] = {0.f, 0.f, 0.f, 0.f};
+      for (int i = 0; i < mt.n1x; ++i) {
+        const float th = T2h[i * N + y], tl = T2l[i * N + y];
+        const float4 phv = *reinterpret_cast<const float4*>(Ph + i * N + x0);
+        const float4 plv = *reinterpret_cast<const float4*>(Pl + i * N + x0);
+        const float pv[4] = {phv.x, phv.y, phv.z, phv.w}, lv[4] = {plv.x, plv.y, plv.z, plv.w};
+  #pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const float p = __fmul_rn(th, pv[q]);
+          const float pe = __fmaf_rn(th, lv[q], __fmaf_rn(tl, pv[q], __fmaf_rn(th, pv[q], -p)));
+          const float sum = __fadd_rn(S[q], p);  // two-sum of S and p (intrinsics: never contracted)
+          const float bb = __fsub_rn(sum, S[q]);
+          C[q] = __fadd_rn(C[q], __fadd_rn(__fadd_rn(__fsub_rn(S[q], __fsub_rn(sum, bb)), __fsub_rn(p, bb)), pe));
+          S[q] = sum;
+        }
+      }
+      float av[4];
+  #pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const float kf = rintf(S[q] * 1.44269504f);
+        const float r = ((S[q] - kf * kLn2Hi) - kf * kLn2Lo) + C[q];
+        av[q] = ldexpf(expf(r), (int)kf);
+      }
+      const long long o = base + (long long)y * N + x0;
+      if (a32) *reinterpret_cast<float4*>(a32 + o) = make_float4(av[0], av[1], av[2], av[3]);
+      if (abf) {
+  #pragma unroll
+        for (int q = 0; q < 4; ++q) abf[o + q] = __float2bfloat16_rn(av[q]);
+      }
     }
   }
 }
@@ -186,7 +196,7 @@ cudaError_t launch_field(const double* xi, int K, const ModeTable& mt, const dou
                          const FieldOut& out, cudaStream_t st) {
   if (S == 0) return cudaSuccess;
   if (!out.log_a && !out.a64 && (out.a32 || out.abf) && N % 4 == 0) {
-    const size_t smem = sizeof(float2) * (size_t)((K + 1) & ~1) +
+    const size_t smem = 2 * sizeof(float2) * (size_t)((K + 1) & ~1) +
                         sizeof(float) * (2 * (size_t)mt.n1x * N + 2 * (size_t)mt.n1d * N);
     static size_t smem_df = 48 * 1024;
     if (smem > smem_df) {
@@ -196,7 +206,8 @@ cudaError_t launch_field(const double* xi, int K, const ModeTable& mt, const dou
     }
     const double cells = (double)S * N * N * N;
     launch_flops("field", (double)S * K * 8 + cells * ((out.a32 ? 4 : 0) + (out.abf ? 2 : 0)),
-                 2.0 * cells * mt.n1x + 2.0 * (double)S * K * N * N, k_field_df, dim3(N, S), kBlock, smem, st, xi, K,
+                 2.0 * cells * mt.n1x + 2.0 * (double)S * K * N * N, k_field_df,
+                 dim3((unsigned)((N + kFieldPlanes - 1) / kFieldPlanes), S), kBlock, smem, st, xi, K,
                  mt, phi, N, out.a32, out.abf);
     return cudaGetLastError();
   }

@@ -645,16 +645,20 @@ __global__ void __launch_bounds__(NT) k_phi_tiled(const double* __restrict__ y, 
 // the same separable sums in pair arithmetic (no FP64 instruction), the 1D tables as
 // pairs, M e written as pairs (the adjoint solve's right-hand side), the partial
 // e.M e of each block returned in FP64.  Each thread takes kPhiRows rows of a
-// 32 x (8 kPhiRows) tile, so the three block barriers of a plane serve four nodes.
+// 32 x (8 kPhiRows) tile, so the three block barriers of a plane serve four nodes;
+// the staged plane is double-buffered and plane m + 1 is copied asynchronously while
+// plane m is summed.
 constexpr int kPhiRows = 4;
 constexpr int kPhiTY = TY * kPhiRows;                        // tile rows
 constexpr int kPhiNPY = kPhiTY + 2, kPhiNP = NPX * kPhiNPY;  // staged plane with halo
+constexpr size_t kPhiSmem = sizeof(float2) * (2 * kPhiNP + kPhiNPY * TX + 3 * kPhiTY * TX);
 __global__ void __launch_bounds__(NT) k_phi_tiled_df(const float2* __restrict__ y, int N, const float2* __restrict__ gtab,
                                                      const float2* __restrict__ mgtab, float2* __restrict__ badj,
                                                      double* __restrict__ partial, int nzc, int zc, int nseg) {
-  __shared__ float2 ys[kPhiNP];
-  __shared__ float2 xsum[kPhiNPY][TX];
-  __shared__ float2 mxy[3][kPhiTY][TX];
+  extern __shared__ __align__(16) unsigned char smp[];
+  float2* ysb = reinterpret_cast<float2*>(smp);  // [2][kPhiNP]: plane m in buffer m & 1
+  float2(*xsum)[TX] = reinterpret_cast<float2(*)[TX]>(ysb + 2 * kPhiNP);                   // [kPhiNPY][TX]
+  float2(*mxy)[kPhiTY][TX] = reinterpret_cast<float2(*)[kPhiTY][TX]>(ysb + 2 * kPhiNP + kPhiNPY * TX);  // [3]
   const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * TX + tx;
   const int n1 = N + 1;
   const int s = blockIdx.z / nzc, chunk = blockIdx.z % nzc;
@@ -667,15 +671,24 @@ __global__ void __launch_bounds__(NT) k_phi_tiled_df(const float2* __restrict__ 
   const int ly0 = kPhiRows * ty;  // the thread's first tile row
   DF yc[kPhiRows], yn[kPhiRows];  // y at the thread's nodes of planes k and k + 1
   auto four = [](DF a) { return DF{4.f * a.h, 4.f * a.l}; };  // exact
-  auto advance = [&](int m, DF* ycen) {
-    const int r3 = (m + 3) % 3;
+  auto load = [&](int m) {  // plane m into buffer m & 1 (zeros outside the grid)
+    float2* ys = ysb + (m & 1) * kPhiNP;
     for (int e = tid; e < kPhiNP; e += NT) {
       const int lx = e % NPX, ly = e / NPX;
       const int i = x0 - 1 + lx, j = y0 - 1 + ly;
-      ys[e] = (m >= 0 && m <= N && i <= N && j <= N) ? yb[i + (long long)n1 * (j + (long long)n1 * m)]
-                                                      : make_float2(0.f, 0.f);
+      const bool ok = m >= 0 && m <= N && i <= N && j <= N;
+      cp_async<8>(ys + e, ok ? yb + i + (long long)n1 * (j + (long long)n1 * m) : yb, ok);
     }
+    cp_async_commit();
+  };
+  // plane m (copied by load(m)) into the x and xy sums; copies plane m + 1 meanwhile
+  // (into the buffer of plane m - 1, whose last reads precede the first barrier)
+  auto advance = [&](int m, DF* ycen) {
+    const int r3 = (m + 3) % 3;
+    const float2* ys = ysb + (m & 1) * kPhiNP;
+    cp_async_wait<0>();
     __syncthreads();
+    if (m + 1 <= kend + 1) load(m + 1);
     for (int e = tid; e < kPhiNPY * TX; e += NT) {
       const int ly = e / TX, lx = e % TX;
       const float2* row = ys + NPX * ly + lx;
@@ -695,6 +708,7 @@ __global__ void __launch_bounds__(NT) k_phi_tiled_df(const float2* __restrict__ 
   const double h6 = 1.0 / (6.0 * N);
   const DF h63 = df_make(df_split(h6 * h6 * h6));
   DF red{0.f, 0.f};
+  load(kbeg - 1);
   advance(kbeg - 1, yn);
   advance(kbeg, yc);
   const DF mgi = gi < N ? df_make(mgtab[gi]) : DF{0.f, 0.f}, ggi = gi < N ? df_make(gtab[gi]) : DF{0.f, 0.f};
@@ -870,8 +884,13 @@ void tiled_res64(const float2* b, long long bstride, const float2* x, const floa
 int tiled_phi_df(const float2* y, int N, int S, const float2* gtab, const float2* mgtab, float2* badj,
                  double* partial, cudaStream_t st) {
   const TiledShape t = tiled_shape(N, S, kPhiRows);
+  static bool smem_set = false;  // once (capture-friendly)
+  if (!smem_set) {
+    cudaFuncSetAttribute(k_phi_tiled_df, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kPhiSmem);
+    smem_set = true;
+  }
   launch("phi_adjrhs", (double)S * nodes_of(N) * 16, k_phi_tiled_df, dim3(t.bx, t.by, (unsigned)(S * t.nzc)),
-         dim3(TX, TY), 0, st, y, N, gtab, mgtab, badj, partial, t.nzc, t.zc, t.nseg);
+         dim3(TX, TY), kPhiSmem, st, y, N, gtab, mgtab, badj, partial, t.nzc, t.zc, t.nseg);
   return t.blocks_per_sample;
 }
 
