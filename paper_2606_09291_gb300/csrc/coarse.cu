@@ -195,6 +195,15 @@ __device__ void post_level(const T* r, const T* a, const T* d, const T* x, T* z,
   }
 }
 
+// asynchronous element copy into shared memory (4 or 8 bytes; the thread waits for its
+// own copies, a block barrier then publishes them)
+template <typename T>
+__device__ __forceinline__ void cp_async_elem(T* dst, const T* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], %2;\n" ::"r"((unsigned)__cvta_generic_to_shared(dst)), "l"(src),
+               "n"(sizeof(T))
+               : "memory");
+}
+
 struct CoarseArgs {
   const void* r;      // restricted residual on the 16^3 level, [S][17^3]
   const void* a[4];   // cell coefficient of the levels 16^3, 8^3, 4^3, 2^3, [S][cells]
@@ -212,15 +221,18 @@ __global__ void __launch_bounds__(kCT, sizeof(T) == 4 ? 2 : 1) k_coarse_vcycle(C
   extern __shared__ __align__(16) unsigned char smraw[];
   T* sm = (T*)smraw;
   const T omega = (T)A.omega;
+  // r and the four coefficient levels, all copies in flight at once
   const T* rg = (const T*)A.r + (long long)s * Lv<16>::nodes;
-  for (int n = threadIdx.x; n < Lv<16>::nodes; n += kCT) sm[M::r16 + n] = rg[n];
+  for (int n = threadIdx.x; n < Lv<16>::nodes; n += kCT) cp_async_elem(sm + M::r16 + n, rg + n);
   const int aoff[4] = {M::a16, M::a8, M::a4, M::a2};
   const int acnt[4] = {Lv<16>::cells, Lv<8>::cells, Lv<4>::cells, Lv<2>::cells};
 #pragma unroll
   for (int l = 0; l < 4; ++l) {
     const T* ag = (const T*)A.a[l] + (long long)s * acnt[l];
-    for (int n = threadIdx.x; n < acnt[l]; n += kCT) sm[aoff[l] + n] = ag[n];
+    for (int n = threadIdx.x; n < acnt[l]; n += kCT) cp_async_elem(sm + aoff[l] + n, ag + n);
   }
+  asm volatile("cp.async.commit_group;\n" ::: "memory");
+  asm volatile("cp.async.wait_all;\n" ::: "memory");
   __syncthreads();
   dinv_level<T>(sm + M::a16, sm + M::d16);
   __syncthreads();

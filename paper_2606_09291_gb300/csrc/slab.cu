@@ -188,17 +188,22 @@ __device__ __forceinline__ void cp_async4(void* dst, const void* src) {
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 
-// bounded wait for phase `parity` of the barrier; false after about a second
+__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
+  uint32_t done;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(done)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return done != 0;
+}
+// bounded wait for phase `parity` of the barrier; false after about a second (the
+// clock is read only when the first try finds the phase incomplete)
 __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+  if (mbar_try(bar, parity)) return true;
   const long long t0 = clock64();
   for (;;) {
-    uint32_t done;
-    asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-        : "=r"(done)
-        : "r"(bar), "r"(parity)
-        : "memory");
-    if (done) return true;
+    if (mbar_try(bar, parity)) return true;
     if (clock64() - t0 > (2LL << 30)) return false;
   }
 }
@@ -340,11 +345,13 @@ __global__ void __launch_bounds__(256, 3) k_slab(SlabArgs A) {
   // the same for the coarse interpolation items (a, b): bit 4j + (p + 2q) for coarse
   // node (a + p, cy0 + b + q) on the coarse boundary
   unsigned cbnd = 0;
+  int ioff[G::NI];  // interpolation item j: offset 2a + 2b (N + 2) of its fine node (2a, 2b)
   if (kPost) {
 #pragma unroll
     for (int j = 0; j < G::NI; ++j) {
       const int it = tid + 256 * j;
       const int a = it % G::NC1, b = it / G::NC1;
+      ioff[j] = 2 * a + 2 * XS * b;
 #pragma unroll
       for (int q = 0; q < 2; ++q)
 #pragma unroll
@@ -369,12 +376,11 @@ __global__ void __launch_bounds__(256, 3) k_slab(SlabArgs A) {
     for (int j = 0; j < G::NI; ++j) {
       const int it = tid + 256 * j;
       if (j == G::NI - 1 && it >= G::NC1 * (G::CNR - 1)) break;
-      const int a = it % G::NC1, b = it / G::NC1;
-      const float* q = cp + a + G::NC1 * b;
+      const float* q = cp + it;  // coarse node (a, b) of item it = a + (N/2 + 1) b
       const unsigned mk = all >> (4 * j);
       const float e00 = (mk & 1u) ? 0.f : q[0], e10 = (mk & 2u) ? 0.f : q[1];
       const float e01 = (mk & 4u) ? 0.f : q[G::NC1], e11 = (mk & 8u) ? 0.f : q[G::NC1 + 1];
-      float* o = ed + 2 * a + XS * (2 * b);
+      float* o = ed + ioff[j];
       const float r0 = 0.5f * (e00 + e10), r1 = 0.5f * (e01 + e11);
       o[0] = e00;
       o[1] = r0;
