@@ -31,7 +31,7 @@ METRIC = "sample-gradients/s (state+adjoint) at rtol 1e-8 vs plain FP64; p99 lat
 # traffic is this ratio times its algorithmic bytes (ncu on the 64^3 slab launches of a
 # 256-sample batch, profiles/slab_passes_c3_ncu.md).  Only valid for the kernel as
 # captured: emptied with each change of that kernel until it is captured again.
-TRAFFIC_RATIO = {"apply_f32": 0.996, "post_f32": 1.018}
+TRAFFIC_RATIO = {"apply_f32": 0.996, "pre_f32": 1.037, "post_f32": 1.017}
 # ALU-bound classes: the operations their launch sites count, against the issue rate of
 # the units that execute them (152 SMs at 2070 MHz: 128 FP32 lanes per SM; FP64 at the
 # nominal 1.25 TFLOP/s, i.e. 0.625 T operations/s)
