@@ -586,6 +586,7 @@ __global__ void __launch_bounds__(256, 3) k_slab(SlabArgs A) {
   // node planes k and k + 1 summed so far (below, then centre) and the operand of node
   // plane k at the own nodes, entering iteration k
   float accB[RY][RX], accC[RY][RX], ctrk[RY][RX];
+  float Cn[RX + 1][RY + 1];  // cell plane k, loaded as the upper plane of iteration k - 1
   if constexpr (!kRes) {
     float W[RX + 2][RY + 2], Cl[RX + 1][RY + 1], Ch[RX + 1][RY + 1];
 #pragma unroll
@@ -603,6 +604,10 @@ __global__ void __launch_bounds__(256, 3) k_slab(SlabArgs A) {
 #pragma unroll
       for (int i = 0; i < RX; ++i) ctrk[t][i] = W[i + 1][t + 1];
     off_term(accC, W, Ch);
+#pragma unroll
+    for (int c = 0; c < RX + 1; ++c)
+#pragma unroll
+      for (int r = 0; r < RY + 1; ++r) Cn[c][r] = Ch[c][r];
   }
   float ux[RY];  // PRE/PREU: x-restricted rows of the last computed plane
   // PRE/PREU: the coarse rows of this warp from plane k (fine rows t = 1, 3, .. of the
@@ -794,8 +799,8 @@ __global__ void __launch_bounds__(256, 3) k_slab(SlabArgs A) {
       } else {
       // operand plane k + 1: completes node plane k (with cell plane k), adds the centre
       // part of node plane k + 1 and starts node plane k + 2 (with cell plane k + 1)
-      float W[RX + 2][RY + 2], Cl[RX + 1][RY + 1];
-      load_cells(k, Cl);
+      float W[RX + 2][RY + 2];
+      const Cel& Cl = Cn;
       load_win(xkp, W);
       off_term(accB, W, Cl);
       const Acc& acc = accB;
@@ -871,6 +876,10 @@ __global__ void __launch_bounds__(256, 3) k_slab(SlabArgs A) {
             ctrk[t][i] = W[i + 1][t + 1];
           }
         off_term(accC, W, Ch);
+#pragma unroll
+        for (int c = 0; c < RX + 1; ++c)
+#pragma unroll
+          for (int r = 0; r < RY + 1; ++r) Cn[c][r] = Ch[c][r];
       }
       }  // not RES
     }
