@@ -253,16 +253,33 @@ __global__ void __launch_bounds__(256, 3) k_slab(SlabArgs A) {
   // PRE/PREU compute one more plane for the restriction (kend0 is even unless it is N-1)
   const int kend = (L::kRestr && kend0 < N - 1) ? kend0 + 1 : kend0;
   constexpr long long kNodes = (long long)N1 * N1 * N1;
+  // RES, first step: the block also owns the boundary nodes of its rows and planes
+  // (column x = 0; row 0 for the first row block; planes 0 and N for the first and
+  // last z chunk), whose solution is 0
+  const int rlo = blockIdx.y == 0 ? 0 : y0, rhi = min(N, y0 + TYT - 1);
+  const int kl = kbeg == 1 ? 0 : kbeg, kh = kend == N - 1 ? N : kend;
   if (A.sc != nullptr && !A.sc[s].active) {
-    if (kRes && A.assign) {  // a sample that takes no step: its solution is 0 (own nodes)
+    if (kRes && A.assign) {  // a sample that takes no step: its solution is 0 (every owned node)
       float2* xo = A.xp + s * kNodes;
-      for (int k = kbeg; k <= kend; ++k)
-        for (int e = tid; e < TYT * N; e += 256) {
-          const int y = y0 + e / N;
-          if (y <= N - 1) xo[(long long)k * N1 * N1 + (long long)y * N1 + 1 + e % N] = make_float2(0.f, 0.f);
-        }
+      const int per = (rhi - rlo + 1) * N1;
+      for (int k = kl; k <= kh; ++k)
+        for (int e = tid; e < per; e += 256)
+          xo[(long long)k * N1 * N1 + (long long)(rlo + e / N1) * N1 + e % N1] = make_float2(0.f, 0.f);
     }
     return;
+  }
+  if (kRes && A.assign) {
+    float2* xo = A.xp + s * kNodes;
+    for (int k = kl; k <= kh; ++k) {
+      float2* xk = xo + (long long)k * N1 * N1;
+      if (k == 0 || k == N) {
+        for (int e = tid; e < (rhi - rlo + 1) * N1; e += 256) xk[(rlo + e / N1) * N1 + e % N1] = make_float2(0.f, 0.f);
+      } else {
+        for (int y = max(rlo, 1) + tid; y <= rhi; y += 256) xk[y * N1] = make_float2(0.f, 0.f);
+        if (rlo == 0)
+          for (int x = tid; x <= N; x += 256) xk[x] = make_float2(0.f, 0.f);
+      }
+    }
   }
   if (*(volatile int*)A.err != 0) return;  // an earlier wait ran out: the results are void anyway
   constexpr long long kCells = (long long)N * N * N;

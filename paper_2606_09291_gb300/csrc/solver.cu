@@ -1040,16 +1040,12 @@ cudaError_t ir_mixed(SolverBufs& B, const float* a32, const __nv_bfloat16* abf, 
   const float2* bdf = b_pair ? b_pair : bsplit;
   // 32^3 and 64^3 grids: one slab pass per refinement step applies the inner solve's
   // last update to x and updates the residual pairs rr (B.bdf; b on the first step) by
-  // rr -= A inc, so x is only written at nodes its block owns; its boundary nodes are
-  // cleared here, once
+  // rr -= A inc, so x is only written at nodes its block owns; the first step also
+  // writes x's boundary nodes (0), each by the block that owns its rows and planes
   const bool sres = tiled && uses_slab(B, N, 4);
   const float* p_last = nullptr;
   if (inner_next <= 0) inner_next = inner_iters;
   int last_inner = inner_iters;  // inner iterations of the step the next refinement pass completes
-  if (sres) {
-    void* xb[1] = {xdf};
-    zero_boundary<double>(xb, 1, N, S, st);
-  }
   if (tiled) {
     const dim3 gi((unsigned)init_blocks(N), (unsigned)S);
     with_grid(N, [&](auto c) {
