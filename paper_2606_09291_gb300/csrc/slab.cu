@@ -116,6 +116,15 @@ __device__ __forceinline__ void res_term(float& S, float& comp, P2 c, float x) {
   S = t.h;
   comp = __fadd_rn(comp, __fadd_rn(t.l, NEG ? -low : low));
 }
+// the same for a single FP32 coefficient c (a cell of the body diagonals)
+template <bool NEG>
+__device__ __forceinline__ void res_term1(float& S, float& comp, float c, float x) {
+  const float p = __fmul_rn(c, x);
+  const float low = __fmaf_rn(c, x, -p);
+  const P2 t = two_sum(S, NEG ? -p : p);
+  S = t.h;
+  comp = __fadd_rn(comp, __fadd_rn(t.l, NEG ? -low : low));
+}
 
 template <int N>
 struct SlabGeo {
@@ -268,18 +277,16 @@ __global__ void __launch_bounds__(256, 3) k_slab(SlabArgs A) {
     }
     return;
   }
-  if (kRes && A.assign) {
+  if (kRes && A.assign) {  // row 0 and planes 0, N here; column x = 0 in the epilogue
     float2* xo = A.xp + s * kNodes;
-    for (int k = kl; k <= kh; ++k) {
-      float2* xk = xo + (long long)k * N1 * N1;
-      if (k == 0 || k == N) {
-        for (int e = tid; e < (rhi - rlo + 1) * N1; e += 256) xk[(rlo + e / N1) * N1 + e % N1] = make_float2(0.f, 0.f);
-      } else {
-        for (int y = max(rlo, 1) + tid; y <= rhi; y += 256) xk[y * N1] = make_float2(0.f, 0.f);
-        if (rlo == 0)
-          for (int x = tid; x <= N; x += 256) xk[x] = make_float2(0.f, 0.f);
-      }
-    }
+    if (rlo == 0)
+      for (int e = tid; e < (kend - kbeg + 1) * N1; e += 256)
+        xo[(long long)(kbeg + e / N1) * N1 * N1 + e % N1] = make_float2(0.f, 0.f);
+    const int per = (rhi - rlo + 1) * N1;
+    if (kl == 0)
+      for (int e = tid; e < per; e += 256) xo[rlo * N1 + e] = make_float2(0.f, 0.f);
+    if (kh == N)
+      for (int e = tid; e < per; e += 256) xo[(long long)N * N1 * N1 + rlo * N1 + e] = make_float2(0.f, 0.f);
   }
   if (*(volatile int*)A.err != 0) return;  // an earlier wait ran out: the results are void anyway
   constexpr long long kCells = (long long)N * N * N;
@@ -768,7 +775,7 @@ __global__ void __launch_bounds__(256, 3) k_slab(SlabArgs A) {
 #pragma unroll
                 for (int q = 0; q < 2; ++q)
 #pragma unroll
-                  for (int p = 0; p < 2; ++p) res_term<true>(S, cmp, P2{C[r][i + p][t + q], 0.f}, W[i + 2 * p][t + 2 * q]);
+                  for (int p = 0; p < 2; ++p) res_term1<true>(S, cmp, C[r][i + p][t + q], W[i + 2 * p][t + 2 * q]);
                 Sa[t][i] = S;
                 Ca[t][i] = cmp;
               }
@@ -811,6 +818,7 @@ __global__ void __launch_bounds__(256, 3) k_slab(SlabArgs A) {
             }
             xo[g] = ok ? xn : make_float2(0.f, 0.f);
           }
+          if (A.assign && lane == 0) xo[gk + t * N1 - 1] = make_float2(0.f, 0.f);  // column x = 0
         }
         if (k < kend) prefetch_res(k + 1);  // after the last use of xpre and rpre
       } else {
@@ -992,9 +1000,10 @@ void slab_apply(const float* z, const float* pold, float* pnew, const float* a, 
 }
 
 // FP32 operations per interior node of the refinement step as written (no sharing
-// between nodes): 12 exact cell-pair sums (6 each), the 8-cell sum (28), 21 compensated
-// product terms (11 each), the scaling and subtraction (16), r.r and the pair update of x (10)
-constexpr double kResOpsPerNode = 12 * 6 + 28 + 21 * 11 + 16 + 10;
+// between nodes): 12 exact cell-pair sums (6 each), the 8-cell sum (28), 13 compensated
+// products with a pair coefficient (11 each) and 8 with a single cell (10 each), the
+// scaling and subtraction (16), r.r and the pair update of x (10)
+constexpr double kResOpsPerNode = 12 * 6 + 28 + 13 * 11 + 8 * 10 + 16 + 10;
 
 void slab_res(const float* d, const float* p, bool d_zero, const SolveScalars* sci, const float2* rr_in,
               long long rr_stride, float2* rr_out, float2* x, bool assign, const float* a, float* r32,

@@ -67,12 +67,15 @@ def test_converged_solves_agree(lib, grid, S):
     assert abs(int(i0.sum()) - int(i1.sum())) <= 12  # at most two extra refinement steps over the batch
 
 
-def test_z_chunks_and_omega_leave_the_solution(lib):
-    """Forced z chunking changes the launch only (bitwise); another smoother damping
-    changes the iterates but not the converged solution beyond the tolerance."""
-    ref = _solve(lib, 3, 2)
-    for zc in (1, 4, 8):
-        out = _solve(lib, 3, 2, z_chunks=zc)
+@pytest.mark.parametrize("grid", [2, 3])
+def test_z_chunks_and_omega_leave_the_solution(lib, grid):
+    """Forced z chunking changes the launch only (bitwise: the fused restriction's
+    chunks overlap by one plane, the coarse rows shared by two row blocks take exactly
+    two additions); another smoother damping changes the iterates but not the
+    converged solution beyond the tolerance."""
+    ref = _solve(lib, grid, 2)
+    for zc in (1, 2, 4, 8):
+        out = _solve(lib, grid, 2, z_chunks=zc)
         assert all(np.array_equal(a, b) for a, b in zip(out[1:], ref[1:]))
-    out = _solve(lib, 3, 2, omega=0.5)
+    out = _solve(lib, grid, 2, omega=0.5)
     assert out[0] == 0 and _rel(out[1], ref[1]) <= 1e-7 and _rel(out[2], ref[2]) <= 1e-7
