@@ -746,18 +746,21 @@ __global__ void __launch_bounds__(256, 3) k_slab(SlabArgs A) {
                 for (int v = 0; v < 2; ++v)
 #pragma unroll
                   for (int u = 0; u < 2; ++u) pxy[v][u] = two_sum(C[0][i + u][t + v], C[1][i + u][t + v]);
-                float S8 = 0.f, E8 = 0.f;
+                float S8 = pxy[0][0].h, E8 = pxy[0][0].l;  // the first pair enters exactly
 #pragma unroll
                 for (int v = 0; v < 2; ++v)
 #pragma unroll
                   for (int u = 0; u < 2; ++u) {
+                    if (v == 0 && u == 0) continue;
                     const P2 q = two_sum(S8, pxy[v][u].h);
                     S8 = q.h;
                     E8 += q.l + pxy[v][u].l;
                   }
-                float S = 0.f, cmp = 0.f;
                 ctr[t][i] = W[i + 1][t + 1];
-                res_term<false>(S, cmp, P2{4.f * S8, 4.f * E8}, W[i + 1][t + 1]);
+                // the centre term starts the sum: its exact product split is (S, cmp)
+                const float c8h = 4.f * S8, c8l = 4.f * E8;
+                float S = __fmul_rn(c8h, W[i + 1][t + 1]);
+                float cmp = __fmaf_rn(c8l, W[i + 1][t + 1], __fmaf_rn(c8h, W[i + 1][t + 1], -S));
 #pragma unroll
                 for (int v = 0; v < 2; ++v)
 #pragma unroll
@@ -1000,10 +1003,11 @@ void slab_apply(const float* z, const float* pold, float* pnew, const float* a, 
 }
 
 // FP32 operations per interior node of the refinement step as written (no sharing
-// between nodes): 12 exact cell-pair sums (6 each), the 8-cell sum (28), 13 compensated
-// products with a pair coefficient (11 each) and 8 with a single cell (10 each), the
-// scaling and subtraction (16), r.r and the pair update of x (10)
-constexpr double kResOpsPerNode = 12 * 6 + 28 + 13 * 11 + 8 * 10 + 16 + 10;
+// between nodes): 12 exact cell-pair sums (6 each), the 8-cell sum (21), the centre
+// product that starts the sum (4), 12 compensated products with a pair coefficient (11
+// each) and 8 with a single cell (10 each), the scaling and subtraction (16), r.r and the
+// pair update of x (10)
+constexpr double kResOpsPerNode = 12 * 6 + 21 + 4 + 12 * 11 + 8 * 10 + 16 + 10;
 
 void slab_res(const float* d, const float* p, bool d_zero, const SolveScalars* sci, const float2* rr_in,
               long long rr_stride, float2* rr_out, float2* x, bool assign, const float* a, float* r32,
