@@ -79,7 +79,7 @@ struct SlabArgs {
   const float* ec;    // POST: coarse correction on grid N/2
   const void* a;      // cell coefficient (TA)
   float* out0;        // APPLY: q   POST: z   RES: r32
-  float* out1;        // APPLY: p_new   PREU: r_new
+  float* out1;        // APPLY: p_new (null on the first APPLY: p = z is not stored)   PREU: r_new
   float* x;           // APPLYX: solution updated with alpha_prev p_old
   double* partial;    // [S][by * nseg]
   const SolveScalars* sc;
@@ -486,7 +486,8 @@ __global__ void __launch_bounds__(256, 3) k_slab(SlabArgs A) {
   const int own0 = (ly0 + 1) * N1 + xw + 1;  // raw index of node (i = 0, t = 0) without the shift
   const int cwin = ly0 * N + xw;             // cell slab index of the window's first cell
   float* out0 = L::kRestr ? nullptr : A.out0 + s * kNodes;
-  float* out1 = (kApply || MODE == SL_PREU) ? A.out1 + s * kNodes : nullptr;
+  // APPLY with out1 null: the first p equals z and is not stored (the caller reads z)
+  float* out1 = ((kApply || MODE == SL_PREU) && A.out1 != nullptr) ? A.out1 + s * kNodes : nullptr;
   float* xg = (MODE == SL_APPLYX) ? A.x + s * kNodes : nullptr;
   // bit t RX + i: node (i, t) is interior (the others, x = N or y = N, are written 0)
   unsigned okb = 0;
@@ -857,7 +858,7 @@ __global__ void __launch_bounds__(256, 3) k_slab(SlabArgs A) {
             const float pv = ctr[t][i];  // 0 off the interior (derived with the mask)
             const float qv = ok ? ax : 0.f;
             out0[g] = qv;
-            out1[g] = pv;
+            if (MODE == SL_APPLYX || out1 != nullptr) out1[g] = pv;
             red = fmaf(pv, qv, red);
             if (MODE == SL_APPLYX) xg[g] = ok ? xv[t][i] + alpha * o1[own] : 0.f;
           } else if (MODE == SL_PRE) {
@@ -999,7 +1000,7 @@ void slab_apply(const float* z, const float* pold, float* pnew, const float* a, 
   if (with_x)
     dispatch<float, SL_APPLYX>(N, "apply_f32", sbytes(N, bt.n, x_first ? 5 : 6, 1, 4), A, bt, st);
   else
-    dispatch<float, SL_APPLY>(N, "apply_f32", sbytes(N, bt.n, first ? 3 : 4, 1, 4), A, bt, st);
+    dispatch<float, SL_APPLY>(N, "apply_f32", sbytes(N, bt.n, (first ? 3 : 4) - (pnew ? 0 : 1), 1, 4), A, bt, st);
 }
 
 // FP32 operations per interior node of the refinement step as written (no sharing

@@ -699,7 +699,7 @@ void build_hierarchy_mixed(SolverBufs& B, const __nv_bfloat16* abf, double omega
 // r_new = r0 - alpha fuse_q (written to r_new) and the V-cycle runs on r_new.
 template <typename T, typename TA0>
 static int vcycle(SolverBufs& B, const T* r0, const TA0* a0, const SolveScalars* sc, T omega, cudaStream_t st,
-                  const T* fuse_q = nullptr, T* r_new = nullptr) {
+                  const T* fuse_q = nullptr, T* r_new = nullptr, T* z0 = nullptr) {
   const int S = B.S, J = B.J;
   const int n = B.n_act;            // samples launched (the active ones when compacted)
   const int* act = B.actp;
@@ -768,7 +768,8 @@ static int vcycle(SolverBufs& B, const T* r0, const TA0* a0, const SolveScalars*
     const int Nj = B.N >> j;
     const bool fine = j == 0;
     if (fine && tiled) {
-      tiled_post<T, TA0>(rfine, a0, (const T*)B.dinv[0], (const T*)B.vt[1], (T*)B.vt[0], B.partial, sc, Nj, bt, st);
+      tiled_post<T, TA0>(rfine, a0, (const T*)B.dinv[0], (const T*)B.vt[1], z0 ? z0 : (T*)B.vt[0], B.partial, sc, Nj,
+                         bt, st);
       return tiled_blocks_per_sample(Nj, S, (int)sizeof(T), uses_slab(B, Nj, (int)sizeof(T)));
     }
     if (!fine && tiled && Nj >= kTiledMinN) {
@@ -907,21 +908,35 @@ static cudaError_t pcg_inner_fused(SolverBufs& B, const float* a32, const __nv_b
   const long long nodes = nodes_of(N);
   const float omega = (float)prm.omega;
   float* rb[2] = {r, (float*)B.r2};
-  float* pb[2] = {(float*)B.p, (float*)B.vx[0]};
-  int rc = 0, pc = 0;
   float* q = (float*)B.q;
-  const float* z = (const float*)B.vt[0];
+  // z and p rotate through three vectors: a new p never overwrites the z or the old p
+  // it is formed from, and the V-cycle's z never overwrites the p the next pass reads.
+  // With the slab passes the first p equals z and is not stored (p aliases z).
+  float* const vb[3] = {(float*)B.vt[0], (float*)B.p, (float*)B.vx[0]};
+  const bool alias_first = uses_slab(B, N, 4);
+  auto other = [&](const float* a, const float* b) {
+    for (float* v : vb)
+      if (v != a && v != b) return v;
+    return vb[0];
+  };
+  float* z = vb[0];
+  float* pold = vb[1];  // not read by the first pass
   const int napply = tiled_blocks_per_sample(N, S, 4, uses_slab(B, N, 4));
-  int nrz = vcycle<float, __nv_bfloat16>(B, rb[rc], abf, sc, omega, st);
+  int nrz = vcycle<float, __nv_bfloat16>(B, rb[0], abf, sc, omega, st, nullptr, nullptr, z);
   scalar(B, sc, SM_RZ0, 0, 0, st, nrz);
+  int rc = 0;
   for (int it = 0; it < iters; ++it) {
-    float* pold = pb[pc];
-    float* pnew = pb[pc ^ 1];
-    if (it == 0)
-      tiled_apply<float, float>(z, pold, pnew, a32, q, B.partial, sc, N, bt, 1, st);
-    else
+    float* pnew;
+    if (it == 0) {
+      pnew = alias_first ? z : other(z, pold);
+      tiled_apply<float, float>(z, pold, alias_first ? nullptr : pnew, a32, q, B.partial, sc, N, bt, 1, st);
+    } else {
+      pnew = other(z, pold);
       tiled_apply_x(z, pold, pnew, a32, q, x, B.partial, sc, N, bt, st, it == 1);
-    pc ^= 1;
+    }
+    float* znext = z != pnew ? z : other(pnew, pnew);  // z is dead unless it is the new p
+    pold = pnew;
+    z = znext;
     scalar(B, sc, SM_ALPHA, 0, 0, st, napply);
     if (it == iters - 1) {
       if (p_last) {  // the refinement step applies x (+)= x + alpha p itself
@@ -936,7 +951,7 @@ static cudaError_t pcg_inner_fused(SolverBufs& B, const float* a32, const __nv_b
       });
       break;
     }
-    nrz = vcycle<float, __nv_bfloat16>(B, rb[rc], abf, sc, omega, st, q, rb[rc ^ 1]);
+    nrz = vcycle<float, __nv_bfloat16>(B, rb[rc], abf, sc, omega, st, q, rb[rc ^ 1], z);
     rc ^= 1;
     scalar(B, sc, SM_BETA, 0, 0, st, nrz);
   }
