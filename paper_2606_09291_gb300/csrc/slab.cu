@@ -60,7 +60,8 @@ namespace mlsgd {
 
 namespace {
 
-enum SlabMode { SL_APPLY = 0, SL_PRE = 1, SL_POST = 2, SL_PREU = 4, SL_APPLYX = 5, SL_RES = 6 };
+// SL_APPLYXL: APPLYX as the inner solve's last pass, which needs p.q but not q
+enum SlabMode { SL_APPLY = 0, SL_PRE = 1, SL_POST = 2, SL_PREU = 4, SL_APPLYX = 5, SL_RES = 6, SL_APPLYXL = 7 };
 constexpr int kSegPlanes = 8;  // partial-sum segment (the same as tiled.cu's kZSeg)
 // Raw plane slots: plane m of a chunk (j = m - (kbeg-1)) lives in slot j % 4 of the
 // node vectors whose own-node values the epilogue reads, and in slot j % 3 of D^-1 in
@@ -78,7 +79,7 @@ struct SlabArgs {
   const float* dinv;  // PRE/PREU/POST: omega D^-1 (0 on the boundary)
   const float* ec;    // POST: coarse correction on grid N/2
   const void* a;      // cell coefficient (TA)
-  float* out0;        // APPLY: q   POST: z   RES: r32
+  float* out0;        // APPLY: q (not read by APPLYXL)   POST: z   RES: r32
   float* out1;        // APPLY: p_new (null on the first APPLY: p = z is not stored)   PREU: r_new
   float* x;           // APPLYX: solution updated with alpha_prev p_old
   double* partial;    // [S][by * nseg]
@@ -167,7 +168,7 @@ struct SlabSmem {
   // PRE/PREU: the x-restricted first row of every warp, [plane parity][8 warps][32 lanes]
   static constexpr bool kRestr = MODE == SL_PRE || MODE == SL_PREU;
   static constexpr size_t hx =
-      xpre + (MODE == SL_RES ? 2 * sizeof(float2) : (MODE == SL_APPLYX ? sizeof(float) : 0)) * 256 * G::RX * G::RY;
+      xpre + (MODE == SL_RES ? 2 * sizeof(float2) : (MODE == SL_APPLYX || MODE == SL_APPLYXL ? sizeof(float) : 0)) * 256 * G::RX * G::RY;
   static constexpr size_t total = hx + (kRestr ? sizeof(float) * 512 : 0);
   static_assert((sizeof(TA) == 4 && (MODE == SL_PREU || MODE == SL_POST)) || total + 1024 <= 228 * 1024 / 3,
                 "three blocks per SM");
@@ -236,7 +237,8 @@ __global__ void __launch_bounds__(256, 3) k_slab(SlabArgs A) {
   using G = SlabGeo<N>;
   using L = SlabSmem<N, TA, MODE>;
   constexpr int RX = G::RX, RY = G::RY, TYT = G::TYT, N1 = G::N1, NR = G::NR, XS = G::XS;
-  constexpr bool kApply = MODE == SL_APPLY || MODE == SL_APPLYX;
+  constexpr bool kX = MODE == SL_APPLYX || MODE == SL_APPLYXL;  // APPLY with the x update
+  constexpr bool kApply = MODE == SL_APPLY || kX;
   constexpr bool kPost = MODE == SL_POST;
   constexpr bool kRes = MODE == SL_RES;
   constexpr int NV = L::NV;
@@ -299,7 +301,7 @@ __global__ void __launch_bounds__(256, 3) k_slab(SlabArgs A) {
   const float scale = A.scale;
   float beta = 0.f, alpha = 0.f;
   if (kApply && !A.first) beta = (float)A.sc[s].beta;
-  if (MODE == SL_APPLYX || MODE == SL_PREU) alpha = (float)A.sc[s].alpha;
+  if (kX || MODE == SL_PREU) alpha = (float)A.sc[s].alpha;
   if (kRes) alpha = (float)A.sci[s].alpha;
   auto vin = [&](int v) {
     return v == 0 ? A.in0 : (v == 1 && (MODE == SL_PREU || kApply || kRes) ? A.in1 : A.dinv);
@@ -488,7 +490,7 @@ __global__ void __launch_bounds__(256, 3) k_slab(SlabArgs A) {
   float* out0 = L::kRestr ? nullptr : A.out0 + s * kNodes;
   // APPLY with out1 null: the first p equals z and is not stored (the caller reads z)
   float* out1 = ((kApply || MODE == SL_PREU) && A.out1 != nullptr) ? A.out1 + s * kNodes : nullptr;
-  float* xg = (MODE == SL_APPLYX) ? A.x + s * kNodes : nullptr;
+  float* xg = kX ? A.x + s * kNodes : nullptr;
   // bit t RX + i: node (i, t) is interior (the others, x = N or y = N, are written 0)
   unsigned okb = 0;
 #pragma unroll
@@ -672,7 +674,7 @@ __global__ void __launch_bounds__(256, 3) k_slab(SlabArgs A) {
         if ((okb >> (t * RX + i)) & 1u) cp_async4(xq + t * RX + i, xm + t * N1 + i);
     cp_async_commit();
   };
-  if (MODE == SL_APPLYX && !A.xfirst) prefetch_x(kbeg);
+  if (kX && !A.xfirst) prefetch_x(kbeg);
   // RES: x and rr_in of the own nodes of plane m into xpre, rpre, a plane ahead of their use
   auto prefetch_res = [&](int m) {
     const long long gm = (long long)m * N1 * N1 + gown;
@@ -835,7 +837,7 @@ __global__ void __launch_bounds__(256, 3) k_slab(SlabArgs A) {
       const Acc& acc = accB;
       const Acc& ctr = ctrk;
       float xv[RY][RX];  // APPLYX: x of the own nodes (0 where not interior or not read)
-      if constexpr (MODE == SL_APPLYX) {
+      if constexpr (kX) {
         if (!A.xfirst) cp_async_wait_all();
 #pragma unroll
         for (int t = 0; t < RY; ++t)
@@ -857,10 +859,10 @@ __global__ void __launch_bounds__(256, 3) k_slab(SlabArgs A) {
           if (kApply) {
             const float pv = ctr[t][i];  // 0 off the interior (derived with the mask)
             const float qv = ok ? ax : 0.f;
-            out0[g] = qv;
-            if (MODE == SL_APPLYX || out1 != nullptr) out1[g] = pv;
+            if (MODE != SL_APPLYXL) out0[g] = qv;
+            if (kX || out1 != nullptr) out1[g] = pv;
             red = fmaf(pv, qv, red);
-            if (MODE == SL_APPLYX) xg[g] = ok ? xv[t][i] + alpha * o1[own] : 0.f;
+            if (kX) xg[g] = ok ? xv[t][i] + alpha * o1[own] : 0.f;
           } else if (MODE == SL_PRE) {
             tv[t][i] = ok ? o0[own] - ax : 0.f;
           } else if (MODE == SL_PREU) {
@@ -875,7 +877,7 @@ __global__ void __launch_bounds__(256, 3) k_slab(SlabArgs A) {
           }
         }
       }
-      if constexpr (MODE == SL_APPLYX) {  // after the stores that used this plane's xq
+      if constexpr (kX) {  // after the stores that used this plane's xq
         if (!A.xfirst && k < kend) prefetch_x(k + 1);
       }
       if constexpr (L::kRestr) {  // x-restriction of the thread's rows at coarse column cx
@@ -997,7 +999,9 @@ void slab_apply(const float* z, const float* pold, float* pnew, const float* a, 
   A.err = bt.err;
   A.first = first ? 1 : 0;
   A.xfirst = x_first ? 1 : 0;
-  if (with_x)
+  if (with_x && q == nullptr)  // the last pass of an inner solve: q not stored
+    dispatch<float, SL_APPLYXL>(N, "apply_f32", sbytes(N, bt.n, x_first ? 4 : 5, 1, 4), A, bt, st);
+  else if (with_x)
     dispatch<float, SL_APPLYX>(N, "apply_f32", sbytes(N, bt.n, x_first ? 5 : 6, 1, 4), A, bt, st);
   else
     dispatch<float, SL_APPLY>(N, "apply_f32", sbytes(N, bt.n, (first ? 3 : 4) - (pnew ? 0 : 1), 1, 4), A, bt, st);

@@ -932,7 +932,9 @@ static cudaError_t pcg_inner_fused(SolverBufs& B, const float* a32, const __nv_b
       tiled_apply<float, float>(z, pold, alias_first ? nullptr : pnew, a32, q, B.partial, sc, N, bt, 1, st);
     } else {
       pnew = other(z, pold);
-      tiled_apply_x(z, pold, pnew, a32, q, x, B.partial, sc, N, bt, st, it == 1);
+      // the last pass needs only p.q (for alpha): with the slab passes q is not stored
+      tiled_apply_x(z, pold, pnew, a32, (alias_first && it == iters - 1) ? nullptr : q, x, B.partial, sc, N, bt, st,
+                    it == 1);
     }
     float* znext = z != pnew ? z : other(pnew, pnew);  // z is dead unless it is the new p
     pold = pnew;
