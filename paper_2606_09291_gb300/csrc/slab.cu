@@ -21,7 +21,13 @@
 //     boundaries; they write the interior nodes and, branch-free, the nodes x = N and
 //     y = N of a lane's window (as 0), never x = 0, y = 0 or the planes 0 and N;
 //   * the derived operand plane has an even row stride N + 2, so a lane's window of
-//     RX + 2 columns is read with 8-byte loads when RX = 2.
+//     RX + 2 columns is read with 8-byte loads when RX = 2;
+//   * all passes but RES sum the operator per operand plane: the window of plane
+//     k + 1, read once, completes node plane k, adds the centre part of plane k + 1
+//     and starts plane k + 2 (partial sums and the upper cell plane carried in
+//     registers), so they need one block barrier per plane;
+//   * the first APPLY of an inner solve may leave p unstored (p = z, out1 null) and
+//     APPLYXL, the last APPLYX of an inner solve, stores no q (only p.q is needed).
 // Partial sums (APPLY p.q, POST r.z, RES r.r) are formed per segment of kZSeg interior
 // planes exactly as in tiled.cu (entry seg * by + tile_y per sample).
 //
@@ -32,9 +38,10 @@
 // each warp combines its rows with the first row of the warp above (through shared
 // memory, after the plane's last barrier), and the coarse planes are summed while
 // marching in z.  A chunk computes t on one more plane than it owns (the first plane
-// of the next chunk; nothing of it is stored) so that its last coarse plane is complete; the coarse row at the boundary of
-// two row blocks takes exactly two atomic additions onto a zeroed row (k_zero_seams),
-// so its value does not depend on their order.  Coarse boundary nodes are written 0.
+// of the next chunk; nothing of it is stored) so that its last coarse plane is
+// complete; the coarse row at the boundary of two row blocks takes exactly two atomic
+// additions onto a zeroed row (k_zero_seams), so its value does not depend on their
+// order.  Coarse boundary nodes are written 0.
 //
 // RES is the refinement step of the mixed solver in one pass: the operand is the inner
 // solve's increment inc = d + alpha p, the stencil forms A inc to FP64 accuracy in
@@ -43,7 +50,8 @@
 // step), writes it rounded as the next inner solve's FP32 residual and updates the
 // solution pair x (+)= inc.  Neither rr nor x is read at another block's nodes, so both
 // are updated in place; the recursive residual equals b - A x up to the pair
-// arithmetic's rounding (a few u^2 |A||x| per step, u = 2^-24).
+// arithmetic's rounding (a few u^2 |A||x| per step, u = 2^-24).  The first step also
+// writes x's boundary nodes (0) that the block's rows and planes own.
 //
 // Every wait on an mbarrier is bounded (about a second of SM clock); a wait that
 // runs out sets *err, and the thread then skips its remaining waits and copies but
