@@ -721,7 +721,9 @@ __global__ void __launch_bounds__(256, 3) k_slab(SlabArgs A) {
     {
       // RES: rr_new = rr - A inc to FP64 accuracy in FP32 arithmetic (exact cell-pair
       // sums and products, compensated sums, the scale h/12 and the subtraction as
-      // pairs), r = rr_new rounded, x (+)= inc; the same plane-by-plane order as below
+      // pairs), r = rr_new rounded, x (+)= inc; node plane k from the windows of operand
+      // planes k (first), k - 1 and k + 1 (the pair accumulators leave no registers to
+      // carry partial sums from plane to plane)
       if constexpr (kRes) {
         // cells of the two cell planes around plane k: C[r][cc][cr], cell (xw + cc, row ly0 + cr)
         float C[2][RX + 1][RY + 1];
@@ -731,22 +733,8 @@ __global__ void __launch_bounds__(256, 3) k_slab(SlabArgs A) {
 #pragma unroll
         for (int pl = 0; pl < 3; ++pl) {
           const int order = pl == 0 ? 1 : (pl == 1 ? 0 : 2);  // centre plane first
-          const float* xp = xs + (order == 0 ? xkm : (order == 1 ? xk : xkp)) * G::XPL + ly0 * XS + xw;
           float W[RX + 2][RY + 2];
-#pragma unroll
-          for (int rr = 0; rr < RY + 2; ++rr) {
-            if constexpr (RX == 2) {
-              const float2 a0 = *reinterpret_cast<const float2*>(xp + rr * XS);
-              const float2 a1 = *reinterpret_cast<const float2*>(xp + rr * XS + 2);
-              W[0][rr] = a0.x;
-              W[1][rr] = a0.y;
-              W[2][rr] = a1.x;
-              W[3][rr] = a1.y;
-            } else {
-#pragma unroll
-              for (int c = 0; c < RX + 2; ++c) W[c][rr] = xp[rr * XS + c];
-            }
-          }
+          load_win(order == 0 ? xkm : (order == 1 ? xk : xkp), W);
 #pragma unroll
           for (int t = 0; t < RY; ++t)
 #pragma unroll
