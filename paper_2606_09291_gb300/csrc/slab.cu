@@ -364,14 +364,18 @@ __global__ void __launch_bounds__(256, 3) k_slab(SlabArgs A) {
   // offset modulo 4 of node (0, y0-1, m) of sample s: N+1, (N+1)^2 and (N+1)^3 are 1 mod 4
   auto delta_of = [&](int m) { return (s + m + y0 - 1) & 3; };
 
-  // ---- entries this thread derives: e = tid + 256 j, operand index e + e / N1 (stride N + 2)
+  // ---- entries this thread derives: e = tid + 256 j, in the last, partial round
+  // 256 j + 255 - tid (so that the last warps, not warp 0, which issues the copies, take
+  // them); operand index e + e / N1 (stride N + 2)
+  auto entry = [&](int j) { return j == G::NE - 1 ? 256 * j + 255 - tid : tid + 256 * j; };
+  auto item = [&](int j) { return j == G::NI - 1 ? 256 * j + 255 - tid : tid + 256 * j; };
   // bnd bit j: entry j is a boundary node (x or y on the boundary; the planes 0 and N
   // are handled per plane), derived as 0 whatever the staged vector holds there
   int xo[G::NE];
   unsigned bnd = 0;
 #pragma unroll
   for (int j = 0; j < G::NE; ++j) {
-    const int e = tid + 256 * j;
+    const int e = entry(j);
     const int ly = e / N1, x = e - ly * N1, y = y0 - 1 + ly;
     xo[j] = e + ly;
     if (x == 0 || x == N || y == 0 || y >= N) bnd |= 1u << j;
@@ -383,7 +387,7 @@ __global__ void __launch_bounds__(256, 3) k_slab(SlabArgs A) {
   if (kPost) {
 #pragma unroll
     for (int j = 0; j < G::NI; ++j) {
-      const int it = tid + 256 * j;
+      const int it = item(j);
       const int a = it % G::NC1, b = it / G::NC1;
       ioff[j] = 2 * a + 2 * XS * b;
 #pragma unroll
@@ -408,7 +412,7 @@ __global__ void __launch_bounds__(256, 3) k_slab(SlabArgs A) {
     const unsigned all = (c == 0 || c == G::NC) ? ~0u : cbnd;
 #pragma unroll
     for (int j = 0; j < G::NI; ++j) {
-      const int it = tid + 256 * j;
+      const int it = item(j);
       if (j == G::NI - 1 && it >= G::NC1 * (G::CNR - 1)) break;
       const float* q = cp + it;  // coarse node (a, b) of item it = a + (N/2 + 1) b
       const unsigned mk = all >> (4 * j);
@@ -441,7 +445,7 @@ __global__ void __launch_bounds__(256, 3) k_slab(SlabArgs A) {
     auto each = [&](auto f) {
 #pragma unroll
       for (int j = 0; j < G::NE; ++j) {
-        const int e = tid + 256 * j;
+        const int e = entry(j);
         if (j == G::NE - 1 && e >= NR * N1) break;
         const float v = f(e, xo[j]);
         xp[xo[j]] = ((mask >> j) & 1u) ? 0.f : v;
