@@ -316,8 +316,12 @@ __global__ void __launch_bounds__(256, 3) k_slab(SlabArgs A) {
   };
   bool dead = false;  // a wait of this thread ran out: skip the remaining waits and copies
 
-  // ---- producer (thread 0): plane m into ring slot (m - first) % kRing
+  // ---- producers (threads 0 and 32): plane m into ring slot (m - first) % kRing
   const int first = kbeg - 1;
+  // 64^3: the vectors by thread 0, the cells and coarse planes by thread 32; 32^3: all by
+  // thread 0 (splitting them there costs the APPLY passes register spills)
+  constexpr bool kSplit = N == 64;
+  auto producer = [&] { return tid == 0 || (kSplit && tid == 32); };
   auto span = [&](long long off, int len, int& delta) {  // 16-byte aligned span covering [off, off + len)
     delta = (int)(off & 3);
     return (uint32_t)(4 * ((delta + len + 3) & ~3));
@@ -342,17 +346,21 @@ __global__ void __launch_bounds__(256, 3) k_slab(SlabArgs A) {
     const uint32_t cb0 = c0 ? span(coff0, crows_c * G::NC1, dc) : 0u;  // spans differ with the offset mod 4
     const uint32_t cb1 = c1 ? span(coff1, crows_c * G::NC1, dc) : 0u;
     total += cb0 + cb1;
-    mbar_expect(bar, total);
+    if (!kSplit || tid == 0) {  // the byte count and the node vectors
+      mbar_expect(bar, total);
 #pragma unroll
-    for (int v = 0; v < NV; ++v)
-      if (v < nv)
-        bulk_copy(smem_u32(raw + (L::first_slot(v) + j % L::slots(v)) * G::RAWF), vin(v) + (noff & ~3LL), nb, bar);
-    if (cell) {
-      const long long coff_c = (long long)s * kCells + (long long)m * N * N + (long long)(y0 - 1) * N;
-      bulk_copy(smem_u32((unsigned char*)cs + slot * L::cellb), (const TA*)A.a + coff_c, cb, bar);
+      for (int v = 0; v < NV; ++v)
+        if (v < nv)
+          bulk_copy(smem_u32(raw + (L::first_slot(v) + j % L::slots(v)) * G::RAWF), vin(v) + (noff & ~3LL), nb, bar);
     }
-    if (c0) bulk_copy(smem_u32(craw + ((m >> 1) % 3) * G::CRAWF), A.ec + (coff0 & ~3LL), cb0, bar);
-    if (c1) bulk_copy(smem_u32(craw + (((m >> 1) + 1) % 3) * G::CRAWF), A.ec + (coff1 & ~3LL), cb1, bar);
+    if (!kSplit || tid == 32) {  // thread 32 (warp 1 derives no entry of the partial last round): cells, coarse
+      if (cell) {
+        const long long coff_c = (long long)s * kCells + (long long)m * N * N + (long long)(y0 - 1) * N;
+        bulk_copy(smem_u32((unsigned char*)cs + slot * L::cellb), (const TA*)A.a + coff_c, cb, bar);
+      }
+      if (c0) bulk_copy(smem_u32(craw + ((m >> 1) % 3) * G::CRAWF), A.ec + (coff0 & ~3LL), cb0, bar);
+      if (c1) bulk_copy(smem_u32(craw + (((m >> 1) + 1) % 3) * G::CRAWF), A.ec + (coff1 & ~3LL), cb1, bar);
+    }
   };
   auto wait_plane = [&](int m) {
     const int j = m - first;
@@ -477,7 +485,7 @@ __global__ void __launch_bounds__(256, 3) k_slab(SlabArgs A) {
   // planes first .. first+2 now, first+3 once the prologue has derived plane first
   // (whose D^-1 slot it may reuse); iteration k then copies plane k+3 into the slots of
   // plane k-1 (raw k-1 was last read by compute(k-1), its cells by compute(k))
-  if (tid == 0)
+  if (producer())
     for (int m = first; m <= min(first + kAhead - 1, kend + 1); ++m) issue(m, kPost && m == first);
   wait_plane(first);
   if (kPost) {
@@ -492,7 +500,7 @@ __global__ void __launch_bounds__(256, 3) k_slab(SlabArgs A) {
   wait_plane(kbeg);
   derive(kbeg, xk, 1, false);
   __syncthreads();
-  if (tid == 0 && !dead && first + kAhead <= kend + 1) issue(first + kAhead, false);
+  if (producer() && !dead && first + kAhead <= kend + 1) issue(first + kAhead, false);
 
   // ---- this thread's nodes: x = 1 + RX lane + i, rows y = y0 + RY warp + t
   const int ly0 = RY * warp;                // staged row of the window's first row
@@ -720,7 +728,7 @@ __global__ void __launch_bounds__(256, 3) k_slab(SlabArgs A) {
     // 3-slot vector ring reuses the slot of plane k, last read by derive(k)).
     if constexpr (!kRes) {
       if (L::kRestr && k > kbeg) restrict_plane(k - 1);
-      if (tid == 0 && !dead && k + kAhead <= kend + 1) issue(k + kAhead, false);
+      if (producer() && !dead && k + kAhead <= kend + 1) issue(k + kAhead, false);
     }
     {
       // RES: rr_new = rr - A inc to FP64 accuracy in FP32 arithmetic (exact cell-pair
@@ -924,7 +932,7 @@ __global__ void __launch_bounds__(256, 3) k_slab(SlabArgs A) {
     }
     if constexpr (kRes) {  // RES reads operand planes k-1 .. k+1: a second barrier
       __syncthreads();
-      if (tid == 0 && !dead && k + kAhead <= kend + 1) issue(k + kAhead, false);
+      if (producer() && !dead && k + kAhead <= kend + 1) issue(k + kAhead, false);
     }
     xk = xkp;
     jk3 = jk3p;
