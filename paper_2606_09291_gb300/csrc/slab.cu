@@ -318,10 +318,11 @@ __global__ void __launch_bounds__(256, 3) k_slab(SlabArgs A) {
 
   // ---- producers (threads 0 and 32): plane m into ring slot (m - first) % kRing
   const int first = kbeg - 1;
-  // 64^3: the vectors by thread 0, the cells and coarse planes by thread 32; 32^3: all by
-  // thread 0 (splitting them there costs the APPLY passes register spills)
-  constexpr bool kSplit = N == 64;
-  auto producer = [&] { return tid == 0 || (kSplit && tid == 32); };
+  // 64^3: the node vectors by thread 0 (PREU: the first one; its other two by thread 64),
+  // the cells and coarse planes by thread 32; 32^3: all by thread 0 (splitting them
+  // there, or more ways in the other passes, costs register spills)
+  constexpr bool kSplit = N == 64, kSplit3 = kSplit && MODE == SL_PREU;
+  auto producer = [&] { return tid == 0 || (kSplit && tid == 32) || (kSplit3 && tid == 64); };
   auto span = [&](long long off, int len, int& delta) {  // 16-byte aligned span covering [off, off + len)
     delta = (int)(off & 3);
     return (uint32_t)(4 * ((delta + len + 3) & ~3));
@@ -346,12 +347,19 @@ __global__ void __launch_bounds__(256, 3) k_slab(SlabArgs A) {
     const uint32_t cb0 = c0 ? span(coff0, crows_c * G::NC1, dc) : 0u;  // spans differ with the offset mod 4
     const uint32_t cb1 = c1 ? span(coff1, crows_c * G::NC1, dc) : 0u;
     total += cb0 + cb1;
-    if (!kSplit || tid == 0) {  // the byte count and the node vectors
+    if (!kSplit || tid == 0) {  // the byte count and the node vectors (PREU on 64^3: the first)
       mbar_expect(bar, total);
 #pragma unroll
-      for (int v = 0; v < NV; ++v)
+      for (int v = 0; v < (kSplit3 ? 1 : NV); ++v)
         if (v < nv)
           bulk_copy(smem_u32(raw + (L::first_slot(v) + j % L::slots(v)) * G::RAWF), vin(v) + (noff & ~3LL), nb, bar);
+    }
+    if constexpr (kSplit3) {
+      if (tid == 64) {  // PREU on 64^3: q and omega D^-1
+#pragma unroll
+        for (int v = 1; v < NV; ++v)
+          bulk_copy(smem_u32(raw + (L::first_slot(v) + j % L::slots(v)) * G::RAWF), vin(v) + (noff & ~3LL), nb, bar);
+      }
     }
     if (!kSplit || tid == 32) {  // thread 32 (warp 1 derives no entry of the partial last round): cells, coarse
       if (cell) {
