@@ -318,10 +318,11 @@ __global__ void __launch_bounds__(256, 3) k_slab(SlabArgs A) {
 
   // ---- producers (threads 0 and 32): plane m into ring slot (m - first) % kRing
   const int first = kbeg - 1;
-  // 64^3: the node vectors by thread 0 (PREU: the first one; its other two by thread 64),
-  // the cells and coarse planes by thread 32; 32^3: all by thread 0 (splitting them
-  // there, or more ways in the other passes, costs register spills)
-  constexpr bool kSplit = N == 64, kSplit3 = kSplit && MODE == SL_PREU;
+  // The node vectors by thread 0 (PREU on 64^3: the first one; its other two by thread
+  // 64), the cells and coarse planes by thread 32; the APPLY passes on 32^3: all by
+  // thread 0 (splitting them there, or more ways in the other passes, costs register
+  // spills)
+  constexpr bool kSplit = N == 64 || !kApply, kSplit3 = N == 64 && MODE == SL_PREU;
   auto producer = [&] { return tid == 0 || (kSplit && tid == 32) || (kSplit3 && tid == 64); };
   auto span = [&](long long off, int len, int& delta) {  // 16-byte aligned span covering [off, off + len)
     delta = (int)(off & 3);
